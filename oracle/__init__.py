@@ -1,0 +1,286 @@
+"""ctypes front end of the FP64 CPU oracle (lbm_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the package smoke check and by the
+CPU-baseline leg of bench.py.  The CUDA path never imports it and it never imports the
+CUDA path; the only module both use is `workloads` (seeded inputs, no method arithmetic).
+
+Every function follows the passage cited in lbm_oracle.c.  `maxwell()` is the
+equal-area construction on the Peng-Robinson isotherm (Eq. 49), used to place the
+initial coexisting densities and to check the paper's rho_l ~ 6.5, rho_g ~ 0.38 at
+0.86 Tc (Sec. IV.A).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lbm_oracle.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "liblbm_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class OrcParams(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("bc", C.c_int * 6),
+        ("T_wall", C.c_double * 6),
+        ("hot_dT", C.c_double), ("hot_sigma", C.c_double),
+        ("a", C.c_double), ("b", C.c_double), ("R", C.c_double), ("acentric", C.c_double),
+        ("sigma", C.c_double),
+        ("tau_e", C.c_double), ("tau_v", C.c_double), ("tau_q", C.c_double), ("tau_pi", C.c_double),
+        ("cV", C.c_double), ("d", C.c_double), ("varsigma_q", C.c_double), ("varsigma_pi", C.c_double),
+        ("lambda_mode", C.c_int), ("chi_or_lambda", C.c_double),
+        ("g", C.c_double * 3),
+        ("flow_off", C.c_int), ("thermal_off", C.c_int),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, IEEE arithmetic, OpenMP over z-planes)."""
+    with _lock:
+        if (not force and os.path.exists(_LIB)
+                and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            return _LIB
+        os.makedirs(_LIB_DIR, exist_ok=True)
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=gnu99", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        dp = C.POINTER(C.c_double)
+        L.orc_create.restype = C.c_void_p
+        L.orc_create.argtypes = [C.POINTER(OrcParams)]
+        L.orc_destroy.argtypes = [C.c_void_p]
+        L.orc_init.argtypes = [C.c_void_p, dp, dp, dp]
+        L.orc_step.argtypes = [C.c_void_p, C.c_int]
+        L.orc_moments.argtypes = [C.c_void_p, dp, dp, dp, dp, dp]
+        L.orc_get_pops.argtypes = [C.c_void_p, dp, dp]
+        L.orc_set_pops.argtypes = [C.c_void_p, dp, dp]
+        L.orc_get_diag.argtypes = [C.c_void_p, dp, dp, dp, dp, dp, dp]
+        L.orc_get_rho_ave.restype = C.c_double
+        L.orc_get_rho_ave.argtypes = [C.c_void_p]
+        L.orc_set_rho_ave.argtypes = [C.c_void_p, C.c_double]
+        L.orc_Tc.restype = C.c_double
+        L.orc_Tc.argtypes = [C.POINTER(OrcParams)]
+        L.orc_p_eos.restype = C.c_double
+        L.orc_p_eos.argtypes = [C.POINTER(OrcParams), C.c_double, C.c_double]
+        L.orc_matrix_M.argtypes = [dp]
+        L.orc_matrix_N.argtypes = [dp]
+        L.orc_matrix_Ninv.argtypes = [dp]
+        L.orc_velocities19.argtypes = [C.POINTER(C.c_int)]
+        L.orc_invert.argtypes = [C.c_int, dp, dp]
+        L.orc_collide_node.argtypes = [C.POINTER(OrcParams), dp, dp, dp, C.c_double, dp, dp]
+        L.orc_feq.argtypes = [C.c_double, dp, dp]
+        L.orc_force_pops.argtypes = [C.POINTER(OrcParams), dp, dp, dp, C.c_double, dp]
+        L.orc_num_threads.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _dp(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def params_from_setup(s) -> OrcParams:
+    """Map a workloads.LatticeSetup onto the oracle's parameter struct (its own Tc)."""
+    p = OrcParams()
+    p.nx, p.ny, p.nz = s.nx, s.ny, s.nz
+    for k in range(6):
+        p.bc[k] = int(s.bc[k])
+    p.a, p.b, p.R, p.acentric = s.a, s.b, s.R, s.acentric
+    Tc = lib().orc_Tc(C.byref(p))
+    for k in range(6):
+        p.T_wall[k] = s.T_wall_over_Tc[k] * Tc
+    p.hot_dT = s.hot_dT_over_Tc * Tc
+    p.hot_sigma = s.hot_sigma
+    p.sigma = s.sigma
+    p.tau_e, p.tau_v, p.tau_q, p.tau_pi = s.tau_e, s.tau_v, s.tau_q, s.tau_pi
+    p.cV, p.d, p.varsigma_q, p.varsigma_pi = s.cV, s.d, s.varsigma_q, s.varsigma_pi
+    p.lambda_mode, p.chi_or_lambda = s.lambda_mode, s.chi_or_lambda
+    for k in range(3):
+        p.g[k] = s.gravity[k]
+    p.flow_off, p.thermal_off = s.flow_off, s.thermal_off
+    return p
+
+
+def Tc_of(s) -> float:
+    p = OrcParams()
+    p.a, p.b, p.R, p.acentric = s.a, s.b, s.R, s.acentric
+    return lib().orc_Tc(C.byref(p))
+
+
+def p_eos(s, rho: float, T: float) -> float:
+    p = OrcParams()
+    p.a, p.b, p.R, p.acentric = s.a, s.b, s.R, s.acentric
+    return lib().orc_p_eos(C.byref(p), float(rho), float(T))
+
+
+def maxwell(s, T: float, tol: float = 1e-13):
+    """Coexisting (rho_l, rho_v, p_sat) of Eq. 49 at temperature T by equal areas.
+
+    Solves p(rho_v) = p(rho_l) = p_sat and  int_{rho_v}^{rho_l} (p_sat - p) / rho^2 drho = 0
+    (equal areas in the p - v plane) with scipy's root finder and quadrature.
+    """
+    from scipy.integrate import quad
+    from scipy.optimize import brentq
+
+    P = lambda r: p_eos(s, r, T)
+    # spinodal points: extrema of p(rho) on (0, 1/b)
+    rr = np.linspace(1e-4, 0.999 / s.b, 20001)
+    pp = np.array([P(r) for r in rr])
+    dp = np.diff(pp)
+    idx = np.where(np.sign(dp[1:]) != np.sign(dp[:-1]))[0]
+    if len(idx) < 2:
+        raise ValueError("supercritical temperature: no coexistence")
+    r_max, r_min = rr[idx[0] + 1], rr[idx[1] + 1]
+    p_lo, p_hi = max(P(r_min), 1e-12), P(r_max)
+
+    def roots(ps):
+        rv = brentq(lambda r: P(r) - ps, 0.1 * ps / (s.R * T), r_max)
+        rl = brentq(lambda r: P(r) - ps, r_min, 0.9999 / s.b)
+        return rv, rl
+
+    def area(ps):
+        rv, rl = roots(ps)
+        val, _ = quad(lambda r: (ps - P(r)) / (r * r), rv, rl, epsabs=1e-14, epsrel=1e-13, limit=200)
+        return val
+
+    ps = brentq(area, p_lo * (1 + 1e-9) + 1e-15, p_hi * (1 - 1e-9), xtol=tol * 1e-3, rtol=1e-14)
+    rv, rl = roots(ps)
+    return rl, rv, ps
+
+
+class Oracle:
+    """One FP64 lattice: init(rho, T[, u]) -> step(n) -> moments()."""
+
+    def __init__(self, setup):
+        self.setup = setup
+        self.params = params_from_setup(setup)
+        self.N = setup.n_nodes
+        self.shape = setup.shape
+        self._h = lib().orc_create(C.byref(self.params))
+        if not self._h:
+            raise MemoryError("orc_create failed")
+
+    def close(self):
+        if self._h:
+            lib().orc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def init(self, rho, T, u=None):
+        rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
+        T = np.ascontiguousarray(T, dtype=np.float64).reshape(-1)
+        uu = None if u is None else np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+        rc = lib().orc_init(self._h, _dp(rho), _dp(T), _dp(uu))
+        if rc:
+            raise RuntimeError(f"orc_init rc={rc}")
+
+    def step(self, n: int = 1):
+        rc = lib().orc_step(self._h, int(n))
+        if rc:
+            raise FloatingPointError(f"oracle step failed rc={rc} (non-finite or psi^2 <= 0)")
+
+    def moments(self):
+        out = [np.empty(self.N) for _ in range(5)]
+        rc = lib().orc_moments(self._h, *[_dp(a) for a in out])
+        if rc:
+            raise FloatingPointError(f"oracle moments failed rc={rc}")
+        rho, ux, uy, uz, T = [a.reshape(self.shape) for a in out]
+        return dict(rho=rho, ux=ux, uy=uy, uz=uz, T=T)
+
+    def pops(self):
+        f = np.empty(self.N * 19)
+        g = np.empty(self.N * 7)
+        lib().orc_get_pops(self._h, _dp(f), _dp(g))
+        return f.reshape(self.N, 19), g.reshape(self.N, 7)
+
+    def set_pops(self, f, g):
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)
+        g = np.ascontiguousarray(g, dtype=np.float64).reshape(-1)
+        lib().orc_set_pops(self._h, _dp(f), _dp(g))
+
+    def diag(self):
+        """div u (Eq. 48), grad T (Eq. 45), grad rho, F_m, phi_s, psi of the last step."""
+        N = self.N
+        d = dict(divu=np.empty(N), gradT=np.empty(3 * N), gradrho=np.empty(3 * N),
+                 Fm=np.empty(3 * N), phis=np.empty(N), psi=np.empty(N))
+        lib().orc_get_diag(self._h, _dp(d["divu"]), _dp(d["gradT"]), _dp(d["gradrho"]),
+                           _dp(d["Fm"]), _dp(d["phis"]), _dp(d["psi"]))
+        for k in ("gradT", "gradrho", "Fm"):
+            d[k] = d[k].reshape(self.shape + (3,))
+        for k in ("divu", "phis", "psi"):
+            d[k] = d[k].reshape(self.shape)
+        return d
+
+    @property
+    def rho_ave(self):
+        return lib().orc_get_rho_ave(self._h)
+
+
+def matrices():
+    """M (19x19, rows of Eq. 5), its generic inverse, N and N^-1 (Eqs. 38, 41), velocities."""
+    L = lib()
+    M = np.empty(19 * 19)
+    L.orc_matrix_M(_dp(M))
+    Mi = np.empty(19 * 19)
+    L.orc_invert(19, _dp(M), _dp(Mi))
+    N = np.empty(49)
+    Ni = np.empty(49)
+    L.orc_matrix_N(_dp(N))
+    L.orc_matrix_Ninv(_dp(Ni))
+    e = (C.c_int * 57)()
+    L.orc_velocities19(e)
+    return dict(M=M.reshape(19, 19), Minv=Mi.reshape(19, 19), N=N.reshape(7, 7),
+                Ninv=Ni.reshape(7, 7), e19=np.array(list(e)).reshape(19, 3))
+
+
+def collide_node(setup, f, F, Fm, psi2):
+    p = params_from_setup(setup)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    Fm = np.ascontiguousarray(Fm, dtype=np.float64)
+    fs = np.empty(19)
+    u = np.empty(3)
+    lib().orc_collide_node(C.byref(p), _dp(f), _dp(F), _dp(Fm), float(psi2), _dp(fs), _dp(u))
+    return fs, u
+
+
+def feq(rho, u):
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.empty(19)
+    lib().orc_feq(float(rho), _dp(u), _dp(out))
+    return out
+
+
+def force_pops(setup, F, u, Fm, psi2):
+    p = params_from_setup(setup)
+    out = np.empty(19)
+    lib().orc_force_pops(C.byref(p), _dp(np.ascontiguousarray(F, dtype=np.float64)),
+                         _dp(np.ascontiguousarray(u, dtype=np.float64)),
+                         _dp(np.ascontiguousarray(Fm, dtype=np.float64)), float(psi2), _dp(out))
+    return out
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()

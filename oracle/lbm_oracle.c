@@ -1,0 +1,689 @@
+/*
+ * FP64 CPU oracle of the improved 3D thermal pseudopotential LB model
+ * (Li, Yu & Luo, "Improved three-dimensional thermal multiphase lattice Boltzmann
+ * model for liquid-vapor phase change").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, the package smoke check and the CPU
+ * baseline leg of bench.py load this library.  It shares no code, header, table or
+ * constant with the CUDA path.
+ *
+ * It is the algorithm written out plainly, one node at a time, in the paper's order:
+ *   1. rho = sum f, T = sum g                                  (Eq. 10, Eq. 20)
+ *   2. psi = sqrt(2 (p_EOS - rho cs^2) / (G c^2)), G = -1      (Eq. 8, Peng-Robinson Eq. 49)
+ *   3. F_m = -G psi(x) sum_a w(|e_a|^2) psi(x + e_a) e_a       (Eq. 7)
+ *      F_b = (rho - rho_ave) g                                 (Sec. IV.C buoyancy)
+ *   4. u = (sum e f + F/2) / rho                               (Eq. 10)
+ *   5. m = M f, m* = m - Lambda (m - m_eq) + (I - Lambda/2) S  (Eqs. 3, 5, 6, 9)
+ *      f* = M^-1 m*                                            (Eq. 4)
+ *   6. div u from the m_4 non-equilibrium                      (Eq. 48)
+ *   7. n = N g, grad T = -(n_1..3 - 0) / (varsigma_T cs_T^2)    (Eqs. 38, 45)
+ *   8. phi_s = (chi grad(rho cV)/(rho cV) - u).grad T
+ *              - T/(rho cV) (dp/dT)_rho div u                  (Eq. 18, (dp/dT) ~ rho R/(1-b rho))
+ *   9. Q = w (3/2 phi_s(t) - 1/2 phi_s(t-1))                   (Eqs. 23-24, C = w phi_s)
+ *  10. n* = n - Gamma (n - n_eq), g+ = N^-1 n* + Q             (Eqs. 39-43)
+ *  11. streaming (push, Eq. 4) with halfway bounce-back (Eq. 50) for f and
+ *      anti-bounce-back (Eq. 51) for g at wall faces.
+ *
+ * M is not printed in the paper; its rows are the raw polynomial velocity moments
+ * that the equilibrium moments of Eq. 5 and the force moments of Eq. 9 imply, in the
+ * order of Eq. 5.  M^-1 is obtained by a generic Gauss-Jordan elimination.  N and
+ * N^-1 are the printed matrices of Eqs. 38 and 41.
+ *
+ * Readings where the paper is silent (each also listed in the design notes):
+ *  - c = dt = dx = 1, cs^2 = 1/3, G = -1.
+ *  - Tc = 0.0778 a / (0.45724 b R) (the paper's rounded PR constants, Eq. 49 text).
+ *  - Eq. 48 is used at every node; Eq. 45 with the local varsigma_T.
+ *  - Q at the first step uses C(t-1) := C(t).
+ *  - rho_ave used at step t is the FP64 mean of rho at step t-1 (at step 0 the
+ *    initial mean).
+ *  - Solid / outflow neighbours of the psi and grad-rho stencils take the value of
+ *    their fluid mirror image across the face (neutral wetting).
+ *  - Outflow face: f unknowns copied from the layer inside (zero gradient), g by
+ *    Eq. 51 with T fixed at the face temperature.
+ *  - Bottom-face hot spot: T_w(x,y) = T_wall[-z] + dT exp(-((x-nx/2)^2+(y-ny/2)^2)/(2 s^2)).
+ *
+ * Storage is node-major: f[node*19 + a], g[node*7 + a], node = x + nx (y + ny z).
+ */
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define Q19 19
+#define Q7 7
+
+enum { ORC_PERIODIC = 0, ORC_WALL = 1, ORC_OUTFLOW = 2, ORC_THERMAL_ONLY = 3 };
+
+typedef struct {
+    int nx, ny, nz;
+    int bc[6];               /* faces -x,+x,-y,+y,-z,+z */
+    double T_wall[6];
+    double hot_dT, hot_sigma;
+    double a, b, R, acentric;
+    double sigma;            /* thermodynamic-consistency constant of Eq. 9 */
+    double tau_e, tau_v, tau_q, tau_pi;
+    double cV, d, varsigma_q, varsigma_pi;
+    int lambda_mode;         /* 0: constant chi, 1: constant lambda */
+    double chi_or_lambda;
+    double g[3];
+    int flow_off;            /* f frozen, u = 0, phi_s = 0 (pure conduction) */
+    int thermal_off;         /* g frozen (isothermal) */
+} orc_params;
+
+typedef struct {
+    orc_params p;
+    long N;
+    double *f, *g, *fn, *gn;
+    double *fs, *gp;         /* post-collision f*, g+ */
+    double *rho, *T, *psi;
+    double *phis_prev, *phis;
+    double *divu, *gradT, *gradrho, *Fm;   /* diagnostics of the last step */
+    int first;
+    double rho_ave;          /* value the next step uses */
+    double M[Q19 * Q19], Minv[Q19 * Q19];
+    int ok;
+} orc_state;
+
+/* D3Q19 velocities in the order of Eq. 2 */
+static const int EX[Q19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+static const int EY[Q19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+static const int EZ[Q19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+/* D3Q7 velocities (Eq. 21) */
+static const int TX[Q7] = {0, 1, -1, 0, 0, 0, 0};
+static const int TY[Q7] = {0, 0, 0, 1, -1, 0, 0};
+static const int TZ[Q7] = {0, 0, 0, 0, 0, 1, -1};
+
+/* N and N^-1 as printed (Eqs. 38, 41) */
+static const double NMAT[Q7][Q7] = {
+    {1, 1, 1, 1, 1, 1, 1},
+    {0, 1, -1, 0, 0, 0, 0},
+    {0, 0, 0, 1, -1, 0, 0},
+    {0, 0, 0, 0, 0, 1, -1},
+    {0, 1, 1, 1, 1, 1, 1},
+    {0, 1, 1, -1, -1, 0, 0},
+    {0, 1, 1, 0, 0, -1, -1}};
+static const double NINV6[Q7][Q7] = {   /* times 1/6 */
+    {6, 0, 0, 0, -6, 0, 0},
+    {0, 3, 0, 0, 1, 1, 1},
+    {0, -3, 0, 0, 1, 1, 1},
+    {0, 0, 3, 0, 1, -2, 1},
+    {0, 0, -3, 0, 1, -2, 1},
+    {0, 0, 0, 3, 1, 1, -2},
+    {0, 0, 0, -3, 1, 1, -2}};
+
+static const double CS2 = 1.0 / 3.0;
+static const double G_INT = -1.0;   /* interaction strength G of Eqs. 7-8 */
+
+/* ---------------------------------------------------------------- matrices */
+
+/* Row k of M evaluated at velocity (x,y,z): the polynomial whose moment is m_k. */
+static double m_row(int k, double x, double y, double z) {
+    switch (k) {
+    case 0: return 1.0;
+    case 1: return x;
+    case 2: return y;
+    case 3: return z;
+    case 4: return x * x + y * y + z * z;
+    case 5: return 2 * x * x - y * y - z * z;
+    case 6: return y * y - z * z;
+    case 7: return x * y;
+    case 8: return x * z;
+    case 9: return y * z;
+    case 10: return x * x * y;
+    case 11: return x * y * y;
+    case 12: return x * x * z;
+    case 13: return x * z * z;
+    case 14: return y * y * z;
+    case 15: return y * z * z;
+    case 16: return x * x * y * y;
+    case 17: return x * x * z * z;
+    case 18: return y * y * z * z;
+    }
+    return 0.0;
+}
+
+void orc_matrix_M(double* M) {
+    for (int k = 0; k < Q19; ++k)
+        for (int a = 0; a < Q19; ++a) M[k * Q19 + a] = m_row(k, EX[a], EY[a], EZ[a]);
+}
+
+/* generic Gauss-Jordan inverse with partial pivoting; returns 0 on success */
+int orc_invert(int n, const double* A, double* Ainv) {
+    double* w = (double*)malloc(sizeof(double) * n * 2 * n);
+    if (!w) return -1;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < 2 * n; ++j)
+            w[i * 2 * n + j] = j < n ? A[i * n + j] : (j - n == i ? 1.0 : 0.0);
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(w[r * 2 * n + c]) > fabs(w[piv * 2 * n + c])) piv = r;
+        if (fabs(w[piv * 2 * n + c]) < 1e-300) { free(w); return -2; }
+        if (piv != c)
+            for (int j = 0; j < 2 * n; ++j) {
+                double t = w[c * 2 * n + j]; w[c * 2 * n + j] = w[piv * 2 * n + j]; w[piv * 2 * n + j] = t;
+            }
+        double inv = 1.0 / w[c * 2 * n + c];
+        for (int j = 0; j < 2 * n; ++j) w[c * 2 * n + j] *= inv;
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            double fct = w[r * 2 * n + c];
+            if (fct == 0.0) continue;
+            for (int j = 0; j < 2 * n; ++j) w[r * 2 * n + j] -= fct * w[c * 2 * n + j];
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) Ainv[i * n + j] = w[i * 2 * n + n + j];
+    free(w);
+    return 0;
+}
+
+void orc_matrix_N(double* N) {
+    for (int i = 0; i < Q7; ++i) for (int j = 0; j < Q7; ++j) N[i * Q7 + j] = NMAT[i][j];
+}
+void orc_matrix_Ninv(double* Ni) {
+    for (int i = 0; i < Q7; ++i) for (int j = 0; j < Q7; ++j) Ni[i * Q7 + j] = NINV6[i][j] / 6.0;
+}
+void orc_velocities19(int* e) { for (int a = 0; a < Q19; ++a) { e[3*a] = EX[a]; e[3*a+1] = EY[a]; e[3*a+2] = EZ[a]; } }
+
+/* ---------------------------------------------------------------- thermodynamics */
+
+/* Peng-Robinson constants: a = 0.45724 R^2 Tc^2/pc and b = 0.0778 R Tc/pc (Eq. 49 text) */
+double orc_Tc(const orc_params* p) { return 0.0778 * p->a / (0.45724 * p->b * p->R); }
+
+double orc_p_eos(const orc_params* p, double rho, double T) {
+    double Tc = orc_Tc(p);
+    double om = p->acentric;
+    double kap = 0.37464 + 1.54226 * om - 0.26992 * om * om;
+    double s = 1.0 + kap * (1.0 - sqrt(T / Tc));
+    double theta = s * s;                                        /* vartheta(T) */
+    return rho * p->R * T / (1.0 - p->b * rho)
+         - p->a * theta * rho * rho / (1.0 + 2.0 * p->b * rho - p->b * p->b * rho * rho);
+}
+
+/* (dp/dT)_rho as the paper approximates it in Sec. IV.A */
+static double dpdT(const orc_params* p, double rho) { return rho * p->R / (1.0 - p->b * rho); }
+
+/* ---------------------------------------------------------------- collision pieces */
+
+static void m_equilibrium(double rho, const double u[3], double meq[Q19]) {  /* Eq. 5 */
+    double ux = u[0], uy = u[1], uz = u[2];
+    double u2 = ux * ux + uy * uy + uz * uz;
+    double phi = rho * CS2 * CS2 * (1.0 - 1.5 * u2);
+    meq[0] = rho;
+    meq[1] = rho * ux; meq[2] = rho * uy; meq[3] = rho * uz;
+    meq[4] = rho + rho * u2;
+    meq[5] = rho * (2 * ux * ux - uy * uy - uz * uz);
+    meq[6] = rho * (uy * uy - uz * uz);
+    meq[7] = rho * ux * uy; meq[8] = rho * ux * uz; meq[9] = rho * uy * uz;
+    meq[10] = rho * CS2 * uy + rho * ux * ux * uy;
+    meq[11] = rho * CS2 * ux + rho * uy * uy * ux;
+    meq[12] = rho * CS2 * uz + rho * ux * ux * uz;
+    meq[13] = rho * CS2 * ux + rho * uz * uz * ux;
+    meq[14] = rho * CS2 * uz + rho * uy * uy * uz;
+    meq[15] = rho * CS2 * uy + rho * uz * uz * uy;
+    meq[16] = phi + rho * CS2 * (ux * ux + uy * uy);
+    meq[17] = phi + rho * CS2 * (ux * ux + uz * uz);
+    meq[18] = phi + rho * CS2 * (uy * uy + uz * uz);
+}
+
+static void force_moments(const orc_params* p, const double F[3], const double u[3],
+                          const double Fm[3], double psi2, double S[Q19]) {   /* Eq. 9 */
+    double Fx = F[0], Fy = F[1], Fz = F[2], ux = u[0], uy = u[1], uz = u[2];
+    double Fm2 = Fm[0] * Fm[0] + Fm[1] * Fm[1] + Fm[2] * Fm[2];
+    S[0] = 0.0;
+    S[1] = Fx; S[2] = Fy; S[3] = Fz;
+    S[4] = 2.0 * (Fx * ux + Fy * uy + Fz * uz) + 6.0 * p->sigma * Fm2 / (psi2 * (p->tau_e - 0.5));
+    S[5] = 2.0 * (2 * Fx * ux - Fy * uy - Fz * uz);
+    S[6] = 2.0 * (Fy * uy - Fz * uz);
+    S[7] = Fx * uy + Fy * ux; S[8] = Fx * uz + Fz * ux; S[9] = Fy * uz + Fz * uy;
+    S[10] = CS2 * Fy; S[11] = CS2 * Fx; S[12] = CS2 * Fz;
+    S[13] = CS2 * Fx; S[14] = CS2 * Fz; S[15] = CS2 * Fy;
+    S[16] = 2 * CS2 * (ux * Fx + uy * Fy);
+    S[17] = 2 * CS2 * (ux * Fx + uz * Fz);
+    S[18] = 2 * CS2 * (uy * Fy + uz * Fz);
+}
+
+static void relaxation_rates(const orc_params* p, double L[Q19]) {   /* Eq. 6 */
+    for (int k = 0; k < 4; ++k) L[k] = 1.0;
+    L[4] = 1.0 / p->tau_e;
+    for (int k = 5; k < 10; ++k) L[k] = 1.0 / p->tau_v;
+    for (int k = 10; k < 16; ++k) L[k] = 1.0 / p->tau_q;
+    for (int k = 16; k < 19; ++k) L[k] = 1.0 / p->tau_pi;
+}
+
+/*
+ * MRT collision of one node in moment space (Eq. 3) and back-transform (Eq. 4).
+ * Inputs: f (post-streaming), total force F, interaction force Fm, psi^2.
+ * Outputs: f*, and (optionally) u, m4 - m4eq, S4 for Eq. 48.
+ */
+static void collide_f(const orc_state* s, const double f[Q19], const double F[3],
+                      const double Fm[3], double psi2, double fstar[Q19],
+                      double u_out[3], double* rho_out, double* m4neq, double* S4) {
+    const orc_params* p = &s->p;
+    double rho = 0.0, j[3] = {0, 0, 0};
+    for (int a = 0; a < Q19; ++a) {
+        rho += f[a];
+        j[0] += EX[a] * f[a]; j[1] += EY[a] * f[a]; j[2] += EZ[a] * f[a];
+    }
+    double u[3];
+    for (int i = 0; i < 3; ++i) u[i] = (j[i] + 0.5 * F[i]) / rho;       /* Eq. 10 */
+    double m[Q19], meq[Q19], S[Q19], L[Q19], ms[Q19];
+    for (int k = 0; k < Q19; ++k) {
+        double acc = 0.0;
+        for (int a = 0; a < Q19; ++a) acc += s->M[k * Q19 + a] * f[a];
+        m[k] = acc;
+    }
+    m_equilibrium(rho, u, meq);
+    force_moments(p, F, u, Fm, psi2, S);
+    relaxation_rates(p, L);
+    for (int k = 0; k < Q19; ++k) ms[k] = m[k] - L[k] * (m[k] - meq[k]) + (1.0 - 0.5 * L[k]) * S[k];
+    for (int a = 0; a < Q19; ++a) {
+        double acc = 0.0;
+        for (int k = 0; k < Q19; ++k) acc += s->Minv[a * Q19 + k] * ms[k];
+        fstar[a] = acc;
+    }
+    if (u_out) { u_out[0] = u[0]; u_out[1] = u[1]; u_out[2] = u[2]; }
+    if (rho_out) *rho_out = rho;
+    if (m4neq) *m4neq = m[4] - meq[4];
+    if (S4) *S4 = S[4];
+}
+
+/* ---------------------------------------------------------------- lattice helpers */
+
+static long node_index(const orc_params* p, int x, int y, int z) {
+    return (long)x + (long)p->nx * ((long)y + (long)p->ny * (long)z);
+}
+
+/* Neighbour x+e of the psi / grad-rho stencil: wrap periodic axes, mirror at walls. */
+static long stencil_neighbour(const orc_params* p, int x, int y, int z, int ex, int ey, int ez) {
+    int c[3] = {x + ex, y + ey, z + ez};
+    int n[3] = {p->nx, p->ny, p->nz};
+    for (int k = 0; k < 3; ++k) {
+        if (c[k] >= 0 && c[k] < n[k]) continue;
+        int face = 2 * k + (c[k] < 0 ? 0 : 1);
+        int bc = p->bc[face];
+        if (bc == ORC_PERIODIC || bc == ORC_THERMAL_ONLY) c[k] = (c[k] + n[k]) % n[k];
+        else c[k] = c[k] < 0 ? -1 - c[k] : 2 * n[k] - 1 - c[k];   /* mirror image */
+    }
+    return node_index(p, c[0], c[1], c[2]);
+}
+
+static double wall_T(const orc_params* p, int face, int x, int y) {
+    double T = p->T_wall[face];
+    if (face == 4 && p->hot_dT != 0.0) {
+        double dx = x - 0.5 * p->nx, dy = y - 0.5 * p->ny;
+        T += p->hot_dT * exp(-(dx * dx + dy * dy) / (2.0 * p->hot_sigma * p->hot_sigma));
+    }
+    return T;
+}
+
+static int opposite19(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
+static int opposite7(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
+
+/* ---------------------------------------------------------------- API */
+
+orc_state* orc_create(const orc_params* p) {
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return NULL;
+    orc_state* s = (orc_state*)calloc(1, sizeof(orc_state));
+    if (!s) return NULL;
+    s->p = *p;
+    s->N = (long)p->nx * p->ny * p->nz;
+    long N = s->N;
+    s->f = (double*)malloc(sizeof(double) * N * Q19);
+    s->fn = (double*)malloc(sizeof(double) * N * Q19);
+    s->fs = (double*)malloc(sizeof(double) * N * Q19);
+    s->g = (double*)malloc(sizeof(double) * N * Q7);
+    s->gn = (double*)malloc(sizeof(double) * N * Q7);
+    s->gp = (double*)malloc(sizeof(double) * N * Q7);
+    s->rho = (double*)malloc(sizeof(double) * N);
+    s->T = (double*)malloc(sizeof(double) * N);
+    s->psi = (double*)malloc(sizeof(double) * N);
+    s->phis_prev = (double*)malloc(sizeof(double) * N);
+    s->phis = (double*)malloc(sizeof(double) * N);
+    s->divu = (double*)malloc(sizeof(double) * N);
+    s->gradT = (double*)malloc(sizeof(double) * N * 3);
+    s->gradrho = (double*)malloc(sizeof(double) * N * 3);
+    s->Fm = (double*)malloc(sizeof(double) * N * 3);
+    if (!s->f || !s->fn || !s->fs || !s->g || !s->gn || !s->gp || !s->rho || !s->T || !s->psi ||
+        !s->phis_prev || !s->phis || !s->divu || !s->gradT || !s->gradrho || !s->Fm) {
+        return NULL;
+    }
+    orc_matrix_M(s->M);
+    if (orc_invert(Q19, s->M, s->Minv) != 0) return NULL;
+    s->first = 1;
+    s->ok = 1;
+    return s;
+}
+
+void orc_destroy(orc_state* s) {
+    if (!s) return;
+    free(s->f); free(s->fn); free(s->fs); free(s->g); free(s->gn); free(s->gp);
+    free(s->rho); free(s->T); free(s->psi); free(s->phis_prev); free(s->phis);
+    free(s->divu); free(s->gradT); free(s->gradrho); free(s->Fm);
+    free(s);
+}
+
+/* f = M^-1 m_eq(rho, u0), g = w T (w_0 = 1-d, w_1..6 = d/6, Sec. III.B) */
+int orc_init(orc_state* s, const double* rho, const double* T, const double* u) {
+    const orc_params* p = &s->p;
+    double w7[Q7];
+    w7[0] = 1.0 - p->d;
+    for (int a = 1; a < Q7; ++a) w7[a] = p->d / 6.0;
+    double sum = 0.0;
+    for (long i = 0; i < s->N; ++i) {
+        double uu[3] = {0, 0, 0};
+        if (u) { uu[0] = u[i]; uu[1] = u[s->N + i]; uu[2] = u[2 * s->N + i]; }
+        double meq[Q19];
+        m_equilibrium(rho[i], uu, meq);
+        for (int a = 0; a < Q19; ++a) {
+            double acc = 0.0;
+            for (int k = 0; k < Q19; ++k) acc += s->Minv[a * Q19 + k] * meq[k];
+            s->f[i * Q19 + a] = acc;
+        }
+        for (int a = 0; a < Q7; ++a) s->g[i * Q7 + a] = w7[a] * T[i];
+        sum += rho[i];
+    }
+    s->rho_ave = sum / (double)s->N;
+    s->first = 1;
+    return 0;
+}
+
+/* rho, T, psi of every node from the current (post-streaming) populations */
+static int macroscopic(orc_state* s) {
+    const orc_params* p = &s->p;
+    long N = s->N;
+    int bad = 0;
+#pragma omp parallel for reduction(| : bad) schedule(static)
+    for (long i = 0; i < N; ++i) {
+        double r = 0.0, t = 0.0;
+        for (int a = 0; a < Q19; ++a) r += s->f[i * Q19 + a];
+        for (int a = 0; a < Q7; ++a) t += s->g[i * Q7 + a];
+        s->rho[i] = r;
+        s->T[i] = t;
+        double arg = 2.0 * (orc_p_eos(p, r, t) - r * CS2) / (G_INT * 1.0);   /* Eq. 8, c = 1 */
+        if (!(arg > 0.0) || !isfinite(r) || !isfinite(t)) bad = 1;
+        s->psi[i] = sqrt(arg);
+    }
+    return bad;
+}
+
+/* per-node force pieces: F_m (Eq. 7) and the isotropic gradient of rho (stencil of Sec. III.C) */
+static void node_forces(const orc_state* s, int x, int y, int z, double Fm[3], double grho[3]) {
+    const orc_params* p = &s->p;
+    long i = node_index(p, x, y, z);
+    double acc[3] = {0, 0, 0}, gr[3] = {0, 0, 0};
+    for (int a = 1; a < Q19; ++a) {
+        int e2 = EX[a] * EX[a] + EY[a] * EY[a] + EZ[a] * EZ[a];
+        double w = e2 == 1 ? 1.0 / 6.0 : 1.0 / 12.0;
+        long j = stencil_neighbour(p, x, y, z, EX[a], EY[a], EZ[a]);
+        acc[0] += w * s->psi[j] * EX[a]; acc[1] += w * s->psi[j] * EY[a]; acc[2] += w * s->psi[j] * EZ[a];
+        gr[0] += w * s->rho[j] * EX[a]; gr[1] += w * s->rho[j] * EY[a]; gr[2] += w * s->rho[j] * EZ[a];
+    }
+    for (int k = 0; k < 3; ++k) {
+        Fm[k] = -G_INT * s->psi[i] * acc[k];
+        grho[k] = gr[k];
+    }
+}
+
+static void push_stream(orc_state* s) {
+    const orc_params* p = &s->p;
+    long N = s->N;
+    int n[3] = {p->nx, p->ny, p->nz};
+    double w7[Q7];
+    w7[0] = 1.0 - p->d;
+    for (int a = 1; a < Q7; ++a) w7[a] = p->d / 6.0;
+    for (long i = 0; i < N * Q19; ++i) s->fn[i] = NAN;
+    for (long i = 0; i < N * Q7; ++i) s->gn[i] = NAN;
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                long i = node_index(p, x, y, z);
+                int c0[3] = {x, y, z};
+                if (!p->flow_off) {
+                    for (int a = 0; a < Q19; ++a) {
+                        int c[3] = {x + EX[a], y + EY[a], z + EZ[a]};
+                        int wall = 0, out = 0;
+                        for (int k = 0; k < 3; ++k) {
+                            if (c[k] >= 0 && c[k] < n[k]) continue;
+                            int bc = p->bc[2 * k + (c[k] < 0 ? 0 : 1)];
+                            if (bc == ORC_PERIODIC || bc == ORC_THERMAL_ONLY) c[k] = (c[k] + n[k]) % n[k];
+                            else if (bc == ORC_WALL) wall = 1;
+                            else out = 1;
+                        }
+                        if (wall) s->fn[i * Q19 + opposite19(a)] = s->fs[i * Q19 + a];     /* Eq. 50 */
+                        else if (!out) s->fn[node_index(p, c[0], c[1], c[2]) * Q19 + a] = s->fs[i * Q19 + a];
+                        /* else: leaves through an outflow face */
+                    }
+                }
+                if (!p->thermal_off) {
+                    for (int a = 0; a < Q7; ++a) {
+                        int c[3] = {x + TX[a], y + TY[a], z + TZ[a]};
+                        int face = -1;
+                        for (int k = 0; k < 3; ++k) {
+                            if (c[k] >= 0 && c[k] < n[k]) continue;
+                            int fc = 2 * k + (c[k] < 0 ? 0 : 1);
+                            if (p->bc[fc] == ORC_PERIODIC) c[k] = (c[k] + n[k]) % n[k];
+                            else face = fc;
+                        }
+                        if (face >= 0) {   /* Eq. 51, anti-bounce-back with the face temperature */
+                            double Tw = wall_T(p, face, c0[0], c0[1]);
+                            s->gn[i * Q7 + opposite7(a)] = -s->gp[i * Q7 + a] + 2.0 * w7[a] * Tw;
+                        } else {
+                            s->gn[node_index(p, c[0], c[1], c[2]) * Q7 + a] = s->gp[i * Q7 + a];
+                        }
+                    }
+                }
+            }
+    /* outflow faces: unknown incoming f copied from the layer inside (zero normal gradient) */
+    if (!p->flow_off) {
+        for (int z = 0; z < p->nz; ++z)
+            for (int y = 0; y < p->ny; ++y)
+                for (int x = 0; x < p->nx; ++x) {
+                    long i = node_index(p, x, y, z);
+                    for (int a = 0; a < Q19; ++a) {
+                        if (!isnan(s->fn[i * Q19 + a])) continue;
+                        int c[3] = {x, y, z};
+                        int src[3] = {x - EX[a], y - EY[a], z - EZ[a]};
+                        for (int k = 0; k < 3; ++k) {
+                            if (src[k] >= 0 && src[k] < n[k]) continue;
+                            int bc = p->bc[2 * k + (src[k] < 0 ? 0 : 1)];
+                            if (bc == ORC_OUTFLOW) c[k] += src[k] < 0 ? 1 : -1;
+                        }
+                        s->fn[i * Q19 + a] = s->fn[node_index(p, c[0], c[1], c[2]) * Q19 + a];
+                    }
+                }
+    }
+    if (p->flow_off) memcpy(s->fn, s->f, sizeof(double) * N * Q19);
+    if (p->thermal_off) memcpy(s->gn, s->g, sizeof(double) * N * Q7);
+    double* t;
+    t = s->f; s->f = s->fn; s->fn = t;
+    t = s->g; s->g = s->gn; s->gn = t;
+}
+
+/* one time step; returns 0, or -5 when a non-finite value or psi^2 <= 0 appears */
+static int step_once(orc_state* s) {
+    const orc_params* p = &s->p;
+    long N = s->N;
+    if (macroscopic(s)) return -5;
+    double rho_ave = s->rho_ave;
+    double sum = 0.0;
+    for (long i = 0; i < N; ++i) sum += s->rho[i];
+    double w7[Q7];
+    w7[0] = 1.0 - p->d;
+    for (int a = 1; a < Q7; ++a) w7[a] = p->d / 6.0;
+    const double csT2 = p->d / 3.0;
+    double Gam_q = 1.0 / p->varsigma_q, Gam_pi = 1.0 / p->varsigma_pi;
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                long i = node_index(p, x, y, z);
+                double rho = s->rho[i], T = s->T[i];
+                double Fm[3], grho[3], F[3];
+                node_forces(s, x, y, z, Fm, grho);
+                for (int k = 0; k < 3; ++k) F[k] = Fm[k] + (rho - rho_ave) * p->g[k];
+                double psi2 = s->psi[i] * s->psi[i];
+                double u[3], rr, m4neq, S4;
+                collide_f(s, &s->f[i * Q19], F, Fm, psi2, &s->fs[i * Q19], u, &rr, &m4neq, &S4);
+                /* Eq. 48 */
+                double Fu = F[0] * u[0] + F[1] * u[1] + F[2] * u[2];
+                double divu = (-m4neq / p->tau_e + (1.0 - 0.5 / p->tau_e) * S4 - 2.0 * Fu) / (2.0 * rho * CS2);
+                /* thermal moments, Eq. 38 */
+                double nm[Q7];
+                for (int k = 0; k < Q7; ++k) {
+                    double acc = 0.0;
+                    for (int a = 0; a < Q7; ++a) acc += NMAT[k][a] * s->g[i * Q7 + a];
+                    nm[k] = acc;
+                }
+                double chi = p->lambda_mode ? p->chi_or_lambda / (rho * p->cV) : p->chi_or_lambda;
+                double vsT = chi / csT2 + 0.5;     /* chi = (varsigma_T - 0.5) cs_T^2 dt */
+                double gT[3];
+                for (int k = 0; k < 3; ++k) gT[k] = -(nm[1 + k] - 0.0) / (vsT * csT2);   /* Eq. 45 */
+                /* Eq. 18 with cV constant: grad(rho cV)/(rho cV) = grad rho / rho */
+                double phis = 0.0;
+                if (!p->flow_off) {
+                    for (int k = 0; k < 3; ++k) phis += (chi * grho[k] / rho - u[k]) * gT[k];
+                    phis -= T / (rho * p->cV) * dpdT(p, rho) * divu;
+                } else {
+                    u[0] = u[1] = u[2] = 0.0;
+                    divu = 0.0;
+                }
+                double phis_old = s->first ? phis : s->phis_prev[i];
+                /* Eq. 42 equilibrium moments and Eq. 43 rates */
+                double neq[Q7] = {T, 0.0, 0.0, 0.0, 3.0 * csT2 * T, 0.0, 0.0};
+                double Gm[Q7] = {1.0, 1.0 / vsT, 1.0 / vsT, 1.0 / vsT, Gam_q, Gam_pi, Gam_pi};
+                double ns[Q7];
+                for (int k = 0; k < Q7; ++k) ns[k] = nm[k] - Gm[k] * (nm[k] - neq[k]);    /* Eq. 39 */
+                for (int a = 0; a < Q7; ++a) {
+                    double acc = 0.0;
+                    for (int k = 0; k < Q7; ++k) acc += NINV6[a][k] / 6.0 * ns[k];
+                    double Qa = 1.5 * w7[a] * phis - 0.5 * w7[a] * phis_old;             /* Eq. 23 */
+                    s->gp[i * Q7 + a] = acc + Qa;                                        /* Eq. 40 */
+                }
+                s->phis[i] = phis;
+                s->divu[i] = divu;
+                for (int k = 0; k < 3; ++k) {
+                    s->gradT[3 * i + k] = gT[k];
+                    s->gradrho[3 * i + k] = grho[k];
+                    s->Fm[3 * i + k] = Fm[k];
+                }
+            }
+    push_stream(s);
+    double* t = s->phis_prev; s->phis_prev = s->phis; s->phis = t;
+    s->first = 0;
+    s->rho_ave = sum / (double)N;
+    return 0;
+}
+
+int orc_step(orc_state* s, int nsteps) {
+    for (int k = 0; k < nsteps; ++k) {
+        int rc = step_once(s);
+        if (rc) return rc;
+    }
+    return 0;
+}
+
+/* rho, u = (sum e f + F/2)/rho and T of the current state (F with the rho_ave the next step uses) */
+int orc_moments(orc_state* s, double* rho_o, double* ux, double* uy, double* uz, double* T_o) {
+    const orc_params* p = &s->p;
+    if (macroscopic(s)) return -5;
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) {
+                long i = node_index(p, x, y, z);
+                double Fm[3], grho[3];
+                node_forces(s, x, y, z, Fm, grho);
+                double rho = s->rho[i], j[3] = {0, 0, 0};
+                for (int a = 0; a < Q19; ++a) {
+                    j[0] += EX[a] * s->f[i * Q19 + a];
+                    j[1] += EY[a] * s->f[i * Q19 + a];
+                    j[2] += EZ[a] * s->f[i * Q19 + a];
+                }
+                double u[3];
+                for (int k = 0; k < 3; ++k) {
+                    double F = Fm[k] + (rho - s->rho_ave) * p->g[k];
+                    u[k] = p->flow_off ? 0.0 : (j[k] + 0.5 * F) / rho;
+                }
+                if (rho_o) rho_o[i] = rho;
+                if (ux) ux[i] = u[0];
+                if (uy) uy[i] = u[1];
+                if (uz) uz[i] = u[2];
+                if (T_o) T_o[i] = s->T[i];
+            }
+    return 0;
+}
+
+/* ---------------------------------------------------------------- state access for tests */
+
+void orc_get_pops(const orc_state* s, double* f, double* g) {
+    if (f) memcpy(f, s->f, sizeof(double) * s->N * Q19);
+    if (g) memcpy(g, s->g, sizeof(double) * s->N * Q7);
+}
+void orc_set_pops(orc_state* s, const double* f, const double* g) {
+    if (f) memcpy(s->f, f, sizeof(double) * s->N * Q19);
+    if (g) memcpy(s->g, g, sizeof(double) * s->N * Q7);
+}
+/* diagnostics of the last completed step (pre-streaming values at each node) */
+void orc_get_diag(const orc_state* s, double* divu, double* gradT, double* gradrho,
+                  double* Fm, double* phis, double* psi) {
+    if (divu) memcpy(divu, s->divu, sizeof(double) * s->N);
+    if (gradT) memcpy(gradT, s->gradT, sizeof(double) * s->N * 3);
+    if (gradrho) memcpy(gradrho, s->gradrho, sizeof(double) * s->N * 3);
+    if (Fm) memcpy(Fm, s->Fm, sizeof(double) * s->N * 3);
+    if (phis) memcpy(phis, s->phis_prev, sizeof(double) * s->N);
+    if (psi) memcpy(psi, s->psi, sizeof(double) * s->N);
+}
+double orc_get_rho_ave(const orc_state* s) { return s->rho_ave; }
+void orc_set_rho_ave(orc_state* s, double v) { s->rho_ave = v; }
+
+/* single-node MRT collision for direct checks of Eqs. 3-10 */
+void orc_collide_node(const orc_params* p, const double* f, const double* F, const double* Fm,
+                      double psi2, double* fstar, double* u) {
+    orc_state tmp;
+    memset(&tmp, 0, sizeof(tmp));
+    tmp.p = *p;
+    orc_matrix_M(tmp.M);
+    orc_invert(Q19, tmp.M, tmp.Minv);
+    collide_f(&tmp, f, F, Fm, psi2, fstar, u, NULL, NULL, NULL);
+}
+
+/* equilibrium populations M^-1 m_eq(rho, u) */
+void orc_feq(double rho, const double* u, double* feq) {
+    double M[Q19 * Q19], Mi[Q19 * Q19], meq[Q19];
+    orc_matrix_M(M);
+    orc_invert(Q19, M, Mi);
+    m_equilibrium(rho, u, meq);
+    for (int a = 0; a < Q19; ++a) {
+        double acc = 0.0;
+        for (int k = 0; k < Q19; ++k) acc += Mi[a * Q19 + k] * meq[k];
+        feq[a] = acc;
+    }
+}
+
+/* forcing populations G = M^-1 S (Eq. 9) */
+void orc_force_pops(const orc_params* p, const double* F, const double* u, const double* Fm,
+                    double psi2, double* G) {
+    double M[Q19 * Q19], Mi[Q19 * Q19], S[Q19];
+    orc_matrix_M(M);
+    orc_invert(Q19, M, Mi);
+    force_moments(p, F, u, Fm, psi2, S);
+    for (int a = 0; a < Q19; ++a) {
+        double acc = 0.0;
+        for (int k = 0; k < Q19; ++k) acc += Mi[a * Q19 + k] * S[k];
+        G[a] = acc;
+    }
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
