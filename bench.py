@@ -1,0 +1,368 @@
+"""Throughput benchmark of the lattice update (MLUPS) on the pool-boiling workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
+                    [--kernel auto|two_pass|fused] [--precision fp32|bf16|fp16]
+                    [--workload pool_boiling|evaporation|static_droplet]
+
+A "step" is one lattice time step of the whole update (psi/EOS, interaction and buoyancy
+forces, D3Q19 MRT collision, local div u and grad T, phase-change source, D3Q7 MRT collision,
+streaming with the wall / outflow boundaries) over the 200 x 200 x 300 pool-boiling lattice
+(12.0M nodes).  Prints one JSON line (rank 0).
+
+N > 1 (torchrun): every rank runs an independent replica of the lattice (the update has no
+data-path exchange in this build); a barrier brackets the timed region and the time is the
+max over ranks; value = node updates of all ranks / that time ("scaling": "weak").
+
+--impl reference times the FP64 CPU oracle (the plain restatement of the paper's equations)
+on the host cores, on a bounded sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+BYTES_PER_NODE = {"fp32": 216, "bf16": 112, "fp16": 112}   # algorithmic bytes of one node update
+PREC_CODE = {"fp32": 0, "bf16": 1, "fp16": 2}
+KERNEL_CODE = {"auto": 0, "two_pass": 1, "fused": 2}
+
+
+def workload(name):
+    if name == "pool_boiling":
+        return W.pool_boiling()
+    if name == "evaporation":
+        return W.evaporation()
+    if name == "static_droplet":
+        return W.static_droplet()
+    raise ValueError(name)
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2201_06039_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(name.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel_name, precision, nodes):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        e = d[f"{kernel_name}/{precision}"]
+        if e.get("source_sha") != kernel_source_sha():
+            return None
+        return float(e["dram_bytes_per_node"]) * nodes
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            for k, n in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def init_fields(case):
+    from paper_2201_06039_gb300 import thermo
+    s = case["setup"]
+    Tc = thermo.critical_temperature(s.a, s.b, s.R)
+    Tr = case.get("Tr_drop", case.get("Tr_liquid", 0.86))
+    rl, rv, _ = thermo.coexistence(Tr * Tc, s.a, s.b, s.R, s.acentric)
+    rho, T, u = W.build_fields(case, Tc, rl, rv)
+    return rho.astype(np.float32), T.astype(np.float32)
+
+
+def cpu_baseline_run(case, budget_s=20.0, steps=None, warm=1):
+    """Time the FP64 oracle on a bounded sample: a z-slab of the same workload sized so that one
+    step takes about budget_s / steps seconds (all host cores through OpenMP)."""
+    import oracle
+    s = case["setup"]
+    probe_nodes = 200 * 200 * 10
+    nz_probe = max(2, probe_nodes // (s.nx * s.ny))
+    sub = dict(case)
+    sub_setup = W.LatticeSetup(**{**s.__dict__, "nz": nz_probe})
+    sub["setup"] = sub_setup
+    if "height" in sub:
+        sub["height"] = min(case["height"], nz_probe / 2)
+    Tc = oracle.Tc_of(sub_setup)
+    rl, rv, _ = oracle.maxwell(sub_setup, 0.86 * Tc)
+    rho, T, _ = W.build_fields(sub, Tc, rl, rv)
+    o = oracle.Oracle(sub_setup)
+    o.init(rho, T)
+    o.step(warm)
+    t0 = time.perf_counter()
+    o.step(1)
+    per_step = time.perf_counter() - t0
+    mlups = sub_setup.n_nodes / per_step / 1e6
+    n = steps if steps is not None else max(1, int(budget_s / max(per_step, 1e-3)))
+    n = min(n, 50)
+    t0 = time.perf_counter()
+    o.step(n)
+    dt = time.perf_counter() - t0
+    mlups = sub_setup.n_nodes * n / dt / 1e6
+    o.close()
+    return dict(value=mlups, unit="MLUPS", cores=oracle.num_threads(), kind="oracle",
+                sample=f"{n} steps of a {s.nx}x{s.ny}x{nz_probe} z-slab of the same workload (same "
+                       f"boundaries and parameters), FP64, after {warm + 1} warm-up steps",
+                seconds=dt)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    case = workload(args.workload)
+    import oracle
+    s = case["setup"]
+    total_budget = 150.0
+    per_step_budget = total_budget / max(1, args.steps + args.warmup)
+    # size a z-slab of the workload so that one oracle step fits the per-step budget
+    probe = cpu_baseline_run(case, steps=1, warm=0)
+    nodes = max(s.nx * s.ny * 2, int(probe["value"] * 1e6 * per_step_budget))
+    nz = max(2, min(s.nz, nodes // (s.nx * s.ny)))
+    sub = dict(case)
+    sub_setup = W.LatticeSetup(**{**s.__dict__, "nz": nz})
+    sub["setup"] = sub_setup
+    if "height" in sub:
+        sub["height"] = min(case["height"], nz / 2)
+    Tc = oracle.Tc_of(sub_setup)
+    rl, rv, _ = oracle.maxwell(sub_setup, 0.86 * Tc)
+    rho, T, _ = W.build_fields(sub, Tc, rl, rv)
+    o = oracle.Oracle(sub_setup)
+    o.init(rho, T)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    value = sub_setup.n_nodes * args.steps / dt / 1e6
+    sample = f"each step: one FP64 oracle step of a {s.nx}x{s.ny}x{nz} z-slab of the {case['name']} workload"
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": case["name"], "nodes": case["setup"].n_nodes, "sample_nodes": sub_setup.n_nodes,
+                   "parallelism": "host cores (OpenMP)"},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_mine(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_2201_06039_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2201_06039_gb300 import lbm
+
+    case = workload(args.workload)
+    s = case["setup"]
+    N = s.n_nodes
+    rho, T = init_fields(case)
+    stream = torch.cuda.current_stream()
+    p = lbm.params_from_setup(s, kernel=KERNEL_CODE[args.kernel], precision=PREC_CODE[args.precision],
+                              use_graph=1, check_nonfinite=0)
+    if args.precision != "fp32":
+        p.rho_ref = float(rho.mean())
+        p.T_ref = 0.86 * lbm.lbm_eos_critical(p)[0]
+    lat = lbm.Lattice(p, stream=stream)
+    kernel_name = "fused" if lat.kernel == lbm.LBM_KERNEL_FUSED else "collide"
+
+    # ---- device-resident timing
+    lat.init(torch.from_numpy(rho).cuda(), torch.from_numpy(T).cuda())
+    lat.step(args.warmup)
+    lat.step(args.steps)            # captures the K-step graph outside the timed region
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    e0.record(stream)
+    lat.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    mass, Tsum, _ = lat.totals()
+    finite = math.isfinite(mass) and math.isfinite(Tsum)
+    mlups = N * args.steps * world / (ms * 1e-3) / 1e6
+
+    # ---- per-kernel durations (CUDA events on the lattice's stream) for the roofline
+    kms, kn = lbm.lbm_step_profiled(lat.ctx, max(3, min(50, args.steps)))
+    k_idx = 0 if kernel_name == "fused" else 1
+    k_avg_ms = kms[k_idx] / max(1, kn[k_idx])
+    peak, peak_kind = measured_peaks()
+    bpn = BYTES_PER_NODE[args.precision]
+    achieved = bpn * N / (k_avg_ms * 1e-3) / 1e9
+    traffic = committed_traffic(kernel_name, args.precision, N)
+
+    # ---- end to end through the C-ABI with pinned host buffers (copies inside the timed region)
+    h_rho = torch.from_numpy(rho).pin_memory()
+    h_T = torch.from_numpy(T).pin_memory()
+    outs = [torch.empty(s.shape, dtype=torch.float32).pin_memory() for _ in range(5)]
+
+    def e2e_once():
+        lbm.lbm_init_fields(lat.ctx, h_rho, h_T, None)
+        lbm.lbm_step(lat.ctx, args.steps)
+        lbm.lbm_get_moments(lat.ctx, *outs)
+
+    e2e_once()                      # graph capture for the post-init step count
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_once()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_mlups = N * args.steps * world / e2e_s / 1e6
+
+    launches_per_step = 1 if kernel_name == "fused" else 2
+    line = {
+        "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else f"f32 compute, {args.precision} storage",
+        "data": "synthetic",
+        "config": {"workload": case["name"], "nodes": N, "kernel": kernel_name, "precision": args.precision,
+                   "l2": "no flush: working set %.2f GB > 129 MB L2" % (lbm.lbm_workspace_bytes(p) / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "hbm_gbs_step": bpn * N * args.steps / (ms * 1e-3) / 1e9,
+        "roofline": {"bound": "hbm", "kernel": kernel_name, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "algorithmic_bytes_per_node": bpn, "kernel_avg_ms": k_avg_ms},
+        "e2e": {"value": e2e_mlups, "unit": "MLUPS", "h2d_bytes_per_step": 2 * 4 * N / args.steps,
+                "d2h_bytes_per_step": 5 * 4 * N / args.steps},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "finite": finite,
+    }
+    lat.close()
+    if args.cpu_baseline and rank == 0 and world == 1:
+        line["cpu_baseline"] = {k: v for k, v in cpu_baseline_run(case).items() if k != "seconds"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--kernel", default="auto", choices=list(KERNEL_CODE))
+    ap.add_argument("--precision", default="fp32", choices=list(PREC_CODE))
+    ap.add_argument("--workload", default="pool_boiling")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_mine(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

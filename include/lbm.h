@@ -1,0 +1,157 @@
+/*
+ * C-ABI of the GB300 (sm_103a) implementation of the per-time-step lattice update of
+ * the improved 3D thermal pseudopotential lattice Boltzmann model of
+ * Li, Yu & Luo, "Improved three-dimensional thermal multiphase lattice Boltzmann
+ * model for liquid-vapor phase change" (arXiv 2201.06039).
+ *
+ * One time step is: the D3Q19 MRT pseudopotential LB for density and velocity
+ * (Sec. II, Eqs. 1-10) with the Peng-Robinson equation of state (Sec. IV.A, Eq. 49),
+ * coupled to the D3Q7 MRT temperature LB (Sec. III.C, Eqs. 37-45) whose source
+ * phi_s (Eq. 18, with the second-order time extrapolation of Eqs. 23-24) uses the
+ * local div u of Eq. 48 and the local grad T of Eq. 45, with halfway bounce-back
+ * (Eq. 50) and anti-bounce-back (Eq. 51) walls and the buoyancy force of Sec. IV.C.
+ *
+ * Units are lattice units: c = dx = dt = 1, cs^2 = 1/3, interaction strength G = -1.
+ *
+ * Conventions shared by every call
+ *  - Fields are float32 arrays of nx*ny*nz values, node index x + nx*(y + ny*z)
+ *    (x fastest).  A velocity field is three such planes (ux, uy, uz) back to back.
+ *  - Field pointers may be host or device pointers (told apart with
+ *    cudaPointerGetAttributes).  They are borrowed for the duration of the call only.
+ *  - All device work is enqueued on the stream given in lbm_params.cuda_stream (the
+ *    legacy default stream if NULL).  A context is used by one host thread at a time.
+ *  - Every call returns an lbm_status; LBM_OK is 0, errors are negative.  After an
+ *    error the context stays valid and can be re-initialised with lbm_init_fields.
+ *  - The context owns all device memory it allocates; lbm_destroy frees it.  If
+ *    lbm_params.workspace is non-NULL the state lives there instead (caller-owned,
+ *    at least lbm_workspace_bytes() bytes, 256-byte aligned, device memory), and the
+ *    library allocates nothing for the fields.
+ */
+#ifndef GB300_LBM_H
+#define GB300_LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = -1,      /* invalid argument or parameter (message via lbm_last_error) */
+    LBM_ENOMEM = -2,      /* device or host allocation failed */
+    LBM_ECUDA = -3,       /* a CUDA runtime call failed */
+    LBM_ESTATE = -4,      /* call out of order (e.g. lbm_step before lbm_init_fields) */
+    LBM_ENONFINITE = -5,  /* a non-finite rho/T/psi, or psi^2 <= 0 (Eq. 8 domain) appeared */
+    LBM_ETIMEOUT = -6     /* a bounded device wait gave up */
+} lbm_status;
+
+/* Boundary type of one face of the box (faces ordered -x, +x, -y, +y, -z, +z). */
+typedef enum {
+    LBM_BC_PERIODIC = 0,      /* f and g wrap around */
+    LBM_BC_WALL = 1,          /* f: halfway bounce-back, Eq. 50; g: anti-bounce-back, Eq. 51 */
+    LBM_BC_OUTFLOW = 2,       /* f: zero normal gradient; g: Eq. 51 at T_wall of the face */
+    LBM_BC_THERMAL_ONLY = 3   /* f periodic; g: Eq. 51 at T_wall of the face */
+} lbm_bc;
+
+typedef enum { LBM_FP32 = 0, LBM_BF16_SHIFTED = 1, LBM_FP16_SHIFTED = 2 } lbm_precision;
+
+typedef enum {
+    LBM_KERNEL_AUTO = 0,      /* fastest available variant */
+    LBM_KERNEL_TWO_PASS = 1,  /* psi/EOS kernel, then the stream-collide kernel */
+    LBM_KERNEL_FUSED = 2      /* one z-marching kernel per step (halo recomputation) */
+} lbm_kernel_variant;
+
+typedef struct {
+    int nx, ny, nz;               /* lattice size, each >= 1 */
+    int bc[6];                    /* lbm_bc per face: -x, +x, -y, +y, -z, +z */
+    double T_wall[6];             /* face temperatures of Eq. 51 (absolute, lattice units) */
+    double hot_dT, hot_sigma;     /* -z face: T_w(x,y) = T_wall[4] + hot_dT exp(-r^2/(2 hot_sigma^2)),
+                                     r measured from (nx/2, ny/2); hot_dT = 0 disables */
+    double a, b, R, acentric;     /* Peng-Robinson EOS (Eq. 49); Tc = 0.0778 a / (0.45724 b R) */
+    double sigma;                 /* thermodynamic-consistency constant of Eq. 9 */
+    double tau_e, tau_v, tau_q, tau_pi;     /* relaxation times of Eq. 6 (each > 0.5) */
+    double cV, d, varsigma_q, varsigma_pi;  /* cV of Eq. 18; D3Q7 d (w0 = 1-d, w1..6 = d/6);
+                                               free rates of Eq. 43 */
+    int lambda_mode;              /* 0: chi = chi_or_lambda constant; 1: lambda constant,
+                                     chi = lambda / (rho cV) per node (Sec. IV.A) */
+    double chi_or_lambda;         /* varsigma_T = chi / cs_T^2 + 1/2, cs_T^2 = d/3 */
+    double g[3];                  /* gravity of the buoyancy force F_b = (rho - rho_ave) g */
+    int flow_off;                 /* 1: f frozen, u = 0, phi_s = 0 (pure conduction) */
+    int thermal_off;              /* 1: g frozen (isothermal phase) */
+    int precision;                /* lbm_precision of the stored populations */
+    double rho_ref, T_ref;        /* shifts of 16-bit storage: f - w rho_ref, g - w T_ref */
+    int kernel;                   /* lbm_kernel_variant */
+    int use_graph;                /* 1: lbm_step replays a captured CUDA graph of n steps */
+    int check_nonfinite;          /* 1: lbm_step synchronises and reports LBM_ENONFINITE */
+    void* cuda_stream;            /* borrowed cudaStream_t, NULL = legacy default stream */
+    void* workspace;              /* optional caller-owned device memory (see above) */
+    size_t workspace_bytes;
+} lbm_params;
+
+/* Fill *p with the workload-independent defaults of Sec. IV: tau_e = 1.25, tau_v = 0.8,
+ * tau_q = tau_pi = 1, cV = 5, d = 0.95, varsigma_q = varsigma_pi = 1, a = 2/49, b = 2/21,
+ * R = 1, acentric factor 0.344, all faces periodic, FP32 populations. */
+void lbm_params_default(lbm_params* p);
+
+/* Critical temperature and pressure of the Peng-Robinson EOS with the paper's rounded
+ * constants (Sec. IV.A text after Eq. 49): Tc = 0.0778 a / (0.45724 b R), pc = 0.0778 R Tc / b. */
+int lbm_eos_critical(const lbm_params* p, double* Tc, double* pc);
+
+/* Device bytes the state of a lattice with parameters p needs. */
+size_t lbm_workspace_bytes(const lbm_params* p);
+
+/* Validate p (tau > 0.5, sizes >= 1, outflow faces need >= 2 nodes across, ...), allocate
+ * the state and create a context.  Errors: LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA. */
+int lbm_create(const lbm_params* p, lbm_ctx** out);
+
+/* Set the initial state: f = M^-1 m_eq(rho, u) with the equilibrium moments of Eq. 5,
+ * g = w T (Sec. III.B), phi_s history empty (the first step uses C(t-dt) := C(t) in Eq. 23),
+ * rho_ave = mean of rho.  rho and T are required; u may be NULL (fluid at rest).
+ * Errors: LBM_EINVAL (NULL rho/T), LBM_ECUDA. */
+int lbm_init_fields(lbm_ctx* ctx, const float* rho, const float* T, const float* u);
+
+/* Enqueue n >= 0 time steps (each: Eqs. 7-10, 3-6, 9, 48, 45, 18, 23, 39-43, streaming
+ * of Eq. 4 with Eqs. 50-51).  Returns after enqueueing, unless check_nonfinite is set, in
+ * which case it synchronises the stream and returns LBM_ENONFINITE if any node's rho, T
+ * or psi became non-finite or psi^2 <= 0 during these steps.
+ * Errors: LBM_ESTATE (no init), LBM_EINVAL (n < 0), LBM_ECUDA, LBM_ENONFINITE. */
+int lbm_step(lbm_ctx* ctx, int n);
+
+/* Macroscopic fields of the current state: rho = sum f (Eq. 10), u = (sum e f + F/2)/rho
+ * (Eq. 10, F = F_m of Eq. 7 + F_b with the rho_ave the next step uses), T = sum g (Eq. 20).
+ * Any output pointer may be NULL.  Synchronises the stream before returning.
+ * Errors: LBM_ESTATE, LBM_ECUDA. */
+int lbm_get_moments(lbm_ctx* ctx, float* rho, float* ux, float* uy, float* uz, float* T);
+
+/* FP64 totals of the current state, reduced deterministically on the device:
+ * mass = sum rho, energy = sum T, and the rho_ave the next step uses.  Synchronises. */
+int lbm_get_totals(lbm_ctx* ctx, double* mass, double* T_sum, double* rho_ave);
+
+/* Number of steps taken since lbm_init_fields. */
+long long lbm_steps_done(const lbm_ctx* ctx);
+
+/* Kernel variant the context runs (LBM_KERNEL_TWO_PASS or LBM_KERNEL_FUSED; AUTO resolved). */
+int lbm_kernel_in_use(const lbm_ctx* ctx);
+
+/* Enqueue n steps outside any graph and accumulate, per kernel kind, the device time
+ * measured with CUDA events on the context's stream (kernel_ms[0]: psi/EOS or fused
+ * kernel, [1]: stream-collide kernel, [2]: reductions).  Synchronises.  Used for the
+ * roofline figures; the event gaps make it slightly slower than lbm_step. */
+int lbm_step_profiled(lbm_ctx* ctx, int n, double kernel_ms[3], int launches[3]);
+
+/* Release everything the context owns.  NULL is ignored. */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Static description of a status code. */
+const char* lbm_status_str(int status);
+
+/* Message of the last error on this thread (empty string if none). */
+const char* lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_LBM_H */

@@ -1,0 +1,501 @@
+// Host implementation of the C-ABI declared in include/lbm.h.
+#include <math.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <cuda_runtime.h>
+
+#include "../../include/lbm.h"
+#include "lbm_launch.h"
+
+using namespace gb300lbm;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int status, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return status;
+}
+
+#define CK(call)                                                                            \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(LBM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));         \
+    } while (0)
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+size_t pop_bytes(int precision) { return precision == LBM_FP32 ? 4 : 2; }
+
+struct Layout {
+    size_t f[2], g[2], psirho, phis, sums, partial, counter, flag, total;
+};
+
+Layout layout_of(const lbm_params* p, const DevParams& dp) {
+    Layout L;
+    size_t N = (size_t)dp.N, pb = pop_bytes(p->precision), off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+    L.f[0] = take(19 * N * pb);
+    L.f[1] = take(19 * N * pb);
+    L.g[0] = take(7 * N * pb);
+    L.g[1] = take(7 * N * pb);
+    L.psirho = take(8 * N);
+    L.phis = take(4 * N);
+    L.sums = take(8 * sizeof(double));          // slots: [0..1] [2..3] rho_ave ping-pong, [4..5] totals
+    L.partial = take(sizeof(double2) * (size_t)max_partials(dp));
+    L.counter = take(sizeof(unsigned));
+    L.flag = take(sizeof(int));
+    L.total = off;
+    return L;
+}
+
+const int kGraphCache = 8;
+
+struct GraphEntry {
+    int n, fcur, gcur, slot;
+    cudaGraphExec_t exec;
+    unsigned long long last_use;
+};
+
+}  // namespace
+
+struct lbm_ctx {
+    lbm_params p;
+    DevParams dp;
+    cudaStream_t stream;
+    char* base;
+    bool owns;
+    Layout L;
+    int fcur, gcur, slot;
+    bool fresh_f, fresh_g, first, initialised;
+    long long steps;
+    int variant;   // LBM_KERNEL_TWO_PASS or LBM_KERNEL_FUSED
+    GraphEntry graphs[kGraphCache];
+    int n_graphs;
+    unsigned long long use_clock;
+
+    void* fbuf(int k) { return base + L.f[k]; }
+    void* gbuf(int k) { return base + L.g[k]; }
+    double* sums(int k) { return (double*)(base + L.sums) + 2 * k; }
+    StateBufs bufs() {
+        StateBufs B;
+        B.fsrc = fbuf(fcur);
+        B.gsrc = gbuf(gcur);
+        B.fdst = fbuf(fcur ^ 1);
+        B.gdst = gbuf(gcur ^ 1);
+        B.pull_f = fresh_f ? 0 : 1;
+        B.pull_g = fresh_g ? 0 : 1;
+        B.psirho = (float2*)(base + L.psirho);
+        B.phis = (float*)(base + L.phis);
+        B.partial = (double2*)(base + L.partial);
+        B.counter = (unsigned*)(base + L.counter);
+        B.flag = (int*)(base + L.flag);
+        return B;
+    }
+};
+
+namespace {
+
+double critical_T(const lbm_params* p) { return 0.0778 * p->a / (0.45724 * p->b * p->R); }
+
+int validate(const lbm_params* p) {
+    if (!p) return fail(LBM_EINVAL, "params is NULL");
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(LBM_EINVAL, "lattice size must be >= 1");
+    long long N = (long long)p->nx * p->ny * p->nz;
+    if (N * 19 >= (1LL << 31)) return fail(LBM_EINVAL, "lattice too large (19 N must be < 2^31)");
+    int n[3] = {p->nx, p->ny, p->nz};
+    for (int f = 0; f < 6; ++f) {
+        if (p->bc[f] < 0 || p->bc[f] > 3) return fail(LBM_EINVAL, "bc[%d] = %d is not an lbm_bc", f, p->bc[f]);
+        if (p->bc[f] == LBM_BC_OUTFLOW && n[f / 2] < 2) return fail(LBM_EINVAL, "outflow face needs >= 2 nodes");
+    }
+    for (int a = 0; a < 3; ++a) {
+        bool plo = p->bc[2 * a] == LBM_BC_PERIODIC || p->bc[2 * a] == LBM_BC_THERMAL_ONLY;
+        bool phi = p->bc[2 * a + 1] == LBM_BC_PERIODIC || p->bc[2 * a + 1] == LBM_BC_THERMAL_ONLY;
+        if (plo != phi) return fail(LBM_EINVAL, "axis %d: f is periodic on one face only", a);
+        if ((p->bc[2 * a] == LBM_BC_PERIODIC) != (p->bc[2 * a + 1] == LBM_BC_PERIODIC))
+            return fail(LBM_EINVAL, "axis %d: g is periodic on one face only", a);
+    }
+    if (!(p->tau_e > 0.5 && p->tau_v > 0.5 && p->tau_q > 0.5 && p->tau_pi > 0.5))
+        return fail(LBM_EINVAL, "relaxation times must exceed 1/2");
+    if (!(p->varsigma_q > 0.5 && p->varsigma_pi > 0.5)) return fail(LBM_EINVAL, "varsigma_q, varsigma_pi must exceed 1/2");
+    if (!(p->a > 0 && p->b > 0 && p->R > 0)) return fail(LBM_EINVAL, "EOS constants a, b, R must be positive");
+    if (!(p->d > 0 && p->d < 1)) return fail(LBM_EINVAL, "D3Q7 d must lie in (0, 1)");
+    if (!(p->cV > 0)) return fail(LBM_EINVAL, "cV must be positive");
+    if (!(p->chi_or_lambda > 0)) return fail(LBM_EINVAL, "chi / lambda must be positive");
+    if (p->precision < 0 || p->precision > 2) return fail(LBM_EINVAL, "unknown precision");
+    if (p->kernel < 0 || p->kernel > 2) return fail(LBM_EINVAL, "unknown kernel variant");
+    if (p->hot_dT != 0.0 && !(p->hot_sigma > 0)) return fail(LBM_EINVAL, "hot_sigma must be positive");
+    return LBM_OK;
+}
+
+DevParams make_dev(const lbm_params* p) {
+    DevParams d;
+    memset(&d, 0, sizeof(d));
+    d.nx = p->nx; d.ny = p->ny; d.nz = p->nz;
+    d.N = p->nx * p->ny * p->nz;
+    d.plane = p->nx * p->ny;
+    for (int k = 0; k < 6; ++k) { d.bc[k] = p->bc[k]; d.T_wall[k] = (float)p->T_wall[k]; }
+    d.hot_dT = (float)p->hot_dT;
+    d.hot_inv2s2 = p->hot_dT != 0.0 ? (float)(1.0 / (2.0 * p->hot_sigma * p->hot_sigma)) : 0.f;
+    d.hot_cx = 0.5f * (float)p->nx;
+    d.hot_cy = 0.5f * (float)p->ny;
+    d.a = (float)p->a; d.b = (float)p->b; d.R = (float)p->R;
+    d.Tc = (float)critical_T(p);
+    double w = p->acentric;
+    d.kappa = (float)(0.37464 + 1.54226 * w - 0.26992 * w * w);
+    d.sigma6 = (float)(6.0 * p->sigma / (p->tau_e - 0.5));
+    d.Le = (float)(1.0 / p->tau_e); d.Lv = (float)(1.0 / p->tau_v);
+    d.Lq = (float)(1.0 / p->tau_q); d.Lpi = (float)(1.0 / p->tau_pi);
+    d.inv_tau_e = (float)(1.0 / p->tau_e);
+    d.half_Le = (float)(1.0 - 0.5 / p->tau_e);
+    d.cV = (float)p->cV; d.d = (float)p->d; d.csT2 = (float)(p->d / 3.0);
+    d.w0 = (float)(1.0 - p->d); d.w1 = (float)(p->d / 6.0);
+    d.Gq = (float)(1.0 / p->varsigma_q); d.Gpi = (float)(1.0 / p->varsigma_pi);
+    d.lambda_mode = p->lambda_mode; d.chi_or_lambda = (float)p->chi_or_lambda;
+    d.gx = (float)p->g[0]; d.gy = (float)p->g[1]; d.gz = (float)p->g[2];
+    d.flow_off = p->flow_off; d.thermal_off = p->thermal_off;
+    if (p->precision != LBM_FP32) {
+        for (int a = 0; a < 19; ++a) {
+            int e2 = ex19(a) * ex19(a) + ey19(a) * ey19(a) + ez19(a) * ez19(a);
+            double wa = e2 == 0 ? 1.0 / 3.0 : (e2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+            d.shift_f[a] = (float)(wa * p->rho_ref);
+        }
+        for (int a = 0; a < 7; ++a) d.shift_g[a] = (float)((a == 0 ? 1.0 - p->d : p->d / 6.0) * p->T_ref);
+    }
+    return d;
+}
+
+bool is_device_ptr(const void* ptr) {
+    if (!ptr) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+void drop_graphs(lbm_ctx* c) {
+    for (int k = 0; k < c->n_graphs; ++k) cudaGraphExecDestroy(c->graphs[k].exec);
+    c->n_graphs = 0;
+}
+
+// Enqueue one time step of the selected variant on the context's stream.
+int enqueue_step(lbm_ctx* c, double* kernel_ms = nullptr, int* launches = nullptr, cudaEvent_t* ev = nullptr) {
+    StateBufs B = c->bufs();
+    cudaError_t e;
+    if (c->variant == LBM_KERNEL_FUSED) {
+        if (ev) cudaEventRecord(ev[0], c->stream);
+        e = launch_fused(c->dp, c->p.precision, B, c->sums(c->slot), c->sums(c->slot ^ 1), c->first ? 1 : 0,
+                         c->stream);
+        if (e != cudaSuccess) return fail(LBM_ECUDA, "fused kernel launch: %s", cudaGetErrorString(e));
+        if (ev) {
+            cudaEventRecord(ev[1], c->stream);
+            cudaEventSynchronize(ev[1]);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[0], ev[1]);
+            kernel_ms[0] += ms;
+            launches[0] += 1;
+        }
+    } else {
+        if (ev) cudaEventRecord(ev[0], c->stream);
+        e = launch_psi(c->dp, c->p.precision, B, c->sums(c->slot ^ 1), c->stream);
+        if (e != cudaSuccess) return fail(LBM_ECUDA, "psi kernel launch: %s", cudaGetErrorString(e));
+        if (ev) cudaEventRecord(ev[1], c->stream);
+        e = launch_collide(c->dp, c->p.precision, B, c->sums(c->slot), c->first ? 1 : 0, c->stream);
+        if (e != cudaSuccess) return fail(LBM_ECUDA, "collide kernel launch: %s", cudaGetErrorString(e));
+        if (ev) {
+            cudaEventRecord(ev[2], c->stream);
+            cudaEventSynchronize(ev[2]);
+            float a = 0.f, b = 0.f;
+            cudaEventElapsedTime(&a, ev[0], ev[1]);
+            cudaEventElapsedTime(&b, ev[1], ev[2]);
+            kernel_ms[0] += a;
+            kernel_ms[1] += b;
+            launches[0] += 1;
+            launches[1] += 1;
+        }
+    }
+    if (!c->p.flow_off) { c->fcur ^= 1; c->fresh_f = false; }
+    if (!c->p.thermal_off) { c->gcur ^= 1; c->fresh_g = false; }
+    c->slot ^= 1;
+    c->first = false;
+    c->steps += 1;
+    return LBM_OK;
+}
+
+int run_graph(lbm_ctx* c, int n) {
+    GraphEntry* hit = nullptr;
+    for (int k = 0; k < c->n_graphs; ++k) {
+        GraphEntry& g = c->graphs[k];
+        if (g.n == n && g.fcur == c->fcur && g.gcur == c->gcur && g.slot == c->slot) hit = &g;
+    }
+    if (!hit) {
+        int f0 = c->fcur, g0 = c->gcur, s0 = c->slot;
+        bool ff = c->fresh_f, fg = c->fresh_g, fi = c->first;
+        long long st = c->steps;
+        cudaGraph_t graph;
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = LBM_OK;
+        for (int k = 0; k < n && rc == LBM_OK; ++k) rc = enqueue_step(c);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+        // the capture only recorded work: put the state back, the replay advances it
+        c->fcur = f0; c->gcur = g0; c->slot = s0; c->fresh_f = ff; c->fresh_g = fg; c->first = fi; c->steps = st;
+        if (rc != LBM_OK) { if (e == cudaSuccess) cudaGraphDestroy(graph); return rc; }
+        if (e != cudaSuccess) return fail(LBM_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        cudaGraphExec_t exec;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(LBM_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        if (c->n_graphs == kGraphCache) {
+            int lru = 0;
+            for (int k = 1; k < c->n_graphs; ++k)
+                if (c->graphs[k].last_use < c->graphs[lru].last_use) lru = k;
+            cudaGraphExecDestroy(c->graphs[lru].exec);
+            c->graphs[lru] = c->graphs[--c->n_graphs];
+        }
+        GraphEntry& g = c->graphs[c->n_graphs++];
+        g.n = n; g.fcur = c->fcur; g.gcur = c->gcur; g.slot = c->slot; g.exec = exec;
+        hit = &g;
+    }
+    hit->last_use = ++c->use_clock;
+    CK(cudaGraphLaunch(hit->exec, c->stream));
+    // advance the host-side state exactly as n enqueue_step calls would
+    for (int k = 0; k < n; ++k) {
+        if (!c->p.flow_off) c->fcur ^= 1;
+        if (!c->p.thermal_off) c->gcur ^= 1;
+        c->slot ^= 1;
+    }
+    c->steps += n;
+    return LBM_OK;
+}
+
+int check_flag(lbm_ctx* c) {
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, c->base + c->L.flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (h) {
+        CK(cudaMemsetAsync(c->base + c->L.flag, 0, sizeof(int), c->stream));
+        return fail(LBM_ENONFINITE, "non-finite rho/T/psi or psi^2 <= 0 after step %lld", c->steps);
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_params_default(lbm_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->nx = p->ny = p->nz = 1;
+    p->a = 2.0 / 49.0; p->b = 2.0 / 21.0; p->R = 1.0; p->acentric = 0.344;
+    p->tau_e = 1.25; p->tau_v = 0.8; p->tau_q = 1.0; p->tau_pi = 1.0;
+    p->cV = 5.0; p->d = 0.95; p->varsigma_q = 1.0; p->varsigma_pi = 1.0;
+    p->lambda_mode = 0; p->chi_or_lambda = 0.08;
+    p->precision = LBM_FP32;
+    p->kernel = LBM_KERNEL_AUTO;
+    p->use_graph = 1;
+    p->check_nonfinite = 1;
+}
+
+int lbm_eos_critical(const lbm_params* p, double* Tc, double* pc) {
+    if (!p || !(p->a > 0 && p->b > 0 && p->R > 0)) return fail(LBM_EINVAL, "EOS constants must be positive");
+    double t = critical_T(p);
+    if (Tc) *Tc = t;
+    if (pc) *pc = 0.0778 * p->R * t / p->b;
+    return LBM_OK;
+}
+
+size_t lbm_workspace_bytes(const lbm_params* p) {
+    if (validate(p) != LBM_OK) return 0;
+    DevParams d = make_dev(p);
+    return layout_of(p, d).total;
+}
+
+int lbm_create(const lbm_params* p, lbm_ctx** out) {
+    if (!out) return fail(LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = validate(p);
+    if (rc) return rc;
+    lbm_ctx* c = (lbm_ctx*)calloc(1, sizeof(lbm_ctx));
+    if (!c) return fail(LBM_ENOMEM, "host allocation failed");
+    c->p = *p;
+    c->dp = make_dev(p);
+    c->L = layout_of(p, c->dp);
+    c->stream = (cudaStream_t)p->cuda_stream;
+    if (p->workspace) {
+        if (p->workspace_bytes < c->L.total || ((uintptr_t)p->workspace & 255)) {
+            free(c);
+            return fail(LBM_EINVAL, "workspace too small (%zu < %zu) or not 256-byte aligned", p->workspace_bytes,
+                        c->L.total);
+        }
+        c->base = (char*)p->workspace;
+        c->owns = false;
+    } else {
+        cudaError_t e = cudaMalloc((void**)&c->base, c->L.total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            free(c);
+            return fail(LBM_ENOMEM, "cudaMalloc(%zu): %s", c->L.total, cudaGetErrorString(e));
+        }
+        c->owns = true;
+    }
+    c->variant = p->kernel == LBM_KERNEL_AUTO ? (fused_supported(c->dp) ? LBM_KERNEL_FUSED : LBM_KERNEL_TWO_PASS)
+                                              : p->kernel;
+    if (c->variant == LBM_KERNEL_FUSED && !fused_supported(c->dp)) {
+        if (c->owns) cudaFree(c->base);
+        free(c);
+        return fail(LBM_EINVAL, "fused kernel does not support this lattice");
+    }
+    cudaError_t e = cudaMemsetAsync(c->base + c->L.sums, 0, c->L.flag + sizeof(int) - c->L.sums, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        if (c->owns) cudaFree(c->base);
+        free(c);
+        return fail(LBM_ECUDA, "initial memset: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+int lbm_init_fields(lbm_ctx* c, const float* rho, const float* T, const float* u) {
+    if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+    if (!rho || !T) return fail(LBM_EINVAL, "rho and T are required");
+    size_t N = (size_t)c->dp.N;
+    // stage host inputs in the second population buffer (19 N * >= 2 bytes >= 5 N floats)
+    float* stage = (float*)c->fbuf(1);
+    const float *drho = rho, *dT = T, *du = u;
+    if (!is_device_ptr(rho)) {
+        CK(cudaMemcpyAsync(stage, rho, N * 4, cudaMemcpyHostToDevice, c->stream));
+        drho = stage;
+    }
+    if (!is_device_ptr(T)) {
+        CK(cudaMemcpyAsync(stage + N, T, N * 4, cudaMemcpyHostToDevice, c->stream));
+        dT = stage + N;
+    }
+    if (u && !is_device_ptr(u)) {
+        CK(cudaMemcpyAsync(stage + 2 * N, u, 3 * N * 4, cudaMemcpyHostToDevice, c->stream));
+        du = stage + 2 * N;
+    }
+    drop_graphs(c);
+    c->fcur = 0;
+    c->gcur = 0;
+    c->slot = 0;
+    CK(launch_init(c->dp, c->p.precision, c->fbuf(0), c->gbuf(0), drho, dT, du, c->stream));
+    StateBufs B = c->bufs();
+    CK(launch_sum_field(drho, c->dp.N, B.partial, B.counter, c->sums(0), c->stream));
+    CK(cudaMemsetAsync(c->base + c->L.flag, 0, sizeof(int), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->fresh_f = c->fresh_g = true;
+    c->first = true;
+    c->initialised = true;
+    c->steps = 0;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_ctx* c, int n) {
+    if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+    if (!c->initialised) return fail(LBM_ESTATE, "lbm_step before lbm_init_fields");
+    if (n < 0) return fail(LBM_EINVAL, "n < 0");
+    int rc = LBM_OK;
+    int k = 0;
+    // the first step after init reads the un-streamed state and has no phi_s history
+    while (k < n && (c->first || (c->fresh_f && !c->p.flow_off) || (c->fresh_g && !c->p.thermal_off))) {
+        rc = enqueue_step(c);
+        if (rc) return rc;
+        ++k;
+    }
+    if (k < n) {
+        if (c->p.use_graph) rc = run_graph(c, n - k);
+        else
+            for (; k < n && rc == LBM_OK; ++k) rc = enqueue_step(c);
+        if (rc) return rc;
+    }
+    if (c->p.check_nonfinite) return check_flag(c);
+    return LBM_OK;
+}
+
+int lbm_step_profiled(lbm_ctx* c, int n, double kernel_ms[3], int launches[3]) {
+    if (!c || !kernel_ms || !launches) return fail(LBM_EINVAL, "NULL argument");
+    if (!c->initialised) return fail(LBM_ESTATE, "lbm_step before lbm_init_fields");
+    for (int k = 0; k < 3; ++k) { kernel_ms[k] = 0.0; launches[k] = 0; }
+    cudaEvent_t ev[3];
+    for (int k = 0; k < 3; ++k) CK(cudaEventCreate(&ev[k]));
+    int rc = LBM_OK;
+    for (int k = 0; k < n && rc == LBM_OK; ++k) rc = enqueue_step(c, kernel_ms, launches, ev);
+    for (int k = 0; k < 3; ++k) cudaEventDestroy(ev[k]);
+    if (rc) return rc;
+    if (c->p.check_nonfinite) return check_flag(c);
+    return LBM_OK;
+}
+
+int lbm_get_moments(lbm_ctx* c, float* rho, float* ux, float* uy, float* uz, float* T) {
+    if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+    if (!c->initialised) return fail(LBM_ESTATE, "lbm_get_moments before lbm_init_fields");
+    size_t N = (size_t)c->dp.N;
+    StateBufs B = c->bufs();
+    CK(launch_psi(c->dp, c->p.precision, B, nullptr, c->stream));
+    // outputs staged in the population buffer the next step overwrites anyway
+    float* stage = (float*)c->fbuf(c->fcur ^ 1);
+    float* outs[5] = {rho, ux, uy, uz, T};
+    float* dst[5];
+    for (int k = 0; k < 5; ++k) dst[k] = outs[k] ? (is_device_ptr(outs[k]) ? outs[k] : stage + k * N) : nullptr;
+    CK(launch_moments(c->dp, c->p.precision, B, c->sums(c->slot), dst[0], dst[1], dst[2], dst[3], dst[4], c->stream));
+    for (int k = 0; k < 5; ++k)
+        if (outs[k] && dst[k] != outs[k])
+            CK(cudaMemcpyAsync(outs[k], dst[k], N * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_get_totals(lbm_ctx* c, double* mass, double* T_sum, double* rho_ave) {
+    if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+    if (!c->initialised) return fail(LBM_ESTATE, "lbm_get_totals before lbm_init_fields");
+    StateBufs B = c->bufs();
+    CK(launch_psi(c->dp, c->p.precision, B, c->sums(2), c->stream));
+    double h[6];
+    CK(cudaMemcpyAsync(h, c->sums(0), sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (mass) *mass = h[4];
+    if (T_sum) *T_sum = h[5];
+    if (rho_ave) *rho_ave = h[2 * c->slot] / (double)c->dp.N;
+    return LBM_OK;
+}
+
+long long lbm_steps_done(const lbm_ctx* c) { return c ? c->steps : 0; }
+
+int lbm_kernel_in_use(const lbm_ctx* c) { return c ? c->variant : LBM_EINVAL; }
+
+void lbm_destroy(lbm_ctx* c) {
+    if (!c) return;
+    drop_graphs(c);
+    if (c->owns && c->base) cudaFree(c->base);
+    free(c);
+}
+
+const char* lbm_status_str(int s) {
+    switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_EINVAL: return "invalid argument";
+    case LBM_ENOMEM: return "out of memory";
+    case LBM_ECUDA: return "CUDA error";
+    case LBM_ESTATE: return "call out of order";
+    case LBM_ENONFINITE: return "non-finite value in the lattice";
+    case LBM_ETIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+const char* lbm_last_error(void) { return g_err; }
+
+}  // extern "C"

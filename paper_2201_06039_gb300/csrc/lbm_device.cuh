@@ -1,0 +1,405 @@
+// Device building blocks of the GB300 lattice update: parameters, population codecs,
+// boundary-aware pull, Peng-Robinson psi, D3Q19 MRT collision with the forcing of
+// Eq. 9, local div u (Eq. 48) and grad T (Eq. 45), phase-change source (Eq. 18, 23) and
+// the D3Q7 MRT temperature collision (Eqs. 38-43).
+//
+// Everything here is FP32 arithmetic.  The D3Q19 transform uses the raw polynomial
+// moments of Eq. 5's order (1, e, |e|^2, 2ex^2-ey^2-ez^2, ey^2-ez^2, exey, exez, eyez,
+// ex^2ey, exey^2, ex^2ez, exez^2, ey^2ez, eyez^2, ex^2ey^2, ex^2ez^2, ey^2ez^2) and its
+// closed-form inverse, unrolled by hand (no 19x19 matrix product).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gb300lbm {
+
+enum { BC_PERIODIC = 0, BC_WALL = 1, BC_OUTFLOW = 2, BC_THERMAL_ONLY = 3 };
+
+// D3Q19 velocities in the order of Eq. 2 and D3Q7 velocities of Eq. 21.
+__host__ __device__ constexpr int ex19(int a) {
+    return (a == 1 || a == 7 || a == 9 || a == 11 || a == 13) ? 1
+         : (a == 2 || a == 8 || a == 10 || a == 12 || a == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int ey19(int a) {
+    return (a == 3 || a == 7 || a == 10 || a == 15 || a == 17) ? 1
+         : (a == 4 || a == 8 || a == 9 || a == 16 || a == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int ez19(int a) {
+    return (a == 5 || a == 11 || a == 14 || a == 15 || a == 18) ? 1
+         : (a == 6 || a == 12 || a == 13 || a == 16 || a == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr int opp(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
+__host__ __device__ constexpr int ex7(int a) { return a == 1 ? 1 : a == 2 ? -1 : 0; }
+__host__ __device__ constexpr int ey7(int a) { return a == 3 ? 1 : a == 4 ? -1 : 0; }
+__host__ __device__ constexpr int ez7(int a) { return a == 5 ? 1 : a == 6 ? -1 : 0; }
+
+// Lattice constants and model parameters, converted once on the host.
+struct DevParams {
+    int nx, ny, nz;
+    int N;                    // nx*ny*nz (< 2^31)
+    int plane;                // nx*ny
+    int bc[6];
+    float T_wall[6];
+    float hot_dT, hot_inv2s2, hot_cx, hot_cy;
+    float a, b, R, Tc, kappa; // PR EOS (Eq. 49), kappa = 0.37464 + 1.54226 w - 0.26992 w^2
+    float sigma6;             // 6 sigma / (tau_e - 0.5)   (Eq. 9, S_4)
+    float Le, Lv, Lq, Lpi;    // 1/tau of Eq. 6
+    float inv_tau_e, half_Le; // 1/tau_e, (1 - 1/(2 tau_e)) of Eq. 48
+    float cV, d, csT2, w0, w1;
+    float Gq, Gpi;            // 1/varsigma_q, 1/varsigma_pi (Eq. 43)
+    int lambda_mode;
+    float chi_or_lambda;
+    float gx, gy, gz;
+    int flow_off, thermal_off;
+    float shift_f[19];        // storage shift w_a rho_ref (16-bit storage only, else 0)
+    float shift_g[7];         // storage shift w_a T_ref
+};
+
+// ---------------------------------------------------------------- population storage
+// Populations are stored structure-of-arrays: pop[a * N + node].
+template <typename S> struct Codec;
+template <> struct Codec<float> {
+    static __device__ __forceinline__ float load(const float* p, float) { return __ldg(p); }
+    static __device__ __forceinline__ void store(float* p, float v, float) { *p = v; }
+};
+template <> struct Codec<__nv_bfloat16> {
+    static __device__ __forceinline__ float load(const __nv_bfloat16* p, float s) {
+        return __bfloat162float(__ldg(p)) + s;
+    }
+    static __device__ __forceinline__ void store(__nv_bfloat16* p, float v, float s) {
+        *p = __float2bfloat16_rn(v - s);
+    }
+};
+template <> struct Codec<__half> {
+    static __device__ __forceinline__ float load(const __half* p, float s) {
+        return __half2float(__ldg(p)) + s;
+    }
+    static __device__ __forceinline__ void store(__half* p, float v, float s) {
+        *p = __float2half_rn(v - s);
+    }
+};
+
+// ---------------------------------------------------------------- neighbourhood of a node
+// For each axis: coordinate of the node at -1 / +1 after periodic wrap, or clamped onto the
+// node itself at a non-periodic face (that clamp is both the outflow extrapolation source
+// of the f pull and the mirror image of the psi / grad-rho stencil).  Bit masks mark
+// faces crossed by a pull: fbb (f halfway bounce-back, Eq. 50) and gabb (g anti-bounce-back,
+// Eq. 51).  Bit 2k   : the -1 neighbour along axis k lies behind face 2k.
+//          Bit 2k+1 : the +1 neighbour along axis k lies behind face 2k+1.
+struct Nbr {
+    int xm, xp, ym, yp, zm, zp;   // coordinates
+    unsigned fbb, gabb;
+};
+
+__device__ __forceinline__ bool f_wraps(int bc) { return bc == BC_PERIODIC || bc == BC_THERMAL_ONLY; }
+
+__device__ __forceinline__ void axis_nbr(int c, int n, int bc_lo, int bc_hi, int bit,
+                                         int& cm, int& cp, unsigned& fbb, unsigned& gabb) {
+    cm = c - 1;
+    cp = c + 1;
+    if (c == 0) {
+        cm = f_wraps(bc_lo) ? n - 1 : 0;
+        if (bc_lo == BC_WALL) fbb |= 1u << bit;
+        if (bc_lo != BC_PERIODIC) gabb |= 1u << bit;
+    }
+    if (c == n - 1) {
+        cp = f_wraps(bc_hi) ? 0 : n - 1;
+        if (bc_hi == BC_WALL) fbb |= 2u << bit;
+        if (bc_hi != BC_PERIODIC) gabb |= 2u << bit;
+    }
+}
+
+__device__ __forceinline__ Nbr make_nbr(const DevParams& P, int x, int y, int z) {
+    Nbr n;
+    n.fbb = 0;
+    n.gabb = 0;
+    axis_nbr(x, P.nx, P.bc[0], P.bc[1], 0, n.xm, n.xp, n.fbb, n.gabb);
+    axis_nbr(y, P.ny, P.bc[2], P.bc[3], 2, n.ym, n.yp, n.fbb, n.gabb);
+    axis_nbr(z, P.nz, P.bc[4], P.bc[5], 4, n.zm, n.zp, n.fbb, n.gabb);
+    return n;
+}
+
+__device__ __forceinline__ int node_of(const DevParams& P, int x, int y, int z) {
+    return x + P.nx * (y + P.ny * z);
+}
+
+// Source coordinate of the pull along one axis for velocity component e (x - e).
+__device__ __forceinline__ int src_c(int e, int c, int cm, int cp) { return e > 0 ? cm : (e < 0 ? cp : c); }
+// Neighbour coordinate of the stencil along one axis (x + e).
+__device__ __forceinline__ int nb_c(int e, int c, int cm, int cp) { return e > 0 ? cp : (e < 0 ? cm : c); }
+
+// Does the pull of velocity a cross a wall face (Eq. 50)?
+template <int A> __device__ __forceinline__ bool crosses(unsigned mask) {
+    constexpr int ex = ex19(A), ey = ey19(A), ez = ez19(A);
+    constexpr unsigned m = (ex > 0 ? 1u : 0u) | (ex < 0 ? 2u : 0u) | (ey > 0 ? 4u : 0u) |
+                           (ey < 0 ? 8u : 0u) | (ez > 0 ? 16u : 0u) | (ez < 0 ? 32u : 0u);
+    return (mask & m) != 0u;
+}
+
+__device__ __forceinline__ float wall_T(const DevParams& P, int face, int x, int y) {
+    float T = P.T_wall[face];
+    if (face == 4 && P.hot_dT != 0.f) {
+        float dx = (float)x - P.hot_cx, dy = (float)y - P.hot_cy;
+        T += P.hot_dT * expf(-(dx * dx + dy * dy) * P.hot_inv2s2);
+    }
+    return T;
+}
+
+template <typename S, int A>
+__device__ __forceinline__ float pull_f_one(const DevParams& P, const S* __restrict__ src, int i,
+                                            int x, int y, int z, const Nbr& n) {
+    constexpr int ex = ex19(A), ey = ey19(A), ez = ez19(A);
+    if (A != 0 && crosses<A>(n.fbb))   // Eq. 50: f_a(x_b, t+1) = f*_{abar}(x_b, t)
+        return Codec<S>::load(src + (size_t)opp(A) * P.N + i, P.shift_f[opp(A)]);
+    int s = node_of(P, src_c(ex, x, n.xm, n.xp), src_c(ey, y, n.ym, n.yp), src_c(ez, z, n.zm, n.zp));
+    return Codec<S>::load(src + (size_t)A * P.N + s, P.shift_f[A]);
+}
+
+template <int A> struct Unroll19;
+
+// Pull of all 19 f (pull != 0) or direct read of the node's own values (fresh state).
+template <typename S>
+__device__ __forceinline__ void load_f(const DevParams& P, const S* __restrict__ src, int pull, int i,
+                                       int x, int y, int z, const Nbr& n, float f[19]) {
+    if (pull) {
+#define GB300_PULL(A) f[A] = pull_f_one<S, A>(P, src, i, x, y, z, n);
+        GB300_PULL(0) GB300_PULL(1) GB300_PULL(2) GB300_PULL(3) GB300_PULL(4) GB300_PULL(5)
+        GB300_PULL(6) GB300_PULL(7) GB300_PULL(8) GB300_PULL(9) GB300_PULL(10) GB300_PULL(11)
+        GB300_PULL(12) GB300_PULL(13) GB300_PULL(14) GB300_PULL(15) GB300_PULL(16) GB300_PULL(17)
+        GB300_PULL(18)
+#undef GB300_PULL
+    } else {
+#pragma unroll
+        for (int a = 0; a < 19; ++a) f[a] = Codec<S>::load(src + (size_t)a * P.N + i, P.shift_f[a]);
+    }
+}
+
+template <typename S, int A>
+__device__ __forceinline__ float pull_g_one(const DevParams& P, const S* __restrict__ src, int i,
+                                            int x, int y, int z, const Nbr& n) {
+    constexpr int ex = ex7(A), ey = ey7(A), ez = ez7(A);
+    constexpr int face = ex > 0 ? 0 : ex < 0 ? 1 : ey > 0 ? 2 : ey < 0 ? 3 : ez > 0 ? 4 : 5;
+    if (A != 0 && (n.gabb & (1u << face))) {
+        // Eq. 51: g_a(x_b, t+1) = -g+_{abar}(x_b, t) + 2 w_abar T_w   (w_abar = w_a on D3Q7)
+        float gp = Codec<S>::load(src + (size_t)opp(A) * P.N + i, P.shift_g[opp(A)]);
+        return -gp + 2.f * P.w1 * wall_T(P, face, x, y);
+    }
+    int s = node_of(P, src_c(ex, x, n.xm, n.xp), src_c(ey, y, n.ym, n.yp), src_c(ez, z, n.zm, n.zp));
+    return Codec<S>::load(src + (size_t)A * P.N + s, P.shift_g[A]);
+}
+
+template <typename S>
+__device__ __forceinline__ void load_g(const DevParams& P, const S* __restrict__ src, int pull, int i,
+                                       int x, int y, int z, const Nbr& n, float g[7]) {
+    if (pull) {
+        g[0] = pull_g_one<S, 0>(P, src, i, x, y, z, n);
+        g[1] = pull_g_one<S, 1>(P, src, i, x, y, z, n);
+        g[2] = pull_g_one<S, 2>(P, src, i, x, y, z, n);
+        g[3] = pull_g_one<S, 3>(P, src, i, x, y, z, n);
+        g[4] = pull_g_one<S, 4>(P, src, i, x, y, z, n);
+        g[5] = pull_g_one<S, 5>(P, src, i, x, y, z, n);
+        g[6] = pull_g_one<S, 6>(P, src, i, x, y, z, n);
+    } else {
+#pragma unroll
+        for (int a = 0; a < 7; ++a) g[a] = Codec<S>::load(src + (size_t)a * P.N + i, P.shift_g[a]);
+    }
+}
+
+// ---------------------------------------------------------------- thermodynamics
+// Peng-Robinson pressure (Eq. 49) and psi^2 = 2 (p_EOS - rho cs^2) / (G c^2) with G = -1 (Eq. 8).
+__device__ __forceinline__ float psi_squared(const DevParams& P, float rho, float T) {
+    float s = 1.f + P.kappa * (1.f - sqrtf(T / P.Tc));
+    float theta = s * s;
+    float brho = P.b * rho;
+    float p = rho * P.R * T / (1.f - brho) - P.a * theta * rho * rho / (1.f + 2.f * brho - brho * brho);
+    return 2.f * (rho * (1.f / 3.f) - p);
+}
+
+// ---------------------------------------------------------------- D3Q19 MRT collision
+struct NodeOut {
+    float ux, uy, uz, divu;
+};
+
+// In: post-streaming f, total force F, interaction force Fm, psi^2.  Out: f* in place.
+// Eq. 10 velocity, Eq. 5 equilibrium moments, Eq. 9 forcing, Eq. 6 rates, Eq. 3 relaxation,
+// Eq. 4 back-transform, Eq. 48 divergence.
+__device__ __forceinline__ NodeOut collide_f(const DevParams& P, float f[19], float Fx, float Fy,
+                                             float Fz, float Fm2, float psi2) {
+    const float cs2 = 1.f / 3.f;
+    float rho = 0.f;
+#pragma unroll
+    for (int a = 0; a < 19; ++a) rho += f[a];
+    float jx = (f[1] - f[2]) + (f[7] - f[8]) + (f[9] - f[10]) + (f[11] - f[12]) + (f[13] - f[14]);
+    float jy = (f[3] - f[4]) + (f[7] - f[8]) - (f[9] - f[10]) + (f[15] - f[16]) + (f[17] - f[18]);
+    float jz = (f[5] - f[6]) + (f[11] - f[12]) - (f[13] - f[14]) + (f[15] - f[16]) - (f[17] - f[18]);
+    float inv_rho = 1.f / rho;
+    float ux = (jx + 0.5f * Fx) * inv_rho, uy = (jy + 0.5f * Fy) * inv_rho, uz = (jz + 0.5f * Fz) * inv_rho;
+
+    // raw moments (rows of M)
+    float s7 = f[7] + f[8], s9 = f[9] + f[10], s11 = f[11] + f[12], s13 = f[13] + f[14];
+    float s15 = f[15] + f[16], s17 = f[17] + f[18];
+    float m16 = s7 + s9, m17 = s11 + s13, m18 = s15 + s17;
+    float xx = f[1] + f[2] + m16 + m17;
+    float yy = f[3] + f[4] + m16 + m18;
+    float zz = f[5] + f[6] + m17 + m18;
+    float m4 = xx + yy + zz;
+    float m5 = 2.f * xx - yy - zz;
+    float m6 = yy - zz;
+    float m7 = s7 - s9, m8 = s11 - s13, m9 = s15 - s17;
+    float d7 = f[7] - f[8], d9 = f[9] - f[10], d11 = f[11] - f[12], d13 = f[13] - f[14];
+    float d15 = f[15] - f[16], d17 = f[17] - f[18];
+    float m10 = d7 - d9, m11 = d7 + d9, m12 = d11 - d13, m13 = d11 + d13, m14 = d15 - d17, m15 = d15 + d17;
+
+    // equilibrium moments (Eq. 5)
+    float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz, u2 = ux2 + uy2 + uz2;
+    float phi = rho * (cs2 * cs2) * (1.f - 1.5f * u2);
+    float e4 = rho + rho * u2;
+    float e5 = rho * (2.f * ux2 - uy2 - uz2), e6 = rho * (uy2 - uz2);
+    float e7 = rho * ux * uy, e8 = rho * ux * uz, e9 = rho * uy * uz;
+    float e10 = rho * uy * (cs2 + ux2), e11 = rho * ux * (cs2 + uy2);
+    float e12 = rho * uz * (cs2 + ux2), e13 = rho * ux * (cs2 + uz2);
+    float e14 = rho * uz * (cs2 + uy2), e15 = rho * uy * (cs2 + uz2);
+    float e16 = phi + rho * cs2 * (ux2 + uy2), e17 = phi + rho * cs2 * (ux2 + uz2);
+    float e18 = phi + rho * cs2 * (uy2 + uz2);
+
+    // forcing moments (Eq. 9)
+    float Fu_x = Fx * ux, Fu_y = Fy * uy, Fu_z = Fz * uz;
+    float S4 = 2.f * (Fu_x + Fu_y + Fu_z) + P.sigma6 * Fm2 / psi2;
+    float S5 = 2.f * (2.f * Fu_x - Fu_y - Fu_z), S6 = 2.f * (Fu_y - Fu_z);
+    float S7 = Fx * uy + Fy * ux, S8 = Fx * uz + Fz * ux, S9 = Fy * uz + Fz * uy;
+    float S10 = cs2 * Fy, S11 = cs2 * Fx, S12 = cs2 * Fz, S13 = cs2 * Fx, S14 = cs2 * Fz, S15 = cs2 * Fy;
+    float S16 = 2.f * cs2 * (Fu_x + Fu_y), S17 = 2.f * cs2 * (Fu_x + Fu_z), S18 = 2.f * cs2 * (Fu_y + Fu_z);
+
+    NodeOut o;
+    o.ux = ux; o.uy = uy; o.uz = uz;
+    // Eq. 48 (pre-collision m_4, force-corrected u, full S_4, total F)
+    o.divu = (-(m4 - e4) * P.inv_tau_e + P.half_Le * S4 - 2.f * (Fu_x + Fu_y + Fu_z)) * (1.5f * inv_rho);
+
+    // relaxation (Eq. 3): m* = m - L (m - meq) + (1 - L/2) S
+    const float Le = P.Le, Lv = P.Lv, Lq = P.Lq, Lp = P.Lpi;
+    float r1 = jx + Fx, r2 = jy + Fy, r3 = jz + Fz;   // rates 1: m* = rho u + F/2 = j + F
+    m4 += -Le * (m4 - e4) + (1.f - 0.5f * Le) * S4;
+    m5 += -Lv * (m5 - e5) + (1.f - 0.5f * Lv) * S5;
+    m6 += -Lv * (m6 - e6) + (1.f - 0.5f * Lv) * S6;
+    m7 += -Lv * (m7 - e7) + (1.f - 0.5f * Lv) * S7;
+    m8 += -Lv * (m8 - e8) + (1.f - 0.5f * Lv) * S8;
+    m9 += -Lv * (m9 - e9) + (1.f - 0.5f * Lv) * S9;
+    const float hq = 1.f - 0.5f * Lq, hp = 1.f - 0.5f * Lp;
+    m10 += -Lq * (m10 - e10) + hq * S10;
+    m11 += -Lq * (m11 - e11) + hq * S11;
+    m12 += -Lq * (m12 - e12) + hq * S12;
+    m13 += -Lq * (m13 - e13) + hq * S13;
+    m14 += -Lq * (m14 - e14) + hq * S14;
+    m15 += -Lq * (m15 - e15) + hq * S15;
+    m16 += -Lp * (m16 - e16) + hp * S16;
+    m17 += -Lp * (m17 - e17) + hp * S17;
+    m18 += -Lp * (m18 - e18) + hp * S18;
+
+    // back-transform f* = M^-1 m* (closed form of the raw-moment inverse)
+    float X = (m4 + m5) * (1.f / 3.f);
+    float Y = 0.5f * (m4 - X + m6);
+    float Z = 0.5f * (m4 - X - m6);
+    float ax = X - m16 - m17, bx = r1 - m11 - m13;
+    float ay = Y - m16 - m18, by = r2 - m10 - m15;
+    float az = Z - m17 - m18, bz = r3 - m12 - m14;
+    f[0] = rho - m4 + m16 + m17 + m18;
+    f[1] = 0.5f * (ax + bx); f[2] = 0.5f * (ax - bx);
+    f[3] = 0.5f * (ay + by); f[4] = 0.5f * (ay - by);
+    f[5] = 0.5f * (az + bz); f[6] = 0.5f * (az - bz);
+    f[7] = 0.25f * (m16 + m7 + m10 + m11);
+    f[8] = 0.25f * (m16 + m7 - m10 - m11);
+    f[9] = 0.25f * (m16 - m7 - m10 + m11);
+    f[10] = 0.25f * (m16 - m7 + m10 - m11);
+    f[11] = 0.25f * (m17 + m8 + m12 + m13);
+    f[12] = 0.25f * (m17 + m8 - m12 - m13);
+    f[13] = 0.25f * (m17 - m8 - m12 + m13);
+    f[14] = 0.25f * (m17 - m8 + m12 - m13);
+    f[15] = 0.25f * (m18 + m9 + m14 + m15);
+    f[16] = 0.25f * (m18 + m9 - m14 - m15);
+    f[17] = 0.25f * (m18 - m9 - m14 + m15);
+    f[18] = 0.25f * (m18 - m9 + m14 - m15);
+    return o;
+}
+
+// Equilibrium populations f = M^-1 m_eq(rho, u) (Eq. 5) for the initial state.
+__device__ __forceinline__ void feq(float rho, float ux, float uy, float uz, float f[19]) {
+    const float cs2 = 1.f / 3.f;
+    float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz, u2 = ux2 + uy2 + uz2;
+    float phi = rho * (cs2 * cs2) * (1.f - 1.5f * u2);
+    float m4 = rho + rho * u2, m5 = rho * (2.f * ux2 - uy2 - uz2), m6 = rho * (uy2 - uz2);
+    float m7 = rho * ux * uy, m8 = rho * ux * uz, m9 = rho * uy * uz;
+    float m10 = rho * uy * (cs2 + ux2), m11 = rho * ux * (cs2 + uy2);
+    float m12 = rho * uz * (cs2 + ux2), m13 = rho * ux * (cs2 + uz2);
+    float m14 = rho * uz * (cs2 + uy2), m15 = rho * uy * (cs2 + uz2);
+    float m16 = phi + rho * cs2 * (ux2 + uy2), m17 = phi + rho * cs2 * (ux2 + uz2);
+    float m18 = phi + rho * cs2 * (uy2 + uz2);
+    float X = (m4 + m5) * (1.f / 3.f);
+    float Y = 0.5f * (m4 - X + m6);
+    float Z = 0.5f * (m4 - X - m6);
+    float ax = X - m16 - m17, bx = rho * ux - m11 - m13;
+    float ay = Y - m16 - m18, by = rho * uy - m10 - m15;
+    float az = Z - m17 - m18, bz = rho * uz - m12 - m14;
+    f[0] = rho - m4 + m16 + m17 + m18;
+    f[1] = 0.5f * (ax + bx); f[2] = 0.5f * (ax - bx);
+    f[3] = 0.5f * (ay + by); f[4] = 0.5f * (ay - by);
+    f[5] = 0.5f * (az + bz); f[6] = 0.5f * (az - bz);
+    f[7] = 0.25f * (m16 + m7 + m10 + m11);
+    f[8] = 0.25f * (m16 + m7 - m10 - m11);
+    f[9] = 0.25f * (m16 - m7 - m10 + m11);
+    f[10] = 0.25f * (m16 - m7 + m10 - m11);
+    f[11] = 0.25f * (m17 + m8 + m12 + m13);
+    f[12] = 0.25f * (m17 + m8 - m12 - m13);
+    f[13] = 0.25f * (m17 - m8 - m12 + m13);
+    f[14] = 0.25f * (m17 - m8 + m12 - m13);
+    f[15] = 0.25f * (m18 + m9 + m14 + m15);
+    f[16] = 0.25f * (m18 + m9 - m14 - m15);
+    f[17] = 0.25f * (m18 - m9 - m14 + m15);
+    f[18] = 0.25f * (m18 - m9 + m14 - m15);
+}
+
+// ---------------------------------------------------------------- D3Q7 MRT temperature LB
+// n = N g (Eq. 38); grad T from the first moments (Eq. 45); phi_s (Eq. 18); Q (Eqs. 23-24);
+// n* = n - Gamma (n - n_eq) with n_eq = (T, 0, 0, 0, 3 cs_T^2 T, 0, 0) (Eqs. 39, 42, 43);
+// g+ = N^-1 n* + Q (Eqs. 40-41).  g is replaced by g+ in place; returns phi_s.
+__device__ __forceinline__ float collide_g(const DevParams& P, float g[7], float rho, float T,
+                                           const NodeOut& o, float grx, float gry, float grz,
+                                           float phis_prev, int first) {
+    float n1 = g[1] - g[2], n2 = g[3] - g[4], n3 = g[5] - g[6];
+    float n4 = g[1] + g[2] + g[3] + g[4] + g[5] + g[6];
+    float n5 = g[1] + g[2] - g[3] - g[4];
+    float n6 = g[1] + g[2] - g[5] - g[6];
+    float chi = P.lambda_mode ? P.chi_or_lambda / (rho * P.cV) : P.chi_or_lambda;
+    float vsT = chi / P.csT2 + 0.5f;                 // chi = (varsigma_T - 1/2) cs_T^2
+    float inv_vsT = 1.f / vsT;
+    float k = -inv_vsT / P.csT2;                     // Eq. 45
+    float gTx = k * n1, gTy = k * n2, gTz = k * n3;
+    float phis = 0.f;
+    if (!P.flow_off) {
+        float inv_rho = 1.f / rho;
+        phis = (chi * grx * inv_rho - o.ux) * gTx + (chi * gry * inv_rho - o.uy) * gTy +
+               (chi * grz * inv_rho - o.uz) * gTz;
+        // T/(rho cV) (dp/dT)_rho div u with (dp/dT)_rho ~ rho R / (1 - b rho)
+        phis -= T * P.R / (P.cV * (1.f - P.b * rho)) * o.divu;
+    }
+    float C = first ? phis : phis_prev;
+    float qs = 1.5f * phis - 0.5f * C;               // Q_a = w_a (3/2 phi_s(t) - 1/2 phi_s(t-1))
+    float om = 1.f - inv_vsT;
+    n1 *= om; n2 *= om; n3 *= om;
+    n4 = n4 - P.Gq * (n4 - P.d * T);                 // 3 cs_T^2 T = d T
+    n5 *= 1.f - P.Gpi;
+    n6 *= 1.f - P.Gpi;
+    const float s6 = 1.f / 6.f;
+    float q0 = P.w0 * qs, q1 = P.w1 * qs;
+    g[0] = T - n4 + q0;
+    g[1] = s6 * (3.f * n1 + n4 + n5 + n6) + q1;
+    g[2] = s6 * (-3.f * n1 + n4 + n5 + n6) + q1;
+    g[3] = s6 * (3.f * n2 + n4 - 2.f * n5 + n6) + q1;
+    g[4] = s6 * (-3.f * n2 + n4 - 2.f * n5 + n6) + q1;
+    g[5] = s6 * (3.f * n3 + n4 + n5 - 2.f * n6) + q1;
+    g[6] = s6 * (-3.f * n3 + n4 + n5 - 2.f * n6) + q1;
+    return phis;
+}
+
+}  // namespace gb300lbm

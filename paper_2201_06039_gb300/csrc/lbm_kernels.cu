@@ -1,0 +1,290 @@
+// Two-pass kernels of the lattice update, initialisation, moments and deterministic
+// FP64 reductions.  See lbm_device.cuh for the per-node arithmetic.
+#include "lbm_launch.h"
+
+namespace gb300lbm {
+
+constexpr int TPB_X = 32, TPB_Y = 8, TPB = TPB_X * TPB_Y;
+constexpr int SUM_BLOCKS_MAX = 1184;   // 8 x 148-152 SMs worth of blocks for field sums
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic two-value FP64 sum over the grid: each block writes its partial, the last
+// block to finish (atomic ticket) adds the partials in index order and resets the ticket.
+// The result depends only on the grid shape, never on block scheduling.
+template <int NT>
+__device__ void grid_sum2(double a, double b, double2* partial, unsigned* counter, double* out) {
+    __shared__ double sa[NT / 32], sb[NT / 32];
+    __shared__ int is_last;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int nblocks = gridDim.x * gridDim.y * gridDim.z;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if ((tid & 31) == 0) { sa[tid >> 5] = a; sb[tid >> 5] = b; }
+    __syncthreads();
+    if (tid == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int w = 0; w < NT / 32; ++w) { ta += sa[w]; tb += sb[w]; }
+        partial[bid] = make_double2(ta, tb);
+        __threadfence();
+        unsigned ticket = atomicAdd(counter, 1u);
+        is_last = (ticket == (unsigned)(nblocks - 1));
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    double ta = 0.0, tb = 0.0;
+    for (int k = tid; k < nblocks; k += NT) {
+        double2 p = __ldcg(partial + k);
+        ta += p.x;
+        tb += p.y;
+    }
+    ta = warp_sum(ta);
+    tb = warp_sum(tb);
+    __syncthreads();
+    if ((tid & 31) == 0) { sa[tid >> 5] = ta; sb[tid >> 5] = tb; }
+    __syncthreads();
+    if (tid == 0) {
+        double ra = 0.0, rb = 0.0;
+        for (int w = 0; w < NT / 32; ++w) { ra += sa[w]; rb += sb[w]; }
+        out[0] = ra;
+        out[1] = rb;
+        *counter = 0u;
+    }
+}
+
+// ---------------------------------------------------------------- init
+template <typename S>
+__global__ void __launch_bounds__(TPB) k_init(DevParams P, S* __restrict__ f, S* __restrict__ g,
+                                             const float* __restrict__ rho, const float* __restrict__ T,
+                                             const float* __restrict__ u) {
+    int x = blockIdx.x * TPB_X + threadIdx.x, y = blockIdx.y * TPB_Y + threadIdx.y, z = blockIdx.z;
+    if (x >= P.nx || y >= P.ny) return;
+    int i = node_of(P, x, y, z);
+    float r = rho[i], t = T[i];
+    float ux = 0.f, uy = 0.f, uz = 0.f;
+    if (u) { ux = u[i]; uy = u[P.N + i]; uz = u[2 * P.N + i]; }
+    float fe[19];
+    feq(r, ux, uy, uz, fe);
+#pragma unroll
+    for (int a = 0; a < 19; ++a) Codec<S>::store(f + (size_t)a * P.N + i, fe[a], P.shift_f[a]);
+    Codec<S>::store(g + i, P.w0 * t, P.shift_g[0]);
+#pragma unroll
+    for (int a = 1; a < 7; ++a) Codec<S>::store(g + (size_t)a * P.N + i, P.w1 * t, P.shift_g[a]);
+}
+
+// ---------------------------------------------------------------- psi / EOS pass (S1-S2)
+template <typename S>
+__global__ void __launch_bounds__(TPB) k_psi(DevParams P, const S* __restrict__ fs, const S* __restrict__ gs,
+                                            int pull_f, int pull_g, float2* __restrict__ psirho,
+                                            double2* partial, unsigned* counter, double* sums, int* flag) {
+    int x = blockIdx.x * TPB_X + threadIdx.x, y = blockIdx.y * TPB_Y + threadIdx.y, z = blockIdx.z;
+    double ra = 0.0, ta = 0.0;
+    int bad = 0;
+    if (x < P.nx && y < P.ny) {
+        int i = node_of(P, x, y, z);
+        Nbr n = make_nbr(P, x, y, z);
+        float f[19], g[7];
+        load_f<S>(P, fs, pull_f, i, x, y, z, n, f);
+        load_g<S>(P, gs, pull_g, i, x, y, z, n, g);
+        float rho = 0.f, T = 0.f;
+#pragma unroll
+        for (int a = 0; a < 19; ++a) rho += f[a];
+#pragma unroll
+        for (int a = 0; a < 7; ++a) T += g[a];
+        float psi2 = psi_squared(P, rho, T);
+        bad = !(psi2 > 0.f) || !isfinite(rho) || !isfinite(T);
+        psirho[i] = make_float2(sqrtf(psi2), rho);
+        ra = rho;
+        ta = T;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0 && threadIdx.y == 0) atomicOr(flag, 1);
+    if (sums) grid_sum2<TPB>(ra, ta, partial, counter, sums);
+}
+
+// ---------------------------------------------------------------- neighbourhood terms (S3-S4)
+// F_m = -G psi(x) sum w psi(x+e) e (Eq. 7, G = -1) and grad rho = sum w rho(x+e) e.
+struct Stencil {
+    float Fx, Fy, Fz, gx, gy, gz;
+};
+
+template <int A>
+__device__ __forceinline__ void stencil_term(const DevParams& P, const float2* __restrict__ pr, int x, int y,
+                                             int z, const Nbr& n, Stencil& s) {
+    constexpr int ex = ex19(A), ey = ey19(A), ez = ez19(A);
+    constexpr float w = (ex * ex + ey * ey + ez * ez) == 1 ? (1.f / 6.f) : (1.f / 12.f);
+    int j = node_of(P, nb_c(ex, x, n.xm, n.xp), nb_c(ey, y, n.ym, n.yp), nb_c(ez, z, n.zm, n.zp));
+    float2 q = __ldg(pr + j);
+    if (ex) { s.Fx += (ex * w) * q.x; s.gx += (ex * w) * q.y; }
+    if (ey) { s.Fy += (ey * w) * q.x; s.gy += (ey * w) * q.y; }
+    if (ez) { s.Fz += (ez * w) * q.x; s.gz += (ez * w) * q.y; }
+}
+
+__device__ __forceinline__ Stencil stencil(const DevParams& P, const float2* __restrict__ pr, int x, int y,
+                                           int z, const Nbr& n) {
+    Stencil s = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    stencil_term<1>(P, pr, x, y, z, n, s); stencil_term<2>(P, pr, x, y, z, n, s);
+    stencil_term<3>(P, pr, x, y, z, n, s); stencil_term<4>(P, pr, x, y, z, n, s);
+    stencil_term<5>(P, pr, x, y, z, n, s); stencil_term<6>(P, pr, x, y, z, n, s);
+    stencil_term<7>(P, pr, x, y, z, n, s); stencil_term<8>(P, pr, x, y, z, n, s);
+    stencil_term<9>(P, pr, x, y, z, n, s); stencil_term<10>(P, pr, x, y, z, n, s);
+    stencil_term<11>(P, pr, x, y, z, n, s); stencil_term<12>(P, pr, x, y, z, n, s);
+    stencil_term<13>(P, pr, x, y, z, n, s); stencil_term<14>(P, pr, x, y, z, n, s);
+    stencil_term<15>(P, pr, x, y, z, n, s); stencil_term<16>(P, pr, x, y, z, n, s);
+    stencil_term<17>(P, pr, x, y, z, n, s); stencil_term<18>(P, pr, x, y, z, n, s);
+    return s;
+}
+
+// ---------------------------------------------------------------- stream-collide pass (S3-S12)
+template <typename S>
+__global__ void __launch_bounds__(TPB) k_collide(DevParams P, const S* __restrict__ fs, const S* __restrict__ gs,
+                                                S* __restrict__ fd, S* __restrict__ gd, int pull_f, int pull_g,
+                                                const float2* __restrict__ psirho, const double* __restrict__ sums_cur,
+                                                float* __restrict__ phis, int first) {
+    int x = blockIdx.x * TPB_X + threadIdx.x, y = blockIdx.y * TPB_Y + threadIdx.y, z = blockIdx.z;
+    if (x >= P.nx || y >= P.ny) return;
+    int i = node_of(P, x, y, z);
+    Nbr n = make_nbr(P, x, y, z);
+    float f[19], g[7];
+    load_f<S>(P, fs, pull_f, i, x, y, z, n, f);
+    load_g<S>(P, gs, pull_g, i, x, y, z, n, g);
+    float rho = 0.f, T = 0.f;
+#pragma unroll
+    for (int a = 0; a < 19; ++a) rho += f[a];
+#pragma unroll
+    for (int a = 0; a < 7; ++a) T += g[a];
+    float2 me = __ldg(psirho + i);
+    Stencil st = stencil(P, psirho, x, y, z, n);
+    float Fmx = me.x * st.Fx, Fmy = me.x * st.Fy, Fmz = me.x * st.Fz;
+    float rho_ave = (float)(sums_cur[0] / (double)P.N);
+    float db = rho - rho_ave;
+    float Fx = Fmx + db * P.gx, Fy = Fmy + db * P.gy, Fz = Fmz + db * P.gz;
+    float Fm2 = Fmx * Fmx + Fmy * Fmy + Fmz * Fmz;
+    NodeOut o = collide_f(P, f, Fx, Fy, Fz, Fm2, me.x * me.x);
+    if (!P.flow_off) {
+#pragma unroll
+        for (int a = 0; a < 19; ++a) Codec<S>::store(fd + (size_t)a * P.N + i, f[a], P.shift_f[a]);
+    }
+    float ph = collide_g(P, g, rho, T, o, st.gx, st.gy, st.gz, phis[i], first);
+    if (!P.thermal_off) {
+#pragma unroll
+        for (int a = 0; a < 7; ++a) Codec<S>::store(gd + (size_t)a * P.N + i, g[a], P.shift_g[a]);
+    }
+    phis[i] = ph;
+}
+
+// ---------------------------------------------------------------- moments (lbm_get_moments)
+template <typename S>
+__global__ void __launch_bounds__(TPB) k_moments(DevParams P, const S* __restrict__ fs, const S* __restrict__ gs,
+                                                int pull_f, int pull_g, const float2* __restrict__ psirho,
+                                                const double* __restrict__ sums_cur, float* __restrict__ orho,
+                                                float* __restrict__ oux, float* __restrict__ ouy,
+                                                float* __restrict__ ouz, float* __restrict__ oT) {
+    int x = blockIdx.x * TPB_X + threadIdx.x, y = blockIdx.y * TPB_Y + threadIdx.y, z = blockIdx.z;
+    if (x >= P.nx || y >= P.ny) return;
+    int i = node_of(P, x, y, z);
+    Nbr n = make_nbr(P, x, y, z);
+    float f[19], g[7];
+    load_f<S>(P, fs, pull_f, i, x, y, z, n, f);
+    load_g<S>(P, gs, pull_g, i, x, y, z, n, g);
+    float rho = 0.f, T = 0.f;
+#pragma unroll
+    for (int a = 0; a < 19; ++a) rho += f[a];
+#pragma unroll
+    for (int a = 0; a < 7; ++a) T += g[a];
+    float jx = (f[1] - f[2]) + (f[7] - f[8]) + (f[9] - f[10]) + (f[11] - f[12]) + (f[13] - f[14]);
+    float jy = (f[3] - f[4]) + (f[7] - f[8]) - (f[9] - f[10]) + (f[15] - f[16]) + (f[17] - f[18]);
+    float jz = (f[5] - f[6]) + (f[11] - f[12]) - (f[13] - f[14]) + (f[15] - f[16]) - (f[17] - f[18]);
+    float2 me = __ldg(psirho + i);
+    Stencil st = stencil(P, psirho, x, y, z, n);
+    float rho_ave = (float)(sums_cur[0] / (double)P.N);
+    float db = rho - rho_ave;
+    float Fx = me.x * st.Fx + db * P.gx, Fy = me.x * st.Fy + db * P.gy, Fz = me.x * st.Fz + db * P.gz;
+    float inv = 1.f / rho;
+    bool fz = P.flow_off != 0;
+    if (orho) orho[i] = rho;
+    if (oux) oux[i] = fz ? 0.f : (jx + 0.5f * Fx) * inv;
+    if (ouy) ouy[i] = fz ? 0.f : (jy + 0.5f * Fy) * inv;
+    if (ouz) ouz[i] = fz ? 0.f : (jz + 0.5f * Fz) * inv;
+    if (oT) oT[i] = T;
+}
+
+// ---------------------------------------------------------------- field sum
+__global__ void __launch_bounds__(256) k_sum_field(const float* __restrict__ a, int n, double2* partial,
+                                                   unsigned* counter, double* out) {
+    double acc = 0.0;
+    for (int i = blockIdx.x * 256 + threadIdx.x; i < n; i += gridDim.x * 256) acc += (double)a[i];
+    grid_sum2<256>(acc, 0.0, partial, counter, out);
+}
+
+// ---------------------------------------------------------------- launchers
+static dim3 grid_of(const DevParams& P) {
+    return dim3((P.nx + TPB_X - 1) / TPB_X, (P.ny + TPB_Y - 1) / TPB_Y, P.nz);
+}
+
+int reduce_blocks_psi(const DevParams& P) {
+    dim3 g = grid_of(P);
+    return (int)(g.x * g.y * g.z);
+}
+
+int max_partials(const DevParams& P) {
+    int a = reduce_blocks_psi(P);
+    return a > SUM_BLOCKS_MAX ? a : SUM_BLOCKS_MAX;
+}
+
+#define GB300_DISPATCH(prec, CALL)                                          \
+    switch (prec) {                                                          \
+    case 0: { using S = float; CALL; break; }                                \
+    case 1: { using S = __nv_bfloat16; CALL; break; }                        \
+    case 2: { using S = __half; CALL; break; }                               \
+    default: return cudaErrorInvalidValue;                                   \
+    }
+
+cudaError_t launch_init(const DevParams& P, int precision, void* f, void* g, const float* rho,
+                        const float* T, const float* u, cudaStream_t s) {
+    dim3 blk(TPB_X, TPB_Y);
+    GB300_DISPATCH(precision, (k_init<S><<<grid_of(P), blk, 0, s>>>(P, (S*)f, (S*)g, rho, T, u)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_psi(const DevParams& P, int precision, const StateBufs& B, double* sums, cudaStream_t s) {
+    dim3 blk(TPB_X, TPB_Y);
+    GB300_DISPATCH(precision, (k_psi<S><<<grid_of(P), blk, 0, s>>>(P, (const S*)B.fsrc, (const S*)B.gsrc, B.pull_f,
+                                                                    B.pull_g, B.psirho, B.partial, B.counter, sums,
+                                                                    B.flag)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_collide(const DevParams& P, int precision, const StateBufs& B, const double* sums_cur,
+                           int first, cudaStream_t s) {
+    dim3 blk(TPB_X, TPB_Y);
+    GB300_DISPATCH(precision, (k_collide<S><<<grid_of(P), blk, 0, s>>>(P, (const S*)B.fsrc, (const S*)B.gsrc,
+                                                                        (S*)B.fdst, (S*)B.gdst, B.pull_f, B.pull_g,
+                                                                        B.psirho, sums_cur, B.phis, first)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const DevParams& P, int precision, const StateBufs& B, const double* sums_cur,
+                           float* rho, float* ux, float* uy, float* uz, float* T, cudaStream_t s) {
+    dim3 blk(TPB_X, TPB_Y);
+    GB300_DISPATCH(precision, (k_moments<S><<<grid_of(P), blk, 0, s>>>(P, (const S*)B.fsrc, (const S*)B.gsrc,
+                                                                        B.pull_f, B.pull_g, B.psirho, sums_cur, rho,
+                                                                        ux, uy, uz, T)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_field(const float* a, int n, double2* partial, unsigned* counter, double* out,
+                             cudaStream_t s) {
+    int blocks = (n + 255) / 256;
+    if (blocks > SUM_BLOCKS_MAX) blocks = SUM_BLOCKS_MAX;
+    if (blocks < 1) blocks = 1;
+    k_sum_field<<<blocks, 256, 0, s>>>(a, n, partial, counter, out);
+    return cudaGetLastError();
+}
+
+}  // namespace gb300lbm

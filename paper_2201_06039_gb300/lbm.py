@@ -1,0 +1,261 @@
+"""Thin ctypes binding of the C-ABI in include/lbm.h (same names, argument marshalling only).
+
+Every step of the lattice update runs in the CUDA kernels of libgb300lbm.so; there is no
+CPU fallback.  If the library is missing this module raises at import of `lib()`.
+Field arguments may be numpy arrays (host memory; copied inside the call) or CUDA torch
+tensors (device memory; used in place).  All fields are float32, shape (nz, ny, nx) or
+flat, node index x + nx*(y + ny*z); a velocity field is (3, nz, ny, nx).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ESTATE, LBM_ENONFINITE, LBM_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+LBM_BC_PERIODIC, LBM_BC_WALL, LBM_BC_OUTFLOW, LBM_BC_THERMAL_ONLY = 0, 1, 2, 3
+LBM_FP32, LBM_BF16_SHIFTED, LBM_FP16_SHIFTED = 0, 1, 2
+LBM_KERNEL_AUTO, LBM_KERNEL_TWO_PASS, LBM_KERNEL_FUSED = 0, 1, 2
+
+
+class LbmParams(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("bc", C.c_int * 6),
+        ("T_wall", C.c_double * 6),
+        ("hot_dT", C.c_double), ("hot_sigma", C.c_double),
+        ("a", C.c_double), ("b", C.c_double), ("R", C.c_double), ("acentric", C.c_double),
+        ("sigma", C.c_double),
+        ("tau_e", C.c_double), ("tau_v", C.c_double), ("tau_q", C.c_double), ("tau_pi", C.c_double),
+        ("cV", C.c_double), ("d", C.c_double), ("varsigma_q", C.c_double), ("varsigma_pi", C.c_double),
+        ("lambda_mode", C.c_int), ("chi_or_lambda", C.c_double),
+        ("g", C.c_double * 3),
+        ("flow_off", C.c_int), ("thermal_off", C.c_int),
+        ("precision", C.c_int), ("rho_ref", C.c_double), ("T_ref", C.c_double),
+        ("kernel", C.c_int), ("use_graph", C.c_int), ("check_nonfinite", C.c_int),
+        ("cuda_stream", C.c_void_p),
+        ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
+    ]
+
+
+# every symbol include/lbm.h declares
+EXPORTS = ["lbm_params_default", "lbm_eos_critical", "lbm_workspace_bytes", "lbm_create",
+           "lbm_init_fields", "lbm_step", "lbm_get_moments", "lbm_get_totals", "lbm_steps_done",
+           "lbm_kernel_in_use",
+           "lbm_step_profiled", "lbm_destroy", "lbm_status_str", "lbm_last_error"]
+
+_lib = None
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libgb300lbm.so (building it from source if needed); raise if it cannot be had."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"CUDA library {_build.LIB} is missing: build it with paper_2201_06039_gb300.build")
+    L = C.CDLL(_build.LIB)
+    P = C.POINTER(LbmParams)
+    vp, fp, dp = C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_double)
+    L.lbm_params_default.argtypes = [P]
+    L.lbm_params_default.restype = None
+    L.lbm_eos_critical.argtypes = [P, dp, dp]
+    L.lbm_workspace_bytes.argtypes = [P]
+    L.lbm_workspace_bytes.restype = C.c_size_t
+    L.lbm_create.argtypes = [P, C.POINTER(vp)]
+    L.lbm_init_fields.argtypes = [vp, vp, vp, vp]
+    L.lbm_step.argtypes = [vp, C.c_int]
+    L.lbm_get_moments.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.lbm_get_totals.argtypes = [vp, dp, dp, dp]
+    L.lbm_steps_done.argtypes = [vp]
+    L.lbm_steps_done.restype = C.c_longlong
+    L.lbm_kernel_in_use.argtypes = [vp]
+    L.lbm_step_profiled.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_int)]
+    L.lbm_destroy.argtypes = [vp]
+    L.lbm_destroy.restype = None
+    L.lbm_status_str.argtypes = [C.c_int]
+    L.lbm_status_str.restype = C.c_char_p
+    L.lbm_last_error.argtypes = []
+    L.lbm_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc: int, what: str):
+    if rc != LBM_OK:
+        L = lib(False)
+        raise LbmError(rc, f"{what}: {L.lbm_status_str(rc).decode()}: {L.lbm_last_error().decode()}")
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array (host) or a torch tensor (device or host)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.float32 and a.flags["C_CONTIGUOUS"], "fields must be contiguous float32"
+        return a.ctypes.data
+    import torch
+    if isinstance(a, torch.Tensor):
+        assert a.dtype == torch.float32 and a.is_contiguous(), "fields must be contiguous float32"
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+# ------------------------------------------------------------------- the C-ABI, same names
+def lbm_params_default() -> LbmParams:
+    p = LbmParams()
+    lib().lbm_params_default(C.byref(p))
+    return p
+
+
+def lbm_eos_critical(p: LbmParams):
+    Tc, pc = C.c_double(), C.c_double()
+    _check(lib().lbm_eos_critical(C.byref(p), C.byref(Tc), C.byref(pc)), "lbm_eos_critical")
+    return Tc.value, pc.value
+
+
+def lbm_workspace_bytes(p: LbmParams) -> int:
+    return int(lib().lbm_workspace_bytes(C.byref(p)))
+
+
+def lbm_create(p: LbmParams):
+    h = C.c_void_p()
+    _check(lib().lbm_create(C.byref(p), C.byref(h)), "lbm_create")
+    return h
+
+
+def lbm_init_fields(ctx, rho, T, u=None):
+    _check(lib().lbm_init_fields(ctx, _ptr(rho), _ptr(T), _ptr(u)), "lbm_init_fields")
+
+
+def lbm_step(ctx, n: int):
+    _check(lib().lbm_step(ctx, int(n)), "lbm_step")
+
+
+def lbm_get_moments(ctx, rho=None, ux=None, uy=None, uz=None, T=None):
+    _check(lib().lbm_get_moments(ctx, _ptr(rho), _ptr(ux), _ptr(uy), _ptr(uz), _ptr(T)), "lbm_get_moments")
+
+
+def lbm_get_totals(ctx):
+    m, t, r = C.c_double(), C.c_double(), C.c_double()
+    _check(lib().lbm_get_totals(ctx, C.byref(m), C.byref(t), C.byref(r)), "lbm_get_totals")
+    return m.value, t.value, r.value
+
+
+def lbm_steps_done(ctx) -> int:
+    return int(lib().lbm_steps_done(ctx))
+
+
+def lbm_kernel_in_use(ctx) -> int:
+    return int(lib().lbm_kernel_in_use(ctx))
+
+
+def lbm_step_profiled(ctx, n: int):
+    ms = (C.c_double * 3)()
+    cnt = (C.c_int * 3)()
+    _check(lib().lbm_step_profiled(ctx, int(n), ms, cnt), "lbm_step_profiled")
+    return list(ms), list(cnt)
+
+
+def lbm_destroy(ctx):
+    if ctx:
+        lib().lbm_destroy(ctx)
+
+
+# ------------------------------------------------------------------- convenience
+def params_from_setup(setup, **overrides) -> LbmParams:
+    """Map a workloads.LatticeSetup onto lbm_params (temperatures scaled by this library's Tc)."""
+    p = lbm_params_default()
+    p.nx, p.ny, p.nz = setup.nx, setup.ny, setup.nz
+    for k in range(6):
+        p.bc[k] = int(setup.bc[k])
+    p.a, p.b, p.R, p.acentric = setup.a, setup.b, setup.R, setup.acentric
+    Tc, _ = lbm_eos_critical(p)
+    for k in range(6):
+        p.T_wall[k] = setup.T_wall_over_Tc[k] * Tc
+    p.hot_dT = setup.hot_dT_over_Tc * Tc
+    p.hot_sigma = setup.hot_sigma
+    p.sigma = setup.sigma
+    p.tau_e, p.tau_v, p.tau_q, p.tau_pi = setup.tau_e, setup.tau_v, setup.tau_q, setup.tau_pi
+    p.cV, p.d, p.varsigma_q, p.varsigma_pi = setup.cV, setup.d, setup.varsigma_q, setup.varsigma_pi
+    p.lambda_mode, p.chi_or_lambda = setup.lambda_mode, setup.chi_or_lambda
+    for k in range(3):
+        p.g[k] = setup.gravity[k]
+    p.flow_off, p.thermal_off = setup.flow_off, setup.thermal_off
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+class Lattice:
+    """One lattice on the current CUDA device; device memory comes from torch."""
+
+    def __init__(self, params: LbmParams, stream=None):
+        import torch
+        self.params = params
+        self.shape = (params.nz, params.ny, params.nx)
+        self.N = params.nx * params.ny * params.nz
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        params.cuda_stream = self.stream.cuda_stream
+        nbytes = lbm_workspace_bytes(params)
+        if nbytes == 0:
+            _check(LBM_EINVAL, "lbm_workspace_bytes")
+        self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self._ws.data_ptr()
+        params.workspace = (base + 255) & ~255
+        params.workspace_bytes = nbytes
+        self.ctx = lbm_create(params)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, rho, T, u=None):
+        def f32(a):
+            if a is None or not isinstance(a, np.ndarray):
+                return a
+            return np.ascontiguousarray(a, dtype=np.float32)
+        lbm_init_fields(self.ctx, f32(rho), f32(T), f32(u))
+
+    def step(self, n: int = 1):
+        lbm_step(self.ctx, n)
+
+    def moments(self):
+        """Host copies of rho, ux, uy, uz, T (float32 numpy, shape (nz, ny, nx))."""
+        out = {k: np.empty(self.shape, dtype=np.float32) for k in ("rho", "ux", "uy", "uz", "T")}
+        lbm_get_moments(self.ctx, out["rho"], out["ux"], out["uy"], out["uz"], out["T"])
+        return out
+
+    def totals(self):
+        return lbm_get_totals(self.ctx)
+
+    @property
+    def kernel(self):
+        return lbm_kernel_in_use(self.ctx)
+
+    @property
+    def steps_done(self):
+        return lbm_steps_done(self.ctx)

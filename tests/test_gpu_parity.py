@@ -1,0 +1,163 @@
+"""GPU (C-ABI, CUDA kernels) against the FP64 oracle on identical seeded inputs.
+
+Bar: max|x_gpu - x_oracle| / max|x_oracle| <= 1e-5 for rho, T and each velocity component
+(FP32 populations), element by element over the whole lattice.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests._parity import inputs, rel_errors, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+VARIANTS = [1, 2]   # LBM_KERNEL_TWO_PASS, LBM_KERNEL_FUSED
+
+
+def _variant_ok(v, setup):
+    from paper_2201_06039_gb300 import lbm
+    p = lbm.params_from_setup(setup, kernel=v)
+    try:
+        lat = lbm.Lattice(p)
+        lat.close()
+        return True
+    except lbm.LbmError:
+        return False
+
+
+def _compare(case, steps, variant, tol=TOL, u=None):
+    rho, T, u0 = inputs(case)
+    u = u if u is not None else u0
+    s = case["setup"]
+    if not _variant_ok(variant, s):
+        pytest.skip("variant does not support this lattice")
+    orc = run_oracle(s, rho, T, u, steps)
+    gpu, _ = run_gpu(s, rho, T, u, steps, kernel=variant)
+    err = rel_errors(gpu, orc)
+    print(case.get("name", ""), "variant", variant, "steps", steps, err)
+    for k, v in err.items():
+        assert v <= tol, (k, v, err)
+    return err
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_parity_static_droplet_32cubed_1000_steps(variant):
+    _compare(W.static_droplet(32), 1000, variant)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_parity_ragged_box_walls_outflow_hot_spot(variant):
+    s = W.LatticeSetup(37, 11, 19, bc=(W.BC_WALL, W.BC_WALL, 0, 0, W.BC_WALL, W.BC_OUTFLOW),
+                       T_wall_over_Tc=(0.86, 0.88, 0.86, 0.86, 0.86, 0.86), hot_dT_over_Tc=0.10,
+                       hot_sigma=3.0, sigma=W.SIGMA_STAR, gravity=(0, 0, -3e-5))
+    case = dict(name="ragged pool", setup=s, kind="pool", height=8.0, W=4.0, Tr_liquid=0.86)
+    _compare(case, 300, variant)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_parity_evaporation_thermal_faces_lambda_mode(variant):
+    case = W.evaporation(24, R0=7.0)
+    _compare(case, 300, variant)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_parity_pool_boiling_small(variant):
+    case = W.pool_boiling(40, 36, 48, height=16.0, hot_sigma=4.0)
+    _compare(case, 400, variant)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_parity_flow_off_and_thermal_off(variant):
+    s = W.LatticeSetup(20, 18, 9, sigma=W.SIGMA_STAR, flow_off=1,
+                       bc=(0, 0, 0, 0, W.BC_THERMAL_ONLY, W.BC_THERMAL_ONLY),
+                       T_wall_over_Tc=(0.86, 0.86, 0.86, 0.86, 0.92, 0.84))
+    case = dict(name="conduction", setup=s, kind="droplet", R0=5.0, W=4.0, Tr_drop=0.86, Tr_gas=0.86)
+    _compare(case, 200, variant)
+    s2 = W.LatticeSetup(24, 20, 18, sigma=W.SIGMA_STAR, thermal_off=1)
+    case2 = dict(name="isothermal", setup=s2, kind="droplet", R0=6.0, W=4.0, Tr_drop=0.86, Tr_gas=0.86)
+    _compare(case2, 200, variant)
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 16), (16, 1, 1), (1, 12, 1), (2, 2, 2), (33, 9, 3)])
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_parity_degenerate_and_tiny_lattices(shape, variant):
+    nx, ny, nz = shape
+    s = W.LatticeSetup(nx, ny, nz, sigma=W.SIGMA_STAR, gravity=(0, 0, -3e-5))
+    rho, T = W.random_state(s.shape, 77, rho_lo=0.35, rho_hi=0.45, T_lo=0.060, T_hi=0.065)
+    rho = rho.astype(np.float32).astype(np.float64)
+    T = T.astype(np.float32).astype(np.float64)
+    if not _variant_ok(variant, s):
+        pytest.skip("variant does not support this lattice")
+    orc = run_oracle(s, rho, T, None, 50)
+    gpu, _ = run_gpu(s, rho, T, None, 50, kernel=variant)
+    err = rel_errors(gpu, orc)
+    for k, v in err.items():
+        assert v <= TOL, (k, v, err)
+
+
+def test_graph_replay_is_bit_identical_to_plain_launches():
+    case = W.pool_boiling(40, 36, 48, height=16.0, hot_sigma=4.0)
+    rho, T, u = inputs(case)
+    a, _ = run_gpu(case["setup"], rho, T, u, 37, use_graph=1)
+    b, _ = run_gpu(case["setup"], rho, T, u, 37, use_graph=0)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_gpu_mass_conservation_fp64_totals():
+    case = W.static_droplet(32)
+    rho, T, u = inputs(case)
+    from paper_2201_06039_gb300 import lbm
+    lat = lbm.Lattice(lbm.params_from_setup(case["setup"]))
+    lat.init(rho, T)
+    m0, _, r0 = lat.totals()
+    assert abs(m0 / rho.sum() - 1) < 1e-6
+    lat.step(500)
+    m1, _, r1 = lat.totals()
+    lat.close()
+    assert abs(m1 / m0 - 1) < 1e-6
+    assert abs(r1 * rho.size / m0 - 1) < 1e-6
+
+
+def test_nonfinite_state_reported_and_context_recovers():
+    """Host-side fault injection: a node outside the psi domain (Eq. 8) must surface as
+    LBM_ENONFINITE from lbm_step; re-initialising the context makes it usable again."""
+    from paper_2201_06039_gb300 import lbm
+    case = W.static_droplet(16, R0=4.0)
+    rho, T, u = inputs(case)
+    bad = rho.copy()
+    bad[3, 4, 5] = 9.8          # rho/3 - p_EOS < 0 at 0.86 Tc: psi^2 <= 0
+    lat = lbm.Lattice(lbm.params_from_setup(case["setup"]))
+    lat.init(bad, T)
+    with pytest.raises(lbm.LbmError) as ei:
+        lat.step(3)
+    assert ei.value.status == lbm.LBM_ENONFINITE
+    lat.init(rho, T)
+    lat.step(10)
+    m = lat.moments()
+    assert np.all(np.isfinite(m["rho"]))
+    lat.close()
+
+
+def test_step_before_init_is_a_state_error():
+    from paper_2201_06039_gb300 import lbm
+    lat = lbm.Lattice(lbm.params_from_setup(W.LatticeSetup(8, 8, 8)))
+    with pytest.raises(lbm.LbmError) as ei:
+        lat.step(1)
+    assert ei.value.status == lbm.LBM_ESTATE
+    lat.close()
+
+
+@pytest.mark.slow
+def test_parity_full_size_pool_boiling_200x200x300():
+    """The benchmarked workload at full size (12.0M nodes, the bench's kernel variant and graph
+    replay), a few steps, every node against the oracle."""
+    case = W.pool_boiling()
+    rho, T, u = inputs(case)
+    orc = run_oracle(case["setup"], rho, T, u, 3)
+    gpu, _ = run_gpu(case["setup"], rho, T, u, 3)
+    err = rel_errors(gpu, orc)
+    print("full size", err)
+    for k, v in err.items():
+        assert v <= TOL, (k, v, err)
