@@ -41,7 +41,11 @@ PREC_CODE = {"fp32": 0, "bf16": 1, "fp16": 2}
 KERNEL_CODE = {"auto": 0, "two_pass": 1, "fused": 2}
 
 
-def workload(name):
+def workload(name, nx=None, ny=None, nz=None):
+    if name == "pool_boiling" and (nx or ny or nz):
+        nx, ny, nz = nx or 200, ny or 200, nz or 300
+        scale = nz / 300.0
+        return W.pool_boiling(nx, ny, nz, height=100.0 * scale, hot_sigma=10.0 * min(nx, ny) / 200.0)
     if name == "pool_boiling":
         return W.pool_boiling()
     if name == "evaporation":
@@ -187,7 +191,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    case = workload(args.workload)
+    case = workload(args.workload, args.nx, args.ny, args.nz)
     import oracle
     s = case["setup"]
     total_budget = 150.0
@@ -243,7 +247,7 @@ def run_mine(args):
         torch.distributed.barrier()
     from paper_2201_06039_gb300 import lbm
 
-    case = workload(args.workload)
+    case = workload(args.workload, args.nx, args.ny, args.nz)
     s = case["setup"]
     N = s.n_nodes
     rho, T = init_fields(case)
@@ -355,6 +359,9 @@ def main():
     ap.add_argument("--kernel", default="auto", choices=list(KERNEL_CODE))
     ap.add_argument("--precision", default="fp32", choices=list(PREC_CODE))
     ap.add_argument("--workload", default="pool_boiling")
+    ap.add_argument("--nx", type=int, default=None, help="override the lattice size (profiling runs)")
+    ap.add_argument("--ny", type=int, default=None)
+    ap.add_argument("--nz", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -23,8 +23,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _LIB_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIB_DIR, "liblbm_oracle.so")
+_LIB32 = os.path.join(_LIB_DIR, "liblbm_oracle_f32.so")   # same source, -DORC_REAL=float
 _lock = threading.Lock()
 _lib = None
+_lib32 = None
 
 
 class OrcParams(C.Structure):
@@ -44,52 +46,63 @@ class OrcParams(C.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, IEEE arithmetic, OpenMP over z-planes)."""
+    """Compile the oracle with gcc (plain -O2, IEEE arithmetic, OpenMP over z-planes): the FP64
+    oracle, and the FP32 build of the same source that the tests use to measure rounding floors."""
     with _lock:
-        if (not force and os.path.exists(_LIB)
-                and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-            return _LIB
-        os.makedirs(_LIB_DIR, exist_ok=True)
-        tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=gnu99", "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
+        for out, extra in ((_LIB, []), (_LIB32, ["-DORC_REAL=float"])):
+            if (not force and os.path.exists(out)
+                    and os.path.getmtime(out) >= os.path.getmtime(_SRC)):
+                continue
+            os.makedirs(_LIB_DIR, exist_ok=True)
+            tmp = out + f".tmp{os.getpid()}"
+            cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=gnu99", *extra, "-o", tmp, _SRC, "-lm"]
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, out)
         return _LIB
 
 
-def lib():
-    global _lib
+def lib(precision: str = "f64"):
+    global _lib, _lib32
+    if precision == "f32":
+        if _lib32 is None:
+            build()
+            _lib32 = _bind(C.CDLL(_LIB32))
+        return _lib32
     if _lib is None:
         build()
-        L = C.CDLL(_LIB)
-        dp = C.POINTER(C.c_double)
-        L.orc_create.restype = C.c_void_p
-        L.orc_create.argtypes = [C.POINTER(OrcParams)]
-        L.orc_destroy.argtypes = [C.c_void_p]
-        L.orc_init.argtypes = [C.c_void_p, dp, dp, dp]
-        L.orc_step.argtypes = [C.c_void_p, C.c_int]
-        L.orc_moments.argtypes = [C.c_void_p, dp, dp, dp, dp, dp]
-        L.orc_get_pops.argtypes = [C.c_void_p, dp, dp]
-        L.orc_set_pops.argtypes = [C.c_void_p, dp, dp]
-        L.orc_get_diag.argtypes = [C.c_void_p, dp, dp, dp, dp, dp, dp]
-        L.orc_get_rho_ave.restype = C.c_double
-        L.orc_get_rho_ave.argtypes = [C.c_void_p]
-        L.orc_set_rho_ave.argtypes = [C.c_void_p, C.c_double]
-        L.orc_Tc.restype = C.c_double
-        L.orc_Tc.argtypes = [C.POINTER(OrcParams)]
-        L.orc_p_eos.restype = C.c_double
-        L.orc_p_eos.argtypes = [C.POINTER(OrcParams), C.c_double, C.c_double]
-        L.orc_matrix_M.argtypes = [dp]
-        L.orc_matrix_N.argtypes = [dp]
-        L.orc_matrix_Ninv.argtypes = [dp]
-        L.orc_velocities19.argtypes = [C.POINTER(C.c_int)]
-        L.orc_invert.argtypes = [C.c_int, dp, dp]
-        L.orc_collide_node.argtypes = [C.POINTER(OrcParams), dp, dp, dp, C.c_double, dp, dp]
-        L.orc_feq.argtypes = [C.c_double, dp, dp]
-        L.orc_force_pops.argtypes = [C.POINTER(OrcParams), dp, dp, dp, C.c_double, dp]
-        L.orc_num_threads.restype = C.c_int
-        _lib = L
+        _lib = _bind(C.CDLL(_LIB))
     return _lib
+
+
+def _bind(L):
+    """Declare the argument and return types of the oracle's exported functions."""
+    dp = C.POINTER(C.c_double)
+    L.orc_create.restype = C.c_void_p
+    L.orc_create.argtypes = [C.POINTER(OrcParams)]
+    L.orc_destroy.argtypes = [C.c_void_p]
+    L.orc_init.argtypes = [C.c_void_p, dp, dp, dp]
+    L.orc_step.argtypes = [C.c_void_p, C.c_int]
+    L.orc_moments.argtypes = [C.c_void_p, dp, dp, dp, dp, dp]
+    L.orc_get_pops.argtypes = [C.c_void_p, dp, dp]
+    L.orc_set_pops.argtypes = [C.c_void_p, dp, dp]
+    L.orc_get_diag.argtypes = [C.c_void_p, dp, dp, dp, dp, dp, dp]
+    L.orc_get_rho_ave.restype = C.c_double
+    L.orc_get_rho_ave.argtypes = [C.c_void_p]
+    L.orc_set_rho_ave.argtypes = [C.c_void_p, C.c_double]
+    L.orc_Tc.restype = C.c_double
+    L.orc_Tc.argtypes = [C.POINTER(OrcParams)]
+    L.orc_p_eos.restype = C.c_double
+    L.orc_p_eos.argtypes = [C.POINTER(OrcParams), C.c_double, C.c_double]
+    L.orc_matrix_M.argtypes = [dp]
+    L.orc_matrix_N.argtypes = [dp]
+    L.orc_matrix_Ninv.argtypes = [dp]
+    L.orc_velocities19.argtypes = [C.POINTER(C.c_int)]
+    L.orc_invert.argtypes = [C.c_int, dp, dp]
+    L.orc_collide_node.argtypes = [C.POINTER(OrcParams), dp, dp, dp, C.c_double, dp, dp]
+    L.orc_feq.argtypes = [C.c_double, dp, dp]
+    L.orc_force_pops.argtypes = [C.POINTER(OrcParams), dp, dp, dp, C.c_double, dp]
+    L.orc_num_threads.restype = C.c_int
+    return L
 
 
 def _dp(a: Optional[np.ndarray]):
@@ -169,20 +182,24 @@ def maxwell(s, T: float, tol: float = 1e-13):
 
 
 class Oracle:
-    """One FP64 lattice: init(rho, T[, u]) -> step(n) -> moments()."""
+    """One FP64 lattice: init(rho, T[, u]) -> step(n) -> moments().
 
-    def __init__(self, setup):
+    precision="f32" runs the FP32 build of the same source (rounding-floor measurements only).
+    """
+
+    def __init__(self, setup, precision: str = "f64"):
         self.setup = setup
         self.params = params_from_setup(setup)
         self.N = setup.n_nodes
         self.shape = setup.shape
-        self._h = lib().orc_create(C.byref(self.params))
+        self._L = lib(precision)
+        self._h = self._L.orc_create(C.byref(self.params))
         if not self._h:
             raise MemoryError("orc_create failed")
 
     def close(self):
         if self._h:
-            lib().orc_destroy(self._h)
+            self._L.orc_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -192,18 +209,18 @@ class Oracle:
         rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
         T = np.ascontiguousarray(T, dtype=np.float64).reshape(-1)
         uu = None if u is None else np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
-        rc = lib().orc_init(self._h, _dp(rho), _dp(T), _dp(uu))
+        rc = self._L.orc_init(self._h, _dp(rho), _dp(T), _dp(uu))
         if rc:
             raise RuntimeError(f"orc_init rc={rc}")
 
     def step(self, n: int = 1):
-        rc = lib().orc_step(self._h, int(n))
+        rc = self._L.orc_step(self._h, int(n))
         if rc:
             raise FloatingPointError(f"oracle step failed rc={rc} (non-finite or psi^2 <= 0)")
 
     def moments(self):
         out = [np.empty(self.N) for _ in range(5)]
-        rc = lib().orc_moments(self._h, *[_dp(a) for a in out])
+        rc = self._L.orc_moments(self._h, *[_dp(a) for a in out])
         if rc:
             raise FloatingPointError(f"oracle moments failed rc={rc}")
         rho, ux, uy, uz, T = [a.reshape(self.shape) for a in out]
@@ -212,20 +229,20 @@ class Oracle:
     def pops(self):
         f = np.empty(self.N * 19)
         g = np.empty(self.N * 7)
-        lib().orc_get_pops(self._h, _dp(f), _dp(g))
+        self._L.orc_get_pops(self._h, _dp(f), _dp(g))
         return f.reshape(self.N, 19), g.reshape(self.N, 7)
 
     def set_pops(self, f, g):
         f = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)
         g = np.ascontiguousarray(g, dtype=np.float64).reshape(-1)
-        lib().orc_set_pops(self._h, _dp(f), _dp(g))
+        self._L.orc_set_pops(self._h, _dp(f), _dp(g))
 
     def diag(self):
         """div u (Eq. 48), grad T (Eq. 45), grad rho, F_m, phi_s, psi of the last step."""
         N = self.N
         d = dict(divu=np.empty(N), gradT=np.empty(3 * N), gradrho=np.empty(3 * N),
                  Fm=np.empty(3 * N), phis=np.empty(N), psi=np.empty(N))
-        lib().orc_get_diag(self._h, _dp(d["divu"]), _dp(d["gradT"]), _dp(d["gradrho"]),
+        self._L.orc_get_diag(self._h, _dp(d["divu"]), _dp(d["gradT"]), _dp(d["gradrho"]),
                            _dp(d["Fm"]), _dp(d["phis"]), _dp(d["psi"]))
         for k in ("gradT", "gradrho", "Fm"):
             d[k] = d[k].reshape(self.shape + (3,))
@@ -235,7 +252,7 @@ class Oracle:
 
     @property
     def rho_ave(self):
-        return lib().orc_get_rho_ave(self._h)
+        return self._L.orc_get_rho_ave(self._h)
 
 
 def matrices():

@@ -53,6 +53,15 @@
 #include <omp.h>
 #endif
 
+/* Arithmetic precision of the state and of every per-node operation.  The oracle is FP64;
+ * building with -DORC_REAL=float gives the same algorithm in FP32, which the tests use only to
+ * measure the rounding floor of FP32 arithmetic on a case (matrices, parameters, the rho_ave
+ * mean and the API stay FP64). */
+#ifndef ORC_REAL
+#define ORC_REAL double
+#endif
+typedef ORC_REAL real;
+
 #define Q19 19
 #define Q7 7
 
@@ -77,14 +86,14 @@ typedef struct {
 typedef struct {
     orc_params p;
     long N;
-    double *f, *g, *fn, *gn;
-    double *fs, *gp;         /* post-collision f*, g+ */
-    double *rho, *T, *psi;
-    double *phis_prev, *phis;
-    double *divu, *gradT, *gradrho, *Fm;   /* diagnostics of the last step */
+    real *f, *g, *fn, *gn;
+    real *fs, *gp;         /* post-collision f*, g+ */
+    real *rho, *T, *psi;
+    real *phis_prev, *phis;
+    real *divu, *gradT, *gradrho, *Fm;   /* diagnostics of the last step */
     int first;
-    double rho_ave;          /* value the next step uses */
-    double M[Q19 * Q19], Minv[Q19 * Q19];
+    double rho_ave;        /* value the next step uses (FP64 mean) */
+    real M[Q19 * Q19], Minv[Q19 * Q19];
     int ok;
 } orc_state;
 
@@ -98,7 +107,7 @@ static const int TY[Q7] = {0, 0, 0, 1, -1, 0, 0};
 static const int TZ[Q7] = {0, 0, 0, 0, 0, 1, -1};
 
 /* N and N^-1 as printed (Eqs. 38, 41) */
-static const double NMAT[Q7][Q7] = {
+static const real NMAT[Q7][Q7] = {
     {1, 1, 1, 1, 1, 1, 1},
     {0, 1, -1, 0, 0, 0, 0},
     {0, 0, 0, 1, -1, 0, 0},
@@ -106,7 +115,7 @@ static const double NMAT[Q7][Q7] = {
     {0, 1, 1, 1, 1, 1, 1},
     {0, 1, 1, -1, -1, 0, 0},
     {0, 1, 1, 0, 0, -1, -1}};
-static const double NINV6[Q7][Q7] = {   /* times 1/6 */
+static const real NINV6[Q7][Q7] = {   /* times 1/6 */
     {6, 0, 0, 0, -6, 0, 0},
     {0, 3, 0, 0, 1, 1, 1},
     {0, -3, 0, 0, 1, 1, 1},
@@ -115,8 +124,8 @@ static const double NINV6[Q7][Q7] = {   /* times 1/6 */
     {0, 0, 0, 3, 1, 1, -2},
     {0, 0, 0, -3, 1, 1, -2}};
 
-static const double CS2 = 1.0 / 3.0;
-static const double G_INT = -1.0;   /* interaction strength G of Eqs. 7-8 */
+static const real CS2 = 1.0 / 3.0;
+static const real G_INT = -1.0;   /* interaction strength G of Eqs. 7-8 */
 
 /* ---------------------------------------------------------------- matrices */
 
@@ -195,25 +204,27 @@ void orc_velocities19(int* e) { for (int a = 0; a < Q19; ++a) { e[3*a] = EX[a]; 
 /* Peng-Robinson constants: a = 0.45724 R^2 Tc^2/pc and b = 0.0778 R Tc/pc (Eq. 49 text) */
 double orc_Tc(const orc_params* p) { return 0.0778 * p->a / (0.45724 * p->b * p->R); }
 
-double orc_p_eos(const orc_params* p, double rho, double T) {
-    double Tc = orc_Tc(p);
-    double om = p->acentric;
-    double kap = 0.37464 + 1.54226 * om - 0.26992 * om * om;
-    double s = 1.0 + kap * (1.0 - sqrt(T / Tc));
-    double theta = s * s;                                        /* vartheta(T) */
+static real p_eos(const orc_params* p, real rho, real T) {
+    real Tc = (real)orc_Tc(p);
+    real om = p->acentric;
+    real kap = 0.37464 + 1.54226 * om - 0.26992 * om * om;
+    real s = 1.0 + kap * (1.0 - sqrt(T / Tc));
+    real theta = s * s;                                        /* vartheta(T) */
     return rho * p->R * T / (1.0 - p->b * rho)
          - p->a * theta * rho * rho / (1.0 + 2.0 * p->b * rho - p->b * p->b * rho * rho);
 }
 
+double orc_p_eos(const orc_params* p, double rho, double T) { return (double)p_eos(p, (real)rho, (real)T); }
+
 /* (dp/dT)_rho as the paper approximates it in Sec. IV.A */
-static double dpdT(const orc_params* p, double rho) { return rho * p->R / (1.0 - p->b * rho); }
+static real dpdT(const orc_params* p, real rho) { return rho * p->R / (1.0 - p->b * rho); }
 
 /* ---------------------------------------------------------------- collision pieces */
 
-static void m_equilibrium(double rho, const double u[3], double meq[Q19]) {  /* Eq. 5 */
-    double ux = u[0], uy = u[1], uz = u[2];
-    double u2 = ux * ux + uy * uy + uz * uz;
-    double phi = rho * CS2 * CS2 * (1.0 - 1.5 * u2);
+static void m_equilibrium(real rho, const real u[3], real meq[Q19]) {  /* Eq. 5 */
+    real ux = u[0], uy = u[1], uz = u[2];
+    real u2 = ux * ux + uy * uy + uz * uz;
+    real phi = rho * CS2 * CS2 * (1.0 - 1.5 * u2);
     meq[0] = rho;
     meq[1] = rho * ux; meq[2] = rho * uy; meq[3] = rho * uz;
     meq[4] = rho + rho * u2;
@@ -231,10 +242,10 @@ static void m_equilibrium(double rho, const double u[3], double meq[Q19]) {  /* 
     meq[18] = phi + rho * CS2 * (uy * uy + uz * uz);
 }
 
-static void force_moments(const orc_params* p, const double F[3], const double u[3],
-                          const double Fm[3], double psi2, double S[Q19]) {   /* Eq. 9 */
-    double Fx = F[0], Fy = F[1], Fz = F[2], ux = u[0], uy = u[1], uz = u[2];
-    double Fm2 = Fm[0] * Fm[0] + Fm[1] * Fm[1] + Fm[2] * Fm[2];
+static void force_moments(const orc_params* p, const real F[3], const real u[3],
+                          const real Fm[3], real psi2, real S[Q19]) {   /* Eq. 9 */
+    real Fx = F[0], Fy = F[1], Fz = F[2], ux = u[0], uy = u[1], uz = u[2];
+    real Fm2 = Fm[0] * Fm[0] + Fm[1] * Fm[1] + Fm[2] * Fm[2];
     S[0] = 0.0;
     S[1] = Fx; S[2] = Fy; S[3] = Fz;
     S[4] = 2.0 * (Fx * ux + Fy * uy + Fz * uz) + 6.0 * p->sigma * Fm2 / (psi2 * (p->tau_e - 0.5));
@@ -248,7 +259,7 @@ static void force_moments(const orc_params* p, const double F[3], const double u
     S[18] = 2 * CS2 * (uy * Fy + uz * Fz);
 }
 
-static void relaxation_rates(const orc_params* p, double L[Q19]) {   /* Eq. 6 */
+static void relaxation_rates(const orc_params* p, real L[Q19]) {   /* Eq. 6 */
     for (int k = 0; k < 4; ++k) L[k] = 1.0;
     L[4] = 1.0 / p->tau_e;
     for (int k = 5; k < 10; ++k) L[k] = 1.0 / p->tau_v;
@@ -261,20 +272,20 @@ static void relaxation_rates(const orc_params* p, double L[Q19]) {   /* Eq. 6 */
  * Inputs: f (post-streaming), total force F, interaction force Fm, psi^2.
  * Outputs: f*, and (optionally) u, m4 - m4eq, S4 for Eq. 48.
  */
-static void collide_f(const orc_state* s, const double f[Q19], const double F[3],
-                      const double Fm[3], double psi2, double fstar[Q19],
-                      double u_out[3], double* rho_out, double* m4neq, double* S4) {
+static void collide_f(const orc_state* s, const real f[Q19], const real F[3],
+                      const real Fm[3], real psi2, real fstar[Q19],
+                      real u_out[3], real* rho_out, real* m4neq, real* S4) {
     const orc_params* p = &s->p;
-    double rho = 0.0, j[3] = {0, 0, 0};
+    real rho = 0.0, j[3] = {0, 0, 0};
     for (int a = 0; a < Q19; ++a) {
         rho += f[a];
         j[0] += EX[a] * f[a]; j[1] += EY[a] * f[a]; j[2] += EZ[a] * f[a];
     }
-    double u[3];
+    real u[3];
     for (int i = 0; i < 3; ++i) u[i] = (j[i] + 0.5 * F[i]) / rho;       /* Eq. 10 */
-    double m[Q19], meq[Q19], S[Q19], L[Q19], ms[Q19];
+    real m[Q19], meq[Q19], S[Q19], L[Q19], ms[Q19];
     for (int k = 0; k < Q19; ++k) {
-        double acc = 0.0;
+        real acc = 0.0;
         for (int a = 0; a < Q19; ++a) acc += s->M[k * Q19 + a] * f[a];
         m[k] = acc;
     }
@@ -283,7 +294,7 @@ static void collide_f(const orc_state* s, const double f[Q19], const double F[3]
     relaxation_rates(p, L);
     for (int k = 0; k < Q19; ++k) ms[k] = m[k] - L[k] * (m[k] - meq[k]) + (1.0 - 0.5 * L[k]) * S[k];
     for (int a = 0; a < Q19; ++a) {
-        double acc = 0.0;
+        real acc = 0.0;
         for (int k = 0; k < Q19; ++k) acc += s->Minv[a * Q19 + k] * ms[k];
         fstar[a] = acc;
     }
@@ -313,10 +324,10 @@ static long stencil_neighbour(const orc_params* p, int x, int y, int z, int ex, 
     return node_index(p, c[0], c[1], c[2]);
 }
 
-static double wall_T(const orc_params* p, int face, int x, int y) {
-    double T = p->T_wall[face];
+static real wall_T(const orc_params* p, int face, int x, int y) {
+    real T = p->T_wall[face];
     if (face == 4 && p->hot_dT != 0.0) {
-        double dx = x - 0.5 * p->nx, dy = y - 0.5 * p->ny;
+        real dx = x - 0.5 * p->nx, dy = y - 0.5 * p->ny;
         T += p->hot_dT * exp(-(dx * dx + dy * dy) / (2.0 * p->hot_sigma * p->hot_sigma));
     }
     return T;
@@ -327,6 +338,15 @@ static int opposite7(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
 
 /* ---------------------------------------------------------------- API */
 
+/* M and its inverse in FP64, then stored in the state's precision */
+static int fill_matrices(orc_state* s) {
+    double M[Q19 * Q19], Mi[Q19 * Q19];
+    orc_matrix_M(M);
+    if (orc_invert(Q19, M, Mi) != 0) return -1;
+    for (int k = 0; k < Q19 * Q19; ++k) { s->M[k] = (real)M[k]; s->Minv[k] = (real)Mi[k]; }
+    return 0;
+}
+
 orc_state* orc_create(const orc_params* p) {
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return NULL;
     orc_state* s = (orc_state*)calloc(1, sizeof(orc_state));
@@ -334,27 +354,26 @@ orc_state* orc_create(const orc_params* p) {
     s->p = *p;
     s->N = (long)p->nx * p->ny * p->nz;
     long N = s->N;
-    s->f = (double*)malloc(sizeof(double) * N * Q19);
-    s->fn = (double*)malloc(sizeof(double) * N * Q19);
-    s->fs = (double*)malloc(sizeof(double) * N * Q19);
-    s->g = (double*)malloc(sizeof(double) * N * Q7);
-    s->gn = (double*)malloc(sizeof(double) * N * Q7);
-    s->gp = (double*)malloc(sizeof(double) * N * Q7);
-    s->rho = (double*)malloc(sizeof(double) * N);
-    s->T = (double*)malloc(sizeof(double) * N);
-    s->psi = (double*)malloc(sizeof(double) * N);
-    s->phis_prev = (double*)malloc(sizeof(double) * N);
-    s->phis = (double*)malloc(sizeof(double) * N);
-    s->divu = (double*)malloc(sizeof(double) * N);
-    s->gradT = (double*)malloc(sizeof(double) * N * 3);
-    s->gradrho = (double*)malloc(sizeof(double) * N * 3);
-    s->Fm = (double*)malloc(sizeof(double) * N * 3);
+    s->f = (real*)malloc(sizeof(real) * N * Q19);
+    s->fn = (real*)malloc(sizeof(real) * N * Q19);
+    s->fs = (real*)malloc(sizeof(real) * N * Q19);
+    s->g = (real*)malloc(sizeof(real) * N * Q7);
+    s->gn = (real*)malloc(sizeof(real) * N * Q7);
+    s->gp = (real*)malloc(sizeof(real) * N * Q7);
+    s->rho = (real*)malloc(sizeof(real) * N);
+    s->T = (real*)malloc(sizeof(real) * N);
+    s->psi = (real*)malloc(sizeof(real) * N);
+    s->phis_prev = (real*)malloc(sizeof(real) * N);
+    s->phis = (real*)malloc(sizeof(real) * N);
+    s->divu = (real*)malloc(sizeof(real) * N);
+    s->gradT = (real*)malloc(sizeof(real) * N * 3);
+    s->gradrho = (real*)malloc(sizeof(real) * N * 3);
+    s->Fm = (real*)malloc(sizeof(real) * N * 3);
     if (!s->f || !s->fn || !s->fs || !s->g || !s->gn || !s->gp || !s->rho || !s->T || !s->psi ||
         !s->phis_prev || !s->phis || !s->divu || !s->gradT || !s->gradrho || !s->Fm) {
         return NULL;
     }
-    orc_matrix_M(s->M);
-    if (orc_invert(Q19, s->M, s->Minv) != 0) return NULL;
+    if (fill_matrices(s)) return NULL;
     s->first = 1;
     s->ok = 1;
     return s;
@@ -371,24 +390,24 @@ void orc_destroy(orc_state* s) {
 /* f = M^-1 m_eq(rho, u0), g = w T (w_0 = 1-d, w_1..6 = d/6, Sec. III.B) */
 int orc_init(orc_state* s, const double* rho, const double* T, const double* u) {
     const orc_params* p = &s->p;
-    double w7[Q7];
+    real w7[Q7];
     w7[0] = 1.0 - p->d;
     for (int a = 1; a < Q7; ++a) w7[a] = p->d / 6.0;
     double sum = 0.0;
     for (long i = 0; i < s->N; ++i) {
-        double uu[3] = {0, 0, 0};
+        real uu[3] = {0, 0, 0};
         if (u) { uu[0] = u[i]; uu[1] = u[s->N + i]; uu[2] = u[2 * s->N + i]; }
-        double meq[Q19];
-        m_equilibrium(rho[i], uu, meq);
+        real meq[Q19];
+        m_equilibrium((real)rho[i], uu, meq);
         for (int a = 0; a < Q19; ++a) {
-            double acc = 0.0;
+            real acc = 0.0;
             for (int k = 0; k < Q19; ++k) acc += s->Minv[a * Q19 + k] * meq[k];
             s->f[i * Q19 + a] = acc;
         }
-        for (int a = 0; a < Q7; ++a) s->g[i * Q7 + a] = w7[a] * T[i];
-        sum += rho[i];
+        for (int a = 0; a < Q7; ++a) s->g[i * Q7 + a] = w7[a] * (real)T[i];
+        sum += (double)(real)rho[i];
     }
-    s->rho_ave = sum / (double)s->N;
+    s->rho_ave = sum / (real)s->N;
     s->first = 1;
     return 0;
 }
@@ -400,12 +419,12 @@ static int macroscopic(orc_state* s) {
     int bad = 0;
 #pragma omp parallel for reduction(| : bad) schedule(static)
     for (long i = 0; i < N; ++i) {
-        double r = 0.0, t = 0.0;
+        real r = 0.0, t = 0.0;
         for (int a = 0; a < Q19; ++a) r += s->f[i * Q19 + a];
         for (int a = 0; a < Q7; ++a) t += s->g[i * Q7 + a];
         s->rho[i] = r;
         s->T[i] = t;
-        double arg = 2.0 * (orc_p_eos(p, r, t) - r * CS2) / (G_INT * 1.0);   /* Eq. 8, c = 1 */
+        real arg = 2.0 * (p_eos(p, r, t) - r * CS2) / (G_INT * 1.0);   /* Eq. 8, c = 1 */
         if (!(arg > 0.0) || !isfinite(r) || !isfinite(t)) bad = 1;
         s->psi[i] = sqrt(arg);
     }
@@ -413,13 +432,13 @@ static int macroscopic(orc_state* s) {
 }
 
 /* per-node force pieces: F_m (Eq. 7) and the isotropic gradient of rho (stencil of Sec. III.C) */
-static void node_forces(const orc_state* s, int x, int y, int z, double Fm[3], double grho[3]) {
+static void node_forces(const orc_state* s, int x, int y, int z, real Fm[3], real grho[3]) {
     const orc_params* p = &s->p;
     long i = node_index(p, x, y, z);
-    double acc[3] = {0, 0, 0}, gr[3] = {0, 0, 0};
+    real acc[3] = {0, 0, 0}, gr[3] = {0, 0, 0};
     for (int a = 1; a < Q19; ++a) {
         int e2 = EX[a] * EX[a] + EY[a] * EY[a] + EZ[a] * EZ[a];
-        double w = e2 == 1 ? 1.0 / 6.0 : 1.0 / 12.0;
+        real w = e2 == 1 ? 1.0 / 6.0 : 1.0 / 12.0;
         long j = stencil_neighbour(p, x, y, z, EX[a], EY[a], EZ[a]);
         acc[0] += w * s->psi[j] * EX[a]; acc[1] += w * s->psi[j] * EY[a]; acc[2] += w * s->psi[j] * EZ[a];
         gr[0] += w * s->rho[j] * EX[a]; gr[1] += w * s->rho[j] * EY[a]; gr[2] += w * s->rho[j] * EZ[a];
@@ -434,7 +453,7 @@ static void push_stream(orc_state* s) {
     const orc_params* p = &s->p;
     long N = s->N;
     int n[3] = {p->nx, p->ny, p->nz};
-    double w7[Q7];
+    real w7[Q7];
     w7[0] = 1.0 - p->d;
     for (int a = 1; a < Q7; ++a) w7[a] = p->d / 6.0;
     for (long i = 0; i < N * Q19; ++i) s->fn[i] = NAN;
@@ -472,7 +491,7 @@ static void push_stream(orc_state* s) {
                             else face = fc;
                         }
                         if (face >= 0) {   /* Eq. 51, anti-bounce-back with the face temperature */
-                            double Tw = wall_T(p, face, c0[0], c0[1]);
+                            real Tw = wall_T(p, face, c0[0], c0[1]);
                             s->gn[i * Q7 + opposite7(a)] = -s->gp[i * Q7 + a] + 2.0 * w7[a] * Tw;
                         } else {
                             s->gn[node_index(p, c[0], c[1], c[2]) * Q7 + a] = s->gp[i * Q7 + a];
@@ -499,9 +518,9 @@ static void push_stream(orc_state* s) {
                     }
                 }
     }
-    if (p->flow_off) memcpy(s->fn, s->f, sizeof(double) * N * Q19);
-    if (p->thermal_off) memcpy(s->gn, s->g, sizeof(double) * N * Q7);
-    double* t;
+    if (p->flow_off) memcpy(s->fn, s->f, sizeof(real) * N * Q19);
+    if (p->thermal_off) memcpy(s->gn, s->g, sizeof(real) * N * Q7);
+    real* t;
     t = s->f; s->f = s->fn; s->fn = t;
     t = s->g; s->g = s->gn; s->gn = t;
 }
@@ -511,42 +530,42 @@ static int step_once(orc_state* s) {
     const orc_params* p = &s->p;
     long N = s->N;
     if (macroscopic(s)) return -5;
-    double rho_ave = s->rho_ave;
+    real rho_ave = (real)s->rho_ave;
     double sum = 0.0;
     for (long i = 0; i < N; ++i) sum += s->rho[i];
-    double w7[Q7];
+    real w7[Q7];
     w7[0] = 1.0 - p->d;
     for (int a = 1; a < Q7; ++a) w7[a] = p->d / 6.0;
-    const double csT2 = p->d / 3.0;
-    double Gam_q = 1.0 / p->varsigma_q, Gam_pi = 1.0 / p->varsigma_pi;
+    const real csT2 = p->d / 3.0;
+    real Gam_q = 1.0 / p->varsigma_q, Gam_pi = 1.0 / p->varsigma_pi;
 #pragma omp parallel for schedule(static)
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
                 long i = node_index(p, x, y, z);
-                double rho = s->rho[i], T = s->T[i];
-                double Fm[3], grho[3], F[3];
+                real rho = s->rho[i], T = s->T[i];
+                real Fm[3], grho[3], F[3];
                 node_forces(s, x, y, z, Fm, grho);
                 for (int k = 0; k < 3; ++k) F[k] = Fm[k] + (rho - rho_ave) * p->g[k];
-                double psi2 = s->psi[i] * s->psi[i];
-                double u[3], rr, m4neq, S4;
+                real psi2 = s->psi[i] * s->psi[i];
+                real u[3], rr, m4neq, S4;
                 collide_f(s, &s->f[i * Q19], F, Fm, psi2, &s->fs[i * Q19], u, &rr, &m4neq, &S4);
                 /* Eq. 48 */
-                double Fu = F[0] * u[0] + F[1] * u[1] + F[2] * u[2];
-                double divu = (-m4neq / p->tau_e + (1.0 - 0.5 / p->tau_e) * S4 - 2.0 * Fu) / (2.0 * rho * CS2);
+                real Fu = F[0] * u[0] + F[1] * u[1] + F[2] * u[2];
+                real divu = (-m4neq / p->tau_e + (1.0 - 0.5 / p->tau_e) * S4 - 2.0 * Fu) / (2.0 * rho * CS2);
                 /* thermal moments, Eq. 38 */
-                double nm[Q7];
+                real nm[Q7];
                 for (int k = 0; k < Q7; ++k) {
-                    double acc = 0.0;
+                    real acc = 0.0;
                     for (int a = 0; a < Q7; ++a) acc += NMAT[k][a] * s->g[i * Q7 + a];
                     nm[k] = acc;
                 }
-                double chi = p->lambda_mode ? p->chi_or_lambda / (rho * p->cV) : p->chi_or_lambda;
-                double vsT = chi / csT2 + 0.5;     /* chi = (varsigma_T - 0.5) cs_T^2 dt */
-                double gT[3];
+                real chi = p->lambda_mode ? p->chi_or_lambda / (rho * p->cV) : p->chi_or_lambda;
+                real vsT = chi / csT2 + 0.5;     /* chi = (varsigma_T - 0.5) cs_T^2 dt */
+                real gT[3];
                 for (int k = 0; k < 3; ++k) gT[k] = -(nm[1 + k] - 0.0) / (vsT * csT2);   /* Eq. 45 */
                 /* Eq. 18 with cV constant: grad(rho cV)/(rho cV) = grad rho / rho */
-                double phis = 0.0;
+                real phis = 0.0;
                 if (!p->flow_off) {
                     for (int k = 0; k < 3; ++k) phis += (chi * grho[k] / rho - u[k]) * gT[k];
                     phis -= T / (rho * p->cV) * dpdT(p, rho) * divu;
@@ -554,16 +573,16 @@ static int step_once(orc_state* s) {
                     u[0] = u[1] = u[2] = 0.0;
                     divu = 0.0;
                 }
-                double phis_old = s->first ? phis : s->phis_prev[i];
+                real phis_old = s->first ? phis : s->phis_prev[i];
                 /* Eq. 42 equilibrium moments and Eq. 43 rates */
-                double neq[Q7] = {T, 0.0, 0.0, 0.0, 3.0 * csT2 * T, 0.0, 0.0};
-                double Gm[Q7] = {1.0, 1.0 / vsT, 1.0 / vsT, 1.0 / vsT, Gam_q, Gam_pi, Gam_pi};
-                double ns[Q7];
+                real neq[Q7] = {T, 0.0, 0.0, 0.0, 3.0 * csT2 * T, 0.0, 0.0};
+                real Gm[Q7] = {1.0, 1.0 / vsT, 1.0 / vsT, 1.0 / vsT, Gam_q, Gam_pi, Gam_pi};
+                real ns[Q7];
                 for (int k = 0; k < Q7; ++k) ns[k] = nm[k] - Gm[k] * (nm[k] - neq[k]);    /* Eq. 39 */
                 for (int a = 0; a < Q7; ++a) {
-                    double acc = 0.0;
+                    real acc = 0.0;
                     for (int k = 0; k < Q7; ++k) acc += NINV6[a][k] / 6.0 * ns[k];
-                    double Qa = 1.5 * w7[a] * phis - 0.5 * w7[a] * phis_old;             /* Eq. 23 */
+                    real Qa = 1.5 * w7[a] * phis - 0.5 * w7[a] * phis_old;             /* Eq. 23 */
                     s->gp[i * Q7 + a] = acc + Qa;                                        /* Eq. 40 */
                 }
                 s->phis[i] = phis;
@@ -575,9 +594,9 @@ static int step_once(orc_state* s) {
                 }
             }
     push_stream(s);
-    double* t = s->phis_prev; s->phis_prev = s->phis; s->phis = t;
+    real* t = s->phis_prev; s->phis_prev = s->phis; s->phis = t;
     s->first = 0;
-    s->rho_ave = sum / (double)N;
+    s->rho_ave = sum / (real)N;
     return 0;
 }
 
@@ -597,17 +616,17 @@ int orc_moments(orc_state* s, double* rho_o, double* ux, double* uy, double* uz,
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x) {
                 long i = node_index(p, x, y, z);
-                double Fm[3], grho[3];
+                real Fm[3], grho[3];
                 node_forces(s, x, y, z, Fm, grho);
-                double rho = s->rho[i], j[3] = {0, 0, 0};
+                real rho = s->rho[i], j[3] = {0, 0, 0};
                 for (int a = 0; a < Q19; ++a) {
                     j[0] += EX[a] * s->f[i * Q19 + a];
                     j[1] += EY[a] * s->f[i * Q19 + a];
                     j[2] += EZ[a] * s->f[i * Q19 + a];
                 }
-                double u[3];
+                real u[3];
                 for (int k = 0; k < 3; ++k) {
-                    double F = Fm[k] + (rho - s->rho_ave) * p->g[k];
+                    real F = Fm[k] + (rho - (real)s->rho_ave) * (real)p->g[k];
                     u[k] = p->flow_off ? 0.0 : (j[k] + 0.5 * F) / rho;
                 }
                 if (rho_o) rho_o[i] = rho;
@@ -621,23 +640,26 @@ int orc_moments(orc_state* s, double* rho_o, double* ux, double* uy, double* uz,
 
 /* ---------------------------------------------------------------- state access for tests */
 
+static void to_double(double* dst, const real* src, long n) { for (long k = 0; k < n; ++k) dst[k] = (double)src[k]; }
+static void to_real(real* dst, const double* src, long n) { for (long k = 0; k < n; ++k) dst[k] = (real)src[k]; }
+
 void orc_get_pops(const orc_state* s, double* f, double* g) {
-    if (f) memcpy(f, s->f, sizeof(double) * s->N * Q19);
-    if (g) memcpy(g, s->g, sizeof(double) * s->N * Q7);
+    if (f) to_double(f, s->f, s->N * Q19);
+    if (g) to_double(g, s->g, s->N * Q7);
 }
 void orc_set_pops(orc_state* s, const double* f, const double* g) {
-    if (f) memcpy(s->f, f, sizeof(double) * s->N * Q19);
-    if (g) memcpy(s->g, g, sizeof(double) * s->N * Q7);
+    if (f) to_real(s->f, f, s->N * Q19);
+    if (g) to_real(s->g, g, s->N * Q7);
 }
 /* diagnostics of the last completed step (pre-streaming values at each node) */
 void orc_get_diag(const orc_state* s, double* divu, double* gradT, double* gradrho,
                   double* Fm, double* phis, double* psi) {
-    if (divu) memcpy(divu, s->divu, sizeof(double) * s->N);
-    if (gradT) memcpy(gradT, s->gradT, sizeof(double) * s->N * 3);
-    if (gradrho) memcpy(gradrho, s->gradrho, sizeof(double) * s->N * 3);
-    if (Fm) memcpy(Fm, s->Fm, sizeof(double) * s->N * 3);
-    if (phis) memcpy(phis, s->phis_prev, sizeof(double) * s->N);
-    if (psi) memcpy(psi, s->psi, sizeof(double) * s->N);
+    if (divu) to_double(divu, s->divu, s->N);
+    if (gradT) to_double(gradT, s->gradT, s->N * 3);
+    if (gradrho) to_double(gradrho, s->gradrho, s->N * 3);
+    if (Fm) to_double(Fm, s->Fm, s->N * 3);
+    if (phis) to_double(phis, s->phis_prev, s->N);
+    if (psi) to_double(psi, s->psi, s->N);
 }
 double orc_get_rho_ave(const orc_state* s) { return s->rho_ave; }
 void orc_set_rho_ave(orc_state* s, double v) { s->rho_ave = v; }
@@ -648,20 +670,25 @@ void orc_collide_node(const orc_params* p, const double* f, const double* F, con
     orc_state tmp;
     memset(&tmp, 0, sizeof(tmp));
     tmp.p = *p;
-    orc_matrix_M(tmp.M);
-    orc_invert(Q19, tmp.M, tmp.Minv);
-    collide_f(&tmp, f, F, Fm, psi2, fstar, u, NULL, NULL, NULL);
+    fill_matrices(&tmp);
+    real fr[Q19], Fr[3], Fmr[3], fs[Q19], ur[3];
+    to_real(fr, f, Q19); to_real(Fr, F, 3); to_real(Fmr, Fm, 3);
+    collide_f(&tmp, fr, Fr, Fmr, (real)psi2, fs, ur, NULL, NULL, NULL);
+    to_double(fstar, fs, Q19);
+    to_double(u, ur, 3);
 }
 
 /* equilibrium populations M^-1 m_eq(rho, u) */
 void orc_feq(double rho, const double* u, double* feq) {
-    double M[Q19 * Q19], Mi[Q19 * Q19], meq[Q19];
+    double M[Q19 * Q19], Mi[Q19 * Q19];
+    real meq[Q19], ur[3];
     orc_matrix_M(M);
     orc_invert(Q19, M, Mi);
-    m_equilibrium(rho, u, meq);
+    to_real(ur, u, 3);
+    m_equilibrium((real)rho, ur, meq);
     for (int a = 0; a < Q19; ++a) {
         double acc = 0.0;
-        for (int k = 0; k < Q19; ++k) acc += Mi[a * Q19 + k] * meq[k];
+        for (int k = 0; k < Q19; ++k) acc += Mi[a * Q19 + k] * (double)meq[k];
         feq[a] = acc;
     }
 }
@@ -669,13 +696,15 @@ void orc_feq(double rho, const double* u, double* feq) {
 /* forcing populations G = M^-1 S (Eq. 9) */
 void orc_force_pops(const orc_params* p, const double* F, const double* u, const double* Fm,
                     double psi2, double* G) {
-    double M[Q19 * Q19], Mi[Q19 * Q19], S[Q19];
+    double M[Q19 * Q19], Mi[Q19 * Q19];
+    real S[Q19], Fr[3], ur[3], Fmr[3];
     orc_matrix_M(M);
     orc_invert(Q19, M, Mi);
-    force_moments(p, F, u, Fm, psi2, S);
+    to_real(Fr, F, 3); to_real(ur, u, 3); to_real(Fmr, Fm, 3);
+    force_moments(p, Fr, ur, Fmr, (real)psi2, S);
     for (int a = 0; a < Q19; ++a) {
         double acc = 0.0;
-        for (int k = 0; k < Q19; ++k) acc += Mi[a * Q19 + k] * S[k];
+        for (int k = 0; k < Q19; ++k) acc += Mi[a * Q19 + k] * (double)S[k];
         G[a] = acc;
     }
 }

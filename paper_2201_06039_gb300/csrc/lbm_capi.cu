@@ -71,7 +71,9 @@ struct GraphEntry {
 struct lbm_ctx {
     lbm_params p;
     DevParams dp;
-    cudaStream_t stream;
+    cudaStream_t stream;        // caller's stream: every launch and graph replay goes here
+    cudaStream_t capture;       // private non-blocking stream used only to record graphs
+    cudaStream_t launch;        // stream enqueue_step launches on (== stream, or capture while recording)
     char* base;
     bool owns;
     Layout L;
@@ -194,12 +196,12 @@ int enqueue_step(lbm_ctx* c, double* kernel_ms = nullptr, int* launches = nullpt
     StateBufs B = c->bufs();
     cudaError_t e;
     if (c->variant == LBM_KERNEL_FUSED) {
-        if (ev) cudaEventRecord(ev[0], c->stream);
+        if (ev) cudaEventRecord(ev[0], c->launch);
         e = launch_fused(c->dp, c->p.precision, B, c->sums(c->slot), c->sums(c->slot ^ 1), c->first ? 1 : 0,
-                         c->stream);
+                         c->launch);
         if (e != cudaSuccess) return fail(LBM_ECUDA, "fused kernel launch: %s", cudaGetErrorString(e));
         if (ev) {
-            cudaEventRecord(ev[1], c->stream);
+            cudaEventRecord(ev[1], c->launch);
             cudaEventSynchronize(ev[1]);
             float ms = 0.f;
             cudaEventElapsedTime(&ms, ev[0], ev[1]);
@@ -207,14 +209,14 @@ int enqueue_step(lbm_ctx* c, double* kernel_ms = nullptr, int* launches = nullpt
             launches[0] += 1;
         }
     } else {
-        if (ev) cudaEventRecord(ev[0], c->stream);
-        e = launch_psi(c->dp, c->p.precision, B, c->sums(c->slot ^ 1), c->stream);
+        if (ev) cudaEventRecord(ev[0], c->launch);
+        e = launch_psi(c->dp, c->p.precision, B, c->sums(c->slot ^ 1), c->launch);
         if (e != cudaSuccess) return fail(LBM_ECUDA, "psi kernel launch: %s", cudaGetErrorString(e));
-        if (ev) cudaEventRecord(ev[1], c->stream);
-        e = launch_collide(c->dp, c->p.precision, B, c->sums(c->slot), c->first ? 1 : 0, c->stream);
+        if (ev) cudaEventRecord(ev[1], c->launch);
+        e = launch_collide(c->dp, c->p.precision, B, c->sums(c->slot), c->first ? 1 : 0, c->launch);
         if (e != cudaSuccess) return fail(LBM_ECUDA, "collide kernel launch: %s", cudaGetErrorString(e));
         if (ev) {
-            cudaEventRecord(ev[2], c->stream);
+            cudaEventRecord(ev[2], c->launch);
             cudaEventSynchronize(ev[2]);
             float a = 0.f, b = 0.f;
             cudaEventElapsedTime(&a, ev[0], ev[1]);
@@ -244,10 +246,15 @@ int run_graph(lbm_ctx* c, int n) {
         bool ff = c->fresh_f, fg = c->fresh_g, fi = c->first;
         long long st = c->steps;
         cudaGraph_t graph;
-        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        // record on a private stream (the legacy default stream cannot be captured); the
+        // graph is then replayed on the caller's stream
+        if (!c->capture) CK(cudaStreamCreateWithFlags(&c->capture, cudaStreamNonBlocking));
+        CK(cudaStreamBeginCapture(c->capture, cudaStreamCaptureModeThreadLocal));
+        c->launch = c->capture;
         int rc = LBM_OK;
         for (int k = 0; k < n && rc == LBM_OK; ++k) rc = enqueue_step(c);
-        cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+        cudaError_t e = cudaStreamEndCapture(c->capture, &graph);
+        c->launch = c->stream;
         // the capture only recorded work: put the state back, the replay advances it
         c->fcur = f0; c->gcur = g0; c->slot = s0; c->fresh_f = ff; c->fresh_g = fg; c->first = fi; c->steps = st;
         if (rc != LBM_OK) { if (e == cudaSuccess) cudaGraphDestroy(graph); return rc; }
@@ -333,6 +340,8 @@ int lbm_create(const lbm_params* p, lbm_ctx** out) {
     c->dp = make_dev(p);
     c->L = layout_of(p, c->dp);
     c->stream = (cudaStream_t)p->cuda_stream;
+    c->launch = c->stream;
+    c->capture = nullptr;
     if (p->workspace) {
         if (p->workspace_bytes < c->L.total || ((uintptr_t)p->workspace & 255)) {
             free(c);
@@ -479,6 +488,7 @@ int lbm_kernel_in_use(const lbm_ctx* c) { return c ? c->variant : LBM_EINVAL; }
 void lbm_destroy(lbm_ctx* c) {
     if (!c) return;
     drop_graphs(c);
+    if (c->capture) cudaStreamDestroy(c->capture);
     if (c->owns && c->base) cudaFree(c->base);
     free(c);
 }

@@ -157,8 +157,6 @@ __device__ __forceinline__ float pull_f_one(const DevParams& P, const S* __restr
     return Codec<S>::load(src + (size_t)A * P.N + s, P.shift_f[A]);
 }
 
-template <int A> struct Unroll19;
-
 // Pull of all 19 f (pull != 0) or direct read of the node's own values (fresh state).
 template <typename S>
 __device__ __forceinline__ void load_f(const DevParams& P, const S* __restrict__ src, int pull, int i,
@@ -215,6 +213,33 @@ __device__ __forceinline__ float psi_squared(const DevParams& P, float rho, floa
     float brho = P.b * rho;
     float p = rho * P.R * T / (1.f - brho) - P.a * theta * rho * rho / (1.f + 2.f * brho - brho * brho);
     return 2.f * (rho * (1.f / 3.f) - p);
+}
+
+// f = M^-1 m from the pair sums / differences of the raw moments: a* = f_+ + f_-, b* = f_+ - f_-
+// of the three axis pairs, and the 12 edge populations from m7..m18.  f_0 = rho - sum f_1..18.
+__device__ __forceinline__ void back_transform(float rho, float ax, float bx, float ay, float by, float az,
+                                               float bz, float m7, float m8, float m9, float m10, float m11,
+                                               float m12, float m13, float m14, float m15, float m16,
+                                               float m17, float m18, float f[19]) {
+    f[1] = 0.5f * (ax + bx); f[2] = 0.5f * (ax - bx);
+    f[3] = 0.5f * (ay + by); f[4] = 0.5f * (ay - by);
+    f[5] = 0.5f * (az + bz); f[6] = 0.5f * (az - bz);
+    f[7] = 0.25f * (m16 + m7 + m10 + m11);
+    f[8] = 0.25f * (m16 + m7 - m10 - m11);
+    f[9] = 0.25f * (m16 - m7 - m10 + m11);
+    f[10] = 0.25f * (m16 - m7 + m10 - m11);
+    f[11] = 0.25f * (m17 + m8 + m12 + m13);
+    f[12] = 0.25f * (m17 + m8 - m12 - m13);
+    f[13] = 0.25f * (m17 - m8 - m12 + m13);
+    f[14] = 0.25f * (m17 - m8 + m12 - m13);
+    f[15] = 0.25f * (m18 + m9 + m14 + m15);
+    f[16] = 0.25f * (m18 + m9 - m14 - m15);
+    f[17] = 0.25f * (m18 - m9 - m14 + m15);
+    f[18] = 0.25f * (m18 - m9 + m14 - m15);
+    float s = ((f[1] + f[2]) + (f[3] + f[4]) + (f[5] + f[6])) +
+              (((f[7] + f[8]) + (f[9] + f[10])) + ((f[11] + f[12]) + (f[13] + f[14])) +
+               ((f[15] + f[16]) + (f[17] + f[18])));
+    f[0] = rho - s;
 }
 
 // ---------------------------------------------------------------- D3Q19 MRT collision
@@ -297,29 +322,16 @@ __device__ __forceinline__ NodeOut collide_f(const DevParams& P, float f[19], fl
     m17 += -Lp * (m17 - e17) + hp * S17;
     m18 += -Lp * (m18 - e18) + hp * S18;
 
-    // back-transform f* = M^-1 m* (closed form of the raw-moment inverse)
-    float X = (m4 + m5) * (1.f / 3.f);
+    // back-transform f* = M^-1 m* (closed form of the raw-moment inverse).  Divisions are
+    // correctly rounded (a rounded 1/3 factor biases the sums), and the rest population is formed
+    // last as rho - sum of the others, so that FP32 rounding cannot drift the mass (m_0* = rho).
+    float X = (m4 + m5) / 3.f;
     float Y = 0.5f * (m4 - X + m6);
     float Z = 0.5f * (m4 - X - m6);
     float ax = X - m16 - m17, bx = r1 - m11 - m13;
     float ay = Y - m16 - m18, by = r2 - m10 - m15;
     float az = Z - m17 - m18, bz = r3 - m12 - m14;
-    f[0] = rho - m4 + m16 + m17 + m18;
-    f[1] = 0.5f * (ax + bx); f[2] = 0.5f * (ax - bx);
-    f[3] = 0.5f * (ay + by); f[4] = 0.5f * (ay - by);
-    f[5] = 0.5f * (az + bz); f[6] = 0.5f * (az - bz);
-    f[7] = 0.25f * (m16 + m7 + m10 + m11);
-    f[8] = 0.25f * (m16 + m7 - m10 - m11);
-    f[9] = 0.25f * (m16 - m7 - m10 + m11);
-    f[10] = 0.25f * (m16 - m7 + m10 - m11);
-    f[11] = 0.25f * (m17 + m8 + m12 + m13);
-    f[12] = 0.25f * (m17 + m8 - m12 - m13);
-    f[13] = 0.25f * (m17 - m8 - m12 + m13);
-    f[14] = 0.25f * (m17 - m8 + m12 - m13);
-    f[15] = 0.25f * (m18 + m9 + m14 + m15);
-    f[16] = 0.25f * (m18 + m9 - m14 - m15);
-    f[17] = 0.25f * (m18 - m9 - m14 + m15);
-    f[18] = 0.25f * (m18 - m9 + m14 - m15);
+    back_transform(rho, ax, bx, ay, by, az, bz, m7, m8, m9, m10, m11, m12, m13, m14, m15, m16, m17, m18, f);
     return o;
 }
 
@@ -335,28 +347,13 @@ __device__ __forceinline__ void feq(float rho, float ux, float uy, float uz, flo
     float m14 = rho * uz * (cs2 + uy2), m15 = rho * uy * (cs2 + uz2);
     float m16 = phi + rho * cs2 * (ux2 + uy2), m17 = phi + rho * cs2 * (ux2 + uz2);
     float m18 = phi + rho * cs2 * (uy2 + uz2);
-    float X = (m4 + m5) * (1.f / 3.f);
+    float X = (m4 + m5) / 3.f;
     float Y = 0.5f * (m4 - X + m6);
     float Z = 0.5f * (m4 - X - m6);
     float ax = X - m16 - m17, bx = rho * ux - m11 - m13;
     float ay = Y - m16 - m18, by = rho * uy - m10 - m15;
     float az = Z - m17 - m18, bz = rho * uz - m12 - m14;
-    f[0] = rho - m4 + m16 + m17 + m18;
-    f[1] = 0.5f * (ax + bx); f[2] = 0.5f * (ax - bx);
-    f[3] = 0.5f * (ay + by); f[4] = 0.5f * (ay - by);
-    f[5] = 0.5f * (az + bz); f[6] = 0.5f * (az - bz);
-    f[7] = 0.25f * (m16 + m7 + m10 + m11);
-    f[8] = 0.25f * (m16 + m7 - m10 - m11);
-    f[9] = 0.25f * (m16 - m7 - m10 + m11);
-    f[10] = 0.25f * (m16 - m7 + m10 - m11);
-    f[11] = 0.25f * (m17 + m8 + m12 + m13);
-    f[12] = 0.25f * (m17 + m8 - m12 - m13);
-    f[13] = 0.25f * (m17 - m8 - m12 + m13);
-    f[14] = 0.25f * (m17 - m8 + m12 - m13);
-    f[15] = 0.25f * (m18 + m9 + m14 + m15);
-    f[16] = 0.25f * (m18 + m9 - m14 - m15);
-    f[17] = 0.25f * (m18 - m9 - m14 + m15);
-    f[18] = 0.25f * (m18 - m9 + m14 - m15);
+    back_transform(rho, ax, bx, ay, by, az, bz, m7, m8, m9, m10, m11, m12, m13, m14, m15, m16, m17, m18, f);
 }
 
 // ---------------------------------------------------------------- D3Q7 MRT temperature LB
@@ -390,15 +387,16 @@ __device__ __forceinline__ float collide_g(const DevParams& P, float g[7], float
     n4 = n4 - P.Gq * (n4 - P.d * T);                 // 3 cs_T^2 T = d T
     n5 *= 1.f - P.Gpi;
     n6 *= 1.f - P.Gpi;
-    const float s6 = 1.f / 6.f;
+    // g* = N^-1 n* (Eq. 41) with correctly rounded divisions; g*_0 = T - sum g*_1..6 keeps
+    // sum g* = T free of rounding drift (n_0* = T); then g+ = g* + Q (Eq. 40).
+    float h1 = (3.f * n1 + n4 + n5 + n6) / 6.f, h2 = (-3.f * n1 + n4 + n5 + n6) / 6.f;
+    float h3 = (3.f * n2 + n4 - 2.f * n5 + n6) / 6.f, h4 = (-3.f * n2 + n4 - 2.f * n5 + n6) / 6.f;
+    float h5 = (3.f * n3 + n4 + n5 - 2.f * n6) / 6.f, h6 = (-3.f * n3 + n4 + n5 - 2.f * n6) / 6.f;
+    float h0 = T - ((h1 + h2) + (h3 + h4) + (h5 + h6));
     float q0 = P.w0 * qs, q1 = P.w1 * qs;
-    g[0] = T - n4 + q0;
-    g[1] = s6 * (3.f * n1 + n4 + n5 + n6) + q1;
-    g[2] = s6 * (-3.f * n1 + n4 + n5 + n6) + q1;
-    g[3] = s6 * (3.f * n2 + n4 - 2.f * n5 + n6) + q1;
-    g[4] = s6 * (-3.f * n2 + n4 - 2.f * n5 + n6) + q1;
-    g[5] = s6 * (3.f * n3 + n4 + n5 - 2.f * n6) + q1;
-    g[6] = s6 * (-3.f * n3 + n4 + n5 - 2.f * n6) + q1;
+    g[0] = h0 + q0;
+    g[1] = h1 + q1; g[2] = h2 + q1; g[3] = h3 + q1;
+    g[4] = h4 + q1; g[5] = h5 + q1; g[6] = h6 + q1;
     return phis;
 }
 
