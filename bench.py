@@ -38,7 +38,7 @@ import workloads as W  # noqa: E402
 
 BYTES_PER_NODE = {"fp32": 216, "bf16": 112, "fp16": 112}   # algorithmic bytes of one node update
 PREC_CODE = {"fp32": 0, "bf16": 1, "fp16": 2}
-KERNEL_CODE = {"auto": 0, "two_pass": 1, "fused": 2}
+KERNEL_CODE = {"auto": 0, "two_pass": 1, "fused": 2, "fused_generic": 2}
 
 
 def workload(name, nx=None, ny=None, nz=None):
@@ -253,12 +253,12 @@ def run_mine(args):
     rho, T = init_fields(case)
     stream = torch.cuda.current_stream()
     p = lbm.params_from_setup(s, kernel=KERNEL_CODE[args.kernel], precision=PREC_CODE[args.precision],
-                              use_graph=1, check_nonfinite=0)
+                              use_graph=1, check_nonfinite=0, use_tma=0 if args.kernel == "fused_generic" else 1)
     if args.precision != "fp32":
         p.rho_ref = float(rho.mean())
         p.T_ref = 0.86 * lbm.lbm_eos_critical(p)[0]
     lat = lbm.Lattice(p, stream=stream)
-    kernel_name = "fused" if lat.kernel == lbm.LBM_KERNEL_FUSED else "collide"
+    kernel_name = {lbm.LBM_KERNEL_FUSED: "fused", lbm.LBM_KERNEL_FUSED_TMA: "fused_tma"}.get(lat.kernel, "collide")
 
     # ---- device-resident timing
     lat.init(torch.from_numpy(rho).cuda(), torch.from_numpy(T).cuda())
@@ -291,7 +291,7 @@ def run_mine(args):
 
     # ---- per-kernel durations (CUDA events on the lattice's stream) for the roofline
     kms, kn = lbm.lbm_step_profiled(lat.ctx, max(3, min(50, args.steps)))
-    k_idx = 0 if kernel_name == "fused" else 1
+    k_idx = 1 if kernel_name == "collide" else 0
     k_avg_ms = kms[k_idx] / max(1, kn[k_idx])
     peak, peak_kind = measured_peaks()
     bpn = BYTES_PER_NODE[args.precision]
@@ -319,7 +319,7 @@ def run_mine(args):
         e2e_s = float(t.item())
     e2e_mlups = N * args.steps * world / e2e_s / 1e6
 
-    launches_per_step = 1 if kernel_name == "fused" else 2
+    launches_per_step = 2 if kernel_name == "collide" else 1
     line = {
         "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,

@@ -61,7 +61,9 @@ typedef enum { LBM_FP32 = 0, LBM_BF16_SHIFTED = 1, LBM_FP16_SHIFTED = 2 } lbm_pr
 typedef enum {
     LBM_KERNEL_AUTO = 0,      /* fastest available variant */
     LBM_KERNEL_TWO_PASS = 1,  /* psi/EOS kernel, then the stream-collide kernel */
-    LBM_KERNEL_FUSED = 2      /* one z-marching kernel per step (halo recomputation) */
+    LBM_KERNEL_FUSED = 2,     /* one z-marching kernel per step (halo recomputation) */
+    LBM_KERNEL_FUSED_TMA = 3  /* reported by lbm_kernel_in_use: FUSED with TMA-fed pipeline (FP32,
+                                 x and y faces periodic or thermal-only) */
 } lbm_kernel_variant;
 
 typedef struct {
@@ -85,6 +87,7 @@ typedef struct {
     double rho_ref, T_ref;        /* shifts of 16-bit storage: f - w rho_ref, g - w T_ref */
     int kernel;                   /* lbm_kernel_variant */
     int use_graph;                /* 1: lbm_step replays a captured CUDA graph of n steps */
+    int use_tma;                  /* 1: FUSED uses the TMA-fed pipeline where the lattice allows it */
     int check_nonfinite;          /* 1: lbm_step synchronises and reports LBM_ENONFINITE */
     void* cuda_stream;            /* borrowed cudaStream_t, NULL = legacy default stream */
     void* workspace;              /* optional caller-owned device memory (see above) */
@@ -133,7 +136,9 @@ int lbm_get_totals(lbm_ctx* ctx, double* mass, double* T_sum, double* rho_ave);
 /* Number of steps taken since lbm_init_fields. */
 long long lbm_steps_done(const lbm_ctx* ctx);
 
-/* Kernel variant the context runs (LBM_KERNEL_TWO_PASS or LBM_KERNEL_FUSED; AUTO resolved). */
+/* Kernel variant the context runs (LBM_KERNEL_TWO_PASS, LBM_KERNEL_FUSED or
+ * LBM_KERNEL_FUSED_TMA; AUTO resolved).  The first step after lbm_init_fields, and steps with a
+ * frozen field, always run the generic fused kernel. */
 int lbm_kernel_in_use(const lbm_ctx* ctx);
 
 /* Enqueue n steps outside any graph and accumulate, per kernel kind, the device time

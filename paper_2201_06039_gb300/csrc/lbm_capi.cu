@@ -37,17 +37,17 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 size_t pop_bytes(int precision) { return precision == LBM_FP32 ? 4 : 2; }
 
 struct Layout {
-    size_t f[2], g[2], psirho, phis, sums, partial, counter, flag, total;
+    size_t pops[2], psirho, phis, sums, partial, counter, flag, total;
 };
 
+// Device memory of a context: two population buffers (26 slots of Ns elements: the padded,
+// ghost-carrying storage of lbm_device.cuh), dense (psi, rho) and phi_s fields, FP64 sums.
 Layout layout_of(const lbm_params* p, const DevParams& dp) {
     Layout L;
     size_t N = (size_t)dp.N, pb = pop_bytes(p->precision), off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
-    L.f[0] = take(19 * N * pb);
-    L.f[1] = take(19 * N * pb);
-    L.g[0] = take(7 * N * pb);
-    L.g[1] = take(7 * N * pb);
+    L.pops[0] = take((size_t)kSlots * dp.Ns * pb);
+    L.pops[1] = take((size_t)kSlots * dp.Ns * pb);
     L.psirho = take(8 * N);
     L.phis = take(4 * N);
     L.sums = take(8 * sizeof(double));          // slots: [0..1] [2..3] rho_ave ping-pong, [4..5] totals
@@ -61,7 +61,7 @@ Layout layout_of(const lbm_params* p, const DevParams& dp) {
 const int kGraphCache = 8;
 
 struct GraphEntry {
-    int n, fcur, gcur, slot;
+    int n, cur, slot;
     cudaGraphExec_t exec;
     unsigned long long last_use;
 };
@@ -77,23 +77,22 @@ struct lbm_ctx {
     char* base;
     bool owns;
     Layout L;
-    int fcur, gcur, slot;
+    int cur, slot;              // population buffer holding the state; rho_ave slot of the next step
     bool fresh_f, fresh_g, first, initialised;
     long long steps;
     int variant;   // LBM_KERNEL_TWO_PASS or LBM_KERNEL_FUSED
+    TmaMaps maps;
     GraphEntry graphs[kGraphCache];
     int n_graphs;
     unsigned long long use_clock;
 
-    void* fbuf(int k) { return base + L.f[k]; }
-    void* gbuf(int k) { return base + L.g[k]; }
+    void* pbuf(int k) { return base + L.pops[k]; }
     double* sums(int k) { return (double*)(base + L.sums) + 2 * k; }
     StateBufs bufs() {
         StateBufs B;
-        B.fsrc = fbuf(fcur);
-        B.gsrc = gbuf(gcur);
-        B.fdst = fbuf(fcur ^ 1);
-        B.gdst = gbuf(gcur ^ 1);
+        B.src = pbuf(cur);
+        B.dst = pbuf(cur ^ 1);
+        B.src_index = cur;
         B.pull_f = fresh_f ? 0 : 1;
         B.pull_g = fresh_g ? 0 : 1;
         B.psirho = (float2*)(base + L.psirho);
@@ -112,8 +111,9 @@ double critical_T(const lbm_params* p) { return 0.0778 * p->a / (0.45724 * p->b 
 int validate(const lbm_params* p) {
     if (!p) return fail(LBM_EINVAL, "params is NULL");
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(LBM_EINVAL, "lattice size must be >= 1");
-    long long N = (long long)p->nx * p->ny * p->nz;
-    if (N * 19 >= (1LL << 31)) return fail(LBM_EINVAL, "lattice too large (19 N must be < 2^31)");
+    long long Ws = ((long long)p->nx + kGX + 2 + 7) / 8 * 8, Hs = (long long)p->ny + kGY + 2;
+    if ((long long)kSlots * Ws * Hs * p->nz >= (1LL << 31))
+        return fail(LBM_EINVAL, "lattice too large (26 x padded nodes must be < 2^31)");
     int n[3] = {p->nx, p->ny, p->nz};
     for (int f = 0; f < 6; ++f) {
         if (p->bc[f] < 0 || p->bc[f] > 3) return fail(LBM_EINVAL, "bc[%d] = %d is not an lbm_bc", f, p->bc[f]);
@@ -145,6 +145,10 @@ DevParams make_dev(const lbm_params* p) {
     d.nx = p->nx; d.ny = p->ny; d.nz = p->nz;
     d.N = p->nx * p->ny * p->nz;
     d.plane = p->nx * p->ny;
+    d.Ws = (p->nx + kGX + 2 + 7) / 8 * 8;   // ghost columns -2..-1 and nx..nx+1; 32-byte aligned rows
+    d.Hs = p->ny + kGY + 2;
+    d.splane = d.Ws * d.Hs;
+    d.Ns = d.splane * p->nz;
     for (int k = 0; k < 6; ++k) { d.bc[k] = p->bc[k]; d.T_wall[k] = (float)p->T_wall[k]; }
     d.hot_dT = (float)p->hot_dT;
     d.hot_inv2s2 = p->hot_dT != 0.0 ? (float)(1.0 / (2.0 * p->hot_sigma * p->hot_sigma)) : 0.f;
@@ -152,6 +156,8 @@ DevParams make_dev(const lbm_params* p) {
     d.hot_cy = 0.5f * (float)p->ny;
     d.a = (float)p->a; d.b = (float)p->b; d.R = (float)p->R;
     d.Tc = (float)critical_T(p);
+    d.inv_Tc = (float)(1.0 / critical_T(p));
+    d.inv_N = 1.0 / (double)d.N;
     double w = p->acentric;
     d.kappa = (float)(0.37464 + 1.54226 * w - 0.26992 * w * w);
     d.sigma6 = (float)(6.0 * p->sigma / (p->tau_e - 0.5));
@@ -161,6 +167,7 @@ DevParams make_dev(const lbm_params* p) {
     d.half_Le = (float)(1.0 - 0.5 / p->tau_e);
     d.cV = (float)p->cV; d.d = (float)p->d; d.csT2 = (float)(p->d / 3.0);
     d.w0 = (float)(1.0 - p->d); d.w1 = (float)(p->d / 6.0);
+    d.inv_cV = (float)(1.0 / p->cV); d.inv_csT2 = (float)(3.0 / p->d); d.R_over_cV = (float)(p->R / p->cV);
     d.Gq = (float)(1.0 / p->varsigma_q); d.Gpi = (float)(1.0 / p->varsigma_pi);
     d.lambda_mode = p->lambda_mode; d.chi_or_lambda = (float)p->chi_or_lambda;
     d.gx = (float)p->g[0]; d.gy = (float)p->g[1]; d.gz = (float)p->g[2];
@@ -175,6 +182,15 @@ DevParams make_dev(const lbm_params* p) {
     }
     return d;
 }
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// Tensor maps of both population buffers for the TMA kernel: dims (Ws, Hs, nz, 26) of FP32,
+// boxes (TX + 8, TY + 4, 1, 14) and (TX + 8, TY + 4, 1, 6) of the planned tile shape;
+// out-of-range cells read as zero (never used).
+bool make_tma_maps(lbm_ctx* c);
 
 bool is_device_ptr(const void* ptr) {
     if (!ptr) return false;
@@ -198,7 +214,7 @@ int enqueue_step(lbm_ctx* c, double* kernel_ms = nullptr, int* launches = nullpt
     if (c->variant == LBM_KERNEL_FUSED) {
         if (ev) cudaEventRecord(ev[0], c->launch);
         e = launch_fused(c->dp, c->p.precision, B, c->sums(c->slot), c->sums(c->slot ^ 1), c->first ? 1 : 0,
-                         c->launch);
+                         c->launch, c->maps.ok ? &c->maps : nullptr);
         if (e != cudaSuccess) return fail(LBM_ECUDA, "fused kernel launch: %s", cudaGetErrorString(e));
         if (ev) {
             cudaEventRecord(ev[1], c->launch);
@@ -227,8 +243,11 @@ int enqueue_step(lbm_ctx* c, double* kernel_ms = nullptr, int* launches = nullpt
             launches[1] += 1;
         }
     }
-    if (!c->p.flow_off) { c->fcur ^= 1; c->fresh_f = false; }
-    if (!c->p.thermal_off) { c->gcur ^= 1; c->fresh_g = false; }
+    // both fields are written every step (frozen ones copied through unchanged, so they stay
+    // in their un-streamed "fresh" form)
+    c->cur ^= 1;
+    if (!c->p.flow_off) c->fresh_f = false;
+    if (!c->p.thermal_off) c->fresh_g = false;
     c->slot ^= 1;
     c->first = false;
     c->steps += 1;
@@ -239,10 +258,10 @@ int run_graph(lbm_ctx* c, int n) {
     GraphEntry* hit = nullptr;
     for (int k = 0; k < c->n_graphs; ++k) {
         GraphEntry& g = c->graphs[k];
-        if (g.n == n && g.fcur == c->fcur && g.gcur == c->gcur && g.slot == c->slot) hit = &g;
+        if (g.n == n && g.cur == c->cur && g.slot == c->slot) hit = &g;
     }
     if (!hit) {
-        int f0 = c->fcur, g0 = c->gcur, s0 = c->slot;
+        int c0 = c->cur, s0 = c->slot;
         bool ff = c->fresh_f, fg = c->fresh_g, fi = c->first;
         long long st = c->steps;
         cudaGraph_t graph;
@@ -256,7 +275,7 @@ int run_graph(lbm_ctx* c, int n) {
         cudaError_t e = cudaStreamEndCapture(c->capture, &graph);
         c->launch = c->stream;
         // the capture only recorded work: put the state back, the replay advances it
-        c->fcur = f0; c->gcur = g0; c->slot = s0; c->fresh_f = ff; c->fresh_g = fg; c->first = fi; c->steps = st;
+        c->cur = c0; c->slot = s0; c->fresh_f = ff; c->fresh_g = fg; c->first = fi; c->steps = st;
         if (rc != LBM_OK) { if (e == cudaSuccess) cudaGraphDestroy(graph); return rc; }
         if (e != cudaSuccess) return fail(LBM_ECUDA, "graph capture: %s", cudaGetErrorString(e));
         cudaGraphExec_t exec;
@@ -271,15 +290,14 @@ int run_graph(lbm_ctx* c, int n) {
             c->graphs[lru] = c->graphs[--c->n_graphs];
         }
         GraphEntry& g = c->graphs[c->n_graphs++];
-        g.n = n; g.fcur = c->fcur; g.gcur = c->gcur; g.slot = c->slot; g.exec = exec;
+        g.n = n; g.cur = c->cur; g.slot = c->slot; g.exec = exec;
         hit = &g;
     }
     hit->last_use = ++c->use_clock;
     CK(cudaGraphLaunch(hit->exec, c->stream));
     // advance the host-side state exactly as n enqueue_step calls would
     for (int k = 0; k < n; ++k) {
-        if (!c->p.flow_off) c->fcur ^= 1;
-        if (!c->p.thermal_off) c->gcur ^= 1;
+        c->cur ^= 1;
         c->slot ^= 1;
     }
     c->steps += n;
@@ -292,9 +310,53 @@ int check_flag(lbm_ctx* c) {
     CK(cudaStreamSynchronize(c->stream));
     if (h) {
         CK(cudaMemsetAsync(c->base + c->L.flag, 0, sizeof(int), c->stream));
+        if (h & 2) return fail(LBM_ETIMEOUT, "a bounded pipeline wait in the fused kernel gave up (step %lld)", c->steps);
         return fail(LBM_ENONFINITE, "non-finite rho/T/psi or psi^2 <= 0 after step %lld", c->steps);
     }
     return LBM_OK;
+}
+
+bool make_tma_maps(lbm_ctx* c) {
+    c->maps.ok = false;
+    if (!tma_eligible(c->dp, c->p.precision)) return false;
+    int dev = 0, sms = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+    int shape, zchunk, items;
+    tma_plan_for(c->dp, sms, &shape, &zchunk, &items);
+    if ((size_t)optin < tma_smem_bytes(shape)) return false;
+    if (items > max_partials(c->dp)) return false;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        return false;
+    }
+    EncodeTiledFn encode = (EncodeTiledFn)fn;
+    const DevParams& d = c->dp;
+    cuuint64_t dims[4] = {(cuuint64_t)d.Ws, (cuuint64_t)d.Hs, (cuuint64_t)d.nz, (cuuint64_t)kSlots};
+    cuuint64_t strides[3] = {(cuuint64_t)d.Ws * 4, (cuuint64_t)d.splane * 4, (cuuint64_t)d.Ns * 4};
+    const cuuint32_t bw = (cuuint32_t)tma_box_w(shape), bh = (cuuint32_t)tma_box_h(shape);
+    cuuint32_t box14[4] = {bw, bh, 1, 14}, box6[4] = {bw, bh, 1, 6}, es[4] = {1, 1, 1, 1};
+    for (int k = 0; k < 2; ++k) {
+        void* g = c->pbuf(k);
+        if (encode(&c->maps.m14[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, dims, strides, box14, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+        if (encode(&c->maps.m6[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, dims, strides, box6, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    c->maps.sms = sms;
+    c->maps.shape = shape;
+    c->maps.zchunk = zchunk;
+    c->maps.items = items;
+    c->maps.ok = true;
+    return true;
 }
 
 }  // namespace
@@ -312,6 +374,7 @@ void lbm_params_default(lbm_params* p) {
     p->precision = LBM_FP32;
     p->kernel = LBM_KERNEL_AUTO;
     p->use_graph = 1;
+    p->use_tma = 1;
     p->check_nonfinite = 1;
 }
 
@@ -366,6 +429,7 @@ int lbm_create(const lbm_params* p, lbm_ctx** out) {
         free(c);
         return fail(LBM_EINVAL, "fused kernel does not support this lattice");
     }
+    if (c->variant == LBM_KERNEL_FUSED && p->use_tma != 0) make_tma_maps(c);
     cudaError_t e = cudaMemsetAsync(c->base + c->L.sums, 0, c->L.flag + sizeof(int) - c->L.sums, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
@@ -381,8 +445,8 @@ int lbm_init_fields(lbm_ctx* c, const float* rho, const float* T, const float* u
     if (!c) return fail(LBM_EINVAL, "ctx is NULL");
     if (!rho || !T) return fail(LBM_EINVAL, "rho and T are required");
     size_t N = (size_t)c->dp.N;
-    // stage host inputs in the second population buffer (19 N * >= 2 bytes >= 5 N floats)
-    float* stage = (float*)c->fbuf(1);
+    // stage host inputs in the second population buffer (26 Ns * >= 2 bytes >= 5 N floats)
+    float* stage = (float*)c->pbuf(1);
     const float *drho = rho, *dT = T, *du = u;
     if (!is_device_ptr(rho)) {
         CK(cudaMemcpyAsync(stage, rho, N * 4, cudaMemcpyHostToDevice, c->stream));
@@ -397,10 +461,9 @@ int lbm_init_fields(lbm_ctx* c, const float* rho, const float* T, const float* u
         du = stage + 2 * N;
     }
     drop_graphs(c);
-    c->fcur = 0;
-    c->gcur = 0;
+    c->cur = 0;
     c->slot = 0;
-    CK(launch_init(c->dp, c->p.precision, c->fbuf(0), c->gbuf(0), drho, dT, du, c->stream));
+    CK(launch_init(c->dp, c->p.precision, c->pbuf(0), drho, dT, du, c->stream));
     StateBufs B = c->bufs();
     CK(launch_sum_field(drho, c->dp.N, B.partial, B.counter, c->sums(0), c->stream));
     CK(cudaMemsetAsync(c->base + c->L.flag, 0, sizeof(int), c->stream));
@@ -455,7 +518,7 @@ int lbm_get_moments(lbm_ctx* c, float* rho, float* ux, float* uy, float* uz, flo
     StateBufs B = c->bufs();
     CK(launch_psi(c->dp, c->p.precision, B, nullptr, c->stream));
     // outputs staged in the population buffer the next step overwrites anyway
-    float* stage = (float*)c->fbuf(c->fcur ^ 1);
+    float* stage = (float*)c->pbuf(c->cur ^ 1);
     float* outs[5] = {rho, ux, uy, uz, T};
     float* dst[5];
     for (int k = 0; k < 5; ++k) dst[k] = outs[k] ? (is_device_ptr(outs[k]) ? outs[k] : stage + k * N) : nullptr;
@@ -483,7 +546,11 @@ int lbm_get_totals(lbm_ctx* c, double* mass, double* T_sum, double* rho_ave) {
 
 long long lbm_steps_done(const lbm_ctx* c) { return c ? c->steps : 0; }
 
-int lbm_kernel_in_use(const lbm_ctx* c) { return c ? c->variant : LBM_EINVAL; }
+int lbm_kernel_in_use(const lbm_ctx* c) {
+    if (!c) return LBM_EINVAL;
+    if (c->variant == LBM_KERNEL_FUSED && c->maps.ok) return LBM_KERNEL_FUSED_TMA;
+    return c->variant;
+}
 
 void lbm_destroy(lbm_ctx* c) {
     if (!c) return;

@@ -35,19 +35,37 @@ __host__ __device__ constexpr int ex7(int a) { return a == 1 ? 1 : a == 2 ? -1 :
 __host__ __device__ constexpr int ey7(int a) { return a == 3 ? 1 : a == 4 ? -1 : 0; }
 __host__ __device__ constexpr int ez7(int a) { return a == 5 ? 1 : a == 6 ? -1 : 0; }
 
+// Storage slots of the populations, grouped by e_z so that one tensor copy per group fetches a
+// plane: slots 0..13 have e_z = 0 (f0-4, f7-10, g0-4), 14..19 e_z = +1 (f5, f11, f14, f15, f18,
+// g5), 20..25 e_z = -1 (f6, f12, f13, f16, f17, g6).
+__host__ __device__ constexpr int fslot(int a) {
+    return a <= 4 ? a : a == 5 ? 14 : a == 6 ? 20 : a <= 10 ? a - 2 : a == 11 ? 15 : a == 12 ? 21
+         : a == 13 ? 22 : a == 14 ? 16 : a == 15 ? 17 : a == 16 ? 23 : a == 17 ? 24 : 18;
+}
+__host__ __device__ constexpr int gslot(int a) { return a <= 4 ? 9 + a : a == 5 ? 19 : 25; }
+constexpr int kSlots = 26;
+constexpr int kGX = 8, kGY = 2;   // storage offsets: 8 columns (2 ghosts; rows stay 32-byte aligned), 2 rows
+
 // Lattice constants and model parameters, converted once on the host.
 struct DevParams {
     int nx, ny, nz;
-    int N;                    // nx*ny*nz (< 2^31)
+    int N;                    // nx*ny*nz (< 2^31): dense fields (phi_s history, psi, user fields)
     int plane;                // nx*ny
+    // population storage: node (x, y, z) at (x + kGX) + Ws ((y + kGY) + Hs z), slot s at s * Ns.
+    // Columns x = -2, -1, nx, nx+1 and rows y = -2, -1, ny, ny+1 are ghost copies of the periodic
+    // images (kept current by every kernel that writes populations, only on f-periodic axes).
+    int Ws, Hs, splane, Ns;
     int bc[6];
     float T_wall[6];
     float hot_dT, hot_inv2s2, hot_cx, hot_cy;
     float a, b, R, Tc, kappa; // PR EOS (Eq. 49), kappa = 0.37464 + 1.54226 w - 0.26992 w^2
+    float inv_Tc;
+    double inv_N;             // 1 / (nx ny nz) for the domain mean of rho
     float sigma6;             // 6 sigma / (tau_e - 0.5)   (Eq. 9, S_4)
     float Le, Lv, Lq, Lpi;    // 1/tau of Eq. 6
     float inv_tau_e, half_Le; // 1/tau_e, (1 - 1/(2 tau_e)) of Eq. 48
     float cV, d, csT2, w0, w1;
+    float inv_cV, inv_csT2, R_over_cV;
     float Gq, Gpi;            // 1/varsigma_q, 1/varsigma_pi (Eq. 43)
     int lambda_mode;
     float chi_or_lambda;
@@ -93,7 +111,7 @@ struct Nbr {
     unsigned fbb, gabb;
 };
 
-__device__ __forceinline__ bool f_wraps(int bc) { return bc == BC_PERIODIC || bc == BC_THERMAL_ONLY; }
+__host__ __device__ inline bool f_wraps(int bc) { return bc == BC_PERIODIC || bc == BC_THERMAL_ONLY; }
 
 __device__ __forceinline__ void axis_nbr(int c, int n, int bc_lo, int bc_hi, int bit,
                                          int& cm, int& cp, unsigned& fbb, unsigned& gabb) {
@@ -121,8 +139,12 @@ __device__ __forceinline__ Nbr make_nbr(const DevParams& P, int x, int y, int z)
     return n;
 }
 
+// dense node index (fields) and storage index (populations)
 __device__ __forceinline__ int node_of(const DevParams& P, int x, int y, int z) {
     return x + P.nx * (y + P.ny * z);
+}
+__device__ __forceinline__ int sidx(const DevParams& P, int x, int y, int z) {
+    return (x + kGX) + P.Ws * ((y + kGY) + P.Hs * z);
 }
 
 // Source coordinate of the pull along one axis for velocity component e (x - e).
@@ -152,16 +174,35 @@ __device__ __forceinline__ float pull_f_one(const DevParams& P, const S* __restr
                                             int x, int y, int z, const Nbr& n) {
     constexpr int ex = ex19(A), ey = ey19(A), ez = ez19(A);
     if (A != 0 && crosses<A>(n.fbb))   // Eq. 50: f_a(x_b, t+1) = f*_{abar}(x_b, t)
-        return Codec<S>::load(src + (size_t)opp(A) * P.N + i, P.shift_f[opp(A)]);
-    int s = node_of(P, src_c(ex, x, n.xm, n.xp), src_c(ey, y, n.ym, n.yp), src_c(ez, z, n.zm, n.zp));
-    return Codec<S>::load(src + (size_t)A * P.N + s, P.shift_f[A]);
+        return Codec<S>::load(src + (size_t)fslot(opp(A)) * P.Ns + i, P.shift_f[opp(A)]);
+    int s = sidx(P, src_c(ex, x, n.xm, n.xp), src_c(ey, y, n.ym, n.yp), src_c(ez, z, n.zm, n.zp));
+    return Codec<S>::load(src + (size_t)fslot(A) * P.Ns + s, P.shift_f[A]);
+}
+
+// Node at least one node away from every face: every pull source is i - (ex + nx ey + nx ny ez).
+__device__ __forceinline__ bool deep_interior(const DevParams& P, int x, int y, int z) {
+    return (unsigned)(x - 1) < (unsigned)(P.nx - 2) && (unsigned)(y - 1) < (unsigned)(P.ny - 2) &&
+           (unsigned)(z - 1) < (unsigned)(P.nz - 2);
+}
+
+template <typename S, int A>
+__device__ __forceinline__ float pull_f_fast(const DevParams& P, const S* __restrict__ src, int i) {
+    constexpr int ex = ex19(A), ey = ey19(A), ez = ez19(A);
+    return Codec<S>::load(src + (size_t)fslot(A) * P.Ns + (i - ex - ey * P.Ws - ez * P.splane), P.shift_f[A]);
 }
 
 // Pull of all 19 f (pull != 0) or direct read of the node's own values (fresh state).
 template <typename S>
 __device__ __forceinline__ void load_f(const DevParams& P, const S* __restrict__ src, int pull, int i,
                                        int x, int y, int z, const Nbr& n, float f[19]) {
-    if (pull) {
+    if (pull && deep_interior(P, x, y, z)) {
+#define GB300_PULL(A) f[A] = pull_f_fast<S, A>(P, src, i);
+        GB300_PULL(0) GB300_PULL(1) GB300_PULL(2) GB300_PULL(3) GB300_PULL(4) GB300_PULL(5)
+        GB300_PULL(6) GB300_PULL(7) GB300_PULL(8) GB300_PULL(9) GB300_PULL(10) GB300_PULL(11)
+        GB300_PULL(12) GB300_PULL(13) GB300_PULL(14) GB300_PULL(15) GB300_PULL(16) GB300_PULL(17)
+        GB300_PULL(18)
+#undef GB300_PULL
+    } else if (pull) {
 #define GB300_PULL(A) f[A] = pull_f_one<S, A>(P, src, i, x, y, z, n);
         GB300_PULL(0) GB300_PULL(1) GB300_PULL(2) GB300_PULL(3) GB300_PULL(4) GB300_PULL(5)
         GB300_PULL(6) GB300_PULL(7) GB300_PULL(8) GB300_PULL(9) GB300_PULL(10) GB300_PULL(11)
@@ -170,7 +211,7 @@ __device__ __forceinline__ void load_f(const DevParams& P, const S* __restrict__
 #undef GB300_PULL
     } else {
 #pragma unroll
-        for (int a = 0; a < 19; ++a) f[a] = Codec<S>::load(src + (size_t)a * P.N + i, P.shift_f[a]);
+        for (int a = 0; a < 19; ++a) f[a] = Codec<S>::load(src + (size_t)fslot(a) * P.Ns + i, P.shift_f[a]);
     }
 }
 
@@ -181,17 +222,25 @@ __device__ __forceinline__ float pull_g_one(const DevParams& P, const S* __restr
     constexpr int face = ex > 0 ? 0 : ex < 0 ? 1 : ey > 0 ? 2 : ey < 0 ? 3 : ez > 0 ? 4 : 5;
     if (A != 0 && (n.gabb & (1u << face))) {
         // Eq. 51: g_a(x_b, t+1) = -g+_{abar}(x_b, t) + 2 w_abar T_w   (w_abar = w_a on D3Q7)
-        float gp = Codec<S>::load(src + (size_t)opp(A) * P.N + i, P.shift_g[opp(A)]);
+        float gp = Codec<S>::load(src + (size_t)gslot(opp(A)) * P.Ns + i, P.shift_g[opp(A)]);
         return -gp + 2.f * P.w1 * wall_T(P, face, x, y);
     }
-    int s = node_of(P, src_c(ex, x, n.xm, n.xp), src_c(ey, y, n.ym, n.yp), src_c(ez, z, n.zm, n.zp));
-    return Codec<S>::load(src + (size_t)A * P.N + s, P.shift_g[A]);
+    int s = sidx(P, src_c(ex, x, n.xm, n.xp), src_c(ey, y, n.ym, n.yp), src_c(ez, z, n.zm, n.zp));
+    return Codec<S>::load(src + (size_t)gslot(A) * P.Ns + s, P.shift_g[A]);
 }
 
 template <typename S>
 __device__ __forceinline__ void load_g(const DevParams& P, const S* __restrict__ src, int pull, int i,
                                        int x, int y, int z, const Nbr& n, float g[7]) {
-    if (pull) {
+    if (pull && deep_interior(P, x, y, z)) {
+        g[0] = Codec<S>::load(src + (size_t)gslot(0) * P.Ns + i, P.shift_g[0]);
+        g[1] = Codec<S>::load(src + (size_t)gslot(1) * P.Ns + (i - 1), P.shift_g[1]);
+        g[2] = Codec<S>::load(src + (size_t)gslot(2) * P.Ns + (i + 1), P.shift_g[2]);
+        g[3] = Codec<S>::load(src + (size_t)gslot(3) * P.Ns + (i - P.Ws), P.shift_g[3]);
+        g[4] = Codec<S>::load(src + (size_t)gslot(4) * P.Ns + (i + P.Ws), P.shift_g[4]);
+        g[5] = Codec<S>::load(src + (size_t)gslot(5) * P.Ns + (i - P.splane), P.shift_g[5]);
+        g[6] = Codec<S>::load(src + (size_t)gslot(6) * P.Ns + (i + P.splane), P.shift_g[6]);
+    } else if (pull) {
         g[0] = pull_g_one<S, 0>(P, src, i, x, y, z, n);
         g[1] = pull_g_one<S, 1>(P, src, i, x, y, z, n);
         g[2] = pull_g_one<S, 2>(P, src, i, x, y, z, n);
@@ -201,17 +250,78 @@ __device__ __forceinline__ void load_g(const DevParams& P, const S* __restrict__
         g[6] = pull_g_one<S, 6>(P, src, i, x, y, z, n);
     } else {
 #pragma unroll
-        for (int a = 0; a < 7; ++a) g[a] = Codec<S>::load(src + (size_t)a * P.N + i, P.shift_g[a]);
+        for (int a = 0; a < 7; ++a) g[a] = Codec<S>::load(src + (size_t)gslot(a) * P.Ns + i, P.shift_g[a]);
     }
+}
+
+// Store the 26 post-collision populations at storage index i, walking the slots in order.
+template <typename S>
+__device__ __forceinline__ void store_slots(const DevParams& P, S* __restrict__ dst, int i, const float f[19],
+                                            const float g[7]) {
+    S* q = dst + i;
+#define GB300_ST(V, SH) { Codec<S>::store(q, V, SH); q += P.Ns; }
+    GB300_ST(f[0], P.shift_f[0]) GB300_ST(f[1], P.shift_f[1]) GB300_ST(f[2], P.shift_f[2])
+    GB300_ST(f[3], P.shift_f[3]) GB300_ST(f[4], P.shift_f[4]) GB300_ST(f[7], P.shift_f[7])
+    GB300_ST(f[8], P.shift_f[8]) GB300_ST(f[9], P.shift_f[9]) GB300_ST(f[10], P.shift_f[10])
+    GB300_ST(g[0], P.shift_g[0]) GB300_ST(g[1], P.shift_g[1]) GB300_ST(g[2], P.shift_g[2])
+    GB300_ST(g[3], P.shift_g[3]) GB300_ST(g[4], P.shift_g[4])
+    GB300_ST(f[5], P.shift_f[5]) GB300_ST(f[11], P.shift_f[11]) GB300_ST(f[14], P.shift_f[14])
+    GB300_ST(f[15], P.shift_f[15]) GB300_ST(f[18], P.shift_f[18]) GB300_ST(g[5], P.shift_g[5])
+    GB300_ST(f[6], P.shift_f[6]) GB300_ST(f[12], P.shift_f[12]) GB300_ST(f[13], P.shift_f[13])
+    GB300_ST(f[16], P.shift_f[16]) GB300_ST(f[17], P.shift_f[17]) Codec<S>::store(q, g[6], P.shift_g[6]);
+#undef GB300_ST
+}
+
+// ghost images of coordinate c on an n-periodic axis: columns / rows -2, -1, n, n+1
+__device__ __forceinline__ bool ghost_image(int k, int c, int n, int& gcoord) {
+    const int cand = k == 0 ? -2 : k == 1 ? -1 : k == 2 ? n : n + 1;
+    gcoord = cand;
+    return (((cand % n) + n) % n) == c;
+}
+
+// Store the 26 post-collision populations of node (x, y, z) at storage index i, and into every
+// ghost cell whose periodic image is this node (f-periodic x / y axes only).  The slot order
+// of the store matches fslot / gslot.
+template <typename S>
+__device__ __forceinline__ void store_node(const DevParams& P, S* __restrict__ dst, int i, int x, int y, int z,
+                                           const float f[19], const float g[7]) {
+    store_slots<S>(P, dst, i, f, g);
+    const bool xw = f_wraps(P.bc[0]), yw = f_wraps(P.bc[2]);
+    const bool xe = xw && (x < 2 || x >= P.nx - 2), ye = yw && (y < 2 || y >= P.ny - 2);
+    if (!(xe || ye)) return;
+    for (int kx = -1; kx < 4; ++kx) {          // -1: the node's own column
+        int cx = x;
+        if (kx >= 0 && !(xw && ghost_image(kx, x, P.nx, cx))) continue;
+        for (int ky = -1; ky < 4; ++ky) {
+            int cy = y;
+            if (ky >= 0 && !(yw && ghost_image(ky, y, P.ny, cy))) continue;
+            if (kx < 0 && ky < 0) continue;
+            store_slots<S>(P, dst, sidx(P, cx, cy, z), f, g);
+        }
+    }
+}
+
+// rho = sum f and T = sum g in one fixed pairwise order (every kernel uses these, so all variants
+// agree bit for bit; the tree also shortens the dependency chain)
+__device__ __forceinline__ float sum19(const float f[19]) {
+    float a = (f[1] + f[2]) + (f[3] + f[4]), b = (f[5] + f[6]) + (f[7] + f[8]);
+    float c = (f[9] + f[10]) + (f[11] + f[12]), d = (f[13] + f[14]) + (f[15] + f[16]);
+    float e = (f[17] + f[18]) + f[0];
+    return ((a + b) + (c + d)) + e;
+}
+__device__ __forceinline__ float sum7(const float g[7]) {
+    return ((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + g[0]);
 }
 
 // ---------------------------------------------------------------- thermodynamics
 // Peng-Robinson pressure (Eq. 49) and psi^2 = 2 (p_EOS - rho cs^2) / (G c^2) with G = -1 (Eq. 8).
 __device__ __forceinline__ float psi_squared(const DevParams& P, float rho, float T) {
-    float s = 1.f + P.kappa * (1.f - sqrtf(T / P.Tc));
+    float s = 1.f + P.kappa * (1.f - sqrtf(T * P.inv_Tc));
     float theta = s * s;
     float brho = P.b * rho;
-    float p = rho * P.R * T / (1.f - brho) - P.a * theta * rho * rho / (1.f + 2.f * brho - brho * brho);
+    float d1 = 1.f - brho, d2 = 1.f + 2.f * brho - brho * brho;
+    float inv = __frcp_rn(d1 * d2);   // one reciprocal for both denominators
+    float p = rho * P.R * T * (d2 * inv) - P.a * theta * rho * rho * (d1 * inv);
     return 2.f * (rho * (1.f / 3.f) - p);
 }
 
@@ -244,22 +354,20 @@ __device__ __forceinline__ void back_transform(float rho, float ax, float bx, fl
 
 // ---------------------------------------------------------------- D3Q19 MRT collision
 struct NodeOut {
-    float ux, uy, uz, divu;
+    float ux, uy, uz, divu, inv_rho;
 };
 
-// In: post-streaming f, total force F, interaction force Fm, psi^2.  Out: f* in place.
+// In: post-streaming f with rho = sum19(f), total force F, interaction force Fm, psi^2.
+// Out: f* in place.
 // Eq. 10 velocity, Eq. 5 equilibrium moments, Eq. 9 forcing, Eq. 6 rates, Eq. 3 relaxation,
 // Eq. 4 back-transform, Eq. 48 divergence.
-__device__ __forceinline__ NodeOut collide_f(const DevParams& P, float f[19], float Fx, float Fy,
+__device__ __forceinline__ NodeOut collide_f(const DevParams& P, float f[19], float rho, float Fx, float Fy,
                                              float Fz, float Fm2, float psi2) {
     const float cs2 = 1.f / 3.f;
-    float rho = 0.f;
-#pragma unroll
-    for (int a = 0; a < 19; ++a) rho += f[a];
     float jx = (f[1] - f[2]) + (f[7] - f[8]) + (f[9] - f[10]) + (f[11] - f[12]) + (f[13] - f[14]);
     float jy = (f[3] - f[4]) + (f[7] - f[8]) - (f[9] - f[10]) + (f[15] - f[16]) + (f[17] - f[18]);
     float jz = (f[5] - f[6]) + (f[11] - f[12]) - (f[13] - f[14]) + (f[15] - f[16]) - (f[17] - f[18]);
-    float inv_rho = 1.f / rho;
+    float inv_rho = __frcp_rn(rho);
     float ux = (jx + 0.5f * Fx) * inv_rho, uy = (jy + 0.5f * Fy) * inv_rho, uz = (jz + 0.5f * Fz) * inv_rho;
 
     // raw moments (rows of M)
@@ -291,7 +399,7 @@ __device__ __forceinline__ NodeOut collide_f(const DevParams& P, float f[19], fl
 
     // forcing moments (Eq. 9)
     float Fu_x = Fx * ux, Fu_y = Fy * uy, Fu_z = Fz * uz;
-    float S4 = 2.f * (Fu_x + Fu_y + Fu_z) + P.sigma6 * Fm2 / psi2;
+    float S4 = 2.f * (Fu_x + Fu_y + Fu_z) + P.sigma6 * Fm2 * __frcp_rn(psi2);
     float S5 = 2.f * (2.f * Fu_x - Fu_y - Fu_z), S6 = 2.f * (Fu_y - Fu_z);
     float S7 = Fx * uy + Fy * ux, S8 = Fx * uz + Fz * ux, S9 = Fy * uz + Fz * uy;
     float S10 = cs2 * Fy, S11 = cs2 * Fx, S12 = cs2 * Fz, S13 = cs2 * Fx, S14 = cs2 * Fz, S15 = cs2 * Fy;
@@ -299,6 +407,7 @@ __device__ __forceinline__ NodeOut collide_f(const DevParams& P, float f[19], fl
 
     NodeOut o;
     o.ux = ux; o.uy = uy; o.uz = uz;
+    o.inv_rho = inv_rho;
     // Eq. 48 (pre-collision m_4, force-corrected u, full S_4, total F)
     o.divu = (-(m4 - e4) * P.inv_tau_e + P.half_Le * S4 - 2.f * (Fu_x + Fu_y + Fu_z)) * (1.5f * inv_rho);
 
@@ -322,10 +431,10 @@ __device__ __forceinline__ NodeOut collide_f(const DevParams& P, float f[19], fl
     m17 += -Lp * (m17 - e17) + hp * S17;
     m18 += -Lp * (m18 - e18) + hp * S18;
 
-    // back-transform f* = M^-1 m* (closed form of the raw-moment inverse).  Divisions are
-    // correctly rounded (a rounded 1/3 factor biases the sums), and the rest population is formed
-    // last as rho - sum of the others, so that FP32 rounding cannot drift the mass (m_0* = rho).
-    float X = (m4 + m5) / 3.f;
+    // back-transform f* = M^-1 m* (closed form of the raw-moment inverse).  The rest population
+    // is formed last as rho - sum of the others, so that FP32 rounding (e.g. of the 1/3 factor)
+    // cannot drift the mass: m_0* = rho exactly as Eq. 3 demands.
+    float X = (m4 + m5) * (1.f / 3.f);
     float Y = 0.5f * (m4 - X + m6);
     float Z = 0.5f * (m4 - X - m6);
     float ax = X - m16 - m17, bx = r1 - m11 - m13;
@@ -347,7 +456,7 @@ __device__ __forceinline__ void feq(float rho, float ux, float uy, float uz, flo
     float m14 = rho * uz * (cs2 + uy2), m15 = rho * uy * (cs2 + uz2);
     float m16 = phi + rho * cs2 * (ux2 + uy2), m17 = phi + rho * cs2 * (ux2 + uz2);
     float m18 = phi + rho * cs2 * (uy2 + uz2);
-    float X = (m4 + m5) / 3.f;
+    float X = (m4 + m5) * (1.f / 3.f);
     float Y = 0.5f * (m4 - X + m6);
     float Z = 0.5f * (m4 - X - m6);
     float ax = X - m16 - m17, bx = rho * ux - m11 - m13;
@@ -367,18 +476,18 @@ __device__ __forceinline__ float collide_g(const DevParams& P, float g[7], float
     float n4 = g[1] + g[2] + g[3] + g[4] + g[5] + g[6];
     float n5 = g[1] + g[2] - g[3] - g[4];
     float n6 = g[1] + g[2] - g[5] - g[6];
-    float chi = P.lambda_mode ? P.chi_or_lambda / (rho * P.cV) : P.chi_or_lambda;
-    float vsT = chi / P.csT2 + 0.5f;                 // chi = (varsigma_T - 1/2) cs_T^2
-    float inv_vsT = 1.f / vsT;
-    float k = -inv_vsT / P.csT2;                     // Eq. 45
+    const float inv_rho = o.inv_rho;
+    float chi = P.lambda_mode ? P.chi_or_lambda * inv_rho * P.inv_cV : P.chi_or_lambda;
+    float vsT = chi * P.inv_csT2 + 0.5f;             // chi = (varsigma_T - 1/2) cs_T^2
+    float inv_vsT = __frcp_rn(vsT);
+    float k = -inv_vsT * P.inv_csT2;                 // Eq. 45
     float gTx = k * n1, gTy = k * n2, gTz = k * n3;
     float phis = 0.f;
     if (!P.flow_off) {
-        float inv_rho = 1.f / rho;
         phis = (chi * grx * inv_rho - o.ux) * gTx + (chi * gry * inv_rho - o.uy) * gTy +
                (chi * grz * inv_rho - o.uz) * gTz;
         // T/(rho cV) (dp/dT)_rho div u with (dp/dT)_rho ~ rho R / (1 - b rho)
-        phis -= T * P.R / (P.cV * (1.f - P.b * rho)) * o.divu;
+        phis -= T * P.R_over_cV * __frcp_rn(1.f - P.b * rho) * o.divu;
     }
     float C = first ? phis : phis_prev;
     float qs = 1.5f * phis - 0.5f * C;               // Q_a = w_a (3/2 phi_s(t) - 1/2 phi_s(t-1))
@@ -387,11 +496,15 @@ __device__ __forceinline__ float collide_g(const DevParams& P, float g[7], float
     n4 = n4 - P.Gq * (n4 - P.d * T);                 // 3 cs_T^2 T = d T
     n5 *= 1.f - P.Gpi;
     n6 *= 1.f - P.Gpi;
-    // g* = N^-1 n* (Eq. 41) with correctly rounded divisions; g*_0 = T - sum g*_1..6 keeps
-    // sum g* = T free of rounding drift (n_0* = T); then g+ = g* + Q (Eq. 40).
-    float h1 = (3.f * n1 + n4 + n5 + n6) / 6.f, h2 = (-3.f * n1 + n4 + n5 + n6) / 6.f;
-    float h3 = (3.f * n2 + n4 - 2.f * n5 + n6) / 6.f, h4 = (-3.f * n2 + n4 - 2.f * n5 + n6) / 6.f;
-    float h5 = (3.f * n3 + n4 + n5 - 2.f * n6) / 6.f, h6 = (-3.f * n3 + n4 + n5 - 2.f * n6) / 6.f;
+    // g* = N^-1 n* (Eq. 41); g*_0 = T - sum g*_1..6 keeps sum g* = T free of rounding drift
+    // (n_0* = T; a rounded 1/6 factor would otherwise bias it); then g+ = g* + Q (Eq. 40).
+    const float s6 = 1.f / 6.f;
+    float n456 = n4 + n5 + n6;
+    float h1 = s6 * (n456 + 3.f * n1), h2 = s6 * (n456 - 3.f * n1);
+    float n4_5 = n4 - 2.f * n5 + n6;
+    float h3 = s6 * (n4_5 + 3.f * n2), h4 = s6 * (n4_5 - 3.f * n2);
+    float n4_6 = n4 + n5 - 2.f * n6;
+    float h5 = s6 * (n4_6 + 3.f * n3), h6 = s6 * (n4_6 - 3.f * n3);
     float h0 = T - ((h1 + h2) + (h3 + h4) + (h5 + h6));
     float q0 = P.w0 * qs, q1 = P.w1 * qs;
     g[0] = h0 + q0;

@@ -1,19 +1,24 @@
-// Fused z-marching variant of the lattice update: one kernel per time step.
+// Fused z-marching variants of the lattice update: one kernel per time step.
 //
-// A CTA owns a 32 x TY tile of (x, y) columns and marches through a chunk of z-planes.  For
+// A CTA owns a 32 x 8 tile of (x, y) columns and marches through a chunk of z-planes.  For
 // every plane it
-//   phase A: pulls the 26 populations of each tile node and of the one-node halo ring around
-//            the tile, forms rho = sum f (Eq. 10), T = sum g (Eq. 20) and psi (Eq. 8 with the
-//            Peng-Robinson EOS, Eq. 49), and keeps (psi, rho) in a 3-plane shared-memory ring;
-//            the tile's own populations are parked in shared memory for phase B;
-//   phase B: collides the previous plane: interaction force (Eq. 7) and grad rho from the ring,
-//            buoyancy, D3Q19 MRT collision (Eqs. 3-6, 9, 10), div u (Eq. 48), grad T (Eq. 45),
-//            phi_s (Eq. 18), source Q (Eq. 23) and the D3Q7 MRT collision (Eqs. 38-43), and
-//            stores f*, g+ and phi_s.
-// psi and rho never go to HBM: the halo ring is recomputed from the populations (26 extra
-// population reads per halo node, mostly L2 hits because neighbouring CTAs march through the
-// same planes at the same time).  rho_ave for the buoyancy force is the deterministic FP64
-// mean of this step's rho, used by the next step.
+//   psi pass : pulls the 26 populations of each tile node and of the one-node halo ring around
+//              the tile, forms rho = sum f (Eq. 10), T = sum g (Eq. 20) and psi (Eq. 8 with the
+//              Peng-Robinson EOS, Eq. 49), and keeps (psi, rho) in a shared-memory plane ring;
+//   collision: for the previous plane: interaction force (Eq. 7) and grad rho from the ring,
+//              buoyancy, D3Q19 MRT collision (Eqs. 3-6, 9, 10), div u (Eq. 48), grad T (Eq. 45),
+//              phi_s (Eq. 18), source Q (Eq. 23), D3Q7 MRT collision (Eqs. 38-43); stores f*,
+//              g+ and phi_s.
+// psi and rho never go to HBM: the halo ring is recomputed from the populations.  rho_ave of
+// the buoyancy force is the deterministic FP64 mean of this step's rho, used by the next step.
+//
+// k_fused     : generic (any faces, any storage precision, frozen f or g, first step).
+// k_fused_tma : FP32, f-periodic x and y faces (any z faces).  A producer warp fetches each
+//               plane's pulls for the whole tile + halo with three TMA tensor copies (one per
+//               e_z group of population slots) into a 3-stage shared-memory pipeline guarded by
+//               mbarriers; 11 consumer warps read every pull as one shared-memory load at a
+//               fixed offset.  Persistent CTAs take (z-chunk, tile) items round robin.
+#include <cuda.h>
 #include "lbm_launch.h"
 
 namespace gb300lbm {
@@ -21,6 +26,7 @@ namespace gb300lbm {
 namespace {
 
 constexpr int TX = 32;
+constexpr int kTY = 8;
 
 template <int TY> struct FusedShape {
     static constexpr int kInterior = TX * TY;
@@ -29,7 +35,6 @@ template <int TY> struct FusedShape {
     static constexpr int kThreads = kInterior + kHaloThreads;
     static constexpr int kRingW = TX + 2, kRingH = TY + 2;
     static constexpr int kRingPlane = kRingW * kRingH;
-    // shared memory: two population stages of the tile (float) + the (psi, rho) ring
     static constexpr size_t kStageFloats = 26 * kInterior;
     static constexpr size_t kSmemBytes = 2 * kStageFloats * sizeof(float) + 3 * kRingPlane * sizeof(float2);
 };
@@ -42,25 +47,13 @@ __device__ __forceinline__ int map_coord(int c, int n, int bc_lo, int bc_hi) {
     return c;
 }
 
-template <typename S, int TY>
-__global__ void __launch_bounds__(FusedShape<TY>::kThreads, 2)
-k_fused(DevParams P, const S* __restrict__ fs, const S* __restrict__ gs, S* __restrict__ fd,
-        S* __restrict__ gd, int pull_f, int pull_g, const double* __restrict__ sums_cur, double2* partial,
-        unsigned* counter, double* sums_next, float* __restrict__ phis, int* flag, int first, int zchunk) {
+// ring slot (lx, ly) of a thread: tile nodes first (one warp per row), then the halo ring
+template <int TY>
+__device__ __forceinline__ void slot_of(int tid, int& lx, int& ly) {
     using Sh = FusedShape<TY>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* stage = reinterpret_cast<float*>(smem_raw);                       // [2][26][TY][32]
-    float2* ring = reinterpret_cast<float2*>(stage + 2 * Sh::kStageFloats);  // [3][TY+2][34]
-
-    const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = blockIdx.z * zchunk;
-    const int z1 = min(P.nz, z0 + zchunk);
-
-    // ring slot handled by this thread in phase A
-    int lx = -1, ly = -1;
-    const bool interior = tid < Sh::kInterior;
-    if (interior) {
+    lx = -1;
+    ly = -1;
+    if (tid < Sh::kInterior) {
         lx = (tid & 31) + 1;
         ly = (tid >> 5) + 1;
     } else {
@@ -69,34 +62,139 @@ k_fused(DevParams P, const S* __restrict__ fs, const S* __restrict__ gs, S* __re
         else if (h < 2 * (TX + 2)) { lx = h - (TX + 2); ly = TY + 1; }
         else if (h < Sh::kHaloNodes) { int k = h - 2 * (TX + 2); lx = (k & 1) ? TX + 1 : 0; ly = 1 + (k >> 1); }
     }
+}
+
+// interaction force sum_a w psi(x+e) e and grad rho from the (psi, rho) ring planes
+struct RingStencil {
+    float Fx, Fy, Fz, gx, gy, gz;
+};
+__device__ __forceinline__ RingStencil ring_stencil(const float2* rm, const float2* r0, const float2* rp, int slot,
+                                                   int W) {
+    RingStencil s = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#define GB300_NB(PL, DX, DY, DZ, WGT)                                          \
+    {                                                                          \
+        float2 q = PL[slot + (DY) * W + (DX)];                                 \
+        if (DX) { s.Fx += (DX * WGT) * q.x; s.gx += (DX * WGT) * q.y; }        \
+        if (DY) { s.Fy += (DY * WGT) * q.x; s.gy += (DY * WGT) * q.y; }        \
+        if (DZ) { s.Fz += (DZ * WGT) * q.x; s.gz += (DZ * WGT) * q.y; }        \
+    }
+    const float w1 = 1.f / 6.f, w2 = 1.f / 12.f;
+    GB300_NB(r0, 1, 0, 0, w1) GB300_NB(r0, -1, 0, 0, w1) GB300_NB(r0, 0, 1, 0, w1) GB300_NB(r0, 0, -1, 0, w1)
+    GB300_NB(rp, 0, 0, 1, w1) GB300_NB(rm, 0, 0, -1, w1)
+    GB300_NB(r0, 1, 1, 0, w2) GB300_NB(r0, -1, -1, 0, w2) GB300_NB(r0, 1, -1, 0, w2) GB300_NB(r0, -1, 1, 0, w2)
+    GB300_NB(rp, 1, 0, 1, w2) GB300_NB(rm, -1, 0, -1, w2) GB300_NB(rm, 1, 0, -1, w2) GB300_NB(rp, -1, 0, 1, w2)
+    GB300_NB(rp, 0, 1, 1, w2) GB300_NB(rm, 0, -1, -1, w2) GB300_NB(rm, 0, 1, -1, w2) GB300_NB(rp, 0, -1, 1, w2)
+#undef GB300_NB
+    return s;
+}
+
+__device__ __forceinline__ void kahan_add(float& sum, float& c, float v) {
+    float y = v - c, t = sum + y;
+    c = (t - sum) - y;
+    sum = t;
+}
+
+// barrier 0 = the whole block; other ids = named barrier over the first nthreads threads
+__device__ __forceinline__ void sync_threads(int bar_id, int nthreads) {
+    if (bar_id == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(nthreads) : "memory");
+}
+
+// FP64 sum of (a, b) over the NT threads of the barrier group, written to partial[index]
+template <int NT>
+__device__ void block_partial(double a, double b, double2* partial, int index, int tid, int bar_id, double* sa,
+                              double* sb) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if ((tid & 31) == 0) { sa[tid >> 5] = a; sb[tid >> 5] = b; }
+    sync_threads(bar_id, NT);
+    if (tid == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int w = 0; w < NT / 32; ++w) { ta += sa[w]; tb += sb[w]; }
+        partial[index] = make_double2(ta, tb);
+    }
+    sync_threads(bar_id, NT);
+}
+
+// The last block of the grid to arrive adds partial[0..n) in index order into out[0..1] and
+// resets the ticket: the result depends only on the partials, never on block scheduling.
+template <int NT>
+__device__ void finish_sums(const double2* partial, int n, unsigned* counter, double* out, int tid, int bar_id,
+                            double* sa, double* sb, int* is_last) {
+    if (tid == 0) {
+        __threadfence();
+        unsigned ticket = atomicAdd(counter, 1u);
+        *is_last = ticket == gridDim.x * gridDim.y * gridDim.z - 1;
+    }
+    sync_threads(bar_id, NT);
+    if (!*is_last) return;
+    __threadfence();
+    double ta = 0.0, tb = 0.0;
+    for (int k = tid; k < n; k += NT) {
+        double2 q = __ldcg(partial + k);
+        ta += q.x;
+        tb += q.y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ta += __shfl_down_sync(0xffffffffu, ta, o);
+        tb += __shfl_down_sync(0xffffffffu, tb, o);
+    }
+    if ((tid & 31) == 0) { sa[tid >> 5] = ta; sb[tid >> 5] = tb; }
+    sync_threads(bar_id, NT);
+    if (tid == 0) {
+        double ra = 0.0, rb = 0.0;
+        for (int w = 0; w < NT / 32; ++w) { ra += sa[w]; rb += sb[w]; }
+        out[0] = ra;
+        out[1] = rb;
+        *counter = 0u;
+    }
+}
+
+// ================================================================ generic fused kernel
+template <typename S, int TY>
+__global__ void __launch_bounds__(FusedShape<TY>::kThreads, 2)
+k_fused(DevParams P, const S* __restrict__ src, S* __restrict__ dst, int pull_f, int pull_g,
+        const double* __restrict__ sums_cur, double2* partial, unsigned* counter, double* sums_next,
+        float* __restrict__ phis, int* flag, int first, int zchunk) {
+    using Sh = FusedShape<TY>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* stage = reinterpret_cast<float*>(smem_raw);                       // [2][26][TY][32]
+    float2* ring = reinterpret_cast<float2*>(stage + 2 * Sh::kStageFloats);  // [3][TY+2][34]
+    __shared__ double red_a[Sh::kThreads / 32], red_b[Sh::kThreads / 32];
+    __shared__ int is_last;
+
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * zchunk;
+    const int z1 = min(P.nz, z0 + zchunk);
+    int lx, ly;
+    slot_of<TY>(tid, lx, ly);
+    const bool interior = tid < Sh::kInterior;
     const int gx = x0 + lx - 1, gy = y0 + ly - 1;
-    // slots outside [-1, n] are never read by any stencil
     const bool slot_used = lx >= 0 && gx >= -1 && gx <= P.nx && gy >= -1 && gy <= P.ny;
     const int mx = slot_used ? map_coord(gx, P.nx, P.bc[0], P.bc[1]) : 0;
     const int my = slot_used ? map_coord(gy, P.ny, P.bc[2], P.bc[3]) : 0;
-    // this thread's own node takes part in phase B
     const bool owner = interior && gx < P.nx && gy < P.ny;
     const int slot = ly * Sh::kRingW + lx;
 
-    double r_acc = 0.0, t_acc = 0.0;
+    float r_sum = 0.f, r_c = 0.f, t_sum = 0.f, t_c = 0.f;
     int bad = 0;
-    const float rho_ave = (float)(sums_cur[0] / (double)P.N);
+    const float rho_ave = (float)(sums_cur[0] * P.inv_N);
 
-    // ---------------------------------------------------------------- phase A for plane zp
-    auto phase_a = [&](int zp) {
+    auto psi_pass = [&](int zp) {
         if (!slot_used) return;
         const bool in_chunk = zp >= z0 && zp < z1;
         const int mz = map_coord(zp, P.nz, P.bc[4], P.bc[5]);
-        const int i = node_of(P, mx, my, mz);
+        const int i = sidx(P, mx, my, mz);
         Nbr n = make_nbr(P, mx, my, mz);
         float f[19], g[7];
-        load_f<S>(P, fs, pull_f, i, mx, my, mz, n, f);
-        load_g<S>(P, gs, pull_g, i, mx, my, mz, n, g);
-        float rho = 0.f, T = 0.f;
-#pragma unroll
-        for (int a = 0; a < 19; ++a) rho += f[a];
-#pragma unroll
-        for (int a = 0; a < 7; ++a) T += g[a];
+        load_f<S>(P, src, pull_f, i, mx, my, mz, n, f);
+        load_g<S>(P, src, pull_g, i, mx, my, mz, n, g);
+        float rho = sum19(f), T = sum7(g);
         float psi2 = psi_squared(P, rho, T);
         ring[((zp + 3) % 3) * Sh::kRingPlane + slot] = make_float2(sqrtf(psi2), rho);
         if (owner && in_chunk) {
@@ -105,129 +203,453 @@ k_fused(DevParams P, const S* __restrict__ fs, const S* __restrict__ gs, S* __re
             for (int a = 0; a < 19; ++a) st[a * Sh::kInterior] = f[a];
 #pragma unroll
             for (int a = 0; a < 7; ++a) st[(19 + a) * Sh::kInterior] = g[a];
-            r_acc += (double)rho;
-            t_acc += (double)T;
+            kahan_add(r_sum, r_c, rho);
+            kahan_add(t_sum, t_c, T);
             bad |= !(psi2 > 0.f) || !isfinite(rho) || !isfinite(T);
         }
     };
 
-    // ---------------------------------------------------------------- phase B for plane z
-    auto phase_b = [&](int z) {
+    auto collide = [&](int z) {
         if (!owner) return;
         const int x = gx, y = gy;
-        const int i = node_of(P, x, y, z);
+        const int i = sidx(P, x, y, z), d = node_of(P, x, y, z);
         const float* st = stage + ((z - z0) & 1) * Sh::kStageFloats + tid;
         float f[19], g[7];
 #pragma unroll
         for (int a = 0; a < 19; ++a) f[a] = st[a * Sh::kInterior];
 #pragma unroll
         for (int a = 0; a < 7; ++a) g[a] = st[(19 + a) * Sh::kInterior];
-        float rho = 0.f, T = 0.f;
-#pragma unroll
-        for (int a = 0; a < 19; ++a) rho += f[a];
-#pragma unroll
-        for (int a = 0; a < 7; ++a) T += g[a];
-        const float2* rm = ring + ((z + 2) % 3) * Sh::kRingPlane;   // plane z - 1
+        float rho = sum19(f), T = sum7(g);
+        const float2* rm = ring + ((z + 2) % 3) * Sh::kRingPlane;
         const float2* r0 = ring + (z % 3) * Sh::kRingPlane;
-        const float2* rp = ring + ((z + 1) % 3) * Sh::kRingPlane;   // plane z + 1
+        const float2* rp = ring + ((z + 1) % 3) * Sh::kRingPlane;
         const float2 me = r0[slot];
-        float Fx = 0.f, Fy = 0.f, Fz = 0.f, grx = 0.f, gry = 0.f, grz = 0.f;
-        const int W = Sh::kRingW;
-#define GB300_NB(PL, DX, DY, DZ, WGT)                                      \
-        {                                                                  \
-            float2 q = PL[slot + (DY) * W + (DX)];                         \
-            if (DX) { Fx += (DX * WGT) * q.x; grx += (DX * WGT) * q.y; }   \
-            if (DY) { Fy += (DY * WGT) * q.x; gry += (DY * WGT) * q.y; }   \
-            if (DZ) { Fz += (DZ * WGT) * q.x; grz += (DZ * WGT) * q.y; }   \
-        }
-        const float w1 = 1.f / 6.f, w2 = 1.f / 12.f;
-        GB300_NB(r0, 1, 0, 0, w1) GB300_NB(r0, -1, 0, 0, w1) GB300_NB(r0, 0, 1, 0, w1) GB300_NB(r0, 0, -1, 0, w1)
-        GB300_NB(rp, 0, 0, 1, w1) GB300_NB(rm, 0, 0, -1, w1)
-        GB300_NB(r0, 1, 1, 0, w2) GB300_NB(r0, -1, -1, 0, w2) GB300_NB(r0, 1, -1, 0, w2) GB300_NB(r0, -1, 1, 0, w2)
-        GB300_NB(rp, 1, 0, 1, w2) GB300_NB(rm, -1, 0, -1, w2) GB300_NB(rm, 1, 0, -1, w2) GB300_NB(rp, -1, 0, 1, w2)
-        GB300_NB(rp, 0, 1, 1, w2) GB300_NB(rm, 0, -1, -1, w2) GB300_NB(rm, 0, 1, -1, w2) GB300_NB(rp, 0, -1, 1, w2)
-#undef GB300_NB
-        float Fmx = me.x * Fx, Fmy = me.x * Fy, Fmz = me.x * Fz;
+        RingStencil rs = ring_stencil(rm, r0, rp, slot, Sh::kRingW);
+        float Fmx = me.x * rs.Fx, Fmy = me.x * rs.Fy, Fmz = me.x * rs.Fz;
         float db = rho - rho_ave;
         float Fm2 = Fmx * Fmx + Fmy * Fmy + Fmz * Fmz;
-        NodeOut o = collide_f(P, f, Fmx + db * P.gx, Fmy + db * P.gy, Fmz + db * P.gz, Fm2, me.x * me.x);
-        if (!P.flow_off) {
+        NodeOut o = collide_f(P, f, rho, Fmx + db * P.gx, Fmy + db * P.gy, Fmz + db * P.gz, Fm2, me.x * me.x);
+        float ph = collide_g(P, g, rho, T, o, rs.gx, rs.gy, rs.gz, phis[d], first);
+        // frozen fields keep their stored values (no streaming, no collision)
+        if (P.flow_off) {
 #pragma unroll
-            for (int a = 0; a < 19; ++a) Codec<S>::store(fd + (size_t)a * P.N + i, f[a], P.shift_f[a]);
+            for (int a = 0; a < 19; ++a) f[a] = Codec<S>::load(src + (size_t)fslot(a) * P.Ns + i, P.shift_f[a]);
         }
-        float ph = collide_g(P, g, rho, T, o, grx, gry, grz, phis[i], first);
-        if (!P.thermal_off) {
+        if (P.thermal_off) {
 #pragma unroll
-            for (int a = 0; a < 7; ++a) Codec<S>::store(gd + (size_t)a * P.N + i, g[a], P.shift_g[a]);
+            for (int a = 0; a < 7; ++a) g[a] = Codec<S>::load(src + (size_t)gslot(a) * P.Ns + i, P.shift_g[a]);
         }
-        phis[i] = ph;
+        store_node<S>(P, dst, i, x, y, z, f, g);
+        phis[d] = ph;
     };
 
-    phase_a(z0 - 1);
-    phase_a(z0);
+    psi_pass(z0 - 1);
+    psi_pass(z0);
     __syncthreads();
     for (int z = z0; z < z1; ++z) {
-        phase_a(z + 1);
+        psi_pass(z + 1);
         __syncthreads();
-        phase_b(z);
+        collide(z);
         __syncthreads();
     }
 
     if (__syncthreads_or(bad) && tid == 0) atomicOr(flag, 1);
-    // deterministic FP64 sums of this step's rho and T (rho_ave of the next step)
-    {
-        __shared__ double sa[Sh::kThreads / 32], sb[Sh::kThreads / 32];
-        __shared__ int is_last;
-        double a = r_acc, b = t_acc;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_down_sync(0xffffffffu, a, o);
-            b += __shfl_down_sync(0xffffffffu, b, o);
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    block_partial<Sh::kThreads>((double)r_sum - (double)r_c, (double)t_sum - (double)t_c, partial, bid, tid, 0,
+                                red_a, red_b);
+    finish_sums<Sh::kThreads>(partial, gridDim.x * gridDim.y * gridDim.z, counter, sums_next, tid, 0, red_a, red_b,
+                              &is_last);
+}
+
+// ================================================================ TMA producer / consumer kernel
+// Tile TX x TY; consumer threads: tile slots (row-major), then the halo ring, then idle lanes.
+template <int TX_, int TY_> struct TmaShape {
+    static constexpr int kInterior = TX_ * TY_;
+    static constexpr int kHaloNodes = 2 * (TX_ + 2) + 2 * TY_;
+    static constexpr int kSlotsAll = kInterior + kHaloNodes;        // ring slots with a psi value
+    static constexpr int kPsiWarps = 6;                              // psi pass: slots round robin
+    static constexpr int kColWarps = (kInterior + 31) / 32;          // collision: one node per thread
+    static constexpr int kPsiThreads = kPsiWarps * 32, kColThreads = kColWarps * 32;
+    static constexpr int kThreads = 32 + kPsiThreads + kColThreads;  // producer warp first
+    static constexpr int kRingW = TX_ + 2, kRingPlane = (TX_ + 2) * (TY_ + 2);
+    static constexpr int kWinW = TX_ + 8;               // window columns x0-4 .. x0+TX+3 (16-byte aligned)
+    static constexpr int kWinH = TY_ + 4;               // window rows    y0-2 .. y0+TY+1
+    static constexpr int kWin = kWinW * kWinH;          // floats per population slot
+    static constexpr int kStages = 3, kRing = 4;
+    static constexpr size_t kSmem = (size_t)kStages * kSlots * kWin * sizeof(float) +
+                                    (size_t)kRing * kRingPlane * (sizeof(float2) + sizeof(float));
+};
+
+// ring slot (lx, ly) of slot index q: tile nodes (row-major), then the halo ring
+template <int TX_, int TY_>
+__device__ __forceinline__ void tma_slot_of(int q, int& lx, int& ly) {
+    using Sh = TmaShape<TX_, TY_>;
+    lx = -1;
+    ly = -1;
+    if (q < Sh::kInterior) {
+        lx = q % TX_ + 1;
+        ly = q / TX_ + 1;
+    } else {
+        int h = q - Sh::kInterior;
+        if (h < TX_ + 2) { lx = h; ly = 0; }
+        else if (h < 2 * (TX_ + 2)) { lx = h - (TX_ + 2); ly = TY_ + 1; }
+        else if (h < Sh::kHaloNodes) { int k = h - 2 * (TX_ + 2); lx = (k & 1) ? TX_ + 1 : 0; ly = 1 + (k >> 1); }
+    }
+}
+
+constexpr unsigned kSpinLimit = 1u << 21;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: false after kSpinLimit polls (the caller records a timeout and stops waiting)
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    for (unsigned it = 0; it < kSpinLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_4d(float* smem_dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(smem_u32(smem_dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// source plane of the e_z = +1 group (pulls from z-1) and of the e_z = -1 group (pulls from
+// z+1); -1 at a wall face (all those links bounce back from the node itself)
+__device__ __forceinline__ int src_plane_up(const DevParams& P, int mz) {
+    if (mz > 0) return mz - 1;
+    int bc = P.bc[4];
+    return f_wraps(bc) ? P.nz - 1 : (bc == BC_OUTFLOW ? 0 : -1);
+}
+__device__ __forceinline__ int src_plane_dn(const DevParams& P, int mz) {
+    if (mz < P.nz - 1) return mz + 1;
+    int bc = P.bc[5];
+    return f_wraps(bc) ? 0 : (bc == BC_OUTFLOW ? P.nz - 1 : -1);
+}
+
+// The 26 pulled populations of the node in window cell (wx, wy) of a stage, with the boundary
+// links of its plane mz patched: Eq. 50 for f at z walls (f*_abar of the node itself, read from
+// global memory), Eq. 51 for g at non-periodic z faces (own g+_abar from global memory) and at
+// thermal x / y faces (own g+_abar from the stage).
+template <int WW, int WIN>
+__device__ __forceinline__ void stage_pulls(const DevParams& P, const float* __restrict__ st, int wx, int wy,
+                                            const float* __restrict__ src, int mx, int my, int mz, float f[19],
+                                            float g[7]) {
+    const float* b = st + wy * WW + wx;
+#define GB300_SF(A) f[A] = b[fslot(A) * WIN - ey19(A) * WW - ex19(A)];
+    GB300_SF(0) GB300_SF(1) GB300_SF(2) GB300_SF(3) GB300_SF(4) GB300_SF(5) GB300_SF(6) GB300_SF(7) GB300_SF(8)
+    GB300_SF(9) GB300_SF(10) GB300_SF(11) GB300_SF(12) GB300_SF(13) GB300_SF(14) GB300_SF(15) GB300_SF(16)
+    GB300_SF(17) GB300_SF(18)
+#undef GB300_SF
+#define GB300_SG(A) g[A] = b[gslot(A) * WIN - ey7(A) * WW - ex7(A)];
+    GB300_SG(0) GB300_SG(1) GB300_SG(2) GB300_SG(3) GB300_SG(4) GB300_SG(5) GB300_SG(6)
+#undef GB300_SG
+    if (mz == 0 && P.bc[4] != BC_PERIODIC) {
+        const int i = sidx(P, mx, my, mz);
+        if (P.bc[4] == BC_WALL) {
+            f[5] = __ldg(src + (size_t)fslot(6) * P.Ns + i);
+            f[11] = __ldg(src + (size_t)fslot(12) * P.Ns + i);
+            f[14] = __ldg(src + (size_t)fslot(13) * P.Ns + i);
+            f[15] = __ldg(src + (size_t)fslot(16) * P.Ns + i);
+            f[18] = __ldg(src + (size_t)fslot(17) * P.Ns + i);
         }
-        if ((tid & 31) == 0) { sa[tid >> 5] = a; sb[tid >> 5] = b; }
-        __syncthreads();
-        const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-        const int nblocks = gridDim.x * gridDim.y * gridDim.z;
-        if (tid == 0) {
-            double ta = 0.0, tb = 0.0;
-            for (int w = 0; w < Sh::kThreads / 32; ++w) { ta += sa[w]; tb += sb[w]; }
-            partial[bid] = make_double2(ta, tb);
-            __threadfence();
-            is_last = atomicAdd(counter, 1u) == (unsigned)(nblocks - 1);
+        g[5] = -__ldg(src + (size_t)gslot(6) * P.Ns + i) + 2.f * P.w1 * wall_T(P, 4, mx, my);
+    }
+    if (mz == P.nz - 1 && P.bc[5] != BC_PERIODIC) {
+        const int i = sidx(P, mx, my, mz);
+        if (P.bc[5] == BC_WALL) {
+            f[6] = __ldg(src + (size_t)fslot(5) * P.Ns + i);
+            f[12] = __ldg(src + (size_t)fslot(11) * P.Ns + i);
+            f[13] = __ldg(src + (size_t)fslot(14) * P.Ns + i);
+            f[16] = __ldg(src + (size_t)fslot(15) * P.Ns + i);
+            f[17] = __ldg(src + (size_t)fslot(18) * P.Ns + i);
         }
-        __syncthreads();
-        if (is_last) {
-            __threadfence();
-            double ta = 0.0, tb = 0.0;
-            for (int k = tid; k < nblocks; k += Sh::kThreads) {
-                double2 p = __ldcg(partial + k);
-                ta += p.x;
-                tb += p.y;
+        g[6] = -__ldg(src + (size_t)gslot(5) * P.Ns + i) + 2.f * P.w1 * wall_T(P, 5, mx, my);
+    }
+    if (P.bc[0] == BC_THERMAL_ONLY && mx == 0) g[1] = -b[gslot(2) * WIN] + 2.f * P.w1 * wall_T(P, 0, mx, my);
+    if (P.bc[1] == BC_THERMAL_ONLY && mx == P.nx - 1) g[2] = -b[gslot(1) * WIN] + 2.f * P.w1 * wall_T(P, 1, mx, my);
+    if (P.bc[2] == BC_THERMAL_ONLY && my == 0) g[3] = -b[gslot(4) * WIN] + 2.f * P.w1 * wall_T(P, 2, mx, my);
+    if (P.bc[3] == BC_THERMAL_ONLY && my == P.ny - 1) g[4] = -b[gslot(3) * WIN] + 2.f * P.w1 * wall_T(P, 3, mx, my);
+}
+
+// Warp roles: warp 0 = producer (TMA), warps 1..4 = psi pass, the rest = collision.  Every
+// hand-off goes through an mbarrier:
+//   full[s]      TMA bytes of the stage landed              (producer  -> psi, collision)
+//   empty[s]     psi pass and collision done with a stage    (psi, collision -> producer)
+//   ring_full[r] (psi, rho) of a plane in ring slot r ready   (psi       -> collision)
+//   ring_empty[r] last collision reading ring slot r done     (collision -> psi)
+// Stage uses and ring uses follow one plane counter k across the CTA's items.
+template <int TX_, int TY_>
+__global__ void __launch_bounds__(TmaShape<TX_, TY_>::kThreads, 1)
+k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ CUtensorMap map6, DevParams P,
+            const float* __restrict__ src, float* __restrict__ dst, const double* __restrict__ sums_cur,
+            double2* partial, unsigned* counter, double* sums_next, float* __restrict__ phis, int* flag, int first,
+            int zchunk, int tiles_x, int tiles_y, int n_items) {
+    using Sh = TmaShape<TX_, TY_>;
+    constexpr int kWin = Sh::kWin, kWinW = Sh::kWinW, kStages = Sh::kStages, kRing = Sh::kRing;
+    constexpr int kCol = Sh::kColThreads;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    float* stages = reinterpret_cast<float*>(smem_raw);                          // [3][26][TY+4][TX+8]
+    float2* ring = reinterpret_cast<float2*>(stages + kStages * kSlots * kWin);  // [4][TY+2][TX+2] (psi, rho)
+    float* tring = reinterpret_cast<float*>(ring + kRing * Sh::kRingPlane);      // [4][TY+2][TX+2] T
+    __shared__ __align__(8) unsigned long long full_bar[kStages], empty_bar[kStages], ring_full[kRing],
+        ring_empty[kRing];
+    __shared__ double red_a[kCol / 32], red_b[kCol / 32];
+    __shared__ int is_last;
+    __shared__ volatile int abort_flag;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], Sh::kPsiWarps + Sh::kColWarps);
+        }
+        for (int r = 0; r < kRing; ++r) {
+            mbar_init(&ring_full[r], Sh::kPsiWarps);
+            mbar_init(&ring_empty[r], Sh::kColWarps);
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int ntiles = tiles_x * tiles_y;
+    // bounded wait that turns a timeout into an error flag and stops all further waiting
+    auto wait = [&](unsigned long long* bar, unsigned parity) {
+        if (abort_flag) return;
+        if (!mbar_wait(bar, parity)) {
+            abort_flag = 1;
+            atomicOr(flag, 2);
+        }
+    };
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer (one lane)
+        if (lane == 0) {
+            unsigned k = 0;
+            for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+                const int chunk = item / ntiles, tile = item % ntiles;
+                const int x0 = (tile % tiles_x) * TX_, y0 = (tile / tiles_x) * TY_;
+                const int z0 = chunk * zchunk, z1 = min(P.nz, z0 + zchunk);
+                for (int p = z0 - 1; p <= z1; ++p, ++k) {
+                    const int s = k % kStages;
+                    if (k >= (unsigned)kStages) wait(&empty_bar[s], (k / kStages - 1) & 1);
+                    if (abort_flag) {   // release the waiters without data
+                        mbar_arrive(&full_bar[s]);
+                        continue;
+                    }
+                    const int mz = map_coord(p, P.nz, P.bc[4], P.bc[5]);
+                    const int zu = src_plane_up(P, mz), zd = src_plane_dn(P, mz);
+                    const unsigned bytes = (14u + (zu >= 0 ? 6u : 0u) + (zd >= 0 ? 6u : 0u)) * kWin * 4u;
+                    float* st = stages + (size_t)s * kSlots * kWin;
+                    mbar_expect_tx(&full_bar[s], bytes);
+                    // window origin in storage coordinates: (x0 - 4) + kGX, (y0 - 2) + kGY
+                    const int cx = x0 - 4 + kGX, cy = y0;
+                    tma_load_4d(st, &map14, cx, cy, mz, 0, &full_bar[s]);
+                    if (zu >= 0) tma_load_4d(st + 14 * kWin, &map6, cx, cy, zu, 14, &full_bar[s]);
+                    if (zd >= 0) tma_load_4d(st + 20 * kWin, &map6, cx, cy, zd, 20, &full_bar[s]);
+                }
             }
+            // copies still in flight must land before the CTA exits (bounded)
+            for (unsigned q = (k > (unsigned)kStages ? k - kStages : 0u); q < k; ++q)
+                mbar_wait(&full_bar[q % kStages], (q / kStages) & 1);
+        }
+        __syncwarp();
+    } else if (warp <= Sh::kPsiWarps) {
+        // ------------------------------------------------------------ psi pass
+        const int pt = tid - 32;
+        int bad = 0;
+        unsigned k = 0;
+        for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+            const int chunk = item / ntiles, tile = item % ntiles;
+            const int x0 = (tile % tiles_x) * TX_, y0 = (tile / tiles_x) * TY_;
+            const int z0 = chunk * zchunk, z1 = min(P.nz, z0 + zchunk);
+            for (int p = z0 - 1; p <= z1; ++p, ++k) {
+                const int s = k % kStages, r = k % kRing;
+                if (k >= (unsigned)kRing) wait(&ring_empty[r], (k / kRing - 1) & 1);
+                wait(&full_bar[s], (k / kStages) & 1);
+                const float* st = stages + (size_t)s * kSlots * kWin;
+                const int mz = map_coord(p, P.nz, P.bc[4], P.bc[5]);
+#pragma unroll 2
+                for (int q = pt; q < Sh::kSlotsAll; q += Sh::kPsiThreads) {
+                    int lx, ly;
+                    tma_slot_of<TX_, TY_>(q, lx, ly);
+                    const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+                    if (gx < -1 || gx > P.nx || gy < -1 || gy > P.ny) continue;
+                    const int mx = map_coord(gx, P.nx, P.bc[0], P.bc[1]);
+                    const int my = map_coord(gy, P.ny, P.bc[2], P.bc[3]);
+                    float f[19], g[7];
+                    stage_pulls<kWinW, kWin>(P, st, lx + 3, ly + 1, src, mx, my, mz, f, g);
+                    float rho = sum19(f), T = sum7(g);
+                    const float psi2 = psi_squared(P, rho, T);
+                    ring[r * Sh::kRingPlane + ly * Sh::kRingW + lx] = make_float2(sqrtf(psi2), rho);
+                    tring[r * Sh::kRingPlane + ly * Sh::kRingW + lx] = T;
+                    bad |= !(psi2 > 0.f) || !isfinite(rho) || !isfinite(T);
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&ring_full[r]);
+                    mbar_arrive(&empty_bar[s]);
+                }
+            }
+        }
+        if (bad) atomicOr(flag, 1);
+    } else {
+        // ------------------------------------------------------------ collision
+        const int ct = tid - 32 - Sh::kPsiThreads;
+        const bool node_thread = ct < Sh::kInterior;
+        const int lx = ct % TX_ + 1, ly = ct / TX_ + 1;
+        const int slot = ly * Sh::kRingW + lx;
+        const float rho_ave = (float)(sums_cur[0] * P.inv_N);
+        unsigned k = 0;
+        for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+            const int chunk = item / ntiles, tile = item % ntiles;
+            const int x0 = (tile % tiles_x) * TX_, y0 = (tile / tiles_x) * TY_;
+            const int z0 = chunk * zchunk, z1 = min(P.nz, z0 + zchunk);
+            const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+            const bool owner = node_thread && gx < P.nx && gy < P.ny;
+            float r_sum = 0.f, r_c = 0.f, t_sum = 0.f, t_c = 0.f;
+            // phi_s history of the thread's node, loaded one plane ahead of its use
+            float ph_next = owner ? phis[node_of(P, gx, gy, z0)] : 0.f;
+            for (int p = z0 - 1; p <= z1; ++p, ++k) {
+                wait(&ring_full[k % kRing], (k / kRing) & 1);   // psi(p) ready
+                if (p == z0 - 1) {                               // plane z0-1: psi only
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&empty_bar[k % kStages]);
+                    continue;
+                }
+                if (p == z0) continue;   // plane z0 is collided once psi(z0+1) is ready
+                const int z = p - 1;     // collide plane z in [z0, z1) with ring planes z-1, z, z+1
+                const unsigned kz = k - 1;
+                wait(&full_bar[kz % kStages], (kz / kStages) & 1);
+                const float ph_prev = ph_next;
+                if (owner && z + 1 < z1) ph_next = phis[node_of(P, gx, gy, z + 1)];
+                float f[19], g[7];
+                if (owner) {
+                    const float* sz = stages + (size_t)(kz % kStages) * kSlots * kWin;
+                    stage_pulls<kWinW, kWin>(P, sz, lx + 3, ly + 1, src, gx, gy, z, f, g);
+                }
+                __syncwarp();       // pulls are in registers: the stage of plane z may be refilled
+                if (lane == 0) mbar_arrive(&empty_bar[kz % kStages]);
+                float2 me = make_float2(0.f, 0.f);
+                float T = 0.f;
+                RingStencil rs = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (owner) {
+                    const float2* rm = ring + ((kz - 1) % kRing) * Sh::kRingPlane;
+                    const float2* r0 = ring + (kz % kRing) * Sh::kRingPlane;
+                    const float2* rp = ring + (k % kRing) * Sh::kRingPlane;
+                    me = r0[slot];            // (psi, rho) of the node, from the psi pass
+                    T = tring[(kz % kRing) * Sh::kRingPlane + slot];
+                    rs = ring_stencil(rm, r0, rp, slot, Sh::kRingW);
+                }
+                __syncwarp();       // ring plane z-1 has been read for the last time
+                if (lane == 0) mbar_arrive(&ring_empty[(kz - 1) % kRing]);
+                if (owner) {
+                    const float rho = me.y;
+                    kahan_add(r_sum, r_c, rho);
+                    kahan_add(t_sum, t_c, T);
+                    const float Fmx = me.x * rs.Fx, Fmy = me.x * rs.Fy, Fmz = me.x * rs.Fz;
+                    const float db = rho - rho_ave;
+                    const float Fm2 = Fmx * Fmx + Fmy * Fmy + Fmz * Fmz;
+                    NodeOut o = collide_f(P, f, rho, Fmx + db * P.gx, Fmy + db * P.gy, Fmz + db * P.gz, Fm2, me.x * me.x);
+                    const int d = node_of(P, gx, gy, z);
+                    const float ph = collide_g(P, g, rho, T, o, rs.gx, rs.gy, rs.gz, ph_prev, first);
+                    store_slots<float>(P, dst, sidx(P, gx, gy, z), f, g);   // ghosts: k_ghosts after the step
+                    phis[d] = ph;
+                }
+            }
+            // stage of the item's last plane (psi only); ring planes z1-1 and z1
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&empty_bar[(k - 1) % kStages]);
+                mbar_arrive(&ring_empty[(k - 2) % kRing]);
+                mbar_arrive(&ring_empty[(k - 1) % kRing]);
+            }
+            block_partial<kCol>((double)r_sum - (double)r_c, (double)t_sum - (double)t_c, partial, item, ct, 1,
+                                red_a, red_b);
+        }
+        finish_sums<kCol>(partial, n_items, counter, sums_next, ct, 1, red_a, red_b, &is_last);
+    }
+    __syncthreads();
+}
+
+// Ghost refresh after a TMA step: every ghost cell (columns -2, -1, nx, nx+1 and rows -2, -1,
+// ny, ny+1 of each plane) receives the 26 stored populations of its periodic image.
+__global__ void __launch_bounds__(256) k_ghosts(DevParams P, float* __restrict__ pops) {
+    const int per_plane = 4 * (P.ny + 4) + 4 * P.nx;
+    const int c = blockIdx.x * 256 + threadIdx.x;
+    const int z = blockIdx.y;
+    if (c >= per_plane) return;
+    int gx, gy;
+    if (c < 4 * (P.ny + 4)) {           // ghost columns over all rows, ghost rows included
+        const int k = c / (P.ny + 4);
+        gx = k == 0 ? -2 : k == 1 ? -1 : k == 2 ? P.nx : P.nx + 1;
+        gy = c % (P.ny + 4) - 2;
+    } else {                            // ghost rows over the real columns
+        const int c2 = c - 4 * (P.ny + 4);
+        const int k = c2 / P.nx;
+        gy = k == 0 ? -2 : k == 1 ? -1 : k == 2 ? P.ny : P.ny + 1;
+        gx = c2 % P.nx;
+    }
+    const int ix = ((gx % P.nx) + P.nx) % P.nx, iy = ((gy % P.ny) + P.ny) % P.ny;
+    const int from = sidx(P, ix, iy, z), to = sidx(P, gx, gy, z);
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                ta += __shfl_down_sync(0xffffffffu, ta, o);
-                tb += __shfl_down_sync(0xffffffffu, tb, o);
-            }
-            __syncthreads();
-            if ((tid & 31) == 0) { sa[tid >> 5] = ta; sb[tid >> 5] = tb; }
-            __syncthreads();
-            if (tid == 0) {
-                double ra = 0.0, rb = 0.0;
-                for (int w = 0; w < Sh::kThreads / 32; ++w) { ra += sa[w]; rb += sb[w]; }
-                sums_next[0] = ra;
-                sums_next[1] = rb;
-                *counter = 0u;
+    for (int a = 0; a < kSlots; ++a) pops[(size_t)a * P.Ns + to] = pops[(size_t)a * P.Ns + from];
+}
+
+using Shape0 = TmaShape<32, 8>;
+using Shape1 = TmaShape<40, 7>;
+
+// Plan of the TMA kernel for a lattice: tile shape and z-chunking that minimise the planes x
+// tile nodes of the busiest CTA (items are spread round robin over the persistent CTAs; when
+// every CTA holds one item, neighbouring tiles advance through z together and share their halo
+// reads in L2).
+void tma_plan(const DevParams& P, int ctas, int* shape, int* zchunk, int* items) {
+    const int shapes[2][2] = {{32, 8}, {40, 7}};
+    long long best = -1;
+    for (int sh = 0; sh < 2; ++sh) {
+        const int tx = shapes[sh][0], ty = shapes[sh][1];
+        const int tiles = ((P.nx + tx - 1) / tx) * ((P.ny + ty - 1) / ty);
+        for (int nch = 1; nch <= P.nz; ++nch) {
+            int zc = (P.nz + nch - 1) / nch;
+            int nchunks = (P.nz + zc - 1) / zc;
+            if (zc < 8 && nch > 1) break;
+            long long n = (long long)tiles * nchunks;
+            long long per_cta = (n + ctas - 1) / ctas;
+            long long cost = per_cta * (long long)tx * ty * (zc + 2);
+            if (best < 0 || cost < best) {
+                best = cost;
+                *shape = sh;
+                *zchunk = zc;
+                *items = (int)n;
             }
         }
     }
 }
 
-constexpr int kTY = 8;
-
-int zchunk_for(const DevParams& P, int tiles) {
-    // enough CTAs for about four waves of two CTAs per SM on 152 SMs, chunks of >= 8 planes
-    const int target = 152 * 2 * 4;
+int zchunk_generic(const DevParams& P, int tiles) {
+    const int target = 152 * 2 * 4;   // about four waves of two CTAs per SM
     int chunks = (target + tiles - 1) / tiles;
     int zc = (P.nz + chunks - 1) / chunks;
     if (zc < 8) zc = 8;
@@ -238,30 +660,62 @@ int zchunk_for(const DevParams& P, int tiles) {
 }  // namespace
 
 bool fused_supported(const DevParams& P) {
-    // the grid's CTA count must fit the partial-sum buffer of the reductions
     int tiles = ((P.nx + TX - 1) / TX) * ((P.ny + kTY - 1) / kTY);
-    int zc = zchunk_for(P, tiles);
+    int zc = zchunk_generic(P, tiles);
     long long blocks = (long long)tiles * ((P.nz + zc - 1) / zc);
     return blocks <= (long long)max_partials(P);
 }
 
+bool tma_eligible(const DevParams& P, int precision) {
+    return precision == 0 && P.nx >= 4 && P.ny >= 4 && f_wraps(P.bc[0]) && f_wraps(P.bc[1]) && f_wraps(P.bc[2]) &&
+           f_wraps(P.bc[3]) && !P.flow_off && !P.thermal_off;
+}
+
+size_t tma_smem_bytes(int shape) { return shape == 0 ? Shape0::kSmem : Shape1::kSmem; }
+
+void tma_plan_for(const DevParams& P, int ctas, int* shape, int* zchunk, int* items) {
+    tma_plan(P, ctas, shape, zchunk, items);
+}
+
+int tma_box_w(int shape) { return shape == 0 ? Shape0::kWinW : Shape1::kWinW; }
+int tma_box_h(int shape) { return shape == 0 ? Shape0::kWinH : Shape1::kWinH; }
+
 cudaError_t launch_fused(const DevParams& P, int precision, const StateBufs& B, const double* sums_cur,
-                         double* sums_next, int first, cudaStream_t s) {
+                         double* sums_next, int first, cudaStream_t s, const TmaMaps* maps) {
     using Sh = FusedShape<kTY>;
-    int tiles_x = (P.nx + TX - 1) / TX, tiles_y = (P.ny + kTY - 1) / kTY;
-    int zc = zchunk_for(P, tiles_x * tiles_y);
+    const int tiles_x = (P.nx + TX - 1) / TX, tiles_y = (P.ny + kTY - 1) / kTY;
+    cudaError_t e = cudaSuccess;
+    if (maps && maps->ok && B.pull_f && B.pull_g && tma_eligible(P, precision)) {
+        const int tx = maps->shape == 0 ? 32 : 40, ty = maps->shape == 0 ? 8 : 7;
+        const int txs = (P.nx + tx - 1) / tx, tys = (P.ny + ty - 1) / ty;
+        const int ctas = maps->sms < maps->items ? maps->sms : maps->items;
+#define GB300_TMA(SH, TXV, TYV)                                                                                \
+        {                                                                                                      \
+            e = cudaFuncSetAttribute(k_fused_tma<TXV, TYV>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+                                     (int)SH::kSmem);                                                          \
+            if (e != cudaSuccess) return e;                                                                    \
+            k_fused_tma<TXV, TYV><<<ctas, SH::kThreads, SH::kSmem, s>>>(                                       \
+                maps->m14[B.src_index], maps->m6[B.src_index], P, (const float*)B.src, (float*)B.dst, sums_cur, \
+                B.partial, B.counter, sums_next, B.phis, B.flag, first, maps->zchunk, txs, tys, maps->items);   \
+        }
+        if (maps->shape == 0) GB300_TMA(Shape0, 32, 8) else GB300_TMA(Shape1, 40, 7)
+#undef GB300_TMA
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const int per_plane = 4 * (P.ny + 4) + 4 * P.nx;
+        k_ghosts<<<dim3((per_plane + 255) / 256, P.nz), 256, 0, s>>>(P, (float*)B.dst);
+        return cudaGetLastError();
+    }
+    const int zc = zchunk_generic(P, tiles_x * tiles_y);
     dim3 grid(tiles_x, tiles_y, (P.nz + zc - 1) / zc);
     dim3 block(Sh::kThreads);
-    cudaError_t e = cudaSuccess;
-#define GB300_FUSED(S)                                                                                     \
-    {                                                                                                     \
-        e = cudaFuncSetAttribute(k_fused<S, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,            \
-                                 (int)Sh::kSmemBytes);                                                    \
-        if (e != cudaSuccess) return e;                                                                   \
-        k_fused<S, kTY><<<grid, block, Sh::kSmemBytes, s>>>(P, (const S*)B.fsrc, (const S*)B.gsrc,       \
-                                                            (S*)B.fdst, (S*)B.gdst, B.pull_f, B.pull_g,   \
-                                                            sums_cur, B.partial, B.counter, sums_next,    \
-                                                            B.phis, B.flag, first, zc);                   \
+#define GB300_FUSED(S)                                                                                          \
+    {                                                                                                          \
+        e = cudaFuncSetAttribute(k_fused<S, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::kSmemBytes); \
+        if (e != cudaSuccess) return e;                                                                        \
+        k_fused<S, kTY><<<grid, block, Sh::kSmemBytes, s>>>(P, (const S*)B.src, (S*)B.dst, B.pull_f, B.pull_g,  \
+                                                            sums_cur, B.partial, B.counter, sums_next, B.phis,  \
+                                                            B.flag, first, zc);                                \
     }
     switch (precision) {
     case 0: GB300_FUSED(float) break;

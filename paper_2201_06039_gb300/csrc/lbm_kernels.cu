@@ -60,46 +60,39 @@ __device__ void grid_sum2(double a, double b, double2* partial, unsigned* counte
 
 // ---------------------------------------------------------------- init
 template <typename S>
-__global__ void __launch_bounds__(TPB) k_init(DevParams P, S* __restrict__ f, S* __restrict__ g,
-                                             const float* __restrict__ rho, const float* __restrict__ T,
-                                             const float* __restrict__ u) {
+__global__ void __launch_bounds__(TPB) k_init(DevParams P, S* __restrict__ pops, const float* __restrict__ rho,
+                                             const float* __restrict__ T, const float* __restrict__ u) {
     int x = blockIdx.x * TPB_X + threadIdx.x, y = blockIdx.y * TPB_Y + threadIdx.y, z = blockIdx.z;
     if (x >= P.nx || y >= P.ny) return;
-    int i = node_of(P, x, y, z);
-    float r = rho[i], t = T[i];
+    int d = node_of(P, x, y, z);
+    float r = rho[d], t = T[d];
     float ux = 0.f, uy = 0.f, uz = 0.f;
-    if (u) { ux = u[i]; uy = u[P.N + i]; uz = u[2 * P.N + i]; }
-    float fe[19];
+    if (u) { ux = u[d]; uy = u[P.N + d]; uz = u[2 * P.N + d]; }
+    float fe[19], ge[7];
     feq(r, ux, uy, uz, fe);
+    ge[0] = P.w0 * t;
 #pragma unroll
-    for (int a = 0; a < 19; ++a) Codec<S>::store(f + (size_t)a * P.N + i, fe[a], P.shift_f[a]);
-    Codec<S>::store(g + i, P.w0 * t, P.shift_g[0]);
-#pragma unroll
-    for (int a = 1; a < 7; ++a) Codec<S>::store(g + (size_t)a * P.N + i, P.w1 * t, P.shift_g[a]);
+    for (int a = 1; a < 7; ++a) ge[a] = P.w1 * t;
+    store_node<S>(P, pops, sidx(P, x, y, z), x, y, z, fe, ge);
 }
 
 // ---------------------------------------------------------------- psi / EOS pass (S1-S2)
 template <typename S>
-__global__ void __launch_bounds__(TPB) k_psi(DevParams P, const S* __restrict__ fs, const S* __restrict__ gs,
-                                            int pull_f, int pull_g, float2* __restrict__ psirho,
+__global__ void __launch_bounds__(TPB) k_psi(DevParams P, const S* __restrict__ fs, int pull_f, int pull_g, float2* __restrict__ psirho,
                                             double2* partial, unsigned* counter, double* sums, int* flag) {
     int x = blockIdx.x * TPB_X + threadIdx.x, y = blockIdx.y * TPB_Y + threadIdx.y, z = blockIdx.z;
     double ra = 0.0, ta = 0.0;
     int bad = 0;
     if (x < P.nx && y < P.ny) {
-        int i = node_of(P, x, y, z);
+        int i = sidx(P, x, y, z);
         Nbr n = make_nbr(P, x, y, z);
         float f[19], g[7];
         load_f<S>(P, fs, pull_f, i, x, y, z, n, f);
-        load_g<S>(P, gs, pull_g, i, x, y, z, n, g);
-        float rho = 0.f, T = 0.f;
-#pragma unroll
-        for (int a = 0; a < 19; ++a) rho += f[a];
-#pragma unroll
-        for (int a = 0; a < 7; ++a) T += g[a];
+        load_g<S>(P, fs, pull_g, i, x, y, z, n, g);
+        float rho = sum19(f), T = sum7(g);
         float psi2 = psi_squared(P, rho, T);
         bad = !(psi2 > 0.f) || !isfinite(rho) || !isfinite(T);
-        psirho[i] = make_float2(sqrtf(psi2), rho);
+        psirho[node_of(P, x, y, z)] = make_float2(sqrtf(psi2), rho);
         ra = rho;
         ta = T;
     }
@@ -142,67 +135,61 @@ __device__ __forceinline__ Stencil stencil(const DevParams& P, const float2* __r
 
 // ---------------------------------------------------------------- stream-collide pass (S3-S12)
 template <typename S>
-__global__ void __launch_bounds__(TPB) k_collide(DevParams P, const S* __restrict__ fs, const S* __restrict__ gs,
-                                                S* __restrict__ fd, S* __restrict__ gd, int pull_f, int pull_g,
+__global__ void __launch_bounds__(TPB) k_collide(DevParams P, const S* __restrict__ fs, S* __restrict__ fd,
+                                                int pull_f, int pull_g,
                                                 const float2* __restrict__ psirho, const double* __restrict__ sums_cur,
                                                 float* __restrict__ phis, int first) {
     int x = blockIdx.x * TPB_X + threadIdx.x, y = blockIdx.y * TPB_Y + threadIdx.y, z = blockIdx.z;
     if (x >= P.nx || y >= P.ny) return;
-    int i = node_of(P, x, y, z);
+    int i = sidx(P, x, y, z), d = node_of(P, x, y, z);
     Nbr n = make_nbr(P, x, y, z);
     float f[19], g[7];
     load_f<S>(P, fs, pull_f, i, x, y, z, n, f);
-    load_g<S>(P, gs, pull_g, i, x, y, z, n, g);
-    float rho = 0.f, T = 0.f;
-#pragma unroll
-    for (int a = 0; a < 19; ++a) rho += f[a];
-#pragma unroll
-    for (int a = 0; a < 7; ++a) T += g[a];
-    float2 me = __ldg(psirho + i);
+    load_g<S>(P, fs, pull_g, i, x, y, z, n, g);
+    float rho = sum19(f), T = sum7(g);
+    float2 me = __ldg(psirho + d);
     Stencil st = stencil(P, psirho, x, y, z, n);
     float Fmx = me.x * st.Fx, Fmy = me.x * st.Fy, Fmz = me.x * st.Fz;
-    float rho_ave = (float)(sums_cur[0] / (double)P.N);
+    float rho_ave = (float)(sums_cur[0] * P.inv_N);
     float db = rho - rho_ave;
     float Fx = Fmx + db * P.gx, Fy = Fmy + db * P.gy, Fz = Fmz + db * P.gz;
     float Fm2 = Fmx * Fmx + Fmy * Fmy + Fmz * Fmz;
-    NodeOut o = collide_f(P, f, Fx, Fy, Fz, Fm2, me.x * me.x);
-    if (!P.flow_off) {
+    NodeOut o = collide_f(P, f, rho, Fx, Fy, Fz, Fm2, me.x * me.x);
+    float ph = collide_g(P, g, rho, T, o, st.gx, st.gy, st.gz, phis[d], first);
+    // frozen fields keep their stored values (no streaming, no collision)
+    if (P.flow_off) {
 #pragma unroll
-        for (int a = 0; a < 19; ++a) Codec<S>::store(fd + (size_t)a * P.N + i, f[a], P.shift_f[a]);
+        for (int a = 0; a < 19; ++a) f[a] = Codec<S>::load(fs + (size_t)fslot(a) * P.Ns + i, P.shift_f[a]);
     }
-    float ph = collide_g(P, g, rho, T, o, st.gx, st.gy, st.gz, phis[i], first);
-    if (!P.thermal_off) {
+    if (P.thermal_off) {
 #pragma unroll
-        for (int a = 0; a < 7; ++a) Codec<S>::store(gd + (size_t)a * P.N + i, g[a], P.shift_g[a]);
+        for (int a = 0; a < 7; ++a) g[a] = Codec<S>::load(fs + (size_t)gslot(a) * P.Ns + i, P.shift_g[a]);
     }
-    phis[i] = ph;
+    store_node<S>(P, fd, i, x, y, z, f, g);
+    phis[d] = ph;
 }
 
 // ---------------------------------------------------------------- moments (lbm_get_moments)
 template <typename S>
-__global__ void __launch_bounds__(TPB) k_moments(DevParams P, const S* __restrict__ fs, const S* __restrict__ gs,
-                                                int pull_f, int pull_g, const float2* __restrict__ psirho,
+__global__ void __launch_bounds__(TPB) k_moments(DevParams P, const S* __restrict__ fs, int pull_f, int pull_g, const float2* __restrict__ psirho,
                                                 const double* __restrict__ sums_cur, float* __restrict__ orho,
                                                 float* __restrict__ oux, float* __restrict__ ouy,
                                                 float* __restrict__ ouz, float* __restrict__ oT) {
     int x = blockIdx.x * TPB_X + threadIdx.x, y = blockIdx.y * TPB_Y + threadIdx.y, z = blockIdx.z;
     if (x >= P.nx || y >= P.ny) return;
-    int i = node_of(P, x, y, z);
+    int i = sidx(P, x, y, z);
     Nbr n = make_nbr(P, x, y, z);
     float f[19], g[7];
     load_f<S>(P, fs, pull_f, i, x, y, z, n, f);
-    load_g<S>(P, gs, pull_g, i, x, y, z, n, g);
-    float rho = 0.f, T = 0.f;
-#pragma unroll
-    for (int a = 0; a < 19; ++a) rho += f[a];
-#pragma unroll
-    for (int a = 0; a < 7; ++a) T += g[a];
+    load_g<S>(P, fs, pull_g, i, x, y, z, n, g);
+    float rho = sum19(f), T = sum7(g);
+    i = node_of(P, x, y, z);
     float jx = (f[1] - f[2]) + (f[7] - f[8]) + (f[9] - f[10]) + (f[11] - f[12]) + (f[13] - f[14]);
     float jy = (f[3] - f[4]) + (f[7] - f[8]) - (f[9] - f[10]) + (f[15] - f[16]) + (f[17] - f[18]);
     float jz = (f[5] - f[6]) + (f[11] - f[12]) - (f[13] - f[14]) + (f[15] - f[16]) - (f[17] - f[18]);
     float2 me = __ldg(psirho + i);
     Stencil st = stencil(P, psirho, x, y, z, n);
-    float rho_ave = (float)(sums_cur[0] / (double)P.N);
+    float rho_ave = (float)(sums_cur[0] * P.inv_N);
     float db = rho - rho_ave;
     float Fx = me.x * st.Fx + db * P.gx, Fy = me.x * st.Fy + db * P.gy, Fz = me.x * st.Fz + db * P.gz;
     float inv = 1.f / rho;
@@ -227,7 +214,7 @@ static dim3 grid_of(const DevParams& P) {
     return dim3((P.nx + TPB_X - 1) / TPB_X, (P.ny + TPB_Y - 1) / TPB_Y, P.nz);
 }
 
-int reduce_blocks_psi(const DevParams& P) {
+int reduce_blocks_psi(const DevParams& P) {   // also bounds the fused kernels' blocks / items
     dim3 g = grid_of(P);
     return (int)(g.x * g.y * g.z);
 }
@@ -245,36 +232,33 @@ int max_partials(const DevParams& P) {
     default: return cudaErrorInvalidValue;                                   \
     }
 
-cudaError_t launch_init(const DevParams& P, int precision, void* f, void* g, const float* rho,
-                        const float* T, const float* u, cudaStream_t s) {
+cudaError_t launch_init(const DevParams& P, int precision, void* pops, const float* rho, const float* T,
+                        const float* u, cudaStream_t s) {
     dim3 blk(TPB_X, TPB_Y);
-    GB300_DISPATCH(precision, (k_init<S><<<grid_of(P), blk, 0, s>>>(P, (S*)f, (S*)g, rho, T, u)));
+    GB300_DISPATCH(precision, (k_init<S><<<grid_of(P), blk, 0, s>>>(P, (S*)pops, rho, T, u)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_psi(const DevParams& P, int precision, const StateBufs& B, double* sums, cudaStream_t s) {
     dim3 blk(TPB_X, TPB_Y);
-    GB300_DISPATCH(precision, (k_psi<S><<<grid_of(P), blk, 0, s>>>(P, (const S*)B.fsrc, (const S*)B.gsrc, B.pull_f,
-                                                                    B.pull_g, B.psirho, B.partial, B.counter, sums,
-                                                                    B.flag)));
+    GB300_DISPATCH(precision, (k_psi<S><<<grid_of(P), blk, 0, s>>>(P, (const S*)B.src, B.pull_f, B.pull_g, B.psirho,
+                                                                    B.partial, B.counter, sums, B.flag)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_collide(const DevParams& P, int precision, const StateBufs& B, const double* sums_cur,
                            int first, cudaStream_t s) {
     dim3 blk(TPB_X, TPB_Y);
-    GB300_DISPATCH(precision, (k_collide<S><<<grid_of(P), blk, 0, s>>>(P, (const S*)B.fsrc, (const S*)B.gsrc,
-                                                                        (S*)B.fdst, (S*)B.gdst, B.pull_f, B.pull_g,
-                                                                        B.psirho, sums_cur, B.phis, first)));
+    GB300_DISPATCH(precision, (k_collide<S><<<grid_of(P), blk, 0, s>>>(P, (const S*)B.src, (S*)B.dst, B.pull_f,
+                                                                        B.pull_g, B.psirho, sums_cur, B.phis, first)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_moments(const DevParams& P, int precision, const StateBufs& B, const double* sums_cur,
                            float* rho, float* ux, float* uy, float* uz, float* T, cudaStream_t s) {
     dim3 blk(TPB_X, TPB_Y);
-    GB300_DISPATCH(precision, (k_moments<S><<<grid_of(P), blk, 0, s>>>(P, (const S*)B.fsrc, (const S*)B.gsrc,
-                                                                        B.pull_f, B.pull_g, B.psirho, sums_cur, rho,
-                                                                        ux, uy, uz, T)));
+    GB300_DISPATCH(precision, (k_moments<S><<<grid_of(P), blk, 0, s>>>(P, (const S*)B.src, B.pull_f, B.pull_g,
+                                                                        B.psirho, sums_cur, rho, ux, uy, uz, T)));
     return cudaGetLastError();
 }
 

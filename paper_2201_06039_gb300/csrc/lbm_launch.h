@@ -1,6 +1,7 @@
 // Host-side launchers of the lattice kernels (internal to the library; the public
 // C-ABI is include/lbm.h).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include "lbm_device.cuh"
 
@@ -8,10 +9,9 @@ namespace gb300lbm {
 
 // Device buffers of one lattice state (populations are structure-of-arrays).
 struct StateBufs {
-    const void* fsrc;      // populations read this step
-    const void* gsrc;
-    void* fdst;            // populations written this step
-    void* gdst;
+    const void* src;       // populations read this step (26 slots: f and g, see fslot / gslot)
+    void* dst;             // populations written this step
+    int src_index;         // which of the two population buffers src is (tensor maps are per buffer)
     int pull_f, pull_g;    // 0: state is post-streaming at the node (right after init)
     float2* psirho;        // per node (psi, rho)
     float* phis;           // phi_s history, read and rewritten in place
@@ -22,8 +22,8 @@ struct StateBufs {
 
 int reduce_blocks_psi(const DevParams& P);
 
-cudaError_t launch_init(const DevParams& P, int precision, void* f, void* g, const float* rho,
-                        const float* T, const float* u, cudaStream_t s);
+cudaError_t launch_init(const DevParams& P, int precision, void* pops, const float* rho, const float* T,
+                        const float* u, cudaStream_t s);
 
 // psi/EOS pass: rho, T, psi of every node; optional FP64 sums (rho, T) into sums[0..1].
 cudaError_t launch_psi(const DevParams& P, int precision, const StateBufs& B, double* sums,
@@ -33,10 +33,26 @@ cudaError_t launch_psi(const DevParams& P, int precision, const StateBufs& B, do
 cudaError_t launch_collide(const DevParams& P, int precision, const StateBufs& B,
                            const double* sums_cur, int first, cudaStream_t s);
 
-// fused z-marching variant (psi of the tile halo recomputed from the populations).
-cudaError_t launch_fused(const DevParams& P, int precision, const StateBufs& B,
-                         const double* sums_cur, double* sums_next, int first, cudaStream_t s);
+// Tensor maps of the two population buffers for the TMA variant (4D: x, y, z, slot; boxes of
+// 40 x 12 x 1 x 14 and 40 x 12 x 1 x 6 floats), and the number of SMs for its persistent grid.
+struct TmaMaps {
+    CUtensorMap m14[2], m6[2];
+    bool ok;
+    int sms;
+    int shape, zchunk, items;   // plan of tma_plan_for
+};
+
+// fused z-marching variant (psi of the tile halo recomputed from the populations); uses the
+// TMA kernel when maps are given and the lattice / state qualify (see tma_eligible).
+cudaError_t launch_fused(const DevParams& P, int precision, const StateBufs& B, const double* sums_cur,
+                         double* sums_next, int first, cudaStream_t s, const TmaMaps* maps);
 bool fused_supported(const DevParams& P);
+bool tma_eligible(const DevParams& P, int precision);
+// tile shape 0: 32 x 8, 1: 40 x 7 (window boxes tma_box_w x tma_box_h per population slot)
+void tma_plan_for(const DevParams& P, int ctas, int* shape, int* zchunk, int* items);
+size_t tma_smem_bytes(int shape);
+int tma_box_w(int shape);
+int tma_box_h(int shape);
 
 // macroscopic moments (needs the psi pass on the same state first).
 cudaError_t launch_moments(const DevParams& P, int precision, const StateBufs& B,

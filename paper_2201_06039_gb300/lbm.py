@@ -19,7 +19,7 @@ from . import build as _build
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ESTATE, LBM_ENONFINITE, LBM_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 LBM_BC_PERIODIC, LBM_BC_WALL, LBM_BC_OUTFLOW, LBM_BC_THERMAL_ONLY = 0, 1, 2, 3
 LBM_FP32, LBM_BF16_SHIFTED, LBM_FP16_SHIFTED = 0, 1, 2
-LBM_KERNEL_AUTO, LBM_KERNEL_TWO_PASS, LBM_KERNEL_FUSED = 0, 1, 2
+LBM_KERNEL_AUTO, LBM_KERNEL_TWO_PASS, LBM_KERNEL_FUSED, LBM_KERNEL_FUSED_TMA = 0, 1, 2, 3
 
 
 class LbmParams(C.Structure):
@@ -36,7 +36,7 @@ class LbmParams(C.Structure):
         ("g", C.c_double * 3),
         ("flow_off", C.c_int), ("thermal_off", C.c_int),
         ("precision", C.c_int), ("rho_ref", C.c_double), ("T_ref", C.c_double),
-        ("kernel", C.c_int), ("use_graph", C.c_int), ("check_nonfinite", C.c_int),
+        ("kernel", C.c_int), ("use_graph", C.c_int), ("use_tma", C.c_int), ("check_nonfinite", C.c_int),
         ("cuda_stream", C.c_void_p),
         ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
     ]

@@ -12,12 +12,15 @@ from tests._parity import BAR, bars, fp32_floor, inputs, rel_errors, run_gpu, ru
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = [1, 2]   # LBM_KERNEL_TWO_PASS, LBM_KERNEL_FUSED
+# kernel variants: psi/EOS + stream-collide, generic fused, TMA-fed fused (falls back to the
+# generic fused kernel on lattices it does not cover)
+VARIANTS = ["two_pass", "fused", "fused_tma"]
+OVERRIDES = {"two_pass": dict(kernel=1), "fused": dict(kernel=2, use_tma=0), "fused_tma": dict(kernel=2, use_tma=1)}
 
 
 def _variant_ok(v, setup):
     from paper_2201_06039_gb300 import lbm
-    p = lbm.params_from_setup(setup, kernel=v)
+    p = lbm.params_from_setup(setup, **OVERRIDES[v])
     try:
         lat = lbm.Lattice(p)
         lat.close()
@@ -33,7 +36,7 @@ def _compare(case, steps, variant, fixed_bar=False, u=None):
     if not _variant_ok(variant, s):
         pytest.skip("variant does not support this lattice")
     orc = run_oracle(s, rho, T, u, steps)
-    gpu, _ = run_gpu(s, rho, T, u, steps, kernel=variant)
+    gpu, _ = run_gpu(s, rho, T, u, steps, **OVERRIDES[variant])
     err = rel_errors(gpu, orc)
     if fixed_bar:
         floor, bar = None, {k: BAR for k in err}
@@ -102,12 +105,33 @@ def test_parity_degenerate_and_tiny_lattices(shape, variant):
     if not _variant_ok(variant, s):
         pytest.skip("variant does not support this lattice")
     orc = run_oracle(s, rho, T, None, 50)
-    gpu, _ = run_gpu(s, rho, T, None, 50, kernel=variant)
+    gpu, _ = run_gpu(s, rho, T, None, 50, **OVERRIDES[variant])
     err = rel_errors(gpu, orc)
     bar = bars(fp32_floor(s, rho, T, None, 50, ref=orc))
     print(shape, "gpu", err, "bar", bar)
     for k, v in err.items():
         assert v <= bar[k], (k, v, err, bar)
+
+
+def test_tma_kernel_selected_for_periodic_fp32_lattices():
+    from paper_2201_06039_gb300 import lbm
+    lat = lbm.Lattice(lbm.params_from_setup(W.pool_boiling(64, 48, 40, height=16.0, hot_sigma=4.0)["setup"]))
+    assert lat.kernel == lbm.LBM_KERNEL_FUSED_TMA
+    lat.close()
+    lat = lbm.Lattice(lbm.params_from_setup(W.pool_boiling(64, 48, 40)["setup"], use_tma=0))
+    assert lat.kernel == lbm.LBM_KERNEL_FUSED
+    lat.close()
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_variants_bit_identical(variant):
+    """Every kernel variant computes the same FP32 operations in the same order."""
+    case = W.pool_boiling(72, 40, 30, height=12.0, hot_sigma=4.0)
+    rho, T, u = inputs(case)
+    ref, _ = run_gpu(case["setup"], rho, T, u, 23, **OVERRIDES["two_pass"])
+    got, _ = run_gpu(case["setup"], rho, T, u, 23, **OVERRIDES[variant])
+    for k in ref:
+        assert np.array_equal(ref[k], got[k]), k
 
 
 def test_graph_replay_is_bit_identical_to_plain_launches():
