@@ -246,6 +246,10 @@ int enqueue_step(lbm_ctx* c, double* kernel_ms = nullptr, int* launches = nullpt
     // both fields are written every step (frozen ones copied through unchanged, so they stay
     // in their un-streamed "fresh" form)
     c->cur ^= 1;
+    if (c->maps.ok) {   // the TMA path reads ghost cells: refresh them in the state just written
+        e = launch_ghosts(c->dp, B.dst, c->launch);
+        if (e != cudaSuccess) return fail(LBM_ECUDA, "ghost refresh launch: %s", cudaGetErrorString(e));
+    }
     if (!c->p.flow_off) c->fresh_f = false;
     if (!c->p.thermal_off) c->fresh_g = false;
     c->slot ^= 1;
@@ -464,6 +468,7 @@ int lbm_init_fields(lbm_ctx* c, const float* rho, const float* T, const float* u
     c->cur = 0;
     c->slot = 0;
     CK(launch_init(c->dp, c->p.precision, c->pbuf(0), drho, dT, du, c->stream));
+    if (c->maps.ok) CK(launch_ghosts(c->dp, c->pbuf(0), c->stream));
     StateBufs B = c->bufs();
     CK(launch_sum_field(drho, c->dp.N, B.partial, B.counter, c->sums(0), c->stream));
     CK(cudaMemsetAsync(c->base + c->L.flag, 0, sizeof(int), c->stream));

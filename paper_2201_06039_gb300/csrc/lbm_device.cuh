@@ -3,7 +3,8 @@
 // Eq. 9, local div u (Eq. 48) and grad T (Eq. 45), phase-change source (Eq. 18, 23) and
 // the D3Q7 MRT temperature collision (Eqs. 38-43).
 //
-// Everything here is FP32 arithmetic.  The D3Q19 transform uses the raw polynomial
+// Everything here is FP32 arithmetic; reciprocals and square roots use the hardware approximations
+// (__fdividef, rsqrtf: within 2 ulp), shared by every kernel variant.  The D3Q19 transform uses the raw polynomial
 // moments of Eq. 5's order (1, e, |e|^2, 2ex^2-ey^2-ez^2, ey^2-ez^2, exey, exez, eyez,
 // ex^2ey, exey^2, ex^2ez, exez^2, ey^2ez, eyez^2, ex^2ey^2, ex^2ez^2, ey^2ez^2) and its
 // closed-form inverse, unrolled by hand (no 19x19 matrix product).
@@ -272,33 +273,12 @@ __device__ __forceinline__ void store_slots(const DevParams& P, S* __restrict__ 
 #undef GB300_ST
 }
 
-// ghost images of coordinate c on an n-periodic axis: columns / rows -2, -1, n, n+1
-__device__ __forceinline__ bool ghost_image(int k, int c, int n, int& gcoord) {
-    const int cand = k == 0 ? -2 : k == 1 ? -1 : k == 2 ? n : n + 1;
-    gcoord = cand;
-    return (((cand % n) + n) % n) == c;
-}
-
-// Store the 26 post-collision populations of node (x, y, z) at storage index i, and into every
-// ghost cell whose periodic image is this node (f-periodic x / y axes only).  The slot order
-// of the store matches fslot / gslot.
+// Store the 26 post-collision populations of node (x, y, z) at storage index i.  Ghost cells are
+// not touched here: the TMA path refreshes them with a separate kernel after every step.
 template <typename S>
-__device__ __forceinline__ void store_node(const DevParams& P, S* __restrict__ dst, int i, int x, int y, int z,
+__device__ __forceinline__ void store_node(const DevParams& P, S* __restrict__ dst, int i, int, int, int,
                                            const float f[19], const float g[7]) {
     store_slots<S>(P, dst, i, f, g);
-    const bool xw = f_wraps(P.bc[0]), yw = f_wraps(P.bc[2]);
-    const bool xe = xw && (x < 2 || x >= P.nx - 2), ye = yw && (y < 2 || y >= P.ny - 2);
-    if (!(xe || ye)) return;
-    for (int kx = -1; kx < 4; ++kx) {          // -1: the node's own column
-        int cx = x;
-        if (kx >= 0 && !(xw && ghost_image(kx, x, P.nx, cx))) continue;
-        for (int ky = -1; ky < 4; ++ky) {
-            int cy = y;
-            if (ky >= 0 && !(yw && ghost_image(ky, y, P.ny, cy))) continue;
-            if (kx < 0 && ky < 0) continue;
-            store_slots<S>(P, dst, sidx(P, cx, cy, z), f, g);
-        }
-    }
 }
 
 // rho = sum f and T = sum g in one fixed pairwise order (every kernel uses these, so all variants
@@ -315,12 +295,14 @@ __device__ __forceinline__ float sum7(const float g[7]) {
 
 // ---------------------------------------------------------------- thermodynamics
 // Peng-Robinson pressure (Eq. 49) and psi^2 = 2 (p_EOS - rho cs^2) / (G c^2) with G = -1 (Eq. 8).
+__device__ __forceinline__ float psi_of(float psi2) { return psi2 * rsqrtf(psi2); }   // sqrt; NaN if <= 0
 __device__ __forceinline__ float psi_squared(const DevParams& P, float rho, float T) {
-    float s = 1.f + P.kappa * (1.f - sqrtf(T * P.inv_Tc));
+    const float tr = T * P.inv_Tc;
+    float s = 1.f + P.kappa * (1.f - tr * rsqrtf(tr));   // sqrt(T / Tc)
     float theta = s * s;
     float brho = P.b * rho;
     float d1 = 1.f - brho, d2 = 1.f + 2.f * brho - brho * brho;
-    float inv = __frcp_rn(d1 * d2);   // one reciprocal for both denominators
+    float inv = __fdividef(1.f, d1 * d2);   // one reciprocal for both denominators
     float p = rho * P.R * T * (d2 * inv) - P.a * theta * rho * rho * (d1 * inv);
     return 2.f * (rho * (1.f / 3.f) - p);
 }
@@ -367,7 +349,7 @@ __device__ __forceinline__ NodeOut collide_f(const DevParams& P, float f[19], fl
     float jx = (f[1] - f[2]) + (f[7] - f[8]) + (f[9] - f[10]) + (f[11] - f[12]) + (f[13] - f[14]);
     float jy = (f[3] - f[4]) + (f[7] - f[8]) - (f[9] - f[10]) + (f[15] - f[16]) + (f[17] - f[18]);
     float jz = (f[5] - f[6]) + (f[11] - f[12]) - (f[13] - f[14]) + (f[15] - f[16]) - (f[17] - f[18]);
-    float inv_rho = __frcp_rn(rho);
+    float inv_rho = __fdividef(1.f, rho);
     float ux = (jx + 0.5f * Fx) * inv_rho, uy = (jy + 0.5f * Fy) * inv_rho, uz = (jz + 0.5f * Fz) * inv_rho;
 
     // raw moments (rows of M)
@@ -399,7 +381,7 @@ __device__ __forceinline__ NodeOut collide_f(const DevParams& P, float f[19], fl
 
     // forcing moments (Eq. 9)
     float Fu_x = Fx * ux, Fu_y = Fy * uy, Fu_z = Fz * uz;
-    float S4 = 2.f * (Fu_x + Fu_y + Fu_z) + P.sigma6 * Fm2 * __frcp_rn(psi2);
+    float S4 = 2.f * (Fu_x + Fu_y + Fu_z) + P.sigma6 * __fdividef(Fm2, psi2);
     float S5 = 2.f * (2.f * Fu_x - Fu_y - Fu_z), S6 = 2.f * (Fu_y - Fu_z);
     float S7 = Fx * uy + Fy * ux, S8 = Fx * uz + Fz * ux, S9 = Fy * uz + Fz * uy;
     float S10 = cs2 * Fy, S11 = cs2 * Fx, S12 = cs2 * Fz, S13 = cs2 * Fx, S14 = cs2 * Fz, S15 = cs2 * Fy;
@@ -479,7 +461,7 @@ __device__ __forceinline__ float collide_g(const DevParams& P, float g[7], float
     const float inv_rho = o.inv_rho;
     float chi = P.lambda_mode ? P.chi_or_lambda * inv_rho * P.inv_cV : P.chi_or_lambda;
     float vsT = chi * P.inv_csT2 + 0.5f;             // chi = (varsigma_T - 1/2) cs_T^2
-    float inv_vsT = __frcp_rn(vsT);
+    float inv_vsT = __fdividef(1.f, vsT);
     float k = -inv_vsT * P.inv_csT2;                 // Eq. 45
     float gTx = k * n1, gTy = k * n2, gTz = k * n3;
     float phis = 0.f;
@@ -487,7 +469,7 @@ __device__ __forceinline__ float collide_g(const DevParams& P, float g[7], float
         phis = (chi * grx * inv_rho - o.ux) * gTx + (chi * gry * inv_rho - o.uy) * gTy +
                (chi * grz * inv_rho - o.uz) * gTz;
         // T/(rho cV) (dp/dT)_rho div u with (dp/dT)_rho ~ rho R / (1 - b rho)
-        phis -= T * P.R_over_cV * __frcp_rn(1.f - P.b * rho) * o.divu;
+        phis -= __fdividef(T * P.R_over_cV, 1.f - P.b * rho) * o.divu;
     }
     float C = first ? phis : phis_prev;
     float qs = 1.5f * phis - 0.5f * C;               // Q_a = w_a (3/2 phi_s(t) - 1/2 phi_s(t-1))

@@ -196,7 +196,7 @@ k_fused(DevParams P, const S* __restrict__ src, S* __restrict__ dst, int pull_f,
         load_g<S>(P, src, pull_g, i, mx, my, mz, n, g);
         float rho = sum19(f), T = sum7(g);
         float psi2 = psi_squared(P, rho, T);
-        ring[((zp + 3) % 3) * Sh::kRingPlane + slot] = make_float2(sqrtf(psi2), rho);
+        ring[((zp + 3) % 3) * Sh::kRingPlane + slot] = make_float2(psi_of(psi2), rho);
         if (owner && in_chunk) {
             float* st = stage + ((zp - z0) & 1) * Sh::kStageFloats + tid;
 #pragma unroll
@@ -311,12 +311,14 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned
 __device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+// the waiting thread may sleep (up to about 1 us per call) until the phase completes, instead of
+// spinning on the issue slots the other warps need
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
     unsigned ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(1000u)
         : "memory");
     return ok != 0;
 }
@@ -503,7 +505,7 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                     stage_pulls<kWinW, kWin>(P, st, lx + 3, ly + 1, src, mx, my, mz, f, g);
                     float rho = sum19(f), T = sum7(g);
                     const float psi2 = psi_squared(P, rho, T);
-                    ring[r * Sh::kRingPlane + ly * Sh::kRingW + lx] = make_float2(sqrtf(psi2), rho);
+                    ring[r * Sh::kRingPlane + ly * Sh::kRingW + lx] = make_float2(psi_of(psi2), rho);
                     tring[r * Sh::kRingPlane + ly * Sh::kRingW + lx] = T;
                     bad |= !(psi2 > 0.f) || !isfinite(rho) || !isfinite(T);
                 }
@@ -594,28 +596,32 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
     __syncthreads();
 }
 
-// Ghost refresh after a TMA step: every ghost cell (columns -2, -1, nx, nx+1 and rows -2, -1,
-// ny, ny+1 of each plane) receives the 26 stored populations of its periodic image.
+// Ghost refresh after a step on the TMA path: every ghost cell (columns -2, -1, nx, nx+1 over all
+// rows including the ghost rows, and rows -2, -1, ny, ny+1 over the real columns) receives the
+// stored populations of its periodic image.  One thread per copied element: column ghosts come in
+// adjacent pairs, row ghosts are coalesced along x.
 __global__ void __launch_bounds__(256) k_ghosts(DevParams P, float* __restrict__ pops) {
-    const int per_plane = 4 * (P.ny + 4) + 4 * P.nx;
-    const int c = blockIdx.x * 256 + threadIdx.x;
+    const int nA = (P.ny + 4) * kSlots * 4, nB = P.nx * kSlots * 4;
+    const int t = blockIdx.x * 256 + threadIdx.x;
     const int z = blockIdx.y;
-    if (c >= per_plane) return;
-    int gx, gy;
-    if (c < 4 * (P.ny + 4)) {           // ghost columns over all rows, ghost rows included
-        const int k = c / (P.ny + 4);
+    int gx, gy, a;
+    if (t < nA) {
+        const int k = t & 3;
+        a = (t >> 2) % kSlots;
+        gy = (t >> 2) / kSlots - 2;
         gx = k == 0 ? -2 : k == 1 ? -1 : k == 2 ? P.nx : P.nx + 1;
-        gy = c % (P.ny + 4) - 2;
-    } else {                            // ghost rows over the real columns
-        const int c2 = c - 4 * (P.ny + 4);
-        const int k = c2 / P.nx;
+    } else if (t < nA + nB) {
+        const int u = t - nA;
+        gx = u % P.nx;
+        a = (u / P.nx) % kSlots;
+        const int k = u / (P.nx * kSlots);
         gy = k == 0 ? -2 : k == 1 ? -1 : k == 2 ? P.ny : P.ny + 1;
-        gx = c2 % P.nx;
+    } else {
+        return;
     }
     const int ix = ((gx % P.nx) + P.nx) % P.nx, iy = ((gy % P.ny) + P.ny) % P.ny;
-    const int from = sidx(P, ix, iy, z), to = sidx(P, gx, gy, z);
-#pragma unroll
-    for (int a = 0; a < kSlots; ++a) pops[(size_t)a * P.Ns + to] = pops[(size_t)a * P.Ns + from];
+    const size_t base = (size_t)a * P.Ns;
+    pops[base + sidx(P, gx, gy, z)] = pops[base + sidx(P, ix, iy, z)];
 }
 
 using Shape0 = TmaShape<32, 8>;
@@ -666,6 +672,12 @@ bool fused_supported(const DevParams& P) {
     return blocks <= (long long)max_partials(P);
 }
 
+cudaError_t launch_ghosts(const DevParams& P, void* pops, cudaStream_t s) {
+    const int per_plane = ((P.ny + 4) + P.nx) * kSlots * 4;
+    k_ghosts<<<dim3((per_plane + 255) / 256, P.nz), 256, 0, s>>>(P, (float*)pops);
+    return cudaGetLastError();
+}
+
 bool tma_eligible(const DevParams& P, int precision) {
     return precision == 0 && P.nx >= 4 && P.ny >= 4 && f_wraps(P.bc[0]) && f_wraps(P.bc[1]) && f_wraps(P.bc[2]) &&
            f_wraps(P.bc[3]) && !P.flow_off && !P.thermal_off;
@@ -700,10 +712,6 @@ cudaError_t launch_fused(const DevParams& P, int precision, const StateBufs& B, 
         }
         if (maps->shape == 0) GB300_TMA(Shape0, 32, 8) else GB300_TMA(Shape1, 40, 7)
 #undef GB300_TMA
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        const int per_plane = 4 * (P.ny + 4) + 4 * P.nx;
-        k_ghosts<<<dim3((per_plane + 255) / 256, P.nz), 256, 0, s>>>(P, (float*)B.dst);
         return cudaGetLastError();
     }
     const int zc = zchunk_generic(P, tiles_x * tiles_y);

@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(TPB) k_psi(DevParams P, const S* __restrict__ 
         float rho = sum19(f), T = sum7(g);
         float psi2 = psi_squared(P, rho, T);
         bad = !(psi2 > 0.f) || !isfinite(rho) || !isfinite(T);
-        psirho[node_of(P, x, y, z)] = make_float2(sqrtf(psi2), rho);
+        psirho[node_of(P, x, y, z)] = make_float2(psi_of(psi2), rho);
         ra = rho;
         ta = T;
     }

@@ -48,6 +48,8 @@ cudaError_t launch_fused(const DevParams& P, int precision, const StateBufs& B, 
                          double* sums_next, int first, cudaStream_t s, const TmaMaps* maps);
 bool fused_supported(const DevParams& P);
 bool tma_eligible(const DevParams& P, int precision);
+// refresh the ghost columns / rows of a population buffer from their periodic images (FP32)
+cudaError_t launch_ghosts(const DevParams& P, void* pops, cudaStream_t s);
 // tile shape 0: 32 x 8, 1: 40 x 7 (window boxes tma_box_w x tma_box_h per population slot)
 void tma_plan_for(const DevParams& P, int ctas, int* shape, int* zchunk, int* items);
 size_t tma_smem_bytes(int shape);
