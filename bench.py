@@ -69,13 +69,16 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+KERNEL_SOURCES = ("lbm_fused.cu", "lbm_device.cuh", "lbm_launch.h")   # sources of the timed kernels
+
+
 def kernel_source_sha():
+    """Hash of the sources the timed kernels are built from (stale ncu counters are not reported)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2201_06039_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as fh:
-                h.update(name.encode() + fh.read())
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
