@@ -147,6 +147,27 @@ int lbm_kernel_in_use(const lbm_ctx* ctx);
  * roofline figures; the event gaps make it slightly slower than lbm_step. */
 int lbm_step_profiled(lbm_ctx* ctx, int n, double kernel_ms[3], int launches[3]);
 
+/* Allocation-free FP64 sum of a device float field (the paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory, e.g. code running under a framework
+ * whose memory pool forbids cudaMalloc outside its allocator, plug-ins with a fixed device-memory
+ * budget, or latency-critical sections that must not allocate).
+ *
+ *   field     device pointer to n float32 values (not modified)
+ *   n         0 <= n <= LBM_NOALLOC_MAX_ELEMENTS
+ *   sum_out   host pointer; receives the sum in FP64 (deterministic: fixed-order block partials
+ *             added in index order)
+ *   stream    cudaStream_t to run on (NULL = legacy default stream); the call synchronises it
+ *
+ * The working memory (1024 block partials, a ticket and the result, about 16 KB) is one
+ * file-scope device array of the library, present on every GPU that loads the library until the
+ * process exits; nothing is allocated per call.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress), so make that first call before any stream
+ * capture.  Every call shares the array: calls that overlap on the GPU (other streams, other
+ * host threads) race and must be serialised by the caller.
+ * Errors: LBM_EINVAL (NULL pointers, n out of range; message via lbm_last_error), LBM_ECUDA. */
+#define LBM_NOALLOC_MAX_ELEMENTS (1LL << 31)
+int lbm_field_sum_noalloc(const float* field, long long n, double* sum_out, void* stream);
+
 /* Release everything the context owns.  NULL is ignored. */
 void lbm_destroy(lbm_ctx* ctx);
 

@@ -580,4 +580,9 @@ const char* lbm_status_str(int s) {
 
 const char* lbm_last_error(void) { return g_err; }
 
+// error message hook for the library's other translation units (not exported)
+__attribute__((visibility("hidden"))) void gb300lbm_set_error(const char* msg) {
+    snprintf(g_err, sizeof(g_err), "%s", msg);
+}
+
 }  // extern "C"

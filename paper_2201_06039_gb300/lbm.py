@@ -17,6 +17,7 @@ import numpy as np
 from . import build as _build
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ESTATE, LBM_ENONFINITE, LBM_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+LBM_NOALLOC_MAX_ELEMENTS = 1 << 31
 LBM_BC_PERIODIC, LBM_BC_WALL, LBM_BC_OUTFLOW, LBM_BC_THERMAL_ONLY = 0, 1, 2, 3
 LBM_FP32, LBM_BF16_SHIFTED, LBM_FP16_SHIFTED = 0, 1, 2
 LBM_KERNEL_AUTO, LBM_KERNEL_TWO_PASS, LBM_KERNEL_FUSED, LBM_KERNEL_FUSED_TMA = 0, 1, 2, 3
@@ -46,7 +47,7 @@ class LbmParams(C.Structure):
 EXPORTS = ["lbm_params_default", "lbm_eos_critical", "lbm_workspace_bytes", "lbm_create",
            "lbm_init_fields", "lbm_step", "lbm_get_moments", "lbm_get_totals", "lbm_steps_done",
            "lbm_kernel_in_use",
-           "lbm_step_profiled", "lbm_destroy", "lbm_status_str", "lbm_last_error"]
+           "lbm_step_profiled", "lbm_destroy", "lbm_status_str", "lbm_last_error", "lbm_field_sum_noalloc"]
 
 _lib = None
 
@@ -91,6 +92,7 @@ def lib(build_if_missing: bool = True):
     L.lbm_destroy.restype = None
     L.lbm_status_str.argtypes = [C.c_int]
     L.lbm_status_str.restype = C.c_char_p
+    L.lbm_field_sum_noalloc.argtypes = [vp, C.c_longlong, dp, vp]
     L.lbm_last_error.argtypes = []
     L.lbm_last_error.restype = C.c_char_p
     _lib = L
@@ -171,6 +173,16 @@ def lbm_step_profiled(ctx, n: int):
     cnt = (C.c_int * 3)()
     _check(lib().lbm_step_profiled(ctx, int(n), ms, cnt), "lbm_step_profiled")
     return list(ms), list(cnt)
+
+
+def lbm_field_sum_noalloc(field, n: int, stream=None) -> float:
+    """FP64 sum of n float32 values at device pointer `field` (int) or a CUDA tensor, using no
+    device allocation (see include/lbm.h)."""
+    ptr = field if isinstance(field, int) else _ptr(field)
+    out = C.c_double()
+    st = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    _check(lib().lbm_field_sum_noalloc(ptr, int(n), C.byref(out), st), "lbm_field_sum_noalloc")
+    return out.value
 
 
 def lbm_destroy(ctx):
