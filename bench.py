@@ -2,7 +2,7 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
                     [--kernel auto|two_pass|fused] [--precision fp32|bf16|fp16]
-                    [--workload pool_boiling|evaporation|static_droplet]
+                    [--workload pool_boiling|evaporation|static_droplet|batch]
 
 A "step" is one lattice time step of the whole update (psi/EOS, interaction and buoyancy
 forces, D3Q19 MRT collision, local div u and grad T, phase-change source, D3Q7 MRT collision,
@@ -12,6 +12,10 @@ streaming with the wall / outflow boundaries) over the 200 x 200 x 300 pool-boil
 N > 1 (torchrun): every rank runs an independent replica of the lattice (the update has no
 data-path exchange in this build); a barrier brackets the timed region and the time is the
 max over ranks; value = node updates of all ranks / that time ("scaling": "weak").
+
+--workload batch runs the 256-instance ensemble (periodic droplets and slabs, edges 24..96)
+as one batched persistent launch per step (plan autotuned), beside the same instances advanced
+one after another through single-lattice contexts (the sequential FP32 loop).
 
 --impl reference times the FP64 CPU oracle (the plain restatement of the paper's equations)
 on the host cores, on a bounded sample of the same workload per step.
@@ -234,6 +238,165 @@ def run_reference(args):
     return 0
 
 
+def batch_fields(cases):
+    rho, T = [], []
+    for c in cases:
+        r, t = init_fields(c)
+        rho.append(r.ravel())
+        T.append(t.ravel())
+    return np.concatenate(rho), np.concatenate(T)
+
+
+def run_batch(args):
+    """Batched ensemble: one persistent launch per step over all instances vs a sequential loop."""
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_2201_06039_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2201_06039_gb300 import lbm
+    cases = W.batch_instances()
+    dims = [(c["setup"].nx, c["setup"].ny, c["setup"].nz) for c in cases]
+    rho, T = batch_fields(cases)
+    N = rho.size
+    stream = torch.cuda.current_stream()
+    common = lbm.params_from_setup(cases[0]["setup"], use_graph=1, check_nonfinite=0)
+    bt = lbm.Batch(common, dims, stream=stream)
+    bt.init(torch.from_numpy(rho).cuda(), torch.from_numpy(T).cuda())
+    bt.step(args.warmup)
+    tuned_ms = bt.autotune(3)
+    plan = bt.plan
+    bt.step(args.steps)             # captures the K-step graph outside the timed region
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    e0.record(stream)
+    bt.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    finite = bool(np.all(np.isfinite(bt.totals())))
+    mlups = N * args.steps * world / (ms * 1e-3) / 1e6
+    peak, peak_kind = measured_peaks()
+    k_ms = ms / args.steps          # one batched launch is the whole step
+    achieved = BYTES_PER_NODE["fp32"] * N / (k_ms * 1e-3) / 1e9
+
+    # end to end: host fields in, K steps, host moments out (pinned buffers)
+    h_rho = torch.from_numpy(rho).pin_memory()
+    h_T = torch.from_numpy(T).pin_memory()
+    outs = [torch.empty(N, dtype=torch.float32).pin_memory() for _ in range(5)]
+
+    def e2e_once():
+        lbm.lbm_batch_init_fields(bt.b, h_rho, h_T, None)
+        lbm.lbm_batch_step(bt.b, args.steps)
+        lbm.lbm_batch_get_moments(bt.b, *outs)
+
+    e2e_once()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_once()
+    e2e_s = time.perf_counter() - t0
+    bt.close()
+
+    # the same instances one after another through single-lattice contexts (FP32, own graphs)
+    seq_steps = min(args.steps, 100)
+    lats, off = [], 0
+    for c, (nx, ny, nz) in zip(cases, dims):
+        n = nx * ny * nz
+        lat = lbm.Lattice(lbm.params_from_setup(c["setup"], use_graph=1, check_nonfinite=0), stream=stream)
+        lat.init(torch.from_numpy(rho[off:off + n]).cuda(), torch.from_numpy(T[off:off + n]).cuda())
+        lat.step(seq_steps)
+        lat.step(seq_steps)         # captures the seq_steps graph
+        lats.append(lat)
+        off += n
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for lat in lats:
+        lat.step(seq_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    kernels = sorted({lat.kernel for lat in lats})
+    for lat in lats:
+        lat.close()
+    seq_mlups = N * seq_steps / (seq_ms * 1e-3) / 1e6
+
+    line = {
+        "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batch_{len(cases)}_droplets_and_slabs_edges_24_96", "nodes": N,
+                   "instances": len(cases), "kernel": "fused_batch", "precision": "fp32", "plan": plan,
+                   "l2": "no flush: working set > 129 MB L2",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": "fused_batch", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "algorithmic_bytes_per_node": BYTES_PER_NODE["fp32"], "kernel_avg_ms": k_ms},
+        "sequential": {"value": seq_mlups, "unit": "MLUPS", "steps": seq_steps,
+                       "kernels": kernels, "what": "each instance alone through its own context"},
+        "autotune_ms_per_step": tuned_ms,
+        "e2e": {"value": N * args.steps * world / e2e_s / 1e6, "unit": "MLUPS",
+                "h2d_bytes_per_step": 2 * 4 * N / args.steps, "d2h_bytes_per_step": 5 * 4 * N / args.steps},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "finite": finite,
+    }
+    if args.cpu_baseline and rank == 0 and world == 1:
+        line["cpu_baseline"] = cpu_baseline_batch(cases)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def cpu_baseline_batch(cases, budget_s=15.0):
+    """FP64 oracle over the first instances of the ensemble, one after another."""
+    import oracle
+    nodes = steps_done = 0
+    t_all = 0.0
+    k = 0
+    while t_all < budget_s and k < len(cases):
+        c = cases[k]
+        s = c["setup"]
+        Tc = oracle.Tc_of(s)
+        rl, rv, _ = oracle.maxwell(s, c["Tr_drop"] * Tc)
+        rho, T, _ = W.build_fields(c, Tc, rl, rv)
+        o = oracle.Oracle(s)
+        o.init(rho, T)
+        o.step(1)
+        t0 = time.perf_counter()
+        o.step(3)
+        t_all += time.perf_counter() - t0
+        o.close()
+        nodes += s.n_nodes * 3
+        k += 1
+    return dict(value=nodes / t_all / 1e6, unit="MLUPS", cores=oracle.num_threads(), kind="oracle",
+                sample=f"3 FP64 oracle steps of each of the first {k} ensemble instances, one after another")
+
+
 def run_mine(args):
     import torch
     rank, world, local = dist_env()
@@ -372,6 +535,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_mine(args)
 
 

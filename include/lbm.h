@@ -80,7 +80,9 @@ typedef struct {
     int lambda_mode;              /* 0: chi = chi_or_lambda constant; 1: lambda constant,
                                      chi = lambda / (rho cV) per node (Sec. IV.A) */
     double chi_or_lambda;         /* varsigma_T = chi / cs_T^2 + 1/2, cs_T^2 = d/3 */
-    double g[3];                  /* gravity of the buoyancy force F_b = (rho - rho_ave) g */
+    double g[3];                  /* gravity of the buoyancy force F_b = (rho - rho_b) g */
+    double rho_buoy;              /* rho_b: > 0 fixes it; 0 takes the domain mean rho_ave of the
+                                     previous step (Sec. IV.C) */
     int flow_off;                 /* 1: f frozen, u = 0, phi_s = 0 (pure conduction) */
     int thermal_off;              /* 1: g frozen (isothermal phase) */
     int precision;                /* lbm_precision of the stored populations */
@@ -167,6 +169,41 @@ int lbm_step_profiled(lbm_ctx* ctx, int n, double kernel_ms[3], int launches[3])
  * Errors: LBM_EINVAL (NULL pointers, n out of range; message via lbm_last_error), LBM_ECUDA. */
 #define LBM_NOALLOC_MAX_ELEMENTS (1LL << 31)
 int lbm_field_sum_noalloc(const float* field, long long n, double* sum_out, void* stream);
+
+/* ------------------------------------------------------------------ batched ensemble
+ * Many independent lattices of uneven sizes advanced together (the same update as lbm_step on
+ * each, Secs. II-IV): each time step is ONE persistent kernel launch over all instances, whose
+ * CTAs draw (instance, tile column, z-chunk) work items from a table, largest instances first;
+ * lbm_batch_step(n) replays the n launches as a captured CUDA graph.
+ *
+ *   common   parameters shared by every instance (EOS, relaxation times, faces, gravity,
+ *            precision, stream, use_graph, check_nonfinite); its nx, ny, nz and workspace
+ *            fields are ignored (the batch allocates and owns its device memory)
+ *   dims     3 * n_instances ints: (nx, ny, nz) of instance k at dims[3k .. 3k+2]
+ *
+ * Fields passed to lbm_batch_init_fields and returned by lbm_batch_get_moments are the
+ * instances' fields (layout of a single lattice) concatenated in instance order; u is, per
+ * instance, its three planes (ux, uy, uz) before the next instance's.  rho_ave of the
+ * buoyancy force is each instance's own domain mean.
+ * Errors as for the single-lattice calls; LBM_EINVAL names the offending instance. */
+typedef struct lbm_batch lbm_batch;
+int lbm_batch_create(const lbm_params* common, int n_instances, const int* dims, lbm_batch** out);
+/* nodes of instance k (k < 0: of the whole batch) */
+long long lbm_batch_nodes(const lbm_batch* b, int instance);
+int lbm_batch_init_fields(lbm_batch* b, const float* rho, const float* T, const float* u);
+int lbm_batch_step(lbm_batch* b, int n);
+/* Time every candidate work plan (tile rows 4 or 8, columns split into 1, 2 or 4 z-chunks)
+ * over `steps` steps of the current state, keep the fastest, and restore the state exactly
+ * (the candidates' steps are undone).  Needs free device memory for one copy of the state.
+ * best_ms (nullable) receives the chosen plan's time per step. */
+int lbm_batch_autotune(lbm_batch* b, int steps, double* best_ms);
+/* the plan in use: tile rows, z-chunks per column, work items, persistent CTAs (each nullable) */
+int lbm_batch_plan(const lbm_batch* b, int* tile_rows, int* z_split, int* items, int* ctas);
+int lbm_batch_get_moments(lbm_batch* b, float* rho, float* ux, float* uy, float* uz, float* T);
+/* sums[2k] = sum of rho, sums[2k+1] = sum of T over instance k (FP64, host pointer) */
+int lbm_batch_get_totals(lbm_batch* b, double* sums);
+long long lbm_batch_steps_done(const lbm_batch* b);
+void lbm_batch_destroy(lbm_batch* b);
 
 /* Release everything the context owns.  NULL is ignored. */
 void lbm_destroy(lbm_ctx* ctx);

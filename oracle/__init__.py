@@ -42,6 +42,7 @@ class OrcParams(C.Structure):
         ("lambda_mode", C.c_int), ("chi_or_lambda", C.c_double),
         ("g", C.c_double * 3),
         ("flow_off", C.c_int), ("thermal_off", C.c_int),
+        ("rho_buoy", C.c_double),
     ]
 
 
@@ -131,6 +132,7 @@ def params_from_setup(s) -> OrcParams:
     for k in range(3):
         p.g[k] = s.gravity[k]
     p.flow_off, p.thermal_off = s.flow_off, s.thermal_off
+    p.rho_buoy = s.rho_buoy
     return p
 
 

@@ -9,7 +9,9 @@ state, for sigma on a grid, and picks the sigma* that minimises
 max(|rho_l/rho_l^Maxwell - 1|, |rho_v/rho_v^Maxwell - 1|).
 
 Output: tests/golden/sigma_calibration.json (sigma*, the sweep, Maxwell densities).
-Run:    python -m oracle.calibrate_sigma
+Run:    python -m oracle.calibrate_sigma           (a = 2/49)
+        python -m oracle.calibrate_sigma a1_49     (a = 1/49, the paper's droplet tests; output
+                                                    tests/golden/sigma_calibration_a1_49.json)
 """
 from __future__ import annotations
 
@@ -24,12 +26,12 @@ import workloads as W
 
 GRID = [round(0.09 + 0.0025 * k, 4) for k in range(17)]   # 0.0900 .. 0.1300
 STEPS = 30000
-OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
-                   "tests", "golden", "sigma_calibration.json")
+GOLDEN = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests", "golden")
+VARIANTS = {"a2_49": (2.0 / 49.0, "sigma_calibration.json"), "a1_49": (1.0 / 49.0, "sigma_calibration_a1_49.json")}
 
 
-def flat_interface(sigma: float, steps: int = STEPS, Tr: float = 0.86):
-    s = W.LatticeSetup(1, 1, 128, sigma=sigma, thermal_off=1)
+def flat_interface(sigma: float, steps: int = STEPS, Tr: float = 0.86, a: float = 2.0 / 49.0):
+    s = W.LatticeSetup(1, 1, 128, sigma=sigma, thermal_off=1, a=a)
     Tc = oracle.Tc_of(s)
     rl, rv, ps = oracle.maxwell(s, Tr * Tc)
     rho = W.slab(s.shape, 32.0, 2.0, rl, rv, axis=2)
@@ -44,10 +46,13 @@ def flat_interface(sigma: float, steps: int = STEPS, Tr: float = 0.86):
 
 
 def main():
+    variant = sys.argv[1] if len(sys.argv) > 1 else "a2_49"
+    a, name = VARIANTS[variant]
+    out_path = os.path.join(GOLDEN, name)
     rows = []
     for sg in GRID:
         try:
-            r = flat_interface(sg)
+            r = flat_interface(sg, a=a)
         except FloatingPointError:
             r = dict(sigma=sg, unstable=True)
         rows.append(r)
@@ -55,13 +60,14 @@ def main():
     ok = [r for r in rows if not r.get("unstable")]
     best = min(ok, key=lambda r: max(abs(r["err_l"]), abs(r["err_v"])))
     out = dict(
-        what="sigma* of Eq. 9 from a flat interface (1x1x128, 0.86 Tc, a=2/49) run by the FP64 oracle",
-        script="oracle/calibrate_sigma.py", steps=STEPS, sigma_star=best["sigma"],
+        what=f"sigma* of Eq. 9 from a flat interface (1x1x128, 0.86 Tc, a={'2' if variant == 'a2_49' else '1'}/49) "
+             "run by the FP64 oracle",
+        script="oracle/calibrate_sigma.py", a=a, steps=STEPS, sigma_star=best["sigma"],
         maxwell=dict(rho_l=best["maxwell_l"], rho_v=best["maxwell_v"], p_sat=best["p_sat"]),
         best=best, sweep=rows)
-    with open(OUT, "w") as fh:
+    with open(out_path, "w") as fh:
         json.dump(out, fh, indent=1)
-    print("sigma* =", best["sigma"], "->", OUT)
+    print("sigma* =", best["sigma"], "->", out_path)
     return 0
 
 

@@ -11,7 +11,7 @@
  *   1. rho = sum f, T = sum g                                  (Eq. 10, Eq. 20)
  *   2. psi = sqrt(2 (p_EOS - rho cs^2) / (G c^2)), G = -1      (Eq. 8, Peng-Robinson Eq. 49)
  *   3. F_m = -G psi(x) sum_a w(|e_a|^2) psi(x + e_a) e_a       (Eq. 7)
- *      F_b = (rho - rho_ave) g                                 (Sec. IV.C buoyancy)
+ *      F_b = (rho - rho_b) g, rho_b = rho_ave or a fixed value  (Sec. IV.C buoyancy)
  *   4. u = (sum e f + F/2) / rho                               (Eq. 10)
  *   5. m = M f, m* = m - Lambda (m - m_eq) + (I - Lambda/2) S  (Eqs. 3, 5, 6, 9)
  *      f* = M^-1 m*                                            (Eq. 4)
@@ -81,6 +81,7 @@ typedef struct {
     double g[3];
     int flow_off;            /* f frozen, u = 0, phi_s = 0 (pure conduction) */
     int thermal_off;         /* g frozen (isothermal) */
+    double rho_buoy;         /* > 0: fixed reference density of the buoyancy force, else rho_ave */
 } orc_params;
 
 typedef struct {
@@ -530,7 +531,7 @@ static int step_once(orc_state* s) {
     const orc_params* p = &s->p;
     long N = s->N;
     if (macroscopic(s)) return -5;
-    real rho_ave = (real)s->rho_ave;
+    real rho_ave = p->rho_buoy > 0.0 ? (real)p->rho_buoy : (real)s->rho_ave;
     double sum = 0.0;
     for (long i = 0; i < N; ++i) sum += s->rho[i];
     real w7[Q7];
@@ -626,7 +627,8 @@ int orc_moments(orc_state* s, double* rho_o, double* ux, double* uy, double* uz,
                 }
                 real u[3];
                 for (int k = 0; k < 3; ++k) {
-                    real F = Fm[k] + (rho - (real)s->rho_ave) * (real)p->g[k];
+                    real rb = p->rho_buoy > 0.0 ? (real)p->rho_buoy : (real)s->rho_ave;
+                    real F = Fm[k] + (rho - rb) * (real)p->g[k];
                     u[k] = p->flow_off ? 0.0 : (j[k] + 0.5 * F) / rho;
                 }
                 if (rho_o) rho_o[i] = rho;

@@ -9,13 +9,16 @@
 #include <cuda_runtime.h>
 
 #include "../../include/lbm.h"
+#include "lbm_host.h"
 #include "lbm_launch.h"
 
 using namespace gb300lbm;
 
 namespace {
-
 thread_local char g_err[512] = "";
+}  // namespace
+
+namespace gb300lbm {
 
 int fail(int status, const char* fmt, ...) {
     va_list ap;
@@ -35,6 +38,10 @@ int fail(int status, const char* fmt, ...) {
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 size_t pop_bytes(int precision) { return precision == LBM_FP32 ? 4 : 2; }
+
+}  // namespace gb300lbm
+
+namespace {
 
 struct Layout {
     size_t pops[2], psirho, phis, sums, partial, counter, flag, total;
@@ -104,7 +111,7 @@ struct lbm_ctx {
     }
 };
 
-namespace {
+namespace gb300lbm {
 
 double critical_T(const lbm_params* p) { return 0.0778 * p->a / (0.45724 * p->b * p->R); }
 
@@ -171,6 +178,7 @@ DevParams make_dev(const lbm_params* p) {
     d.Gq = (float)(1.0 / p->varsigma_q); d.Gpi = (float)(1.0 / p->varsigma_pi);
     d.lambda_mode = p->lambda_mode; d.chi_or_lambda = (float)p->chi_or_lambda;
     d.gx = (float)p->g[0]; d.gy = (float)p->g[1]; d.gz = (float)p->g[2];
+    d.rho_buoy = p->rho_buoy > 0.0 ? (float)p->rho_buoy : 0.f;
     d.flow_off = p->flow_off; d.thermal_off = p->thermal_off;
     if (p->precision != LBM_FP32) {
         for (int a = 0; a < 19; ++a) {
@@ -183,15 +191,6 @@ DevParams make_dev(const lbm_params* p) {
     return d;
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-// Tensor maps of both population buffers for the TMA kernel: dims (Ws, Hs, nz, 26) of FP32,
-// boxes (TX + 8, TY + 4, 1, 14) and (TX + 8, TY + 4, 1, 6) of the planned tile shape;
-// out-of-range cells read as zero (never used).
-bool make_tma_maps(lbm_ctx* c);
-
 bool is_device_ptr(const void* ptr) {
     if (!ptr) return false;
     cudaPointerAttributes at;
@@ -201,6 +200,19 @@ bool is_device_ptr(const void* ptr) {
     }
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
+
+}  // namespace gb300lbm
+
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// Tensor maps of both population buffers for the TMA kernel: dims (Ws, Hs, nz, 26) of FP32,
+// boxes (TX + 8, TY + 4, 1, 14) and (TX + 8, TY + 4, 1, 6) of the planned tile shape;
+// out-of-range cells read as zero (never used).
+bool make_tma_maps(lbm_ctx* c);
 
 void drop_graphs(lbm_ctx* c) {
     for (int k = 0; k < c->n_graphs; ++k) cudaGraphExecDestroy(c->graphs[k].exec);
@@ -344,6 +356,10 @@ bool make_tma_maps(lbm_ctx* c) {
     cuuint64_t strides[3] = {(cuuint64_t)d.Ws * 4, (cuuint64_t)d.splane * 4, (cuuint64_t)d.Ns * 4};
     const cuuint32_t bw = (cuuint32_t)tma_box_w(shape), bh = (cuuint32_t)tma_box_h(shape);
     cuuint32_t box14[4] = {bw, bh, 1, 14}, box6[4] = {bw, bh, 1, 6}, es[4] = {1, 1, 1, 1};
+    // output tiles: the real nodes only (x < nx, y < ny in storage coordinates + the offsets), so
+    // that the clipped edge tiles never write the ghost columns and rows
+    cuuint64_t dims_out[4] = {(cuuint64_t)(d.nx + kGX), (cuuint64_t)(d.ny + kGY), (cuuint64_t)d.nz, (cuuint64_t)kSlots};
+    cuuint32_t box_out[4] = {(cuuint32_t)tma_tile_w(shape), (cuuint32_t)tma_tile_h(shape), 1, (cuuint32_t)kSlots};
     for (int k = 0; k < 2; ++k) {
         void* g = c->pbuf(k);
         if (encode(&c->maps.m14[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, dims, strides, box14, es,
@@ -352,6 +368,10 @@ bool make_tma_maps(lbm_ctx* c) {
             return false;
         if (encode(&c->maps.m6[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, dims, strides, box6, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+        if (encode(&c->maps.mout[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, dims_out, strides, box_out, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;
     }

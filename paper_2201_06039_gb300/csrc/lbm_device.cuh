@@ -71,10 +71,17 @@ struct DevParams {
     int lambda_mode;
     float chi_or_lambda;
     float gx, gy, gz;
+    float rho_buoy;           // > 0: fixed reference density of the buoyancy force, else rho_ave
     int flow_off, thermal_off;
     float shift_f[19];        // storage shift w_a rho_ref (16-bit storage only, else 0)
     float shift_g[7];         // storage shift w_a T_ref
 };
+
+// reference density of the buoyancy force F_b = (rho - rho_b) g: fixed, or the domain mean of the
+// previous step (Sec. IV.C) from its FP64 sum
+__device__ __forceinline__ float buoyancy_ref(const DevParams& P, double rho_sum, double inv_N) {
+    return P.rho_buoy > 0.f ? P.rho_buoy : (float)(rho_sum * inv_N);
+}
 
 // ---------------------------------------------------------------- population storage
 // Populations are stored structure-of-arrays: pop[a * N + node].

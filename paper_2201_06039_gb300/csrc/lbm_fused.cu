@@ -155,22 +155,16 @@ __device__ void finish_sums(const double2* partial, int n, unsigned* counter, do
 }
 
 // ================================================================ generic fused kernel
+// One tile column: the (x, y) tile at (x0, y0), planes [z0, z1), by all threads of the block.
+// Adds the tile's rho and T to the Kahan pairs (r_sum, r_c), (t_sum, t_c) of the owner threads
+// and ORs a non-finite / psi-domain failure into bad.
 template <typename S, int TY>
-__global__ void __launch_bounds__(FusedShape<TY>::kThreads, 2)
-k_fused(DevParams P, const S* __restrict__ src, S* __restrict__ dst, int pull_f, int pull_g,
-        const double* __restrict__ sums_cur, double2* partial, unsigned* counter, double* sums_next,
-        float* __restrict__ phis, int* flag, int first, int zchunk) {
+__device__ __forceinline__ void fused_column(const DevParams& P, const S* __restrict__ src, S* __restrict__ dst,
+                                             int pull_f, int pull_g, float rho_ave, float* __restrict__ phis,
+                                             int first, int x0, int y0, int z0, int z1, float* stage, float2* ring,
+                                             float& r_sum, float& r_c, float& t_sum, float& t_c, int& bad) {
     using Sh = FusedShape<TY>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* stage = reinterpret_cast<float*>(smem_raw);                       // [2][26][TY][32]
-    float2* ring = reinterpret_cast<float2*>(stage + 2 * Sh::kStageFloats);  // [3][TY+2][34]
-    __shared__ double red_a[Sh::kThreads / 32], red_b[Sh::kThreads / 32];
-    __shared__ int is_last;
-
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = blockIdx.z * zchunk;
-    const int z1 = min(P.nz, z0 + zchunk);
     int lx, ly;
     slot_of<TY>(tid, lx, ly);
     const bool interior = tid < Sh::kInterior;
@@ -180,10 +174,6 @@ k_fused(DevParams P, const S* __restrict__ src, S* __restrict__ dst, int pull_f,
     const int my = slot_used ? map_coord(gy, P.ny, P.bc[2], P.bc[3]) : 0;
     const bool owner = interior && gx < P.nx && gy < P.ny;
     const int slot = ly * Sh::kRingW + lx;
-
-    float r_sum = 0.f, r_c = 0.f, t_sum = 0.f, t_c = 0.f;
-    int bad = 0;
-    const float rho_ave = (float)(sums_cur[0] * P.inv_N);
 
     auto psi_pass = [&](int zp) {
         if (!slot_used) return;
@@ -252,6 +242,27 @@ k_fused(DevParams P, const S* __restrict__ src, S* __restrict__ dst, int pull_f,
         collide(z);
         __syncthreads();
     }
+}
+
+template <typename S, int TY>
+__global__ void __launch_bounds__(FusedShape<TY>::kThreads, 2)
+k_fused(DevParams P, const S* __restrict__ src, S* __restrict__ dst, int pull_f, int pull_g,
+        const double* __restrict__ sums_cur, double2* partial, unsigned* counter, double* sums_next,
+        float* __restrict__ phis, int* flag, int first, int zchunk) {
+    using Sh = FusedShape<TY>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* stage = reinterpret_cast<float*>(smem_raw);                       // [2][26][TY][32]
+    float2* ring = reinterpret_cast<float2*>(stage + 2 * Sh::kStageFloats);  // [3][TY+2][34]
+    __shared__ double red_a[Sh::kThreads / 32], red_b[Sh::kThreads / 32];
+    __shared__ int is_last;
+
+    const int tid = threadIdx.x;
+    const int z0 = blockIdx.z * zchunk;
+    float r_sum = 0.f, r_c = 0.f, t_sum = 0.f, t_c = 0.f;
+    int bad = 0;
+    const float rho_ave = buoyancy_ref(P, sums_cur[0], P.inv_N);
+    fused_column<S, TY>(P, src, dst, pull_f, pull_g, rho_ave, phis, first, blockIdx.x * TX, blockIdx.y * TY, z0,
+                        min(P.nz, z0 + zchunk), stage, ring, r_sum, r_c, t_sum, t_c, bad);
 
     if (__syncthreads_or(bad) && tid == 0) atomicOr(flag, 1);
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
@@ -259,6 +270,76 @@ k_fused(DevParams P, const S* __restrict__ src, S* __restrict__ dst, int pull_f,
                                 red_a, red_b);
     finish_sums<Sh::kThreads>(partial, gridDim.x * gridDim.y * gridDim.z, counter, sums_next, tid, 0, red_a, red_b,
                               &is_last);
+}
+
+// ================================================================ batched ensemble
+// Many independent lattices in one launch.  Persistent CTAs draw (instance, tile column) items
+// from a table through an atomic work counter, so uneven instances balance themselves; every
+// item runs the generic fused update above with the geometry of its instance and the shared
+// model constants of P.  Per-item FP64 partials of (rho, T) are reduced per instance, in item
+// order, by the last CTA to finish, which also re-arms both counters for the next launch.
+template <typename S, int TY>
+__global__ void __launch_bounds__(FusedShape<TY>::kThreads, 2)
+k_fused_batch(DevParams P, const BatchInst* __restrict__ insts, const BatchItem* __restrict__ items, int n_items,
+              int n_inst, const S* __restrict__ src, S* __restrict__ dst, int pull_f, int pull_g,
+              const double* __restrict__ sums_cur, double2* partial, unsigned* counters, double* sums_next,
+              float* __restrict__ phis, int* flag, int first) {
+    using Sh = FusedShape<TY>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* stage = reinterpret_cast<float*>(smem_raw);
+    float2* ring = reinterpret_cast<float2*>(stage + 2 * Sh::kStageFloats);
+    __shared__ double red_a[Sh::kThreads / 32], red_b[Sh::kThreads / 32];
+    __shared__ int next_item, is_last;
+    const int tid = threadIdx.x;
+    int bad = 0;
+    for (;;) {
+        if (tid == 0) next_item = (int)atomicAdd(&counters[0], 1u);
+        __syncthreads();
+        const int it = next_item;
+        __syncthreads();
+        if (it >= n_items) break;
+        const BatchItem w = items[it];
+        const BatchInst I = insts[w.inst];
+        DevParams Q = P;
+        Q.nx = I.nx; Q.ny = I.ny; Q.nz = I.nz;
+        Q.plane = I.nx * I.ny;
+        Q.N = Q.plane * I.nz;
+        Q.Ws = I.Ws; Q.Hs = I.Hs;
+        Q.splane = I.Ws * I.Hs;
+        Q.Ns = Q.splane * I.nz;
+        Q.inv_N = I.inv_N;
+        Q.hot_cx = 0.5f * (float)I.nx;
+        Q.hot_cy = 0.5f * (float)I.ny;
+        float r_sum = 0.f, r_c = 0.f, t_sum = 0.f, t_c = 0.f;
+        const float rho_ave = buoyancy_ref(P, sums_cur[2 * w.inst], I.inv_N);
+        fused_column<S, TY>(Q, src + I.pop_off, dst + I.pop_off, pull_f, pull_g, rho_ave, phis + I.field_off, first,
+                            w.x0, w.y0, w.z0, w.z1, stage, ring, r_sum, r_c, t_sum, t_c, bad);
+        block_partial<Sh::kThreads>((double)r_sum - (double)r_c, (double)t_sum - (double)t_c, partial, it, tid, 0,
+                                    red_a, red_b);
+    }
+    if (__syncthreads_or(bad) && tid == 0) atomicOr(flag, 1);
+    if (tid == 0) {
+        __threadfence();
+        is_last = atomicAdd(&counters[1], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    for (int k = tid; k < n_inst; k += Sh::kThreads) {
+        const BatchInst I = insts[k];
+        double a = 0.0, b = 0.0;
+        for (int j = I.item0; j < I.item0 + I.n_items; ++j) {
+            const double2 q = __ldcg(partial + j);
+            a += q.x;
+            b += q.y;
+        }
+        sums_next[2 * k] = a;
+        sums_next[2 * k + 1] = b;
+    }
+    if (tid == 0) {
+        counters[0] = 0u;
+        counters[1] = 0u;
+    }
 }
 
 // ================================================================ TMA producer / consumer kernel
@@ -270,14 +351,20 @@ template <int TX_, int TY_> struct TmaShape {
     static constexpr int kPsiWarps = 6;                              // psi pass: slots round robin
     static constexpr int kColWarps = (kInterior + 31) / 32;          // collision: one node per thread
     static constexpr int kPsiThreads = kPsiWarps * 32, kColThreads = kColWarps * 32;
-    static constexpr int kThreads = 32 + kPsiThreads + kColThreads;  // producer warp first
+    static constexpr int kPsiPerThread = (kSlotsAll + kPsiThreads - 1) / kPsiThreads;
+    static constexpr int kThreads = 64 + kPsiThreads + kColThreads;  // producer warp, storer warp first
     static constexpr int kRingW = TX_ + 2, kRingPlane = (TX_ + 2) * (TY_ + 2);
     static constexpr int kWinW = TX_ + 8;               // window columns x0-4 .. x0+TX+3 (16-byte aligned)
     static constexpr int kWinH = TY_ + 4;               // window rows    y0-2 .. y0+TY+1
     static constexpr int kWin = kWinW * kWinH;          // floats per population slot
     static constexpr int kStages = 3, kRing = 4;
-    static constexpr size_t kSmem = (size_t)kStages * kSlots * kWin * sizeof(float) +
+    static constexpr size_t kStageBytes = (size_t)kStages * kSlots * kWin * sizeof(float);
+    // collided plane, slot-major [26][TY][TX]: source of one TMA tensor store per plane
+    static constexpr size_t kOutBytes = ((size_t)kSlots * kInterior * sizeof(float) + 127) / 128 * 128;
+    static constexpr size_t kSmem = kStageBytes + kOutBytes +
                                     (size_t)kRing * kRingPlane * (sizeof(float2) + sizeof(float));
+    static_assert(kStageBytes % 128 == 0, "TMA destinations must stay 128-byte aligned");
+    static_assert(kPsiPerThread <= 2, "psi threads hold at most two ring slots");
 };
 
 // ring slot (lx, ly) of slot index q: tile nodes (row-major), then the halo ring
@@ -337,6 +424,24 @@ __device__ __forceinline__ void tma_load_4d(float* smem_dst, const CUtensorMap* 
         : "memory");
 }
 
+// tensor store of a shared-memory box (bulk async-group completion); the box is clipped at the
+// tensor's bounds
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const float* smem_src, int c0, int c1, int c2,
+                                             int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4, %5}], [%1];" ::"l"(
+            reinterpret_cast<unsigned long long>(map)),
+        "r"(smem_u32(smem_src)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// generic-proxy shared-memory writes of this thread become visible to the async (TMA) proxy
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // source plane of the e_z = +1 group (pulls from z-1) and of the e_z = -1 group (pulls from
 // z+1); -1 at a wall face (all those links bounce back from the node itself)
 __device__ __forceinline__ int src_plane_up(const DevParams& P, int mz) {
@@ -355,10 +460,9 @@ __device__ __forceinline__ int src_plane_dn(const DevParams& P, int mz) {
 // global memory), Eq. 51 for g at non-periodic z faces (own g+_abar from global memory) and at
 // thermal x / y faces (own g+_abar from the stage).
 template <int WW, int WIN>
-__device__ __forceinline__ void stage_pulls(const DevParams& P, const float* __restrict__ st, int wx, int wy,
+__device__ __forceinline__ void stage_pulls(const DevParams& P, const float* __restrict__ b,
                                             const float* __restrict__ src, int mx, int my, int mz, float f[19],
                                             float g[7]) {
-    const float* b = st + wy * WW + wx;
 #define GB300_SF(A) f[A] = b[fslot(A) * WIN - ey19(A) * WW - ex19(A)];
     GB300_SF(0) GB300_SF(1) GB300_SF(2) GB300_SF(3) GB300_SF(4) GB300_SF(5) GB300_SF(6) GB300_SF(7) GB300_SF(8)
     GB300_SF(9) GB300_SF(10) GB300_SF(11) GB300_SF(12) GB300_SF(13) GB300_SF(14) GB300_SF(15) GB300_SF(16)
@@ -395,28 +499,32 @@ __device__ __forceinline__ void stage_pulls(const DevParams& P, const float* __r
     if (P.bc[3] == BC_THERMAL_ONLY && my == P.ny - 1) g[4] = -b[gslot(3) * WIN] + 2.f * P.w1 * wall_T(P, 3, mx, my);
 }
 
-// Warp roles: warp 0 = producer (TMA), warps 1..4 = psi pass, the rest = collision.  Every
-// hand-off goes through an mbarrier:
+// Warp roles: warp 0 = producer (TMA loads), warp 1 = storer (TMA stores), the next kPsiWarps =
+// psi pass, the rest = collision.  Every hand-off goes through an mbarrier:
 //   full[s]      TMA bytes of the stage landed              (producer  -> psi, collision)
 //   empty[s]     psi pass and collision done with a stage    (psi, collision -> producer)
 //   ring_full[r] (psi, rho) of a plane in ring slot r ready   (psi       -> collision)
 //   ring_empty[r] last collision reading ring slot r done     (collision -> psi)
-// Stage uses and ring uses follow one plane counter k across the CTA's items.
+//   out_full     collided plane written to the out buffer    (collision -> storer)
+//   out_empty    tensor store has read the out buffer         (storer    -> collision)
+// Stage uses and ring uses follow one plane counter k across the CTA's items; out-buffer uses
+// follow the collided-plane counter u.
 template <int TX_, int TY_>
 __global__ void __launch_bounds__(TmaShape<TX_, TY_>::kThreads, 1)
-k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ CUtensorMap map6, DevParams P,
-            const float* __restrict__ src, float* __restrict__ dst, const double* __restrict__ sums_cur,
-            double2* partial, unsigned* counter, double* sums_next, float* __restrict__ phis, int* flag, int first,
-            int zchunk, int tiles_x, int tiles_y, int n_items) {
+k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ CUtensorMap map6,
+            const __grid_constant__ CUtensorMap map_out, DevParams P, const float* __restrict__ src,
+            const double* __restrict__ sums_cur, double2* partial, unsigned* counter, double* sums_next,
+            float* __restrict__ phis, int* flag, int first, int zchunk, int tiles_x, int tiles_y, int n_items) {
     using Sh = TmaShape<TX_, TY_>;
     constexpr int kWin = Sh::kWin, kWinW = Sh::kWinW, kStages = Sh::kStages, kRing = Sh::kRing;
     constexpr int kCol = Sh::kColThreads;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     float* stages = reinterpret_cast<float*>(smem_raw);                          // [3][26][TY+4][TX+8]
-    float2* ring = reinterpret_cast<float2*>(stages + kStages * kSlots * kWin);  // [4][TY+2][TX+2] (psi, rho)
+    float* out = reinterpret_cast<float*>(smem_raw + Sh::kStageBytes);           // [26][TY][TX]
+    float2* ring = reinterpret_cast<float2*>(smem_raw + Sh::kStageBytes + Sh::kOutBytes);  // [4][TY+2][TX+2]
     float* tring = reinterpret_cast<float*>(ring + kRing * Sh::kRingPlane);      // [4][TY+2][TX+2] T
     __shared__ __align__(8) unsigned long long full_bar[kStages], empty_bar[kStages], ring_full[kRing],
-        ring_empty[kRing];
+        ring_empty[kRing], out_full, out_empty;
     __shared__ double red_a[kCol / 32], red_b[kCol / 32];
     __shared__ int is_last;
     __shared__ volatile int abort_flag;
@@ -432,6 +540,8 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
             mbar_init(&ring_full[r], Sh::kPsiWarps);
             mbar_init(&ring_empty[r], Sh::kColWarps);
         }
+        mbar_init(&out_full, Sh::kColWarps);
+        mbar_init(&out_empty, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -478,35 +588,73 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                 mbar_wait(&full_bar[q % kStages], (q / kStages) & 1);
         }
         __syncwarp();
-    } else if (warp <= Sh::kPsiWarps) {
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ storer (one lane)
+        if (lane == 0) {
+            unsigned u = 0;
+            for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+                const int chunk = item / ntiles, tile = item % ntiles;
+                const int x0 = (tile % tiles_x) * TX_, y0 = (tile / tiles_x) * TY_;
+                const int z0 = chunk * zchunk, z1 = min(P.nz, z0 + zchunk);
+                for (int z = z0; z < z1; ++z, ++u) {
+                    wait(&out_full, u & 1);
+                    if (!abort_flag) {
+                        // the box starts at the tile origin (x a multiple of 4 floats); cells
+                        // beyond (nx, ny) fall outside the tensor and are not written
+                        tma_store_4d(&map_out, out, x0 + kGX, y0 + kGY, z, 0);
+                        bulk_commit();
+                        bulk_wait_read_all();
+                    }
+                    mbar_arrive(&out_empty);
+                }
+            }
+            bulk_wait_all();   // the stores have completed before the CTA exits
+        }
+        __syncwarp();
+    } else if (warp < 2 + Sh::kPsiWarps) {
         // ------------------------------------------------------------ psi pass
-        const int pt = tid - 32;
+        const int pt = tid - 64;
+        int lxs[2], lys[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int q = pt + j * Sh::kPsiThreads;
+            lxs[j] = -1;
+            lys[j] = -1;
+            if (j < Sh::kPsiPerThread && q < Sh::kSlotsAll) tma_slot_of<TX_, TY_>(q, lxs[j], lys[j]);
+        }
         int bad = 0;
         unsigned k = 0;
         for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
             const int chunk = item / ntiles, tile = item % ntiles;
             const int x0 = (tile % tiles_x) * TX_, y0 = (tile / tiles_x) * TY_;
             const int z0 = chunk * zchunk, z1 = min(P.nz, z0 + zchunk);
+            // slot geometry of this item, fixed across its planes
+            bool use[2];
+            int mxs[2], mys[2], woff[2], roff[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int gx = x0 + lxs[j] - 1, gy = y0 + lys[j] - 1;
+                use[j] = lxs[j] >= 0 && gx >= -1 && gx <= P.nx && gy >= -1 && gy <= P.ny;
+                mxs[j] = use[j] ? map_coord(gx, P.nx, P.bc[0], P.bc[1]) : 0;
+                mys[j] = use[j] ? map_coord(gy, P.ny, P.bc[2], P.bc[3]) : 0;
+                woff[j] = (lys[j] + 1) * kWinW + lxs[j] + 3;
+                roff[j] = lys[j] * Sh::kRingW + lxs[j];
+            }
             for (int p = z0 - 1; p <= z1; ++p, ++k) {
                 const int s = k % kStages, r = k % kRing;
                 if (k >= (unsigned)kRing) wait(&ring_empty[r], (k / kRing - 1) & 1);
                 wait(&full_bar[s], (k / kStages) & 1);
                 const float* st = stages + (size_t)s * kSlots * kWin;
                 const int mz = map_coord(p, P.nz, P.bc[4], P.bc[5]);
-#pragma unroll 2
-                for (int q = pt; q < Sh::kSlotsAll; q += Sh::kPsiThreads) {
-                    int lx, ly;
-                    tma_slot_of<TX_, TY_>(q, lx, ly);
-                    const int gx = x0 + lx - 1, gy = y0 + ly - 1;
-                    if (gx < -1 || gx > P.nx || gy < -1 || gy > P.ny) continue;
-                    const int mx = map_coord(gx, P.nx, P.bc[0], P.bc[1]);
-                    const int my = map_coord(gy, P.ny, P.bc[2], P.bc[3]);
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    if (!use[j]) continue;
                     float f[19], g[7];
-                    stage_pulls<kWinW, kWin>(P, st, lx + 3, ly + 1, src, mx, my, mz, f, g);
+                    stage_pulls<kWinW, kWin>(P, st + woff[j], src, mxs[j], mys[j], mz, f, g);
                     float rho = sum19(f), T = sum7(g);
                     const float psi2 = psi_squared(P, rho, T);
-                    ring[r * Sh::kRingPlane + ly * Sh::kRingW + lx] = make_float2(psi_of(psi2), rho);
-                    tring[r * Sh::kRingPlane + ly * Sh::kRingW + lx] = T;
+                    ring[r * Sh::kRingPlane + roff[j]] = make_float2(psi_of(psi2), rho);
+                    tring[r * Sh::kRingPlane + roff[j]] = T;
                     bad |= !(psi2 > 0.f) || !isfinite(rho) || !isfinite(T);
                 }
                 __syncwarp();
@@ -519,12 +667,14 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
         if (bad) atomicOr(flag, 1);
     } else {
         // ------------------------------------------------------------ collision
-        const int ct = tid - 32 - Sh::kPsiThreads;
+        const int ct = tid - 64 - Sh::kPsiThreads;
         const bool node_thread = ct < Sh::kInterior;
         const int lx = ct % TX_ + 1, ly = ct / TX_ + 1;
         const int slot = ly * Sh::kRingW + lx;
-        const float rho_ave = (float)(sums_cur[0] * P.inv_N);
-        unsigned k = 0;
+        const int woff = (ly + 1) * kWinW + lx + 3;
+        const float rho_ave = buoyancy_ref(P, sums_cur[0], P.inv_N);
+        float* const outp = out + ct;
+        unsigned k = 0, u = 0;
         for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
             const int chunk = item / ntiles, tile = item % ntiles;
             const int x0 = (tile % tiles_x) * TX_, y0 = (tile / tiles_x) * TY_;
@@ -550,7 +700,7 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                 float f[19], g[7];
                 if (owner) {
                     const float* sz = stages + (size_t)(kz % kStages) * kSlots * kWin;
-                    stage_pulls<kWinW, kWin>(P, sz, lx + 3, ly + 1, src, gx, gy, z, f, g);
+                    stage_pulls<kWinW, kWin>(P, sz + woff, src, gx, gy, z, f, g);
                 }
                 __syncwarp();       // pulls are in registers: the stage of plane z may be refilled
                 if (lane == 0) mbar_arrive(&empty_bar[kz % kStages]);
@@ -567,6 +717,7 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                 }
                 __syncwarp();       // ring plane z-1 has been read for the last time
                 if (lane == 0) mbar_arrive(&ring_empty[(kz - 1) % kRing]);
+                float ph = 0.f;
                 if (owner) {
                     const float rho = me.y;
                     kahan_add(r_sum, r_c, rho);
@@ -575,11 +726,21 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                     const float db = rho - rho_ave;
                     const float Fm2 = Fmx * Fmx + Fmy * Fmy + Fmz * Fmz;
                     NodeOut o = collide_f(P, f, rho, Fmx + db * P.gx, Fmy + db * P.gy, Fmz + db * P.gz, Fm2, me.x * me.x);
-                    const int d = node_of(P, gx, gy, z);
-                    const float ph = collide_g(P, g, rho, T, o, rs.gx, rs.gy, rs.gz, ph_prev, first);
-                    store_slots<float>(P, dst, sidx(P, gx, gy, z), f, g);   // ghosts: k_ghosts after the step
-                    phis[d] = ph;
+                    ph = collide_g(P, g, rho, T, o, rs.gx, rs.gy, rs.gz, ph_prev, first);
                 }
+                // the out buffer is free once the tensor store of the previous plane has read it
+                if (u > 0) wait(&out_empty, (u - 1) & 1);
+                if (owner) {
+#pragma unroll
+                    for (int a = 0; a < 19; ++a) outp[fslot(a) * Sh::kInterior] = f[a];
+#pragma unroll
+                    for (int a = 0; a < 7; ++a) outp[gslot(a) * Sh::kInterior] = g[a];
+                    phis[node_of(P, gx, gy, z)] = ph;   // ghosts: k_ghosts after the step
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&out_full);
+                ++u;
             }
             // stage of the item's last plane (psi only); ring planes z1-1 and z1
             __syncwarp();
@@ -691,6 +852,8 @@ void tma_plan_for(const DevParams& P, int ctas, int* shape, int* zchunk, int* it
 
 int tma_box_w(int shape) { return shape == 0 ? Shape0::kWinW : Shape1::kWinW; }
 int tma_box_h(int shape) { return shape == 0 ? Shape0::kWinH : Shape1::kWinH; }
+int tma_tile_w(int shape) { return shape == 0 ? 32 : 40; }
+int tma_tile_h(int shape) { return shape == 0 ? 8 : 7; }
 
 cudaError_t launch_fused(const DevParams& P, int precision, const StateBufs& B, const double* sums_cur,
                          double* sums_next, int first, cudaStream_t s, const TmaMaps* maps) {
@@ -707,8 +870,9 @@ cudaError_t launch_fused(const DevParams& P, int precision, const StateBufs& B, 
                                      (int)SH::kSmem);                                                          \
             if (e != cudaSuccess) return e;                                                                    \
             k_fused_tma<TXV, TYV><<<ctas, SH::kThreads, SH::kSmem, s>>>(                                       \
-                maps->m14[B.src_index], maps->m6[B.src_index], P, (const float*)B.src, (float*)B.dst, sums_cur, \
-                B.partial, B.counter, sums_next, B.phis, B.flag, first, maps->zchunk, txs, tys, maps->items);   \
+                maps->m14[B.src_index], maps->m6[B.src_index], maps->mout[B.src_index ^ 1], P,                 \
+                (const float*)B.src, sums_cur, B.partial, B.counter, sums_next, B.phis, B.flag, first,         \
+                maps->zchunk, txs, tys, maps->items);                                                          \
         }
         if (maps->shape == 0) GB300_TMA(Shape0, 32, 8) else GB300_TMA(Shape1, 40, 7)
 #undef GB300_TMA
@@ -733,6 +897,57 @@ cudaError_t launch_fused(const DevParams& P, int precision, const StateBufs& B, 
     }
 #undef GB300_FUSED
     if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+int batch_tile_rows(int ty) { return ty == 4 ? 4 : kTY; }
+
+int batch_ctas_per_sm(int precision, int ty) {
+    int n = 0;
+#define GB300_OCC(S, TYV)                                                                                      \
+    {                                                                                                          \
+        using Sh = FusedShape<TYV>;                                                                            \
+        if (cudaFuncSetAttribute(k_fused_batch<S, TYV>, cudaFuncAttributeMaxDynamicSharedMemorySize,            \
+                                 (int)Sh::kSmemBytes) != cudaSuccess ||                                        \
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused_batch<S, TYV>, Sh::kThreads,             \
+                                                          Sh::kSmemBytes) != cudaSuccess)                      \
+            n = 0;                                                                                             \
+    }
+#define GB300_OCC_TY(S) { if (ty == 4) GB300_OCC(S, 4) else GB300_OCC(S, kTY) }
+    switch (precision) {
+    case 0: GB300_OCC_TY(float) break;
+    case 1: GB300_OCC_TY(__nv_bfloat16) break;
+    case 2: GB300_OCC_TY(__half) break;
+    }
+#undef GB300_OCC_TY
+#undef GB300_OCC
+    cudaGetLastError();
+    return n;
+}
+
+cudaError_t launch_fused_batch(const DevParams& P, int precision, int ty, const BatchInst* insts,
+                               const BatchItem* items, int n_items, int n_inst, const StateBufs& B,
+                               const double* sums_cur, double* sums_next, int first, int ctas, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+#define GB300_BATCH(S, TYV)                                                                                    \
+    {                                                                                                          \
+        using Sh = FusedShape<TYV>;                                                                            \
+        e = cudaFuncSetAttribute(k_fused_batch<S, TYV>, cudaFuncAttributeMaxDynamicSharedMemorySize,            \
+                                 (int)Sh::kSmemBytes);                                                         \
+        if (e != cudaSuccess) return e;                                                                        \
+        k_fused_batch<S, TYV><<<ctas, Sh::kThreads, Sh::kSmemBytes, s>>>(                                      \
+            P, insts, items, n_items, n_inst, (const S*)B.src, (S*)B.dst, B.pull_f, B.pull_g, sums_cur,        \
+            B.partial, B.counter, sums_next, B.phis, B.flag, first);                                           \
+    }
+#define GB300_BATCH_TY(S) { if (ty == 4) GB300_BATCH(S, 4) else GB300_BATCH(S, kTY) }
+    switch (precision) {
+    case 0: GB300_BATCH_TY(float) break;
+    case 1: GB300_BATCH_TY(__nv_bfloat16) break;
+    case 2: GB300_BATCH_TY(__half) break;
+    default: return cudaErrorInvalidValue;
+    }
+#undef GB300_BATCH_TY
+#undef GB300_BATCH
     return cudaGetLastError();
 }
 

@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(TPB) k_collide(DevParams P, const S* __restric
     float2 me = __ldg(psirho + d);
     Stencil st = stencil(P, psirho, x, y, z, n);
     float Fmx = me.x * st.Fx, Fmy = me.x * st.Fy, Fmz = me.x * st.Fz;
-    float rho_ave = (float)(sums_cur[0] * P.inv_N);
+    float rho_ave = buoyancy_ref(P, sums_cur[0], P.inv_N);
     float db = rho - rho_ave;
     float Fx = Fmx + db * P.gx, Fy = Fmy + db * P.gy, Fz = Fmz + db * P.gz;
     float Fm2 = Fmx * Fmx + Fmy * Fmy + Fmz * Fmz;
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(TPB) k_moments(DevParams P, const S* __restric
     float jz = (f[5] - f[6]) + (f[11] - f[12]) - (f[13] - f[14]) + (f[15] - f[16]) - (f[17] - f[18]);
     float2 me = __ldg(psirho + i);
     Stencil st = stencil(P, psirho, x, y, z, n);
-    float rho_ave = (float)(sums_cur[0] * P.inv_N);
+    float rho_ave = buoyancy_ref(P, sums_cur[0], P.inv_N);
     float db = rho - rho_ave;
     float Fx = me.x * st.Fx + db * P.gx, Fy = me.x * st.Fy + db * P.gy, Fz = me.x * st.Fz + db * P.gz;
     float inv = 1.f / rho;

@@ -33,10 +33,12 @@ cudaError_t launch_psi(const DevParams& P, int precision, const StateBufs& B, do
 cudaError_t launch_collide(const DevParams& P, int precision, const StateBufs& B,
                            const double* sums_cur, int first, cudaStream_t s);
 
-// Tensor maps of the two population buffers for the TMA variant (4D: x, y, z, slot; boxes of
-// 40 x 12 x 1 x 14 and 40 x 12 x 1 x 6 floats), and the number of SMs for its persistent grid.
+// Tensor maps of the two population buffers for the TMA variant (4D: x, y, z, slot): the load
+// windows (boxes (TX + 8) x (TY + 4) x 1 x 14 and x 6 over the padded storage) and the output
+// tile (box TX x TY x 1 x 26 over the real nodes only, so that stores stop at nx, ny); and the
+// number of SMs for its persistent grid.
 struct TmaMaps {
-    CUtensorMap m14[2], m6[2];
+    CUtensorMap m14[2], m6[2], mout[2];
     bool ok;
     int sms;
     int shape, zchunk, items;   // plan of tma_plan_for
@@ -55,6 +57,8 @@ void tma_plan_for(const DevParams& P, int ctas, int* shape, int* zchunk, int* it
 size_t tma_smem_bytes(int shape);
 int tma_box_w(int shape);
 int tma_box_h(int shape);
+int tma_tile_w(int shape);
+int tma_tile_h(int shape);
 
 // macroscopic moments (needs the psi pass on the same state first).
 cudaError_t launch_moments(const DevParams& P, int precision, const StateBufs& B,
@@ -66,5 +70,29 @@ cudaError_t launch_sum_field(const float* a, int n, double2* partial, unsigned* 
                              double* out, cudaStream_t s);
 
 int max_partials(const DevParams& P);
+
+// ---------------------------------------------------------------- batched ensemble
+// Geometry of one instance (device table).  Instance k owns elements [pop_off, pop_off + 26 Ns)
+// of each population buffer (same padded layout as a single lattice) and nodes
+// [field_off, field_off + N) of the dense fields; its items are item0 .. item0 + n_items - 1.
+struct BatchInst {
+    int nx, ny, nz, Ws, Hs;
+    int item0, n_items, pad_;
+    long long pop_off, field_off;
+    double inv_N;
+};
+// One work item: tile column (x0, y0) of 32 x TY nodes, planes [z0, z1) of instance inst.
+struct BatchItem {
+    int inst, x0, y0, z0, z1, pad_;
+};
+// Batched fused update.  B.counter points at two unsigned counters (work, ticket) that must be
+// zero before the first launch (every launch leaves them at zero); B.partial holds one double2
+// per item; sums_cur / sums_next hold (sum rho, sum T) per instance.  ty: tile rows (4 or 8).
+cudaError_t launch_fused_batch(const DevParams& P, int precision, int ty, const BatchInst* insts,
+                               const BatchItem* items, int n_items, int n_inst, const StateBufs& B,
+                               const double* sums_cur, double* sums_next, int first, int ctas, cudaStream_t s);
+// resident CTAs per SM of the batched kernel (0 if it cannot launch)
+int batch_ctas_per_sm(int precision, int ty);
+int batch_tile_rows(int ty);
 
 }  // namespace gb300lbm

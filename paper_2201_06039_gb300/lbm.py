@@ -34,7 +34,7 @@ class LbmParams(C.Structure):
         ("tau_e", C.c_double), ("tau_v", C.c_double), ("tau_q", C.c_double), ("tau_pi", C.c_double),
         ("cV", C.c_double), ("d", C.c_double), ("varsigma_q", C.c_double), ("varsigma_pi", C.c_double),
         ("lambda_mode", C.c_int), ("chi_or_lambda", C.c_double),
-        ("g", C.c_double * 3),
+        ("g", C.c_double * 3), ("rho_buoy", C.c_double),
         ("flow_off", C.c_int), ("thermal_off", C.c_int),
         ("precision", C.c_int), ("rho_ref", C.c_double), ("T_ref", C.c_double),
         ("kernel", C.c_int), ("use_graph", C.c_int), ("use_tma", C.c_int), ("check_nonfinite", C.c_int),
@@ -47,7 +47,10 @@ class LbmParams(C.Structure):
 EXPORTS = ["lbm_params_default", "lbm_eos_critical", "lbm_workspace_bytes", "lbm_create",
            "lbm_init_fields", "lbm_step", "lbm_get_moments", "lbm_get_totals", "lbm_steps_done",
            "lbm_kernel_in_use",
-           "lbm_step_profiled", "lbm_destroy", "lbm_status_str", "lbm_last_error", "lbm_field_sum_noalloc"]
+           "lbm_step_profiled", "lbm_destroy", "lbm_status_str", "lbm_last_error", "lbm_field_sum_noalloc",
+           "lbm_batch_create", "lbm_batch_nodes", "lbm_batch_init_fields", "lbm_batch_step", "lbm_batch_autotune",
+           "lbm_batch_plan", "lbm_batch_get_moments", "lbm_batch_get_totals", "lbm_batch_steps_done",
+           "lbm_batch_destroy"]
 
 _lib = None
 
@@ -95,6 +98,20 @@ def lib(build_if_missing: bool = True):
     L.lbm_field_sum_noalloc.argtypes = [vp, C.c_longlong, dp, vp]
     L.lbm_last_error.argtypes = []
     L.lbm_last_error.restype = C.c_char_p
+    ip = C.POINTER(C.c_int)
+    L.lbm_batch_create.argtypes = [P, C.c_int, ip, C.POINTER(vp)]
+    L.lbm_batch_nodes.argtypes = [vp, C.c_int]
+    L.lbm_batch_nodes.restype = C.c_longlong
+    L.lbm_batch_init_fields.argtypes = [vp, vp, vp, vp]
+    L.lbm_batch_step.argtypes = [vp, C.c_int]
+    L.lbm_batch_autotune.argtypes = [vp, C.c_int, dp]
+    L.lbm_batch_plan.argtypes = [vp, ip, ip, ip, ip]
+    L.lbm_batch_get_moments.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.lbm_batch_get_totals.argtypes = [vp, dp]
+    L.lbm_batch_steps_done.argtypes = [vp]
+    L.lbm_batch_steps_done.restype = C.c_longlong
+    L.lbm_batch_destroy.argtypes = [vp]
+    L.lbm_batch_destroy.restype = None
     _lib = L
     return L
 
@@ -190,6 +207,57 @@ def lbm_destroy(ctx):
         lib().lbm_destroy(ctx)
 
 
+def lbm_batch_create(common: LbmParams, dims):
+    """dims: sequence of (nx, ny, nz) per instance."""
+    flat = (C.c_int * (3 * len(dims)))(*[int(v) for d in dims for v in d])
+    b = C.c_void_p()
+    _check(lib().lbm_batch_create(C.byref(common), len(dims), flat, C.byref(b)), "lbm_batch_create")
+    return b
+
+
+def lbm_batch_nodes(b, instance: int = -1) -> int:
+    return lib().lbm_batch_nodes(b, instance)
+
+
+def lbm_batch_init_fields(b, rho, T, u=None):
+    _check(lib().lbm_batch_init_fields(b, _ptr(rho), _ptr(T), _ptr(u)), "lbm_batch_init_fields")
+
+
+def lbm_batch_step(b, n: int):
+    _check(lib().lbm_batch_step(b, n), "lbm_batch_step")
+
+
+def lbm_batch_autotune(b, steps: int) -> float:
+    ms = C.c_double()
+    _check(lib().lbm_batch_autotune(b, steps, C.byref(ms)), "lbm_batch_autotune")
+    return ms.value
+
+
+def lbm_batch_plan(b):
+    v = [C.c_int() for _ in range(4)]
+    _check(lib().lbm_batch_plan(b, *[C.byref(x) for x in v]), "lbm_batch_plan")
+    return dict(tile_rows=v[0].value, z_split=v[1].value, items=v[2].value, ctas=v[3].value)
+
+
+def lbm_batch_get_moments(b, rho=None, ux=None, uy=None, uz=None, T=None):
+    _check(lib().lbm_batch_get_moments(b, _ptr(rho), _ptr(ux), _ptr(uy), _ptr(uz), _ptr(T)), "lbm_batch_get_moments")
+
+
+def lbm_batch_get_totals(b, n_instances: int) -> np.ndarray:
+    out = np.zeros(2 * n_instances, dtype=np.float64)
+    _check(lib().lbm_batch_get_totals(b, out.ctypes.data_as(C.POINTER(C.c_double))), "lbm_batch_get_totals")
+    return out.reshape(n_instances, 2)
+
+
+def lbm_batch_steps_done(b) -> int:
+    return lib().lbm_batch_steps_done(b)
+
+
+def lbm_batch_destroy(b):
+    if b:
+        lib().lbm_batch_destroy(b)
+
+
 # ------------------------------------------------------------------- convenience
 def params_from_setup(setup, **overrides) -> LbmParams:
     """Map a workloads.LatticeSetup onto lbm_params (temperatures scaled by this library's Tc)."""
@@ -210,6 +278,7 @@ def params_from_setup(setup, **overrides) -> LbmParams:
     for k in range(3):
         p.g[k] = setup.gravity[k]
     p.flow_off, p.thermal_off = setup.flow_off, setup.thermal_off
+    p.rho_buoy = getattr(setup, "rho_buoy", 0.0)
     for k, v in overrides.items():
         setattr(p, k, v)
     return p
@@ -271,3 +340,60 @@ class Lattice:
     @property
     def steps_done(self):
         return lbm_steps_done(self.ctx)
+
+
+class Batch:
+    """Batched ensemble of independent lattices (same model constants, uneven sizes)."""
+
+    def __init__(self, common: LbmParams, dims, stream=None):
+        import torch
+        self.dims = [tuple(int(v) for v in d) for d in dims]
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        common.cuda_stream = self.stream.cuda_stream
+        common.workspace = None
+        common.workspace_bytes = 0
+        self.b = lbm_batch_create(common, self.dims)
+        self.sizes = [lbm_batch_nodes(self.b, k) for k in range(len(self.dims))]
+        self.N = lbm_batch_nodes(self.b, -1)
+
+    def close(self):
+        if getattr(self, "b", None):
+            lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, rho, T, u=None):
+        """rho, T: per-instance arrays (shape (nz, ny, nx)) or one concatenated float32 array."""
+        def cat(a):
+            if a is None or not isinstance(a, (list, tuple)):
+                return a if a is None or not isinstance(a, np.ndarray) else np.ascontiguousarray(a, np.float32)
+            return np.ascontiguousarray(np.concatenate([np.asarray(x, np.float32).ravel() for x in a]))
+        lbm_batch_init_fields(self.b, cat(rho), cat(T), cat(u))
+
+    def step(self, n: int = 1):
+        lbm_batch_step(self.b, n)
+
+    def autotune(self, steps: int = 3) -> float:
+        return lbm_batch_autotune(self.b, steps)
+
+    @property
+    def plan(self):
+        return lbm_batch_plan(self.b)
+
+    def moments(self):
+        """Per-instance dicts of host float32 arrays rho, ux, uy, uz, T (shape (nz, ny, nx))."""
+        flat = {k: np.empty(self.N, dtype=np.float32) for k in ("rho", "ux", "uy", "uz", "T")}
+        lbm_batch_get_moments(self.b, flat["rho"], flat["ux"], flat["uy"], flat["uz"], flat["T"])
+        out, off = [], 0
+        for (nx, ny, nz), n in zip(self.dims, self.sizes):
+            out.append({k: v[off:off + n].reshape(nz, ny, nx) for k, v in flat.items()})
+            off += n
+        return out
+
+    def totals(self):
+        return lbm_batch_get_totals(self.b, len(self.dims))

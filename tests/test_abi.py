@@ -88,3 +88,16 @@ def test_thermo_coexistence_agrees_with_paper():
     Tc = G.thermo.critical_temperature(2 / 49, 2 / 21, 1.0)
     rl, rv, _ = G.thermo.coexistence(0.86 * Tc)
     assert abs(rl - 6.5) < 0.05 and abs(rv - 0.38) < 0.005
+
+
+def test_batch_create_rejects_bad_instances_on_host():
+    import ctypes as C
+    p = G.lbm_params_default()
+    L = G.lib()
+    out = C.c_void_p()
+    dims = (C.c_int * 6)(24, 24, 24, 0, 5, 5)
+    assert L.lbm_batch_create(C.byref(p), 2, dims, C.byref(out)) == G.LBM_EINVAL
+    assert b"instance 1" in L.lbm_last_error()
+    assert L.lbm_batch_create(C.byref(p), 0, dims, C.byref(out)) == G.LBM_EINVAL
+    assert L.lbm_batch_create(C.byref(p), 1, None, C.byref(out)) == G.LBM_EINVAL
+    assert not out.value

@@ -1,0 +1,150 @@
+"""Batched ensemble (lbm_batch_*): independent lattices of uneven sizes in one persistent launch
+per step, against the FP64 oracle run on each instance alone, against single-lattice contexts,
+and for the autotuner's state restoration."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from tests._parity import bars, fp32_floor, inputs, rel_errors, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _cases():
+    """Droplets and slabs of ragged sizes and different temperatures (periodic boxes)."""
+    out = []
+    for k, (dims, kind, Tr, R) in enumerate([((24, 24, 24), "droplet", 0.86, 7.0),
+                                              ((29, 26, 31), "slab", 0.82, 6.0),
+                                              ((40, 33, 36), "droplet", 0.88, 9.0),
+                                              ((5, 3, 2), "slab", 0.86, 1.0),
+                                              ((33, 9, 17), "droplet", 0.84, 4.0)]):
+        s = W.LatticeSetup(*dims, sigma=W.SIGMA_STAR)
+        out.append(dict(name=f"inst{k}", setup=s, kind=kind, R0=R, W=4.0, Tr_drop=Tr, Tr_gas=Tr,
+                        noise=1e-3, noise_seed=W.MASTER_SEED + 77 + k))
+    return out
+
+
+def _batch(cases, **over):
+    from paper_2201_06039_gb300 import lbm
+    common = lbm.params_from_setup(cases[0]["setup"], **over)
+    return lbm.Batch(common, [(c["setup"].nx, c["setup"].ny, c["setup"].nz) for c in cases])
+
+
+def _fields(cases):
+    """Seeded fields of each case; boxes thinner than 4 nodes hold uniform vapour (+ noise)."""
+    rho, T = [], []
+    for c in cases:
+        r, t, _ = inputs(c)
+        s = c["setup"]
+        if min(s.nx, s.ny, s.nz) < 4:
+            rv = oracle.maxwell(s, c["Tr_drop"] * oracle.Tc_of(s))[1]
+            r = W.add_noise(np.full(s.shape, rv), c["noise_seed"], 1e-3).astype(np.float32).astype(np.float64)
+        rho.append(r)
+        T.append(t)
+    return rho, T
+
+
+def test_batch_matches_oracle_per_instance():
+    cases = _cases()
+    rho, T = _fields(cases)
+    steps = 200
+    b = _batch(cases)
+    b.init(rho, T)
+    b.step(steps)
+    got = b.moments()
+    b.close()
+    for c, r, t, g in zip(cases, rho, T, got):
+        ref = run_oracle(c["setup"], r, t, None, steps)
+        err = rel_errors(g, ref)
+        bar = bars(fp32_floor(c["setup"], r, t, None, steps, ref=ref))
+        print(c["name"], c["setup"].shape, err, bar)
+        for k, v in err.items():
+            assert v <= bar[k], (c["name"], k, v, bar[k])
+
+
+def test_batch_matches_single_lattices():
+    from paper_2201_06039_gb300 import lbm
+    cases = _cases()
+    rho, T = _fields(cases)
+    steps = 57
+    b = _batch(cases)
+    b.init(rho, T)
+    b.step(steps)
+    got = b.moments()
+    b.close()
+    for c, r, t, g in zip(cases, rho, T, got):
+        p = lbm.params_from_setup(c["setup"], kernel=2, use_tma=0)
+        lat = lbm.Lattice(p)
+        lat.init(r.astype(np.float32), t.astype(np.float32))
+        lat.step(steps)
+        m = lat.moments()
+        lat.close()
+        err = rel_errors(g, {k: v.astype(np.float64) for k, v in m.items()})
+        for k, v in err.items():
+            assert v <= 1e-6, (c["name"], k, v)
+
+
+def test_autotune_restores_state_and_keeps_results():
+    cases = _cases()
+    rho, T = _fields(cases)
+    b = _batch(cases)
+    b.init(rho, T)
+    b.step(5)
+    before = b.moments()
+    ms = b.autotune(2)
+    plan = b.plan
+    assert ms > 0 and plan["tile_rows"] in (4, 8) and plan["z_split"] in (1, 2, 4)
+    assert plan["items"] >= len(cases) and plan["ctas"] >= 1
+    after = b.moments()
+    for x, y in zip(before, after):
+        for k in x:
+            assert np.array_equal(x[k], y[k]), k
+    b.step(20)
+    tuned = b.moments()
+    b.close()
+    ref = _batch(cases)
+    ref.init(rho, T)
+    ref.step(25)
+    plain = ref.moments()
+    ref.close()
+    for x, y in zip(tuned, plain):
+        err = rel_errors(x, {k: v.astype(np.float64) for k, v in y.items()})
+        for k, v in err.items():
+            assert v <= 1e-6, (k, v)
+
+
+def test_batch_conserves_mass_per_instance():
+    cases = _cases()
+    rho, T = _fields(cases)
+    b = _batch(cases)
+    b.init(rho, T)
+    m0 = b.totals()[:, 0].copy()
+    b.step(300)
+    m1 = b.totals()[:, 0]
+    b.close()
+    rel = np.abs(m1 / m0 - 1.0)
+    assert np.all(rel < 1e-6), rel
+
+
+def test_batch_of_256_ensemble_instances_steps_finite():
+    """The 256-instance ensemble (edges 24..96) runs a few steps with finite totals and the
+    expected total node count."""
+    cases = W.batch_instances()
+    dims = [(c["setup"].nx, c["setup"].ny, c["setup"].nz) for c in cases]
+    total = sum(x * y * z for x, y, z in dims)
+    from paper_2201_06039_gb300 import lbm
+    b = lbm.Batch(lbm.params_from_setup(cases[0]["setup"]), dims)
+    assert b.N == total
+    Tc = oracle.Tc_of(cases[0]["setup"])
+    rho, T = [], []
+    for c in cases:
+        rl, rv, _ = oracle.maxwell(c["setup"], c["Tr_drop"] * Tc)
+        r, t, _ = W.build_fields(c, Tc, rl, rv)
+        rho.append(r)
+        T.append(t)
+    b.init(rho, T)
+    b.step(10)
+    tot = b.totals()
+    b.close()
+    assert np.all(np.isfinite(tot))

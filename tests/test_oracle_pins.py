@@ -52,6 +52,8 @@ def test_maxwell_coexistence_matches_paper():
     # equal pressures at the two roots
     assert abs(oracle.p_eos(s, rl, 0.86 * Tc) - ps) < 1e-12
     assert abs(oracle.p_eos(s, rv, 0.86 * Tc) - ps) < 1e-12
+    # the vapour reference density of the open-top pool-boiling preset is this root
+    assert abs(rv - W.RHO_V_086) < 1e-5
 
 
 def test_peng_robinson_critical_point():
@@ -269,6 +271,25 @@ def test_mass_and_momentum_conservation_periodic_two_phase():
     assert np.allclose(p0, 0, atol=1e-11)
 
 
+def test_fixed_buoyancy_reference_accelerates_uniform_box():
+    """F_b = (rho - rho_b) g with a fixed rho_b: a uniform periodic box (F_m = 0) gains total
+    momentum N (rho - rho_b) g per step (Eq. 3 adds F to the momentum); with the domain-mean
+    reference the same box feels no force."""
+    g = -2e-5
+    for rho_b, expect_per_step in ((0.2, None), (0.0, 0.0)):
+        s = W.LatticeSetup(6, 5, 4, sigma=0.11, gravity=(0.0, 0.0, g), rho_buoy=rho_b)
+        Tc = oracle.Tc_of(s)
+        rho0 = 0.38
+        o = oracle.Oracle(s)
+        o.init(np.full(s.shape, rho0), np.full(s.shape, 0.86 * Tc))
+        steps = 7
+        o.step(steps)
+        f, _ = o.pops()
+        pz = (f @ E19).sum(0)[2]
+        per_step = s.n_nodes * (rho0 - rho_b) * g if expect_per_step is None else expect_per_step
+        assert abs(pz - steps * per_step) < 1e-12 + 1e-9 * abs(steps * per_step), (rho_b, pz)
+
+
 def test_mass_conservation_bounce_back_box():
     """Eq. 50 walls on all faces: the closed box conserves mass exactly."""
     s = W.LatticeSetup(12, 10, 14, bc=(1, 1, 1, 1, 1, 1), sigma=0.11, gravity=(0, 0, -3e-5),
@@ -376,6 +397,18 @@ def test_flat_interface_coexistence_at_sigma_star():
     assert abs(r["err_l"]) < 0.02 and abs(r["err_v"]) < 0.02
     pv = paper()["coexistence_0.86Tc"]
     assert abs(r["rho_l"] - pv["rho_l"]) < 0.05 and abs(r["rho_v"] - pv["rho_g"]) < 0.01
+
+
+@pytest.mark.slow
+def test_flat_interface_coexistence_at_sigma_star_a_1_49():
+    """a = 1/49 (the paper's droplet tests, used by the ensemble): its own sigma* from the
+    committed calibration keeps the flat interface on Maxwell (<= 2%)."""
+    with open(os.path.join(GOLD, "sigma_calibration_a1_49.json")) as fh:
+        cal = json.load(fh)
+    assert cal["sigma_star"] == W.SIGMA_STAR_A1_49
+    from oracle.calibrate_sigma import flat_interface
+    r = flat_interface(W.SIGMA_STAR_A1_49, steps=20000, a=1.0 / 49.0)
+    assert abs(r["err_l"]) < 0.02 and abs(r["err_v"]) < 0.02
 
 
 @pytest.mark.slow
