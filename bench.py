@@ -59,6 +59,21 @@ def workload(name, nx=None, ny=None, nz=None):
     raise ValueError(name)
 
 
+def job_time_ms(ms_local, world, device="cuda"):
+    """The job's time: the maximum of the ranks' times (every rank gets it)."""
+    if world <= 1:
+        return float(ms_local)
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(nodes_per_rank, steps, world, ms):
+    """Node updates of all ranks divided by the job's time (replicas: weak scaling)."""
+    return nodes_per_rank * steps * world / (ms * 1e-3) / 1e6
+
+
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
@@ -291,13 +306,9 @@ def run_batch(args):
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = job_time_ms(e0.elapsed_time(e1), world)
     finite = bool(np.all(np.isfinite(bt.totals())))
-    mlups = N * args.steps * world / (ms * 1e-3) / 1e6
+    mlups = whole_job_mlups(N, args.steps, world, ms)
     peak, peak_kind = measured_peaks()
     k_ms = ms / args.steps          # one batched launch is the whole step
     achieved = BYTES_PER_NODE["fp32"] * N / (k_ms * 1e-3) / 1e9
@@ -316,7 +327,7 @@ def run_batch(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_once()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = job_time_ms((time.perf_counter() - t0) * 1e3, world) * 1e-3
     bt.close()
 
     # the same instances one after another through single-lattice contexts (FP32, own graphs)
@@ -356,7 +367,7 @@ def run_batch(args):
         "sequential": {"value": seq_mlups, "unit": "MLUPS", "steps": seq_steps,
                        "kernels": kernels, "what": "each instance alone through its own context"},
         "autotune_ms_per_step": tuned_ms,
-        "e2e": {"value": N * args.steps * world / e2e_s / 1e6, "unit": "MLUPS",
+        "e2e": {"value": whole_job_mlups(N, args.steps, world, e2e_s * 1e3), "unit": "MLUPS",
                 "h2d_bytes_per_step": 2 * 4 * N / args.steps, "d2h_bytes_per_step": 5 * 4 * N / args.steps},
         "gpu_launches": args.steps,
         "clocks": clocks,
@@ -446,14 +457,10 @@ def run_mine(args):
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = job_time_ms(e0.elapsed_time(e1), world)
     mass, Tsum, _ = lat.totals()
     finite = math.isfinite(mass) and math.isfinite(Tsum)
-    mlups = N * args.steps * world / (ms * 1e-3) / 1e6
+    mlups = whole_job_mlups(N, args.steps, world, ms)
 
     # ---- per-kernel durations (CUDA events on the lattice's stream) for the roofline
     kms, kn = lbm.lbm_step_profiled(lat.ctx, max(3, min(50, args.steps)))
@@ -478,15 +485,11 @@ def run_mine(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_once()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_mlups = N * args.steps * world / e2e_s / 1e6
+    e2e_s = job_time_ms((time.perf_counter() - t0) * 1e3, world) * 1e-3
+    e2e_mlups = whole_job_mlups(N, args.steps, world, e2e_s * 1e3)
 
-    # two-pass: psi/EOS + stream-collide; TMA: fused + ghost refresh; generic fused: one kernel
-    launches_per_step = 1 if kernel_name == "fused" else 2
+    # kernels per step as counted by the profiled steps (fused or psi + collide, ghost refresh)
+    launches_per_step = sum(kn) / max(3, min(50, args.steps))
     line = {
         "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,

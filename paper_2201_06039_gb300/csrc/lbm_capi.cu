@@ -259,8 +259,17 @@ int enqueue_step(lbm_ctx* c, double* kernel_ms = nullptr, int* launches = nullpt
     // in their un-streamed "fresh" form)
     c->cur ^= 1;
     if (c->maps.ok) {   // the TMA path reads ghost cells: refresh them in the state just written
+        if (ev) cudaEventRecord(ev[0], c->launch);
         e = launch_ghosts(c->dp, B.dst, c->launch);
         if (e != cudaSuccess) return fail(LBM_ECUDA, "ghost refresh launch: %s", cudaGetErrorString(e));
+        if (ev) {
+            cudaEventRecord(ev[1], c->launch);
+            cudaEventSynchronize(ev[1]);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[0], ev[1]);
+            kernel_ms[2] += ms;
+            launches[2] += 1;
+        }
     }
     if (!c->p.flow_off) c->fresh_f = false;
     if (!c->p.thermal_off) c->fresh_g = false;
@@ -356,10 +365,14 @@ bool make_tma_maps(lbm_ctx* c) {
     cuuint64_t strides[3] = {(cuuint64_t)d.Ws * 4, (cuuint64_t)d.splane * 4, (cuuint64_t)d.Ns * 4};
     const cuuint32_t bw = (cuuint32_t)tma_box_w(shape), bh = (cuuint32_t)tma_box_h(shape);
     cuuint32_t box14[4] = {bw, bh, 1, 14}, box6[4] = {bw, bh, 1, 6}, es[4] = {1, 1, 1, 1};
-    // output tiles: the real nodes only (x < nx, y < ny in storage coordinates + the offsets), so
-    // that the clipped edge tiles never write the ghost columns and rows
-    cuuint64_t dims_out[4] = {(cuuint64_t)(d.nx + kGX), (cuuint64_t)(d.ny + kGY), (cuuint64_t)d.nz, (cuuint64_t)kSlots};
-    cuuint32_t box_out[4] = {(cuuint32_t)tma_tile_w(shape), (cuuint32_t)tma_tile_h(shape), 1, (cuuint32_t)kSlots};
+    // output tiles, dimensions ordered (x, slot, y, z) to match the [row][slot][x] out buffer; the
+    // tensor spans the real nodes only (x < nx, y < ny in storage coordinates + the offsets), and
+    // the last tile row gets a box of exactly its rows, so no box ever extends past ny
+    const int th = tma_tile_h(shape), ry = d.ny - th * ((d.ny - 1) / th);
+    cuuint64_t dims_out[4] = {(cuuint64_t)(d.nx + kGX), (cuuint64_t)kSlots, (cuuint64_t)(d.ny + kGY), (cuuint64_t)d.nz};
+    cuuint64_t strides_out[3] = {(cuuint64_t)d.Ns * 4, (cuuint64_t)d.Ws * 4, (cuuint64_t)d.splane * 4};
+    cuuint32_t box_out[4] = {(cuuint32_t)tma_tile_w(shape), (cuuint32_t)kSlots, (cuuint32_t)th, 1};
+    cuuint32_t box_top[4] = {(cuuint32_t)tma_tile_w(shape), (cuuint32_t)kSlots, (cuuint32_t)ry, 1};
     for (int k = 0; k < 2; ++k) {
         void* g = c->pbuf(k);
         if (encode(&c->maps.m14[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, dims, strides, box14, es,
@@ -370,7 +383,11 @@ bool make_tma_maps(lbm_ctx* c) {
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;
-        if (encode(&c->maps.mout[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, dims_out, strides, box_out, es,
+        if (encode(&c->maps.mout[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, dims_out, strides_out, box_out, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+        if (encode(&c->maps.mout_top[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, dims_out, strides_out, box_top, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;

@@ -359,7 +359,8 @@ template <int TX_, int TY_> struct TmaShape {
     static constexpr int kWin = kWinW * kWinH;          // floats per population slot
     static constexpr int kStages = 3, kRing = 4;
     static constexpr size_t kStageBytes = (size_t)kStages * kSlots * kWin * sizeof(float);
-    // collided plane, slot-major [26][TY][TX]: source of one TMA tensor store per plane
+    // collided plane, row-major [TY][26][TX]: source of one TMA tensor store per plane (a box of
+    // fewer rows reads a prefix of it)
     static constexpr size_t kOutBytes = ((size_t)kSlots * kInterior * sizeof(float) + 127) / 128 * 128;
     static constexpr size_t kSmem = kStageBytes + kOutBytes +
                                     (size_t)kRing * kRingPlane * (sizeof(float2) + sizeof(float));
@@ -512,15 +513,16 @@ __device__ __forceinline__ void stage_pulls(const DevParams& P, const float* __r
 template <int TX_, int TY_>
 __global__ void __launch_bounds__(TmaShape<TX_, TY_>::kThreads, 1)
 k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ CUtensorMap map6,
-            const __grid_constant__ CUtensorMap map_out, DevParams P, const float* __restrict__ src,
-            const double* __restrict__ sums_cur, double2* partial, unsigned* counter, double* sums_next,
-            float* __restrict__ phis, int* flag, int first, int zchunk, int tiles_x, int tiles_y, int n_items) {
+            const __grid_constant__ CUtensorMap map_out, const __grid_constant__ CUtensorMap map_out_top,
+            DevParams P, const float* __restrict__ src, const double* __restrict__ sums_cur,
+            double2* partial, unsigned* counter, double* sums_next, float* __restrict__ phis, int* flag,
+            int first, int zchunk, int tiles_x, int tiles_y, int n_items) {
     using Sh = TmaShape<TX_, TY_>;
     constexpr int kWin = Sh::kWin, kWinW = Sh::kWinW, kStages = Sh::kStages, kRing = Sh::kRing;
     constexpr int kCol = Sh::kColThreads;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     float* stages = reinterpret_cast<float*>(smem_raw);                          // [3][26][TY+4][TX+8]
-    float* out = reinterpret_cast<float*>(smem_raw + Sh::kStageBytes);           // [26][TY][TX]
+    float* out = reinterpret_cast<float*>(smem_raw + Sh::kStageBytes);           // [TY][26][TX]
     float2* ring = reinterpret_cast<float2*>(smem_raw + Sh::kStageBytes + Sh::kOutBytes);  // [4][TY+2][TX+2]
     float* tring = reinterpret_cast<float*>(ring + kRing * Sh::kRingPlane);      // [4][TY+2][TX+2] T
     __shared__ __align__(8) unsigned long long full_bar[kStages], empty_bar[kStages], ring_full[kRing],
@@ -596,12 +598,14 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                 const int chunk = item / ntiles, tile = item % ntiles;
                 const int x0 = (tile % tiles_x) * TX_, y0 = (tile / tiles_x) * TY_;
                 const int z0 = chunk * zchunk, z1 = min(P.nz, z0 + zchunk);
+                // box (x, slot, y, z) at the tile origin (x a multiple of 4 floats); the last tile
+                // row uses the map whose box holds exactly its rows, so a box never reaches past
+                // ny; columns beyond nx fall outside the tensor and are not written
+                const CUtensorMap* m = y0 + TY_ > P.ny ? &map_out_top : &map_out;
                 for (int z = z0; z < z1; ++z, ++u) {
                     wait(&out_full, u & 1);
                     if (!abort_flag) {
-                        // the box starts at the tile origin (x a multiple of 4 floats); cells
-                        // beyond (nx, ny) fall outside the tensor and are not written
-                        tma_store_4d(&map_out, out, x0 + kGX, y0 + kGY, z, 0);
+                        tma_store_4d(m, out, x0 + kGX, 0, y0 + kGY, z);
                         bulk_commit();
                         bulk_wait_read_all();
                     }
@@ -657,6 +661,8 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                     tring[r * Sh::kRingPlane + roff[j]] = T;
                     bad |= !(psi2 > 0.f) || !isfinite(rho) || !isfinite(T);
                 }
+                // every lane's ring writes are complete before lane 0 signals the other warps
+                __threadfence_block();
                 __syncwarp();
                 if (lane == 0) {
                     mbar_arrive(&ring_full[r]);
@@ -673,7 +679,7 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
         const int slot = ly * Sh::kRingW + lx;
         const int woff = (ly + 1) * kWinW + lx + 3;
         const float rho_ave = buoyancy_ref(P, sums_cur[0], P.inv_N);
-        float* const outp = out + ct;
+        float* const outp = out + (ly - 1) * (kSlots * TX_) + (lx - 1);
         unsigned k = 0, u = 0;
         for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
             const int chunk = item / ntiles, tile = item % ntiles;
@@ -732,14 +738,15 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                 if (u > 0) wait(&out_empty, (u - 1) & 1);
                 if (owner) {
 #pragma unroll
-                    for (int a = 0; a < 19; ++a) outp[fslot(a) * Sh::kInterior] = f[a];
+                    for (int a = 0; a < 19; ++a) outp[fslot(a) * TX_] = f[a];
 #pragma unroll
-                    for (int a = 0; a < 7; ++a) outp[gslot(a) * Sh::kInterior] = g[a];
-                    phis[node_of(P, gx, gy, z)] = ph;   // ghosts: k_ghosts after the step
+                    for (int a = 0; a < 7; ++a) outp[gslot(a) * TX_] = g[a];
                 }
+                // every lane's out writes become visible to the tensor store before lane 0 signals
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&out_full);
+                if (owner) phis[node_of(P, gx, gy, z)] = ph;
                 ++u;
             }
             // stage of the item's last plane (psi only); ring planes z1-1 and z1
@@ -759,30 +766,45 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
 
 // Ghost refresh after a step on the TMA path: every ghost cell (columns -2, -1, nx, nx+1 over all
 // rows including the ghost rows, and rows -2, -1, ny, ny+1 over the real columns) receives the
-// stored populations of its periodic image.  One thread per copied element: column ghosts come in
-// adjacent pairs, row ghosts are coalesced along x.
+// stored populations of its periodic image.  Threads [0, nA): one (row, slot) each, copying the
+// column pairs (nx-2, nx-1) -> (-2, -1) and (0, 1) -> (nx, nx+1) (as float2 when nx is even);
+// threads [nA, nA + nB): one (ghost row, slot, 4-column group) each (as float4 when nx % 4 == 0).
 __global__ void __launch_bounds__(256) k_ghosts(DevParams P, float* __restrict__ pops) {
-    const int nA = (P.ny + 4) * kSlots * 4, nB = P.nx * kSlots * 4;
+    const int nA = (P.ny + 4) * kSlots;
+    const int groups = (P.nx + 3) / 4;
+    const int nB = 4 * kSlots * groups;
     const int t = blockIdx.x * 256 + threadIdx.x;
     const int z = blockIdx.y;
-    int gx, gy, a;
     if (t < nA) {
-        const int k = t & 3;
-        a = (t >> 2) % kSlots;
-        gy = (t >> 2) / kSlots - 2;
-        gx = k == 0 ? -2 : k == 1 ? -1 : k == 2 ? P.nx : P.nx + 1;
+        const int a = t % kSlots, gy = t / kSlots - 2;
+        const int iy = ((gy % P.ny) + P.ny) % P.ny;
+        float* base = pops + (size_t)a * P.Ns;
+        const int yrow = sidx(P, 0, gy, z), irow = sidx(P, 0, iy, z);
+        if ((P.nx & 1) == 0) {
+            const float2 hi = *reinterpret_cast<const float2*>(base + irow + P.nx - 2);
+            const float2 lo = *reinterpret_cast<const float2*>(base + irow);
+            *reinterpret_cast<float2*>(base + yrow - 2) = hi;
+            *reinterpret_cast<float2*>(base + yrow + P.nx) = lo;
+        } else {
+            const float h0 = base[irow + P.nx - 2], h1 = base[irow + P.nx - 1], l0 = base[irow], l1 = base[irow + 1];
+            base[yrow - 2] = h0;
+            base[yrow - 1] = h1;
+            base[yrow + P.nx] = l0;
+            base[yrow + P.nx + 1] = l1;
+        }
     } else if (t < nA + nB) {
         const int u = t - nA;
-        gx = u % P.nx;
-        a = (u / P.nx) % kSlots;
-        const int k = u / (P.nx * kSlots);
-        gy = k == 0 ? -2 : k == 1 ? -1 : k == 2 ? P.ny : P.ny + 1;
-    } else {
-        return;
+        const int q = u % groups, a = (u / groups) % kSlots, k = u / (groups * kSlots);
+        const int gy = k == 0 ? -2 : k == 1 ? -1 : k == 2 ? P.ny : P.ny + 1;
+        const int iy = ((gy % P.ny) + P.ny) % P.ny;
+        float* base = pops + (size_t)a * P.Ns;
+        const int dst = sidx(P, 4 * q, gy, z), src = sidx(P, 4 * q, iy, z);
+        if ((P.nx & 3) == 0) {
+            *reinterpret_cast<float4*>(base + dst) = *reinterpret_cast<const float4*>(base + src);
+        } else {
+            for (int c = 0; c < 4 && 4 * q + c < P.nx; ++c) base[dst + c] = base[src + c];
+        }
     }
-    const int ix = ((gx % P.nx) + P.nx) % P.nx, iy = ((gy % P.ny) + P.ny) % P.ny;
-    const size_t base = (size_t)a * P.Ns;
-    pops[base + sidx(P, gx, gy, z)] = pops[base + sidx(P, ix, iy, z)];
 }
 
 using Shape0 = TmaShape<32, 8>;
@@ -834,7 +856,7 @@ bool fused_supported(const DevParams& P) {
 }
 
 cudaError_t launch_ghosts(const DevParams& P, void* pops, cudaStream_t s) {
-    const int per_plane = ((P.ny + 4) + P.nx) * kSlots * 4;
+    const int per_plane = (P.ny + 4) * kSlots + 4 * kSlots * ((P.nx + 3) / 4);
     k_ghosts<<<dim3((per_plane + 255) / 256, P.nz), 256, 0, s>>>(P, (float*)pops);
     return cudaGetLastError();
 }
@@ -870,9 +892,9 @@ cudaError_t launch_fused(const DevParams& P, int precision, const StateBufs& B, 
                                      (int)SH::kSmem);                                                          \
             if (e != cudaSuccess) return e;                                                                    \
             k_fused_tma<TXV, TYV><<<ctas, SH::kThreads, SH::kSmem, s>>>(                                       \
-                maps->m14[B.src_index], maps->m6[B.src_index], maps->mout[B.src_index ^ 1], P,                 \
-                (const float*)B.src, sums_cur, B.partial, B.counter, sums_next, B.phis, B.flag, first,         \
-                maps->zchunk, txs, tys, maps->items);                                                          \
+                maps->m14[B.src_index], maps->m6[B.src_index], maps->mout[B.src_index ^ 1],                    \
+                maps->mout_top[B.src_index ^ 1], P, (const float*)B.src, sums_cur, B.partial, B.counter,      \
+                sums_next, B.phis, B.flag, first, maps->zchunk, txs, tys, maps->items);                        \
         }
         if (maps->shape == 0) GB300_TMA(Shape0, 32, 8) else GB300_TMA(Shape1, 40, 7)
 #undef GB300_TMA

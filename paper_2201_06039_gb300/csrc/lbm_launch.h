@@ -33,12 +33,12 @@ cudaError_t launch_psi(const DevParams& P, int precision, const StateBufs& B, do
 cudaError_t launch_collide(const DevParams& P, int precision, const StateBufs& B,
                            const double* sums_cur, int first, cudaStream_t s);
 
-// Tensor maps of the two population buffers for the TMA variant (4D: x, y, z, slot): the load
-// windows (boxes (TX + 8) x (TY + 4) x 1 x 14 and x 6 over the padded storage) and the output
-// tile (box TX x TY x 1 x 26 over the real nodes only, so that stores stop at nx, ny); and the
-// number of SMs for its persistent grid.
+// Tensor maps of the two population buffers for the TMA variant: the load windows (4D x, y, z,
+// slot; boxes (TX + 8) x (TY + 4) x 1 x 14 and x 6 over the padded storage) and the output tile
+// (4D x, slot, y, z over the real nodes only; boxes TX x 26 x TY x 1, and TX x 26 x (rows of the
+// last tile row) x 1 in mout_top); and the number of SMs for its persistent grid.
 struct TmaMaps {
-    CUtensorMap m14[2], m6[2], mout[2];
+    CUtensorMap m14[2], m6[2], mout[2], mout_top[2];
     bool ok;
     int sms;
     int shape, zchunk, items;   // plan of tma_plan_for

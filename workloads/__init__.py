@@ -200,7 +200,8 @@ def batch_instances(count: int = 256, seed: int = MASTER_SEED) -> List[Dict]:
     """Ensemble of periodic droplets (even i) and flat slabs (odd i) of uneven size.
 
     The EOS constant is a = 1/49, as in the paper's droplet tests (Sec. IV.A), with its own
-    calibrated sigma*.  (With a = 2/49 the larger droplets below 0.85 Tc diverge within 50 steps:
+    calibrated sigma*, and the initial tanh interface is 6 lattice units wide.  (With a = 2/49, or
+    with narrower initial interfaces, the larger droplets below 0.85 Tc diverge within 50 steps:
     the start-up compression wave converges on the droplet centre and the phase-change source
     amplifies it.)"""
     out = []
@@ -211,7 +212,7 @@ def batch_instances(count: int = 256, seed: int = MASTER_SEED) -> List[Dict]:
         R_frac = 0.20 + 0.15 * r[2]
         s = LatticeSetup(L, L, L, a=1.0 / 49.0, sigma=SIGMA_STAR_A1_49)
         out.append(dict(name=f"inst{i}", setup=s, kind="droplet" if i % 2 == 0 else "slab",
-                        R0=R_frac * L, W=4.0, Tr_drop=Tr, Tr_gas=Tr, noise=1e-3,
+                        R0=R_frac * L, W=6.0, Tr_drop=Tr, Tr_gas=Tr, noise=1e-3,
                         noise_seed=seed + 1000003 + i))
     return out
 
