@@ -223,10 +223,11 @@ void drop_graphs(lbm_ctx* c) {
 int enqueue_step(lbm_ctx* c, double* kernel_ms = nullptr, int* launches = nullptr, cudaEvent_t* ev = nullptr) {
     StateBufs B = c->bufs();
     cudaError_t e;
+    bool ghosts_done = false;
     if (c->variant == LBM_KERNEL_FUSED) {
         if (ev) cudaEventRecord(ev[0], c->launch);
         e = launch_fused(c->dp, c->p.precision, B, c->sums(c->slot), c->sums(c->slot ^ 1), c->first ? 1 : 0,
-                         c->launch, c->maps.ok ? &c->maps : nullptr);
+                         c->launch, c->maps.ok ? &c->maps : nullptr, &ghosts_done);
         if (e != cudaSuccess) return fail(LBM_ECUDA, "fused kernel launch: %s", cudaGetErrorString(e));
         if (ev) {
             cudaEventRecord(ev[1], c->launch);
@@ -258,7 +259,7 @@ int enqueue_step(lbm_ctx* c, double* kernel_ms = nullptr, int* launches = nullpt
     // both fields are written every step (frozen ones copied through unchanged, so they stay
     // in their un-streamed "fresh" form)
     c->cur ^= 1;
-    if (c->maps.ok) {   // the TMA path reads ghost cells: refresh them in the state just written
+    if (c->maps.ok && !ghosts_done) {   // the TMA path reads ghost cells: refresh them in the state just written
         if (ev) cudaEventRecord(ev[0], c->launch);
         e = launch_ghosts(c->dp, B.dst, c->launch);
         if (e != cudaSuccess) return fail(LBM_ECUDA, "ghost refresh launch: %s", cudaGetErrorString(e));
@@ -373,6 +374,15 @@ bool make_tma_maps(lbm_ctx* c) {
     cuuint64_t strides_out[3] = {(cuuint64_t)d.Ns * 4, (cuuint64_t)d.Ws * 4, (cuuint64_t)d.splane * 4};
     cuuint32_t box_out[4] = {(cuuint32_t)tma_tile_w(shape), (cuuint32_t)kSlots, (cuuint32_t)th, 1};
     cuuint32_t box_top[4] = {(cuuint32_t)tma_tile_w(shape), (cuuint32_t)kSlots, (cuuint32_t)ry, 1};
+    // ghost boxes over the whole padded plane (they always lie inside it)
+    const int tw = tma_tile_w(shape), rx = d.nx - tw * ((d.nx - 1) / tw);
+    cuuint64_t dims_pad[4] = {(cuuint64_t)d.Ws, (cuuint64_t)kSlots, (cuuint64_t)d.Hs, (cuuint64_t)d.nz};
+    cuuint32_t box_gcol[4] = {4, (cuuint32_t)kSlots, (cuuint32_t)th, 1};
+    cuuint32_t box_gcol_top[4] = {4, (cuuint32_t)kSlots, (cuuint32_t)ry, 1};
+    cuuint32_t box_grow[4] = {(cuuint32_t)tw, (cuuint32_t)kSlots, 2, 1};
+    cuuint32_t box_grow_right[4] = {(cuuint32_t)rx, (cuuint32_t)kSlots, 2, 1};
+    cuuint32_t box_gcor[4] = {4, (cuuint32_t)kSlots, 2, 1};
+    c->maps.ghosts = tma_ghosts_in_kernel(d, shape);
     for (int k = 0; k < 2; ++k) {
         void* g = c->pbuf(k);
         if (encode(&c->maps.m14[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, dims, strides, box14, es,
@@ -391,6 +401,16 @@ bool make_tma_maps(lbm_ctx* c) {
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;
+        if (c->maps.ghosts) {
+            CUtensorMap* gm[5] = {&c->maps.mgcol[k], &c->maps.mgcol_top[k], &c->maps.mgrow[k], &c->maps.mgrow_right[k],
+                                  &c->maps.mgcor[k]};
+            cuuint32_t* gb[5] = {box_gcol, box_gcol_top, box_grow, box_grow_right, box_gcor};
+            for (int q = 0; q < 5; ++q)
+                if (encode(gm[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, dims_pad, strides_out, gb[q], es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                    c->maps.ghosts = false;
+        }
     }
     c->maps.sms = sms;
     c->maps.shape = shape;

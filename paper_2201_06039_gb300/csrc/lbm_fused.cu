@@ -358,11 +358,19 @@ template <int TX_, int TY_> struct TmaShape {
     static constexpr int kWinH = TY_ + 4;               // window rows    y0-2 .. y0+TY+1
     static constexpr int kWin = kWinW * kWinH;          // floats per population slot
     static constexpr int kStages = 3, kRing = 4;
+    static constexpr int kPrefetch = 2;                 // planes between an L2 prefetch and its load
     static constexpr size_t kStageBytes = (size_t)kStages * kSlots * kWin * sizeof(float);
     // collided plane, row-major [TY][26][TX]: source of one TMA tensor store per plane (a box of
     // fewer rows reads a prefix of it)
     static constexpr size_t kOutBytes = ((size_t)kSlots * kInterior * sizeof(float) + 127) / 128 * 128;
-    static constexpr size_t kSmem = kStageBytes + kOutBytes +
+    // periodic images of an edge tile, tensor-stored into the ghost cells: 4 edge columns
+    // [TY][26][4], 2 edge rows [2][26][w] (w = the tile's real columns), and the 4 x 2 corner
+    // block [2][26][4]; each is laid out exactly as the box that stores it
+    static constexpr size_t kGColBytes = ((size_t)TY_ * kSlots * 4 * sizeof(float) + 127) / 128 * 128;
+    static constexpr size_t kGRowBytes = ((size_t)2 * kSlots * TX_ * sizeof(float) + 127) / 128 * 128;
+    static constexpr size_t kGCorBytes = ((size_t)2 * kSlots * 4 * sizeof(float) + 127) / 128 * 128;
+    static constexpr size_t kGhostBytes = kGColBytes + kGRowBytes + kGCorBytes;
+    static constexpr size_t kSmem = kStageBytes + kOutBytes + kGhostBytes +
                                     (size_t)kRing * kRingPlane * (sizeof(float2) + sizeof(float));
     static_assert(kStageBytes % 128 == 0, "TMA destinations must stay 128-byte aligned");
     static_assert(kPsiPerThread <= 2, "psi threads hold at most two ring slots");
@@ -423,6 +431,14 @@ __device__ __forceinline__ void tma_load_4d(float* smem_dst, const CUtensorMap* 
         "%5}], [%6];" ::"r"(smem_u32(smem_dst)),
         "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
         : "memory");
+}
+
+// prefetch of a tensor box into L2 (no shared memory, no completion signal)
+__device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap* map, int c0, int c1, int c2, int c3) {
+    asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(
+                     reinterpret_cast<unsigned long long>(map)),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+                 : "memory");
 }
 
 // tensor store of a shared-memory box (bulk async-group completion); the box is clipped at the
@@ -514,16 +530,22 @@ template <int TX_, int TY_>
 __global__ void __launch_bounds__(TmaShape<TX_, TY_>::kThreads, 1)
 k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ CUtensorMap map6,
             const __grid_constant__ CUtensorMap map_out, const __grid_constant__ CUtensorMap map_out_top,
-            DevParams P, const float* __restrict__ src, const double* __restrict__ sums_cur,
-            double2* partial, unsigned* counter, double* sums_next, float* __restrict__ phis, int* flag,
-            int first, int zchunk, int tiles_x, int tiles_y, int n_items) {
+            const __grid_constant__ CUtensorMap map_gcol, const __grid_constant__ CUtensorMap map_gcol_top,
+            const __grid_constant__ CUtensorMap map_grow, const __grid_constant__ CUtensorMap map_grow_right,
+            const __grid_constant__ CUtensorMap map_gcor, int ghosts, DevParams P, const float* __restrict__ src,
+            const double* __restrict__ sums_cur, double2* partial, unsigned* counter, double* sums_next,
+            float* __restrict__ phis, int* flag, int first, int zchunk, int tiles_x, int tiles_y, int n_items) {
     using Sh = TmaShape<TX_, TY_>;
     constexpr int kWin = Sh::kWin, kWinW = Sh::kWinW, kStages = Sh::kStages, kRing = Sh::kRing;
-    constexpr int kCol = Sh::kColThreads;
+    constexpr int kCol = Sh::kColThreads, kPrefetch = Sh::kPrefetch;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     float* stages = reinterpret_cast<float*>(smem_raw);                          // [3][26][TY+4][TX+8]
     float* out = reinterpret_cast<float*>(smem_raw + Sh::kStageBytes);           // [TY][26][TX]
-    float2* ring = reinterpret_cast<float2*>(smem_raw + Sh::kStageBytes + Sh::kOutBytes);  // [4][TY+2][TX+2]
+    float* gcol = reinterpret_cast<float*>(smem_raw + Sh::kStageBytes + Sh::kOutBytes);          // [TY][26][4]
+    float* grow = reinterpret_cast<float*>(smem_raw + Sh::kStageBytes + Sh::kOutBytes + Sh::kGColBytes);  // [2][26][TX]
+    float* gcor = reinterpret_cast<float*>(smem_raw + Sh::kStageBytes + Sh::kOutBytes + Sh::kGColBytes +
+                                           Sh::kGRowBytes);                      // [2][26][4]
+    float2* ring = reinterpret_cast<float2*>(smem_raw + Sh::kStageBytes + Sh::kOutBytes + Sh::kGhostBytes);  // [4][TY+2][TX+2]
     float* tring = reinterpret_cast<float*>(ring + kRing * Sh::kRingPlane);      // [4][TY+2][TX+2] T
     __shared__ __align__(8) unsigned long long full_bar[kStages], empty_bar[kStages], ring_full[kRing],
         ring_empty[kRing], out_full, out_empty;
@@ -583,6 +605,16 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                     tma_load_4d(st, &map14, cx, cy, mz, 0, &full_bar[s]);
                     if (zu >= 0) tma_load_4d(st + 14 * kWin, &map6, cx, cy, zu, 14, &full_bar[s]);
                     if (zd >= 0) tma_load_4d(st + 20 * kWin, &map6, cx, cy, zd, 20, &full_bar[s]);
+                    // pull the window of a plane kPrefetch ahead into L2, so that its load into a
+                    // stage (issued once a stage frees) waits on L2 rather than on DRAM
+                    const int pf = p + kPrefetch;
+                    if (pf <= z1) {
+                        const int fz = map_coord(pf, P.nz, P.bc[4], P.bc[5]);
+                        const int fu = src_plane_up(P, fz), fd = src_plane_dn(P, fz);
+                        tma_prefetch_4d(&map14, cx, cy, fz, 0);
+                        if (fu >= 0) tma_prefetch_4d(&map6, cx, cy, fu, 14);
+                        if (fd >= 0) tma_prefetch_4d(&map6, cx, cy, fd, 20);
+                    }
                 }
             }
             // copies still in flight must land before the CTA exits (bounded)
@@ -602,10 +634,22 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                 // row uses the map whose box holds exactly its rows, so a box never reaches past
                 // ny; columns beyond nx fall outside the tensor and are not written
                 const CUtensorMap* m = y0 + TY_ > P.ny ? &map_out_top : &map_out;
+                // ghost cells written from this tile (storage coordinates; every box lies inside
+                // the padded plane exactly): its 4 edge columns to the opposite ghost columns, its
+                // 2 edge rows to the opposite ghost rows, and the corner block
+                const bool left = ghosts && x0 == 0, right = ghosts && x0 + TX_ >= P.nx;
+                const bool bottom = ghosts && y0 == 0, top = ghosts && y0 + TY_ >= P.ny;
+                const int gx_col = right ? kGX - 4 : P.nx + kGX;      // destination of the column box
+                const int gy_row = top ? kGY - 2 : P.ny + kGY;        // destination of the row box
+                const CUtensorMap* mc = y0 + TY_ > P.ny ? &map_gcol_top : &map_gcol;
+                const CUtensorMap* mr = x0 + TX_ > P.nx ? &map_grow_right : &map_grow;
                 for (int z = z0; z < z1; ++z, ++u) {
                     wait(&out_full, u & 1);
                     if (!abort_flag) {
                         tma_store_4d(m, out, x0 + kGX, 0, y0 + kGY, z);
+                        if (left || right) tma_store_4d(mc, gcol, gx_col, 0, y0 + kGY, z);
+                        if (top || bottom) tma_store_4d(mr, grow, x0 + kGX, 0, gy_row, z);
+                        if ((left || right) && (top || bottom)) tma_store_4d(&map_gcor, gcor, gx_col, 0, gy_row, z);
                         bulk_commit();
                         bulk_wait_read_all();
                     }
@@ -687,6 +731,15 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
             const int z0 = chunk * zchunk, z1 = min(P.nz, z0 + zchunk);
             const int gx = x0 + lx - 1, gy = y0 + ly - 1;
             const bool owner = node_thread && gx < P.nx && gy < P.ny;
+            // this node's place in the ghost staging tiles of an edge tile (-1: none)
+            const bool eright = ghosts && x0 + TX_ >= P.nx, eleft = ghosts && x0 == 0;
+            const bool etop = ghosts && y0 + TY_ >= P.ny, ebottom = ghosts && y0 == 0;
+            const int cx4 = !owner ? -1 : eright ? (gx >= P.nx - 4 ? gx - (P.nx - 4) : -1)
+                                        : eleft ? (gx < 4 ? gx : -1) : -1;
+            const int ry2 = !owner ? -1 : etop ? (gy >= P.ny - 2 ? gy - (P.ny - 2) : -1)
+                                        : ebottom ? (gy < 2 ? gy : -1) : -1;
+            // the edge-row tile is as wide as the tile's real columns (the box reads it densely)
+            const int rw = min(TX_, P.nx - x0);
             float r_sum = 0.f, r_c = 0.f, t_sum = 0.f, t_c = 0.f;
             // phi_s history of the thread's node, loaded one plane ahead of its use
             float ph_next = owner ? phis[node_of(P, gx, gy, z0)] : 0.f;
@@ -741,6 +794,27 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                     for (int a = 0; a < 19; ++a) outp[fslot(a) * TX_] = f[a];
 #pragma unroll
                     for (int a = 0; a < 7; ++a) outp[gslot(a) * TX_] = g[a];
+                    if (cx4 >= 0) {   // edge column: [TY][26][4]
+                        float* q = gcol + (ly - 1) * (kSlots * 4) + cx4;
+#pragma unroll
+                        for (int a = 0; a < 19; ++a) q[fslot(a) * 4] = f[a];
+#pragma unroll
+                        for (int a = 0; a < 7; ++a) q[gslot(a) * 4] = g[a];
+                    }
+                    if (ry2 >= 0) {   // edge row: [2][26][rw]
+                        float* q = grow + ry2 * (kSlots * rw) + (lx - 1);
+#pragma unroll
+                        for (int a = 0; a < 19; ++a) q[fslot(a) * rw] = f[a];
+#pragma unroll
+                        for (int a = 0; a < 7; ++a) q[gslot(a) * rw] = g[a];
+                    }
+                    if (cx4 >= 0 && ry2 >= 0) {   // corner block: [2][26][4]
+                        float* q = gcor + ry2 * (kSlots * 4) + cx4;
+#pragma unroll
+                        for (int a = 0; a < 19; ++a) q[fslot(a) * 4] = f[a];
+#pragma unroll
+                        for (int a = 0; a < 7; ++a) q[gslot(a) * 4] = g[a];
+                    }
                 }
                 // every lane's out writes become visible to the tensor store before lane 0 signals
                 fence_proxy_async_smem();
@@ -875,17 +949,26 @@ void tma_plan_for(const DevParams& P, int ctas, int* shape, int* zchunk, int* it
 int tma_box_w(int shape) { return shape == 0 ? Shape0::kWinW : Shape1::kWinW; }
 int tma_box_h(int shape) { return shape == 0 ? Shape0::kWinH : Shape1::kWinH; }
 int tma_tile_w(int shape) { return shape == 0 ? 32 : 40; }
+bool tma_ghosts_in_kernel(const DevParams& P, int shape) {
+    const int tx = tma_tile_w(shape), ty = shape == 0 ? 8 : 7;
+    // 4-column boxes on 16-byte boundaries, at least two tiles per axis (an edge tile is never
+    // both left and right, top and bottom), edge tiles at least 4 columns and 2 rows wide, and
+    // room for the 4 ghost columns past nx in the padded rows
+    return P.nx % 4 == 0 && P.nx > tx && P.ny > ty && P.ny % ty != 1 && P.Ws >= P.nx + kGX + 4;
+}
 int tma_tile_h(int shape) { return shape == 0 ? 8 : 7; }
 
 cudaError_t launch_fused(const DevParams& P, int precision, const StateBufs& B, const double* sums_cur,
-                         double* sums_next, int first, cudaStream_t s, const TmaMaps* maps) {
+                         double* sums_next, int first, cudaStream_t s, const TmaMaps* maps, bool* ghosts_written) {
     using Sh = FusedShape<kTY>;
     const int tiles_x = (P.nx + TX - 1) / TX, tiles_y = (P.ny + kTY - 1) / kTY;
     cudaError_t e = cudaSuccess;
+    if (ghosts_written) *ghosts_written = false;
     if (maps && maps->ok && B.pull_f && B.pull_g && tma_eligible(P, precision)) {
         const int tx = maps->shape == 0 ? 32 : 40, ty = maps->shape == 0 ? 8 : 7;
         const int txs = (P.nx + tx - 1) / tx, tys = (P.ny + ty - 1) / ty;
         const int ctas = maps->sms < maps->items ? maps->sms : maps->items;
+        if (ghosts_written) *ghosts_written = maps->ghosts;
 #define GB300_TMA(SH, TXV, TYV)                                                                                \
         {                                                                                                      \
             e = cudaFuncSetAttribute(k_fused_tma<TXV, TYV>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
@@ -893,8 +976,10 @@ cudaError_t launch_fused(const DevParams& P, int precision, const StateBufs& B, 
             if (e != cudaSuccess) return e;                                                                    \
             k_fused_tma<TXV, TYV><<<ctas, SH::kThreads, SH::kSmem, s>>>(                                       \
                 maps->m14[B.src_index], maps->m6[B.src_index], maps->mout[B.src_index ^ 1],                    \
-                maps->mout_top[B.src_index ^ 1], P, (const float*)B.src, sums_cur, B.partial, B.counter,      \
-                sums_next, B.phis, B.flag, first, maps->zchunk, txs, tys, maps->items);                        \
+                maps->mout_top[B.src_index ^ 1], maps->mgcol[B.src_index ^ 1], maps->mgcol_top[B.src_index ^ 1], \
+                maps->mgrow[B.src_index ^ 1], maps->mgrow_right[B.src_index ^ 1], maps->mgcor[B.src_index ^ 1], \
+                maps->ghosts ? 1 : 0, P, (const float*)B.src, sums_cur, B.partial, B.counter, sums_next, B.phis, \
+                B.flag, first, maps->zchunk, txs, tys, maps->items);                                           \
         }
         if (maps->shape == 0) GB300_TMA(Shape0, 32, 8) else GB300_TMA(Shape1, 40, 7)
 #undef GB300_TMA

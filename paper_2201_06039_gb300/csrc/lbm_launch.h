@@ -39,6 +39,11 @@ cudaError_t launch_collide(const DevParams& P, int precision, const StateBufs& B
 // last tile row) x 1 in mout_top); and the number of SMs for its persistent grid.
 struct TmaMaps {
     CUtensorMap m14[2], m6[2], mout[2], mout_top[2];
+    // ghost stores (4D x, slot, y, z over the whole padded plane): edge-column box 4 x 26 x TY (and
+    // x rows of the last tile row), edge-row box TX x 26 x 2 (and x columns of the last tile
+    // column), corner box 4 x 26 x 2
+    CUtensorMap mgcol[2], mgcol_top[2], mgrow[2], mgrow_right[2], mgcor[2];
+    bool ghosts;   // the TMA kernel writes the ghost cells itself (no refresh kernel)
     bool ok;
     int sms;
     int shape, zchunk, items;   // plan of tma_plan_for
@@ -46,8 +51,10 @@ struct TmaMaps {
 
 // fused z-marching variant (psi of the tile halo recomputed from the populations); uses the
 // TMA kernel when maps are given and the lattice / state qualify (see tma_eligible).
+// *ghosts_written (nullable) tells whether the launch also refreshed the ghost cells of dst.
 cudaError_t launch_fused(const DevParams& P, int precision, const StateBufs& B, const double* sums_cur,
-                         double* sums_next, int first, cudaStream_t s, const TmaMaps* maps);
+                         double* sums_next, int first, cudaStream_t s, const TmaMaps* maps,
+                         bool* ghosts_written = nullptr);
 bool fused_supported(const DevParams& P);
 bool tma_eligible(const DevParams& P, int precision);
 // refresh the ghost columns / rows of a population buffer from their periodic images (FP32)
@@ -58,6 +65,7 @@ size_t tma_smem_bytes(int shape);
 int tma_box_w(int shape);
 int tma_box_h(int shape);
 int tma_tile_w(int shape);
+bool tma_ghosts_in_kernel(const DevParams& P, int shape);
 int tma_tile_h(int shape);
 
 // macroscopic moments (needs the psi pass on the same state first).
