@@ -261,7 +261,7 @@ int enqueue_step(lbm_ctx* c, double* kernel_ms = nullptr, int* launches = nullpt
     c->cur ^= 1;
     if (c->maps.ok && !ghosts_done) {   // the TMA path reads ghost cells: refresh them in the state just written
         if (ev) cudaEventRecord(ev[0], c->launch);
-        e = launch_ghosts(c->dp, B.dst, c->launch);
+        e = launch_ghosts(c->dp, c->p.precision, B.dst, c->launch);
         if (e != cudaSuccess) return fail(LBM_ECUDA, "ghost refresh launch: %s", cudaGetErrorString(e));
         if (ev) {
             cudaEventRecord(ev[1], c->launch);
@@ -351,7 +351,7 @@ bool make_tma_maps(lbm_ctx* c) {
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
     int shape, zchunk, items;
     tma_plan_for(c->dp, sms, &shape, &zchunk, &items);
-    if ((size_t)optin < tma_smem_bytes(shape)) return false;
+    if ((size_t)optin < tma_smem_bytes(shape, c->p.precision)) return false;
     if (items > max_partials(c->dp)) return false;
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -363,41 +363,46 @@ bool make_tma_maps(lbm_ctx* c) {
     EncodeTiledFn encode = (EncodeTiledFn)fn;
     const DevParams& d = c->dp;
     cuuint64_t dims[4] = {(cuuint64_t)d.Ws, (cuuint64_t)d.Hs, (cuuint64_t)d.nz, (cuuint64_t)kSlots};
-    cuuint64_t strides[3] = {(cuuint64_t)d.Ws * 4, (cuuint64_t)d.splane * 4, (cuuint64_t)d.Ns * 4};
-    const cuuint32_t bw = (cuuint32_t)tma_box_w(shape), bh = (cuuint32_t)tma_box_h(shape);
+    const cuuint64_t E = (cuuint64_t)pop_bytes(c->p.precision);
+    const CUtensorMapDataType dt = c->p.precision == LBM_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : c->p.precision == LBM_BF16_SHIFTED ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    cuuint64_t strides[3] = {(cuuint64_t)d.Ws * E, (cuuint64_t)d.splane * E, (cuuint64_t)d.Ns * E};
+    const cuuint32_t bw = (cuuint32_t)tma_box_w(shape, c->p.precision), bh = (cuuint32_t)tma_box_h(shape);
     cuuint32_t box14[4] = {bw, bh, 1, 14}, box6[4] = {bw, bh, 1, 6}, es[4] = {1, 1, 1, 1};
     // output tiles, dimensions ordered (x, slot, y, z) to match the [row][slot][x] out buffer; the
     // tensor spans the real nodes only (x < nx, y < ny in storage coordinates + the offsets), and
     // the last tile row gets a box of exactly its rows, so no box ever extends past ny
     const int th = tma_tile_h(shape), ry = d.ny - th * ((d.ny - 1) / th);
     cuuint64_t dims_out[4] = {(cuuint64_t)(d.nx + kGX), (cuuint64_t)kSlots, (cuuint64_t)(d.ny + kGY), (cuuint64_t)d.nz};
-    cuuint64_t strides_out[3] = {(cuuint64_t)d.Ns * 4, (cuuint64_t)d.Ws * 4, (cuuint64_t)d.splane * 4};
+    cuuint64_t strides_out[3] = {(cuuint64_t)d.Ns * E, (cuuint64_t)d.Ws * E, (cuuint64_t)d.splane * E};
     cuuint32_t box_out[4] = {(cuuint32_t)tma_tile_w(shape), (cuuint32_t)kSlots, (cuuint32_t)th, 1};
     cuuint32_t box_top[4] = {(cuuint32_t)tma_tile_w(shape), (cuuint32_t)kSlots, (cuuint32_t)ry, 1};
     // ghost boxes over the whole padded plane (they always lie inside it)
     const int tw = tma_tile_w(shape), rx = d.nx - tw * ((d.nx - 1) / tw);
     cuuint64_t dims_pad[4] = {(cuuint64_t)d.Ws, (cuuint64_t)kSlots, (cuuint64_t)d.Hs, (cuuint64_t)d.nz};
-    cuuint32_t box_gcol[4] = {4, (cuuint32_t)kSlots, (cuuint32_t)th, 1};
-    cuuint32_t box_gcol_top[4] = {4, (cuuint32_t)kSlots, (cuuint32_t)ry, 1};
+    const cuuint32_t gw = (cuuint32_t)tma_ghost_cols(c->p.precision);
+    cuuint32_t box_gcol[4] = {gw, (cuuint32_t)kSlots, (cuuint32_t)th, 1};
+    cuuint32_t box_gcol_top[4] = {gw, (cuuint32_t)kSlots, (cuuint32_t)ry, 1};
     cuuint32_t box_grow[4] = {(cuuint32_t)tw, (cuuint32_t)kSlots, 2, 1};
     cuuint32_t box_grow_right[4] = {(cuuint32_t)rx, (cuuint32_t)kSlots, 2, 1};
-    cuuint32_t box_gcor[4] = {4, (cuuint32_t)kSlots, 2, 1};
-    c->maps.ghosts = tma_ghosts_in_kernel(d, shape);
+    cuuint32_t box_gcor[4] = {gw, (cuuint32_t)kSlots, 2, 1};
+    c->maps.ghosts = tma_ghosts_in_kernel(d, shape, c->p.precision);
     for (int k = 0; k < 2; ++k) {
         void* g = c->pbuf(k);
-        if (encode(&c->maps.m14[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, dims, strides, box14, es,
+        if (encode(&c->maps.m14[k], dt, 4, g, dims, strides, box14, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;
-        if (encode(&c->maps.m6[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, dims, strides, box6, es,
+        if (encode(&c->maps.m6[k], dt, 4, g, dims, strides, box6, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;
-        if (encode(&c->maps.mout[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, dims_out, strides_out, box_out, es,
+        if (encode(&c->maps.mout[k], dt, 4, g, dims_out, strides_out, box_out, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;
-        if (encode(&c->maps.mout_top[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, dims_out, strides_out, box_top, es,
+        if (encode(&c->maps.mout_top[k], dt, 4, g, dims_out, strides_out, box_top, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;
@@ -406,7 +411,7 @@ bool make_tma_maps(lbm_ctx* c) {
                                   &c->maps.mgcor[k]};
             cuuint32_t* gb[5] = {box_gcol, box_gcol_top, box_grow, box_grow_right, box_gcor};
             for (int q = 0; q < 5; ++q)
-                if (encode(gm[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, g, dims_pad, strides_out, gb[q], es,
+                if (encode(gm[q], dt, 4, g, dims_pad, strides_out, gb[q], es,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
                     c->maps.ghosts = false;
@@ -525,7 +530,7 @@ int lbm_init_fields(lbm_ctx* c, const float* rho, const float* T, const float* u
     c->cur = 0;
     c->slot = 0;
     CK(launch_init(c->dp, c->p.precision, c->pbuf(0), drho, dT, du, c->stream));
-    if (c->maps.ok) CK(launch_ghosts(c->dp, c->pbuf(0), c->stream));
+    if (c->maps.ok) CK(launch_ghosts(c->dp, c->p.precision, c->pbuf(0), c->stream));
     StateBufs B = c->bufs();
     CK(launch_sum_field(drho, c->dp.N, B.partial, B.counter, c->sums(0), c->stream));
     CK(cudaMemsetAsync(c->base + c->L.flag, 0, sizeof(int), c->stream));

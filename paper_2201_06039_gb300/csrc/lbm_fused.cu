@@ -344,7 +344,11 @@ k_fused_batch(DevParams P, const BatchInst* __restrict__ insts, const BatchItem*
 
 // ================================================================ TMA producer / consumer kernel
 // Tile TX x TY; consumer threads: tile slots (row-major), then the halo ring, then idle lanes.
-template <int TX_, int TY_> struct TmaShape {
+constexpr size_t align128(size_t v) { return (v + 127) / 128 * 128; }
+
+template <int TX_, int TY_, typename S_ = float> struct TmaShape {
+    using S = S_;
+    static constexpr int kE = (int)sizeof(S);                        // bytes per stored population
     static constexpr int kInterior = TX_ * TY_;
     static constexpr int kHaloNodes = 2 * (TX_ + 2) + 2 * TY_;
     static constexpr int kSlotsAll = kInterior + kHaloNodes;        // ring slots with a psi value
@@ -353,33 +357,49 @@ template <int TX_, int TY_> struct TmaShape {
     static constexpr int kPsiThreads = kPsiWarps * 32, kColThreads = kColWarps * 32;
     static constexpr int kPsiPerThread = (kSlotsAll + kPsiThreads - 1) / kPsiThreads;
     static constexpr int kThreads = 64 + kPsiThreads + kColThreads;  // producer warp, storer warp first
+    // registers per thread: the SM's 64K for one CTA, whose warps are allocated in groups of four
+    // (threads rounded up to 128) and whose per-thread count goes in steps of 8
+    static constexpr int kAllocThreads = (kThreads + 127) / 128 * 128;
+    static constexpr int kMaxRegs = (65536 / kAllocThreads) / 8 * 8 > 255 ? 255 : (65536 / kAllocThreads) / 8 * 8;
     static constexpr int kRingW = TX_ + 2, kRingPlane = (TX_ + 2) * (TY_ + 2);
-    static constexpr int kWinW = TX_ + 8;               // window columns x0-4 .. x0+TX+3 (16-byte aligned)
+    // a window row starts kXOff columns left of the tile, on a 16-byte boundary
+    static constexpr int kXOff = 16 / kE;
+    static constexpr int kWinW = TX_ + 2 * kXOff;       // window columns x0-kXOff .. x0+TX+kXOff-1
     static constexpr int kWinH = TY_ + 4;               // window rows    y0-2 .. y0+TY+1
-    static constexpr int kWin = kWinW * kWinH;          // floats per population slot
-    static constexpr int kStages = 3, kRing = 4;
+    static constexpr int kWin = kWinW * kWinH;          // elements per population slot
+    // a stage holds the three slot groups (e_z = 0: slots 0-13, +1: 14-19, -1: 20-25), each
+    // starting on a 128-byte boundary
+    static constexpr size_t kGrp1 = align128((size_t)14 * kWin * kE);
+    static constexpr size_t kGrp2 = kGrp1 + align128((size_t)6 * kWin * kE);
+    static constexpr size_t kStageOne = kGrp2 + align128((size_t)6 * kWin * kE);
+    static constexpr int kStages = kE == 4 ? 3 : 5, kRing = 4;
     static constexpr int kPrefetch = 2;                 // planes between an L2 prefetch and its load
-    static constexpr size_t kStageBytes = (size_t)kStages * kSlots * kWin * sizeof(float);
+    static constexpr size_t kStageBytes = (size_t)kStages * kStageOne;
     // collided plane, row-major [TY][26][TX]: source of one TMA tensor store per plane (a box of
     // fewer rows reads a prefix of it)
-    static constexpr size_t kOutBytes = ((size_t)kSlots * kInterior * sizeof(float) + 127) / 128 * 128;
-    // periodic images of an edge tile, tensor-stored into the ghost cells: 4 edge columns
-    // [TY][26][4], 2 edge rows [2][26][w] (w = the tile's real columns), and the 4 x 2 corner
-    // block [2][26][4]; each is laid out exactly as the box that stores it
-    static constexpr size_t kGColBytes = ((size_t)TY_ * kSlots * 4 * sizeof(float) + 127) / 128 * 128;
-    static constexpr size_t kGRowBytes = ((size_t)2 * kSlots * TX_ * sizeof(float) + 127) / 128 * 128;
-    static constexpr size_t kGCorBytes = ((size_t)2 * kSlots * 4 * sizeof(float) + 127) / 128 * 128;
+    static constexpr size_t kOutBytes = align128((size_t)kSlots * kInterior * kE);
+    // periodic images of an edge tile, tensor-stored into the ghost cells: kGW edge columns
+    // [TY][26][kGW], 2 edge rows [2][26][w] (w = the tile's real columns), and the kGW x 2 corner
+    // block [2][26][kGW]; each is laid out exactly as the box that stores it (kGW columns = 16 B)
+    static constexpr int kGW = 16 / kE;
+    static constexpr size_t kGColBytes = align128((size_t)TY_ * kSlots * kGW * kE);
+    static constexpr size_t kGRowBytes = align128((size_t)2 * kSlots * TX_ * kE);
+    static constexpr size_t kGCorBytes = align128((size_t)2 * kSlots * kGW * kE);
     static constexpr size_t kGhostBytes = kGColBytes + kGRowBytes + kGCorBytes;
     static constexpr size_t kSmem = kStageBytes + kOutBytes + kGhostBytes +
                                     (size_t)kRing * kRingPlane * (sizeof(float2) + sizeof(float));
-    static_assert(kStageBytes % 128 == 0, "TMA destinations must stay 128-byte aligned");
+    // element offset of storage slot s inside a stage
+    static constexpr __host__ __device__ int slot_off(int s) {
+        return s < 14 ? s * kWin : s < 20 ? (int)(kGrp1 / kE) + (s - 14) * kWin : (int)(kGrp2 / kE) + (s - 20) * kWin;
+    }
     static_assert(kPsiPerThread <= 2, "psi threads hold at most two ring slots");
+    static_assert(TX_ % 8 == 0, "tile origins on 16-byte boundaries for 2-byte storage");
 };
 
 // ring slot (lx, ly) of slot index q: tile nodes (row-major), then the halo ring
 template <int TX_, int TY_>
 __device__ __forceinline__ void tma_slot_of(int q, int& lx, int& ly) {
-    using Sh = TmaShape<TX_, TY_>;
+    using Sh = TmaShape<TX_, TY_, float>;
     lx = -1;
     ly = -1;
     if (q < Sh::kInterior) {
@@ -424,7 +444,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
-__device__ __forceinline__ void tma_load_4d(float* smem_dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+__device__ __forceinline__ void tma_load_4d(void* smem_dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
                                             unsigned long long* bar) {
     asm volatile(
         "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
@@ -443,7 +463,7 @@ __device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap* map, int c0, 
 
 // tensor store of a shared-memory box (bulk async-group completion); the box is clipped at the
 // tensor's bounds
-__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const float* smem_src, int c0, int c1, int c2,
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const void* smem_src, int c0, int c1, int c2,
                                              int c3) {
     asm volatile(
         "cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4, %5}], [%1];" ::"l"(
@@ -472,48 +492,69 @@ __device__ __forceinline__ int src_plane_dn(const DevParams& P, int mz) {
     return f_wraps(bc) ? 0 : (bc == BC_OUTFLOW ? P.nz - 1 : -1);
 }
 
-// The 26 pulled populations of the node in window cell (wx, wy) of a stage, with the boundary
-// links of its plane mz patched: Eq. 50 for f at z walls (f*_abar of the node itself, read from
-// global memory), Eq. 51 for g at non-periodic z faces (own g+_abar from global memory) and at
-// thermal x / y faces (own g+_abar from the stage).
-template <int WW, int WIN>
-__device__ __forceinline__ void stage_pulls(const DevParams& P, const float* __restrict__ b,
-                                            const float* __restrict__ src, int mx, int my, int mz, float f[19],
-                                            float g[7]) {
-#define GB300_SF(A) f[A] = b[fslot(A) * WIN - ey19(A) * WW - ex19(A)];
+// Stored population <-> FP32 (shifted 16-bit storage: stored = value - w_a ref, rounded to
+// nearest even; the same operations as the generic kernels' Codec).
+template <typename S> __device__ __forceinline__ float st_dec(S v, float sh);
+template <> __device__ __forceinline__ float st_dec<float>(float v, float) { return v; }
+template <> __device__ __forceinline__ float st_dec<__nv_bfloat16>(__nv_bfloat16 v, float sh) {
+    return __bfloat162float(v) + sh;
+}
+template <> __device__ __forceinline__ float st_dec<__half>(__half v, float sh) { return __half2float(v) + sh; }
+template <typename S> __device__ __forceinline__ S st_enc(float v, float sh);
+template <> __device__ __forceinline__ float st_enc<float>(float v, float) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 st_enc<__nv_bfloat16>(float v, float sh) {
+    return __float2bfloat16_rn(v - sh);
+}
+template <> __device__ __forceinline__ __half st_enc<__half>(float v, float sh) { return __float2half_rn(v - sh); }
+
+// The 26 pulled populations of the node whose window cell is b (a pointer into a stage), with the
+// boundary links of its plane mz patched: Eq. 50 for f at z walls (f*_abar of the node itself,
+// read from global memory), Eq. 51 for g at non-periodic z faces (own g+_abar from global memory)
+// and at thermal x / y faces (own g+_abar from the stage).
+template <class Sh>
+__device__ __forceinline__ void stage_pulls(const DevParams& P, const typename Sh::S* __restrict__ b,
+                                            const typename Sh::S* __restrict__ src, int mx, int my, int mz,
+                                            float f[19], float g[7]) {
+    using S = typename Sh::S;
+    constexpr int WW = Sh::kWinW;
+#define GB300_SF(A) f[A] = st_dec<S>(b[Sh::slot_off(fslot(A)) - ey19(A) * WW - ex19(A)], P.shift_f[A]);
     GB300_SF(0) GB300_SF(1) GB300_SF(2) GB300_SF(3) GB300_SF(4) GB300_SF(5) GB300_SF(6) GB300_SF(7) GB300_SF(8)
     GB300_SF(9) GB300_SF(10) GB300_SF(11) GB300_SF(12) GB300_SF(13) GB300_SF(14) GB300_SF(15) GB300_SF(16)
     GB300_SF(17) GB300_SF(18)
 #undef GB300_SF
-#define GB300_SG(A) g[A] = b[gslot(A) * WIN - ey7(A) * WW - ex7(A)];
+#define GB300_SG(A) g[A] = st_dec<S>(b[Sh::slot_off(gslot(A)) - ey7(A) * WW - ex7(A)], P.shift_g[A]);
     GB300_SG(0) GB300_SG(1) GB300_SG(2) GB300_SG(3) GB300_SG(4) GB300_SG(5) GB300_SG(6)
 #undef GB300_SG
     if (mz == 0 && P.bc[4] != BC_PERIODIC) {
         const int i = sidx(P, mx, my, mz);
         if (P.bc[4] == BC_WALL) {
-            f[5] = __ldg(src + (size_t)fslot(6) * P.Ns + i);
-            f[11] = __ldg(src + (size_t)fslot(12) * P.Ns + i);
-            f[14] = __ldg(src + (size_t)fslot(13) * P.Ns + i);
-            f[15] = __ldg(src + (size_t)fslot(16) * P.Ns + i);
-            f[18] = __ldg(src + (size_t)fslot(17) * P.Ns + i);
+            f[5] = Codec<S>::load(src + (size_t)fslot(6) * P.Ns + i, P.shift_f[6]);
+            f[11] = Codec<S>::load(src + (size_t)fslot(12) * P.Ns + i, P.shift_f[12]);
+            f[14] = Codec<S>::load(src + (size_t)fslot(13) * P.Ns + i, P.shift_f[13]);
+            f[15] = Codec<S>::load(src + (size_t)fslot(16) * P.Ns + i, P.shift_f[16]);
+            f[18] = Codec<S>::load(src + (size_t)fslot(17) * P.Ns + i, P.shift_f[17]);
         }
-        g[5] = -__ldg(src + (size_t)gslot(6) * P.Ns + i) + 2.f * P.w1 * wall_T(P, 4, mx, my);
+        g[5] = -Codec<S>::load(src + (size_t)gslot(6) * P.Ns + i, P.shift_g[6]) + 2.f * P.w1 * wall_T(P, 4, mx, my);
     }
     if (mz == P.nz - 1 && P.bc[5] != BC_PERIODIC) {
         const int i = sidx(P, mx, my, mz);
         if (P.bc[5] == BC_WALL) {
-            f[6] = __ldg(src + (size_t)fslot(5) * P.Ns + i);
-            f[12] = __ldg(src + (size_t)fslot(11) * P.Ns + i);
-            f[13] = __ldg(src + (size_t)fslot(14) * P.Ns + i);
-            f[16] = __ldg(src + (size_t)fslot(15) * P.Ns + i);
-            f[17] = __ldg(src + (size_t)fslot(18) * P.Ns + i);
+            f[6] = Codec<S>::load(src + (size_t)fslot(5) * P.Ns + i, P.shift_f[5]);
+            f[12] = Codec<S>::load(src + (size_t)fslot(11) * P.Ns + i, P.shift_f[11]);
+            f[13] = Codec<S>::load(src + (size_t)fslot(14) * P.Ns + i, P.shift_f[14]);
+            f[16] = Codec<S>::load(src + (size_t)fslot(15) * P.Ns + i, P.shift_f[15]);
+            f[17] = Codec<S>::load(src + (size_t)fslot(18) * P.Ns + i, P.shift_f[18]);
         }
-        g[6] = -__ldg(src + (size_t)gslot(5) * P.Ns + i) + 2.f * P.w1 * wall_T(P, 5, mx, my);
+        g[6] = -Codec<S>::load(src + (size_t)gslot(5) * P.Ns + i, P.shift_g[5]) + 2.f * P.w1 * wall_T(P, 5, mx, my);
     }
-    if (P.bc[0] == BC_THERMAL_ONLY && mx == 0) g[1] = -b[gslot(2) * WIN] + 2.f * P.w1 * wall_T(P, 0, mx, my);
-    if (P.bc[1] == BC_THERMAL_ONLY && mx == P.nx - 1) g[2] = -b[gslot(1) * WIN] + 2.f * P.w1 * wall_T(P, 1, mx, my);
-    if (P.bc[2] == BC_THERMAL_ONLY && my == 0) g[3] = -b[gslot(4) * WIN] + 2.f * P.w1 * wall_T(P, 2, mx, my);
-    if (P.bc[3] == BC_THERMAL_ONLY && my == P.ny - 1) g[4] = -b[gslot(3) * WIN] + 2.f * P.w1 * wall_T(P, 3, mx, my);
+    if (P.bc[0] == BC_THERMAL_ONLY && mx == 0)
+        g[1] = -st_dec<S>(b[Sh::slot_off(gslot(2))], P.shift_g[2]) + 2.f * P.w1 * wall_T(P, 0, mx, my);
+    if (P.bc[1] == BC_THERMAL_ONLY && mx == P.nx - 1)
+        g[2] = -st_dec<S>(b[Sh::slot_off(gslot(1))], P.shift_g[1]) + 2.f * P.w1 * wall_T(P, 1, mx, my);
+    if (P.bc[2] == BC_THERMAL_ONLY && my == 0)
+        g[3] = -st_dec<S>(b[Sh::slot_off(gslot(4))], P.shift_g[4]) + 2.f * P.w1 * wall_T(P, 2, mx, my);
+    if (P.bc[3] == BC_THERMAL_ONLY && my == P.ny - 1)
+        g[4] = -st_dec<S>(b[Sh::slot_off(gslot(3))], P.shift_g[3]) + 2.f * P.w1 * wall_T(P, 3, mx, my);
 }
 
 // Warp roles: warp 0 = producer (TMA loads), warp 1 = storer (TMA stores), the next kPsiWarps =
@@ -526,25 +567,25 @@ __device__ __forceinline__ void stage_pulls(const DevParams& P, const float* __r
 //   out_empty    tensor store has read the out buffer         (storer    -> collision)
 // Stage uses and ring uses follow one plane counter k across the CTA's items; out-buffer uses
 // follow the collided-plane counter u.
-template <int TX_, int TY_>
-__global__ void __launch_bounds__(TmaShape<TX_, TY_>::kThreads, 1)
+template <int TX_, int TY_, typename S>
+__global__ void __maxnreg__((TmaShape<TX_, TY_, S>::kMaxRegs))
 k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ CUtensorMap map6,
             const __grid_constant__ CUtensorMap map_out, const __grid_constant__ CUtensorMap map_out_top,
             const __grid_constant__ CUtensorMap map_gcol, const __grid_constant__ CUtensorMap map_gcol_top,
             const __grid_constant__ CUtensorMap map_grow, const __grid_constant__ CUtensorMap map_grow_right,
-            const __grid_constant__ CUtensorMap map_gcor, int ghosts, DevParams P, const float* __restrict__ src,
+            const __grid_constant__ CUtensorMap map_gcor, int ghosts, DevParams P, const S* __restrict__ src,
             const double* __restrict__ sums_cur, double2* partial, unsigned* counter, double* sums_next,
             float* __restrict__ phis, int* flag, int first, int zchunk, int tiles_x, int tiles_y, int n_items) {
-    using Sh = TmaShape<TX_, TY_>;
-    constexpr int kWin = Sh::kWin, kWinW = Sh::kWinW, kStages = Sh::kStages, kRing = Sh::kRing;
-    constexpr int kCol = Sh::kColThreads, kPrefetch = Sh::kPrefetch;
+    using Sh = TmaShape<TX_, TY_, S>;
+    constexpr int kWinW = Sh::kWinW, kStages = Sh::kStages, kRing = Sh::kRing;
+    constexpr int kCol = Sh::kColThreads, kPrefetch = Sh::kPrefetch, kGW = Sh::kGW;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    float* stages = reinterpret_cast<float*>(smem_raw);                          // [3][26][TY+4][TX+8]
-    float* out = reinterpret_cast<float*>(smem_raw + Sh::kStageBytes);           // [TY][26][TX]
-    float* gcol = reinterpret_cast<float*>(smem_raw + Sh::kStageBytes + Sh::kOutBytes);          // [TY][26][4]
-    float* grow = reinterpret_cast<float*>(smem_raw + Sh::kStageBytes + Sh::kOutBytes + Sh::kGColBytes);  // [2][26][TX]
-    float* gcor = reinterpret_cast<float*>(smem_raw + Sh::kStageBytes + Sh::kOutBytes + Sh::kGColBytes +
-                                           Sh::kGRowBytes);                      // [2][26][4]
+    // stage s: smem_raw + s * kStageOne (three slot groups of [slots][TY+4][TX+2 kXOff])
+    S* out = reinterpret_cast<S*>(smem_raw + Sh::kStageBytes);                   // [TY][26][TX]
+    S* gcol = reinterpret_cast<S*>(smem_raw + Sh::kStageBytes + Sh::kOutBytes);  // [TY][26][kGW]
+    S* grow = reinterpret_cast<S*>(smem_raw + Sh::kStageBytes + Sh::kOutBytes + Sh::kGColBytes);  // [2][26][w]
+    S* gcor = reinterpret_cast<S*>(smem_raw + Sh::kStageBytes + Sh::kOutBytes + Sh::kGColBytes +
+                                   Sh::kGRowBytes);                              // [2][26][kGW]
     float2* ring = reinterpret_cast<float2*>(smem_raw + Sh::kStageBytes + Sh::kOutBytes + Sh::kGhostBytes);  // [4][TY+2][TX+2]
     float* tring = reinterpret_cast<float*>(ring + kRing * Sh::kRingPlane);      // [4][TY+2][TX+2] T
     __shared__ __align__(8) unsigned long long full_bar[kStages], empty_bar[kStages], ring_full[kRing],
@@ -597,14 +638,15 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                     }
                     const int mz = map_coord(p, P.nz, P.bc[4], P.bc[5]);
                     const int zu = src_plane_up(P, mz), zd = src_plane_dn(P, mz);
-                    const unsigned bytes = (14u + (zu >= 0 ? 6u : 0u) + (zd >= 0 ? 6u : 0u)) * kWin * 4u;
-                    float* st = stages + (size_t)s * kSlots * kWin;
+                    const unsigned bytes =
+                        (14u + (zu >= 0 ? 6u : 0u) + (zd >= 0 ? 6u : 0u)) * (unsigned)(Sh::kWin * Sh::kE);
+                    unsigned char* st = smem_raw + (size_t)s * Sh::kStageOne;
                     mbar_expect_tx(&full_bar[s], bytes);
-                    // window origin in storage coordinates: (x0 - 4) + kGX, (y0 - 2) + kGY
-                    const int cx = x0 - 4 + kGX, cy = y0;
+                    // window origin in storage coordinates: (x0 - kXOff) + kGX, (y0 - 2) + kGY
+                    const int cx = x0 - Sh::kXOff + kGX, cy = y0;
                     tma_load_4d(st, &map14, cx, cy, mz, 0, &full_bar[s]);
-                    if (zu >= 0) tma_load_4d(st + 14 * kWin, &map6, cx, cy, zu, 14, &full_bar[s]);
-                    if (zd >= 0) tma_load_4d(st + 20 * kWin, &map6, cx, cy, zd, 20, &full_bar[s]);
+                    if (zu >= 0) tma_load_4d(st + Sh::kGrp1, &map6, cx, cy, zu, 14, &full_bar[s]);
+                    if (zd >= 0) tma_load_4d(st + Sh::kGrp2, &map6, cx, cy, zd, 20, &full_bar[s]);
                     // pull the window of a plane kPrefetch ahead into L2, so that its load into a
                     // stage (issued once a stage frees) waits on L2 rather than on DRAM
                     const int pf = p + kPrefetch;
@@ -639,7 +681,7 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                 // 2 edge rows to the opposite ghost rows, and the corner block
                 const bool left = ghosts && x0 == 0, right = ghosts && x0 + TX_ >= P.nx;
                 const bool bottom = ghosts && y0 == 0, top = ghosts && y0 + TY_ >= P.ny;
-                const int gx_col = right ? kGX - 4 : P.nx + kGX;      // destination of the column box
+                const int gx_col = right ? kGX - kGW : P.nx + kGX;    // destination of the column box
                 const int gy_row = top ? kGY - 2 : P.ny + kGY;        // destination of the row box
                 const CUtensorMap* mc = y0 + TY_ > P.ny ? &map_gcol_top : &map_gcol;
                 const CUtensorMap* mr = x0 + TX_ > P.nx ? &map_grow_right : &map_grow;
@@ -685,20 +727,20 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                 use[j] = lxs[j] >= 0 && gx >= -1 && gx <= P.nx && gy >= -1 && gy <= P.ny;
                 mxs[j] = use[j] ? map_coord(gx, P.nx, P.bc[0], P.bc[1]) : 0;
                 mys[j] = use[j] ? map_coord(gy, P.ny, P.bc[2], P.bc[3]) : 0;
-                woff[j] = (lys[j] + 1) * kWinW + lxs[j] + 3;
+                woff[j] = (lys[j] + 1) * kWinW + lxs[j] - 1 + Sh::kXOff;
                 roff[j] = lys[j] * Sh::kRingW + lxs[j];
             }
             for (int p = z0 - 1; p <= z1; ++p, ++k) {
                 const int s = k % kStages, r = k % kRing;
                 if (k >= (unsigned)kRing) wait(&ring_empty[r], (k / kRing - 1) & 1);
                 wait(&full_bar[s], (k / kStages) & 1);
-                const float* st = stages + (size_t)s * kSlots * kWin;
+                const S* st = reinterpret_cast<const S*>(smem_raw + (size_t)s * Sh::kStageOne);
                 const int mz = map_coord(p, P.nz, P.bc[4], P.bc[5]);
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
                     if (!use[j]) continue;
                     float f[19], g[7];
-                    stage_pulls<kWinW, kWin>(P, st + woff[j], src, mxs[j], mys[j], mz, f, g);
+                    stage_pulls<Sh>(P, st + woff[j], src, mxs[j], mys[j], mz, f, g);
                     float rho = sum19(f), T = sum7(g);
                     const float psi2 = psi_squared(P, rho, T);
                     ring[r * Sh::kRingPlane + roff[j]] = make_float2(psi_of(psi2), rho);
@@ -721,9 +763,9 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
         const bool node_thread = ct < Sh::kInterior;
         const int lx = ct % TX_ + 1, ly = ct / TX_ + 1;
         const int slot = ly * Sh::kRingW + lx;
-        const int woff = (ly + 1) * kWinW + lx + 3;
+        const int woff = (ly + 1) * kWinW + lx - 1 + Sh::kXOff;
         const float rho_ave = buoyancy_ref(P, sums_cur[0], P.inv_N);
-        float* const outp = out + (ly - 1) * (kSlots * TX_) + (lx - 1);
+        S* const outp = out + (ly - 1) * (kSlots * TX_) + (lx - 1);
         unsigned k = 0, u = 0;
         for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
             const int chunk = item / ntiles, tile = item % ntiles;
@@ -734,8 +776,8 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
             // this node's place in the ghost staging tiles of an edge tile (-1: none)
             const bool eright = ghosts && x0 + TX_ >= P.nx, eleft = ghosts && x0 == 0;
             const bool etop = ghosts && y0 + TY_ >= P.ny, ebottom = ghosts && y0 == 0;
-            const int cx4 = !owner ? -1 : eright ? (gx >= P.nx - 4 ? gx - (P.nx - 4) : -1)
-                                        : eleft ? (gx < 4 ? gx : -1) : -1;
+            const int cx4 = !owner ? -1 : eright ? (gx >= P.nx - kGW ? gx - (P.nx - kGW) : -1)
+                                        : eleft ? (gx < kGW ? gx : -1) : -1;
             const int ry2 = !owner ? -1 : etop ? (gy >= P.ny - 2 ? gy - (P.ny - 2) : -1)
                                         : ebottom ? (gy < 2 ? gy : -1) : -1;
             // the edge-row tile is as wide as the tile's real columns (the box reads it densely)
@@ -758,8 +800,8 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                 if (owner && z + 1 < z1) ph_next = phis[node_of(P, gx, gy, z + 1)];
                 float f[19], g[7];
                 if (owner) {
-                    const float* sz = stages + (size_t)(kz % kStages) * kSlots * kWin;
-                    stage_pulls<kWinW, kWin>(P, sz + woff, src, gx, gy, z, f, g);
+                    const S* sz = reinterpret_cast<const S*>(smem_raw + (size_t)(kz % kStages) * Sh::kStageOne);
+                    stage_pulls<Sh>(P, sz + woff, src, gx, gy, z, f, g);
                 }
                 __syncwarp();       // pulls are in registers: the stage of plane z may be refilled
                 if (lane == 0) mbar_arrive(&empty_bar[kz % kStages]);
@@ -790,30 +832,35 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                 // the out buffer is free once the tensor store of the previous plane has read it
                 if (u > 0) wait(&out_empty, (u - 1) & 1);
                 if (owner) {
+                    S fe[19], ge[7];   // stored form of f*, g+
 #pragma unroll
-                    for (int a = 0; a < 19; ++a) outp[fslot(a) * TX_] = f[a];
+                    for (int a = 0; a < 19; ++a) fe[a] = st_enc<S>(f[a], P.shift_f[a]);
 #pragma unroll
-                    for (int a = 0; a < 7; ++a) outp[gslot(a) * TX_] = g[a];
-                    if (cx4 >= 0) {   // edge column: [TY][26][4]
-                        float* q = gcol + (ly - 1) * (kSlots * 4) + cx4;
+                    for (int a = 0; a < 7; ++a) ge[a] = st_enc<S>(g[a], P.shift_g[a]);
 #pragma unroll
-                        for (int a = 0; a < 19; ++a) q[fslot(a) * 4] = f[a];
+                    for (int a = 0; a < 19; ++a) outp[fslot(a) * TX_] = fe[a];
 #pragma unroll
-                        for (int a = 0; a < 7; ++a) q[gslot(a) * 4] = g[a];
+                    for (int a = 0; a < 7; ++a) outp[gslot(a) * TX_] = ge[a];
+                    if (cx4 >= 0) {   // edge column: [TY][26][kGW]
+                        S* q = gcol + (ly - 1) * (kSlots * kGW) + cx4;
+#pragma unroll
+                        for (int a = 0; a < 19; ++a) q[fslot(a) * kGW] = fe[a];
+#pragma unroll
+                        for (int a = 0; a < 7; ++a) q[gslot(a) * kGW] = ge[a];
                     }
                     if (ry2 >= 0) {   // edge row: [2][26][rw]
-                        float* q = grow + ry2 * (kSlots * rw) + (lx - 1);
+                        S* q = grow + ry2 * (kSlots * rw) + (lx - 1);
 #pragma unroll
-                        for (int a = 0; a < 19; ++a) q[fslot(a) * rw] = f[a];
+                        for (int a = 0; a < 19; ++a) q[fslot(a) * rw] = fe[a];
 #pragma unroll
-                        for (int a = 0; a < 7; ++a) q[gslot(a) * rw] = g[a];
+                        for (int a = 0; a < 7; ++a) q[gslot(a) * rw] = ge[a];
                     }
-                    if (cx4 >= 0 && ry2 >= 0) {   // corner block: [2][26][4]
-                        float* q = gcor + ry2 * (kSlots * 4) + cx4;
+                    if (cx4 >= 0 && ry2 >= 0) {   // corner block: [2][26][kGW]
+                        S* q = gcor + ry2 * (kSlots * kGW) + cx4;
 #pragma unroll
-                        for (int a = 0; a < 19; ++a) q[fslot(a) * 4] = f[a];
+                        for (int a = 0; a < 19; ++a) q[fslot(a) * kGW] = fe[a];
 #pragma unroll
-                        for (int a = 0; a < 7; ++a) q[gslot(a) * 4] = g[a];
+                        for (int a = 0; a < 7; ++a) q[gslot(a) * kGW] = ge[a];
                     }
                 }
                 // every lane's out writes become visible to the tensor store before lane 0 signals
@@ -841,9 +888,18 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
 // Ghost refresh after a step on the TMA path: every ghost cell (columns -2, -1, nx, nx+1 over all
 // rows including the ghost rows, and rows -2, -1, ny, ny+1 over the real columns) receives the
 // stored populations of its periodic image.  Threads [0, nA): one (row, slot) each, copying the
-// column pairs (nx-2, nx-1) -> (-2, -1) and (0, 1) -> (nx, nx+1) (as float2 when nx is even);
-// threads [nA, nA + nB): one (ghost row, slot, 4-column group) each (as float4 when nx % 4 == 0).
-__global__ void __launch_bounds__(256) k_ghosts(DevParams P, float* __restrict__ pops) {
+// column pairs (nx-2, nx-1) -> (-2, -1) and (0, 1) -> (nx, nx+1) (as one word pair when nx is
+// even); threads [nA, nA + nB): one (ghost row, slot, 4-column group) each (one wide word when
+// nx % 4 == 0).  Raw element bits are copied, so any storage type works.
+template <int E> struct RawPair;
+template <> struct RawPair<4> { using T = uint2; using Q = uint4; using W = unsigned; };
+template <> struct RawPair<2> { using T = unsigned; using Q = uint2; using W = unsigned short; };
+template <typename S>
+__global__ void __launch_bounds__(256) k_ghosts(DevParams P, S* __restrict__ pops) {
+    using R = RawPair<(int)sizeof(S)>;
+    using T2 = typename R::T;
+    using T4 = typename R::Q;
+    using T1 = typename R::W;
     const int nA = (P.ny + 4) * kSlots;
     const int groups = (P.nx + 3) / 4;
     const int nB = 4 * kSlots * groups;
@@ -852,37 +908,39 @@ __global__ void __launch_bounds__(256) k_ghosts(DevParams P, float* __restrict__
     if (t < nA) {
         const int a = t % kSlots, gy = t / kSlots - 2;
         const int iy = ((gy % P.ny) + P.ny) % P.ny;
-        float* base = pops + (size_t)a * P.Ns;
+        S* base = pops + (size_t)a * P.Ns;
         const int yrow = sidx(P, 0, gy, z), irow = sidx(P, 0, iy, z);
         if ((P.nx & 1) == 0) {
-            const float2 hi = *reinterpret_cast<const float2*>(base + irow + P.nx - 2);
-            const float2 lo = *reinterpret_cast<const float2*>(base + irow);
-            *reinterpret_cast<float2*>(base + yrow - 2) = hi;
-            *reinterpret_cast<float2*>(base + yrow + P.nx) = lo;
+            const T2 hi = *reinterpret_cast<const T2*>(base + irow + P.nx - 2);
+            const T2 lo = *reinterpret_cast<const T2*>(base + irow);
+            *reinterpret_cast<T2*>(base + yrow - 2) = hi;
+            *reinterpret_cast<T2*>(base + yrow + P.nx) = lo;
         } else {
-            const float h0 = base[irow + P.nx - 2], h1 = base[irow + P.nx - 1], l0 = base[irow], l1 = base[irow + 1];
-            base[yrow - 2] = h0;
-            base[yrow - 1] = h1;
-            base[yrow + P.nx] = l0;
-            base[yrow + P.nx + 1] = l1;
+            T1* b1 = reinterpret_cast<T1*>(base);
+            const T1 h0 = b1[irow + P.nx - 2], h1 = b1[irow + P.nx - 1], l0 = b1[irow], l1 = b1[irow + 1];
+            b1[yrow - 2] = h0;
+            b1[yrow - 1] = h1;
+            b1[yrow + P.nx] = l0;
+            b1[yrow + P.nx + 1] = l1;
         }
     } else if (t < nA + nB) {
         const int u = t - nA;
         const int q = u % groups, a = (u / groups) % kSlots, k = u / (groups * kSlots);
         const int gy = k == 0 ? -2 : k == 1 ? -1 : k == 2 ? P.ny : P.ny + 1;
         const int iy = ((gy % P.ny) + P.ny) % P.ny;
-        float* base = pops + (size_t)a * P.Ns;
+        S* base = pops + (size_t)a * P.Ns;
         const int dst = sidx(P, 4 * q, gy, z), src = sidx(P, 4 * q, iy, z);
         if ((P.nx & 3) == 0) {
-            *reinterpret_cast<float4*>(base + dst) = *reinterpret_cast<const float4*>(base + src);
+            *reinterpret_cast<T4*>(base + dst) = *reinterpret_cast<const T4*>(base + src);
         } else {
-            for (int c = 0; c < 4 && 4 * q + c < P.nx; ++c) base[dst + c] = base[src + c];
+            T1* b1 = reinterpret_cast<T1*>(base);
+            for (int c = 0; c < 4 && 4 * q + c < P.nx; ++c) b1[dst + c] = b1[src + c];
         }
     }
 }
 
-using Shape0 = TmaShape<32, 8>;
-using Shape1 = TmaShape<40, 7>;
+template <typename S> using Shape0 = TmaShape<32, 8, S>;
+template <typename S> using Shape1 = TmaShape<40, 7, S>;
 
 // Plan of the TMA kernel for a lattice: tile shape and z-chunking that minimise the planes x
 // tile nodes of the busiest CTA (items are spread round robin over the persistent CTAs; when
@@ -929,32 +987,41 @@ bool fused_supported(const DevParams& P) {
     return blocks <= (long long)max_partials(P);
 }
 
-cudaError_t launch_ghosts(const DevParams& P, void* pops, cudaStream_t s) {
+cudaError_t launch_ghosts(const DevParams& P, int precision, void* pops, cudaStream_t s) {
     const int per_plane = (P.ny + 4) * kSlots + 4 * kSlots * ((P.nx + 3) / 4);
-    k_ghosts<<<dim3((per_plane + 255) / 256, P.nz), 256, 0, s>>>(P, (float*)pops);
+    const dim3 grid((per_plane + 255) / 256, P.nz);
+    if (precision == 0) k_ghosts<float><<<grid, 256, 0, s>>>(P, (float*)pops);
+    else k_ghosts<__half><<<grid, 256, 0, s>>>(P, (__half*)pops);   // raw 2-byte copies (BF16 or FP16)
     return cudaGetLastError();
 }
 
 bool tma_eligible(const DevParams& P, int precision) {
-    return precision == 0 && P.nx >= 4 && P.ny >= 4 && f_wraps(P.bc[0]) && f_wraps(P.bc[1]) && f_wraps(P.bc[2]) &&
-           f_wraps(P.bc[3]) && !P.flow_off && !P.thermal_off;
+    return precision >= 0 && precision <= 2 && P.nx >= 4 && P.ny >= 4 && f_wraps(P.bc[0]) && f_wraps(P.bc[1]) &&
+           f_wraps(P.bc[2]) && f_wraps(P.bc[3]) && !P.flow_off && !P.thermal_off;
 }
 
-size_t tma_smem_bytes(int shape) { return shape == 0 ? Shape0::kSmem : Shape1::kSmem; }
+size_t tma_smem_bytes(int shape, int precision) {
+    if (precision == 0) return shape == 0 ? Shape0<float>::kSmem : Shape1<float>::kSmem;
+    return shape == 0 ? Shape0<__half>::kSmem : Shape1<__half>::kSmem;
+}
 
 void tma_plan_for(const DevParams& P, int ctas, int* shape, int* zchunk, int* items) {
     tma_plan(P, ctas, shape, zchunk, items);
 }
 
-int tma_box_w(int shape) { return shape == 0 ? Shape0::kWinW : Shape1::kWinW; }
-int tma_box_h(int shape) { return shape == 0 ? Shape0::kWinH : Shape1::kWinH; }
+int tma_box_w(int shape, int precision) {
+    if (precision == 0) return shape == 0 ? Shape0<float>::kWinW : Shape1<float>::kWinW;
+    return shape == 0 ? Shape0<__half>::kWinW : Shape1<__half>::kWinW;
+}
+int tma_box_h(int shape) { return shape == 0 ? Shape0<float>::kWinH : Shape1<float>::kWinH; }
 int tma_tile_w(int shape) { return shape == 0 ? 32 : 40; }
-bool tma_ghosts_in_kernel(const DevParams& P, int shape) {
-    const int tx = tma_tile_w(shape), ty = shape == 0 ? 8 : 7;
-    // 4-column boxes on 16-byte boundaries, at least two tiles per axis (an edge tile is never
-    // both left and right, top and bottom), edge tiles at least 4 columns and 2 rows wide, and
-    // room for the 4 ghost columns past nx in the padded rows
-    return P.nx % 4 == 0 && P.nx > tx && P.ny > ty && P.ny % ty != 1 && P.Ws >= P.nx + kGX + 4;
+int tma_ghost_cols(int precision) { return precision == 0 ? 4 : 8; }   // 16 bytes of columns
+bool tma_ghosts_in_kernel(const DevParams& P, int shape, int precision) {
+    const int tx = tma_tile_w(shape), ty = shape == 0 ? 8 : 7, gw = tma_ghost_cols(precision);
+    // ghost-column boxes (gw columns = 16 bytes) on 16-byte boundaries, at least two tiles per
+    // axis (an edge tile is never both left and right, top and bottom), edge tiles at least gw
+    // columns and 2 rows wide, and room for the gw ghost columns past nx in the padded rows
+    return P.nx % gw == 0 && P.nx > tx && P.ny > ty && P.ny % ty != 1 && P.Ws >= P.nx + kGX + gw;
 }
 int tma_tile_h(int shape) { return shape == 0 ? 8 : 7; }
 
@@ -969,19 +1036,26 @@ cudaError_t launch_fused(const DevParams& P, int precision, const StateBufs& B, 
         const int txs = (P.nx + tx - 1) / tx, tys = (P.ny + ty - 1) / ty;
         const int ctas = maps->sms < maps->items ? maps->sms : maps->items;
         if (ghosts_written) *ghosts_written = maps->ghosts;
-#define GB300_TMA(SH, TXV, TYV)                                                                                \
+#define GB300_TMA(SH, TXV, TYV, ST)                                                                            \
         {                                                                                                      \
-            e = cudaFuncSetAttribute(k_fused_tma<TXV, TYV>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+            e = cudaFuncSetAttribute(k_fused_tma<TXV, TYV, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
                                      (int)SH::kSmem);                                                          \
             if (e != cudaSuccess) return e;                                                                    \
-            k_fused_tma<TXV, TYV><<<ctas, SH::kThreads, SH::kSmem, s>>>(                                       \
+            k_fused_tma<TXV, TYV, ST><<<ctas, SH::kThreads, SH::kSmem, s>>>(                                   \
                 maps->m14[B.src_index], maps->m6[B.src_index], maps->mout[B.src_index ^ 1],                    \
                 maps->mout_top[B.src_index ^ 1], maps->mgcol[B.src_index ^ 1], maps->mgcol_top[B.src_index ^ 1], \
                 maps->mgrow[B.src_index ^ 1], maps->mgrow_right[B.src_index ^ 1], maps->mgcor[B.src_index ^ 1], \
-                maps->ghosts ? 1 : 0, P, (const float*)B.src, sums_cur, B.partial, B.counter, sums_next, B.phis, \
+                maps->ghosts ? 1 : 0, P, (const ST*)B.src, sums_cur, B.partial, B.counter, sums_next, B.phis,   \
                 B.flag, first, maps->zchunk, txs, tys, maps->items);                                           \
         }
-        if (maps->shape == 0) GB300_TMA(Shape0, 32, 8) else GB300_TMA(Shape1, 40, 7)
+        if (precision == 0) {
+            if (maps->shape == 0) GB300_TMA(Shape0<float>, 32, 8, float) else GB300_TMA(Shape1<float>, 40, 7, float)
+        } else if (precision == 1) {
+            if (maps->shape == 0) GB300_TMA(Shape0<__nv_bfloat16>, 32, 8, __nv_bfloat16)
+            else GB300_TMA(Shape1<__nv_bfloat16>, 40, 7, __nv_bfloat16)
+        } else {
+            if (maps->shape == 0) GB300_TMA(Shape0<__half>, 32, 8, __half) else GB300_TMA(Shape1<__half>, 40, 7, __half)
+        }
 #undef GB300_TMA
         return cudaGetLastError();
     }

@@ -34,14 +34,14 @@ cudaError_t launch_collide(const DevParams& P, int precision, const StateBufs& B
                            const double* sums_cur, int first, cudaStream_t s);
 
 // Tensor maps of the two population buffers for the TMA variant: the load windows (4D x, y, z,
-// slot; boxes (TX + 8) x (TY + 4) x 1 x 14 and x 6 over the padded storage) and the output tile
+// slot; boxes (TX + 2 * 16 bytes of columns) x (TY + 4) x 1 x 14 and x 6 over the padded storage) and the output tile
 // (4D x, slot, y, z over the real nodes only; boxes TX x 26 x TY x 1, and TX x 26 x (rows of the
 // last tile row) x 1 in mout_top); and the number of SMs for its persistent grid.
 struct TmaMaps {
     CUtensorMap m14[2], m6[2], mout[2], mout_top[2];
-    // ghost stores (4D x, slot, y, z over the whole padded plane): edge-column box 4 x 26 x TY (and
+    // ghost stores (4D x, slot, y, z over the whole padded plane): edge-column box gw x 26 x TY (and
     // x rows of the last tile row), edge-row box TX x 26 x 2 (and x columns of the last tile
-    // column), corner box 4 x 26 x 2
+    // column), corner box gw x 26 x 2, gw = 16 bytes of columns
     CUtensorMap mgcol[2], mgcol_top[2], mgrow[2], mgrow_right[2], mgcor[2];
     bool ghosts;   // the TMA kernel writes the ghost cells itself (no refresh kernel)
     bool ok;
@@ -57,15 +57,16 @@ cudaError_t launch_fused(const DevParams& P, int precision, const StateBufs& B, 
                          bool* ghosts_written = nullptr);
 bool fused_supported(const DevParams& P);
 bool tma_eligible(const DevParams& P, int precision);
-// refresh the ghost columns / rows of a population buffer from their periodic images (FP32)
-cudaError_t launch_ghosts(const DevParams& P, void* pops, cudaStream_t s);
+// refresh the ghost columns / rows of a population buffer from their periodic images
+cudaError_t launch_ghosts(const DevParams& P, int precision, void* pops, cudaStream_t s);
 // tile shape 0: 32 x 8, 1: 40 x 7 (window boxes tma_box_w x tma_box_h per population slot)
 void tma_plan_for(const DevParams& P, int ctas, int* shape, int* zchunk, int* items);
-size_t tma_smem_bytes(int shape);
-int tma_box_w(int shape);
+size_t tma_smem_bytes(int shape, int precision);
+int tma_box_w(int shape, int precision);
 int tma_box_h(int shape);
 int tma_tile_w(int shape);
-bool tma_ghosts_in_kernel(const DevParams& P, int shape);
+bool tma_ghosts_in_kernel(const DevParams& P, int shape, int precision);
+int tma_ghost_cols(int precision);
 int tma_tile_h(int shape);
 
 // macroscopic moments (needs the psi pass on the same state first).

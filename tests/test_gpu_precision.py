@@ -68,3 +68,28 @@ def test_shifted_storage_field_errors_vs_fp64_oracle(downscaled, storage):
     for k, v in err.items():
         assert np.isfinite(v) and v <= BUDGET[storage][k], (storage, k, v, err)
 
+
+
+@pytest.mark.parametrize("storage", ["bf16", "fp16"])
+@pytest.mark.parametrize("dims", [(72, 40, 30), (41, 15, 20), (200, 22, 9)])
+def test_16bit_tma_kernel_bit_identical_to_generic(storage, dims):
+    """The TMA kernel with shifted 16-bit stages, output tiles and ghost stores (in-kernel ghosts
+    for nx % 8 == 0, the refresh kernel otherwise) computes exactly what the generic fused and
+    the two-pass kernels compute on the same 16-bit storage."""
+    from paper_2201_06039_gb300 import lbm
+    from tests._parity import run_gpu
+    nx, ny, nz = dims
+    case = W.pool_boiling(nx, ny, nz, height=nz / 2.5, hot_sigma=3.0)
+    rho, T, u = inputs(case)
+    s = case["setup"]
+    Tc = oracle.Tc_of(s)
+    over = dict(precision=PREC[storage], rho_ref=float(np.mean(rho)), T_ref=0.86 * Tc)
+    lat = lbm.Lattice(lbm.params_from_setup(s, kernel=2, use_tma=1, **over))
+    assert lat.kernel == lbm.LBM_KERNEL_FUSED_TMA
+    lat.close()
+    tma, _ = run_gpu(s, rho, T, u, 11, kernel=2, use_tma=1, **over)
+    gen, _ = run_gpu(s, rho, T, u, 11, kernel=2, use_tma=0, **over)
+    two, _ = run_gpu(s, rho, T, u, 11, kernel=1, **over)
+    for k in tma:
+        assert np.array_equal(tma[k], gen[k]), (storage, dims, k)
+        assert np.array_equal(tma[k], two[k]), (storage, dims, k)
