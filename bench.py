@@ -408,6 +408,62 @@ def cpu_baseline_batch(cases, budget_s=15.0):
                 sample=f"3 FP64 oracle steps of each of the first {k} ensemble instances, one after another")
 
 
+def rel_err(a, b):
+    """max |a - b| / max |b| (u as a vector: the largest component error over the largest |u_k|)."""
+    out = {}
+    for k in ("rho", "T"):
+        out[k] = float(np.max(np.abs(a[k].astype(np.float64) - b[k]))) / float(np.max(np.abs(b[k])))
+    den = max(float(np.max(np.abs(b[k]))) for k in ("ux", "uy", "uz"))
+    out["u"] = max(float(np.max(np.abs(a[k].astype(np.float64) - b[k]))) for k in ("ux", "uy", "uz")) / den
+    return out
+
+
+def compare_16bit(lbm, case, rho, T, stream, steps):
+    """Shifted BF16 / FP16 storage beside FP32: throughput on the benchmark lattice, and the field
+    error against FP32 storage on the 64 x 64 x 96 copy of the workload after 300 steps (the FP64
+    oracle comparison of the same case is a GPU test)."""
+    import torch
+    out = {"error_case": "64x64x96 pool boiling, 300 steps, max-norm relative to FP32 storage"}
+    s = case["setup"]
+    small = W.pool_boiling_downscaled()
+    r_s, t_s = init_fields(small)
+    Tc_small = lbm.lbm_eos_critical(lbm.params_from_setup(small["setup"]))[0]
+    ref = None
+    res = {}
+    for prec in ("fp32", "bf16", "fp16"):
+        over = {} if prec == "fp32" else dict(precision=PREC_CODE[prec], rho_ref=float(r_s.mean()),
+                                              T_ref=0.86 * Tc_small)
+        lat = lbm.Lattice(lbm.params_from_setup(small["setup"], check_nonfinite=0, **over), stream=stream)
+        lat.init(r_s, t_s)
+        lat.step(300)
+        m = lat.moments()
+        lat.close()
+        if prec == "fp32":
+            ref = {k: v.astype(np.float64) for k, v in m.items()}
+        else:
+            res[prec] = rel_err(m, ref)
+    for prec in ("bf16", "fp16"):
+        p = lbm.params_from_setup(s, check_nonfinite=0, precision=PREC_CODE[prec], rho_ref=float(rho.mean()))
+        p.T_ref = 0.86 * lbm.lbm_eos_critical(p)[0]
+        lat = lbm.Lattice(p, stream=stream)
+        lat.init(torch.from_numpy(rho).cuda(), torch.from_numpy(T).cuda())
+        lat.step(10)
+        lat.step(steps)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[prec] = {"value": s.n_nodes / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms,
+                     "algorithmic_bytes_per_node": BYTES_PER_NODE[prec], "steps": steps,
+                     "err_vs_fp32": res[prec]}
+        lat.close()
+    return out
+
+
 def run_mine(args):
     import torch
     rank, world, local = dist_env()
@@ -510,6 +566,8 @@ def run_mine(args):
         "finite": finite,
     }
     lat.close()
+    if args.precision == "fp32" and args.compare_16bit and args.workload == "pool_boiling" and not args.nx:
+        line["storage_16bit"] = compare_16bit(lbm, case, rho, T, stream, min(args.steps, 500))
     if args.cpu_baseline and rank == 0 and world == 1:
         line["cpu_baseline"] = {k: v for k, v in cpu_baseline_run(case).items() if k != "seconds"}
     if rank == 0:
@@ -533,6 +591,8 @@ def main():
     ap.add_argument("--ny", type=int, default=None)
     ap.add_argument("--nz", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-16bit", dest="compare_16bit", action="store_false",
+                    help="skip the BF16 / FP16 storage comparison of the default run")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -392,7 +392,7 @@ template <int TX_, int TY_, typename S_ = float> struct TmaShape {
     static constexpr __host__ __device__ int slot_off(int s) {
         return s < 14 ? s * kWin : s < 20 ? (int)(kGrp1 / kE) + (s - 14) * kWin : (int)(kGrp2 / kE) + (s - 20) * kWin;
     }
-    static_assert(kPsiPerThread <= 2, "psi threads hold at most two ring slots");
+    static_assert(kPsiPerThread <= 3, "psi threads hold at most three ring slots");
     static_assert(TX_ % 8 == 0, "tile origins on 16-byte boundaries for 2-byte storage");
 };
 
@@ -704,13 +704,14 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
     } else if (warp < 2 + Sh::kPsiWarps) {
         // ------------------------------------------------------------ psi pass
         const int pt = tid - 64;
-        int lxs[2], lys[2];
+        constexpr int J = Sh::kPsiPerThread;
+        int lxs[J], lys[J];
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
+        for (int j = 0; j < J; ++j) {
             const int q = pt + j * Sh::kPsiThreads;
             lxs[j] = -1;
             lys[j] = -1;
-            if (j < Sh::kPsiPerThread && q < Sh::kSlotsAll) tma_slot_of<TX_, TY_>(q, lxs[j], lys[j]);
+            if (q < Sh::kSlotsAll) tma_slot_of<TX_, TY_>(q, lxs[j], lys[j]);
         }
         int bad = 0;
         unsigned k = 0;
@@ -719,10 +720,10 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
             const int x0 = (tile % tiles_x) * TX_, y0 = (tile / tiles_x) * TY_;
             const int z0 = chunk * zchunk, z1 = min(P.nz, z0 + zchunk);
             // slot geometry of this item, fixed across its planes
-            bool use[2];
-            int mxs[2], mys[2], woff[2], roff[2];
+            bool use[J];
+            int mxs[J], mys[J], woff[J], roff[J];
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
+            for (int j = 0; j < J; ++j) {
                 const int gx = x0 + lxs[j] - 1, gy = y0 + lys[j] - 1;
                 use[j] = lxs[j] >= 0 && gx >= -1 && gx <= P.nx && gy >= -1 && gy <= P.ny;
                 mxs[j] = use[j] ? map_coord(gx, P.nx, P.bc[0], P.bc[1]) : 0;
@@ -737,7 +738,7 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                 const S* st = reinterpret_cast<const S*>(smem_raw + (size_t)s * Sh::kStageOne);
                 const int mz = map_coord(p, P.nz, P.bc[4], P.bc[5]);
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
+                for (int j = 0; j < J; ++j) {
                     if (!use[j]) continue;
                     float f[19], g[7];
                     stage_pulls<Sh>(P, st + woff[j], src, mxs[j], mys[j], mz, f, g);

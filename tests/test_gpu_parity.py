@@ -223,3 +223,37 @@ def test_parity_full_size_pool_boiling_200x200x300():
     print("full size", err)
     for k, v in err.items():
         assert v <= BAR, (k, v, err)
+
+
+def test_evaporating_droplet_follows_the_d2_law():
+    """Sec. IV.A: a droplet at 0.86 Tc in vapour held at 0.95 Tc evaporates with (D/D0)^2 linear
+    in time once the start-up transient has passed (the paper's D^2 law; slope not pinned).
+    D = (6 V / pi)^(1/3), V = nodes above the mid density (rho_l + rho_v) / 2.  The fit starts at
+    step 3500: before that the interface is still relaxing; later the closed 64^3 box slowly
+    fills with vapour and the rate eases (measured R^2 0.976 from step 2500, 0.983 from 3500)."""
+    import oracle
+    from paper_2201_06039_gb300 import lbm
+    case = W.evaporation(64, R0=16.0)
+    rho, T, u = inputs(case)
+    s = case["setup"]
+    Tc = oracle.Tc_of(s)
+    rl, rv, _ = oracle.maxwell(s, 0.86 * Tc)
+    mid = 0.5 * (rl + rv)
+    lat = lbm.Lattice(lbm.params_from_setup(s))
+    lat.init(rho.astype(np.float32), T.astype(np.float32))
+    times, d2 = [], []
+    for k in range(16):
+        lat.step(500)
+        r = lat.moments()["rho"]
+        D = (6.0 * float((r > mid).sum()) / np.pi) ** (1.0 / 3.0)
+        times.append(500 * (k + 1))
+        d2.append(D * D)
+    lat.close()
+    t = np.array(times[6:], dtype=float)
+    y = np.array(d2[6:]) / d2[0]
+    A = np.vstack([t, np.ones_like(t)]).T
+    coef, res, _, _ = np.linalg.lstsq(A, y, rcond=None)
+    r2 = 1.0 - float(res[0]) / float(((y - y.mean()) ** 2).sum())
+    print("D^2/D0^2", np.round(np.array(d2) / d2[0], 4).tolist(), "slope", coef[0], "R2", r2)
+    assert coef[0] < 0, "the droplet must shrink"
+    assert r2 >= 0.98, r2
