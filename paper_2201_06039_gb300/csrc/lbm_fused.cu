@@ -787,15 +787,18 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
             // phi_s history of the thread's node, loaded one plane ahead of its use
             float ph_next = owner ? phis[node_of(P, gx, gy, z0)] : 0.f;
             for (int p = z0 - 1; p <= z1; ++p, ++k) {
-                wait(&ring_full[k % kRing], (k / kRing) & 1);   // psi(p) ready
-                if (p == z0 - 1) {                               // plane z0-1: psi only
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&empty_bar[k % kStages]);
-                    continue;
+                if (p <= z0) {
+                    wait(&ring_full[k % kRing], (k / kRing) & 1);   // psi(p) ready
+                    if (p == z0 - 1) {                               // plane z0-1: psi only
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&empty_bar[k % kStages]);
+                    }
+                    continue;   // plane z0 is collided once psi(z0+1) is ready
                 }
-                if (p == z0) continue;   // plane z0 is collided once psi(z0+1) is ready
                 const int z = p - 1;     // collide plane z in [z0, z1) with ring planes z-1, z, z+1
                 const unsigned kz = k - 1;
+                // the pulls of plane z come first, so that its stage is released before the wait
+                // for psi(z+1)
                 wait(&full_bar[kz % kStages], (kz / kStages) & 1);
                 const float ph_prev = ph_next;
                 if (owner && z + 1 < z1) ph_next = phis[node_of(P, gx, gy, z + 1)];
@@ -806,6 +809,7 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                 }
                 __syncwarp();       // pulls are in registers: the stage of plane z may be refilled
                 if (lane == 0) mbar_arrive(&empty_bar[kz % kStages]);
+                wait(&ring_full[k % kRing], (k / kRing) & 1);   // psi(z+1) ready
                 float2 me = make_float2(0.f, 0.f);
                 float T = 0.f;
                 RingStencil rs = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
