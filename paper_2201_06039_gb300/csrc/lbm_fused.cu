@@ -13,11 +13,13 @@
 // the buoyancy force is the deterministic FP64 mean of this step's rho, used by the next step.
 //
 // k_fused     : generic (any faces, any storage precision, frozen f or g, first step).
-// k_fused_tma : FP32, f-periodic x and y faces (any z faces).  A producer warp fetches each
-//               plane's pulls for the whole tile + halo with three TMA tensor copies (one per
-//               e_z group of population slots) into a 3-stage shared-memory pipeline guarded by
-//               mbarriers; 11 consumer warps read every pull as one shared-memory load at a
-//               fixed offset.  Persistent CTAs take (z-chunk, tile) items round robin.
+// k_fused_tma : FP32 or shifted 16-bit storage, f-periodic x and y faces (any z faces).  A
+//               producer warp fetches each plane's pulls for the whole tile + halo with three TMA
+//               tensor copies (one per e_z group of population slots) into a multi-stage
+//               shared-memory pipeline guarded by mbarriers; psi warps and collision warps read
+//               every pull as one shared-memory load at a fixed offset.  FP32 planes leave through
+//               TMA tensor stores, 16-bit planes through direct stores of the collision threads.
+//               Persistent CTAs take (z-chunk, tile) items round robin.
 #include <cuda.h>
 #include "lbm_launch.h"
 
@@ -250,7 +252,7 @@ k_fused(DevParams P, const S* __restrict__ src, S* __restrict__ dst, int pull_f,
         const double* __restrict__ sums_cur, double2* partial, unsigned* counter, double* sums_next,
         float* __restrict__ phis, int* flag, int first, int zchunk) {
     using Sh = FusedShape<TY>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     float* stage = reinterpret_cast<float*>(smem_raw);                       // [2][26][TY][32]
     float2* ring = reinterpret_cast<float2*>(stage + 2 * Sh::kStageFloats);  // [3][TY+2][34]
     __shared__ double red_a[Sh::kThreads / 32], red_b[Sh::kThreads / 32];
@@ -285,7 +287,7 @@ k_fused_batch(DevParams P, const BatchInst* __restrict__ insts, const BatchItem*
               const double* __restrict__ sums_cur, double2* partial, unsigned* counters, double* sums_next,
               float* __restrict__ phis, int* flag, int first) {
     using Sh = FusedShape<TY>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
     float* stage = reinterpret_cast<float*>(smem_raw);
     float2* ring = reinterpret_cast<float2*>(stage + 2 * Sh::kStageFloats);
     __shared__ double red_a[Sh::kThreads / 32], red_b[Sh::kThreads / 32];
@@ -356,7 +358,13 @@ template <int TX_, int TY_, typename S_ = float> struct TmaShape {
     static constexpr int kColWarps = (kInterior + 31) / 32;          // collision: one node per thread
     static constexpr int kPsiThreads = kPsiWarps * 32, kColThreads = kColWarps * 32;
     static constexpr int kPsiPerThread = (kSlotsAll + kPsiThreads - 1) / kPsiThreads;
-    static constexpr int kThreads = 64 + kPsiThreads + kColThreads;  // producer warp, storer warp first
+    // Output path.  FP32: the collided plane goes to an output tile in shared memory and leaves by
+    // TMA tensor stores issued by a storer warp.  16-bit storage: every collision thread stores its
+    // populations straight to global memory (no output tile, no storer warp), which frees shared
+    // memory for the L1 cache and measured faster for 2-byte elements.
+    static constexpr bool kDirect = kE == 2;
+    static constexpr int kLeadWarps = kDirect ? 1 : 2;              // producer (+ storer) warps first
+    static constexpr int kThreads = 32 * kLeadWarps + kPsiThreads + kColThreads;
     // registers per thread: the SM's 64K for one CTA, whose warps are allocated in groups of four
     // (threads rounded up to 128) and whose per-thread count goes in steps of 8
     static constexpr int kAllocThreads = (kThreads + 127) / 128 * 128;
@@ -386,8 +394,8 @@ template <int TX_, int TY_, typename S_ = float> struct TmaShape {
     static constexpr size_t kGRowBytes = align128((size_t)2 * kSlots * TX_ * kE);
     static constexpr size_t kGCorBytes = align128((size_t)2 * kSlots * kGW * kE);
     static constexpr size_t kGhostBytes = kGColBytes + kGRowBytes + kGCorBytes;
-    static constexpr size_t kSmem = kStageBytes + kOutBytes + kGhostBytes +
-                                    (size_t)kRing * kRingPlane * (sizeof(float2) + sizeof(float));
+    static constexpr size_t kRingOff = kStageBytes + (kDirect ? 0 : kOutBytes + kGhostBytes);
+    static constexpr size_t kSmem = kRingOff + (size_t)kRing * kRingPlane * (sizeof(float2) + sizeof(float));
     // element offset of storage slot s inside a stage
     static constexpr __host__ __device__ int slot_off(int s) {
         return s < 14 ? s * kWin : s < 20 ? (int)(kGrp1 / kE) + (s - 14) * kWin : (int)(kGrp2 / kE) + (s - 20) * kWin;
@@ -557,14 +565,14 @@ __device__ __forceinline__ void stage_pulls(const DevParams& P, const typename S
         g[4] = -st_dec<S>(b[Sh::slot_off(gslot(3))], P.shift_g[3]) + 2.f * P.w1 * wall_T(P, 3, mx, my);
 }
 
-// Warp roles: warp 0 = producer (TMA loads), warp 1 = storer (TMA stores), the next kPsiWarps =
-// psi pass, the rest = collision.  Every hand-off goes through an mbarrier:
+// Warp roles: warp 0 = producer (TMA loads), warp 1 = storer (TMA stores; FP32 only), the next
+// kPsiWarps = psi pass, the rest = collision.  Every hand-off goes through an mbarrier:
 //   full[s]      TMA bytes of the stage landed              (producer  -> psi, collision)
 //   empty[s]     psi pass and collision done with a stage    (psi, collision -> producer)
 //   ring_full[r] (psi, rho) of a plane in ring slot r ready   (psi       -> collision)
 //   ring_empty[r] last collision reading ring slot r done     (collision -> psi)
-//   out_full     collided plane written to the out buffer    (collision -> storer)
-//   out_empty    tensor store has read the out buffer         (storer    -> collision)
+//   out_full     collided plane written to the out buffer    (collision -> storer; FP32)
+//   out_empty    tensor store has read the out buffer         (storer    -> collision; FP32)
 // Stage uses and ring uses follow one plane counter k across the CTA's items; out-buffer uses
 // follow the collided-plane counter u.
 template <int TX_, int TY_, typename S>
@@ -574,6 +582,7 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
             const __grid_constant__ CUtensorMap map_gcol, const __grid_constant__ CUtensorMap map_gcol_top,
             const __grid_constant__ CUtensorMap map_grow, const __grid_constant__ CUtensorMap map_grow_right,
             const __grid_constant__ CUtensorMap map_gcor, int ghosts, DevParams P, const S* __restrict__ src,
+            S* __restrict__ dst,
             const double* __restrict__ sums_cur, double2* partial, unsigned* counter, double* sums_next,
             float* __restrict__ phis, int* flag, int first, int zchunk, int tiles_x, int tiles_y, int n_items) {
     using Sh = TmaShape<TX_, TY_, S>;
@@ -586,7 +595,7 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
     S* grow = reinterpret_cast<S*>(smem_raw + Sh::kStageBytes + Sh::kOutBytes + Sh::kGColBytes);  // [2][26][w]
     S* gcor = reinterpret_cast<S*>(smem_raw + Sh::kStageBytes + Sh::kOutBytes + Sh::kGColBytes +
                                    Sh::kGRowBytes);                              // [2][26][kGW]
-    float2* ring = reinterpret_cast<float2*>(smem_raw + Sh::kStageBytes + Sh::kOutBytes + Sh::kGhostBytes);  // [4][TY+2][TX+2]
+    float2* ring = reinterpret_cast<float2*>(smem_raw + Sh::kRingOff);           // [4][TY+2][TX+2]
     float* tring = reinterpret_cast<float*>(ring + kRing * Sh::kRingPlane);      // [4][TY+2][TX+2] T
     __shared__ __align__(8) unsigned long long full_bar[kStages], empty_bar[kStages], ring_full[kRing],
         ring_empty[kRing], out_full, out_empty;
@@ -664,7 +673,7 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                 mbar_wait(&full_bar[q % kStages], (q / kStages) & 1);
         }
         __syncwarp();
-    } else if (warp == 1) {
+    } else if (!Sh::kDirect && warp == 1) {
         // ------------------------------------------------------------ storer (one lane)
         if (lane == 0) {
             unsigned u = 0;
@@ -701,9 +710,9 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
             bulk_wait_all();   // the stores have completed before the CTA exits
         }
         __syncwarp();
-    } else if (warp < 2 + Sh::kPsiWarps) {
+    } else if (warp < Sh::kLeadWarps + Sh::kPsiWarps) {
         // ------------------------------------------------------------ psi pass
-        const int pt = tid - 64;
+        const int pt = tid - 32 * Sh::kLeadWarps;
         constexpr int J = Sh::kPsiPerThread;
         int lxs[J], lys[J];
 #pragma unroll
@@ -760,7 +769,7 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
         if (bad) atomicOr(flag, 1);
     } else {
         // ------------------------------------------------------------ collision
-        const int ct = tid - 64 - Sh::kPsiThreads;
+        const int ct = tid - 32 * Sh::kLeadWarps - Sh::kPsiThreads;
         const bool node_thread = ct < Sh::kInterior;
         const int lx = ct % TX_ + 1, ly = ct / TX_ + 1;
         const int slot = ly * Sh::kRingW + lx;
@@ -783,6 +792,10 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                                         : ebottom ? (gy < 2 ? gy : -1) : -1;
             // the edge-row tile is as wide as the tile's real columns (the box reads it densely)
             const int rw = min(TX_, P.nx - x0);
+            // direct stores: periodic images of this node in the ghost cells, columns within kGW of
+            // an x edge and rows within 2 of a y edge (0: none)
+            const int gxi = !(Sh::kDirect && owner && ghosts) ? 0 : gx < kGW ? P.nx : gx >= P.nx - kGW ? -P.nx : 0;
+            const int gyi = !(Sh::kDirect && owner && ghosts) ? 0 : gy < 2 ? P.ny : gy >= P.ny - 2 ? -P.ny : 0;
             float r_sum = 0.f, r_c = 0.f, t_sum = 0.f, t_c = 0.f;
             // phi_s history of the thread's node, loaded one plane ahead of its use
             float ph_next = owner ? phis[node_of(P, gx, gy, z0)] : 0.f;
@@ -834,44 +847,65 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                     NodeOut o = collide_f(P, f, rho, Fmx + db * P.gx, Fmy + db * P.gy, Fmz + db * P.gz, Fm2, me.x * me.x);
                     ph = collide_g(P, g, rho, T, o, rs.gx, rs.gy, rs.gz, ph_prev, first);
                 }
-                // the out buffer is free once the tensor store of the previous plane has read it
-                if (u > 0) wait(&out_empty, (u - 1) & 1);
-                if (owner) {
-                    S fe[19], ge[7];   // stored form of f*, g+
+                if constexpr (Sh::kDirect) {
+                    if (owner) {
+                        S fe[19], ge[7];   // stored form of f*, g+
 #pragma unroll
-                    for (int a = 0; a < 19; ++a) fe[a] = st_enc<S>(f[a], P.shift_f[a]);
+                        for (int a = 0; a < 19; ++a) fe[a] = st_enc<S>(f[a], P.shift_f[a]);
 #pragma unroll
-                    for (int a = 0; a < 7; ++a) ge[a] = st_enc<S>(g[a], P.shift_g[a]);
+                        for (int a = 0; a < 7; ++a) ge[a] = st_enc<S>(g[a], P.shift_g[a]);
+                        auto put = [&](int xx, int yy) {
+                            S* d = dst + sidx(P, xx, yy, z);
 #pragma unroll
-                    for (int a = 0; a < 19; ++a) outp[fslot(a) * TX_] = fe[a];
+                            for (int a = 0; a < 19; ++a) d[(size_t)fslot(a) * P.Ns] = fe[a];
 #pragma unroll
-                    for (int a = 0; a < 7; ++a) outp[gslot(a) * TX_] = ge[a];
-                    if (cx4 >= 0) {   // edge column: [TY][26][kGW]
-                        S* q = gcol + (ly - 1) * (kSlots * kGW) + cx4;
-#pragma unroll
-                        for (int a = 0; a < 19; ++a) q[fslot(a) * kGW] = fe[a];
-#pragma unroll
-                        for (int a = 0; a < 7; ++a) q[gslot(a) * kGW] = ge[a];
+                            for (int a = 0; a < 7; ++a) d[(size_t)gslot(a) * P.Ns] = ge[a];
+                        };
+                        put(gx, gy);
+                        if (gxi) put(gx + gxi, gy);
+                        if (gyi) put(gx, gy + gyi);
+                        if (gxi && gyi) put(gx + gxi, gy + gyi);
                     }
-                    if (ry2 >= 0) {   // edge row: [2][26][rw]
-                        S* q = grow + ry2 * (kSlots * rw) + (lx - 1);
+                } else {
+                    // the out buffer is free once the tensor store of the previous plane has read it
+                    if (u > 0) wait(&out_empty, (u - 1) & 1);
+                    if (owner) {
+                        S fe[19], ge[7];   // stored form of f*, g+
 #pragma unroll
-                        for (int a = 0; a < 19; ++a) q[fslot(a) * rw] = fe[a];
+                        for (int a = 0; a < 19; ++a) fe[a] = st_enc<S>(f[a], P.shift_f[a]);
 #pragma unroll
-                        for (int a = 0; a < 7; ++a) q[gslot(a) * rw] = ge[a];
+                        for (int a = 0; a < 7; ++a) ge[a] = st_enc<S>(g[a], P.shift_g[a]);
+#pragma unroll
+                        for (int a = 0; a < 19; ++a) outp[fslot(a) * TX_] = fe[a];
+#pragma unroll
+                        for (int a = 0; a < 7; ++a) outp[gslot(a) * TX_] = ge[a];
+                        if (cx4 >= 0) {   // edge column: [TY][26][kGW]
+                            S* q = gcol + (ly - 1) * (kSlots * kGW) + cx4;
+#pragma unroll
+                            for (int a = 0; a < 19; ++a) q[fslot(a) * kGW] = fe[a];
+#pragma unroll
+                            for (int a = 0; a < 7; ++a) q[gslot(a) * kGW] = ge[a];
+                        }
+                        if (ry2 >= 0) {   // edge row: [2][26][rw]
+                            S* q = grow + ry2 * (kSlots * rw) + (lx - 1);
+#pragma unroll
+                            for (int a = 0; a < 19; ++a) q[fslot(a) * rw] = fe[a];
+#pragma unroll
+                            for (int a = 0; a < 7; ++a) q[gslot(a) * rw] = ge[a];
+                        }
+                        if (cx4 >= 0 && ry2 >= 0) {   // corner block: [2][26][kGW]
+                            S* q = gcor + ry2 * (kSlots * kGW) + cx4;
+#pragma unroll
+                            for (int a = 0; a < 19; ++a) q[fslot(a) * kGW] = fe[a];
+#pragma unroll
+                            for (int a = 0; a < 7; ++a) q[gslot(a) * kGW] = ge[a];
+                        }
                     }
-                    if (cx4 >= 0 && ry2 >= 0) {   // corner block: [2][26][kGW]
-                        S* q = gcor + ry2 * (kSlots * kGW) + cx4;
-#pragma unroll
-                        for (int a = 0; a < 19; ++a) q[fslot(a) * kGW] = fe[a];
-#pragma unroll
-                        for (int a = 0; a < 7; ++a) q[gslot(a) * kGW] = ge[a];
-                    }
+                    // every lane's out writes become visible to the tensor store before lane 0 signals
+                    fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&out_full);
                 }
-                // every lane's out writes become visible to the tensor store before lane 0 signals
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&out_full);
                 if (owner) phis[node_of(P, gx, gy, z)] = ph;
                 ++u;
             }
@@ -1050,7 +1084,8 @@ cudaError_t launch_fused(const DevParams& P, int precision, const StateBufs& B, 
                 maps->m14[B.src_index], maps->m6[B.src_index], maps->mout[B.src_index ^ 1],                    \
                 maps->mout_top[B.src_index ^ 1], maps->mgcol[B.src_index ^ 1], maps->mgcol_top[B.src_index ^ 1], \
                 maps->mgrow[B.src_index ^ 1], maps->mgrow_right[B.src_index ^ 1], maps->mgcor[B.src_index ^ 1], \
-                maps->ghosts ? 1 : 0, P, (const ST*)B.src, sums_cur, B.partial, B.counter, sums_next, B.phis,   \
+                maps->ghosts ? 1 : 0, P, (const ST*)B.src, (ST*)B.dst, sums_cur, B.partial, B.counter,          \
+                sums_next, B.phis,                                                                             \
                 B.flag, first, maps->zchunk, txs, tys, maps->items);                                           \
         }
         if (precision == 0) {
