@@ -172,7 +172,7 @@ __device__ __forceinline__ float wall_T(const DevParams& P, int face, int x, int
     float T = P.T_wall[face];
     if (face == 4 && P.hot_dT != 0.f) {
         float dx = (float)x - P.hot_cx, dy = (float)y - P.hot_cy;
-        T += P.hot_dT * expf(-(dx * dx + dy * dy) * P.hot_inv2s2);
+        T += P.hot_dT * expf(-__fmaf_rn(dy, dy, __fmul_rn(dx, dx)) * P.hot_inv2s2);
     }
     return T;
 }
@@ -301,6 +301,11 @@ __device__ __forceinline__ float sum7(const float g[7]) {
 }
 
 // ---------------------------------------------------------------- thermodynamics
+// Rounding.  Where two or more products are summed, the sum is written with explicit
+// __fmaf_rn / __fmul_rn: left as plain arithmetic, the compiler may fuse either product into the
+// add and chooses differently in different kernels, so kernels that share these functions would
+// no longer round alike (a sum with one product has one fusion and is left to the compiler).
+//
 // Peng-Robinson pressure (Eq. 49) and psi^2 = 2 (p_EOS - rho cs^2) / (G c^2) with G = -1 (Eq. 8).
 __device__ __forceinline__ float psi_of(float psi2) { return psi2 * rsqrtf(psi2); }   // sqrt; NaN if <= 0
 __device__ __forceinline__ float psi_squared(const DevParams& P, float rho, float T) {
@@ -310,7 +315,7 @@ __device__ __forceinline__ float psi_squared(const DevParams& P, float rho, floa
     float brho = P.b * rho;
     float d1 = 1.f - brho, d2 = 1.f + 2.f * brho - brho * brho;
     float inv = __fdividef(1.f, d1 * d2);   // one reciprocal for both denominators
-    float p = rho * P.R * T * (d2 * inv) - P.a * theta * rho * rho * (d1 * inv);
+    float p = __fmaf_rn(-(P.a * theta * rho * rho), d1 * inv, __fmul_rn(rho * P.R * T, d2 * inv));
     return 2.f * (rho * (1.f / 3.f) - p);
 }
 
@@ -342,9 +347,31 @@ __device__ __forceinline__ void back_transform(float rho, float ax, float bx, fl
 }
 
 // ---------------------------------------------------------------- D3Q19 MRT collision
+// One moment of Eq. 3: m* = m - L (m - m_eq) + (1 - L/2) S = m + (-L (m - m_eq) + h S), with every
+// rounding step explicit.  Written as plain arithmetic the sum of two products leaves the compiler
+// free to fuse either product into the add, and it chose differently in different kernels.
+__device__ __forceinline__ float relax(float m, float eq, float S, float L, float h) {
+    return __fadd_rn(m, __fmaf_rn(-L, __fsub_rn(m, eq), __fmul_rn(h, S)));
+}
+
 struct NodeOut {
     float ux, uy, uz, divu, inv_rho;
 };
+
+// Interaction force F_m = -G psi sum_a w_a psi(x + e_a) e_a (Eq. 7, G = -1) from the stencil sums
+// (sx, sy, sz), |F_m|^2, and the total force F = F_m + (rho - rho_ave) g (buoyancy).
+struct Forces {
+    float Fx, Fy, Fz, Fm2;
+};
+__device__ __forceinline__ Forces total_force(const DevParams& P, float psi, float sx, float sy, float sz, float db) {
+    const float mx = __fmul_rn(psi, sx), my = __fmul_rn(psi, sy), mz = __fmul_rn(psi, sz);
+    Forces F;
+    F.Fm2 = __fmaf_rn(mz, mz, __fmaf_rn(my, my, __fmul_rn(mx, mx)));
+    F.Fx = __fmaf_rn(db, P.gx, mx);
+    F.Fy = __fmaf_rn(db, P.gy, my);
+    F.Fz = __fmaf_rn(db, P.gz, mz);
+    return F;
+}
 
 // In: post-streaming f with rho = sum19(f), total force F, interaction force Fm, psi^2.
 // Out: f* in place.
@@ -375,8 +402,8 @@ __device__ __forceinline__ NodeOut collide_f(const DevParams& P, float f[19], fl
     float m10 = d7 - d9, m11 = d7 + d9, m12 = d11 - d13, m13 = d11 + d13, m14 = d15 - d17, m15 = d15 + d17;
 
     // equilibrium moments (Eq. 5)
-    float ux2 = ux * ux, uy2 = uy * uy, uz2 = uz * uz, u2 = ux2 + uy2 + uz2;
-    float phi = rho * (cs2 * cs2) * (1.f - 1.5f * u2);
+    float ux2 = __fmul_rn(ux, ux), uy2 = __fmul_rn(uy, uy), uz2 = __fmul_rn(uz, uz), u2 = ux2 + uy2 + uz2;
+    float phi = __fmul_rn(rho * (cs2 * cs2), 1.f - 1.5f * u2);
     float e4 = rho + rho * u2;
     float e5 = rho * (2.f * ux2 - uy2 - uz2), e6 = rho * (uy2 - uz2);
     float e7 = rho * ux * uy, e8 = rho * ux * uz, e9 = rho * uy * uz;
@@ -387,10 +414,11 @@ __device__ __forceinline__ NodeOut collide_f(const DevParams& P, float f[19], fl
     float e18 = phi + rho * cs2 * (uy2 + uz2);
 
     // forcing moments (Eq. 9)
-    float Fu_x = Fx * ux, Fu_y = Fy * uy, Fu_z = Fz * uz;
-    float S4 = 2.f * (Fu_x + Fu_y + Fu_z) + P.sigma6 * __fdividef(Fm2, psi2);
+    float Fu_x = __fmul_rn(Fx, ux), Fu_y = __fmul_rn(Fy, uy), Fu_z = __fmul_rn(Fz, uz);
+    float S4 = __fmaf_rn(P.sigma6, __fdividef(Fm2, psi2), 2.f * (Fu_x + Fu_y + Fu_z));
     float S5 = 2.f * (2.f * Fu_x - Fu_y - Fu_z), S6 = 2.f * (Fu_y - Fu_z);
-    float S7 = Fx * uy + Fy * ux, S8 = Fx * uz + Fz * ux, S9 = Fy * uz + Fz * uy;
+    float S7 = __fmaf_rn(Fy, ux, __fmul_rn(Fx, uy)), S8 = __fmaf_rn(Fz, ux, __fmul_rn(Fx, uz));
+    float S9 = __fmaf_rn(Fz, uy, __fmul_rn(Fy, uz));
     float S10 = cs2 * Fy, S11 = cs2 * Fx, S12 = cs2 * Fz, S13 = cs2 * Fx, S14 = cs2 * Fz, S15 = cs2 * Fy;
     float S16 = 2.f * cs2 * (Fu_x + Fu_y), S17 = 2.f * cs2 * (Fu_x + Fu_z), S18 = 2.f * cs2 * (Fu_y + Fu_z);
 
@@ -398,32 +426,33 @@ __device__ __forceinline__ NodeOut collide_f(const DevParams& P, float f[19], fl
     o.ux = ux; o.uy = uy; o.uz = uz;
     o.inv_rho = inv_rho;
     // Eq. 48 (pre-collision m_4, force-corrected u, full S_4, total F)
-    o.divu = (-(m4 - e4) * P.inv_tau_e + P.half_Le * S4 - 2.f * (Fu_x + Fu_y + Fu_z)) * (1.5f * inv_rho);
+    o.divu = (__fmaf_rn(P.half_Le, S4, __fmul_rn(-(m4 - e4), P.inv_tau_e)) - 2.f * (Fu_x + Fu_y + Fu_z)) *
+             (1.5f * inv_rho);
 
     // relaxation (Eq. 3): m* = m - L (m - meq) + (1 - L/2) S
     const float Le = P.Le, Lv = P.Lv, Lq = P.Lq, Lp = P.Lpi;
     float r1 = jx + Fx, r2 = jy + Fy, r3 = jz + Fz;   // rates 1: m* = rho u + F/2 = j + F
-    m4 += -Le * (m4 - e4) + (1.f - 0.5f * Le) * S4;
-    m5 += -Lv * (m5 - e5) + (1.f - 0.5f * Lv) * S5;
-    m6 += -Lv * (m6 - e6) + (1.f - 0.5f * Lv) * S6;
-    m7 += -Lv * (m7 - e7) + (1.f - 0.5f * Lv) * S7;
-    m8 += -Lv * (m8 - e8) + (1.f - 0.5f * Lv) * S8;
-    m9 += -Lv * (m9 - e9) + (1.f - 0.5f * Lv) * S9;
-    const float hq = 1.f - 0.5f * Lq, hp = 1.f - 0.5f * Lp;
-    m10 += -Lq * (m10 - e10) + hq * S10;
-    m11 += -Lq * (m11 - e11) + hq * S11;
-    m12 += -Lq * (m12 - e12) + hq * S12;
-    m13 += -Lq * (m13 - e13) + hq * S13;
-    m14 += -Lq * (m14 - e14) + hq * S14;
-    m15 += -Lq * (m15 - e15) + hq * S15;
-    m16 += -Lp * (m16 - e16) + hp * S16;
-    m17 += -Lp * (m17 - e17) + hp * S17;
-    m18 += -Lp * (m18 - e18) + hp * S18;
+    const float he = 1.f - 0.5f * Le, hv = 1.f - 0.5f * Lv, hq = 1.f - 0.5f * Lq, hp = 1.f - 0.5f * Lp;
+    m4 = relax(m4, e4, S4, Le, he);
+    m5 = relax(m5, e5, S5, Lv, hv);
+    m6 = relax(m6, e6, S6, Lv, hv);
+    m7 = relax(m7, e7, S7, Lv, hv);
+    m8 = relax(m8, e8, S8, Lv, hv);
+    m9 = relax(m9, e9, S9, Lv, hv);
+    m10 = relax(m10, e10, S10, Lq, hq);
+    m11 = relax(m11, e11, S11, Lq, hq);
+    m12 = relax(m12, e12, S12, Lq, hq);
+    m13 = relax(m13, e13, S13, Lq, hq);
+    m14 = relax(m14, e14, S14, Lq, hq);
+    m15 = relax(m15, e15, S15, Lq, hq);
+    m16 = relax(m16, e16, S16, Lp, hp);
+    m17 = relax(m17, e17, S17, Lp, hp);
+    m18 = relax(m18, e18, S18, Lp, hp);
 
     // back-transform f* = M^-1 m* (closed form of the raw-moment inverse).  The rest population
     // is formed last as rho - sum of the others, so that FP32 rounding (e.g. of the 1/3 factor)
     // cannot drift the mass: m_0* = rho exactly as Eq. 3 demands.
-    float X = (m4 + m5) * (1.f / 3.f);
+    float X = __fmul_rn(m4 + m5, 1.f / 3.f);
     float Y = 0.5f * (m4 - X + m6);
     float Z = 0.5f * (m4 - X - m6);
     float ax = X - m16 - m17, bx = r1 - m11 - m13;
@@ -473,27 +502,28 @@ __device__ __forceinline__ float collide_g(const DevParams& P, float g[7], float
     float gTx = k * n1, gTy = k * n2, gTz = k * n3;
     float phis = 0.f;
     if (!P.flow_off) {
-        phis = (chi * grx * inv_rho - o.ux) * gTx + (chi * gry * inv_rho - o.uy) * gTy +
-               (chi * grz * inv_rho - o.uz) * gTz;
+        phis = __fmaf_rn(chi * grz * inv_rho - o.uz, gTz,
+                         __fmaf_rn(chi * gry * inv_rho - o.uy, gTy, __fmul_rn(chi * grx * inv_rho - o.ux, gTx)));
         // T/(rho cV) (dp/dT)_rho div u with (dp/dT)_rho ~ rho R / (1 - b rho)
         phis -= __fdividef(T * P.R_over_cV, 1.f - P.b * rho) * o.divu;
     }
     float C = first ? phis : phis_prev;
-    float qs = 1.5f * phis - 0.5f * C;               // Q_a = w_a (3/2 phi_s(t) - 1/2 phi_s(t-1))
+    float qs = __fmaf_rn(-0.5f, C, __fmul_rn(1.5f, phis));   // Q_a = w_a (3/2 phi_s(t) - 1/2 phi_s(t-1))
     float om = 1.f - inv_vsT;
-    n1 *= om; n2 *= om; n3 *= om;
-    n4 = n4 - P.Gq * (n4 - P.d * T);                 // 3 cs_T^2 T = d T
-    n5 *= 1.f - P.Gpi;
-    n6 *= 1.f - P.Gpi;
+    n1 = __fmul_rn(n1, om); n2 = __fmul_rn(n2, om); n3 = __fmul_rn(n3, om);
+    // n4* = n4 - Gq (n4 - d T) with 3 cs_T^2 T = d T; explicit rounding as in relax()
+    n4 = __fsub_rn(n4, __fmul_rn(P.Gq, __fsub_rn(n4, __fmul_rn(P.d, T))));
+    n5 = __fmul_rn(n5, 1.f - P.Gpi);
+    n6 = __fmul_rn(n6, 1.f - P.Gpi);
     // g* = N^-1 n* (Eq. 41); g*_0 = T - sum g*_1..6 keeps sum g* = T free of rounding drift
     // (n_0* = T; a rounded 1/6 factor would otherwise bias it); then g+ = g* + Q (Eq. 40).
     const float s6 = 1.f / 6.f;
     float n456 = n4 + n5 + n6;
-    float h1 = s6 * (n456 + 3.f * n1), h2 = s6 * (n456 - 3.f * n1);
+    float h1 = __fmul_rn(s6, n456 + 3.f * n1), h2 = __fmul_rn(s6, n456 - 3.f * n1);
     float n4_5 = n4 - 2.f * n5 + n6;
-    float h3 = s6 * (n4_5 + 3.f * n2), h4 = s6 * (n4_5 - 3.f * n2);
+    float h3 = __fmul_rn(s6, n4_5 + 3.f * n2), h4 = __fmul_rn(s6, n4_5 - 3.f * n2);
     float n4_6 = n4 + n5 - 2.f * n6;
-    float h5 = s6 * (n4_6 + 3.f * n3), h6 = s6 * (n4_6 - 3.f * n3);
+    float h5 = __fmul_rn(s6, n4_6 + 3.f * n3), h6 = __fmul_rn(s6, n4_6 - 3.f * n3);
     float h0 = T - ((h1 + h2) + (h3 + h4) + (h5 + h6));
     float q0 = P.w0 * qs, q1 = P.w1 * qs;
     g[0] = h0 + q0;

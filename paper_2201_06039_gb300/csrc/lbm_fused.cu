@@ -217,10 +217,8 @@ __device__ __forceinline__ void fused_column(const DevParams& P, const S* __rest
         const float2* rp = ring + ((z + 1) % 3) * Sh::kRingPlane;
         const float2 me = r0[slot];
         RingStencil rs = ring_stencil(rm, r0, rp, slot, Sh::kRingW);
-        float Fmx = me.x * rs.Fx, Fmy = me.x * rs.Fy, Fmz = me.x * rs.Fz;
-        float db = rho - rho_ave;
-        float Fm2 = Fmx * Fmx + Fmy * Fmy + Fmz * Fmz;
-        NodeOut o = collide_f(P, f, rho, Fmx + db * P.gx, Fmy + db * P.gy, Fmz + db * P.gz, Fm2, me.x * me.x);
+        const Forces F = total_force(P, me.x, rs.Fx, rs.Fy, rs.Fz, rho - rho_ave);
+        NodeOut o = collide_f(P, f, rho, F.Fx, F.Fy, F.Fz, F.Fm2, me.x * me.x);
         float ph = collide_g(P, g, rho, T, o, rs.gx, rs.gy, rs.gz, phis[d], first);
         // frozen fields keep their stored values (no streaming, no collision)
         if (P.flow_off) {
@@ -841,10 +839,8 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                     const float rho = me.y;
                     kahan_add(r_sum, r_c, rho);
                     kahan_add(t_sum, t_c, T);
-                    const float Fmx = me.x * rs.Fx, Fmy = me.x * rs.Fy, Fmz = me.x * rs.Fz;
-                    const float db = rho - rho_ave;
-                    const float Fm2 = Fmx * Fmx + Fmy * Fmy + Fmz * Fmz;
-                    NodeOut o = collide_f(P, f, rho, Fmx + db * P.gx, Fmy + db * P.gy, Fmz + db * P.gz, Fm2, me.x * me.x);
+                    const Forces F = total_force(P, me.x, rs.Fx, rs.Fy, rs.Fz, rho - rho_ave);
+                    NodeOut o = collide_f(P, f, rho, F.Fx, F.Fy, F.Fz, F.Fm2, me.x * me.x);
                     ph = collide_g(P, g, rho, T, o, rs.gx, rs.gy, rs.gz, ph_prev, first);
                 }
                 if constexpr (Sh::kDirect) {

@@ -149,12 +149,9 @@ __global__ void __launch_bounds__(TPB) k_collide(DevParams P, const S* __restric
     float rho = sum19(f), T = sum7(g);
     float2 me = __ldg(psirho + d);
     Stencil st = stencil(P, psirho, x, y, z, n);
-    float Fmx = me.x * st.Fx, Fmy = me.x * st.Fy, Fmz = me.x * st.Fz;
     float rho_ave = buoyancy_ref(P, sums_cur[0], P.inv_N);
-    float db = rho - rho_ave;
-    float Fx = Fmx + db * P.gx, Fy = Fmy + db * P.gy, Fz = Fmz + db * P.gz;
-    float Fm2 = Fmx * Fmx + Fmy * Fmy + Fmz * Fmz;
-    NodeOut o = collide_f(P, f, rho, Fx, Fy, Fz, Fm2, me.x * me.x);
+    const Forces F = total_force(P, me.x, st.Fx, st.Fy, st.Fz, rho - rho_ave);
+    NodeOut o = collide_f(P, f, rho, F.Fx, F.Fy, F.Fz, F.Fm2, me.x * me.x);
     float ph = collide_g(P, g, rho, T, o, st.gx, st.gy, st.gz, phis[d], first);
     // frozen fields keep their stored values (no streaming, no collision)
     if (P.flow_off) {

@@ -77,6 +77,17 @@ def test_parity_evaporation_thermal_faces_lambda_mode(variant):
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
+def test_parity_general_relaxation_rates(variant):
+    """Relaxation rates other than the paper's unit rates of the third- and fourth-order D3Q19
+    moments (tau_q, tau_pi, Eq. 6) and of the D3Q7 moments n_4..n_6 (varsigma_q, varsigma_pi,
+    Eq. 43): the general relaxation branch of both collisions against the oracle."""
+    s = W.LatticeSetup(28, 24, 20, sigma=W.SIGMA_STAR, tau_q=1.2, tau_pi=0.9, varsigma_q=1.1,
+                       varsigma_pi=0.95)
+    case = dict(name="general rates", setup=s, kind="droplet", R0=7.0, W=4.0, Tr_drop=0.86, Tr_gas=0.88)
+    _compare(case, 300, variant)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
 def test_parity_pool_boiling_small(variant):
     case = W.pool_boiling(40, 36, 48, height=16.0, hot_sigma=4.0)
     _compare(case, 400, variant)
@@ -130,6 +141,21 @@ def test_variants_bit_identical(variant):
     rho, T, u = inputs(case)
     ref, _ = run_gpu(case["setup"], rho, T, u, 23, **OVERRIDES["two_pass"])
     got, _ = run_gpu(case["setup"], rho, T, u, 23, **OVERRIDES[variant])
+    for k in ref:
+        assert np.array_equal(ref[k], got[k]), k
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_variants_bit_identical_general_rates(variant):
+    """The same with relaxation rates other than the paper's unit rates, where the products of
+    the relaxation (Eq. 3, Eq. 43) are inexact and any difference in how a kernel rounds them
+    would show."""
+    s = W.LatticeSetup(72, 40, 30, sigma=W.SIGMA_STAR, tau_q=1.2, tau_pi=0.9, varsigma_q=1.1,
+                       varsigma_pi=0.95)
+    case = dict(name="general rates", setup=s, kind="droplet", R0=9.0, W=4.0, Tr_drop=0.86, Tr_gas=0.88)
+    rho, T, u = inputs(case)
+    ref, _ = run_gpu(s, rho, T, u, 23, **OVERRIDES["two_pass"])
+    got, _ = run_gpu(s, rho, T, u, 23, **OVERRIDES[variant])
     for k in ref:
         assert np.array_equal(ref[k], got[k]), k
 
