@@ -62,8 +62,9 @@ typedef enum {
     LBM_KERNEL_AUTO = 0,      /* fastest available variant */
     LBM_KERNEL_TWO_PASS = 1,  /* psi/EOS kernel, then the stream-collide kernel */
     LBM_KERNEL_FUSED = 2,     /* one z-marching kernel per step (halo recomputation) */
-    LBM_KERNEL_FUSED_TMA = 3  /* reported by lbm_kernel_in_use: FUSED with TMA-fed pipeline (FP32,
-                                 x and y faces periodic or thermal-only) */
+    LBM_KERNEL_FUSED_TMA = 3  /* reported by lbm_kernel_in_use: FUSED with TMA-fed pipeline (any
+                                 storage precision; x and y faces periodic or thermal-only;
+                                 nx, ny >= 4; flow and temperature both evolving) */
 } lbm_kernel_variant;
 
 typedef struct {
