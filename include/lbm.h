@@ -176,7 +176,8 @@ int lbm_field_sum_noalloc(const float* field, long long n, double* sum_out, void
  * Many independent lattices of uneven sizes advanced together (the same update as lbm_step on
  * each, Secs. II-IV): each time step is ONE persistent kernel launch over all instances, whose
  * CTAs draw (instance, tile column, z-chunk) work items from a table, largest instances first;
- * lbm_batch_step(n) replays the n launches as a captured CUDA graph.
+ * lbm_batch_step(n) replays the n launches as a captured CUDA graph.  Every plan computes the
+ * states of single-lattice contexts bit for bit.
  *
  *   common   parameters shared by every instance (EOS, relaxation times, faces, gravity,
  *            precision, stream, use_graph, check_nonfinite); its nx, ny, nz and workspace
@@ -201,6 +202,9 @@ int lbm_batch_step(lbm_batch* b, int n);
 int lbm_batch_autotune(lbm_batch* b, int steps, double* best_ms);
 /* the plan in use: tile rows, z-chunks per column, work items, persistent CTAs (each nullable) */
 int lbm_batch_plan(const lbm_batch* b, int* tile_rows, int* z_split, int* items, int* ctas);
+/* Select a plan by its tile rows (4 or 8) and z-chunks per column (1, 2 or 4); LBM_EINVAL if
+ * there is no such plan. */
+int lbm_batch_select_plan(lbm_batch* b, int tile_rows, int z_split);
 int lbm_batch_get_moments(lbm_batch* b, float* rho, float* ux, float* uy, float* uz, float* T);
 /* sums[2k] = sum of rho, sums[2k+1] = sum of T over instance k (FP64, host pointer) */
 int lbm_batch_get_totals(lbm_batch* b, double* sums);

@@ -217,6 +217,7 @@ int check_batch_flag(lbm_batch* b) {
     GB300_CK(cudaStreamSynchronize(b->stream));
     if (h) {
         GB300_CK(cudaMemsetAsync(b->base + b->off_flag, 0, sizeof(int), b->stream));
+        if (h & 2) return fail(LBM_ETIMEOUT, "a bounded device wait gave up (step %lld)", b->steps);
         return fail(LBM_ENONFINITE, "non-finite rho/T/psi or psi^2 <= 0 in the batch after step %lld", b->steps);
     }
     return LBM_OK;
@@ -458,6 +459,13 @@ int lbm_batch_plan(const lbm_batch* b, int* tile_rows, int* z_split, int* items,
     if (items) *items = b->n_items;
     if (ctas) *ctas = b->ctas;
     return LBM_OK;
+}
+
+int lbm_batch_select_plan(lbm_batch* b, int tile_rows, int z_split) {
+    if (!b) return fail(LBM_EINVAL, "batch is NULL");
+    for (int q = 0; q < kNumPlans; ++q)
+        if (kPlans[q].ty == tile_rows && kPlans[q].zsplit == z_split) return set_plan(b, q);
+    return fail(LBM_EINVAL, "no plan with tile rows %d and %d z-chunks", tile_rows, z_split);
 }
 
 int lbm_batch_get_moments(lbm_batch* b, float* rho, float* ux, float* uy, float* uz, float* T) {

@@ -49,8 +49,8 @@ EXPORTS = ["lbm_params_default", "lbm_eos_critical", "lbm_workspace_bytes", "lbm
            "lbm_kernel_in_use",
            "lbm_step_profiled", "lbm_destroy", "lbm_status_str", "lbm_last_error", "lbm_field_sum_noalloc",
            "lbm_batch_create", "lbm_batch_nodes", "lbm_batch_init_fields", "lbm_batch_step", "lbm_batch_autotune",
-           "lbm_batch_plan", "lbm_batch_get_moments", "lbm_batch_get_totals", "lbm_batch_steps_done",
-           "lbm_batch_destroy"]
+           "lbm_batch_plan", "lbm_batch_select_plan", "lbm_batch_get_moments", "lbm_batch_get_totals",
+           "lbm_batch_steps_done", "lbm_batch_destroy"]
 
 _lib = None
 
@@ -106,6 +106,7 @@ def lib(build_if_missing: bool = True):
     L.lbm_batch_step.argtypes = [vp, C.c_int]
     L.lbm_batch_autotune.argtypes = [vp, C.c_int, dp]
     L.lbm_batch_plan.argtypes = [vp, ip, ip, ip, ip]
+    L.lbm_batch_select_plan.argtypes = [vp, C.c_int, C.c_int]
     L.lbm_batch_get_moments.argtypes = [vp, vp, vp, vp, vp, vp]
     L.lbm_batch_get_totals.argtypes = [vp, dp]
     L.lbm_batch_steps_done.argtypes = [vp]
@@ -237,6 +238,11 @@ def lbm_batch_plan(b):
     v = [C.c_int() for _ in range(4)]
     _check(lib().lbm_batch_plan(b, *[C.byref(x) for x in v]), "lbm_batch_plan")
     return dict(tile_rows=v[0].value, z_split=v[1].value, items=v[2].value, ctas=v[3].value)
+
+
+def lbm_batch_select_plan(b, tile_rows: int, z_split: int):
+    """Select a work plan: tile rows 4 or 8, columns split into 1, 2 or 4 z-chunks."""
+    _check(lib().lbm_batch_select_plan(b, tile_rows, z_split), "lbm_batch_select_plan")
 
 
 def lbm_batch_get_moments(b, rho=None, ux=None, uy=None, uz=None, T=None):
@@ -384,6 +390,9 @@ class Batch:
     @property
     def plan(self):
         return lbm_batch_plan(self.b)
+
+    def select_plan(self, tile_rows: int, z_split: int):
+        lbm_batch_select_plan(self.b, tile_rows, z_split)
 
     def moments(self):
         """Per-instance dicts of host float32 arrays rho, ux, uy, uz, T (shape (nz, ny, nx))."""
