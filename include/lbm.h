@@ -122,8 +122,10 @@ int lbm_init_fields(lbm_ctx* ctx, const float* rho, const float* T, const float*
 /* Enqueue n >= 0 time steps (each: Eqs. 7-10, 3-6, 9, 48, 45, 18, 23, 39-43, streaming
  * of Eq. 4 with Eqs. 50-51).  Returns after enqueueing, unless check_nonfinite is set, in
  * which case it synchronises the stream and returns LBM_ENONFINITE if any node's rho, T
- * or psi became non-finite or psi^2 <= 0 during these steps.
- * Errors: LBM_ESTATE (no init), LBM_EINVAL (n < 0), LBM_ECUDA, LBM_ENONFINITE. */
+ * or psi became non-finite or psi^2 <= 0 during these steps, or LBM_ETIMEOUT if a bounded
+ * pipeline wait of the TMA kernel gave up (the state of those steps is then not to be trusted;
+ * re-initialise).
+ * Errors: LBM_ESTATE (no init), LBM_EINVAL (n < 0), LBM_ECUDA, LBM_ENONFINITE, LBM_ETIMEOUT. */
 int lbm_step(lbm_ctx* ctx, int n);
 
 /* Macroscopic fields of the current state: rho = sum f (Eq. 10), u = (sum e f + F/2)/rho
