@@ -95,6 +95,11 @@ typedef struct {
     void* cuda_stream;            /* borrowed cudaStream_t, NULL = legacy default stream */
     void* workspace;              /* optional caller-owned device memory (see above) */
     size_t workspace_bytes;
+    int test_stall;               /* test of the timeout path only (0 in normal use): in the next
+                                     step of the TMA kernel the producer waits for its first stage
+                                     to be released before loading it, which nothing can do, so
+                                     the bounded waits give up and lbm_step reports LBM_ETIMEOUT;
+                                     cleared once that step is enqueued (never graph-captured) */
 } lbm_params;
 
 /* Fill *p with the workload-independent defaults of Sec. IV: tau_e = 1.25, tau_v = 0.8,

@@ -180,6 +180,7 @@ DevParams make_dev(const lbm_params* p) {
     d.gx = (float)p->g[0]; d.gy = (float)p->g[1]; d.gz = (float)p->g[2];
     d.rho_buoy = p->rho_buoy > 0.0 ? (float)p->rho_buoy : 0.f;
     d.flow_off = p->flow_off; d.thermal_off = p->thermal_off;
+    d.test_stall = p->test_stall ? 1 : 0;
     if (p->precision != LBM_FP32) {
         for (int a = 0; a < 19; ++a) {
             int e2 = ex19(a) * ex19(a) + ey19(a) * ey19(a) + ez19(a) * ez19(a);
@@ -229,6 +230,7 @@ int enqueue_step(lbm_ctx* c, double* kernel_ms = nullptr, int* launches = nullpt
         e = launch_fused(c->dp, c->p.precision, B, c->sums(c->slot), c->sums(c->slot ^ 1), c->first ? 1 : 0,
                          c->launch, c->maps.ok ? &c->maps : nullptr, &ghosts_done);
         if (e != cudaSuccess) return fail(LBM_ECUDA, "fused kernel launch: %s", cudaGetErrorString(e));
+        if (c->maps.ok && B.pull_f && B.pull_g) c->dp.test_stall = 0;   // one stalled TMA step only
         if (ev) {
             cudaEventRecord(ev[1], c->launch);
             cudaEventSynchronize(ev[1]);
@@ -555,7 +557,7 @@ int lbm_step(lbm_ctx* c, int n) {
         ++k;
     }
     if (k < n) {
-        if (c->p.use_graph) rc = run_graph(c, n - k);
+        if (c->p.use_graph && !c->dp.test_stall) rc = run_graph(c, n - k);   // never capture a stall
         else
             for (; k < n && rc == LBM_OK; ++k) rc = enqueue_step(c);
         if (rc) return rc;

@@ -73,6 +73,7 @@ struct DevParams {
     float gx, gy, gz;
     float rho_buoy;           // > 0: fixed reference density of the buoyancy force, else rho_ave
     int flow_off, thermal_off;
+    int test_stall;           // timeout-path test: the TMA producer waits on a barrier nothing completes
     float shift_f[19];        // storage shift w_a rho_ref (16-bit storage only, else 0)
     float shift_g[7];         // storage shift w_a T_ref
 };

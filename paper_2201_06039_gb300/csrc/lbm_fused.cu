@@ -638,7 +638,11 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                 const int z0 = chunk * zchunk, z1 = min(P.nz, z0 + zchunk);
                 for (int p = z0 - 1; p <= z1; ++p, ++k) {
                     const int s = k % kStages;
-                    if (k >= (unsigned)kStages) wait(&empty_bar[s], (k / kStages - 1) & 1);
+                    // a stage is free once the previous use's phase of its empty barrier completed;
+                    // the timeout-path test (test_stall) waits on the first use's own phase instead,
+                    // which nothing can complete before this load: the bounded wait runs out
+                    if (k >= (unsigned)kStages || P.test_stall)
+                        wait(&empty_bar[s], k >= (unsigned)kStages ? (k / kStages - 1) & 1 : 0u);
                     if (abort_flag) {   // release the waiters without data
                         mbar_arrive(&full_bar[s]);
                         continue;

@@ -39,7 +39,7 @@ class LbmParams(C.Structure):
         ("precision", C.c_int), ("rho_ref", C.c_double), ("T_ref", C.c_double),
         ("kernel", C.c_int), ("use_graph", C.c_int), ("use_tma", C.c_int), ("check_nonfinite", C.c_int),
         ("cuda_stream", C.c_void_p),
-        ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
+        ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t), ("test_stall", C.c_int),
     ]
 
 

@@ -228,6 +228,32 @@ def test_nonfinite_state_reported_and_context_recovers():
     lat.close()
 
 
+def test_bounded_wait_timeout_reports_etimeout_and_context_recovers():
+    """The TMA kernel's waits are bounded: with test_stall set, the producer of every CTA waits
+    for its first stage to be released before loading it, which nothing can do (no copy issued,
+    nothing faults); the waits run out after their poll limit (about 2 s), the kernel raises the
+    abort flag, every role finishes without data, and lbm_step reports LBM_ETIMEOUT.  The stall applies to one step only: re-initialised,
+    the same context steps normally and stays finite and bit-identical to a fresh context."""
+    from paper_2201_06039_gb300 import lbm
+    case = W.pool_boiling(64, 48, 24, height=10.0, hot_sigma=3.0)
+    rho, T, u = inputs(case)
+    s = case["setup"]
+    lat = lbm.Lattice(lbm.params_from_setup(s, use_graph=0, test_stall=1))
+    assert lat.kernel == lbm.LBM_KERNEL_FUSED_TMA
+    lat.init(rho.astype(np.float32), T.astype(np.float32))
+    lat.step(1)                        # the first step reads un-streamed state: generic kernel
+    with pytest.raises(lbm.LbmError) as ei:
+        lat.step(1)                    # the stalled TMA step
+    assert ei.value.status == lbm.LBM_ETIMEOUT
+    lat.init(rho.astype(np.float32), T.astype(np.float32))
+    lat.step(12)
+    got = lat.moments()
+    lat.close()
+    ref, _ = run_gpu(s, rho, T, u, 12)
+    for k in ref:
+        assert np.array_equal(got[k], ref[k]), k
+
+
 def test_step_before_init_is_a_state_error():
     from paper_2201_06039_gb300 import lbm
     lat = lbm.Lattice(lbm.params_from_setup(W.LatticeSetup(8, 8, 8)))
