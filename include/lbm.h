@@ -100,6 +100,9 @@ typedef struct {
                                      to be released before loading it, which nothing can do, so
                                      the bounded waits give up and lbm_step reports LBM_ETIMEOUT;
                                      cleared once that step is enqueued (never graph-captured) */
+    int thermal_bgk;              /* 1: single-relaxation-time (BGK) D3Q7 collision, every
+                                     non-conserved moment relaxed at 1/varsigma_T, in place of
+                                     the free rates varsigma_q, varsigma_pi of Eq. 43 (MRT) */
 } lbm_params;
 
 /* Fill *p with the workload-independent defaults of Sec. IV: tau_e = 1.25, tau_v = 0.8,

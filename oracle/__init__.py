@@ -43,6 +43,7 @@ class OrcParams(C.Structure):
         ("g", C.c_double * 3),
         ("flow_off", C.c_int), ("thermal_off", C.c_int),
         ("rho_buoy", C.c_double),
+        ("thermal_bgk", C.c_int),
     ]
 
 
@@ -133,6 +134,7 @@ def params_from_setup(s) -> OrcParams:
         p.g[k] = s.gravity[k]
     p.flow_off, p.thermal_off = s.flow_off, s.thermal_off
     p.rho_buoy = s.rho_buoy
+    p.thermal_bgk = int(s.thermal_bgk)
     return p
 
 

@@ -82,6 +82,8 @@ typedef struct {
     int flow_off;            /* f frozen, u = 0, phi_s = 0 (pure conduction) */
     int thermal_off;         /* g frozen (isothermal) */
     double rho_buoy;         /* > 0: fixed reference density of the buoyancy force, else rho_ave */
+    int thermal_bgk;         /* 1: single-relaxation-time (BGK) D3Q7 collision: every non-conserved
+                                moment relaxes at 1/varsigma_T, in place of the free rates of Eq. 43 */
 } orc_params;
 
 typedef struct {
@@ -578,6 +580,7 @@ static int step_once(orc_state* s) {
                 /* Eq. 42 equilibrium moments and Eq. 43 rates */
                 real neq[Q7] = {T, 0.0, 0.0, 0.0, 3.0 * csT2 * T, 0.0, 0.0};
                 real Gm[Q7] = {1.0, 1.0 / vsT, 1.0 / vsT, 1.0 / vsT, Gam_q, Gam_pi, Gam_pi};
+                if (p->thermal_bgk) Gm[4] = Gm[5] = Gm[6] = 1.0 / vsT;   /* BGK: one rate */
                 real ns[Q7];
                 for (int k = 0; k < Q7; ++k) ns[k] = nm[k] - Gm[k] * (nm[k] - neq[k]);    /* Eq. 39 */
                 for (int a = 0; a < Q7; ++a) {

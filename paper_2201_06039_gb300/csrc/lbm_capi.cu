@@ -181,6 +181,7 @@ DevParams make_dev(const lbm_params* p) {
     d.rho_buoy = p->rho_buoy > 0.0 ? (float)p->rho_buoy : 0.f;
     d.flow_off = p->flow_off; d.thermal_off = p->thermal_off;
     d.test_stall = p->test_stall ? 1 : 0;
+    d.thermal_bgk = p->thermal_bgk ? 1 : 0;
     if (p->precision != LBM_FP32) {
         for (int a = 0; a < 19; ++a) {
             int e2 = ex19(a) * ex19(a) + ey19(a) * ey19(a) + ez19(a) * ez19(a);

@@ -74,6 +74,7 @@ struct DevParams {
     float rho_buoy;           // > 0: fixed reference density of the buoyancy force, else rho_ave
     int flow_off, thermal_off;
     int test_stall;           // timeout-path test: the TMA producer waits on a barrier nothing completes
+    int thermal_bgk;          // 1: BGK D3Q7 collision (n4..n6 relaxed at 1/varsigma_T too)
     float shift_f[19];        // storage shift w_a rho_ref (16-bit storage only, else 0)
     float shift_g[7];         // storage shift w_a T_ref
 };
@@ -512,10 +513,12 @@ __device__ __forceinline__ float collide_g(const DevParams& P, float g[7], float
     float qs = __fmaf_rn(-0.5f, C, __fmul_rn(1.5f, phis));   // Q_a = w_a (3/2 phi_s(t) - 1/2 phi_s(t-1))
     float om = 1.f - inv_vsT;
     n1 = __fmul_rn(n1, om); n2 = __fmul_rn(n2, om); n3 = __fmul_rn(n3, om);
-    // n4* = n4 - Gq (n4 - d T) with 3 cs_T^2 T = d T; explicit rounding as in relax()
-    n4 = __fsub_rn(n4, __fmul_rn(P.Gq, __fsub_rn(n4, __fmul_rn(P.d, T))));
-    n5 = __fmul_rn(n5, 1.f - P.Gpi);
-    n6 = __fmul_rn(n6, 1.f - P.Gpi);
+    // n4* = n4 - Gq (n4 - d T) with 3 cs_T^2 T = d T; explicit rounding as in relax().  The BGK
+    // variant relaxes n4..n6 at the rate of n1..n3, 1/varsigma_T.
+    const float Gq = P.thermal_bgk ? inv_vsT : P.Gq, Gpi = P.thermal_bgk ? inv_vsT : P.Gpi;
+    n4 = __fsub_rn(n4, __fmul_rn(Gq, __fsub_rn(n4, __fmul_rn(P.d, T))));
+    n5 = __fmul_rn(n5, 1.f - Gpi);
+    n6 = __fmul_rn(n6, 1.f - Gpi);
     // g* = N^-1 n* (Eq. 41); g*_0 = T - sum g*_1..6 keeps sum g* = T free of rounding drift
     // (n_0* = T; a rounded 1/6 factor would otherwise bias it); then g+ = g* + Q (Eq. 40).
     const float s6 = 1.f / 6.f;

@@ -88,6 +88,16 @@ def test_parity_general_relaxation_rates(variant):
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
+def test_parity_thermal_bgk(variant):
+    """The BGK D3Q7 collision switch (thermal_bgk: every non-conserved moment at 1/varsigma_T)
+    on the evaporating droplet with its constant-lambda conductivity, against the oracle."""
+    case = W.evaporation(24, R0=7.0)
+    s = case["setup"]
+    case = dict(case, setup=W.LatticeSetup(**{**s.__dict__, "thermal_bgk": 1}))
+    _compare(case, 300, variant)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
 def test_parity_pool_boiling_small(variant):
     case = W.pool_boiling(40, 36, 48, height=16.0, hot_sigma=4.0)
     _compare(case, 400, variant)

@@ -210,6 +210,51 @@ def test_pure_conduction_decay():
     assert abs(Tn.mean() - T0) < 1e-14
 
 
+def _d3q7_two_steps(T0, w0, wi, om, bgk):
+    """Temperature after two steps of the D3Q7 LB with frozen flow (phi_s = 0, Q = 0) from the
+    equilibrium populations g = w T0, on a periodic box, written out population by population.
+    BGK: g* = (1 - om) g + om w T.  MRT with the paper's unit free rates (varsigma_q = varsigma_pi
+    = 1): n1..n3 relax at om, n4 to its equilibrium d T, n5 = n6 = 0 (Eqs. 38-43)."""
+    dirs = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]
+    w = [w0] + [wi] * 6
+    def stream(g):   # pull: g_a(x) <- g_a(x - e_a); arrays are [z][y][x]
+        return [np.roll(np.roll(np.roll(ga, ex, axis=2), ey, axis=1), ez, axis=0)
+                for ga, (ex, ey, ez) in zip(g, dirs)]
+    g = stream([wa * T0 for wa in w])          # step 1: the initial state is at equilibrium
+    T1 = sum(g)
+    if bgk:
+        gs = [(1 - om) * ga + om * wa * T1 for ga, wa in zip(g, w)]
+    else:
+        n1, n2, n3 = g[1] - g[2], g[3] - g[4], g[5] - g[6]
+        d = 6 * wi
+        n1, n2, n3 = (1 - om) * n1, (1 - om) * n2, (1 - om) * n3
+        n4 = d * T1                           # Gq = 1: straight to 3 cs_T^2 T = d T
+        gs = [T1 - n4, (n4 + 3 * n1) / 6, (n4 - 3 * n1) / 6, (n4 + 3 * n2) / 6, (n4 - 3 * n2) / 6,
+              (n4 + 3 * n3) / 6, (n4 - 3 * n3) / 6]
+    return sum(stream(gs))
+
+
+@pytest.mark.parametrize("bgk", [0, 1])
+def test_thermal_collision_bgk_and_mrt_two_steps_bruteforce(bgk):
+    """The BGK switch of the D3Q7 collision (one rate 1/varsigma_T for every non-conserved moment)
+    and the paper's MRT (free rates varsigma_q = varsigma_pi = 1) against the two-step population
+    recursion written out directly; the two collisions differ visibly on a random 3D field."""
+    s = small_setup(nx=6, ny=5, nz=4, flow_off=1, chi_or_lambda=0.08, thermal_bgk=bgk)
+    Tc, rho, _ = _single_phase(s)
+    T0 = 0.86 * Tc * (1.0 + 0.05 * W.uniform(W.MASTER_SEED + 5, s.n_nodes, -1.0, 1.0)).reshape(s.shape)
+    o = oracle.Oracle(s)
+    o.init(rho, T0)
+    o.step(2)
+    T2 = o.moments()["T"]
+    d = s.d
+    csT2 = d / 3.0
+    om = 1.0 / (0.08 / csT2 + 0.5)
+    want = _d3q7_two_steps(T0, 1.0 - d, d / 6.0, om, bgk)
+    other = _d3q7_two_steps(T0, 1.0 - d, d / 6.0, om, 1 - bgk)
+    assert np.max(np.abs(T2 - want)) < 1e-14 * Tc, np.max(np.abs(T2 - want))
+    assert np.max(np.abs(T2 - other)) > 1e-6 * Tc
+
+
 def test_anti_bounce_back_linear_profile():
     """Eq. 51 walls at two temperatures give the linear steady conduction profile."""
     nz = 16

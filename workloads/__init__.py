@@ -136,6 +136,7 @@ class LatticeSetup:
     flow_off: int = 0             # f frozen (pure conduction checks)
     thermal_off: int = 0          # g frozen (isothermal phase)
     rho_buoy: float = 0.0         # > 0: fixed reference density of the buoyancy force (else rho_ave)
+    thermal_bgk: int = 0          # 1: BGK D3Q7 collision (one rate 1/varsigma_T) instead of MRT
 
     @property
     def shape(self):
