@@ -103,6 +103,11 @@ typedef struct {
     int thermal_bgk;              /* 1: single-relaxation-time (BGK) D3Q7 collision, every
                                      non-conserved moment relaxed at 1/varsigma_T, in place of
                                      the free rates varsigma_q, varsigma_pi of Eq. 43 (MRT) */
+    int divu_mode;                /* 0: div u of Eq. 48 at every node (default); 1: isotropic
+                                     finite differences of u (gradient weights of Sec. III.C) at
+                                     nodes whose stencil stays inside the fluid, Eq. 48 next to
+                                     wall and outflow faces.  Runs the two-pass kernels plus a
+                                     velocity pass (kernel AUTO or TWO_PASS; FUSED is rejected) */
 } lbm_params;
 
 /* Fill *p with the workload-independent defaults of Sec. IV: tau_e = 1.25, tau_v = 0.8,

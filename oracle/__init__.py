@@ -44,6 +44,7 @@ class OrcParams(C.Structure):
         ("flow_off", C.c_int), ("thermal_off", C.c_int),
         ("rho_buoy", C.c_double),
         ("thermal_bgk", C.c_int),
+        ("divu_mode", C.c_int),
     ]
 
 
@@ -103,6 +104,8 @@ def _bind(L):
     L.orc_collide_node.argtypes = [C.POINTER(OrcParams), dp, dp, dp, C.c_double, dp, dp]
     L.orc_feq.argtypes = [C.c_double, dp, dp]
     L.orc_force_pops.argtypes = [C.POINTER(OrcParams), dp, dp, dp, C.c_double, dp]
+    L.orc_fd_divergence.argtypes = [C.POINTER(OrcParams), dp, dp]
+    L.orc_fd_divergence.restype = None
     L.orc_num_threads.restype = C.c_int
     return L
 
@@ -135,6 +138,7 @@ def params_from_setup(s) -> OrcParams:
     p.flow_off, p.thermal_off = s.flow_off, s.thermal_off
     p.rho_buoy = s.rho_buoy
     p.thermal_bgk = int(s.thermal_bgk)
+    p.divu_mode = int(getattr(s, "divu_mode", 0))
     return p
 
 
@@ -242,7 +246,8 @@ class Oracle:
         self._L.orc_set_pops(self._h, _dp(f), _dp(g))
 
     def diag(self):
-        """div u (Eq. 48), grad T (Eq. 45), grad rho, F_m, phi_s, psi of the last step."""
+        """div u (Eq. 48, or finite differences in divu_mode 1), grad T (Eq. 45), grad rho, F_m, phi_s,
+        psi of the last step."""
         N = self.N
         d = dict(divu=np.empty(N), gradT=np.empty(3 * N), gradrho=np.empty(3 * N),
                  Fm=np.empty(3 * N), phis=np.empty(N), psi=np.empty(N))
@@ -301,6 +306,16 @@ def force_pops(setup, F, u, Fm, psi2):
                          _dp(np.ascontiguousarray(u, dtype=np.float64)),
                          _dp(np.ascontiguousarray(Fm, dtype=np.float64)), float(psi2), _dp(out))
     return out
+
+
+def fd_divergence(setup, u: np.ndarray) -> np.ndarray:
+    """The oracle's isotropic finite-difference divergence of a given velocity field u (shape
+    (3, nz, ny, nx)) at every node, neighbours wrapped or mirrored by the setup's faces."""
+    p = params_from_setup(setup)
+    ui = np.ascontiguousarray(np.moveaxis(np.asarray(u, dtype=np.float64), 0, -1).reshape(-1))
+    out = np.empty(setup.n_nodes, dtype=np.float64)
+    lib().orc_fd_divergence(C.byref(p), _dp(ui), _dp(out))
+    return out.reshape(setup.shape)
 
 
 def num_threads() -> int:

@@ -84,6 +84,9 @@ typedef struct {
     double rho_buoy;         /* > 0: fixed reference density of the buoyancy force, else rho_ave */
     int thermal_bgk;         /* 1: single-relaxation-time (BGK) D3Q7 collision: every non-conserved
                                 moment relaxes at 1/varsigma_T, in place of the free rates of Eq. 43 */
+    int divu_mode;           /* 0: div u by Eq. 48 at every node; 1: isotropic finite differences of
+                                u, with Eq. 48 only at nodes whose stencil reaches a wall or
+                                outflow face (the traditional treatment Sec. III.C describes) */
 } orc_params;
 
 typedef struct {
@@ -94,6 +97,7 @@ typedef struct {
     real *rho, *T, *psi;
     real *phis_prev, *phis;
     real *divu, *gradT, *gradrho, *Fm;   /* diagnostics of the last step */
+    real *uvec;                          /* u of every node (finite-difference div u) */
     int first;
     double rho_ave;        /* value the next step uses (FP64 mean) */
     real M[Q19 * Q19], Minv[Q19 * Q19];
@@ -327,6 +331,30 @@ static long stencil_neighbour(const orc_params* p, int x, int y, int z, int ex, 
     return node_index(p, c[0], c[1], c[2]);
 }
 
+/* 1 if a stencil neighbour of (x, y, z) lies beyond a wall or outflow face */
+static int next_to_solid(const orc_params* p, int x, int y, int z) {
+    int c[3] = {x, y, z}, n[3] = {p->nx, p->ny, p->nz};
+    for (int k = 0; k < 3; ++k) {
+        if (c[k] == 0 && !(p->bc[2 * k] == ORC_PERIODIC || p->bc[2 * k] == ORC_THERMAL_ONLY)) return 1;
+        if (c[k] == n[k] - 1 && !(p->bc[2 * k + 1] == ORC_PERIODIC || p->bc[2 * k + 1] == ORC_THERMAL_ONLY)) return 1;
+    }
+    return 0;
+}
+
+/* Isotropic finite-difference divergence with the weights of the gradient stencil of Sec. III.C:
+   div u (x) = (1/cs^2) sum_a w_a e_a . u(x + e_a) = sum_a W_a e_a . u(x + e_a), W = 1/6 on the
+   faces (w = 1/18), 1/12 on the edges (w = 1/36); u holds 3 values per node. */
+static real fd_divergence(const orc_params* p, const real* u, int x, int y, int z) {
+    real acc = 0.0;
+    for (int a = 1; a < Q19; ++a) {
+        int e2 = EX[a] * EX[a] + EY[a] * EY[a] + EZ[a] * EZ[a];
+        real w = e2 == 1 ? 1.0 / 6.0 : 1.0 / 12.0;
+        long j = stencil_neighbour(p, x, y, z, EX[a], EY[a], EZ[a]);
+        acc += w * (EX[a] * u[3 * j] + EY[a] * u[3 * j + 1] + EZ[a] * u[3 * j + 2]);
+    }
+    return acc;
+}
+
 static real wall_T(const orc_params* p, int face, int x, int y) {
     real T = p->T_wall[face];
     if (face == 4 && p->hot_dT != 0.0) {
@@ -369,11 +397,12 @@ orc_state* orc_create(const orc_params* p) {
     s->phis_prev = (real*)malloc(sizeof(real) * N);
     s->phis = (real*)malloc(sizeof(real) * N);
     s->divu = (real*)malloc(sizeof(real) * N);
+    s->uvec = (real*)malloc(sizeof(real) * N * 3);
     s->gradT = (real*)malloc(sizeof(real) * N * 3);
     s->gradrho = (real*)malloc(sizeof(real) * N * 3);
     s->Fm = (real*)malloc(sizeof(real) * N * 3);
     if (!s->f || !s->fn || !s->fs || !s->g || !s->gn || !s->gp || !s->rho || !s->T || !s->psi ||
-        !s->phis_prev || !s->phis || !s->divu || !s->gradT || !s->gradrho || !s->Fm) {
+        !s->phis_prev || !s->phis || !s->divu || !s->uvec || !s->gradT || !s->gradrho || !s->Fm) {
         return NULL;
     }
     if (fill_matrices(s)) return NULL;
@@ -386,7 +415,7 @@ void orc_destroy(orc_state* s) {
     if (!s) return;
     free(s->f); free(s->fn); free(s->fs); free(s->g); free(s->gn); free(s->gp);
     free(s->rho); free(s->T); free(s->psi); free(s->phis_prev); free(s->phis);
-    free(s->divu); free(s->gradT); free(s->gradrho); free(s->Fm);
+    free(s->divu); free(s->uvec); free(s->gradT); free(s->gradrho); free(s->Fm);
     free(s);
 }
 
@@ -541,6 +570,24 @@ static int step_once(orc_state* s) {
     for (int a = 1; a < Q7; ++a) w7[a] = p->d / 6.0;
     const real csT2 = p->d / 3.0;
     real Gam_q = 1.0 / p->varsigma_q, Gam_pi = 1.0 / p->varsigma_pi;
+    if (p->divu_mode == 1) {
+        /* u of every node first (Eq. 10 with the total force), for the finite differences */
+#pragma omp parallel for schedule(static)
+        for (int z = 0; z < p->nz; ++z)
+            for (int y = 0; y < p->ny; ++y)
+                for (int x = 0; x < p->nx; ++x) {
+                    long i = node_index(p, x, y, z);
+                    real rho = s->rho[i], Fm[3], grho[3], j[3] = {0.0, 0.0, 0.0};
+                    node_forces(s, x, y, z, Fm, grho);
+                    for (int a = 0; a < Q19; ++a) {
+                        j[0] += EX[a] * s->f[i * Q19 + a];
+                        j[1] += EY[a] * s->f[i * Q19 + a];
+                        j[2] += EZ[a] * s->f[i * Q19 + a];
+                    }
+                    for (int k = 0; k < 3; ++k)
+                        s->uvec[3 * i + k] = (j[k] + 0.5 * (Fm[k] + (rho - rho_ave) * p->g[k])) / rho;
+                }
+    }
 #pragma omp parallel for schedule(static)
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
@@ -556,6 +603,7 @@ static int step_once(orc_state* s) {
                 /* Eq. 48 */
                 real Fu = F[0] * u[0] + F[1] * u[1] + F[2] * u[2];
                 real divu = (-m4neq / p->tau_e + (1.0 - 0.5 / p->tau_e) * S4 - 2.0 * Fu) / (2.0 * rho * CS2);
+                if (p->divu_mode == 1 && !next_to_solid(p, x, y, z)) divu = fd_divergence(p, s->uvec, x, y, z);
                 /* thermal moments, Eq. 38 */
                 real nm[Q7];
                 for (int k = 0; k < Q7; ++k) {
@@ -712,6 +760,18 @@ void orc_force_pops(const orc_params* p, const double* F, const double* u, const
         for (int k = 0; k < Q19; ++k) acc += Mi[a * Q19 + k] * (double)S[k];
         G[a] = acc;
     }
+}
+
+/* finite-difference divergence of a given field u (3 per node) at every node (test helper) */
+void orc_fd_divergence(const orc_params* p, const double* u, double* out) {
+    long N = (long)p->nx * p->ny * p->nz;
+    real* ur = (real*)malloc(sizeof(real) * 3 * N);
+    if (!ur) return;
+    for (long k = 0; k < 3 * N; ++k) ur[k] = (real)u[k];
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x) out[node_index(p, x, y, z)] = (double)fd_divergence(p, ur, x, y, z);
+    free(ur);
 }
 
 int orc_num_threads(void) {

@@ -91,6 +91,7 @@ struct lbm_batch {
         B.partial = (double2*)(base + off_partial);
         B.counter = k < 0 ? counters() : counters() + 2;
         B.flag = (int*)(base + off_flag);
+        B.vel = nullptr;
         return B;
     }
 };
@@ -233,6 +234,7 @@ int lbm_batch_create(const lbm_params* common, int n_instances, const int* dims,
     if (!common || !dims) return fail(LBM_EINVAL, "common and dims are required");
     if (n_instances < 1) return fail(LBM_EINVAL, "n_instances must be >= 1");
     if (common->kernel == LBM_KERNEL_TWO_PASS) return fail(LBM_EINVAL, "the batch runs the fused kernel only");
+    if (common->divu_mode != 0) return fail(LBM_EINVAL, "the batch computes div u by Eq. 48 only (divu_mode 0)");
     lbm_batch* b = new (std::nothrow) lbm_batch();
     if (!b) return fail(LBM_ENOMEM, "host allocation failed");
     b->p = *common;

@@ -44,7 +44,7 @@ size_t pop_bytes(int precision) { return precision == LBM_FP32 ? 4 : 2; }
 namespace {
 
 struct Layout {
-    size_t pops[2], psirho, phis, sums, partial, counter, flag, total;
+    size_t pops[2], psirho, phis, sums, partial, counter, flag, vel, total;
 };
 
 // Device memory of a context: two population buffers (26 slots of Ns elements: the padded,
@@ -61,6 +61,7 @@ Layout layout_of(const lbm_params* p, const DevParams& dp) {
     L.partial = take(sizeof(double2) * (size_t)max_partials(dp));
     L.counter = take(sizeof(unsigned));
     L.flag = take(sizeof(int));
+    L.vel = take(p->divu_mode == 1 ? 16 * N : 0);
     L.total = off;
     return L;
 }
@@ -107,6 +108,7 @@ struct lbm_ctx {
         B.partial = (double2*)(base + L.partial);
         B.counter = (unsigned*)(base + L.counter);
         B.flag = (int*)(base + L.flag);
+        B.vel = p.divu_mode == 1 ? (float4*)(base + L.vel) : nullptr;
         return B;
     }
 };
@@ -142,6 +144,9 @@ int validate(const lbm_params* p) {
     if (!(p->chi_or_lambda > 0)) return fail(LBM_EINVAL, "chi / lambda must be positive");
     if (p->precision < 0 || p->precision > 2) return fail(LBM_EINVAL, "unknown precision");
     if (p->kernel < 0 || p->kernel > 2) return fail(LBM_EINVAL, "unknown kernel variant");
+    if (p->divu_mode < 0 || p->divu_mode > 1) return fail(LBM_EINVAL, "divu_mode must be 0 or 1");
+    if (p->divu_mode == 1 && p->kernel == LBM_KERNEL_FUSED)
+        return fail(LBM_EINVAL, "finite-difference div u runs on the two-pass kernels (kernel AUTO or TWO_PASS)");
     if (p->hot_dT != 0.0 && !(p->hot_sigma > 0)) return fail(LBM_EINVAL, "hot_sigma must be positive");
     return LBM_OK;
 }
@@ -182,6 +187,7 @@ DevParams make_dev(const lbm_params* p) {
     d.flow_off = p->flow_off; d.thermal_off = p->thermal_off;
     d.test_stall = p->test_stall ? 1 : 0;
     d.thermal_bgk = p->thermal_bgk ? 1 : 0;
+    d.divu_mode = p->divu_mode;
     if (p->precision != LBM_FP32) {
         for (int a = 0; a < 19; ++a) {
             int e2 = ex19(a) * ex19(a) + ey19(a) * ey19(a) + ez19(a) * ez19(a);
@@ -245,6 +251,10 @@ int enqueue_step(lbm_ctx* c, double* kernel_ms = nullptr, int* launches = nullpt
         e = launch_psi(c->dp, c->p.precision, B, c->sums(c->slot ^ 1), c->launch);
         if (e != cudaSuccess) return fail(LBM_ECUDA, "psi kernel launch: %s", cudaGetErrorString(e));
         if (ev) cudaEventRecord(ev[1], c->launch);
+        if (B.vel) {   // u of every node for the finite-difference div u of the collide pass
+            e = launch_velocity(c->dp, c->p.precision, B, c->sums(c->slot), c->launch);
+            if (e != cudaSuccess) return fail(LBM_ECUDA, "velocity kernel launch: %s", cudaGetErrorString(e));
+        }
         e = launch_collide(c->dp, c->p.precision, B, c->sums(c->slot), c->first ? 1 : 0, c->launch);
         if (e != cudaSuccess) return fail(LBM_ECUDA, "collide kernel launch: %s", cudaGetErrorString(e));
         if (ev) {
@@ -491,8 +501,9 @@ int lbm_create(const lbm_params* p, lbm_ctx** out) {
         }
         c->owns = true;
     }
-    c->variant = p->kernel == LBM_KERNEL_AUTO ? (fused_supported(c->dp) ? LBM_KERNEL_FUSED : LBM_KERNEL_TWO_PASS)
-                                              : p->kernel;
+    c->variant = p->kernel == LBM_KERNEL_AUTO
+                     ? (fused_supported(c->dp) && p->divu_mode == 0 ? LBM_KERNEL_FUSED : LBM_KERNEL_TWO_PASS)
+                     : p->kernel;
     if (c->variant == LBM_KERNEL_FUSED && !fused_supported(c->dp)) {
         if (c->owns) cudaFree(c->base);
         free(c);

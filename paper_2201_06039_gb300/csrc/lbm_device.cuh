@@ -75,6 +75,7 @@ struct DevParams {
     int flow_off, thermal_off;
     int test_stall;           // timeout-path test: the TMA producer waits on a barrier nothing completes
     int thermal_bgk;          // 1: BGK D3Q7 collision (n4..n6 relaxed at 1/varsigma_T too)
+    int divu_mode;            // 1: finite-difference div u away from solid faces (two-pass kernels)
     float shift_f[19];        // storage shift w_a rho_ref (16-bit storage only, else 0)
     float shift_g[7];         // storage shift w_a T_ref
 };

@@ -133,12 +133,70 @@ __device__ __forceinline__ Stencil stencil(const DevParams& P, const float2* __r
     return s;
 }
 
+// ---------------------------------------------------------------- velocity pass
+// u = (sum e f + F/2) / rho (Eq. 10, total force F) of every node, for the finite-difference
+// div u of the collide pass (divu_mode 1); same arithmetic as the collision's u.
+template <typename S>
+__global__ void __launch_bounds__(TPB) k_velocity(DevParams P, const S* __restrict__ fs, int pull_f,
+                                                 const float2* __restrict__ psirho,
+                                                 const double* __restrict__ sums_cur, float4* __restrict__ vel) {
+    int x = blockIdx.x * TPB_X + threadIdx.x, y = blockIdx.y * TPB_Y + threadIdx.y, z = blockIdx.z;
+    if (x >= P.nx || y >= P.ny) return;
+    int i = sidx(P, x, y, z), d = node_of(P, x, y, z);
+    Nbr n = make_nbr(P, x, y, z);
+    float f[19];
+    load_f<S>(P, fs, pull_f, i, x, y, z, n, f);
+    float rho = sum19(f);
+    float jx = (f[1] - f[2]) + (f[7] - f[8]) + (f[9] - f[10]) + (f[11] - f[12]) + (f[13] - f[14]);
+    float jy = (f[3] - f[4]) + (f[7] - f[8]) - (f[9] - f[10]) + (f[15] - f[16]) + (f[17] - f[18]);
+    float jz = (f[5] - f[6]) + (f[11] - f[12]) - (f[13] - f[14]) + (f[15] - f[16]) - (f[17] - f[18]);
+    float2 me = __ldg(psirho + d);
+    Stencil st = stencil(P, psirho, x, y, z, n);
+    const Forces F = total_force(P, me.x, st.Fx, st.Fy, st.Fz, rho - buoyancy_ref(P, sums_cur[0], P.inv_N));
+    const float inv_rho = __fdividef(1.f, rho);
+    vel[d] = make_float4((jx + 0.5f * F.Fx) * inv_rho, (jy + 0.5f * F.Fy) * inv_rho, (jz + 0.5f * F.Fz) * inv_rho, 0.f);
+}
+
+// Does the gradient stencil of (x, y, z) reach past a wall or outflow face?  There div u stays
+// Eq. 48 in divu_mode 1.
+__device__ __forceinline__ bool next_to_solid(const DevParams& P, int x, int y, int z) {
+    return (x == 0 && !f_wraps(P.bc[0])) || (x == P.nx - 1 && !f_wraps(P.bc[1])) ||
+           (y == 0 && !f_wraps(P.bc[2])) || (y == P.ny - 1 && !f_wraps(P.bc[3])) ||
+           (z == 0 && !f_wraps(P.bc[4])) || (z == P.nz - 1 && !f_wraps(P.bc[5]));
+}
+
+// isotropic finite-difference divergence: sum_a W_a e_a . u(x + e_a), W = 1/6 (faces), 1/12 (edges)
+template <int A>
+__device__ __forceinline__ void fd_term(const DevParams& P, const float4* __restrict__ vel, int x, int y, int z,
+                                        const Nbr& n, float& acc) {
+    constexpr int ex = ex19(A), ey = ey19(A), ez = ez19(A);
+    constexpr float w = (ex * ex + ey * ey + ez * ez) == 1 ? (1.f / 6.f) : (1.f / 12.f);
+    const float4 q = __ldg(vel + node_of(P, nb_c(ex, x, n.xm, n.xp), nb_c(ey, y, n.ym, n.yp), nb_c(ez, z, n.zm, n.zp)));
+    if (ex) acc = __fmaf_rn(ex * w, q.x, acc);
+    if (ey) acc = __fmaf_rn(ey * w, q.y, acc);
+    if (ez) acc = __fmaf_rn(ez * w, q.z, acc);
+}
+__device__ __forceinline__ float fd_divergence(const DevParams& P, const float4* __restrict__ vel, int x, int y,
+                                               int z, const Nbr& n) {
+    float acc = 0.f;
+    fd_term<1>(P, vel, x, y, z, n, acc); fd_term<2>(P, vel, x, y, z, n, acc);
+    fd_term<3>(P, vel, x, y, z, n, acc); fd_term<4>(P, vel, x, y, z, n, acc);
+    fd_term<5>(P, vel, x, y, z, n, acc); fd_term<6>(P, vel, x, y, z, n, acc);
+    fd_term<7>(P, vel, x, y, z, n, acc); fd_term<8>(P, vel, x, y, z, n, acc);
+    fd_term<9>(P, vel, x, y, z, n, acc); fd_term<10>(P, vel, x, y, z, n, acc);
+    fd_term<11>(P, vel, x, y, z, n, acc); fd_term<12>(P, vel, x, y, z, n, acc);
+    fd_term<13>(P, vel, x, y, z, n, acc); fd_term<14>(P, vel, x, y, z, n, acc);
+    fd_term<15>(P, vel, x, y, z, n, acc); fd_term<16>(P, vel, x, y, z, n, acc);
+    fd_term<17>(P, vel, x, y, z, n, acc); fd_term<18>(P, vel, x, y, z, n, acc);
+    return acc;
+}
+
 // ---------------------------------------------------------------- stream-collide pass (S3-S12)
 template <typename S>
 __global__ void __launch_bounds__(TPB) k_collide(DevParams P, const S* __restrict__ fs, S* __restrict__ fd,
                                                 int pull_f, int pull_g,
                                                 const float2* __restrict__ psirho, const double* __restrict__ sums_cur,
-                                                float* __restrict__ phis, int first) {
+                                                float* __restrict__ phis, int first, const float4* __restrict__ vel) {
     int x = blockIdx.x * TPB_X + threadIdx.x, y = blockIdx.y * TPB_Y + threadIdx.y, z = blockIdx.z;
     if (x >= P.nx || y >= P.ny) return;
     int i = sidx(P, x, y, z), d = node_of(P, x, y, z);
@@ -152,6 +210,7 @@ __global__ void __launch_bounds__(TPB) k_collide(DevParams P, const S* __restric
     float rho_ave = buoyancy_ref(P, sums_cur[0], P.inv_N);
     const Forces F = total_force(P, me.x, st.Fx, st.Fy, st.Fz, rho - rho_ave);
     NodeOut o = collide_f(P, f, rho, F.Fx, F.Fy, F.Fz, F.Fm2, me.x * me.x);
+    if (vel && !next_to_solid(P, x, y, z)) o.divu = fd_divergence(P, vel, x, y, z, n);   // divu_mode 1
     float ph = collide_g(P, g, rho, T, o, st.gx, st.gy, st.gz, phis[d], first);
     // frozen fields keep their stored values (no streaming, no collision)
     if (P.flow_off) {
@@ -247,7 +306,16 @@ cudaError_t launch_collide(const DevParams& P, int precision, const StateBufs& B
                            int first, cudaStream_t s) {
     dim3 blk(TPB_X, TPB_Y);
     GB300_DISPATCH(precision, (k_collide<S><<<grid_of(P), blk, 0, s>>>(P, (const S*)B.src, (S*)B.dst, B.pull_f,
-                                                                        B.pull_g, B.psirho, sums_cur, B.phis, first)));
+                                                                        B.pull_g, B.psirho, sums_cur, B.phis, first,
+                                                                        B.vel)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_velocity(const DevParams& P, int precision, const StateBufs& B, const double* sums_cur,
+                            cudaStream_t s) {
+    dim3 blk(TPB_X, TPB_Y);
+    GB300_DISPATCH(precision, (k_velocity<S><<<grid_of(P), blk, 0, s>>>(P, (const S*)B.src, B.pull_f, B.psirho,
+                                                                         sums_cur, B.vel)));
     return cudaGetLastError();
 }
 

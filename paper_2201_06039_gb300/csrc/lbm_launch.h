@@ -18,6 +18,7 @@ struct StateBufs {
     double2* partial;      // per-block partial sums of the deterministic reduction
     unsigned* counter;     // last-block counter of the reduction (kept at 0 between launches)
     int* flag;             // non-finite flag
+    float4* vel;           // per node u (finite-difference div u only; NULL otherwise)
 };
 
 int reduce_blocks_psi(const DevParams& P);
@@ -30,6 +31,9 @@ cudaError_t launch_psi(const DevParams& P, int precision, const StateBufs& B, do
                        cudaStream_t s);
 
 // stream-collide pass of the two-pass variant.
+// u = (sum e f + F/2) / rho of every node into B.vel (finite-difference div u)
+cudaError_t launch_velocity(const DevParams& P, int precision, const StateBufs& B, const double* sums_cur,
+                            cudaStream_t s);
 cudaError_t launch_collide(const DevParams& P, int precision, const StateBufs& B,
                            const double* sums_cur, int first, cudaStream_t s);
 

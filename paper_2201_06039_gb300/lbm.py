@@ -40,7 +40,7 @@ class LbmParams(C.Structure):
         ("kernel", C.c_int), ("use_graph", C.c_int), ("use_tma", C.c_int), ("check_nonfinite", C.c_int),
         ("cuda_stream", C.c_void_p),
         ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t), ("test_stall", C.c_int),
-        ("thermal_bgk", C.c_int),
+        ("thermal_bgk", C.c_int), ("divu_mode", C.c_int),
     ]
 
 
@@ -287,6 +287,7 @@ def params_from_setup(setup, **overrides) -> LbmParams:
     p.flow_off, p.thermal_off = setup.flow_off, setup.thermal_off
     p.rho_buoy = getattr(setup, "rho_buoy", 0.0)
     p.thermal_bgk = int(getattr(setup, "thermal_bgk", 0))
+    p.divu_mode = int(getattr(setup, "divu_mode", 0))
     for k, v in overrides.items():
         setattr(p, k, v)
     return p

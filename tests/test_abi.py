@@ -58,7 +58,7 @@ def test_workspace_bytes_counts_state():
 
 
 @pytest.mark.parametrize("field,value", [("nx", 0), ("tau_v", 0.5), ("d", 1.5), ("precision", 7),
-                                         ("kernel", 9), ("chi_or_lambda", -1.0)])
+                                         ("kernel", 9), ("chi_or_lambda", -1.0), ("divu_mode", 2)])
 def test_invalid_params_rejected_on_host(field, value):
     p = G.lbm_params_default()
     p.nx = p.ny = p.nz = 8
@@ -67,6 +67,21 @@ def test_invalid_params_rejected_on_host(field, value):
         G.lbm_create(p)
     assert ei.value.status == G.LBM_EINVAL
     assert G.lbm_workspace_bytes(p) == 0
+
+
+def test_finite_difference_divu_needs_the_two_pass_kernels():
+    p = G.lbm_params_default()
+    p.nx = p.ny = p.nz = 8
+    p.divu_mode = 1
+    p.kernel = G.LBM_KERNEL_FUSED
+    with pytest.raises(G.LbmError) as ei:
+        G.lbm_create(p)
+    assert ei.value.status == G.LBM_EINVAL and "two-pass" in str(ei.value)
+    q = G.lbm_params_default()
+    q.divu_mode = 1
+    with pytest.raises(G.LbmError) as ei:
+        G.lbm_batch_create(q, [(8, 8, 8)])
+    assert ei.value.status == G.LBM_EINVAL
 
 
 def test_one_sided_periodic_axis_rejected():

@@ -97,6 +97,19 @@ def test_parity_thermal_bgk(variant):
     _compare(case, 300, variant)
 
 
+@pytest.mark.parametrize("case_name", ["pool", "evaporation"])
+def test_parity_finite_difference_divu(case_name):
+    """divu_mode 1: isotropic finite differences of u (velocity pass + two-pass kernels) in the
+    interior, Eq. 48 next to the wall and outflow faces, against the oracle in the same mode; on
+    the pool (walls, outflow, hot spot, gravity) and on the droplet with thermal faces."""
+    if case_name == "pool":
+        case = W.pool_boiling(40, 36, 48, height=16.0, hot_sigma=4.0)
+    else:
+        case = W.evaporation(24, R0=7.0)
+    case = dict(case, setup=W.LatticeSetup(**{**case["setup"].__dict__, "divu_mode": 1}))
+    _compare(case, 300, "two_pass")
+
+
 @pytest.mark.parametrize("variant", VARIANTS)
 def test_parity_pool_boiling_small(variant):
     case = W.pool_boiling(40, 36, 48, height=16.0, hot_sigma=4.0)

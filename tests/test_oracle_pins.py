@@ -255,6 +255,42 @@ def test_thermal_collision_bgk_and_mrt_two_steps_bruteforce(bgk):
     assert np.max(np.abs(T2 - other)) > 1e-6 * Tc
 
 
+def test_finite_difference_divergence_of_sine_fields():
+    """The isotropic finite-difference divergence (weights 1/6 on faces, 1/12 on edges) of
+    u = sin(2 pi x / L) along each axis is, on the lattice, cos(2 pi x / L) sin(2 pi / L)
+    exactly: a plain sum over the 18 neighbours, checked axis by axis on a periodic box."""
+    s = small_setup(nx=12, ny=10, nz=8)
+    for axis, L in ((0, 12), (1, 10), (2, 8)):
+        zz, yy, xx = np.meshgrid(np.arange(8), np.arange(10), np.arange(12), indexing="ij")
+        c = (xx, yy, zz)[axis]
+        u = np.zeros((3,) + s.shape)
+        u[axis] = np.sin(2 * np.pi * c / L)
+        got = oracle.fd_divergence(s, u)
+        want = np.cos(2 * np.pi * c / L) * np.sin(2 * np.pi / L)
+        assert np.max(np.abs(got - want)) < 1e-14, (axis, np.max(np.abs(got - want)))
+
+
+def test_divu_mode_keeps_eq48_next_to_walls_only():
+    """divu_mode = 1 (finite differences in the interior) leaves div u of Eq. 48 on the layers
+    next to the bottom wall and the top outflow and changes it inside the pool (first step,
+    both runs from the same state)."""
+    case = W.pool_boiling(12, 10, 16, height=6.0, hot_sigma=2.0)
+    s0 = case["setup"]
+    s1 = W.LatticeSetup(**{**s0.__dict__, "divu_mode": 1})
+    Tc = oracle.Tc_of(s0)
+    rl, rv, _ = oracle.maxwell(s0, 0.86 * Tc)
+    rho, T, _ = W.build_fields(case, Tc, rl, rv)
+    div = []
+    for s in (s0, s1):
+        o = oracle.Oracle(s)
+        o.init(rho, T)
+        o.step(1)
+        div.append(o.diag()["divu"])
+        o.close()
+    assert np.array_equal(div[0][0], div[1][0]) and np.array_equal(div[0][-1], div[1][-1])
+    assert np.max(np.abs(div[0][1:-1] - div[1][1:-1])) > 1e-6 * np.max(np.abs(div[0]))
+
+
 def test_anti_bounce_back_linear_profile():
     """Eq. 51 walls at two temperatures give the linear steady conduction profile."""
     nz = 16

@@ -137,6 +137,7 @@ class LatticeSetup:
     thermal_off: int = 0          # g frozen (isothermal phase)
     rho_buoy: float = 0.0         # > 0: fixed reference density of the buoyancy force (else rho_ave)
     thermal_bgk: int = 0          # 1: BGK D3Q7 collision (one rate 1/varsigma_T) instead of MRT
+    divu_mode: int = 0            # 1: finite-difference div u in the interior, Eq. 48 next to solid faces
 
     @property
     def shape(self):
