@@ -154,6 +154,19 @@ int lbm_get_totals(lbm_ctx* ctx, double* mass, double* T_sum, double* rho_ave);
 /* Number of steps taken since lbm_init_fields. */
 long long lbm_steps_done(const lbm_ctx* ctx);
 
+/* Checkpoint of the state (every population of the current buffer, the phi_s history of
+ * Eqs. 23-24, the sums that give the next step's rho_ave, the step count), for resuming a run
+ * later or in another context of the same lattice size and storage precision: the steps that
+ * follow lbm_load_state are bit-identical to those the saving context would have taken.
+ *   lbm_state_bytes  size of a checkpoint of this context (0 if ctx is NULL)
+ *   lbm_save_state   writes it to buf (host memory, at least lbm_state_bytes bytes); synchronises
+ *   lbm_load_state   reads it from buf (host memory); LBM_EINVAL if it was written for another
+ *                    lattice size or precision, or is not a checkpoint; synchronises
+ * Errors: LBM_EINVAL (NULL or short buffer, mismatch), LBM_ESTATE (save before init), LBM_ECUDA. */
+size_t lbm_state_bytes(const lbm_ctx* ctx);
+int lbm_save_state(lbm_ctx* ctx, void* buf, size_t bytes);
+int lbm_load_state(lbm_ctx* ctx, const void* buf, size_t bytes);
+
 /* Kernel variant the context runs (LBM_KERNEL_TWO_PASS, LBM_KERNEL_FUSED or
  * LBM_KERNEL_FUSED_TMA; AUTO resolved).  The first step after lbm_init_fields, and steps with a
  * frozen field, always run the generic fused kernel. */

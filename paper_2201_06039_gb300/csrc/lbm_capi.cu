@@ -627,6 +627,75 @@ int lbm_get_totals(lbm_ctx* c, double* mass, double* T_sum, double* rho_ave) {
 
 long long lbm_steps_done(const lbm_ctx* c) { return c ? c->steps : 0; }
 
+// Checkpoint layout: a fixed header, the current population buffer (26 slots of Ns elements,
+// ghost cells included), the phi_s history (N floats), the two sums of the next step's rho_ave.
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int version, nx, ny, nz, precision, fresh_f, fresh_g, first;
+    long long steps, pop_bytes, phis_bytes;
+};
+const char kCkptMagic[8] = {'G', 'B', '3', 'L', 'B', 'M', 'C', 'K'};
+size_t ckpt_pop_bytes(const lbm_ctx* c) { return (size_t)kSlots * c->dp.Ns * pop_bytes(c->p.precision); }
+}  // namespace
+
+size_t lbm_state_bytes(const lbm_ctx* c) {
+    if (!c) return 0;
+    return sizeof(CkptHeader) + ckpt_pop_bytes(c) + 4 * (size_t)c->dp.N + 2 * sizeof(double);
+}
+
+int lbm_save_state(lbm_ctx* c, void* buf, size_t bytes) {
+    if (!c || !buf) return fail(LBM_EINVAL, "ctx and buf are required");
+    if (!c->initialised) return fail(LBM_ESTATE, "lbm_save_state before lbm_init_fields");
+    if (bytes < lbm_state_bytes(c)) return fail(LBM_EINVAL, "buffer of %zu bytes, %zu needed", bytes, lbm_state_bytes(c));
+    CkptHeader h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, kCkptMagic, 8);
+    h.version = 1;
+    h.nx = c->p.nx; h.ny = c->p.ny; h.nz = c->p.nz; h.precision = c->p.precision;
+    h.fresh_f = c->fresh_f; h.fresh_g = c->fresh_g; h.first = c->first;
+    h.steps = c->steps;
+    h.pop_bytes = (long long)ckpt_pop_bytes(c);
+    h.phis_bytes = 4LL * c->dp.N;
+    char* out = (char*)buf;
+    memcpy(out, &h, sizeof(h));
+    out += sizeof(h);
+    CK(cudaMemcpyAsync(out, c->pbuf(c->cur), (size_t)h.pop_bytes, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(out + h.pop_bytes, c->base + c->L.phis, (size_t)h.phis_bytes, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(out + h.pop_bytes + h.phis_bytes, c->sums(c->slot), 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_load_state(lbm_ctx* c, const void* buf, size_t bytes) {
+    if (!c || !buf) return fail(LBM_EINVAL, "ctx and buf are required");
+    if (bytes < sizeof(CkptHeader)) return fail(LBM_EINVAL, "not a checkpoint (%zu bytes)", bytes);
+    CkptHeader h;
+    memcpy(&h, buf, sizeof(h));
+    if (memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1) return fail(LBM_EINVAL, "not a checkpoint");
+    if (h.nx != c->p.nx || h.ny != c->p.ny || h.nz != c->p.nz || h.precision != c->p.precision)
+        return fail(LBM_EINVAL, "checkpoint of a %d x %d x %d lattice (precision %d), context is %d x %d x %d (%d)",
+                    h.nx, h.ny, h.nz, h.precision, c->p.nx, c->p.ny, c->p.nz, c->p.precision);
+    if (bytes < lbm_state_bytes(c) || h.pop_bytes != (long long)ckpt_pop_bytes(c) || h.phis_bytes != 4LL * c->dp.N)
+        return fail(LBM_EINVAL, "checkpoint is truncated or of another layout");
+    const char* in = (const char*)buf + sizeof(h);
+    CK(cudaMemcpyAsync(c->pbuf(c->cur), in, (size_t)h.pop_bytes, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->base + c->L.phis, in + h.pop_bytes, (size_t)h.phis_bytes, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->sums(c->slot), in + h.pop_bytes + h.phis_bytes, 2 * sizeof(double), cudaMemcpyHostToDevice,
+                       c->stream));
+    // the saving context may not have kept the ghost cells (kernels without TMA do not use them)
+    if (c->maps.ok && !h.fresh_f && !h.fresh_g) CK(launch_ghosts(c->dp, c->p.precision, c->pbuf(c->cur), c->stream));
+    CK(cudaMemsetAsync(c->base + c->L.flag, 0, sizeof(int), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->fresh_f = h.fresh_f != 0;
+    c->fresh_g = h.fresh_g != 0;
+    c->first = h.first != 0;
+    c->steps = h.steps;
+    c->initialised = true;
+    return LBM_OK;
+}
+
 int lbm_kernel_in_use(const lbm_ctx* c) {
     if (!c) return LBM_EINVAL;
     if (c->variant == LBM_KERNEL_FUSED && c->maps.ok) return LBM_KERNEL_FUSED_TMA;

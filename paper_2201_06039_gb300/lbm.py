@@ -49,6 +49,7 @@ EXPORTS = ["lbm_params_default", "lbm_eos_critical", "lbm_workspace_bytes", "lbm
            "lbm_init_fields", "lbm_step", "lbm_get_moments", "lbm_get_totals", "lbm_steps_done",
            "lbm_kernel_in_use",
            "lbm_step_profiled", "lbm_destroy", "lbm_status_str", "lbm_last_error", "lbm_field_sum_noalloc",
+           "lbm_state_bytes", "lbm_save_state", "lbm_load_state",
            "lbm_batch_create", "lbm_batch_nodes", "lbm_batch_init_fields", "lbm_batch_step", "lbm_batch_autotune",
            "lbm_batch_plan", "lbm_batch_select_plan", "lbm_batch_get_moments", "lbm_batch_get_totals",
            "lbm_batch_steps_done", "lbm_batch_destroy"]
@@ -90,6 +91,10 @@ def lib(build_if_missing: bool = True):
     L.lbm_get_totals.argtypes = [vp, dp, dp, dp]
     L.lbm_steps_done.argtypes = [vp]
     L.lbm_steps_done.restype = C.c_longlong
+    L.lbm_state_bytes.argtypes = [vp]
+    L.lbm_state_bytes.restype = C.c_size_t
+    L.lbm_save_state.argtypes = [vp, vp, C.c_size_t]
+    L.lbm_load_state.argtypes = [vp, vp, C.c_size_t]
     L.lbm_kernel_in_use.argtypes = [vp]
     L.lbm_step_profiled.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_int)]
     L.lbm_destroy.argtypes = [vp]
@@ -181,6 +186,22 @@ def lbm_get_totals(ctx):
 
 def lbm_steps_done(ctx) -> int:
     return int(lib().lbm_steps_done(ctx))
+
+
+def lbm_state_bytes(ctx) -> int:
+    return int(lib().lbm_state_bytes(ctx))
+
+
+def lbm_save_state(ctx) -> np.ndarray:
+    """Checkpoint of the context's state as a host byte array."""
+    buf = np.empty(lbm_state_bytes(ctx), dtype=np.uint8)
+    _check(lib().lbm_save_state(ctx, buf.ctypes.data, buf.nbytes), "lbm_save_state")
+    return buf
+
+
+def lbm_load_state(ctx, buf: np.ndarray):
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    _check(lib().lbm_load_state(ctx, buf.ctypes.data, buf.nbytes), "lbm_load_state")
 
 
 def lbm_kernel_in_use(ctx) -> int:
@@ -349,6 +370,12 @@ class Lattice:
     @property
     def steps_done(self):
         return lbm_steps_done(self.ctx)
+
+    def save_state(self) -> np.ndarray:
+        return lbm_save_state(self.ctx)
+
+    def load_state(self, buf: np.ndarray):
+        lbm_load_state(self.ctx, buf)
 
 
 class Batch:

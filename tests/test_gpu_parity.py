@@ -277,6 +277,53 @@ def test_bounded_wait_timeout_reports_etimeout_and_context_recovers():
         assert np.array_equal(got[k], ref[k]), k
 
 
+@pytest.mark.parametrize("kernels", [(dict(kernel=2, use_tma=1), dict(kernel=2, use_tma=1)),
+                                     (dict(kernel=1), dict(kernel=2, use_tma=1)),
+                                     (dict(kernel=2, use_tma=1), dict(kernel=2, use_tma=0))])
+def test_checkpoint_resume_is_bit_identical(kernels):
+    """lbm_save_state after 40 steps and lbm_load_state into a fresh context (same or another
+    kernel variant; the loader refreshes the ghost cells the TMA kernel reads) continue exactly
+    as the saving context does: 25 more steps, bit for bit, steps counted on."""
+    from paper_2201_06039_gb300 import lbm
+    case = W.pool_boiling(72, 40, 30, height=12.0, hot_sigma=4.0)
+    rho, T, u = inputs(case)
+    s = case["setup"]
+    a = lbm.Lattice(lbm.params_from_setup(s, **kernels[0]))
+    a.init(rho.astype(np.float32), T.astype(np.float32))
+    a.step(40)
+    ck = a.save_state()
+    assert ck.nbytes == lbm.lbm_state_bytes(a.ctx)
+    a.step(25)
+    want = a.moments()
+    a.close()
+    b = lbm.Lattice(lbm.params_from_setup(s, **kernels[1]))
+    b.load_state(ck)
+    assert b.steps_done == 40
+    b.step(25)
+    got = b.moments()
+    assert b.steps_done == 65
+    b.close()
+    for k in want:
+        assert np.array_equal(got[k], want[k]), k
+
+
+def test_checkpoint_of_another_lattice_is_rejected():
+    from paper_2201_06039_gb300 import lbm
+    case = W.static_droplet(16, R0=4.0)
+    rho, T, u = inputs(case)
+    a = lbm.Lattice(lbm.params_from_setup(case["setup"]))
+    a.init(rho.astype(np.float32), T.astype(np.float32))
+    ck = a.save_state()
+    a.close()
+    b = lbm.Lattice(lbm.params_from_setup(W.static_droplet(20, R0=4.0)["setup"]))
+    with pytest.raises(lbm.LbmError) as ei:
+        b.load_state(ck)
+    assert ei.value.status == lbm.LBM_EINVAL
+    with pytest.raises(lbm.LbmError):
+        b.load_state(ck[:100])
+    b.close()
+
+
 def test_step_before_init_is_a_state_error():
     from paper_2201_06039_gb300 import lbm
     lat = lbm.Lattice(lbm.params_from_setup(W.LatticeSetup(8, 8, 8)))
