@@ -108,6 +108,14 @@ typedef struct {
                                      nodes whose stencil stays inside the fluid, Eq. 48 next to
                                      wall and outflow faces.  Runs the two-pass kernels plus a
                                      velocity pass (kernel AUTO or TWO_PASS; FUSED is rejected) */
+    double wall_rho;              /* wetting of the -z wall (LBM_BC_WALL): virtual density of the
+                                     solid layer below it in the psi and grad-rho stencils (its psi
+                                     from Eqs. 8, 49 at the wall temperature); 0 = neutral mirror
+                                     (the solid node copies the fluid node above it) */
+    double wall_rho_patch, wall_patch_half;   /* virtual density inside the square
+                                     |x - nx/2| < half, |y - ny/2| < half of the -z wall (the
+                                     hydrophobic region of the boiling test, Sec. IV.C; a side of
+                                     55 nodes is half = 27.5); half 0 = no patch */
 } lbm_params;
 
 /* Fill *p with the workload-independent defaults of Sec. IV: tau_e = 1.25, tau_v = 0.8,

@@ -45,6 +45,7 @@ class OrcParams(C.Structure):
         ("rho_buoy", C.c_double),
         ("thermal_bgk", C.c_int),
         ("divu_mode", C.c_int),
+        ("wall_rho", C.c_double), ("wall_rho_patch", C.c_double), ("wall_patch_half", C.c_double),
     ]
 
 
@@ -139,6 +140,9 @@ def params_from_setup(s) -> OrcParams:
     p.rho_buoy = s.rho_buoy
     p.thermal_bgk = int(s.thermal_bgk)
     p.divu_mode = int(getattr(s, "divu_mode", 0))
+    p.wall_rho = float(getattr(s, "wall_rho", 0.0))
+    p.wall_rho_patch = float(getattr(s, "wall_rho_patch", 0.0))
+    p.wall_patch_half = float(getattr(s, "wall_patch_half", 0.0))
     return p
 
 

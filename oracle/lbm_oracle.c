@@ -87,6 +87,10 @@ typedef struct {
     int divu_mode;           /* 0: div u by Eq. 48 at every node; 1: isotropic finite differences of
                                 u, with Eq. 48 only at nodes whose stencil reaches a wall or
                                 outflow face (the traditional treatment Sec. III.C describes) */
+    double wall_rho;         /* > 0: wetting -z wall: virtual density of the solid layer below it in
+                                the psi and grad-rho stencils (psi at the wall temperature) */
+    double wall_rho_patch, wall_patch_half;   /* virtual density inside the square
+                                |x - nx/2| < half, |y - ny/2| < half; half 0: none */
 } orc_params;
 
 typedef struct {
@@ -463,17 +467,34 @@ static int macroscopic(orc_state* s) {
     return bad;
 }
 
+/* psi and rho of the solid node below (x, y) of a wetting -z wall: the virtual density (the
+   patch value inside the square around (nx/2, ny/2)), psi from Eqs. 8, 49 at T_w(x, y) */
+static void wall_virtual(const orc_params* p, int x, int y, real* psi, real* rho) {
+    real dx = (real)x - 0.5 * p->nx, dy = (real)y - 0.5 * p->ny;
+    real h = p->wall_patch_half;
+    real rw = (h > 0.0 && fabs(dx) < h && fabs(dy) < h) ? (real)p->wall_rho_patch : (real)p->wall_rho;
+    real Tw = wall_T(p, 4, x, y);
+    *psi = sqrt(2.0 * (p_eos(p, rw, Tw) - rw * CS2) / (G_INT * 1.0));
+    *rho = rw;
+}
+
 /* per-node force pieces: F_m (Eq. 7) and the isotropic gradient of rho (stencil of Sec. III.C) */
 static void node_forces(const orc_state* s, int x, int y, int z, real Fm[3], real grho[3]) {
     const orc_params* p = &s->p;
     long i = node_index(p, x, y, z);
+    const int wet = p->wall_rho > 0.0 && p->bc[4] == ORC_WALL;
     real acc[3] = {0, 0, 0}, gr[3] = {0, 0, 0};
     for (int a = 1; a < Q19; ++a) {
         int e2 = EX[a] * EX[a] + EY[a] * EY[a] + EZ[a] * EZ[a];
         real w = e2 == 1 ? 1.0 / 6.0 : 1.0 / 12.0;
         long j = stencil_neighbour(p, x, y, z, EX[a], EY[a], EZ[a]);
-        acc[0] += w * s->psi[j] * EX[a]; acc[1] += w * s->psi[j] * EY[a]; acc[2] += w * s->psi[j] * EZ[a];
-        gr[0] += w * s->rho[j] * EX[a]; gr[1] += w * s->rho[j] * EY[a]; gr[2] += w * s->rho[j] * EZ[a];
+        real ps = s->psi[j], rh = s->rho[j];
+        if (wet && z + EZ[a] < 0) {   /* solid layer below the wetting wall */
+            long jj = stencil_neighbour(p, x, y, 0, EX[a], EY[a], 0);
+            wall_virtual(p, (int)(jj % p->nx), (int)((jj / p->nx) % p->ny), &ps, &rh);
+        }
+        acc[0] += w * ps * EX[a]; acc[1] += w * ps * EY[a]; acc[2] += w * ps * EZ[a];
+        gr[0] += w * rh * EX[a]; gr[1] += w * rh * EY[a]; gr[2] += w * rh * EZ[a];
     }
     for (int k = 0; k < 3; ++k) {
         Fm[k] = -G_INT * s->psi[i] * acc[k];

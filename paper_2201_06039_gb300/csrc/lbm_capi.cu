@@ -145,6 +145,10 @@ int validate(const lbm_params* p) {
     if (p->precision < 0 || p->precision > 2) return fail(LBM_EINVAL, "unknown precision");
     if (p->kernel < 0 || p->kernel > 2) return fail(LBM_EINVAL, "unknown kernel variant");
     if (p->divu_mode < 0 || p->divu_mode > 1) return fail(LBM_EINVAL, "divu_mode must be 0 or 1");
+    if (p->wall_rho < 0.0 || (p->wall_rho > 0.0 && p->bc[4] != LBM_BC_WALL))
+        return fail(LBM_EINVAL, "wall_rho > 0 needs a wall (LBM_BC_WALL) at the -z face");
+    if (p->wall_patch_half < 0.0 || (p->wall_patch_half > 0.0 && !(p->wall_rho > 0.0 && p->wall_rho_patch > 0.0)))
+        return fail(LBM_EINVAL, "a wetting patch needs wall_rho > 0 and wall_rho_patch > 0");
     if (p->divu_mode == 1 && p->kernel == LBM_KERNEL_FUSED)
         return fail(LBM_EINVAL, "finite-difference div u runs on the two-pass kernels (kernel AUTO or TWO_PASS)");
     if (p->hot_dT != 0.0 && !(p->hot_sigma > 0)) return fail(LBM_EINVAL, "hot_sigma must be positive");
@@ -188,6 +192,12 @@ DevParams make_dev(const lbm_params* p) {
     d.test_stall = p->test_stall ? 1 : 0;
     d.thermal_bgk = p->thermal_bgk ? 1 : 0;
     d.divu_mode = p->divu_mode;
+    d.wet = p->wall_rho > 0.0 && p->bc[4] == LBM_BC_WALL ? 1 : 0;
+    d.wet_rho = (float)p->wall_rho;
+    d.wet_rho_patch = (float)p->wall_rho_patch;
+    d.wet_half = p->wall_patch_half > 0.0 ? (float)p->wall_patch_half : 0.f;
+    d.wet_cx = 0.5f * (float)p->nx;
+    d.wet_cy = 0.5f * (float)p->ny;
     if (p->precision != LBM_FP32) {
         for (int a = 0; a < 19; ++a) {
             int e2 = ex19(a) * ex19(a) + ey19(a) * ey19(a) + ez19(a) * ez19(a);

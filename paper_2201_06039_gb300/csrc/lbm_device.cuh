@@ -76,6 +76,8 @@ struct DevParams {
     int test_stall;           // timeout-path test: the TMA producer waits on a barrier nothing completes
     int thermal_bgk;          // 1: BGK D3Q7 collision (n4..n6 relaxed at 1/varsigma_T too)
     int divu_mode;            // 1: finite-difference div u away from solid faces (two-pass kernels)
+    int wet;                  // 1: virtual-density solid layer below the -z wall (wetting)
+    float wet_rho, wet_rho_patch, wet_half, wet_cx, wet_cy;
     float shift_f[19];        // storage shift w_a rho_ref (16-bit storage only, else 0)
     float shift_g[7];         // storage shift w_a T_ref
 };
@@ -320,6 +322,15 @@ __device__ __forceinline__ float psi_squared(const DevParams& P, float rho, floa
     float inv = __fdividef(1.f, d1 * d2);   // one reciprocal for both denominators
     float p = __fmaf_rn(-(P.a * theta * rho * rho), d1 * inv, __fmul_rn(rho * P.R * T, d2 * inv));
     return 2.f * (rho * (1.f / 3.f) - p);
+}
+
+// (psi, rho) of the solid node below (x, y) of the -z wall when it carries a virtual density
+// (wetting): rho_w outside the square patch, the patch value inside, psi from Eqs. 8, 49 at the wall
+// temperature T_w(x, y).
+__device__ __forceinline__ float2 wall_psirho(const DevParams& P, int x, int y) {
+    const float dx = (float)x - P.wet_cx, dy = (float)y - P.wet_cy;
+    const float rw = fabsf(dx) < P.wet_half && fabsf(dy) < P.wet_half ? P.wet_rho_patch : P.wet_rho;
+    return make_float2(psi_of(psi_squared(P, rw, wall_T(P, 4, x, y))), rw);
 }
 
 // f = M^-1 m from the pair sums / differences of the raw moments: a* = f_+ + f_-, b* = f_+ - f_-

@@ -112,7 +112,11 @@ __device__ __forceinline__ void stencil_term(const DevParams& P, const float2* _
     constexpr int ex = ex19(A), ey = ey19(A), ez = ez19(A);
     constexpr float w = (ex * ex + ey * ey + ez * ez) == 1 ? (1.f / 6.f) : (1.f / 12.f);
     int j = node_of(P, nb_c(ex, x, n.xm, n.xp), nb_c(ey, y, n.ym, n.yp), nb_c(ez, z, n.zm, n.zp));
-    float2 q = __ldg(pr + j);
+    float2 q;
+    if (ez < 0 && z == 0 && P.wet)   // solid layer below a wetting -z wall: virtual (psi, rho)
+        q = wall_psirho(P, nb_c(ex, x, n.xm, n.xp), nb_c(ey, y, n.ym, n.yp));
+    else
+        q = __ldg(pr + j);
     if (ex) { s.Fx += (ex * w) * q.x; s.gx += (ex * w) * q.y; }
     if (ey) { s.Fy += (ey * w) * q.x; s.gy += (ey * w) * q.y; }
     if (ez) { s.Fz += (ez * w) * q.x; s.gz += (ez * w) * q.y; }

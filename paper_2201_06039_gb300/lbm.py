@@ -41,6 +41,7 @@ class LbmParams(C.Structure):
         ("cuda_stream", C.c_void_p),
         ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t), ("test_stall", C.c_int),
         ("thermal_bgk", C.c_int), ("divu_mode", C.c_int),
+        ("wall_rho", C.c_double), ("wall_rho_patch", C.c_double), ("wall_patch_half", C.c_double),
     ]
 
 
@@ -309,6 +310,9 @@ def params_from_setup(setup, **overrides) -> LbmParams:
     p.rho_buoy = getattr(setup, "rho_buoy", 0.0)
     p.thermal_bgk = int(getattr(setup, "thermal_bgk", 0))
     p.divu_mode = int(getattr(setup, "divu_mode", 0))
+    p.wall_rho = getattr(setup, "wall_rho", 0.0)
+    p.wall_rho_patch = getattr(setup, "wall_rho_patch", 0.0)
+    p.wall_patch_half = getattr(setup, "wall_patch_half", 0.0)
     for k, v in overrides.items():
         setattr(p, k, v)
     return p

@@ -84,6 +84,21 @@ def test_finite_difference_divu_needs_the_two_pass_kernels():
     assert ei.value.status == G.LBM_EINVAL
 
 
+@pytest.mark.parametrize("bottom,rho_w,rho_p,radius", [(0, 0.5, 0.0, 0.0), (1, -0.1, 0.0, 0.0),
+                                                       (1, 0.5, 0.0, 3.0), (1, 0.0, 0.3, 3.0),
+                                                       (1, 0.5, 0.3, -1.0)])
+def test_wetting_wall_parameters_checked(bottom, rho_w, rho_p, radius):
+    """A virtual wall density needs a -z wall; a patch needs both densities positive."""
+    p = G.lbm_params_default()
+    p.nx = p.ny = p.nz = 8
+    if bottom:
+        p.bc[4] = p.bc[5] = G.LBM_BC_WALL
+    p.wall_rho, p.wall_rho_patch, p.wall_patch_half = rho_w, rho_p, radius
+    with pytest.raises(G.LbmError) as ei:
+        G.lbm_create(p)
+    assert ei.value.status == G.LBM_EINVAL
+
+
 def test_one_sided_periodic_axis_rejected():
     p = G.lbm_params_default()
     p.nx = p.ny = p.nz = 8

@@ -7,6 +7,7 @@ floor of the case), the floor being measured with the FP32 build of the oracle.
 import numpy as np
 import pytest
 
+import oracle
 import workloads as W
 from tests._parity import BAR, bars, fp32_floor, inputs, rel_errors, run_gpu, run_oracle
 
@@ -113,6 +114,21 @@ def test_parity_finite_difference_divu(case_name):
 @pytest.mark.parametrize("variant", VARIANTS)
 def test_parity_pool_boiling_small(variant):
     case = W.pool_boiling(40, 36, 48, height=16.0, hot_sigma=4.0)
+    _compare(case, 400, variant)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_parity_wetting_wall_with_patch(variant):
+    """Virtual-density wetting of the bottom wall (a liquid-like solid layer) with a square
+    patch of vapour-like virtual density over the hot spot, on the small pool: the solid layer
+    enters the psi and grad-rho stencils of every kernel variant, against the oracle."""
+    case = W.pool_boiling(40, 36, 48, height=16.0, hot_sigma=4.0)
+    s = case["setup"]
+    Tc = oracle.Tc_of(s)
+    rl, rv, _ = oracle.maxwell(s, 0.86 * Tc)
+    case = dict(case, setup=W.LatticeSetup(**{**s.__dict__, "wall_rho": rl,
+                                              "wall_rho_patch": rv + 0.3 * (rl - rv),
+                                              "wall_patch_half": 5.5}))
     _compare(case, 400, variant)
 
 

@@ -422,6 +422,39 @@ def test_isotropic_gradient_exact_for_linear_field_and_zero_force_uniform():
     assert np.max(np.abs(o2.diag()["Fm"])) < 1e-15
 
 
+def test_wetting_wall_virtual_density_closed_form():
+    """Uniform liquid over a -z wall whose solid layer carries a virtual density rho_w (and
+    rho_p inside the square |x - 6| < 3, |y - 6| < 3): in the bottom layer the five
+    neighbours below are solid, the five above are fluid (weights 1/6 + 4 x 1/12 = 1/2), so
+    F_m,z = -G psi_f (psi_f - psi_w) / 2 and d rho / dz = (rho_f - rho_w) / 2, with psi_w from
+    Eq. 8 at the wall temperature; F_m,x = F_m,y = 0 where all five solid neighbours share one
+    density, and the layers above feel nothing."""
+    s = W.LatticeSetup(12, 12, 8, bc=(0, 0, 0, 0, 1, 1), sigma=0.11, flow_off=1,
+                       T_wall_over_Tc=(0.86, 0.86, 0.86, 0.86, 0.93, 0.86),
+                       wall_rho=0.55, wall_rho_patch=0.21, wall_patch_half=3.0)
+    Tc = oracle.Tc_of(s)
+    rho_f, T_f, T_w = 0.62, 0.86 * Tc, 0.93 * Tc
+    o = oracle.Oracle(s)
+    o.init(np.full(s.shape, rho_f), np.full(s.shape, T_f))
+    o.step(1)
+    d = o.diag()
+    psi = lambda r, t: math.sqrt(2.0 * (r / 3.0 - oracle.p_eos(s, r, t)))
+    psi_f = psi(rho_f, T_f)
+    assert abs(d["psi"][3, 5, 5] - psi_f) < 1e-12
+    for (y, x), rho_w in (((6, 6), 0.21), ((1, 1), 0.55), ((10, 2), 0.55)):
+        psi_w = psi(rho_w, T_w)
+        assert abs(d["Fm"][0, y, x, 2] - 0.5 * psi_f * (psi_f - psi_w)) < 1e-13, (y, x)
+        assert np.max(np.abs(d["Fm"][0, y, x, :2])) < 1e-14
+        assert abs(d["gradrho"][0, y, x, 2] - 0.5 * (rho_f - rho_w)) < 1e-14
+    # a patch edge node sees both densities below it: the x force points along the contrast
+    psi_p, psi_o = psi(0.21, T_w), psi(0.55, T_w)
+    # (9, 6): dx = 3 (outside), neighbours x = 8 inside (dx 2), x = 10 outside
+    fx = psi_f * (1.0 / 12.0) * (psi_o - psi_p)   # -G psi_f w (psi(x+1, -1) - psi(x-1, -1))
+    assert abs(d["Fm"][0, 6, 9, 0] - fx) < 1e-13
+    assert np.max(np.abs(d["Fm"][1:])) < 1e-14
+    assert np.max(np.abs(d["gradrho"][1:-1])) < 1e-14
+
+
 def test_local_gradT_matches_finite_difference():
     """Eq. 45 (local) against a central difference of T in a smooth conduction field."""
     L = 48

@@ -138,6 +138,9 @@ class LatticeSetup:
     rho_buoy: float = 0.0         # > 0: fixed reference density of the buoyancy force (else rho_ave)
     thermal_bgk: int = 0          # 1: BGK D3Q7 collision (one rate 1/varsigma_T) instead of MRT
     divu_mode: int = 0            # 1: finite-difference div u in the interior, Eq. 48 next to solid faces
+    wall_rho: float = 0.0         # > 0: virtual density of the solid layer below the -z wall (wetting)
+    wall_rho_patch: float = 0.0   # virtual density inside the patch around (nx/2, ny/2)
+    wall_patch_half: float = 0.0  # half side of the square patch; 0: no patch
 
     @property
     def shape(self):
