@@ -119,15 +119,16 @@ def test_parity_pool_boiling_small(variant):
 
 @pytest.mark.parametrize("variant", VARIANTS)
 def test_parity_wetting_wall_with_patch(variant):
-    """Virtual-density wetting of the bottom wall (a liquid-like solid layer) with a square
-    patch of vapour-like virtual density over the hot spot, on the small pool: the solid layer
-    enters the psi and grad-rho stencils of every kernel variant, against the oracle."""
+    """Virtual-density wetting of the bottom wall (hydrophilic: half way between the coexistence
+    densities) with a square hydrophobic patch (a quarter of the way) over the hot spot, on the
+    small pool: the solid layer enters the psi and grad-rho stencils of every kernel variant,
+    against the oracle."""
     case = W.pool_boiling(40, 36, 48, height=16.0, hot_sigma=4.0)
     s = case["setup"]
     Tc = oracle.Tc_of(s)
     rl, rv, _ = oracle.maxwell(s, 0.86 * Tc)
-    case = dict(case, setup=W.LatticeSetup(**{**s.__dict__, "wall_rho": rl,
-                                              "wall_rho_patch": rv + 0.3 * (rl - rv),
+    case = dict(case, setup=W.LatticeSetup(**{**s.__dict__, "wall_rho": rv + 0.5 * (rl - rv),
+                                              "wall_rho_patch": rv + 0.25 * (rl - rv),
                                               "wall_patch_half": 5.5}))
     _compare(case, 400, variant)
 
