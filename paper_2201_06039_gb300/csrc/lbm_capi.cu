@@ -44,7 +44,7 @@ size_t pop_bytes(int precision) { return precision == LBM_FP32 ? 4 : 2; }
 namespace {
 
 struct Layout {
-    size_t pops[2], psirho, phis, sums, partial, counter, flag, vel, total;
+    size_t pops[2], psirho, phis, sums, partial, counter, flag, vel, wall, total;
 };
 
 // Device memory of a context: two population buffers (26 slots of Ns elements: the padded,
@@ -62,6 +62,7 @@ Layout layout_of(const lbm_params* p, const DevParams& dp) {
     L.counter = take(sizeof(unsigned));
     L.flag = take(sizeof(int));
     L.vel = take(p->divu_mode == 1 ? 16 * N : 0);
+    L.wall = take(dp.wet ? 8 * (size_t)dp.nx * dp.ny : 0);
     L.total = off;
     return L;
 }
@@ -521,6 +522,10 @@ int lbm_create(const lbm_params* p, lbm_ctx** out) {
     }
     if (c->variant == LBM_KERNEL_FUSED && p->use_tma != 0) make_tma_maps(c);
     cudaError_t e = cudaMemsetAsync(c->base + c->L.sums, 0, c->L.flag + sizeof(int) - c->L.sums, c->stream);
+    if (e == cudaSuccess && c->dp.wet) {
+        c->dp.wall_tab = (const float2*)(c->base + c->L.wall);
+        e = launch_wall_table(c->dp, (float2*)(c->base + c->L.wall), c->stream);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         if (c->owns) cudaFree(c->base);

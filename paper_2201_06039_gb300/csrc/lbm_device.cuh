@@ -78,6 +78,7 @@ struct DevParams {
     int divu_mode;            // 1: finite-difference div u away from solid faces (two-pass kernels)
     int wet;                  // 1: virtual-density solid layer below the -z wall (wetting)
     float wet_rho, wet_rho_patch, wet_half, wet_cx, wet_cy;
+    const float2* wall_tab;   // (psi, rho) of that layer per (x, y), nx * ny, x fastest (wet only)
     float shift_f[19];        // storage shift w_a rho_ref (16-bit storage only, else 0)
     float shift_g[7];         // storage shift w_a T_ref
 };
@@ -326,11 +327,16 @@ __device__ __forceinline__ float psi_squared(const DevParams& P, float rho, floa
 
 // (psi, rho) of the solid node below (x, y) of the -z wall when it carries a virtual density
 // (wetting): rho_w outside the square patch, the patch value inside, psi from Eqs. 8, 49 at the wall
-// temperature T_w(x, y).
+// temperature T_w(x, y).  Constant in time: k_wall_table evaluates it once per context into
+// P.wall_tab, which the stencils read (wall_entry).
 __device__ __forceinline__ float2 wall_psirho(const DevParams& P, int x, int y) {
     const float dx = (float)x - P.wet_cx, dy = (float)y - P.wet_cy;
     const float rw = fabsf(dx) < P.wet_half && fabsf(dy) < P.wet_half ? P.wet_rho_patch : P.wet_rho;
     return make_float2(psi_of(psi_squared(P, rw, wall_T(P, 4, x, y))), rw);
+}
+
+__device__ __forceinline__ float2 wall_entry(const DevParams& P, int x, int y) {
+    return __ldg(P.wall_tab + (size_t)y * P.nx + x);
 }
 
 // f = M^-1 m from the pair sums / differences of the raw moments: a* = f_+ + f_-, b* = f_+ - f_-

@@ -180,7 +180,7 @@ __device__ __forceinline__ void fused_column(const DevParams& P, const S* __rest
     auto psi_pass = [&](int zp) {
         if (!slot_used) return;
         if (zp < 0 && P.wet) {   // solid layer below a wetting -z wall: virtual (psi, rho)
-            ring[((zp + 3) % 3) * Sh::kRingPlane + slot] = wall_psirho(P, mx, my);
+            ring[((zp + 3) % 3) * Sh::kRingPlane + slot] = wall_entry(P, mx, my);
             return;
         }
         const bool in_chunk = zp >= z0 && zp < z1;
@@ -314,8 +314,6 @@ k_fused_batch(DevParams P, const BatchInst* __restrict__ insts, const BatchItem*
         Q.inv_N = I.inv_N;
         Q.hot_cx = 0.5f * (float)I.nx;
         Q.hot_cy = 0.5f * (float)I.ny;
-        Q.wet_cx = Q.hot_cx;
-        Q.wet_cy = Q.hot_cy;
         float r_sum = 0.f, r_c = 0.f, t_sum = 0.f, t_c = 0.f;
         const float rho_ave = buoyancy_ref(P, sums_cur[2 * w.inst], I.inv_N);
         fused_column<S, TY>(Q, src + I.pop_off, dst + I.pop_off, pull_f, pull_g, rho_ave, phis + I.field_off, first,
@@ -754,15 +752,14 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                 wait(&full_bar[s], (k / kStages) & 1);
                 const S* st = reinterpret_cast<const S*>(smem_raw + (size_t)s * Sh::kStageOne);
                 const int mz = map_coord(p, P.nz, P.bc[4], P.bc[5]);
-                const bool solid = p < 0 && P.wet;   // virtual (psi, rho) below a wetting -z wall
+                if (p < 0 && P.wet) {   // virtual (psi, rho) of the solid layer below a wetting -z wall
+#pragma unroll
+                    for (int j = 0; j < J; ++j)
+                        if (use[j]) ring[r * Sh::kRingPlane + roff[j]] = wall_entry(P, mxs[j], mys[j]);
+                } else
 #pragma unroll
                 for (int j = 0; j < J; ++j) {
                     if (!use[j]) continue;
-                    if (solid) {
-                        ring[r * Sh::kRingPlane + roff[j]] = wall_psirho(P, mxs[j], mys[j]);
-                        tring[r * Sh::kRingPlane + roff[j]] = 0.f;
-                        continue;
-                    }
                     float f[19], g[7];
                     stage_pulls<Sh>(P, st + woff[j], src, mxs[j], mys[j], mz, f, g);
                     float rho = sum19(f), T = sum7(g);

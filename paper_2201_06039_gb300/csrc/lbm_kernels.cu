@@ -114,7 +114,7 @@ __device__ __forceinline__ void stencil_term(const DevParams& P, const float2* _
     int j = node_of(P, nb_c(ex, x, n.xm, n.xp), nb_c(ey, y, n.ym, n.yp), nb_c(ez, z, n.zm, n.zp));
     float2 q;
     if (ez < 0 && z == 0 && P.wet)   // solid layer below a wetting -z wall: virtual (psi, rho)
-        q = wall_psirho(P, nb_c(ex, x, n.xm, n.xp), nb_c(ey, y, n.ym, n.yp));
+        q = wall_entry(P, nb_c(ex, x, n.xm, n.xp), nb_c(ey, y, n.ym, n.yp));
     else
         q = __ldg(pr + j);
     if (ex) { s.Fx += (ex * w) * q.x; s.gx += (ex * w) * q.y; }
@@ -312,6 +312,17 @@ cudaError_t launch_collide(const DevParams& P, int precision, const StateBufs& B
     GB300_DISPATCH(precision, (k_collide<S><<<grid_of(P), blk, 0, s>>>(P, (const S*)B.src, (S*)B.dst, B.pull_f,
                                                                         B.pull_g, B.psirho, sums_cur, B.phis, first,
                                                                         B.vel)));
+    return cudaGetLastError();
+}
+
+// (psi, rho) of the virtual-density solid layer below the -z wall, one entry per (x, y)
+__global__ void k_wall_table(DevParams P, float2* tab) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x < P.nx && y < P.ny) tab[(size_t)y * P.nx + x] = wall_psirho(P, x, y);
+}
+
+cudaError_t launch_wall_table(const DevParams& P, float2* tab, cudaStream_t s) {
+    k_wall_table<<<dim3((P.nx + 127) / 128, P.ny), 128, 0, s>>>(P, tab);
     return cudaGetLastError();
 }
 

@@ -99,6 +99,15 @@ def test_wetting_wall_parameters_checked(bottom, rho_w, rho_p, radius):
     assert ei.value.status == G.LBM_EINVAL
 
 
+def test_batch_has_no_wetting_wall():
+    q = G.lbm_params_default()
+    q.bc[4] = q.bc[5] = G.LBM_BC_WALL
+    q.wall_rho = 2.5
+    with pytest.raises(G.LbmError) as ei:
+        G.lbm_batch_create(q, [(8, 8, 8)])
+    assert ei.value.status == G.LBM_EINVAL and "wetting" in str(ei.value)
+
+
 def test_one_sided_periodic_axis_rejected():
     p = G.lbm_params_default()
     p.nx = p.ny = p.nz = 8

@@ -54,6 +54,7 @@ def test_maxwell_coexistence_matches_paper():
     assert abs(oracle.p_eos(s, rv, 0.86 * Tc) - ps) < 1e-12
     # the vapour reference density of the open-top pool-boiling preset is this root
     assert abs(rv - W.RHO_V_086) < 1e-5
+    assert abs(rl - W.RHO_L_086) < 1e-5   # and the wall densities of the nucleate-boiling preset
 
 
 def test_peng_robinson_critical_point():
