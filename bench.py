@@ -2,7 +2,7 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mine|reference]
                     [--kernel auto|two_pass|fused] [--precision fp32|bf16|fp16]
-                    [--workload pool_boiling|evaporation|static_droplet|batch]
+                    [--workload pool_boiling|evaporation|static_droplet|nucleate_boiling|batch]
 
 A "step" is one lattice time step of the whole update (psi/EOS, interaction and buoyancy
 forces, D3Q19 MRT collision, local div u and grad T, phase-change source, D3Q7 MRT collision,
@@ -56,6 +56,8 @@ def workload(name, nx=None, ny=None, nz=None):
         return W.evaporation()
     if name == "static_droplet":
         return W.static_droplet()
+    if name == "nucleate_boiling":
+        return W.nucleate_boiling()
     raise ValueError(name)
 
 

@@ -160,7 +160,7 @@ __device__ void finish_sums(const double2* partial, int n, unsigned* counter, do
 // One tile column: the (x, y) tile at (x0, y0), planes [z0, z1), by all threads of the block.
 // Adds the tile's rho and T to the Kahan pairs (r_sum, r_c), (t_sum, t_c) of the owner threads
 // and ORs a non-finite / psi-domain failure into bad.
-template <typename S, int TY>
+template <typename S, int TY, bool kWet>
 __device__ __forceinline__ void fused_column(const DevParams& P, const S* __restrict__ src, S* __restrict__ dst,
                                              int pull_f, int pull_g, float rho_ave, float* __restrict__ phis,
                                              int first, int x0, int y0, int z0, int z1, float* stage, float2* ring,
@@ -179,7 +179,7 @@ __device__ __forceinline__ void fused_column(const DevParams& P, const S* __rest
 
     auto psi_pass = [&](int zp) {
         if (!slot_used) return;
-        if (zp < 0 && P.wet) {   // solid layer below a wetting -z wall: virtual (psi, rho)
+        if (kWet && zp < 0 && P.wet) {   // solid layer below a wetting -z wall: virtual (psi, rho)
             ring[((zp + 3) % 3) * Sh::kRingPlane + slot] = wall_entry(P, mx, my);
             return;
         }
@@ -265,7 +265,7 @@ k_fused(DevParams P, const S* __restrict__ src, S* __restrict__ dst, int pull_f,
     float r_sum = 0.f, r_c = 0.f, t_sum = 0.f, t_c = 0.f;
     int bad = 0;
     const float rho_ave = buoyancy_ref(P, sums_cur[0], P.inv_N);
-    fused_column<S, TY>(P, src, dst, pull_f, pull_g, rho_ave, phis, first, blockIdx.x * TX, blockIdx.y * TY, z0,
+    fused_column<S, TY, true>(P, src, dst, pull_f, pull_g, rho_ave, phis, first, blockIdx.x * TX, blockIdx.y * TY, z0,
                         min(P.nz, z0 + zchunk), stage, ring, r_sum, r_c, t_sum, t_c, bad);
 
     if (__syncthreads_or(bad) && tid == 0) atomicOr(flag, 1);
@@ -316,7 +316,7 @@ k_fused_batch(DevParams P, const BatchInst* __restrict__ insts, const BatchItem*
         Q.hot_cy = 0.5f * (float)I.ny;
         float r_sum = 0.f, r_c = 0.f, t_sum = 0.f, t_c = 0.f;
         const float rho_ave = buoyancy_ref(P, sums_cur[2 * w.inst], I.inv_N);
-        fused_column<S, TY>(Q, src + I.pop_off, dst + I.pop_off, pull_f, pull_g, rho_ave, phis + I.field_off, first,
+        fused_column<S, TY, false>(Q, src + I.pop_off, dst + I.pop_off, pull_f, pull_g, rho_ave, phis + I.field_off, first,
                             w.x0, w.y0, w.z0, w.z1, stage, ring, r_sum, r_c, t_sum, t_c, bad);
         block_partial<Sh::kThreads>((double)r_sum - (double)r_c, (double)t_sum - (double)t_c, partial, it, tid, 0,
                                     red_a, red_b);
@@ -577,7 +577,7 @@ __device__ __forceinline__ void stage_pulls(const DevParams& P, const typename S
 //   out_empty    tensor store has read the out buffer         (storer    -> collision; FP32)
 // Stage uses and ring uses follow one plane counter k across the CTA's items; out-buffer uses
 // follow the collided-plane counter u.
-template <int TX_, int TY_, typename S>
+template <int TX_, int TY_, typename S, bool kWet>
 __global__ void __maxnreg__((TmaShape<TX_, TY_, S>::kMaxRegs))
 k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ CUtensorMap map6,
             const __grid_constant__ CUtensorMap map_out, const __grid_constant__ CUtensorMap map_out_top,
@@ -752,7 +752,7 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                 wait(&full_bar[s], (k / kStages) & 1);
                 const S* st = reinterpret_cast<const S*>(smem_raw + (size_t)s * Sh::kStageOne);
                 const int mz = map_coord(p, P.nz, P.bc[4], P.bc[5]);
-                if (p < 0 && P.wet) {   // virtual (psi, rho) of the solid layer below a wetting -z wall
+                if (kWet && p < 0) {   // virtual (psi, rho) of the solid layer below a wetting -z wall
 #pragma unroll
                     for (int j = 0; j < J; ++j)
                         if (use[j]) ring[r * Sh::kRingPlane + roff[j]] = wall_entry(P, mxs[j], mys[j]);
@@ -1045,7 +1045,7 @@ cudaError_t launch_ghosts(const DevParams& P, int precision, void* pops, cudaStr
 
 bool tma_eligible(const DevParams& P, int precision) {
     return precision >= 0 && precision <= 2 && P.nx >= 4 && P.ny >= 4 && f_wraps(P.bc[0]) && f_wraps(P.bc[1]) &&
-           f_wraps(P.bc[2]) && f_wraps(P.bc[3]) && !P.flow_off && !P.thermal_off;
+           f_wraps(P.bc[2]) && f_wraps(P.bc[3]) && !P.flow_off && !P.thermal_off && (!P.wet || precision == 0);
 }
 
 size_t tma_smem_bytes(int shape, int precision) {
@@ -1084,12 +1084,12 @@ cudaError_t launch_fused(const DevParams& P, int precision, const StateBufs& B, 
         const int txs = (P.nx + tx - 1) / tx, tys = (P.ny + ty - 1) / ty;
         const int ctas = maps->sms < maps->items ? maps->sms : maps->items;
         if (ghosts_written) *ghosts_written = maps->ghosts;
-#define GB300_TMA(SH, TXV, TYV, ST)                                                                            \
+#define GB300_TMA(SH, TXV, TYV, ST, WET)                                                                       \
         {                                                                                                      \
-            e = cudaFuncSetAttribute(k_fused_tma<TXV, TYV, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+            e = cudaFuncSetAttribute(k_fused_tma<TXV, TYV, ST, WET>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                      (int)SH::kSmem);                                                          \
             if (e != cudaSuccess) return e;                                                                    \
-            k_fused_tma<TXV, TYV, ST><<<ctas, SH::kThreads, SH::kSmem, s>>>(                                   \
+            k_fused_tma<TXV, TYV, ST, WET><<<ctas, SH::kThreads, SH::kSmem, s>>>(                              \
                 maps->m14[B.src_index], maps->m6[B.src_index], maps->mout[B.src_index ^ 1],                    \
                 maps->mout_top[B.src_index ^ 1], maps->mgcol[B.src_index ^ 1], maps->mgcol_top[B.src_index ^ 1], \
                 maps->mgrow[B.src_index ^ 1], maps->mgrow_right[B.src_index ^ 1], maps->mgcor[B.src_index ^ 1], \
@@ -1097,13 +1097,20 @@ cudaError_t launch_fused(const DevParams& P, int precision, const StateBufs& B, 
                 sums_next, B.phis,                                                                             \
                 B.flag, first, maps->zchunk, txs, tys, maps->items);                                           \
         }
-        if (precision == 0) {
-            if (maps->shape == 0) GB300_TMA(Shape0<float>, 32, 8, float) else GB300_TMA(Shape1<float>, 40, 7, float)
+        // the wetting wall's solid plane is a separate instantiation (FP32 storage only), so that
+        // the kernel without it carries no trace of it
+        if (precision == 0 && P.wet) {
+            if (maps->shape == 0) GB300_TMA(Shape0<float>, 32, 8, float, true)
+            else GB300_TMA(Shape1<float>, 40, 7, float, true)
+        } else if (precision == 0) {
+            if (maps->shape == 0) GB300_TMA(Shape0<float>, 32, 8, float, false)
+            else GB300_TMA(Shape1<float>, 40, 7, float, false)
         } else if (precision == 1) {
-            if (maps->shape == 0) GB300_TMA(Shape0<__nv_bfloat16>, 32, 8, __nv_bfloat16)
-            else GB300_TMA(Shape1<__nv_bfloat16>, 40, 7, __nv_bfloat16)
+            if (maps->shape == 0) GB300_TMA(Shape0<__nv_bfloat16>, 32, 8, __nv_bfloat16, false)
+            else GB300_TMA(Shape1<__nv_bfloat16>, 40, 7, __nv_bfloat16, false)
         } else {
-            if (maps->shape == 0) GB300_TMA(Shape0<__half>, 32, 8, __half) else GB300_TMA(Shape1<__half>, 40, 7, __half)
+            if (maps->shape == 0) GB300_TMA(Shape0<__half>, 32, 8, __half, false)
+            else GB300_TMA(Shape1<__half>, 40, 7, __half, false)
         }
 #undef GB300_TMA
         return cudaGetLastError();
