@@ -116,6 +116,16 @@ typedef struct {
                                      |x - nx/2| < half, |y - ny/2| < half of the -z wall (the
                                      hydrophobic region of the boiling test, Sec. IV.C; a side of
                                      55 nodes is half = 27.5); half 0 = no patch */
+    int wall_scheme;              /* wetting of the -z wall: 0 = the fixed virtual densities above;
+                                     1 = densities that follow the fluid (the improved virtual-density
+                                     scheme the paper uses, Sec. II.C): every step the solid node
+                                     below (x, y) takes rho_w = max(phi rho_ave - drho, rho_ave / 10),
+                                     rho_ave the weighted mean (w = 1/6 face, 1/12 edge) of the
+                                     densities of its five fluid neighbours in the layer z = 0;
+                                     phi >= 1 makes the wall hydrophilic, drho > 0 hydrophobic.
+                                     Needs a -z LBM_BC_WALL and wall_rho = wall_rho_patch = 0 */
+    double wall_phi, wall_drho;               /* scheme 1: phi > 0 and drho >= 0 outside the patch */
+    double wall_phi_patch, wall_drho_patch;   /* scheme 1: the same inside the patch */
 } lbm_params;
 
 /* Fill *p with the workload-independent defaults of Sec. IV: tau_e = 1.25, tau_v = 0.8,

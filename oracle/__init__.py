@@ -46,6 +46,8 @@ class OrcParams(C.Structure):
         ("thermal_bgk", C.c_int),
         ("divu_mode", C.c_int),
         ("wall_rho", C.c_double), ("wall_rho_patch", C.c_double), ("wall_patch_half", C.c_double),
+        ("wall_scheme", C.c_int), ("wall_phi", C.c_double), ("wall_drho", C.c_double),
+        ("wall_phi_patch", C.c_double), ("wall_drho_patch", C.c_double),
     ]
 
 
@@ -143,6 +145,9 @@ def params_from_setup(s) -> OrcParams:
     p.wall_rho = float(getattr(s, "wall_rho", 0.0))
     p.wall_rho_patch = float(getattr(s, "wall_rho_patch", 0.0))
     p.wall_patch_half = float(getattr(s, "wall_patch_half", 0.0))
+    p.wall_scheme = int(getattr(s, "wall_scheme", 0))
+    for k in ("wall_phi", "wall_drho", "wall_phi_patch", "wall_drho_patch"):
+        setattr(p, k, float(getattr(s, k, 0.0)))
     return p
 
 

@@ -91,6 +91,9 @@ typedef struct {
                                 the psi and grad-rho stencils (psi at the wall temperature) */
     double wall_rho_patch, wall_patch_half;   /* virtual density inside the square
                                 |x - nx/2| < half, |y - ny/2| < half; half 0: none */
+    int wall_scheme;         /* 1: virtual density phi rho_ave - drho (floored at rho_ave / 10) from
+                                the fluid neighbours of each solid node, every step */
+    double wall_phi, wall_drho, wall_phi_patch, wall_drho_patch;
 } orc_params;
 
 typedef struct {
@@ -467,12 +470,35 @@ static int macroscopic(orc_state* s) {
     return bad;
 }
 
-/* psi and rho of the solid node below (x, y) of a wetting -z wall: the virtual density (the
-   patch value inside the square around (nx/2, ny/2)), psi from Eqs. 8, 49 at T_w(x, y) */
-static void wall_virtual(const orc_params* p, int x, int y, real* psi, real* rho) {
+/* psi and rho of the solid node (x, y, -1) below a wetting -z wall, psi from Eqs. 8, 49 at
+   T_w(x, y).  Scheme 0: the fixed virtual density (the patch value inside the square around
+   (nx/2, ny/2)).  Scheme 1 (the improved virtual-density scheme named in Sec. II.C):
+   rho_w = phi rho_ave - drho, rho_ave = sum_a w_a rho(x_s + e_a) s(x_s + e_a) / sum_a w_a s(x_s + e_a)
+   over the velocity set, s = 1 on fluid nodes and 0 on solid ones; floored at rho_ave / 10 so that
+   psi_w stays real. */
+static void wall_virtual(const orc_state* s, int x, int y, real* psi, real* rho) {
+    const orc_params* p = &s->p;
     real dx = (real)x - 0.5 * p->nx, dy = (real)y - 0.5 * p->ny;
     real h = p->wall_patch_half;
-    real rw = (h > 0.0 && fabs(dx) < h && fabs(dy) < h) ? (real)p->wall_rho_patch : (real)p->wall_rho;
+    int in = h > 0.0 && fabs(dx) < h && fabs(dy) < h;
+    real rw;
+    if (p->wall_scheme == 1) {
+        real num = 0.0, den = 0.0;
+        for (int a = 1; a < Q19; ++a) {
+            if (EZ[a] != 1) continue;   /* the other neighbours of (x, y, -1) are solid */
+            int e2 = EX[a] * EX[a] + EY[a] * EY[a] + EZ[a] * EZ[a];
+            real w = e2 == 1 ? 1.0 / 6.0 : 1.0 / 12.0;
+            long j = stencil_neighbour(p, x, y, -1, EX[a], EY[a], EZ[a]);
+            num += w * s->rho[j];
+            den += w;
+        }
+        real ra = num / den;
+        real phi = in ? p->wall_phi_patch : p->wall_phi, drho = in ? p->wall_drho_patch : p->wall_drho;
+        rw = phi * ra - drho;
+        if (rw < 0.1 * ra) rw = 0.1 * ra;
+    } else {
+        rw = in ? (real)p->wall_rho_patch : (real)p->wall_rho;
+    }
     real Tw = wall_T(p, 4, x, y);
     *psi = sqrt(2.0 * (p_eos(p, rw, Tw) - rw * CS2) / (G_INT * 1.0));
     *rho = rw;
@@ -482,7 +508,7 @@ static void wall_virtual(const orc_params* p, int x, int y, real* psi, real* rho
 static void node_forces(const orc_state* s, int x, int y, int z, real Fm[3], real grho[3]) {
     const orc_params* p = &s->p;
     long i = node_index(p, x, y, z);
-    const int wet = p->wall_rho > 0.0 && p->bc[4] == ORC_WALL;
+    const int wet = (p->wall_rho > 0.0 || p->wall_scheme == 1) && p->bc[4] == ORC_WALL;
     real acc[3] = {0, 0, 0}, gr[3] = {0, 0, 0};
     for (int a = 1; a < Q19; ++a) {
         int e2 = EX[a] * EX[a] + EY[a] * EY[a] + EZ[a] * EZ[a];
@@ -491,7 +517,7 @@ static void node_forces(const orc_state* s, int x, int y, int z, real Fm[3], rea
         real ps = s->psi[j], rh = s->rho[j];
         if (wet && z + EZ[a] < 0) {   /* solid layer below the wetting wall */
             long jj = stencil_neighbour(p, x, y, 0, EX[a], EY[a], 0);
-            wall_virtual(p, (int)(jj % p->nx), (int)((jj / p->nx) % p->ny), &ps, &rh);
+            wall_virtual(s, (int)(jj % p->nx), (int)((jj / p->nx) % p->ny), &ps, &rh);
         }
         acc[0] += w * ps * EX[a]; acc[1] += w * ps * EY[a]; acc[2] += w * ps * EZ[a];
         gr[0] += w * rh * EX[a]; gr[1] += w * rh * EY[a]; gr[2] += w * rh * EZ[a];

@@ -235,7 +235,8 @@ int lbm_batch_create(const lbm_params* common, int n_instances, const int* dims,
     if (n_instances < 1) return fail(LBM_EINVAL, "n_instances must be >= 1");
     if (common->kernel == LBM_KERNEL_TWO_PASS) return fail(LBM_EINVAL, "the batch runs the fused kernel only");
     if (common->divu_mode != 0) return fail(LBM_EINVAL, "the batch computes div u by Eq. 48 only (divu_mode 0)");
-    if (common->wall_rho != 0.0) return fail(LBM_EINVAL, "the batch has no wetting wall (wall_rho 0)");
+    if (common->wall_rho != 0.0 || common->wall_scheme != 0)
+        return fail(LBM_EINVAL, "the batch has no wetting wall (wall_rho 0, wall_scheme 0)");
     lbm_batch* b = new (std::nothrow) lbm_batch();
     if (!b) return fail(LBM_ENOMEM, "host allocation failed");
     b->p = *common;

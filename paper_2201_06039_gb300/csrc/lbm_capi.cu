@@ -146,10 +146,21 @@ int validate(const lbm_params* p) {
     if (p->precision < 0 || p->precision > 2) return fail(LBM_EINVAL, "unknown precision");
     if (p->kernel < 0 || p->kernel > 2) return fail(LBM_EINVAL, "unknown kernel variant");
     if (p->divu_mode < 0 || p->divu_mode > 1) return fail(LBM_EINVAL, "divu_mode must be 0 or 1");
+    if (p->wall_scheme != 0 && p->wall_scheme != 1) return fail(LBM_EINVAL, "wall_scheme must be 0 or 1");
     if (p->wall_rho < 0.0 || (p->wall_rho > 0.0 && p->bc[4] != LBM_BC_WALL))
         return fail(LBM_EINVAL, "wall_rho > 0 needs a wall (LBM_BC_WALL) at the -z face");
-    if (p->wall_patch_half < 0.0 || (p->wall_patch_half > 0.0 && !(p->wall_rho > 0.0 && p->wall_rho_patch > 0.0)))
+    if (p->wall_patch_half < 0.0) return fail(LBM_EINVAL, "wall_patch_half must be >= 0");
+    if (p->wall_scheme == 0 && p->wall_patch_half > 0.0 && !(p->wall_rho > 0.0 && p->wall_rho_patch > 0.0))
         return fail(LBM_EINVAL, "a wetting patch needs wall_rho > 0 and wall_rho_patch > 0");
+    if (p->wall_scheme == 1) {
+        if (p->bc[4] != LBM_BC_WALL) return fail(LBM_EINVAL, "wall_scheme 1 needs a wall (LBM_BC_WALL) at the -z face");
+        if (p->wall_rho != 0.0 || p->wall_rho_patch != 0.0)
+            return fail(LBM_EINVAL, "wall_scheme 1 takes wall_phi / wall_drho, not wall_rho");
+        if (!(p->wall_phi > 0.0) || !(p->wall_drho >= 0.0))
+            return fail(LBM_EINVAL, "wall_scheme 1 needs wall_phi > 0 and wall_drho >= 0");
+        if (p->wall_patch_half > 0.0 && (!(p->wall_phi_patch > 0.0) || !(p->wall_drho_patch >= 0.0)))
+            return fail(LBM_EINVAL, "a wetting patch needs wall_phi_patch > 0 and wall_drho_patch >= 0");
+    }
     if (p->divu_mode == 1 && p->kernel == LBM_KERNEL_FUSED)
         return fail(LBM_EINVAL, "finite-difference div u runs on the two-pass kernels (kernel AUTO or TWO_PASS)");
     if (p->hot_dT != 0.0 && !(p->hot_sigma > 0)) return fail(LBM_EINVAL, "hot_sigma must be positive");
@@ -193,7 +204,12 @@ DevParams make_dev(const lbm_params* p) {
     d.test_stall = p->test_stall ? 1 : 0;
     d.thermal_bgk = p->thermal_bgk ? 1 : 0;
     d.divu_mode = p->divu_mode;
-    d.wet = p->wall_rho > 0.0 && p->bc[4] == LBM_BC_WALL ? 1 : 0;
+    d.wet = (p->wall_rho > 0.0 || p->wall_scheme == 1) && p->bc[4] == LBM_BC_WALL ? 1 : 0;
+    d.wet_scheme = p->wall_scheme;
+    d.wet_phi = (float)p->wall_phi;
+    d.wet_drho = (float)p->wall_drho;
+    d.wet_phi_p = (float)p->wall_phi_patch;
+    d.wet_drho_p = (float)p->wall_drho_patch;
     d.wet_rho = (float)p->wall_rho;
     d.wet_rho_patch = (float)p->wall_rho_patch;
     d.wet_half = p->wall_patch_half > 0.0 ? (float)p->wall_patch_half : 0.f;
@@ -243,6 +259,10 @@ int enqueue_step(lbm_ctx* c, double* kernel_ms = nullptr, int* launches = nullpt
     StateBufs B = c->bufs();
     cudaError_t e;
     bool ghosts_done = false;
+    if (c->dp.wet && c->dp.wet_scheme == 1) {   // virtual densities of this step from the fluid layer z = 0
+        e = launch_wall_table(c->dp, c->p.precision, B.src, B.pull_f, (float2*)(c->base + c->L.wall), c->launch);
+        if (e != cudaSuccess) return fail(LBM_ECUDA, "wall table launch: %s", cudaGetErrorString(e));
+    }
     if (c->variant == LBM_KERNEL_FUSED) {
         if (ev) cudaEventRecord(ev[0], c->launch);
         e = launch_fused(c->dp, c->p.precision, B, c->sums(c->slot), c->sums(c->slot ^ 1), c->first ? 1 : 0,
@@ -522,9 +542,10 @@ int lbm_create(const lbm_params* p, lbm_ctx** out) {
     }
     if (c->variant == LBM_KERNEL_FUSED && p->use_tma != 0) make_tma_maps(c);
     cudaError_t e = cudaMemsetAsync(c->base + c->L.sums, 0, c->L.flag + sizeof(int) - c->L.sums, c->stream);
-    if (e == cudaSuccess && c->dp.wet) {
+    if (e == cudaSuccess && c->dp.wet) {   // scheme 0: the table is constant; scheme 1: refreshed every step
         c->dp.wall_tab = (const float2*)(c->base + c->L.wall);
-        e = launch_wall_table(c->dp, (float2*)(c->base + c->L.wall), c->stream);
+        if (c->dp.wet_scheme == 0)
+            e = launch_wall_table(c->dp, c->p.precision, nullptr, 0, (float2*)(c->base + c->L.wall), c->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {

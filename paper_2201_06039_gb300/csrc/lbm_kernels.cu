@@ -315,14 +315,35 @@ cudaError_t launch_collide(const DevParams& P, int precision, const StateBufs& B
     return cudaGetLastError();
 }
 
-// (psi, rho) of the virtual-density solid layer below the -z wall, one entry per (x, y)
-__global__ void k_wall_table(DevParams P, float2* tab) {
+// (psi, rho) of the virtual-density solid layer below the -z wall, one entry per (x, y).  For
+// scheme 1 the mean density of the solid node's fluid neighbours, (x, y, 0) with weight 1/6 and
+// its four in-plane neighbours with 1/12 each (sum of weights 1/2), comes from the populations
+// this step pulls, summed as the psi pass sums them.
+template <typename S>
+__global__ void __launch_bounds__(128) k_wall_table(DevParams P, const S* __restrict__ fs, int pull_f,
+                                                    float2* __restrict__ tab) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x < P.nx && y < P.ny) tab[(size_t)y * P.nx + x] = wall_psirho(P, x, y);
+    if (x >= P.nx || y >= P.ny) return;
+    float rho_ave = 0.f;
+    if (P.wet_scheme == 1) {
+        const Nbr n = make_nbr(P, x, y, 0);
+        auto rho_at = [&](int xx, int yy) {
+            const Nbr m = make_nbr(P, xx, yy, 0);
+            float f[19];
+            load_f<S>(P, fs, pull_f, sidx(P, xx, yy, 0), xx, yy, 0, m, f);
+            return sum19(f);
+        };
+        const float rc = rho_at(x, y);
+        const float r4 = __fadd_rn(__fadd_rn(rho_at(n.xm, y), rho_at(n.xp, y)), __fadd_rn(rho_at(x, n.ym), rho_at(x, n.yp)));
+        rho_ave = __fadd_rn(__fmul_rn(rc, 1.f / 3.f), __fmul_rn(r4, 1.f / 6.f));
+    }
+    tab[(size_t)y * P.nx + x] = wall_psirho(P, x, y, rho_ave);
 }
 
-cudaError_t launch_wall_table(const DevParams& P, float2* tab, cudaStream_t s) {
-    k_wall_table<<<dim3((P.nx + 127) / 128, P.ny), 128, 0, s>>>(P, tab);
+cudaError_t launch_wall_table(const DevParams& P, int precision, const void* fs, int pull_f, float2* tab,
+                              cudaStream_t s) {
+    const dim3 grid((P.nx + 127) / 128, P.ny);
+    GB300_DISPATCH(precision, (k_wall_table<S><<<grid, 128, 0, s>>>(P, (const S*)fs, pull_f, tab)));
     return cudaGetLastError();
 }
 

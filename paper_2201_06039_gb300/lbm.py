@@ -42,6 +42,8 @@ class LbmParams(C.Structure):
         ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t), ("test_stall", C.c_int),
         ("thermal_bgk", C.c_int), ("divu_mode", C.c_int),
         ("wall_rho", C.c_double), ("wall_rho_patch", C.c_double), ("wall_patch_half", C.c_double),
+        ("wall_scheme", C.c_int), ("wall_phi", C.c_double), ("wall_drho", C.c_double),
+        ("wall_phi_patch", C.c_double), ("wall_drho_patch", C.c_double),
     ]
 
 
@@ -313,6 +315,9 @@ def params_from_setup(setup, **overrides) -> LbmParams:
     p.wall_rho = getattr(setup, "wall_rho", 0.0)
     p.wall_rho_patch = getattr(setup, "wall_rho_patch", 0.0)
     p.wall_patch_half = getattr(setup, "wall_patch_half", 0.0)
+    p.wall_scheme = getattr(setup, "wall_scheme", 0)
+    for k in ("wall_phi", "wall_drho", "wall_phi_patch", "wall_drho_patch"):
+        setattr(p, k, getattr(setup, k, 0.0))
     for k, v in overrides.items():
         setattr(p, k, v)
     return p

@@ -99,6 +99,27 @@ def test_wetting_wall_parameters_checked(bottom, rho_w, rho_p, radius):
     assert ei.value.status == G.LBM_EINVAL
 
 
+@pytest.mark.parametrize("kw", [dict(wall_scheme=2), dict(wall_scheme=1, wall_phi=0.0),
+                                dict(wall_scheme=1, wall_phi=1.1, wall_drho=-0.5),
+                                dict(wall_scheme=1, wall_phi=1.1, wall_rho=2.0),
+                                dict(wall_scheme=1, wall_phi=1.1, wall_patch_half=3.0),
+                                dict(wall_scheme=1, wall_phi=1.1, wall_patch_half=3.0, wall_phi_patch=1.0,
+                                     wall_drho_patch=-1.0),
+                                dict(wall_scheme=1, wall_phi=1.1, bottom=0)])
+def test_wetting_scheme1_parameters_checked(kw):
+    """Scheme 1 needs a -z wall, phi > 0, drho >= 0 (per region) and no fixed densities."""
+    kw = dict(kw)
+    p = G.lbm_params_default()
+    p.nx = p.ny = p.nz = 8
+    if kw.pop("bottom", 1):
+        p.bc[4] = p.bc[5] = G.LBM_BC_WALL
+    for k, v in kw.items():
+        setattr(p, k, v)
+    with pytest.raises(G.LbmError) as ei:
+        G.lbm_create(p)
+    assert ei.value.status == G.LBM_EINVAL
+
+
 def test_batch_has_no_wetting_wall():
     q = G.lbm_params_default()
     q.bc[4] = q.bc[5] = G.LBM_BC_WALL

@@ -117,19 +117,24 @@ def test_parity_pool_boiling_small(variant):
     _compare(case, 400, variant)
 
 
+@pytest.mark.parametrize("scheme", [0, 1])
 @pytest.mark.parametrize("variant", VARIANTS)
-def test_parity_wetting_wall_with_patch(variant):
-    """Virtual-density wetting of the bottom wall (hydrophilic: half way between the coexistence
-    densities) with a square hydrophobic patch (a quarter of the way) over the hot spot, on the
-    small pool: the solid layer enters the psi and grad-rho stencils of every kernel variant,
-    against the oracle."""
+def test_parity_wetting_wall_with_patch(variant, scheme):
+    """Virtual-density wetting of the bottom wall with a square hydrophobic patch over the hot
+    spot, on the small pool, against the oracle for every kernel variant.  Scheme 0: fixed
+    densities (the rest half way between the coexistence densities, the patch a quarter of the
+    way).  Scheme 1: densities that follow the fluid layer every step (phi = 1.1 on the rest,
+    drho = 1.5 on the patch)."""
     case = W.pool_boiling(40, 36, 48, height=16.0, hot_sigma=4.0)
     s = case["setup"]
     Tc = oracle.Tc_of(s)
     rl, rv, _ = oracle.maxwell(s, 0.86 * Tc)
-    case = dict(case, setup=W.LatticeSetup(**{**s.__dict__, "wall_rho": rv + 0.5 * (rl - rv),
-                                              "wall_rho_patch": rv + 0.25 * (rl - rv),
-                                              "wall_patch_half": 5.5}))
+    if scheme == 0:
+        wet = {"wall_rho": rv + 0.5 * (rl - rv), "wall_rho_patch": rv + 0.25 * (rl - rv)}
+    else:
+        wet = {"wall_scheme": 1, "wall_phi": 1.1, "wall_drho": 0.0, "wall_phi_patch": 1.0,
+               "wall_drho_patch": 1.5}
+    case = dict(case, setup=W.LatticeSetup(**{**s.__dict__, **wet, "wall_patch_half": 5.5}))
     _compare(case, 400, variant)
 
 

