@@ -633,6 +633,9 @@ int lbm_get_moments(lbm_ctx* c, float* rho, float* ux, float* uy, float* uz, flo
     if (!c->initialised) return fail(LBM_ESTATE, "lbm_get_moments before lbm_init_fields");
     size_t N = (size_t)c->dp.N;
     StateBufs B = c->bufs();
+    // u carries F_m / 2: a scheme-1 wetting wall's virtual densities must be those of this state
+    if (c->dp.wet && c->dp.wet_scheme == 1)
+        CK(launch_wall_table(c->dp, c->p.precision, B.src, B.pull_f, (float2*)(c->base + c->L.wall), c->stream));
     CK(launch_psi(c->dp, c->p.precision, B, nullptr, c->stream));
     // outputs staged in the population buffer the next step overwrites anyway
     float* stage = (float*)c->pbuf(c->cur ^ 1);
