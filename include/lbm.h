@@ -193,7 +193,7 @@ int lbm_kernel_in_use(const lbm_ctx* ctx);
 /* Enqueue n steps outside any graph and accumulate, per kernel kind, the device time
  * measured with CUDA events on the context's stream and the number of launches
  * (kernel_ms[0]: psi/EOS or fused kernel, [1]: stream-collide kernel, [2]: ghost-cell
- * refresh).  Synchronises.  Used for the roofline figures; the event gaps make it slightly
+ * refresh and the per-step table of a scheme-1 wetting wall).  Synchronises.  Used for the roofline figures; the event gaps make it slightly
  * slower than lbm_step. */
 int lbm_step_profiled(lbm_ctx* ctx, int n, double kernel_ms[3], int launches[3]);
 

@@ -260,8 +260,17 @@ int enqueue_step(lbm_ctx* c, double* kernel_ms = nullptr, int* launches = nullpt
     cudaError_t e;
     bool ghosts_done = false;
     if (c->dp.wet && c->dp.wet_scheme == 1) {   // virtual densities of this step from the fluid layer z = 0
+        if (ev) cudaEventRecord(ev[0], c->launch);
         e = launch_wall_table(c->dp, c->p.precision, B.src, B.pull_f, (float2*)(c->base + c->L.wall), c->launch);
         if (e != cudaSuccess) return fail(LBM_ECUDA, "wall table launch: %s", cudaGetErrorString(e));
+        if (ev) {
+            cudaEventRecord(ev[1], c->launch);
+            cudaEventSynchronize(ev[1]);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[0], ev[1]);
+            kernel_ms[2] += ms;
+            launches[2] += 1;
+        }
     }
     if (c->variant == LBM_KERNEL_FUSED) {
         if (ev) cudaEventRecord(ev[0], c->launch);

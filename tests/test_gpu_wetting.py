@@ -1,0 +1,117 @@
+"""Wetting wall on the GPU: contact angles of the improved virtual-density scheme and the bubble
+nucleation and departure test of Sec. IV.C on the paper's 200 x 200 x 280 geometry.
+
+These check behaviour the paper describes (a sessile droplet takes the angle the wall parameters
+set; a bubble nucleates on the hydrophobic patch, grows and departs, leaving a residual bubble);
+the element-wise parity of the same kernels against the oracle is in test_gpu_parity.py.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _cap_angle(rho, rho_mid):
+    """Contact angle of a sessile drop centred on (nx/2, ny/2) on the -z wall (at z = -1/2): the
+    sphere through the apex and the base circle (radius extrapolated from the layers z = 0, 1)."""
+    nz, ny, nx = rho.shape
+    cy, cx = ny // 2, nx // 2
+    col = rho[:, cy, cx]
+    if col[0] < rho_mid:
+        return 180.0
+    k = int(np.nonzero(col < rho_mid)[0][0])
+    h = (k - 1) + (col[k - 1] - rho_mid) / (col[k - 1] - col[k]) + 0.5
+
+    def radius(z):
+        row = rho[z, cy, cx:]
+        j = int(np.nonzero(row < rho_mid)[0][0])
+        return (j - 1) + (row[j - 1] - rho_mid) / (row[j - 1] - row[j])
+
+    r0, r1 = radius(0), radius(1)
+    a = r0 - 0.5 * (r1 - r0)
+    R = (a * a + h * h) / (2 * h)
+    return math.degrees(math.acos((R - h) / R))
+
+
+@pytest.mark.parametrize("kw,theta,tol", [(dict(wall_phi=1.0, wall_drho=0.0), 90.0, 5.0),
+                                          (dict(wall_phi=W.WET_PHI_37, wall_drho=0.0), 37.0, 3.0),
+                                          (dict(wall_phi=1.0, wall_drho=W.WET_DRHO_130), 130.0, 3.0)])
+def test_contact_angle_of_the_improved_virtual_density_wall(kw, theta, tol):
+    """A hemispherical drop of radius 30 on a scheme-1 wall (120 x 120 x 70, isothermal at
+    0.86 Tc, 20000 steps) settles at the angle its parameters were chosen for: about 90 degrees
+    for phi = 1, drho = 0 (rho_w = rho_ave, a neutral wall), 37 and 130 degrees for the two
+    values of the nucleate-boiling preset."""
+    from paper_2201_06039_gb300 import lbm
+    n, nz = 120, 70
+    s = W.LatticeSetup(n, n, nz, bc=(0, 0, 0, 0, 1, 1), sigma=W.SIGMA_STAR, thermal_off=1,
+                       T_wall_over_Tc=(0.86,) * 6, wall_scheme=1, **kw)
+    Tc = oracle.Tc_of(s)
+    rl, rv, _ = oracle.maxwell(s, 0.86 * Tc)
+    rho = W.droplet((nz, n, n), 30.0, 4.0, rl, rv, periodic=(True, True, False), center=(n / 2, n / 2, -0.5))
+    lat = lbm.Lattice(lbm.params_from_setup(s))
+    lat.init(rho.astype(np.float32), np.full(rho.shape, 0.86 * Tc, np.float32))
+    lat.step(20000)
+    r = lat.moments()["rho"].astype(np.float64)
+    lat.close()
+    th = _cap_angle(r, 0.5 * (rl + rv))
+    print("contact angle", kw, th)
+    assert abs(th - theta) < tol, (kw, th)
+
+
+def _segments(col, mid):
+    """(first, last) z of each run of vapour (rho < mid) along a column."""
+    v = col < mid
+    out, z = [], 0
+    while z < len(v):
+        if v[z]:
+            z0 = z
+            while z < len(v) and v[z]:
+                z += 1
+            out.append((z0, z - 1))
+        else:
+            z += 1
+    return out
+
+
+def test_nucleate_boiling_bubble_departs_from_the_hydrophobic_patch():
+    """Sec. IV.C on the paper's geometry (200 x 200 x 280, liquid up to z = 200, wall at 0.96 Tc,
+    hydrophobic 55 x 55 square at about 130 degrees, the rest at about 37 degrees, g = 1.5e-5,
+    chi = 0.08): vapour covers the patch and not the rest, the bubble on the patch grows, and
+    within 20000 steps it departs, a vapour region on the centre column with liquid below and
+    above it, while a residual bubble stays on the patch."""
+    from paper_2201_06039_gb300 import lbm
+    case = W.nucleate_boiling()
+    s = case["setup"]
+    Tc = oracle.Tc_of(s)
+    rl, rv, _ = oracle.maxwell(s, 0.86 * Tc)
+    rho, T, _ = W.build_fields(case, Tc, rl, rv)
+    mid = 0.5 * (rl + rv)
+    ys, xs = np.mgrid[0:s.ny, 0:s.nx]
+    patch = (np.abs(xs - 0.5 * s.nx) < s.wall_patch_half) & (np.abs(ys - 0.5 * s.ny) < s.wall_patch_half)
+    lat = lbm.Lattice(lbm.params_from_setup(s))
+    lat.init(rho.astype(np.float32), T.astype(np.float32))
+    heights, departed = {}, None
+    for k in range(1000, 20001, 1000):
+        lat.step(1000)
+        r = lat.moments()["rho"]
+        assert np.isfinite(r).all(), k
+        seg = _segments(r[:, s.ny // 2, s.nx // 2], mid)
+        print("step", k, "patch vapour", float((r[0][patch] < mid).mean()), "rest vapour",
+              float((r[0][~patch] < mid).mean()), "centre column", seg)
+        if k == 3000:
+            assert (r[0][patch] < mid).mean() > 0.9
+            assert (r[0][~patch] < mid).mean() < 0.1
+        if seg and seg[0][0] == 0:
+            heights[k] = seg[0][1]
+        if len(seg) >= 3 and seg[0][0] == 0 and seg[1][0] > seg[0][1] + 1 and seg[1][1] < seg[-1][0] - 1:
+            departed = k
+            break
+    lat.close()
+    assert heights.get(3000, 0) < heights.get(6000, 0) < heights.get(9000, 0), heights
+    assert departed is not None, heights
+    print("departure between steps", departed - 1000, "and", departed)

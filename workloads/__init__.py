@@ -213,8 +213,8 @@ def pool_boiling_downscaled() -> Dict:
 # a sessile-droplet sweep on this model (contact angle from the droplet's cap) to give about
 # 37 degrees (hydrophilic, phi) and 130 degrees (hydrophobic, drho), the two angles of the
 # nucleate boiling test (Sec. IV.C).
-WET_PHI_37 = 1.2
-WET_DRHO_130 = 1.0
+WET_PHI_37 = 1.40
+WET_DRHO_130 = 0.284
 
 
 def nucleate_boiling(nx: int = 200, ny: int = 200, nz: int = 280, liquid: float = 200.0,
