@@ -115,3 +115,87 @@ def test_nucleate_boiling_bubble_departs_from_the_hydrophobic_patch():
     assert heights.get(3000, 0) < heights.get(6000, 0) < heights.get(9000, 0), heights
     assert departed is not None, heights
     print("departure between steps", departed - 1000, "and", departed)
+
+
+def _wet_pool(scheme, nx=72, ny=40, nz=30):
+    case = W.pool_boiling(nx, ny, nz, height=12.0, hot_sigma=4.0)
+    s = case["setup"]
+    if scheme == 0:
+        Tc = oracle.Tc_of(s)
+        rl, rv, _ = oracle.maxwell(s, 0.86 * Tc)
+        wet = {"wall_rho": rv + 0.5 * (rl - rv), "wall_rho_patch": rv + 0.25 * (rl - rv)}
+    else:
+        wet = {"wall_scheme": 1, "wall_phi": 1.3, "wall_drho": 0.0, "wall_phi_patch": 1.0,
+               "wall_drho_patch": 0.25}
+    return dict(case, setup=W.LatticeSetup(**{**s.__dict__, **wet, "wall_patch_half": 6.5}))
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_wetting_variants_bit_identical(scheme):
+    """With a wetting wall (either scheme) the TMA kernel's kWet instantiation, the generic fused
+    kernel and the two-pass kernels give the same state bit for bit after 60 steps."""
+    from paper_2201_06039_gb300 import lbm
+    from tests._parity import inputs, run_gpu
+    case = _wet_pool(scheme)
+    s = case["setup"]
+    rho, T, u = inputs(case)
+    lat = lbm.Lattice(lbm.params_from_setup(s, kernel=2, use_tma=1))
+    assert lat.kernel == lbm.LBM_KERNEL_FUSED_TMA
+    lat.close()
+    tma, _ = run_gpu(s, rho, T, u, 60, kernel=2, use_tma=1)
+    gen, _ = run_gpu(s, rho, T, u, 60, kernel=2, use_tma=0)
+    two, _ = run_gpu(s, rho, T, u, 60, kernel=1)
+    for k in tma:
+        assert np.array_equal(tma[k], gen[k]), (scheme, k)
+        assert np.array_equal(tma[k], two[k]), (scheme, k)
+
+
+@pytest.mark.parametrize("storage", ["bf16", "fp16"])
+def test_wetting_with_16bit_storage(storage):
+    """Shifted 16-bit storage with a scheme-1 wetting wall runs the generic fused kernel (the
+    wetting TMA instantiation is FP32 only), agrees bit for bit with the two-pass kernels on the
+    same storage and stays within the 16-bit error budget of the FP64 oracle after 300 steps."""
+    from paper_2201_06039_gb300 import lbm
+    from tests._parity import inputs, rel_errors, run_gpu, run_oracle
+    case = _wet_pool(1)
+    s = case["setup"]
+    rho, T, u = inputs(case)
+    Tc = oracle.Tc_of(s)
+    over = dict(precision={"bf16": 1, "fp16": 2}[storage], rho_ref=float(np.mean(rho)), T_ref=0.86 * Tc)
+    lat = lbm.Lattice(lbm.params_from_setup(s, kernel=2, use_tma=1, **over))
+    assert lat.kernel == lbm.LBM_KERNEL_FUSED
+    lat.close()
+    gen, _ = run_gpu(s, rho, T, u, 300, kernel=2, use_tma=1, **over)
+    two, _ = run_gpu(s, rho, T, u, 300, kernel=1, **over)
+    for k in gen:
+        assert np.array_equal(gen[k], two[k]), (storage, k)
+    err = rel_errors(gen, run_oracle(s, rho, T, u, 300))
+    budget = {"bf16": dict(rho=5e-2, T=1e-1), "fp16": dict(rho=1e-2, T=3e-2)}[storage]
+    print(storage, "wetting wall, errors against the FP64 oracle", err)
+    for k, v in budget.items():
+        assert err[k] <= v, (storage, k, err)
+
+
+def test_checkpoint_resume_with_a_following_wetting_wall():
+    """A scheme-1 wall's virtual densities are rebuilt from the state every step, so a checkpoint
+    needs nothing more: save after 40 steps, load into a fresh context, 25 more steps, bit for
+    bit equal to the saving context."""
+    from paper_2201_06039_gb300 import lbm
+    from tests._parity import inputs
+    case = _wet_pool(1)
+    s = case["setup"]
+    rho, T, _ = inputs(case)
+    a = lbm.Lattice(lbm.params_from_setup(s))
+    a.init(rho.astype(np.float32), T.astype(np.float32))
+    a.step(40)
+    ck = a.save_state()
+    a.step(25)
+    want = a.moments()
+    a.close()
+    b = lbm.Lattice(lbm.params_from_setup(s))
+    b.load_state(ck)
+    b.step(25)
+    got = b.moments()
+    b.close()
+    for k in want:
+        assert np.array_equal(want[k], got[k]), k
