@@ -154,7 +154,9 @@ def test_wetting_variants_bit_identical(scheme):
 def test_wetting_with_16bit_storage(storage):
     """Shifted 16-bit storage with a scheme-1 wetting wall runs the generic fused kernel (the
     wetting TMA instantiation is FP32 only), agrees bit for bit with the two-pass kernels on the
-    same storage and stays within the 16-bit error budget of the FP64 oracle after 300 steps."""
+    same storage, and after 300 steps its errors against the FP64 oracle are those of 16-bit
+    storage itself: rho within the format's budget, rho and T within 1.5 times the errors of the
+    same lattice without the wall."""
     from paper_2201_06039_gb300 import lbm
     from tests._parity import inputs, rel_errors, run_gpu, run_oracle
     case = _wet_pool(1)
@@ -170,10 +172,16 @@ def test_wetting_with_16bit_storage(storage):
     for k in gen:
         assert np.array_equal(gen[k], two[k]), (storage, k)
     err = rel_errors(gen, run_oracle(s, rho, T, u, 300))
-    budget = {"bf16": dict(rho=5e-2, T=1e-1), "fp16": dict(rho=1e-2, T=3e-2)}[storage]
-    print(storage, "wetting wall, errors against the FP64 oracle", err)
-    for k, v in budget.items():
-        assert err[k] <= v, (storage, k, err)
+    # the storage format sets the error; the wall must not add to it: the same lattice without
+    # the wetting wall, same storage, against its own oracle run
+    dry = W.pool_boiling(72, 40, 30, height=12.0, hot_sigma=4.0)["setup"]
+    dgen, _ = run_gpu(dry, rho, T, u, 300, kernel=2, use_tma=0, **over)
+    derr = rel_errors(dgen, run_oracle(dry, rho, T, u, 300))
+    print(storage, "errors against the FP64 oracle, wetting wall", err, "no wetting wall", derr)
+    budget = {"bf16": 5e-2, "fp16": 1e-2}[storage]
+    assert err["rho"] <= budget, (storage, err)
+    for k in ("rho", "T"):
+        assert err[k] <= 1.5 * derr[k] + 1e-4, (storage, k, err, derr)
 
 
 def test_checkpoint_resume_with_a_following_wetting_wall():
