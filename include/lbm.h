@@ -185,6 +185,16 @@ size_t lbm_state_bytes(const lbm_ctx* ctx);
 int lbm_save_state(lbm_ctx* ctx, void* buf, size_t bytes);
 int lbm_load_state(lbm_ctx* ctx, const void* buf, size_t bytes);
 
+/* Wettability map of a scheme-1 wetting wall (wall_scheme 1, Sec. II.C): phi and drho of the
+ * solid node below every (x, y) of the -z wall, nx * ny floats each, x fastest, host or device
+ * memory (copied; the caller keeps ownership).  lbm_create fills the map from wall_phi /
+ * wall_drho and the patch values; this call replaces it for the steps that follow, e.g. to pin
+ * a contact line by a step in wettability around a drop's footprint.  The map is a parameter,
+ * not part of the state: checkpoints do not carry it.
+ * Errors: LBM_EINVAL (NULL ctx or array, a phi <= 0, a drho < 0 or a non-finite value: the map is
+ * then left unchanged), LBM_ESTATE (the context has no scheme-1 wall), LBM_ECUDA.  Synchronises. */
+int lbm_set_wall_map(lbm_ctx* ctx, const float* phi, const float* drho);
+
 /* Kernel variant the context runs (LBM_KERNEL_TWO_PASS, LBM_KERNEL_FUSED or
  * LBM_KERNEL_FUSED_TMA; AUTO resolved).  The first step after lbm_init_fields, and steps with a
  * frozen field, always run the generic fused kernel. */

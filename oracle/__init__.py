@@ -91,6 +91,7 @@ def _bind(L):
     L.orc_moments.argtypes = [C.c_void_p, dp, dp, dp, dp, dp]
     L.orc_get_pops.argtypes = [C.c_void_p, dp, dp]
     L.orc_set_pops.argtypes = [C.c_void_p, dp, dp]
+    L.orc_set_wall_map.argtypes = [C.c_void_p, dp, dp]
     L.orc_get_diag.argtypes = [C.c_void_p, dp, dp, dp, dp, dp, dp]
     L.orc_get_rho_ave.restype = C.c_double
     L.orc_get_rho_ave.argtypes = [C.c_void_p]
@@ -253,6 +254,14 @@ class Oracle:
         f = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)
         g = np.ascontiguousarray(g, dtype=np.float64).reshape(-1)
         self._L.orc_set_pops(self._h, _dp(f), _dp(g))
+
+    def set_wall_map(self, phi, drho):
+        """(phi, drho) of a scheme-1 wetting wall per (x, y), arrays of ny x nx."""
+        phi = np.ascontiguousarray(phi, dtype=np.float64).reshape(-1)
+        drho = np.ascontiguousarray(drho, dtype=np.float64).reshape(-1)
+        assert phi.size == drho.size == self.shape[1] * self.shape[2]
+        if self._L.orc_set_wall_map(self._h, _dp(phi), _dp(drho)) != 0:
+            raise ValueError("wall map: phi must be > 0 and drho >= 0")
 
     def diag(self):
         """div u (Eq. 48, or finite differences in divu_mode 1), grad T (Eq. 45), grad rho, F_m, phi_s,

@@ -105,6 +105,7 @@ typedef struct {
     real *phis_prev, *phis;
     real *divu, *gradT, *gradrho, *Fm;   /* diagnostics of the last step */
     real *uvec;                          /* u of every node (finite-difference div u) */
+    real *wphi, *wdrho;                  /* wall scheme 1: phi and drho per (x, y) of the -z wall */
     int first;
     double rho_ave;        /* value the next step uses (FP64 mean) */
     real M[Q19 * Q19], Minv[Q19 * Q19];
@@ -413,9 +414,34 @@ orc_state* orc_create(const orc_params* p) {
         return NULL;
     }
     if (fill_matrices(s)) return NULL;
+    /* wettability map of a scheme-1 wall: the patch values inside the square around
+       (nx/2, ny/2), the rest values elsewhere, until orc_set_wall_map replaces it */
+    s->wphi = (real*)malloc(sizeof(real) * p->nx * p->ny);
+    s->wdrho = (real*)malloc(sizeof(real) * p->nx * p->ny);
+    if (!s->wphi || !s->wdrho) return NULL;
+    for (int y = 0; y < p->ny; ++y)
+        for (int x = 0; x < p->nx; ++x) {
+            real dx = (real)x - 0.5 * p->nx, dy = (real)y - 0.5 * p->ny, h = p->wall_patch_half;
+            int in = h > 0.0 && fabs(dx) < h && fabs(dy) < h;
+            s->wphi[y * p->nx + x] = in ? p->wall_phi_patch : p->wall_phi;
+            s->wdrho[y * p->nx + x] = in ? p->wall_drho_patch : p->wall_drho;
+        }
     s->first = 1;
     s->ok = 1;
     return s;
+}
+
+/* replace the wettability map (nx * ny values each, x fastest); -1 and no change if a phi <= 0,
+   a drho < 0 or a value is not finite */
+int orc_set_wall_map(orc_state* s, const double* phi, const double* drho) {
+    long M = (long)s->p.nx * s->p.ny;
+    for (long i = 0; i < M; ++i)
+        if (!(phi[i] > 0.0) || !(drho[i] >= 0.0) || !isfinite(phi[i]) || !isfinite(drho[i])) return -1;
+    for (long i = 0; i < M; ++i) {
+        s->wphi[i] = (real)phi[i];
+        s->wdrho[i] = (real)drho[i];
+    }
+    return 0;
 }
 
 void orc_destroy(orc_state* s) {
@@ -423,6 +449,7 @@ void orc_destroy(orc_state* s) {
     free(s->f); free(s->fn); free(s->fs); free(s->g); free(s->gn); free(s->gp);
     free(s->rho); free(s->T); free(s->psi); free(s->phis_prev); free(s->phis);
     free(s->divu); free(s->uvec); free(s->gradT); free(s->gradrho); free(s->Fm);
+    free(s->wphi); free(s->wdrho);
     free(s);
 }
 
@@ -472,7 +499,8 @@ static int macroscopic(orc_state* s) {
 
 /* psi and rho of the solid node (x, y, -1) below a wetting -z wall, psi from Eqs. 8, 49 at
    T_w(x, y).  Scheme 0: the fixed virtual density (the patch value inside the square around
-   (nx/2, ny/2)).  Scheme 1 (the improved virtual-density scheme named in Sec. II.C):
+   (nx/2, ny/2)).  Scheme 1 (the improved virtual-density scheme named in Sec. II.C), with the
+   node's (phi, drho) from the wettability map:
    rho_w = phi rho_ave - drho, rho_ave = sum_a w_a rho(x_s + e_a) s(x_s + e_a) / sum_a w_a s(x_s + e_a)
    over the velocity set, s = 1 on fluid nodes and 0 on solid ones; floored at rho_ave / 10 so that
    psi_w stays real. */
@@ -493,7 +521,7 @@ static void wall_virtual(const orc_state* s, int x, int y, real* psi, real* rho)
             den += w;
         }
         real ra = num / den;
-        real phi = in ? p->wall_phi_patch : p->wall_phi, drho = in ? p->wall_drho_patch : p->wall_drho;
+        real phi = s->wphi[y * p->nx + x], drho = s->wdrho[y * p->nx + x];
         rw = phi * ra - drho;
         if (rw < 0.1 * ra) rw = 0.1 * ra;
     } else {

@@ -44,7 +44,7 @@ size_t pop_bytes(int precision) { return precision == LBM_FP32 ? 4 : 2; }
 namespace {
 
 struct Layout {
-    size_t pops[2], psirho, phis, sums, partial, counter, flag, vel, wall, total;
+    size_t pops[2], psirho, phis, sums, partial, counter, flag, vel, wall, wpar, wbad, total;
 };
 
 // Device memory of a context: two population buffers (26 slots of Ns elements: the padded,
@@ -63,6 +63,8 @@ Layout layout_of(const lbm_params* p, const DevParams& dp) {
     L.flag = take(sizeof(int));
     L.vel = take(p->divu_mode == 1 ? 16 * N : 0);
     L.wall = take(dp.wet ? 8 * (size_t)dp.nx * dp.ny : 0);
+    L.wpar = take(dp.wet && dp.wet_scheme == 1 ? 8 * (size_t)dp.nx * dp.ny : 0);
+    L.wbad = take(dp.wet && dp.wet_scheme == 1 ? sizeof(int) : 0);
     L.total = off;
     return L;
 }
@@ -553,8 +555,12 @@ int lbm_create(const lbm_params* p, lbm_ctx** out) {
     cudaError_t e = cudaMemsetAsync(c->base + c->L.sums, 0, c->L.flag + sizeof(int) - c->L.sums, c->stream);
     if (e == cudaSuccess && c->dp.wet) {   // scheme 0: the table is constant; scheme 1: refreshed every step
         c->dp.wall_tab = (const float2*)(c->base + c->L.wall);
-        if (c->dp.wet_scheme == 0)
+        if (c->dp.wet_scheme == 0) {
             e = launch_wall_table(c->dp, c->p.precision, nullptr, 0, (float2*)(c->base + c->L.wall), c->stream);
+        } else {   // the wettability map starts from the rest / patch parameters
+            c->dp.wall_par = (const float2*)(c->base + c->L.wpar);
+            e = launch_wall_params(c->dp, (float2*)(c->base + c->L.wpar), c->stream);
+        }
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
@@ -712,6 +718,34 @@ int lbm_save_state(lbm_ctx* c, void* buf, size_t bytes) {
     CK(cudaMemcpyAsync(out + h.pop_bytes, c->base + c->L.phis, (size_t)h.phis_bytes, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaMemcpyAsync(out + h.pop_bytes + h.phis_bytes, c->sums(c->slot), 2 * sizeof(double), cudaMemcpyDeviceToHost,
                        c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_set_wall_map(lbm_ctx* c, const float* phi, const float* drho) {
+    if (!c || !phi || !drho) return fail(LBM_EINVAL, "ctx, phi and drho are required");
+    if (!(c->dp.wet && c->dp.wet_scheme == 1)) return fail(LBM_ESTATE, "the context has no scheme-1 wetting wall");
+    const size_t M = (size_t)c->dp.nx * c->dp.ny;
+    // host inputs staged in the population buffer the next step overwrites anyway
+    float* stage = (float*)c->pbuf(c->cur ^ 1);
+    const float* dphi = phi;
+    const float* ddrho = drho;
+    if (!is_device_ptr(phi)) {
+        CK(cudaMemcpyAsync(stage, phi, M * 4, cudaMemcpyHostToDevice, c->stream));
+        dphi = stage;
+    }
+    if (!is_device_ptr(drho)) {
+        CK(cudaMemcpyAsync(stage + M, drho, M * 4, cudaMemcpyHostToDevice, c->stream));
+        ddrho = stage + M;
+    }
+    int* bad = (int*)(c->base + c->L.wbad);
+    int h = 0;
+    CK(cudaMemsetAsync(bad, 0, sizeof(int), c->stream));
+    CK(launch_wall_map(c->dp, dphi, ddrho, nullptr, bad, 0, c->stream));   // check every value first
+    CK(cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (h) return fail(LBM_EINVAL, "wall map: every phi must be > 0 and every drho >= 0 (finite)");
+    CK(launch_wall_map(c->dp, dphi, ddrho, (float2*)(c->base + c->L.wpar), bad, 1, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return LBM_OK;
 }

@@ -80,6 +80,7 @@ struct DevParams {
     float wet_rho, wet_rho_patch, wet_half, wet_cx, wet_cy;
     int wet_scheme;           // 0: fixed virtual densities; 1: phi rho_ave - drho from the fluid layer
     float wet_phi, wet_drho, wet_phi_p, wet_drho_p;
+    const float2* wall_par;   // scheme 1: (phi, drho) per (x, y), nx * ny, x fastest
     const float2* wall_tab;   // (psi, rho) of that layer per (x, y), nx * ny, x fastest (wet only)
     float shift_f[19];        // storage shift w_a rho_ref (16-bit storage only, else 0)
     float shift_g[7];         // storage shift w_a T_ref
@@ -327,21 +328,26 @@ __device__ __forceinline__ float psi_squared(const DevParams& P, float rho, floa
     return 2.f * (rho * (1.f / 3.f) - p);
 }
 
+// Is (x, y) of the -z wall inside the square patch |x - nx/2| < h, |y - ny/2| < h?
+__device__ __forceinline__ bool wall_in_patch(const DevParams& P, int x, int y) {
+    const float dx = (float)x - P.wet_cx, dy = (float)y - P.wet_cy;
+    return fabsf(dx) < P.wet_half && fabsf(dy) < P.wet_half;
+}
+
 // (psi, rho) of the solid node below (x, y) of the -z wall when it carries a virtual density
 // (wetting), psi from Eqs. 8, 49 at the wall temperature T_w(x, y).  Scheme 0: rho_w outside the
-// square patch, the patch value inside.  Scheme 1: phi rho_ave - drho with the region's (phi,
-// drho), floored at rho_ave / 10; rho_ave is the weighted mean density of the node's five fluid
-// neighbours.  k_wall_table evaluates it into P.wall_tab (once per context for scheme 0, at the
-// start of every step for scheme 1), which the stencils read (wall_entry).
+// square patch, the patch value inside.  Scheme 1: phi rho_ave - drho with the node's (phi, drho)
+// from the wettability map P.wall_par, floored at rho_ave / 10; rho_ave is the weighted mean
+// density of the node's five fluid neighbours.  k_wall_table evaluates it into P.wall_tab (once
+// per context for scheme 0, at the start of every step for scheme 1), which the stencils read
+// (wall_entry).
 __device__ __forceinline__ float2 wall_psirho(const DevParams& P, int x, int y, float rho_ave) {
-    const float dx = (float)x - P.wet_cx, dy = (float)y - P.wet_cy;
-    const bool in = fabsf(dx) < P.wet_half && fabsf(dy) < P.wet_half;
     float rw;
     if (P.wet_scheme == 1) {
-        const float phi = in ? P.wet_phi_p : P.wet_phi, drho = in ? P.wet_drho_p : P.wet_drho;
-        rw = fmaxf(__fsub_rn(__fmul_rn(phi, rho_ave), drho), __fmul_rn(0.1f, rho_ave));
+        const float2 pd = P.wall_par[(size_t)y * P.nx + x];
+        rw = fmaxf(__fsub_rn(__fmul_rn(pd.x, rho_ave), pd.y), __fmul_rn(0.1f, rho_ave));
     } else {
-        rw = in ? P.wet_rho_patch : P.wet_rho;
+        rw = wall_in_patch(P, x, y) ? P.wet_rho_patch : P.wet_rho;
     }
     return make_float2(psi_of(psi_squared(P, rw, wall_T(P, 4, x, y))), rw);
 }

@@ -340,6 +340,41 @@ __global__ void __launch_bounds__(128) k_wall_table(DevParams P, const S* __rest
     tab[(size_t)y * P.nx + x] = wall_psirho(P, x, y, rho_ave);
 }
 
+// Wettability map of a scheme-1 wall from the rest / patch parameters (phi, drho)
+__global__ void k_wall_params(DevParams P, float2* par) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const bool in = wall_in_patch(P, x, y);
+    par[(size_t)y * P.nx + x] = in ? make_float2(P.wet_phi_p, P.wet_drho_p) : make_float2(P.wet_phi, P.wet_drho);
+}
+
+// A user map (phi, drho as two planes of nx * ny) checked and interleaved: bad != 0 if any value
+// is out of range (phi <= 0, drho < 0, non-finite), in which case nothing is written (a first
+// pass only checks).
+__global__ void k_wall_map(DevParams P, const float* __restrict__ phi, const float* __restrict__ drho,
+                           float2* par, int* bad, int write) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const size_t i = (size_t)y * P.nx + x;
+    const float a = phi[i], b = drho[i];
+    if (!write) {
+        if (!(a > 0.f) || !(b >= 0.f) || !isfinite(a) || !isfinite(b)) atomicOr(bad, 1);
+    } else {
+        par[i] = make_float2(a, b);
+    }
+}
+
+cudaError_t launch_wall_params(const DevParams& P, float2* par, cudaStream_t s) {
+    k_wall_params<<<dim3((P.nx + 127) / 128, P.ny), 128, 0, s>>>(P, par);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wall_map(const DevParams& P, const float* phi, const float* drho, float2* par, int* bad,
+                            int write, cudaStream_t s) {
+    k_wall_map<<<dim3((P.nx + 127) / 128, P.ny), 128, 0, s>>>(P, phi, drho, par, bad, write);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_wall_table(const DevParams& P, int precision, const void* fs, int pull_f, float2* tab,
                               cudaStream_t s) {
     const dim3 grid((P.nx + 127) / 128, P.ny);

@@ -32,6 +32,9 @@ cudaError_t launch_psi(const DevParams& P, int precision, const StateBufs& B, do
 
 // stream-collide pass of the two-pass variant.
 // u = (sum e f + F/2) / rho of every node into B.vel (finite-difference div u)
+cudaError_t launch_wall_params(const DevParams& P, float2* par, cudaStream_t s);
+cudaError_t launch_wall_map(const DevParams& P, const float* phi, const float* drho, float2* par, int* bad,
+                            int write, cudaStream_t s);
 cudaError_t launch_wall_table(const DevParams& P, int precision, const void* fs, int pull_f, float2* tab,
                               cudaStream_t s);
 cudaError_t launch_velocity(const DevParams& P, int precision, const StateBufs& B, const double* sums_cur,

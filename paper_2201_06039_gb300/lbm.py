@@ -52,7 +52,7 @@ EXPORTS = ["lbm_params_default", "lbm_eos_critical", "lbm_workspace_bytes", "lbm
            "lbm_init_fields", "lbm_step", "lbm_get_moments", "lbm_get_totals", "lbm_steps_done",
            "lbm_kernel_in_use",
            "lbm_step_profiled", "lbm_destroy", "lbm_status_str", "lbm_last_error", "lbm_field_sum_noalloc",
-           "lbm_state_bytes", "lbm_save_state", "lbm_load_state",
+           "lbm_state_bytes", "lbm_save_state", "lbm_load_state", "lbm_set_wall_map",
            "lbm_batch_create", "lbm_batch_nodes", "lbm_batch_init_fields", "lbm_batch_step", "lbm_batch_autotune",
            "lbm_batch_plan", "lbm_batch_select_plan", "lbm_batch_get_moments", "lbm_batch_get_totals",
            "lbm_batch_steps_done", "lbm_batch_destroy"]
@@ -98,6 +98,7 @@ def lib(build_if_missing: bool = True):
     L.lbm_state_bytes.restype = C.c_size_t
     L.lbm_save_state.argtypes = [vp, vp, C.c_size_t]
     L.lbm_load_state.argtypes = [vp, vp, C.c_size_t]
+    L.lbm_set_wall_map.argtypes = [vp, vp, vp]
     L.lbm_kernel_in_use.argtypes = [vp]
     L.lbm_step_profiled.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_int)]
     L.lbm_destroy.argtypes = [vp]
@@ -205,6 +206,11 @@ def lbm_save_state(ctx) -> np.ndarray:
 def lbm_load_state(ctx, buf: np.ndarray):
     buf = np.ascontiguousarray(buf, dtype=np.uint8)
     _check(lib().lbm_load_state(ctx, buf.ctypes.data, buf.nbytes), "lbm_load_state")
+
+
+def lbm_set_wall_map(ctx, phi, drho):
+    """(phi, drho) of a scheme-1 wetting wall per (x, y): float32 arrays of ny x nx (numpy or torch)."""
+    _check(lib().lbm_set_wall_map(ctx, _ptr(phi), _ptr(drho)), "lbm_set_wall_map")
 
 
 def lbm_kernel_in_use(ctx) -> int:
@@ -385,6 +391,11 @@ class Lattice:
 
     def load_state(self, buf: np.ndarray):
         lbm_load_state(self.ctx, buf)
+
+    def set_wall_map(self, phi, drho):
+        def f32(a):
+            return np.ascontiguousarray(a, dtype=np.float32) if isinstance(a, np.ndarray) else a
+        lbm_set_wall_map(self.ctx, f32(phi), f32(drho))
 
 
 class Batch:

@@ -120,6 +120,11 @@ def test_wetting_scheme1_parameters_checked(kw):
     assert ei.value.status == G.LBM_EINVAL
 
 
+def test_set_wall_map_needs_a_context():
+    lib = G.lib()
+    assert lib.lbm_set_wall_map(None, None, None) == G.LBM_EINVAL
+
+
 def test_batch_has_no_wetting_wall():
     q = G.lbm_params_default()
     q.bc[4] = q.bc[5] = G.LBM_BC_WALL

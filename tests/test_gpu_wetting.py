@@ -207,3 +207,85 @@ def test_checkpoint_resume_with_a_following_wetting_wall():
     b.close()
     for k in want:
         assert np.array_equal(want[k], got[k]), k
+
+
+def _map_for(s, seed):
+    """A wettability map with a hydrophobic square, a hydrophilic ring around it and random
+    values elsewhere (phi in [1, 1.4] or drho in [0, 0.3])."""
+    ny, nx = s.ny, s.nx
+    ys, xs = np.mgrid[0:ny, 0:nx]
+    r = np.maximum(np.abs(xs - nx / 2), np.abs(ys - ny / 2))
+    phi = np.where(r < 4, 1.0, np.where(r < 8, 1.4, 1.0 + 0.4 * W.uniform(seed, nx * ny).reshape(ny, nx)))
+    drho = np.where(r < 4, 0.3, np.where(r < 8, 0.0, 0.3 * W.uniform(seed + 1, nx * ny).reshape(ny, nx)))
+    return phi, drho
+
+
+@pytest.mark.parametrize("variant", ["two_pass", "fused", "fused_tma"])
+def test_parity_wettability_map(variant):
+    """A per-node wettability map set through lbm_set_wall_map, on the small pool, against the
+    oracle with the same map (bar: the FP32 build of the oracle with the map, times 4)."""
+    from paper_2201_06039_gb300 import lbm
+    from tests._parity import bars, inputs, rel_errors
+    over = {"two_pass": dict(kernel=1), "fused": dict(kernel=2, use_tma=0),
+            "fused_tma": dict(kernel=2, use_tma=1)}[variant]
+    case = W.pool_boiling(40, 36, 48, height=16.0, hot_sigma=4.0)
+    s = W.LatticeSetup(**{**case["setup"].__dict__, "wall_scheme": 1, "wall_phi": 1.0})
+    case = dict(case, setup=s)
+    rho, T, u = inputs(case)
+    phi, drho = _map_for(s, 91)
+    steps = 400
+
+    def orc(precision):
+        o = oracle.Oracle(s, precision=precision)
+        o.init(rho, T, u)
+        o.set_wall_map(phi, drho)
+        o.step(steps)
+        m = o.moments()
+        o.close()
+        return m
+
+    ref = orc("f64")
+    floor = rel_errors(orc("f32"), ref)
+    lat = lbm.Lattice(lbm.params_from_setup(s, **over))
+    lat.init(rho.astype(np.float32), T.astype(np.float32))
+    lat.set_wall_map(phi.astype(np.float32), drho.astype(np.float32))
+    lat.step(steps)
+    gpu = lat.moments()
+    lat.close()
+    err = rel_errors(gpu, ref)
+    bar = bars(floor)
+    print("wettability map", variant, "gpu", err, "fp32 floor", floor)
+    for k, v in err.items():
+        assert v <= bar[k], (k, v, bar[k])
+
+
+def test_wall_map_errors_leave_the_map_unchanged():
+    """lbm_set_wall_map: LBM_ESTATE without a scheme-1 wall; LBM_EINVAL for a phi <= 0, a negative
+    drho or a NaN, after which the steps are those of a context that never made the call."""
+    from paper_2201_06039_gb300 import lbm
+    from tests._parity import inputs
+    case = _wet_pool(0)
+    lat = lbm.Lattice(lbm.params_from_setup(case["setup"]))
+    ny, nx = case["setup"].ny, case["setup"].nx
+    with pytest.raises(lbm.LbmError) as ei:
+        lat.set_wall_map(np.ones((ny, nx), np.float32), np.zeros((ny, nx), np.float32))
+    assert ei.value.status == lbm.LBM_ESTATE
+    lat.close()
+    case = _wet_pool(1)
+    s = case["setup"]
+    rho, T, _ = inputs(case)
+    runs = []
+    for bad in (None, "phi", "drho", "nan"):
+        lat = lbm.Lattice(lbm.params_from_setup(s))
+        lat.init(rho.astype(np.float32), T.astype(np.float32))
+        if bad:
+            phi, drho = np.full((ny, nx), 1.2, np.float32), np.full((ny, nx), 0.1, np.float32)
+            {"phi": phi, "drho": drho, "nan": phi}[bad][3, 5] = np.nan if bad == "nan" else -0.5
+            with pytest.raises(lbm.LbmError) as ei:
+                lat.set_wall_map(phi, drho)
+            assert ei.value.status == lbm.LBM_EINVAL
+        lat.step(20)
+        runs.append(lat.moments()["rho"])
+        lat.close()
+    for r in runs[1:]:
+        assert np.array_equal(runs[0], r)

@@ -455,14 +455,16 @@ def test_wetting_wall_virtual_density_closed_form():
     assert np.max(np.abs(d["gradrho"][1:-1])) < 1e-14
 
 
-def test_wetting_scheme1_neighbour_average_bruteforce():
+@pytest.mark.parametrize("use_map", [False, True])
+def test_wetting_scheme1_neighbour_average_bruteforce(use_map):
     """Wall scheme 1 (the improved virtual-density scheme): on a random density layer z = 0 over
     a uniform bulk, the oracle's grad rho and F_m in that layer equal a brute-force sum over the
     velocity set of Eq. 2 in which each solid node (x, y, -1) carries
     rho_w = max(phi rho_ave - drho, rho_ave / 10), rho_ave the weight-averaged density of its
     fluid neighbours (the directions with e_z = +1), phi and drho of the patch inside the square
     |x - nx/2| < h, |y - ny/2| < h, and psi_w from Eq. 8 at the wall temperature.  The patch's
-    drho is large enough that part of it sits on the floor."""
+    drho is large enough that part of it sits on the floor.  With use_map, a random wettability
+    map (phi in [1, 1.4], drho in [0, 3] per node) replaces the rest / patch values."""
     nx, ny, nz = 10, 9, 6
     s = W.LatticeSetup(nx, ny, nz, bc=(0, 0, 0, 0, 1, 1), sigma=0.11, flow_off=1,
                        T_wall_over_Tc=(0.86, 0.86, 0.86, 0.86, 0.93, 0.86),
@@ -474,6 +476,10 @@ def test_wetting_scheme1_neighbour_average_bruteforce():
     rho[0] = W.uniform(77, nx * ny, 0.5, 6.0).reshape(ny, nx)
     o = oracle.Oracle(s)
     o.init(rho, np.full(s.shape, T_f))
+    if use_map:
+        mphi = W.uniform(78, nx * ny, 1.0, 1.4).reshape(ny, nx)
+        mdrho = W.uniform(79, nx * ny, 0.0, 3.0).reshape(ny, nx)
+        o.set_wall_map(mphi, mdrho)
     o.step(1)
     d = o.diag()
     psi = lambda r, t: math.sqrt(2.0 * (r / 3.0 - oracle.p_eos(s, r, t)))
@@ -488,6 +494,8 @@ def test_wetting_scheme1_neighbour_average_bruteforce():
         ra = num / den
         inside = abs(xs - nx / 2) < 2.5 and abs(ys - ny / 2) < 2.5
         phi, drho = (1.0, 2.5) if inside else (1.15, 0.0)
+        if use_map:
+            phi, drho = mphi[ys, xs], mdrho[ys, xs]
         return max(phi * ra - drho, 0.1 * ra)
 
     for y in range(ny):
@@ -510,10 +518,30 @@ def test_wetting_scheme1_neighbour_average_bruteforce():
     floored = 0
     for ys in range(ny):
         for xs in range(nx):
-            if abs(xs - nx / 2) < 2.5 and abs(ys - ny / 2) < 2.5:
-                ra = sum(w(e) * rho[0, (ys + e[1]) % ny, (xs + e[0]) % nx] for e in E19[1:] if e[2] == 1) / 0.5
+            ra = sum(w(e) * rho[0, (ys + e[1]) % ny, (xs + e[0]) % nx] for e in E19[1:] if e[2] == 1) / 0.5
+            if use_map:
+                floored += mphi[ys, xs] * ra - mdrho[ys, xs] < 0.1 * ra
+            elif abs(xs - nx / 2) < 2.5 and abs(ys - ny / 2) < 2.5:
                 floored += ra - 2.5 < 0.1 * ra
-    assert 0 < floored < 25
+    assert 0 < floored < (nx * ny if use_map else 25)
+
+
+def test_wall_map_rejects_bad_values_and_keeps_the_old_map():
+    s = W.LatticeSetup(6, 5, 4, bc=(0, 0, 0, 0, 1, 1), sigma=0.11, wall_scheme=1, wall_phi=1.1)
+    Tc = oracle.Tc_of(s)
+    runs = []
+    for bad in (None, "phi", "drho"):
+        o = oracle.Oracle(s)
+        o.init(np.full(s.shape, 0.6), np.full(s.shape, 0.86 * Tc))
+        if bad:
+            phi, drho = np.full((5, 6), 1.2), np.full((5, 6), 0.1)
+            (phi if bad == "phi" else drho)[2, 3] = -0.5
+            with pytest.raises(ValueError):
+                o.set_wall_map(phi, drho)
+        o.step(3)
+        runs.append(o.moments()["rho"])
+        o.close()
+    assert np.array_equal(runs[0], runs[1]) and np.array_equal(runs[0], runs[2])
 
 
 def test_local_gradT_matches_finite_difference():

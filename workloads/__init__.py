@@ -234,6 +234,23 @@ def nucleate_boiling(nx: int = 200, ny: int = 200, nz: int = 280, liquid: float 
                 W=W, Tr_liquid=0.86)
 
 
+def heated_surface_droplet(nx: int = 200, ny: int = 200, nz: int = 100, R0: float = 30.0,
+                           W: float = 4.0) -> Dict:
+    """Droplet evaporation on a heated surface (Sec. IV.B): a hemispherical drop of radius 30 at
+    the centre of a bottom wall at 0.87 Tc (contact angle about 88 degrees: a scheme-1 wall with
+    phi = 1, drho = 0.005), open top held at T_sat = 0.86 Tc, periodic x and y, no gravity,
+    chi = 0.02, and the EOS constant and sigma* of the droplet tests (a = 1/49).  The paper runs
+    the first 10^4 steps without the thermal model (thermal_off); the contact-line pinning of
+    its hysteresis window is set by the caller through the wettability map."""
+    s = LatticeSetup(nx, ny, nz, bc=(BC_PERIODIC, BC_PERIODIC, BC_PERIODIC, BC_PERIODIC,
+                                     BC_WALL, BC_OUTFLOW),
+                     T_wall_over_Tc=(0.86, 0.86, 0.86, 0.86, 0.87, 0.86), hot_dT_over_Tc=0.0,
+                     a=1.0 / 49.0, sigma=SIGMA_STAR_A1_49, lambda_mode=0, chi_or_lambda=0.02,
+                     gravity=(0.0, 0.0, 0.0), wall_scheme=1, wall_phi=1.0, wall_drho=0.005)
+    return dict(name=f"heated_surface_droplet_{nx}x{ny}x{nz}", setup=s, kind="sessile", R0=R0,
+                W=W, Tr_drop=0.86, Tr_gas=0.86)
+
+
 def batch_instances(count: int = 256, seed: int = MASTER_SEED) -> List[Dict]:
     """Ensemble of periodic droplets (even i) and flat slabs (odd i) of uneven size.
 
@@ -278,6 +295,11 @@ def build_fields(case: Dict, Tc: float, rho_l: float, rho_v: float,
             T = np.where(r <= case["R0"], case["Tr_drop"] * Tc, case["Tr_gas"] * Tc)
     elif kind == "slab":
         rho = slab(shape, case["R0"], case["W"], rho_l, rho_v, axis=2)
+        T = np.full(shape, case["Tr_drop"] * Tc)
+    elif kind == "sessile":   # hemisphere on the -z wall (the wall plane is z = -1/2)
+        nz, ny, nx = shape
+        rho = droplet(shape, case["R0"], case["W"], rho_l, rho_v, periodic=periodic,
+                      center=(nx / 2.0, ny / 2.0, -0.5))
         T = np.full(shape, case["Tr_drop"] * Tc)
     elif kind == "pool":
         rho = pool(shape, case["height"], case["W"], rho_l, rho_v)
