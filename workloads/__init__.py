@@ -241,14 +241,17 @@ def heated_surface_droplet(nx: int = 200, ny: int = 200, nz: int = 100, R0: floa
     phi = 1, drho = 0.005), open top held at T_sat = 0.86 Tc, periodic x and y, no gravity,
     chi = 0.02, and the EOS constant and sigma* of the droplet tests (a = 1/49).  The paper runs
     the first 10^4 steps without the thermal model (thermal_off); the contact-line pinning of
-    its hysteresis window is set by the caller through the wettability map."""
+    its hysteresis window is set by the caller through the wettability map.  The vapour starts at
+    0.42 rather than the flat-interface coexistence density 0.38: the drop's Laplace pressure
+    holds its vapour above saturation, and a vapour started at 0.38 takes the whole drop up in
+    this 4M-node box while it settles."""
     s = LatticeSetup(nx, ny, nz, bc=(BC_PERIODIC, BC_PERIODIC, BC_PERIODIC, BC_PERIODIC,
                                      BC_WALL, BC_OUTFLOW),
                      T_wall_over_Tc=(0.86, 0.86, 0.86, 0.86, 0.87, 0.86), hot_dT_over_Tc=0.0,
                      a=1.0 / 49.0, sigma=SIGMA_STAR_A1_49, lambda_mode=0, chi_or_lambda=0.02,
                      gravity=(0.0, 0.0, 0.0), wall_scheme=1, wall_phi=1.0, wall_drho=0.005)
     return dict(name=f"heated_surface_droplet_{nx}x{ny}x{nz}", setup=s, kind="sessile", R0=R0,
-                W=W, Tr_drop=0.86, Tr_gas=0.86)
+                W=W, Tr_drop=0.86, Tr_gas=0.86, rho_gas=0.42)
 
 
 def batch_instances(count: int = 256, seed: int = MASTER_SEED) -> List[Dict]:
@@ -298,7 +301,7 @@ def build_fields(case: Dict, Tc: float, rho_l: float, rho_v: float,
         T = np.full(shape, case["Tr_drop"] * Tc)
     elif kind == "sessile":   # hemisphere on the -z wall (the wall plane is z = -1/2)
         nz, ny, nx = shape
-        rho = droplet(shape, case["R0"], case["W"], rho_l, rho_v, periodic=periodic,
+        rho = droplet(shape, case["R0"], case["W"], rho_l, case.get("rho_gas", rho_v), periodic=periodic,
                       center=(nx / 2.0, ny / 2.0, -0.5))
         T = np.full(shape, case["Tr_drop"] * Tc)
     elif kind == "pool":
