@@ -37,7 +37,13 @@
  *  - rho_ave used at step t is the FP64 mean of rho at step t-1 (at step 0 the
  *    initial mean).
  *  - Solid / outflow neighbours of the psi and grad-rho stencils take the value of
- *    their fluid mirror image across the face (neutral wetting).
+ *    their fluid mirror image across the face (neutral wetting), unless the -z wall
+ *    carries a virtual density (wall_virtual): a fixed one per region (scheme 0), or the
+ *    improved virtual-density scheme Sec. II.C names, rho_w = phi rho_ave - drho from the
+ *    solid node's fluid neighbours with (phi, drho) from a per-node wettability map
+ *    (scheme 1; floored at rho_ave / 10, our addition).
+ *  - Options outside the default path: BGK D3Q7 collision (thermal_bgk), isotropic
+ *    finite-difference div u away from solid faces (divu_mode 1).
  *  - Outflow face: f unknowns copied from the layer inside (zero gradient), g by
  *    Eq. 51 with T fixed at the face temperature.
  *  - Bottom-face hot spot: T_w(x,y) = T_wall[-z] + dT exp(-((x-nx/2)^2+(y-ny/2)^2)/(2 s^2)).
