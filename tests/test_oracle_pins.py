@@ -526,6 +526,40 @@ def test_wetting_scheme1_neighbour_average_bruteforce(use_map):
     assert 0 < floored < (nx * ny if use_map else 25)
 
 
+@pytest.mark.parametrize("phi,drho,kind", [(1.0, 0.0, "neutral"), (1.3, 0.0, "wets"), (1.0, 0.2, "recedes")])
+def test_wetting_scheme1_contact_line_of_a_standing_slab(phi, drho, kind):
+    """A liquid slab standing on the wall with vertical interfaces (48 x 2 x 24, isothermal,
+    3000 steps): with phi = 1, drho = 0 (rho_w equal to the neighbours' mean: the neutral wall
+    the scheme is built around) the interfaces stay vertical, within a node over 12 layers
+    (about 90 degrees); phi > 1 pulls the liquid out along the wall (hydrophilic) and drho > 0
+    pulls it back (hydrophobic)."""
+    s = W.LatticeSetup(48, 2, 24, bc=(0, 0, 0, 0, 1, 1), sigma=W.SIGMA_STAR, thermal_off=1,
+                       wall_scheme=1, wall_phi=phi, wall_drho=drho)
+    Tc = oracle.Tc_of(s)
+    rl, rv, _ = oracle.maxwell(s, 0.86 * Tc)
+    mid = 0.5 * (rl + rv)
+    x = np.arange(48)[None, None, :] * np.ones(s.shape)
+    rho = W.tanh_profile(np.abs(x - 23.5), 12.0, 4.0, rl, rv)
+    o = oracle.Oracle(s)
+    o.init(rho, np.full(s.shape, 0.86 * Tc))
+    o.step(3000)
+    r = o.moments()["rho"]
+    o.close()
+
+    def edge(z):   # right-hand interface position in layer z
+        row = r[z, 0, 24:]
+        j = int(np.nonzero(row < mid)[0][0])
+        return 24 + j - 1 + (row[j - 1] - mid) / (row[j - 1] - row[j])
+
+    spread = edge(0) - edge(12)
+    if kind == "neutral":
+        assert abs(spread) < 1.0, spread
+    elif kind == "wets":
+        assert spread > 3.0, spread
+    else:
+        assert spread < -2.0, spread
+
+
 def test_wall_map_rejects_bad_values_and_keeps_the_old_map():
     s = W.LatticeSetup(6, 5, 4, bc=(0, 0, 0, 0, 1, 1), sigma=0.11, wall_scheme=1, wall_phi=1.1)
     Tc = oracle.Tc_of(s)
