@@ -118,7 +118,7 @@ typedef struct {
                                      55 nodes is half = 27.5); half 0 = no patch */
     int wall_scheme;              /* wetting of the -z wall: 0 = the fixed virtual densities above;
                                      1 = densities that follow the fluid (the improved virtual-density
-                                     scheme the paper uses, Sec. II.C): every step the solid node
+                                     scheme the paper uses, Sec. III.C): every step the solid node
                                      below (x, y) takes rho_w = max(phi rho_ave - drho, rho_ave / 10),
                                      rho_ave the weighted mean (w = 1/6 face, 1/12 edge) of the
                                      densities of its five fluid neighbours in the layer z = 0;
@@ -185,7 +185,7 @@ size_t lbm_state_bytes(const lbm_ctx* ctx);
 int lbm_save_state(lbm_ctx* ctx, void* buf, size_t bytes);
 int lbm_load_state(lbm_ctx* ctx, const void* buf, size_t bytes);
 
-/* Wettability map of a scheme-1 wetting wall (wall_scheme 1, Sec. II.C): phi and drho of the
+/* Wettability map of a scheme-1 wetting wall (wall_scheme 1, Sec. III.C): phi and drho of the
  * solid node below every (x, y) of the -z wall, nx * ny floats each, x fastest, host or device
  * memory (copied; the caller keeps ownership).  lbm_create fills the map from wall_phi /
  * wall_drho and the patch values; this call replaces it for the steps that follow, e.g. to pin

@@ -39,7 +39,7 @@
  *  - Solid / outflow neighbours of the psi and grad-rho stencils take the value of
  *    their fluid mirror image across the face (neutral wetting), unless the -z wall
  *    carries a virtual density (wall_virtual): a fixed one per region (scheme 0), or the
- *    improved virtual-density scheme Sec. II.C names, rho_w = phi rho_ave - drho from the
+ *    improved virtual-density scheme Sec. III.C names, rho_w = phi rho_ave - drho from the
  *    solid node's fluid neighbours with (phi, drho) from a per-node wettability map
  *    (scheme 1; floored at rho_ave / 10, our addition).
  *  - Options outside the default path: BGK D3Q7 collision (thermal_bgk), isotropic
@@ -505,7 +505,7 @@ static int macroscopic(orc_state* s) {
 
 /* psi and rho of the solid node (x, y, -1) below a wetting -z wall, psi from Eqs. 8, 49 at
    T_w(x, y).  Scheme 0: the fixed virtual density (the patch value inside the square around
-   (nx/2, ny/2)).  Scheme 1 (the improved virtual-density scheme named in Sec. II.C), with the
+   (nx/2, ny/2)).  Scheme 1 (the improved virtual-density scheme named in Sec. III.C), with the
    node's (phi, drho) from the wettability map:
    rho_w = phi rho_ave - drho, rho_ave = sum_a w_a rho(x_s + e_a) s(x_s + e_a) / sum_a w_a s(x_s + e_a)
    over the velocity set, s = 1 on fluid nodes and 0 on solid ones; floored at rho_ave / 10 so that
