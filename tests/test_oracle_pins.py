@@ -526,6 +526,27 @@ def test_wetting_scheme1_neighbour_average_bruteforce(use_map):
     assert 0 < floored < (nx * ny if use_map else 25)
 
 
+def test_wetting_scheme1_neutral_wall_on_a_uniform_liquid_exerts_no_force():
+    """phi = 1, drho = 0 on a uniform liquid at the wall temperature: rho_w = rho_ave = rho_f,
+    psi_w = psi_f, so the bottom layer feels no F_m and no density gradient, as far from the
+    wall; with drho > 0 it feels F_m,z = psi_f (psi_f - psi_w) / 2 with psi_w at rho_f - drho."""
+    for drho in (0.0, 0.7):
+        s = W.LatticeSetup(7, 6, 5, bc=(0, 0, 0, 0, 1, 1), sigma=0.11, flow_off=1,
+                           wall_scheme=1, wall_phi=1.0, wall_drho=drho)
+        Tc = oracle.Tc_of(s)
+        rho_f, T = 5.9, 0.86 * Tc
+        o = oracle.Oracle(s)
+        o.init(np.full(s.shape, rho_f), np.full(s.shape, T))
+        o.step(1)
+        d = o.diag()
+        o.close()
+        psi = lambda r: math.sqrt(2.0 * (r / 3.0 - oracle.p_eos(s, r, T)))
+        want = 0.5 * psi(rho_f) * (psi(rho_f) - psi(rho_f - drho))
+        assert np.max(np.abs(d["Fm"][0, :, :, 2] - want)) < 1e-13
+        assert np.max(np.abs(d["gradrho"][0, :, :, 2] - 0.5 * drho)) < 1e-13
+        assert np.max(np.abs(d["Fm"][0, :, :, :2])) < 1e-14 and np.max(np.abs(d["Fm"][1:-1])) < 1e-14
+
+
 @pytest.mark.parametrize("phi,drho,kind", [(1.0, 0.0, "neutral"), (1.3, 0.0, "wets"), (1.0, 0.2, "recedes")])
 def test_wetting_scheme1_contact_line_of_a_standing_slab(phi, drho, kind):
     """A liquid slab standing on the wall with vertical interfaces (48 x 2 x 24, isothermal,
