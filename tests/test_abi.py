@@ -120,6 +120,21 @@ def test_wetting_scheme1_parameters_checked(kw):
     assert ei.value.status == G.LBM_EINVAL
 
 
+def test_setup_fields_reach_both_parameter_structs():
+    """Every wetting and option field of a LatticeSetup arrives unchanged in lbm_params and in the
+    oracle's parameter struct (the two sides map the record independently)."""
+    import oracle
+    import workloads as W
+    kw = dict(wall_rho=0.0, wall_scheme=1, wall_phi=1.23, wall_drho=0.045, wall_phi_patch=1.01,
+              wall_drho_patch=0.287, wall_patch_half=27.5, thermal_bgk=1, divu_mode=1)
+    s = W.LatticeSetup(20, 18, 16, bc=(0, 0, 0, 0, 1, 2), **kw)
+    p = G.params_from_setup(s)
+    q = oracle.params_from_setup(s)
+    for k, v in kw.items():
+        assert getattr(p, k) == v and getattr(q, k) == v, k
+    assert list(p.bc) == list(s.bc) and list(q.bc) == list(s.bc)
+
+
 def test_set_wall_map_needs_a_context():
     lib = G.lib()
     assert lib.lbm_set_wall_map(None, None, None) == G.LBM_EINVAL
