@@ -73,3 +73,12 @@ def test_heated_surface_droplet_preset_is_the_papers_geometry():
     row = rho[0, 100, 100:]
     x = int(np.nonzero(row < mid)[0][0])
     assert 29 <= x <= 31
+
+
+def test_cpu_baseline_sample_of_the_wetting_workloads():
+    """bench.py's CPU-baseline leg runs the oracle on a z-slab of the nucleate-boiling and the
+    heated-surface workloads (wetting wall, patch, open top) and reports a positive rate."""
+    import bench
+    for case in (W.nucleate_boiling(), W.heated_surface_droplet()):
+        out = bench.cpu_baseline_run(case, steps=1, warm=0)
+        assert out["value"] > 0 and out["kind"] == "oracle", case["name"]
