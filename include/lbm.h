@@ -84,7 +84,7 @@ typedef struct {
     double g[3];                  /* gravity of the buoyancy force F_b = (rho - rho_b) g */
     double rho_buoy;              /* rho_b: > 0 fixes it; 0 takes the domain mean rho_ave of the
                                      previous step (Sec. IV.C) */
-    int flow_off;                 /* 1: f frozen, u = 0, phi_s = 0 (pure conduction) */
+    int flow_off;                 /* 1: f frozen, a static fluid: u = 0 and div u = 0 in Eq. 18, which keeps its conduction term chi grad(rho cV).grad T/(rho cV) */
     int thermal_off;              /* 1: g frozen (isothermal phase) */
     int precision;                /* lbm_precision of the stored populations */
     double rho_ref, T_ref;        /* shifts of 16-bit storage: f - w rho_ref, g - w T_ref */

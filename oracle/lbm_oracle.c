@@ -85,7 +85,7 @@ typedef struct {
     int lambda_mode;         /* 0: constant chi, 1: constant lambda */
     double chi_or_lambda;
     double g[3];
-    int flow_off;            /* f frozen, u = 0, phi_s = 0 (pure conduction) */
+    int flow_off;            /* f frozen: a static fluid (u = 0, div u = 0; Eq. 18 keeps its conduction term) */
     int thermal_off;         /* g frozen (isothermal) */
     double rho_buoy;         /* > 0: fixed reference density of the buoyancy force, else rho_ave */
     int thermal_bgk;         /* 1: single-relaxation-time (BGK) D3Q7 collision: every non-conserved
@@ -696,15 +696,15 @@ static int step_once(orc_state* s) {
                 real vsT = chi / csT2 + 0.5;     /* chi = (varsigma_T - 0.5) cs_T^2 dt */
                 real gT[3];
                 for (int k = 0; k < 3; ++k) gT[k] = -(nm[1 + k] - 0.0) / (vsT * csT2);   /* Eq. 45 */
-                /* Eq. 18 with cV constant: grad(rho cV)/(rho cV) = grad rho / rho */
-                real phis = 0.0;
-                if (!p->flow_off) {
-                    for (int k = 0; k < 3; ++k) phis += (chi * grho[k] / rho - u[k]) * gT[k];
-                    phis -= T / (rho * p->cV) * dpdT(p, rho) * divu;
-                } else {
+                /* Eq. 18 with cV constant: grad(rho cV)/(rho cV) = grad rho / rho.  A frozen flow is
+                   a static fluid: u = 0 and div u = 0, and only the conduction term remains */
+                if (p->flow_off) {
                     u[0] = u[1] = u[2] = 0.0;
                     divu = 0.0;
                 }
+                real phis = 0.0;
+                for (int k = 0; k < 3; ++k) phis += (chi * grho[k] / rho - u[k]) * gT[k];
+                phis -= T / (rho * p->cV) * dpdT(p, rho) * divu;
                 real phis_old = s->first ? phis : s->phis_prev[i];
                 /* Eq. 42 equilibrium moments and Eq. 43 rates */
                 real neq[Q7] = {T, 0.0, 0.0, 0.0, 3.0 * csT2 * T, 0.0, 0.0};

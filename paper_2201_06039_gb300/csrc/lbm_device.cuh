@@ -537,12 +537,15 @@ __device__ __forceinline__ float collide_g(const DevParams& P, float g[7], float
     float inv_vsT = __fdividef(1.f, vsT);
     float k = -inv_vsT * P.inv_csT2;                 // Eq. 45
     float gTx = k * n1, gTy = k * n2, gTz = k * n3;
-    float phis = 0.f;
+    float phis;
     if (!P.flow_off) {
         phis = __fmaf_rn(chi * grz * inv_rho - o.uz, gTz,
                          __fmaf_rn(chi * gry * inv_rho - o.uy, gTy, __fmul_rn(chi * grx * inv_rho - o.ux, gTx)));
         // T/(rho cV) (dp/dT)_rho div u with (dp/dT)_rho ~ rho R / (1 - b rho)
         phis -= __fdividef(T * P.R_over_cV, 1.f - P.b * rho) * o.divu;
+    } else {
+        // frozen flow: a static fluid (u = 0, div u = 0); the conduction term of Eq. 18 remains
+        phis = __fmaf_rn(chi * grz * inv_rho, gTz, __fmaf_rn(chi * gry * inv_rho, gTy, __fmul_rn(chi * grx * inv_rho, gTx)));
     }
     float C = first ? phis : phis_prev;
     float qs = __fmaf_rn(-0.5f, C, __fmul_rn(1.5f, phis));   // Q_a = w_a (3/2 phi_s(t) - 1/2 phi_s(t-1))

@@ -133,7 +133,7 @@ class LatticeSetup:
     lambda_mode: int = 0          # 0: constant chi, 1: constant lambda
     chi_or_lambda: float = 0.08
     gravity: Tuple[float, float, float] = (0.0, 0.0, 0.0)
-    flow_off: int = 0             # f frozen (pure conduction checks)
+    flow_off: int = 0             # f frozen: a static fluid (u = 0, div u = 0; conduction only)
     thermal_off: int = 0          # g frozen (isothermal phase)
     rho_buoy: float = 0.0         # > 0: fixed reference density of the buoyancy force (else rho_ave)
     thermal_bgk: int = 0          # 1: BGK D3Q7 collision (one rate 1/varsigma_T) instead of MRT
