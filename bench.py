@@ -449,6 +449,7 @@ def compare_16bit(lbm, case, rho, T, stream, steps):
         p.T_ref = 0.86 * lbm.lbm_eos_critical(p)[0]
         lat = lbm.Lattice(p, stream=stream)
         lat.init(torch.from_numpy(rho).cuda(), torch.from_numpy(T).cuda())
+        lat.autotune(steps=20)
         lat.step(10)
         lat.step(steps)
         torch.cuda.synchronize()
@@ -497,6 +498,7 @@ def run_mine(args):
 
     # ---- device-resident timing
     lat.init(torch.from_numpy(rho).cuda(), torch.from_numpy(T).cuda())
+    tuned = lat.autotune(steps=20) if lat.kernel == lbm.LBM_KERNEL_FUSED_TMA else None   # plan by timing
     lat.step(args.warmup)
     lat.step(args.steps)            # captures the K-step graph outside the timed region
     torch.cuda.synchronize()
@@ -555,6 +557,8 @@ def run_mine(args):
         "dtype": "f32" if args.precision == "fp32" else f"f32 compute, {args.precision} storage",
         "data": "synthetic",
         "config": {"workload": case["name"], "nodes": N, "kernel": kernel_name, "precision": args.precision,
+                   "plan": None if tuned is None else {"tile": list(lbm.lbm_plan_shapes()[tuned["shape"]]),
+                                                       "zchunk": tuned["zchunk"]},
                    "l2": "no flush: working set %.2f GB > 129 MB L2" % (lbm.lbm_workspace_bytes(p) / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "hbm_gbs_step": bpn * N * args.steps / (ms * 1e-3) / 1e9,

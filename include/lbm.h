@@ -200,6 +200,30 @@ int lbm_set_wall_map(lbm_ctx* ctx, const float* phi, const float* drho);
  * frozen field, always run the generic fused kernel. */
 int lbm_kernel_in_use(const lbm_ctx* ctx);
 
+/* Tile plan of the TMA kernel (the default path on lattices with f-periodic x and y faces).  A
+ * persistent CTA per SM marches tiles of tile_w x tile_h nodes up z; the lattice is cut into
+ * items (tile, z-chunk of zchunk planes) taken round robin by the CTAs.  The plan is chosen at
+ * lbm_create from a model of the kernel's cost; these calls report, pin or measure it.  Plans do
+ * not change results: every plan computes the same state bit for bit.
+ *   lbm_plan_shapes  number of tile shapes, and each one's tile_w / tile_h (arrays of max ints;
+ *                    either may be NULL)
+ *   lbm_get_plan     the plan in use: shape index, z-chunk, items, persistent CTAs (each
+ *                    nullable); shape -1 if the context does not run the TMA kernel
+ *   lbm_select_plan  pin a shape (-1: the model's choice) and a z-chunk (0: the model's choice
+ *                    for that shape); drops the captured step graphs.  LBM_EINVAL if the plan
+ *                    does not fit (the previous plan is kept), LBM_ESTATE if the context does not
+ *                    run the TMA kernel
+ *   lbm_autotune     time `steps` steps of every shape (with its modelled z-chunk and with whole
+ *                    columns) on the current state, keep the fastest and restore the state
+ *                    exactly; best_ms (nullable) receives its time per step.  Takes the pending
+ *                    first step after lbm_init_fields first.  Needs free device memory for one
+ *                    copy of the state (LBM_ENOMEM otherwise).  Synchronises.
+ * No counterpart in the paper: this is the build's scheduling of the update (Secs. II-III). */
+int lbm_plan_shapes(int* tile_w, int* tile_h, int max);
+int lbm_get_plan(const lbm_ctx* ctx, int* shape, int* zchunk, int* items, int* ctas);
+int lbm_select_plan(lbm_ctx* ctx, int shape, int zchunk);
+int lbm_autotune(lbm_ctx* ctx, int steps, double* best_ms);
+
 /* Enqueue n steps outside any graph and accumulate, per kernel kind, the device time
  * measured with CUDA events on the context's stream and the number of launches
  * (kernel_ms[0]: psi/EOS or fused kernel, [1]: stream-collide kernel, [2]: ghost-cell

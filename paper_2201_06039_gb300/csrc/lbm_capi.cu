@@ -93,6 +93,7 @@ struct lbm_ctx {
     long long steps;
     int variant;   // LBM_KERNEL_TWO_PASS or LBM_KERNEL_FUSED
     TmaMaps maps;
+    int plan_shape, plan_zchunk;   // TMA plan pinned by lbm_select_plan (-1 / 0: automatic)
     GraphEntry graphs[kGraphCache];
     int n_graphs;
     unsigned long long use_clock;
@@ -404,9 +405,9 @@ bool make_tma_maps(lbm_ctx* c) {
     if (cudaGetDevice(&dev) != cudaSuccess) return false;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
-    int shape, zchunk, items;
-    tma_plan_for(c->dp, sms, &shape, &zchunk, &items);
-    if ((size_t)optin < tma_smem_bytes(shape, c->p.precision)) return false;
+    int shape = -1, zchunk = 0, items = 0;
+    tma_plan_for(c->dp, sms, c->plan_shape, c->plan_zchunk, &shape, &zchunk, &items);
+    if (shape < 0 || (size_t)optin < tma_smem_bytes(shape, c->p.precision)) return false;
     if (items > max_partials(c->dp)) return false;
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -551,6 +552,8 @@ int lbm_create(const lbm_params* p, lbm_ctx** out) {
         free(c);
         return fail(LBM_EINVAL, "fused kernel does not support this lattice");
     }
+    c->plan_shape = -1;
+    c->plan_zchunk = 0;
     if (c->variant == LBM_KERNEL_FUSED && p->use_tma != 0) make_tma_maps(c);
     cudaError_t e = cudaMemsetAsync(c->base + c->L.sums, 0, c->L.flag + sizeof(int) - c->L.sums, c->stream);
     if (e == cudaSuccess && c->dp.wet) {   // scheme 0: the table is constant; scheme 1: refreshed every step
@@ -776,6 +779,131 @@ int lbm_load_state(lbm_ctx* c, const void* buf, size_t bytes) {
     c->steps = h.steps;
     c->initialised = true;
     return LBM_OK;
+}
+
+int lbm_plan_shapes(int* tile_w, int* tile_h, int max) {
+    const int n = tma_num_shapes();
+    for (int k = 0; k < n && k < max; ++k) {
+        if (tile_w) tile_w[k] = tma_tile_w(k);
+        if (tile_h) tile_h[k] = tma_tile_h(k);
+    }
+    return n;
+}
+
+int lbm_get_plan(const lbm_ctx* c, int* shape, int* zchunk, int* items, int* ctas) {
+    if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+    const bool ok = c->maps.ok;
+    if (shape) *shape = ok ? c->maps.shape : -1;
+    if (zchunk) *zchunk = ok ? c->maps.zchunk : 0;
+    if (items) *items = ok ? c->maps.items : 0;
+    if (ctas) *ctas = ok ? (c->maps.sms < c->maps.items ? c->maps.sms : c->maps.items) : 0;
+    return LBM_OK;
+}
+
+int lbm_select_plan(lbm_ctx* c, int shape, int zchunk) {
+    if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+    if (shape < -1 || shape >= tma_num_shapes() || zchunk < 0)
+        return fail(LBM_EINVAL, "no tile shape %d (0..%d, -1 automatic) or z-chunk %d < 0", shape,
+                    tma_num_shapes() - 1, zchunk);
+    if (c->variant != LBM_KERNEL_FUSED || c->p.use_tma == 0 || !tma_eligible(c->dp, c->p.precision))
+        return fail(LBM_ESTATE, "the context does not run the TMA kernel");
+    const int s0 = c->plan_shape, z0 = c->plan_zchunk;
+    c->plan_shape = shape;
+    c->plan_zchunk = zchunk;
+    drop_graphs(c);   // the graphs captured the old plan's launches
+    if (!make_tma_maps(c)) {
+        c->plan_shape = s0;
+        c->plan_zchunk = z0;
+        make_tma_maps(c);
+        return fail(LBM_EINVAL, "plan (shape %d, z-chunk %d) does not fit this lattice and GPU", shape, zchunk);
+    }
+    return LBM_OK;
+}
+
+int lbm_autotune(lbm_ctx* c, int steps, double* best_ms) {
+    if (!c) return fail(LBM_EINVAL, "ctx is NULL");
+    if (!c->initialised) return fail(LBM_ESTATE, "lbm_autotune before lbm_init_fields");
+    if (steps < 1) return fail(LBM_EINVAL, "steps must be >= 1");
+    if (c->variant != LBM_KERNEL_FUSED || c->p.use_tma == 0 || !c->maps.ok)
+        return fail(LBM_ESTATE, "the context does not run the TMA kernel");
+    // the first step after lbm_init_fields runs the generic kernel: take it before timing
+    int rc = LBM_OK;
+    while (rc == LBM_OK && (c->first || c->fresh_f || c->fresh_g)) rc = enqueue_step(c);
+    if (rc) return rc;
+    const size_t popb = (size_t)kSlots * c->dp.Ns * pop_bytes(c->p.precision), phib = 4 * (size_t)c->dp.N;
+    const size_t sumb = 8 * sizeof(double);
+    char* save = nullptr;
+    cudaError_t e = cudaMalloc((void**)&save, popb + phib + sumb);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LBM_ENOMEM, "autotune state copy: %s", cudaGetErrorString(e));
+    }
+    const int c0 = c->cur, sl0 = c->slot;
+    const long long st0 = c->steps;
+    const int s_keep = c->plan_shape, z_keep = c->plan_zchunk;
+    auto save_or_restore = [&](bool restore) -> cudaError_t {
+        char* a[3] = {(char*)c->pbuf(c0), c->base + c->L.phis, c->base + c->L.sums};
+        char* b[3] = {save, save + popb, save + popb + phib};
+        size_t n[3] = {popb, phib, sumb};
+        for (int k = 0; k < 3; ++k) {
+            cudaError_t r = cudaMemcpyAsync(restore ? a[k] : b[k], restore ? b[k] : a[k], n[k],
+                                            cudaMemcpyDeviceToDevice, c->stream);
+            if (r != cudaSuccess) return r;
+        }
+        return cudaSuccess;
+    };
+    cudaEvent_t ev[2];
+    cudaEventCreate(&ev[0]);
+    cudaEventCreate(&ev[1]);
+    int sms = c->maps.sms;
+    float best_t = -1.f;
+    int best_shape = -1, best_zc = 0;
+    e = save_or_restore(false);
+    if (e != cudaSuccess) rc = fail(LBM_ECUDA, "autotune save: %s", cudaGetErrorString(e));
+    // candidates: every tile shape with its modelled best z-chunk, and the whole column
+    for (int sh = 0; sh < tma_num_shapes() && rc == LBM_OK; ++sh) {
+        int shape = -1, zc_model = 0, items = 0;
+        tma_plan_for(c->dp, sms, sh, 0, &shape, &zc_model, &items);
+        const int zcs[2] = {zc_model, c->dp.nz};
+        for (int q = 0; q < 2 && rc == LBM_OK; ++q) {
+            if (q == 1 && zcs[1] == zcs[0]) continue;
+            c->plan_shape = sh;
+            c->plan_zchunk = zcs[q];
+            drop_graphs(c);
+            if (!make_tma_maps(c)) continue;   // does not fit this GPU
+            rc = enqueue_step(c);   // warm-up
+            cudaEventRecord(ev[0], c->stream);
+            for (int k = 0; k < steps && rc == LBM_OK; ++k) rc = enqueue_step(c);
+            cudaEventRecord(ev[1], c->stream);
+            if (cudaEventSynchronize(ev[1]) != cudaSuccess) rc = fail(LBM_ECUDA, "autotune timing failed");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[0], ev[1]);
+            if (rc == LBM_OK && (best_t < 0.f || ms < best_t)) {
+                best_t = ms;
+                best_shape = sh;
+                best_zc = zcs[q];
+            }
+            e = save_or_restore(true);
+            if (e != cudaSuccess && rc == LBM_OK) rc = fail(LBM_ECUDA, "autotune restore: %s", cudaGetErrorString(e));
+            c->cur = c0;
+            c->slot = sl0;
+            c->steps = st0;
+        }
+    }
+    cudaStreamSynchronize(c->stream);
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    cudaFree(save);
+    c->plan_shape = rc == LBM_OK && best_shape >= 0 ? best_shape : s_keep;
+    c->plan_zchunk = rc == LBM_OK && best_shape >= 0 ? best_zc : z_keep;
+    drop_graphs(c);
+    make_tma_maps(c);
+    if (rc == LBM_OK) {
+        CK(cudaMemsetAsync(c->base + c->L.flag, 0, sizeof(int), c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        if (best_ms) *best_ms = best_t / steps;
+    }
+    return rc;
 }
 
 int lbm_kernel_in_use(const lbm_ctx* c) {

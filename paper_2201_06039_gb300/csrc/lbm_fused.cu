@@ -347,7 +347,8 @@ k_fused_batch(DevParams P, const BatchInst* __restrict__ insts, const BatchItem*
 }
 
 // ================================================================ TMA producer / consumer kernel
-// Tile TX x TY; consumer threads: tile slots (row-major), then the halo ring, then idle lanes.
+// Tile TX x TY.  Warps: producer, storer (FP32 only), compute warps (one tile node per thread:
+// pull, psi, collision), one halo warp (psi of the one-node ring around the tile).
 constexpr size_t align128(size_t v) { return (v + 127) / 128 * 128; }
 
 template <int TX_, int TY_, typename S_ = float> struct TmaShape {
@@ -356,21 +357,22 @@ template <int TX_, int TY_, typename S_ = float> struct TmaShape {
     static constexpr int kInterior = TX_ * TY_;
     static constexpr int kHaloNodes = 2 * (TX_ + 2) + 2 * TY_;
     static constexpr int kSlotsAll = kInterior + kHaloNodes;        // ring slots with a psi value
-    static constexpr int kPsiWarps = 6;                              // psi pass: slots round robin
-    static constexpr int kColWarps = (kInterior + 31) / 32;          // collision: one node per thread
-    static constexpr int kPsiThreads = kPsiWarps * 32, kColThreads = kColWarps * 32;
-    static constexpr int kPsiPerThread = (kSlotsAll + kPsiThreads - 1) / kPsiThreads;
+    static constexpr int kCompWarps = (kInterior + 31) / 32;         // one tile node per thread
+    static constexpr int kHaloWarps = 1;
+    static constexpr int kHaloPerLane = (kHaloNodes + 31) / 32;      // halo slots of one halo lane
+    static constexpr int kCompThreads = kCompWarps * 32, kHaloThreads = kHaloWarps * 32;
     // Output path.  FP32: the collided plane goes to an output tile in shared memory and leaves by
-    // TMA tensor stores issued by a storer warp.  16-bit storage: every collision thread stores its
+    // TMA tensor stores issued by a storer warp.  16-bit storage: every compute thread stores its
     // populations straight to global memory (no output tile, no storer warp), which frees shared
-    // memory for the L1 cache and measured faster for 2-byte elements.
+    // memory for the L1 cache.
     static constexpr bool kDirect = kE == 2;
     static constexpr int kLeadWarps = kDirect ? 1 : 2;              // producer (+ storer) warps first
-    static constexpr int kThreads = 32 * kLeadWarps + kPsiThreads + kColThreads;
-    // registers per thread: the SM's 64K for one CTA, whose warps are allocated in groups of four
-    // (threads rounded up to 128) and whose per-thread count goes in steps of 8
-    static constexpr int kAllocThreads = (kThreads + 127) / 128 * 128;
-    static constexpr int kMaxRegs = (65536 / kAllocThreads) / 8 * 8 > 255 ? 255 : (65536 / kAllocThreads) / 8 * 8;
+    static constexpr int kThreads = 32 * kLeadWarps + kCompThreads + kHaloThreads;
+    // registers per thread: warp w runs on SM sub-partition w % 4, whose register file holds 16K
+    // registers; the per-thread count goes in steps of 8
+    static constexpr int kWarpsPerSub = (kThreads / 32 + 3) / 4;
+    static constexpr int kMaxRegs = (16384 / (32 * kWarpsPerSub)) / 8 * 8 > 255 ? 255
+                                  : (16384 / (32 * kWarpsPerSub)) / 8 * 8;
     static constexpr int kRingW = TX_ + 2, kRingPlane = (TX_ + 2) * (TY_ + 2);
     // a window row starts kXOff columns left of the tile, on a 16-byte boundary
     static constexpr int kXOff = 16 / kE;
@@ -382,7 +384,20 @@ template <int TX_, int TY_, typename S_ = float> struct TmaShape {
     static constexpr size_t kGrp1 = align128((size_t)14 * kWin * kE);
     static constexpr size_t kGrp2 = kGrp1 + align128((size_t)6 * kWin * kE);
     static constexpr size_t kStageOne = kGrp2 + align128((size_t)6 * kWin * kE);
-    static constexpr int kStages = kE == 4 ? 3 : 5, kRing = 4;
+    // ring of (psi, rho) planes: planes z-1, z, z+1 of the collision and the plane pulled ahead
+    // (the halo warp writes the next item's first planes only once every warp has passed the
+    // stage barrier of that item, so four planes also cover the item boundaries)
+    static constexpr int kRing = 4;
+    // as many stages as fit in one CTA's 227 KB beside the other buffers (at most 3 for FP32, 4 for
+    // 16-bit storage; at least 2)
+    static constexpr size_t kFixed = (kDirect ? 0 : align128((size_t)kSlots * kInterior * kE) +
+                                      align128((size_t)TY_ * kSlots * (16 / kE) * kE) +
+                                      align128((size_t)2 * kSlots * TX_ * kE) +
+                                      align128((size_t)2 * kSlots * (16 / kE) * kE)) +
+                                     (size_t)kRing * (TX_ + 2) * (TY_ + 2) * sizeof(float2) + 2048;
+    static constexpr int kStagesFit = (int)((227 * 1024 - kFixed) / kStageOne);
+    static constexpr int kStages = kStagesFit > (kE == 4 ? 3 : 4) ? (kE == 4 ? 3 : 4) : kStagesFit;
+    static_assert(kStages >= 2, "two stages of the tile's window fit in shared memory");
     static constexpr int kPrefetch = 2;                 // planes between an L2 prefetch and its load
     static constexpr size_t kStageBytes = (size_t)kStages * kStageOne;
     // collided plane, row-major [TY][26][TX]: source of one TMA tensor store per plane (a box of
@@ -397,13 +412,18 @@ template <int TX_, int TY_, typename S_ = float> struct TmaShape {
     static constexpr size_t kGCorBytes = align128((size_t)2 * kSlots * kGW * kE);
     static constexpr size_t kGhostBytes = kGColBytes + kGRowBytes + kGCorBytes;
     static constexpr size_t kRingOff = kStageBytes + (kDirect ? 0 : kOutBytes + kGhostBytes);
-    static constexpr size_t kSmem = kRingOff + (size_t)kRing * kRingPlane * (sizeof(float2) + sizeof(float));
+    static constexpr size_t kSmem = kRingOff + (size_t)kRing * kRingPlane * sizeof(float2);
     // element offset of storage slot s inside a stage
     static constexpr __host__ __device__ int slot_off(int s) {
         return s < 14 ? s * kWin : s < 20 ? (int)(kGrp1 / kE) + (s - 14) * kWin : (int)(kGrp2 / kE) + (s - 20) * kWin;
     }
-    static_assert(kPsiPerThread <= 3, "psi threads hold at most three ring slots");
-    static_assert(TX_ % 8 == 0, "tile origins on 16-byte boundaries for 2-byte storage");
+    // thread counts of the named barriers (see k_fused_tma)
+    static constexpr int kCntRing = kCompThreads + kHaloThreads;
+    static constexpr int kCntEmpty = kCompThreads + kHaloThreads + 32;
+    static constexpr int kCntOut = kCompThreads + 32;
+    static_assert(TX_ % 8 == 0 || kE == 4, "tile origins on 16-byte boundaries for 2-byte storage");
+    static_assert(TX_ % 4 == 0, "tile origins on 16-byte boundaries");
+    static_assert(kSmem <= 227 * 1024, "shared memory of one CTA");
 };
 
 // ring slot (lx, ly) of slot index q: tile nodes (row-major), then the halo ring
@@ -567,16 +587,31 @@ __device__ __forceinline__ void stage_pulls(const DevParams& P, const typename S
         g[4] = -st_dec<S>(b[Sh::slot_off(gslot(3))], P.shift_g[3]) + 2.f * P.w1 * wall_T(P, 3, mx, my);
 }
 
-// Warp roles: warp 0 = producer (TMA loads), warp 1 = storer (TMA stores; FP32 only), the next
-// kPsiWarps = psi pass, the rest = collision.  Every hand-off goes through an mbarrier:
-//   full[s]      TMA bytes of the stage landed              (producer  -> psi, collision)
-//   empty[s]     psi pass and collision done with a stage    (psi, collision -> producer)
-//   ring_full[r] (psi, rho) of a plane in ring slot r ready   (psi       -> collision)
-//   ring_empty[r] last collision reading ring slot r done     (collision -> psi)
-//   out_full     collided plane written to the out buffer    (collision -> storer; FP32)
-//   out_empty    tensor store has read the out buffer         (storer    -> collision; FP32)
-// Stage uses and ring uses follow one plane counter k across the CTA's items; out-buffer uses
-// follow the collided-plane counter u.
+// named barriers of the TMA kernel (bar.sync / bar.arrive; 0 is __syncthreads): the waiting
+// warps block in hardware and issue nothing while they wait
+constexpr int kBarRing = 1, kBarComp = 2, kBarOutFull = 3, kBarOutEmpty = 4, kBarEmpty0 = 5;
+__device__ __forceinline__ void nb_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+__device__ __forceinline__ void nb_arrive(int id, int nthreads) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Warp roles: warp 0 = producer (TMA loads), warp 1 = storer (TMA stores; FP32 only), then the
+// compute warps (thread t owns tile node t: it pulls the node's 26 populations once, writes the
+// node's (psi, rho) into the ring, keeps the populations in registers and collides the node one
+// plane later), then one halo warp (psi of the ring around the tile, kHaloPerLane slots a lane).
+// Hand-offs:
+//   full[s]    mbarrier: the TMA bytes of stage s landed (producer -> compute, halo; bounded waits)
+//   EMPTY s    named, bar.sync by producer, compute and halo: the stage's pulls are done and it
+//              may be refilled (the producer waits for use k before loading use k + kStages)
+//   RING       named, bar.sync by compute and halo once per collided plane z: psi of z + 1 is in
+//   OUT_FULL   named, compute bar.arrive -> storer bar.sync: the out tile holds plane z (FP32)
+//   OUT_EMPTY  named, storer bar.arrive -> compute bar.sync: the tensor store has read it (FP32)
+// Stage uses and ring planes follow one plane counter k across the CTA's items.  Every role runs
+// the same sequence of named-barrier operations whatever happens: an abort (a TMA wait that ran
+// out) skips only the mbarrier waits, the copies and the work, so no barrier is left incomplete,
+// and since both sides of EMPTY wait, no role runs ahead of the others into a later barrier use.
 template <int TX_, int TY_, typename S, bool kWet>
 __global__ void __maxnreg__((TmaShape<TX_, TY_, S>::kMaxRegs))
 k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ CUtensorMap map6,
@@ -588,8 +623,8 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
             const double* __restrict__ sums_cur, double2* partial, unsigned* counter, double* sums_next,
             float* __restrict__ phis, int* flag, int first, int zchunk, int tiles_x, int tiles_y, int n_items) {
     using Sh = TmaShape<TX_, TY_, S>;
-    constexpr int kWinW = Sh::kWinW, kStages = Sh::kStages, kRing = Sh::kRing;
-    constexpr int kCol = Sh::kColThreads, kPrefetch = Sh::kPrefetch, kGW = Sh::kGW;
+    constexpr int kWinW = Sh::kWinW, kStages = Sh::kStages, kRing = Sh::kRing, kRP = Sh::kRingPlane;
+    constexpr int kComp = Sh::kCompThreads, kPrefetch = Sh::kPrefetch, kGW = Sh::kGW;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // stage s: smem_raw + s * kStageOne (three slot groups of [slots][TY+4][TX+2 kXOff])
     S* out = reinterpret_cast<S*>(smem_raw + Sh::kStageBytes);                   // [TY][26][TX]
@@ -597,203 +632,149 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
     S* grow = reinterpret_cast<S*>(smem_raw + Sh::kStageBytes + Sh::kOutBytes + Sh::kGColBytes);  // [2][26][w]
     S* gcor = reinterpret_cast<S*>(smem_raw + Sh::kStageBytes + Sh::kOutBytes + Sh::kGColBytes +
                                    Sh::kGRowBytes);                              // [2][26][kGW]
-    float2* ring = reinterpret_cast<float2*>(smem_raw + Sh::kRingOff);           // [4][TY+2][TX+2]
-    float* tring = reinterpret_cast<float*>(ring + kRing * Sh::kRingPlane);      // [4][TY+2][TX+2] T
-    __shared__ __align__(8) unsigned long long full_bar[kStages], empty_bar[kStages], ring_full[kRing],
-        ring_empty[kRing], out_full, out_empty;
-    __shared__ double red_a[kCol / 32], red_b[kCol / 32];
+    float2* ring = reinterpret_cast<float2*>(smem_raw + Sh::kRingOff);           // [kRing][TY+2][TX+2]
+    __shared__ __align__(8) unsigned long long full_bar[kStages], stall_bar;
+    __shared__ double red_a[kComp / 32], red_b[kComp / 32];
     __shared__ int is_last;
     __shared__ volatile int abort_flag;
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(&full_bar[s], 1);
-            mbar_init(&empty_bar[s], Sh::kPsiWarps + Sh::kColWarps);
-        }
-        for (int r = 0; r < kRing; ++r) {
-            mbar_init(&ring_full[r], Sh::kPsiWarps);
-            mbar_init(&ring_empty[r], Sh::kColWarps);
-        }
-        mbar_init(&out_full, Sh::kColWarps);
-        mbar_init(&out_empty, 1);
+        for (int s = 0; s < kStages; ++s) mbar_init(&full_bar[s], 1);
+        mbar_init(&stall_bar, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     const int ntiles = tiles_x * tiles_y;
-    // bounded wait that turns a timeout into an error flag and stops all further waiting
-    auto wait = [&](unsigned long long* bar, unsigned parity) {
+    // bounded wait for the bytes of a stage use: a timeout raises the abort flag, after which no
+    // role waits for a copy again
+    auto wait_full = [&](int s, unsigned parity) {
         if (abort_flag) return;
-        if (!mbar_wait(bar, parity)) {
+        if (!mbar_wait(&full_bar[s], parity)) {
             abort_flag = 1;
             atomicOr(flag, 2);
         }
     };
+    auto stage_of = [&](int s) { return reinterpret_cast<const S*>(smem_raw + (size_t)s * Sh::kStageOne); };
 
     if (warp == 0) {
-        // ------------------------------------------------------------ producer (one lane)
-        if (lane == 0) {
-            unsigned k = 0;
-            for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-                const int chunk = item / ntiles, tile = item % ntiles;
-                const int x0 = (tile % tiles_x) * TX_, y0 = (tile / tiles_x) * TY_;
-                const int z0 = chunk * zchunk, z1 = min(P.nz, z0 + zchunk);
-                for (int p = z0 - 1; p <= z1; ++p, ++k) {
-                    const int s = k % kStages;
-                    // a stage is free once the previous use's phase of its empty barrier completed;
-                    // the timeout-path test (test_stall) waits on the first use's own phase instead,
-                    // which nothing can complete before this load: the bounded wait runs out
-                    if (k >= (unsigned)kStages || P.test_stall)
-                        wait(&empty_bar[s], k >= (unsigned)kStages ? (k / kStages - 1) & 1 : 0u);
-                    if (abort_flag) {   // release the waiters without data
-                        mbar_arrive(&full_bar[s]);
-                        continue;
-                    }
-                    const int mz = map_coord(p, P.nz, P.bc[4], P.bc[5]);
-                    const int zu = src_plane_up(P, mz), zd = src_plane_dn(P, mz);
-                    const unsigned bytes =
-                        (14u + (zu >= 0 ? 6u : 0u) + (zd >= 0 ? 6u : 0u)) * (unsigned)(Sh::kWin * Sh::kE);
-                    unsigned char* st = smem_raw + (size_t)s * Sh::kStageOne;
-                    mbar_expect_tx(&full_bar[s], bytes);
-                    // window origin in storage coordinates: (x0 - kXOff) + kGX, (y0 - 2) + kGY
-                    const int cx = x0 - Sh::kXOff + kGX, cy = y0;
-                    tma_load_4d(st, &map14, cx, cy, mz, 0, &full_bar[s]);
-                    if (zu >= 0) tma_load_4d(st + Sh::kGrp1, &map6, cx, cy, zu, 14, &full_bar[s]);
-                    if (zd >= 0) tma_load_4d(st + Sh::kGrp2, &map6, cx, cy, zd, 20, &full_bar[s]);
-                    // pull the window of a plane kPrefetch ahead into L2, so that its load into a
-                    // stage (issued once a stage frees) waits on L2 rather than on DRAM
-                    const int pf = p + kPrefetch;
-                    if (pf <= z1) {
-                        const int fz = map_coord(pf, P.nz, P.bc[4], P.bc[5]);
-                        const int fu = src_plane_up(P, fz), fd = src_plane_dn(P, fz);
-                        tma_prefetch_4d(&map14, cx, cy, fz, 0);
-                        if (fu >= 0) tma_prefetch_4d(&map6, cx, cy, fu, 14);
-                        if (fd >= 0) tma_prefetch_4d(&map6, cx, cy, fd, 20);
-                    }
-                }
-            }
-            // copies still in flight must land before the CTA exits (bounded)
-            for (unsigned q = (k > (unsigned)kStages ? k - kStages : 0u); q < k; ++q)
-                mbar_wait(&full_bar[q % kStages], (q / kStages) & 1);
-        }
-        __syncwarp();
-    } else if (!Sh::kDirect && warp == 1) {
-        // ------------------------------------------------------------ storer (one lane)
-        if (lane == 0) {
-            unsigned u = 0;
-            for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-                const int chunk = item / ntiles, tile = item % ntiles;
-                const int x0 = (tile % tiles_x) * TX_, y0 = (tile / tiles_x) * TY_;
-                const int z0 = chunk * zchunk, z1 = min(P.nz, z0 + zchunk);
-                // box (x, slot, y, z) at the tile origin (x a multiple of 4 floats); the last tile
-                // row uses the map whose box holds exactly its rows, so a box never reaches past
-                // ny; columns beyond nx fall outside the tensor and are not written
-                const CUtensorMap* m = y0 + TY_ > P.ny ? &map_out_top : &map_out;
-                // ghost cells written from this tile (storage coordinates; every box lies inside
-                // the padded plane exactly): its 4 edge columns to the opposite ghost columns, its
-                // 2 edge rows to the opposite ghost rows, and the corner block
-                const bool left = ghosts && x0 == 0, right = ghosts && x0 + TX_ >= P.nx;
-                const bool bottom = ghosts && y0 == 0, top = ghosts && y0 + TY_ >= P.ny;
-                const int gx_col = right ? kGX - kGW : P.nx + kGX;    // destination of the column box
-                const int gy_row = top ? kGY - 2 : P.ny + kGY;        // destination of the row box
-                const CUtensorMap* mc = y0 + TY_ > P.ny ? &map_gcol_top : &map_gcol;
-                const CUtensorMap* mr = x0 + TX_ > P.nx ? &map_grow_right : &map_grow;
-                for (int z = z0; z < z1; ++z, ++u) {
-                    wait(&out_full, u & 1);
-                    if (!abort_flag) {
-                        tma_store_4d(m, out, x0 + kGX, 0, y0 + kGY, z);
-                        if (left || right) tma_store_4d(mc, gcol, gx_col, 0, y0 + kGY, z);
-                        if (top || bottom) tma_store_4d(mr, grow, x0 + kGX, 0, gy_row, z);
-                        if ((left || right) && (top || bottom)) tma_store_4d(&map_gcor, gcor, gx_col, 0, gy_row, z);
-                        bulk_commit();
-                        bulk_wait_read_all();
-                    }
-                    mbar_arrive(&out_empty);
-                }
-            }
-            bulk_wait_all();   // the stores have completed before the CTA exits
-        }
-        __syncwarp();
-    } else if (warp < Sh::kLeadWarps + Sh::kPsiWarps) {
-        // ------------------------------------------------------------ psi pass
-        const int pt = tid - 32 * Sh::kLeadWarps;
-        constexpr int J = Sh::kPsiPerThread;
-        int lxs[J], lys[J];
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-            const int q = pt + j * Sh::kPsiThreads;
-            lxs[j] = -1;
-            lys[j] = -1;
-            if (q < Sh::kSlotsAll) tma_slot_of<TX_, TY_>(q, lxs[j], lys[j]);
-        }
-        int bad = 0;
+        // ------------------------------------------------------------ producer (lane 0 issues)
         unsigned k = 0;
         for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
             const int chunk = item / ntiles, tile = item % ntiles;
             const int x0 = (tile % tiles_x) * TX_, y0 = (tile / tiles_x) * TY_;
             const int z0 = chunk * zchunk, z1 = min(P.nz, z0 + zchunk);
-            // slot geometry of this item, fixed across its planes
-            bool use[J];
-            int mxs[J], mys[J], woff[J], roff[J];
-#pragma unroll
-            for (int j = 0; j < J; ++j) {
-                const int gx = x0 + lxs[j] - 1, gy = y0 + lys[j] - 1;
-                use[j] = lxs[j] >= 0 && gx >= -1 && gx <= P.nx && gy >= -1 && gy <= P.ny;
-                mxs[j] = use[j] ? map_coord(gx, P.nx, P.bc[0], P.bc[1]) : 0;
-                mys[j] = use[j] ? map_coord(gy, P.ny, P.bc[2], P.bc[3]) : 0;
-                woff[j] = (lys[j] + 1) * kWinW + lxs[j] - 1 + Sh::kXOff;
-                roff[j] = lys[j] * Sh::kRingW + lxs[j];
-            }
+            // window origin in storage coordinates: (x0 - kXOff) + kGX, (y0 - 2) + kGY
+            const int cx = x0 - Sh::kXOff + kGX, cy = y0;
             for (int p = z0 - 1; p <= z1; ++p, ++k) {
-                const int s = k % kStages, r = k % kRing;
-                if (k >= (unsigned)kRing) wait(&ring_empty[r], (k / kRing - 1) & 1);
-                wait(&full_bar[s], (k / kStages) & 1);
-                const S* st = reinterpret_cast<const S*>(smem_raw + (size_t)s * Sh::kStageOne);
-                const int mz = map_coord(p, P.nz, P.bc[4], P.bc[5]);
-                if (kWet && p < 0) {   // virtual (psi, rho) of the solid layer below a wetting -z wall
-#pragma unroll
-                    for (int j = 0; j < J; ++j)
-                        if (use[j]) ring[r * Sh::kRingPlane + roff[j]] = wall_entry(P, mxs[j], mys[j]);
-                } else
-#pragma unroll
-                for (int j = 0; j < J; ++j) {
-                    if (!use[j]) continue;
-                    float f[19], g[7];
-                    stage_pulls<Sh>(P, st + woff[j], src, mxs[j], mys[j], mz, f, g);
-                    float rho = sum19(f), T = sum7(g);
-                    const float psi2 = psi_squared(P, rho, T);
-                    ring[r * Sh::kRingPlane + roff[j]] = make_float2(psi_of(psi2), rho);
-                    tring[r * Sh::kRingPlane + roff[j]] = T;
-                    bad |= !(psi2 > 0.f) || !isfinite(rho) || !isfinite(T);
-                }
-                // every lane's ring writes are complete before lane 0 signals the other warps
-                __threadfence_block();
-                __syncwarp();
+                const int s = k % kStages;
+                if (k >= (unsigned)kStages) nb_sync(kBarEmpty0 + s, Sh::kCntEmpty);   // use k - kStages done
                 if (lane == 0) {
-                    mbar_arrive(&ring_full[r]);
-                    mbar_arrive(&empty_bar[s]);
+                    if (P.test_stall && k == 0) {
+                        // timeout-path test: the first stage's data never comes; the producer waits
+                        // (bounded) on a barrier nothing completes, then releases the stage empty
+                        if (!mbar_wait(&stall_bar, 0u)) {
+                            abort_flag = 1;
+                            atomicOr(flag, 2);
+                        }
+                        mbar_arrive(&full_bar[s]);
+                    } else if (abort_flag) {
+                        mbar_arrive(&full_bar[s]);   // release the waiters without data
+                    } else {
+                        const int mz = map_coord(p, P.nz, P.bc[4], P.bc[5]);
+                        const int zu = src_plane_up(P, mz), zd = src_plane_dn(P, mz);
+                        const unsigned bytes =
+                            (14u + (zu >= 0 ? 6u : 0u) + (zd >= 0 ? 6u : 0u)) * (unsigned)(Sh::kWin * Sh::kE);
+                        unsigned char* st = smem_raw + (size_t)s * Sh::kStageOne;
+                        mbar_expect_tx(&full_bar[s], bytes);
+                        tma_load_4d(st, &map14, cx, cy, mz, 0, &full_bar[s]);
+                        if (zu >= 0) tma_load_4d(st + Sh::kGrp1, &map6, cx, cy, zu, 14, &full_bar[s]);
+                        if (zd >= 0) tma_load_4d(st + Sh::kGrp2, &map6, cx, cy, zd, 20, &full_bar[s]);
+                        // pull the window of a plane kPrefetch ahead into L2, so that its load into a
+                        // stage (issued once a stage frees) waits on L2 rather than on DRAM
+                        const int pf = p + kPrefetch;
+                        if (pf <= z1) {
+                            const int fz = map_coord(pf, P.nz, P.bc[4], P.bc[5]);
+                            const int fu = src_plane_up(P, fz), fd = src_plane_dn(P, fz);
+                            tma_prefetch_4d(&map14, cx, cy, fz, 0);
+                            if (fu >= 0) tma_prefetch_4d(&map6, cx, cy, fu, 14);
+                            if (fd >= 0) tma_prefetch_4d(&map6, cx, cy, fd, 20);
+                        }
+                    }
                 }
+                __syncwarp();
             }
         }
-        if (bad) atomicOr(flag, 1);
-    } else {
-        // ------------------------------------------------------------ collision
-        const int ct = tid - 32 * Sh::kLeadWarps - Sh::kPsiThreads;
+        // the releases of the last stage uses (every use of EMPTY is matched on both sides)
+        const unsigned q0 = k > (unsigned)kStages ? k - kStages : 0u;
+        for (unsigned q = q0; q < k; ++q) nb_sync(kBarEmpty0 + q % kStages, Sh::kCntEmpty);
+        // copies still in flight land before the CTA exits (every use completes one phase; bounded)
+        if (lane == 0)
+            for (unsigned q = q0; q < k; ++q) mbar_wait(&full_bar[q % kStages], (q / kStages) & 1);
+        __syncwarp();
+    } else if (!Sh::kDirect && warp == 1) {
+        // ------------------------------------------------------------ storer (lane 0 issues)
+        nb_arrive(kBarOutEmpty, Sh::kCntOut);   // the out tile starts free
+        for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+            const int chunk = item / ntiles, tile = item % ntiles;
+            const int x0 = (tile % tiles_x) * TX_, y0 = (tile / tiles_x) * TY_;
+            const int z0 = chunk * zchunk, z1 = min(P.nz, z0 + zchunk);
+            const bool last_item = item + (int)gridDim.x >= n_items;
+            // box (x, slot, y, z) at the tile origin (x a multiple of 4 floats); the last tile
+            // row uses the map whose box holds exactly its rows, so a box never reaches past
+            // ny; columns beyond nx fall outside the tensor and are not written
+            const CUtensorMap* m = y0 + TY_ > P.ny ? &map_out_top : &map_out;
+            // ghost cells written from this tile (storage coordinates; every box lies inside
+            // the padded plane exactly): its 4 edge columns to the opposite ghost columns, its
+            // 2 edge rows to the opposite ghost rows, and the corner block
+            const bool left = ghosts && x0 == 0, right = ghosts && x0 + TX_ >= P.nx;
+            const bool bottom = ghosts && y0 == 0, top = ghosts && y0 + TY_ >= P.ny;
+            const int gx_col = right ? kGX - kGW : P.nx + kGX;    // destination of the column box
+            const int gy_row = top ? kGY - 2 : P.ny + kGY;        // destination of the row box
+            const CUtensorMap* mc = y0 + TY_ > P.ny ? &map_gcol_top : &map_gcol;
+            const CUtensorMap* mr = x0 + TX_ > P.nx ? &map_grow_right : &map_grow;
+            for (int z = z0; z < z1; ++z) {
+                nb_sync(kBarOutFull, Sh::kCntOut);
+                if (lane == 0 && !abort_flag) {
+                    tma_store_4d(m, out, x0 + kGX, 0, y0 + kGY, z);
+                    if (left || right) tma_store_4d(mc, gcol, gx_col, 0, y0 + kGY, z);
+                    if (top || bottom) tma_store_4d(mr, grow, x0 + kGX, 0, gy_row, z);
+                    if ((left || right) && (top || bottom)) tma_store_4d(&map_gcor, gcor, gx_col, 0, gy_row, z);
+                    bulk_commit();
+                    bulk_wait_read_all();
+                }
+                __syncwarp();
+                // the compute warps wait for this release before they write the next plane (none
+                // after the CTA's last plane)
+                if (!(last_item && z == z1 - 1)) nb_arrive(kBarOutEmpty, Sh::kCntOut);
+            }
+        }
+        if (lane == 0) bulk_wait_all();   // the stores have completed before the CTA exits
+        __syncwarp();
+    } else if (warp < Sh::kLeadWarps + Sh::kCompWarps) {
+        // ------------------------------------------------------------ compute
+        const int ct = tid - 32 * Sh::kLeadWarps;
         const bool node_thread = ct < Sh::kInterior;
         const int lx = ct % TX_ + 1, ly = ct / TX_ + 1;
         const int slot = ly * Sh::kRingW + lx;
         const int woff = (ly + 1) * kWinW + lx - 1 + Sh::kXOff;
         const float rho_ave = buoyancy_ref(P, sums_cur[0], P.inv_N);
         S* const outp = out + (ly - 1) * (kSlots * TX_) + (lx - 1);
-        unsigned k = 0, u = 0;
+        int bad = 0;
+        unsigned k = 0;
         for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
             const int chunk = item / ntiles, tile = item % ntiles;
             const int x0 = (tile % tiles_x) * TX_, y0 = (tile / tiles_x) * TY_;
             const int z0 = chunk * zchunk, z1 = min(P.nz, z0 + zchunk);
             const int gx = x0 + lx - 1, gy = y0 + ly - 1;
             const bool owner = node_thread && gx < P.nx && gy < P.ny;
+            // a tile slot just past the lattice edge (partial tile) holds the psi of the periodic
+            // image or mirror node there, as the halo ring does
+            const bool used = node_thread && gx <= P.nx && gy <= P.ny;
+            const int mx = used ? map_coord(gx, P.nx, P.bc[0], P.bc[1]) : 0;
+            const int my = used ? map_coord(gy, P.ny, P.bc[2], P.bc[3]) : 0;
             // this node's place in the ghost staging tiles of an edge tile (-1: none)
             const bool eright = ghosts && x0 + TX_ >= P.nx, eleft = ghosts && x0 == 0;
             const bool etop = ghosts && y0 + TY_ >= P.ny, ebottom = ghosts && y0 == 0;
@@ -810,59 +791,54 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
             float r_sum = 0.f, r_c = 0.f, t_sum = 0.f, t_c = 0.f;
             // phi_s history of the thread's node, loaded one plane ahead of its use
             float ph_next = owner ? phis[node_of(P, gx, gy, z0)] : 0.f;
-            for (int p = z0 - 1; p <= z1; ++p, ++k) {
-                if (p <= z0) {
-                    wait(&ring_full[k % kRing], (k / kRing) & 1);   // psi(p) ready
-                    if (p == z0 - 1) {                               // plane z0-1: psi only
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&empty_bar[k % kStages]);
-                    }
-                    continue;   // plane z0 is collided once psi(z0+1) is ready
+
+            // pull plane p (stage use k) into (fo, go), put the node's (psi, rho) into ring plane k
+            auto pull_plane = [&](int p, float* fo, float* go, float& ro, float& To, float& po) {
+                const int s = k % kStages;
+                wait_full(s, (k / kStages) & 1);
+                float2* rp = ring + (k % kRing) * kRP + slot;
+                if (kWet && p < 0) {   // solid layer below a wetting -z wall: virtual (psi, rho)
+                    if (used) *rp = wall_entry(P, mx, my);
+                } else if (used) {
+                    const int mz = map_coord(p, P.nz, P.bc[4], P.bc[5]);
+                    stage_pulls<Sh>(P, stage_of(s) + woff, src, mx, my, mz, fo, go);
+                    ro = sum19(fo);
+                    To = sum7(go);
+                    const float psi2 = psi_squared(P, ro, To);
+                    po = psi_of(psi2);
+                    *rp = make_float2(po, ro);
+                    bad |= !(psi2 > 0.f) || !isfinite(ro) || !isfinite(To);
                 }
-                const int z = p - 1;     // collide plane z in [z0, z1) with ring planes z-1, z, z+1
-                const unsigned kz = k - 1;
-                // the pulls of plane z come first, so that its stage is released before the wait
-                // for psi(z+1)
-                wait(&full_bar[kz % kStages], (kz / kStages) & 1);
+                nb_sync(kBarEmpty0 + s, Sh::kCntEmpty);   // the stage may be refilled
+                ++k;
+            };
+            // one collided plane z: pull plane z + 1 (into the n-set), wait for the ring, collide
+            // plane z (the c-set), store it
+            auto iterate = [&](int z, float* fc, float* gc, float rc, float Tc, float pc, float* fn, float* gn,
+                               float& rn, float& Tn, float& pn) {
+                pull_plane(z + 1, fn, gn, rn, Tn, pn);
+                nb_sync(kBarRing, Sh::kCntRing);         // psi of planes z - 1, z, z + 1 in the ring
                 const float ph_prev = ph_next;
                 if (owner && z + 1 < z1) ph_next = phis[node_of(P, gx, gy, z + 1)];
-                float f[19], g[7];
-                if (owner) {
-                    const S* sz = reinterpret_cast<const S*>(smem_raw + (size_t)(kz % kStages) * Sh::kStageOne);
-                    stage_pulls<Sh>(P, sz + woff, src, gx, gy, z, f, g);
-                }
-                __syncwarp();       // pulls are in registers: the stage of plane z may be refilled
-                if (lane == 0) mbar_arrive(&empty_bar[kz % kStages]);
-                wait(&ring_full[k % kRing], (k / kRing) & 1);   // psi(z+1) ready
-                float2 me = make_float2(0.f, 0.f);
-                float T = 0.f;
-                RingStencil rs = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                if (owner) {
-                    const float2* rm = ring + ((kz - 1) % kRing) * Sh::kRingPlane;
-                    const float2* r0 = ring + (kz % kRing) * Sh::kRingPlane;
-                    const float2* rp = ring + (k % kRing) * Sh::kRingPlane;
-                    me = r0[slot];            // (psi, rho) of the node, from the psi pass
-                    T = tring[(kz % kRing) * Sh::kRingPlane + slot];
-                    rs = ring_stencil(rm, r0, rp, slot, Sh::kRingW);
-                }
-                __syncwarp();       // ring plane z-1 has been read for the last time
-                if (lane == 0) mbar_arrive(&ring_empty[(kz - 1) % kRing]);
                 float ph = 0.f;
                 if (owner) {
-                    const float rho = me.y;
-                    kahan_add(r_sum, r_c, rho);
-                    kahan_add(t_sum, t_c, T);
-                    const Forces F = total_force(P, me.x, rs.Fx, rs.Fy, rs.Fz, rho - rho_ave);
-                    NodeOut o = collide_f(P, f, rho, F.Fx, F.Fy, F.Fz, F.Fm2, me.x * me.x);
-                    ph = collide_g(P, g, rho, T, o, rs.gx, rs.gy, rs.gz, ph_prev, first);
+                    const float2* rm = ring + ((k - 3) % kRing) * kRP;
+                    const float2* r0 = ring + ((k - 2) % kRing) * kRP;
+                    const float2* rq = ring + ((k - 1) % kRing) * kRP;
+                    const RingStencil rs = ring_stencil(rm, r0, rq, slot, Sh::kRingW);
+                    kahan_add(r_sum, r_c, rc);
+                    kahan_add(t_sum, t_c, Tc);
+                    const Forces F = total_force(P, pc, rs.Fx, rs.Fy, rs.Fz, rc - rho_ave);
+                    NodeOut o = collide_f(P, fc, rc, F.Fx, F.Fy, F.Fz, F.Fm2, pc * pc);
+                    ph = collide_g(P, gc, rc, Tc, o, rs.gx, rs.gy, rs.gz, ph_prev, first);
                 }
                 if constexpr (Sh::kDirect) {
                     if (owner) {
                         S fe[19], ge[7];   // stored form of f*, g+
 #pragma unroll
-                        for (int a = 0; a < 19; ++a) fe[a] = st_enc<S>(f[a], P.shift_f[a]);
+                        for (int a = 0; a < 19; ++a) fe[a] = st_enc<S>(fc[a], P.shift_f[a]);
 #pragma unroll
-                        for (int a = 0; a < 7; ++a) ge[a] = st_enc<S>(g[a], P.shift_g[a]);
+                        for (int a = 0; a < 7; ++a) ge[a] = st_enc<S>(gc[a], P.shift_g[a]);
                         auto put = [&](int xx, int yy) {
                             S* d = dst + sidx(P, xx, yy, z);
 #pragma unroll
@@ -876,14 +852,13 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                         if (gxi && gyi) put(gx + gxi, gy + gyi);
                     }
                 } else {
-                    // the out buffer is free once the tensor store of the previous plane has read it
-                    if (u > 0) wait(&out_empty, (u - 1) & 1);
+                    nb_sync(kBarOutEmpty, Sh::kCntOut);   // the tensor store has read the previous plane
                     if (owner) {
-                        S fe[19], ge[7];   // stored form of f*, g+
+                        S fe[19], ge[7];
 #pragma unroll
-                        for (int a = 0; a < 19; ++a) fe[a] = st_enc<S>(f[a], P.shift_f[a]);
+                        for (int a = 0; a < 19; ++a) fe[a] = st_enc<S>(fc[a], P.shift_f[a]);
 #pragma unroll
-                        for (int a = 0; a < 7; ++a) ge[a] = st_enc<S>(g[a], P.shift_g[a]);
+                        for (int a = 0; a < 7; ++a) ge[a] = st_enc<S>(gc[a], P.shift_g[a]);
 #pragma unroll
                         for (int a = 0; a < 19; ++a) outp[fslot(a) * TX_] = fe[a];
 #pragma unroll
@@ -910,25 +885,79 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                             for (int a = 0; a < 7; ++a) q[gslot(a) * kGW] = ge[a];
                         }
                     }
-                    // every lane's out writes become visible to the tensor store before lane 0 signals
+                    // this thread's out writes become visible to the tensor store (async proxy)
                     fence_proxy_async_smem();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&out_full);
+                    nb_arrive(kBarOutFull, Sh::kCntOut);
                 }
                 if (owner) phis[node_of(P, gx, gy, z)] = ph;
-                ++u;
+            };
+
+            // the populations of the plane being collided (a) and of the plane pulled ahead (b)
+            float fa[19], ga[7], ra = 0.f, Ta = 0.f, pa = 0.f;
+            float fb[19], gb[7], rb = 0.f, Tb = 0.f, pb = 0.f;
+            pull_plane(z0 - 1, fb, gb, rb, Tb, pb);   // psi only
+            pull_plane(z0, fa, ga, ra, Ta, pa);
+            // one copy of the loop body (the instruction cache holds it; unrolled twice to swap the
+            // two register sets it measured slower), so the pulled-ahead set is moved over
+#pragma unroll 1
+            for (int z = z0; z < z1; ++z) {
+                iterate(z, fa, ga, ra, Ta, pa, fb, gb, rb, Tb, pb);
+#pragma unroll
+                for (int a = 0; a < 19; ++a) fa[a] = fb[a];
+#pragma unroll
+                for (int a = 0; a < 7; ++a) ga[a] = gb[a];
+                ra = rb;
+                Ta = Tb;
+                pa = pb;
             }
-            // stage of the item's last plane (psi only); ring planes z1-1 and z1
-            __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(&empty_bar[(k - 1) % kStages]);
-                mbar_arrive(&ring_empty[(k - 2) % kRing]);
-                mbar_arrive(&ring_empty[(k - 1) % kRing]);
-            }
-            block_partial<kCol>((double)r_sum - (double)r_c, (double)t_sum - (double)t_c, partial, item, ct, 1,
-                                red_a, red_b);
+            block_partial<kComp>((double)r_sum - (double)r_c, (double)t_sum - (double)t_c, partial, item, ct,
+                                 kBarComp, red_a, red_b);
         }
-        finish_sums<kCol>(partial, n_items, counter, sums_next, ct, 1, red_a, red_b, &is_last);
+        if (bad) atomicOr(flag, 1);
+        finish_sums<kComp>(partial, n_items, counter, sums_next, ct, kBarComp, red_a, red_b, &is_last);
+    } else {
+        // ------------------------------------------------------------ halo psi (one warp)
+        int bad = 0;
+        unsigned k = 0;
+        for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+            const int chunk = item / ntiles, tile = item % ntiles;
+            const int x0 = (tile % tiles_x) * TX_, y0 = (tile / tiles_x) * TY_;
+            const int z0 = chunk * zchunk, z1 = min(P.nz, z0 + zchunk);
+            for (int p = z0 - 1; p <= z1; ++p, ++k) {
+                const int s = k % kStages;
+                float2* rp = ring + (k % kRing) * kRP;
+                wait_full(s, (k / kStages) & 1);
+                const S* st = stage_of(s);
+                const int mz = map_coord(p, P.nz, P.bc[4], P.bc[5]);
+                // kHaloPerLane slots a lane, rolled (one copy of the pull and EOS code); the slot
+                // geometry is recomputed per plane rather than kept in an indexed array
+#pragma unroll 1
+                for (int j = 0; j < Sh::kHaloPerLane; ++j) {
+                    const int q = Sh::kInterior + lane + 32 * j;
+                    if (q >= Sh::kSlotsAll) break;
+                    int lx, ly;
+                    tma_slot_of<TX_, TY_>(q, lx, ly);
+                    const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+                    if (gx < -1 || gx > P.nx || gy < -1 || gy > P.ny) continue;
+                    const int mx = map_coord(gx, P.nx, P.bc[0], P.bc[1]);
+                    const int my = map_coord(gy, P.ny, P.bc[2], P.bc[3]);
+                    const int roff = ly * Sh::kRingW + lx;
+                    if (kWet && p < 0) {   // virtual (psi, rho) of the solid layer below a wetting -z wall
+                        rp[roff] = wall_entry(P, mx, my);
+                        continue;
+                    }
+                    float f[19], g[7];
+                    stage_pulls<Sh>(P, st + (ly + 1) * kWinW + lx - 1 + Sh::kXOff, src, mx, my, mz, f, g);
+                    const float rho = sum19(f), T = sum7(g);
+                    const float psi2 = psi_squared(P, rho, T);
+                    rp[roff] = make_float2(psi_of(psi2), rho);
+                    bad |= !(psi2 > 0.f) || !isfinite(rho) || !isfinite(T);
+                }
+                nb_sync(kBarEmpty0 + s, Sh::kCntEmpty);   // the stage may be refilled
+                if (p > z0) nb_sync(kBarRing, Sh::kCntRing);   // one ring barrier per collided plane
+            }
+        }
+        if (bad) atomicOr(flag, 1);
     }
     __syncthreads();
 }
@@ -987,32 +1016,45 @@ __global__ void __launch_bounds__(256) k_ghosts(DevParams P, S* __restrict__ pop
     }
 }
 
-template <typename S> using Shape0 = TmaShape<32, 8, S>;
-template <typename S> using Shape1 = TmaShape<40, 7, S>;
+// Tile shapes of the TMA kernel (index = plan shape): 8 and 9 compute warps (about two per SM
+// sub-partition, up to 160 registers a thread), and two 384-node shapes with 12 (three per
+// sub-partition, 128 registers a thread).  kTmaRate is each shape's node rate per CTA relative
+// to 32 x 8, measured on the 200 x 200 x 300 pool (one GB300); 48 x 8 and 16 x 16 measured
+// slower still and are not offered.
+#define GB300_TMA_SHAPES(M) M(0, 32, 8) M(1, 40, 7) M(2, 32, 12) M(3, 24, 16)
+constexpr int kNumTmaShapes = 4;
+constexpr int kTmaTX[kNumTmaShapes] = {32, 40, 32, 24};
+constexpr int kTmaTY[kNumTmaShapes] = {8, 7, 12, 16};
+constexpr double kTmaRate[kNumTmaShapes] = {1.0, 1.0, 1.25, 1.12};
 
-// Plan of the TMA kernel for a lattice: tile shape and z-chunking that minimise the planes x
-// tile nodes of the busiest CTA (items are spread round robin over the persistent CTAs; when
-// every CTA holds one item, neighbouring tiles advance through z together and share their halo
-// reads in L2).
-void tma_plan(const DevParams& P, int ctas, int* shape, int* zchunk, int* items) {
-    const int shapes[2][2] = {{32, 8}, {40, 7}};
-    long long best = -1;
-    for (int sh = 0; sh < 2; ++sh) {
-        const int tx = shapes[sh][0], ty = shapes[sh][1];
+// Plan of the TMA kernel for a lattice: the tile shape and z-chunking with the least modelled
+// time of the busiest CTA.  Items (tile, z-chunk) go round robin to the persistent CTAs; a plane
+// of an item costs its tile nodes over the shape's rate, and an item about two planes more (its
+// two psi-only planes and the pipeline's fill).  forced_shape / forced_zchunk (>= 0 / > 0) pin
+// either choice.  lbm_autotune replaces the model by measurement.
+void tma_plan(const DevParams& P, int ctas, int forced_shape, int forced_zchunk, int* shape, int* zchunk,
+              int* items) {
+    double best = -1.0;
+    *shape = -1;
+    for (int sh = 0; sh < kNumTmaShapes; ++sh) {
+        if (forced_shape >= 0 && sh != forced_shape) continue;
+        const int tx = kTmaTX[sh], ty = kTmaTY[sh];
         const int tiles = ((P.nx + tx - 1) / tx) * ((P.ny + ty - 1) / ty);
         for (int nch = 1; nch <= P.nz; ++nch) {
             int zc = (P.nz + nch - 1) / nch;
-            int nchunks = (P.nz + zc - 1) / zc;
-            if (zc < 8 && nch > 1) break;
-            long long n = (long long)tiles * nchunks;
-            long long per_cta = (n + ctas - 1) / ctas;
-            long long cost = per_cta * (long long)tx * ty * (zc + 2);
+            if (forced_zchunk > 0) zc = forced_zchunk < P.nz ? forced_zchunk : P.nz;
+            const int nchunks = (P.nz + zc - 1) / zc;
+            if (forced_zchunk <= 0 && zc < 16 && nch > 1) break;
+            const long long n = (long long)tiles * nchunks;
+            const long long per_cta = (n + ctas - 1) / ctas;
+            const double cost = (double)per_cta * tx * ty / kTmaRate[sh] * (zc + 2.0);
             if (best < 0 || cost < best) {
                 best = cost;
                 *shape = sh;
                 *zchunk = zc;
                 *items = (int)n;
             }
+            if (forced_zchunk > 0) break;
         }
     }
 }
@@ -1049,29 +1091,32 @@ bool tma_eligible(const DevParams& P, int precision) {
 }
 
 size_t tma_smem_bytes(int shape, int precision) {
-    if (precision == 0) return shape == 0 ? Shape0<float>::kSmem : Shape1<float>::kSmem;
-    return shape == 0 ? Shape0<__half>::kSmem : Shape1<__half>::kSmem;
+#define GB300_SMEM(I, X, Y) \
+    case I: return precision == 0 ? TmaShape<X, Y, float>::kSmem : TmaShape<X, Y, __half>::kSmem;
+    switch (shape) { GB300_TMA_SHAPES(GB300_SMEM) }
+#undef GB300_SMEM
+    return (size_t)-1;
 }
 
-void tma_plan_for(const DevParams& P, int ctas, int* shape, int* zchunk, int* items) {
-    tma_plan(P, ctas, shape, zchunk, items);
+void tma_plan_for(const DevParams& P, int ctas, int forced_shape, int forced_zchunk, int* shape, int* zchunk,
+                  int* items) {
+    tma_plan(P, ctas, forced_shape, forced_zchunk, shape, zchunk, items);
 }
 
-int tma_box_w(int shape, int precision) {
-    if (precision == 0) return shape == 0 ? Shape0<float>::kWinW : Shape1<float>::kWinW;
-    return shape == 0 ? Shape0<__half>::kWinW : Shape1<__half>::kWinW;
-}
-int tma_box_h(int shape) { return shape == 0 ? Shape0<float>::kWinH : Shape1<float>::kWinH; }
-int tma_tile_w(int shape) { return shape == 0 ? 32 : 40; }
+int tma_num_shapes() { return kNumTmaShapes; }
+
+int tma_box_w(int shape, int precision) { return kTmaTX[shape] + 2 * (precision == 0 ? 4 : 8); }
+int tma_box_h(int shape) { return kTmaTY[shape] + 4; }
+int tma_tile_w(int shape) { return kTmaTX[shape]; }
 int tma_ghost_cols(int precision) { return precision == 0 ? 4 : 8; }   // 16 bytes of columns
 bool tma_ghosts_in_kernel(const DevParams& P, int shape, int precision) {
-    const int tx = tma_tile_w(shape), ty = shape == 0 ? 8 : 7, gw = tma_ghost_cols(precision);
+    const int tx = tma_tile_w(shape), ty = kTmaTY[shape], gw = tma_ghost_cols(precision);
     // ghost-column boxes (gw columns = 16 bytes) on 16-byte boundaries, at least two tiles per
     // axis (an edge tile is never both left and right, top and bottom), edge tiles at least gw
     // columns and 2 rows wide, and room for the gw ghost columns past nx in the padded rows
     return P.nx % gw == 0 && P.nx > tx && P.ny > ty && P.ny % ty != 1 && P.Ws >= P.nx + kGX + gw;
 }
-int tma_tile_h(int shape) { return shape == 0 ? 8 : 7; }
+int tma_tile_h(int shape) { return kTmaTY[shape]; }
 
 cudaError_t launch_fused(const DevParams& P, int precision, const StateBufs& B, const double* sums_cur,
                          double* sums_next, int first, cudaStream_t s, const TmaMaps* maps, bool* ghosts_written) {
@@ -1080,12 +1125,13 @@ cudaError_t launch_fused(const DevParams& P, int precision, const StateBufs& B, 
     cudaError_t e = cudaSuccess;
     if (ghosts_written) *ghosts_written = false;
     if (maps && maps->ok && B.pull_f && B.pull_g && tma_eligible(P, precision)) {
-        const int tx = maps->shape == 0 ? 32 : 40, ty = maps->shape == 0 ? 8 : 7;
+        const int tx = kTmaTX[maps->shape], ty = kTmaTY[maps->shape];
         const int txs = (P.nx + tx - 1) / tx, tys = (P.ny + ty - 1) / ty;
         const int ctas = maps->sms < maps->items ? maps->sms : maps->items;
         if (ghosts_written) *ghosts_written = maps->ghosts;
-#define GB300_TMA(SH, TXV, TYV, ST, WET)                                                                       \
+#define GB300_TMA(TXV, TYV, ST, WET)                                                                           \
         {                                                                                                      \
+            using SH = TmaShape<TXV, TYV, ST>;                                                                 \
             e = cudaFuncSetAttribute(k_fused_tma<TXV, TYV, ST, WET>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                      (int)SH::kSmem);                                                          \
             if (e != cudaSuccess) return e;                                                                    \
@@ -1099,19 +1145,18 @@ cudaError_t launch_fused(const DevParams& P, int precision, const StateBufs& B, 
         }
         // the wetting wall's solid plane is a separate instantiation (FP32 storage only), so that
         // the kernel without it carries no trace of it
-        if (precision == 0 && P.wet) {
-            if (maps->shape == 0) GB300_TMA(Shape0<float>, 32, 8, float, true)
-            else GB300_TMA(Shape1<float>, 40, 7, float, true)
-        } else if (precision == 0) {
-            if (maps->shape == 0) GB300_TMA(Shape0<float>, 32, 8, float, false)
-            else GB300_TMA(Shape1<float>, 40, 7, float, false)
-        } else if (precision == 1) {
-            if (maps->shape == 0) GB300_TMA(Shape0<__nv_bfloat16>, 32, 8, __nv_bfloat16, false)
-            else GB300_TMA(Shape1<__nv_bfloat16>, 40, 7, __nv_bfloat16, false)
-        } else {
-            if (maps->shape == 0) GB300_TMA(Shape0<__half>, 32, 8, __half, false)
-            else GB300_TMA(Shape1<__half>, 40, 7, __half, false)
+#define GB300_TMA_CASE(I, X, Y)                                                                                \
+        case I:                                                                                                \
+            if (precision == 0 && P.wet) GB300_TMA(X, Y, float, true)                                          \
+            else if (precision == 0) GB300_TMA(X, Y, float, false)                                             \
+            else if (precision == 1) GB300_TMA(X, Y, __nv_bfloat16, false)                                     \
+            else GB300_TMA(X, Y, __half, false)                                                                \
+            break;
+        switch (maps->shape) {
+            GB300_TMA_SHAPES(GB300_TMA_CASE)
+        default: return cudaErrorInvalidValue;
         }
+#undef GB300_TMA_CASE
 #undef GB300_TMA
         return cudaGetLastError();
     }

@@ -68,8 +68,12 @@ bool fused_supported(const DevParams& P);
 bool tma_eligible(const DevParams& P, int precision);
 // refresh the ghost columns / rows of a population buffer from their periodic images
 cudaError_t launch_ghosts(const DevParams& P, int precision, void* pops, cudaStream_t s);
-// tile shape 0: 32 x 8, 1: 40 x 7 (window boxes tma_box_w x tma_box_h per population slot)
-void tma_plan_for(const DevParams& P, int ctas, int* shape, int* zchunk, int* items);
+// tile shapes 0: 32 x 8, 1: 40 x 7, 2: 32 x 12, 3: 24 x 16 (window boxes tma_box_w x tma_box_h per
+// population slot)
+// forced_shape >= 0 / forced_zchunk > 0 pin the shape / the z-chunk of the plan
+void tma_plan_for(const DevParams& P, int ctas, int forced_shape, int forced_zchunk, int* shape, int* zchunk,
+                  int* items);
+int tma_num_shapes();
 size_t tma_smem_bytes(int shape, int precision);
 int tma_box_w(int shape, int precision);
 int tma_box_h(int shape);

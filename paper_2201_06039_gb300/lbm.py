@@ -51,7 +51,8 @@ class LbmParams(C.Structure):
 EXPORTS = ["lbm_params_default", "lbm_eos_critical", "lbm_workspace_bytes", "lbm_create",
            "lbm_init_fields", "lbm_step", "lbm_get_moments", "lbm_get_totals", "lbm_steps_done",
            "lbm_kernel_in_use",
-           "lbm_step_profiled", "lbm_destroy", "lbm_status_str", "lbm_last_error", "lbm_field_sum_noalloc",
+           "lbm_step_profiled", "lbm_plan_shapes", "lbm_get_plan", "lbm_select_plan", "lbm_autotune",
+           "lbm_destroy", "lbm_status_str", "lbm_last_error", "lbm_field_sum_noalloc",
            "lbm_state_bytes", "lbm_save_state", "lbm_load_state", "lbm_set_wall_map",
            "lbm_batch_create", "lbm_batch_nodes", "lbm_batch_init_fields", "lbm_batch_step", "lbm_batch_autotune",
            "lbm_batch_plan", "lbm_batch_select_plan", "lbm_batch_get_moments", "lbm_batch_get_totals",
@@ -101,6 +102,10 @@ def lib(build_if_missing: bool = True):
     L.lbm_set_wall_map.argtypes = [vp, vp, vp]
     L.lbm_kernel_in_use.argtypes = [vp]
     L.lbm_step_profiled.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_int)]
+    L.lbm_plan_shapes.argtypes = [C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int]
+    L.lbm_get_plan.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.lbm_select_plan.argtypes = [vp, C.c_int, C.c_int]
+    L.lbm_autotune.argtypes = [vp, C.c_int, dp]
     L.lbm_destroy.argtypes = [vp]
     L.lbm_destroy.restype = None
     L.lbm_status_str.argtypes = [C.c_int]
@@ -222,6 +227,32 @@ def lbm_step_profiled(ctx, n: int):
     cnt = (C.c_int * 3)()
     _check(lib().lbm_step_profiled(ctx, int(n), ms, cnt), "lbm_step_profiled")
     return list(ms), list(cnt)
+
+
+def lbm_plan_shapes():
+    """[(tile_w, tile_h), ...] of the TMA kernel's tile shapes, by shape index."""
+    n = int(lib().lbm_plan_shapes(None, None, 0))
+    w = (C.c_int * n)()
+    h = (C.c_int * n)()
+    lib().lbm_plan_shapes(w, h, n)
+    return list(zip(list(w), list(h)))
+
+
+def lbm_get_plan(ctx):
+    """(shape, zchunk, items, ctas) of the TMA plan in use; shape -1 without the TMA kernel."""
+    v = [C.c_int() for _ in range(4)]
+    _check(lib().lbm_get_plan(ctx, *[C.byref(x) for x in v]), "lbm_get_plan")
+    return tuple(x.value for x in v)
+
+
+def lbm_select_plan(ctx, shape: int, zchunk: int = 0):
+    _check(lib().lbm_select_plan(ctx, int(shape), int(zchunk)), "lbm_select_plan")
+
+
+def lbm_autotune(ctx, steps: int) -> float:
+    ms = C.c_double()
+    _check(lib().lbm_autotune(ctx, int(steps), C.byref(ms)), "lbm_autotune")
+    return ms.value
 
 
 def lbm_field_sum_noalloc(field, n: int, stream=None) -> float:
@@ -396,6 +427,49 @@ class Lattice:
         def f32(a):
             return np.ascontiguousarray(a, dtype=np.float32) if isinstance(a, np.ndarray) else a
         lbm_set_wall_map(self.ctx, f32(phi), f32(drho))
+
+    @property
+    def plan(self):
+        """(shape, zchunk, items, ctas) of the TMA plan in use (shape -1: no TMA kernel)."""
+        return lbm_get_plan(self.ctx)
+
+    def select_plan(self, shape: int, zchunk: int = 0):
+        lbm_select_plan(self.ctx, shape, zchunk)
+
+    def plan_key(self) -> str:
+        """Cache key of the plan choice: lattice size, storage, faces, wetting wall and the GPU."""
+        import torch
+        p = self.params
+        wet = int(p.wall_scheme == 1 or p.wall_rho > 0)
+        dev = torch.cuda.get_device_name(torch.cuda.current_device()).replace(" ", "_")
+        return (f"{p.nx}x{p.ny}x{p.nz}/prec{p.precision}/bc{''.join(str(int(b)) for b in p.bc)}"
+                f"/wet{wet}/{dev}")
+
+    def autotune(self, steps: int = 10, cache: str = None) -> dict:
+        """Pick the TMA plan by timing (lbm_autotune), or take it from the JSON file `cache` if that
+        holds an entry for this lattice (plan_key).  A fresh measurement is written to `cache`.
+        Returns {"shape", "zchunk", "ms_per_step" (None when taken from the cache), "cached"}."""
+        import json
+        key = self.plan_key()
+        table = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as fh:
+                table = json.load(fh)
+        hit = table.get(key)
+        if hit is not None:
+            self.select_plan(hit["shape"], hit["zchunk"])
+            return dict(shape=hit["shape"], zchunk=hit["zchunk"], ms_per_step=None, cached=True)
+        ms = lbm_autotune(self.ctx, steps)
+        shape, zchunk, _, _ = self.plan
+        if cache:
+            table[key] = dict(shape=shape, zchunk=zchunk, ms_per_step=ms, steps=steps)
+            d = os.path.dirname(os.path.abspath(cache))
+            os.makedirs(d, exist_ok=True)
+            tmp = cache + f".tmp{os.getpid()}"
+            with open(tmp, "w") as fh:
+                json.dump(table, fh, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return dict(shape=shape, zchunk=zchunk, ms_per_step=ms, cached=False)
 
 
 class Batch:
