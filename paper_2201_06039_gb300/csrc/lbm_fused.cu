@@ -66,19 +66,22 @@ __device__ __forceinline__ void slot_of(int tid, int& lx, int& ly) {
     }
 }
 
-// interaction force sum_a w psi(x+e) e and grad rho from the (psi, rho) ring planes
+// interaction force sum_a w psi(x+e) e and grad rho from the (psi, rho) ring planes: each
+// neighbour's (psi, rho) pair is added to the (F, grad rho) pair of every axis it lies along with
+// one paired FP32 fma (per lane the same rounding as two scalar fmas), in the velocity order of
+// Eq. 2 (the two-pass kernels' stencil adds in the same order, so every variant agrees bit for bit)
 struct RingStencil {
     float Fx, Fy, Fz, gx, gy, gz;
 };
 __device__ __forceinline__ RingStencil ring_stencil(const float2* rm, const float2* r0, const float2* rp, int slot,
                                                    int W) {
-    RingStencil s = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#define GB300_NB(PL, DX, DY, DZ, WGT)                                          \
-    {                                                                          \
-        float2 q = PL[slot + (DY) * W + (DX)];                                 \
-        if (DX) { s.Fx += (DX * WGT) * q.x; s.gx += (DX * WGT) * q.y; }        \
-        if (DY) { s.Fy += (DY * WGT) * q.x; s.gy += (DY * WGT) * q.y; }        \
-        if (DZ) { s.Fz += (DZ * WGT) * q.x; s.gz += (DZ * WGT) * q.y; }        \
+    float2 ax = make_float2(0.f, 0.f), ay = ax, az = ax;
+#define GB300_NB(PL, DX, DY, DZ, WGT)                                                          \
+    {                                                                                          \
+        const float2 q = PL[slot + (DY) * W + (DX)];                                           \
+        if (DX) ax = __ffma2_rn(make_float2((DX) * (WGT), (DX) * (WGT)), q, ax);                 \
+        if (DY) ay = __ffma2_rn(make_float2((DY) * (WGT), (DY) * (WGT)), q, ay);                 \
+        if (DZ) az = __ffma2_rn(make_float2((DZ) * (WGT), (DZ) * (WGT)), q, az);                 \
     }
     const float w1 = 1.f / 6.f, w2 = 1.f / 12.f;
     GB300_NB(r0, 1, 0, 0, w1) GB300_NB(r0, -1, 0, 0, w1) GB300_NB(r0, 0, 1, 0, w1) GB300_NB(r0, 0, -1, 0, w1)
@@ -87,7 +90,7 @@ __device__ __forceinline__ RingStencil ring_stencil(const float2* rm, const floa
     GB300_NB(rp, 1, 0, 1, w2) GB300_NB(rm, -1, 0, -1, w2) GB300_NB(rm, 1, 0, -1, w2) GB300_NB(rp, -1, 0, 1, w2)
     GB300_NB(rp, 0, 1, 1, w2) GB300_NB(rm, 0, -1, -1, w2) GB300_NB(rm, 0, 1, -1, w2) GB300_NB(rp, 0, -1, 1, w2)
 #undef GB300_NB
-    return s;
+    return RingStencil{ax.x, ay.x, az.x, ax.y, ay.y, az.y};
 }
 
 __device__ __forceinline__ void kahan_add(float& sum, float& c, float v) {
@@ -361,12 +364,10 @@ template <int TX_, int TY_, typename S_ = float> struct TmaShape {
     static constexpr int kHaloWarps = 1;
     static constexpr int kHaloPerLane = (kHaloNodes + 31) / 32;      // halo slots of one halo lane
     static constexpr int kCompThreads = kCompWarps * 32, kHaloThreads = kHaloWarps * 32;
-    // Output path.  FP32: the collided plane goes to an output tile in shared memory and leaves by
-    // TMA tensor stores issued by a storer warp.  16-bit storage: every compute thread stores its
-    // populations straight to global memory (no output tile, no storer warp), which frees shared
-    // memory for the L1 cache.
-    static constexpr bool kDirect = kE == 2;
-    static constexpr int kLeadWarps = kDirect ? 1 : 2;              // producer (+ storer) warps first
+    // Output path: the collided plane goes to an output tile in shared memory and leaves by TMA
+    // tensor stores issued by a storer warp (direct global stores by the compute threads measured
+    // slower, for FP32 and for 16-bit storage alike).
+    static constexpr int kLeadWarps = 2;                             // producer and storer warps first
     static constexpr int kThreads = 32 * kLeadWarps + kCompThreads + kHaloThreads;
     // registers per thread: warp w runs on SM sub-partition w % 4, whose register file holds 16K
     // registers; the per-thread count goes in steps of 8
@@ -390,15 +391,14 @@ template <int TX_, int TY_, typename S_ = float> struct TmaShape {
     static constexpr int kRing = 4;
     // as many stages as fit in one CTA's 227 KB beside the other buffers (at most 3 for FP32, 4 for
     // 16-bit storage; at least 2)
-    static constexpr size_t kFixed = (kDirect ? 0 : align128((size_t)kSlots * kInterior * kE) +
-                                      align128((size_t)TY_ * kSlots * (16 / kE) * kE) +
-                                      align128((size_t)2 * kSlots * TX_ * kE) +
-                                      align128((size_t)2 * kSlots * (16 / kE) * kE)) +
+    static constexpr size_t kFixed = align128((size_t)kSlots * kInterior * kE) +
+                                     align128((size_t)TY_ * kSlots * (16 / kE) * kE) +
+                                     align128((size_t)2 * kSlots * TX_ * kE) +
+                                     align128((size_t)2 * kSlots * (16 / kE) * kE) +
                                      (size_t)kRing * (TX_ + 2) * (TY_ + 2) * sizeof(float2) + 2048;
     static constexpr int kStagesFit = (int)((227 * 1024 - kFixed) / kStageOne);
     static constexpr int kStages = kStagesFit > (kE == 4 ? 3 : 4) ? (kE == 4 ? 3 : 4) : kStagesFit;
     static_assert(kStages >= 2, "two stages of the tile's window fit in shared memory");
-    static constexpr int kPrefetch = 2;                 // planes between an L2 prefetch and its load
     static constexpr size_t kStageBytes = (size_t)kStages * kStageOne;
     // collided plane, row-major [TY][26][TX]: source of one TMA tensor store per plane (a box of
     // fewer rows reads a prefix of it)
@@ -411,7 +411,7 @@ template <int TX_, int TY_, typename S_ = float> struct TmaShape {
     static constexpr size_t kGRowBytes = align128((size_t)2 * kSlots * TX_ * kE);
     static constexpr size_t kGCorBytes = align128((size_t)2 * kSlots * kGW * kE);
     static constexpr size_t kGhostBytes = kGColBytes + kGRowBytes + kGCorBytes;
-    static constexpr size_t kRingOff = kStageBytes + (kDirect ? 0 : kOutBytes + kGhostBytes);
+    static constexpr size_t kRingOff = kStageBytes + kOutBytes + kGhostBytes;
     static constexpr size_t kSmem = kRingOff + (size_t)kRing * kRingPlane * sizeof(float2);
     // element offset of storage slot s inside a stage
     static constexpr __host__ __device__ int slot_off(int s) {
@@ -481,14 +481,6 @@ __device__ __forceinline__ void tma_load_4d(void* smem_dst, const CUtensorMap* m
         "%5}], [%6];" ::"r"(smem_u32(smem_dst)),
         "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
         : "memory");
-}
-
-// prefetch of a tensor box into L2 (no shared memory, no completion signal)
-__device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap* map, int c0, int c1, int c2, int c3) {
-    asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(
-                     reinterpret_cast<unsigned long long>(map)),
-                 "r"(c0), "r"(c1), "r"(c2), "r"(c3)
-                 : "memory");
 }
 
 // tensor store of a shared-memory box (bulk async-group completion); the box is clipped at the
@@ -624,7 +616,7 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
             float* __restrict__ phis, int* flag, int first, int zchunk, int tiles_x, int tiles_y, int n_items) {
     using Sh = TmaShape<TX_, TY_, S>;
     constexpr int kWinW = Sh::kWinW, kStages = Sh::kStages, kRing = Sh::kRing, kRP = Sh::kRingPlane;
-    constexpr int kComp = Sh::kCompThreads, kPrefetch = Sh::kPrefetch, kGW = Sh::kGW;
+    constexpr int kComp = Sh::kCompThreads, kGW = Sh::kGW;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // stage s: smem_raw + s * kStageOne (three slot groups of [slots][TY+4][TX+2 kXOff])
     S* out = reinterpret_cast<S*>(smem_raw + Sh::kStageBytes);                   // [TY][26][TX]
@@ -692,16 +684,6 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                         tma_load_4d(st, &map14, cx, cy, mz, 0, &full_bar[s]);
                         if (zu >= 0) tma_load_4d(st + Sh::kGrp1, &map6, cx, cy, zu, 14, &full_bar[s]);
                         if (zd >= 0) tma_load_4d(st + Sh::kGrp2, &map6, cx, cy, zd, 20, &full_bar[s]);
-                        // pull the window of a plane kPrefetch ahead into L2, so that its load into a
-                        // stage (issued once a stage frees) waits on L2 rather than on DRAM
-                        const int pf = p + kPrefetch;
-                        if (pf <= z1) {
-                            const int fz = map_coord(pf, P.nz, P.bc[4], P.bc[5]);
-                            const int fu = src_plane_up(P, fz), fd = src_plane_dn(P, fz);
-                            tma_prefetch_4d(&map14, cx, cy, fz, 0);
-                            if (fu >= 0) tma_prefetch_4d(&map6, cx, cy, fu, 14);
-                            if (fd >= 0) tma_prefetch_4d(&map6, cx, cy, fd, 20);
-                        }
                     }
                 }
                 __syncwarp();
@@ -714,7 +696,7 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
         if (lane == 0)
             for (unsigned q = q0; q < k; ++q) mbar_wait(&full_bar[q % kStages], (q / kStages) & 1);
         __syncwarp();
-    } else if (!Sh::kDirect && warp == 1) {
+    } else if (warp == 1) {
         // ------------------------------------------------------------ storer (lane 0 issues)
         nb_arrive(kBarOutEmpty, Sh::kCntOut);   // the out tile starts free
         for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
@@ -784,10 +766,6 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                                         : ebottom ? (gy < 2 ? gy : -1) : -1;
             // the edge-row tile is as wide as the tile's real columns (the box reads it densely)
             const int rw = min(TX_, P.nx - x0);
-            // direct stores: periodic images of this node in the ghost cells, columns within kGW of
-            // an x edge and rows within 2 of a y edge (0: none)
-            const int gxi = !(Sh::kDirect && owner && ghosts) ? 0 : gx < kGW ? P.nx : gx >= P.nx - kGW ? -P.nx : 0;
-            const int gyi = !(Sh::kDirect && owner && ghosts) ? 0 : gy < 2 ? P.ny : gy >= P.ny - 2 ? -P.ny : 0;
             float r_sum = 0.f, r_c = 0.f, t_sum = 0.f, t_c = 0.f;
             // phi_s history of the thread's node, loaded one plane ahead of its use
             float ph_next = owner ? phis[node_of(P, gx, gy, z0)] : 0.f;
@@ -832,27 +810,8 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                     NodeOut o = collide_f(P, fc, rc, F.Fx, F.Fy, F.Fz, F.Fm2, pc * pc);
                     ph = collide_g(P, gc, rc, Tc, o, rs.gx, rs.gy, rs.gz, ph_prev, first);
                 }
-                if constexpr (Sh::kDirect) {
-                    if (owner) {
-                        S fe[19], ge[7];   // stored form of f*, g+
-#pragma unroll
-                        for (int a = 0; a < 19; ++a) fe[a] = st_enc<S>(fc[a], P.shift_f[a]);
-#pragma unroll
-                        for (int a = 0; a < 7; ++a) ge[a] = st_enc<S>(gc[a], P.shift_g[a]);
-                        auto put = [&](int xx, int yy) {
-                            S* d = dst + sidx(P, xx, yy, z);
-#pragma unroll
-                            for (int a = 0; a < 19; ++a) d[(size_t)fslot(a) * P.Ns] = fe[a];
-#pragma unroll
-                            for (int a = 0; a < 7; ++a) d[(size_t)gslot(a) * P.Ns] = ge[a];
-                        };
-                        put(gx, gy);
-                        if (gxi) put(gx + gxi, gy);
-                        if (gyi) put(gx, gy + gyi);
-                        if (gxi && gyi) put(gx + gxi, gy + gyi);
-                    }
-                } else {
-                    nb_sync(kBarOutEmpty, Sh::kCntOut);   // the tensor store has read the previous plane
+                nb_sync(kBarOutEmpty, Sh::kCntOut);   // the tensor store has read the previous plane
+                {
                     if (owner) {
                         S fe[19], ge[7];
 #pragma unroll

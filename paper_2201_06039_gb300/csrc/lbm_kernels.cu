@@ -103,9 +103,11 @@ __global__ void __launch_bounds__(TPB) k_psi(DevParams P, const S* __restrict__ 
 // ---------------------------------------------------------------- neighbourhood terms (S3-S4)
 // F_m = -G psi(x) sum w psi(x+e) e (Eq. 7, G = -1) and grad rho = sum w rho(x+e) e.
 struct Stencil {
-    float Fx, Fy, Fz, gx, gy, gz;
+    float2 x, y, z;   // (F component, grad rho component) per axis
 };
 
+// one neighbour's (psi, rho) added to each axis pair with one paired FP32 fma, in the order and
+// the rounding of the fused kernels' ring stencil
 template <int A>
 __device__ __forceinline__ void stencil_term(const DevParams& P, const float2* __restrict__ pr, int x, int y,
                                              int z, const Nbr& n, Stencil& s) {
@@ -117,14 +119,14 @@ __device__ __forceinline__ void stencil_term(const DevParams& P, const float2* _
         q = wall_entry(P, nb_c(ex, x, n.xm, n.xp), nb_c(ey, y, n.ym, n.yp));
     else
         q = __ldg(pr + j);
-    if (ex) { s.Fx += (ex * w) * q.x; s.gx += (ex * w) * q.y; }
-    if (ey) { s.Fy += (ey * w) * q.x; s.gy += (ey * w) * q.y; }
-    if (ez) { s.Fz += (ez * w) * q.x; s.gz += (ez * w) * q.y; }
+    if (ex) s.x = __ffma2_rn(make_float2(ex * w, ex * w), q, s.x);
+    if (ey) s.y = __ffma2_rn(make_float2(ey * w, ey * w), q, s.y);
+    if (ez) s.z = __ffma2_rn(make_float2(ez * w, ez * w), q, s.z);
 }
 
 __device__ __forceinline__ Stencil stencil(const DevParams& P, const float2* __restrict__ pr, int x, int y,
                                            int z, const Nbr& n) {
-    Stencil s = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    Stencil s = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     stencil_term<1>(P, pr, x, y, z, n, s); stencil_term<2>(P, pr, x, y, z, n, s);
     stencil_term<3>(P, pr, x, y, z, n, s); stencil_term<4>(P, pr, x, y, z, n, s);
     stencil_term<5>(P, pr, x, y, z, n, s); stencil_term<6>(P, pr, x, y, z, n, s);
@@ -156,7 +158,7 @@ __global__ void __launch_bounds__(TPB) k_velocity(DevParams P, const S* __restri
     float jz = (f[5] - f[6]) + (f[11] - f[12]) - (f[13] - f[14]) + (f[15] - f[16]) - (f[17] - f[18]);
     float2 me = __ldg(psirho + d);
     Stencil st = stencil(P, psirho, x, y, z, n);
-    const Forces F = total_force(P, me.x, st.Fx, st.Fy, st.Fz, rho - buoyancy_ref(P, sums_cur[0], P.inv_N));
+    const Forces F = total_force(P, me.x, st.x.x, st.y.x, st.z.x, rho - buoyancy_ref(P, sums_cur[0], P.inv_N));
     const float inv_rho = __fdividef(1.f, rho);
     vel[d] = make_float4((jx + 0.5f * F.Fx) * inv_rho, (jy + 0.5f * F.Fy) * inv_rho, (jz + 0.5f * F.Fz) * inv_rho, 0.f);
 }
@@ -212,10 +214,10 @@ __global__ void __launch_bounds__(TPB) k_collide(DevParams P, const S* __restric
     float2 me = __ldg(psirho + d);
     Stencil st = stencil(P, psirho, x, y, z, n);
     float rho_ave = buoyancy_ref(P, sums_cur[0], P.inv_N);
-    const Forces F = total_force(P, me.x, st.Fx, st.Fy, st.Fz, rho - rho_ave);
+    const Forces F = total_force(P, me.x, st.x.x, st.y.x, st.z.x, rho - rho_ave);
     NodeOut o = collide_f(P, f, rho, F.Fx, F.Fy, F.Fz, F.Fm2, me.x * me.x);
     if (vel && !next_to_solid(P, x, y, z)) o.divu = fd_divergence(P, vel, x, y, z, n);   // divu_mode 1
-    float ph = collide_g(P, g, rho, T, o, st.gx, st.gy, st.gz, phis[d], first);
+    float ph = collide_g(P, g, rho, T, o, st.x.y, st.y.y, st.z.y, phis[d], first);
     // frozen fields keep their stored values (no streaming, no collision)
     if (P.flow_off) {
 #pragma unroll
@@ -251,7 +253,7 @@ __global__ void __launch_bounds__(TPB) k_moments(DevParams P, const S* __restric
     Stencil st = stencil(P, psirho, x, y, z, n);
     float rho_ave = buoyancy_ref(P, sums_cur[0], P.inv_N);
     float db = rho - rho_ave;
-    float Fx = me.x * st.Fx + db * P.gx, Fy = me.x * st.Fy + db * P.gy, Fz = me.x * st.Fz + db * P.gz;
+    float Fx = me.x * st.x.x + db * P.gx, Fy = me.x * st.y.x + db * P.gy, Fz = me.x * st.z.x + db * P.gz;
     float inv = 1.f / rho;
     bool fz = P.flow_off != 0;
     if (orho) orho[i] = rho;
