@@ -45,7 +45,9 @@ typedef enum {
     LBM_ECUDA = -3,       /* a CUDA runtime call failed */
     LBM_ESTATE = -4,      /* call out of order (e.g. lbm_step before lbm_init_fields) */
     LBM_ENONFINITE = -5,  /* a non-finite rho/T/psi, or psi^2 <= 0 (Eq. 8 domain) appeared */
-    LBM_ETIMEOUT = -6     /* a bounded device wait gave up */
+    LBM_ETIMEOUT = -6,    /* a bounded device wait gave up */
+    LBM_EBOUNDS = -7      /* bounds-checked builds only: a kernel index fell outside its buffer
+                             (the access was skipped; the state is not to be trusted) */
 } lbm_status;
 
 /* Boundary type of one face of the box (faces ordered -x, +x, -y, +y, -z, +z). */
@@ -155,8 +157,10 @@ int lbm_init_fields(lbm_ctx* ctx, const float* rho, const float* T, const float*
  * which case it synchronises the stream and returns LBM_ENONFINITE if any node's rho, T
  * or psi became non-finite or psi^2 <= 0 during these steps, or LBM_ETIMEOUT if a bounded
  * pipeline wait of the TMA kernel gave up (the state of those steps is then not to be trusted;
- * re-initialise).
- * Errors: LBM_ESTATE (no init), LBM_EINVAL (n < 0), LBM_ECUDA, LBM_ENONFINITE, LBM_ETIMEOUT. */
+ * re-initialise), or, in a library built with -DLBM_BOUNDS_CHECK (libgb300lbm_bounds.so), LBM_EBOUNDS
+ * if a kernel index fell outside its buffer.
+ * Errors: LBM_ESTATE (no init), LBM_EINVAL (n < 0), LBM_ECUDA, LBM_ENONFINITE, LBM_ETIMEOUT,
+ * LBM_EBOUNDS. */
 int lbm_step(lbm_ctx* ctx, int n);
 
 /* Macroscopic fields of the current state: rho = sum f (Eq. 10), u = (sum e f + F/2)/rho
@@ -236,7 +240,8 @@ int lbm_step_profiled(lbm_ctx* ctx, int n, double kernel_ms[3], int launches[3])
  * whose memory pool forbids cudaMalloc outside its allocator, plug-ins with a fixed device-memory
  * budget, or latency-critical sections that must not allocate).
  *
- *   field     device pointer to n float32 values (not modified)
+ *   field     device (or managed) pointer of the current device to n float32 values, all inside
+ *             one allocation (not modified)
  *   n         0 <= n <= LBM_NOALLOC_MAX_ELEMENTS
  *   sum_out   host pointer; receives the sum in FP64 (deterministic: fixed-order block partials
  *             added in index order)
@@ -245,10 +250,13 @@ int lbm_step_profiled(lbm_ctx* ctx, int n, double kernel_ms[3], int launches[3])
  * The working memory (1024 block partials, a ticket and the result, about 16 KB) is one
  * file-scope device array of the library, present on every GPU that loads the library until the
  * process exits; nothing is allocated per call.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress), so make that first call before any stream
- * capture.  Every call shares the array: calls that overlap on the GPU (other streams, other
- * host threads) race and must be serialised by the caller.
- * Errors: LBM_EINVAL (NULL pointers, n out of range; message via lbm_last_error), LBM_ECUDA. */
+ * array's device address (cudaGetSymbolAddress).  The call synchronises its stream and copies
+ * the result to host memory, so it must not be made while its stream is being captured (it
+ * returns LBM_ESTATE then, before any work).  Every call shares the array: calls that overlap on
+ * the GPU (other streams, other host threads) race and must be serialised by the caller.
+ * Errors (message via lbm_last_error): LBM_EINVAL (NULL pointers, n out of range, field not
+ * device memory of the current device, or the n floats running past the end of field's
+ * allocation: all checked before any launch), LBM_ESTATE (stream capture), LBM_ECUDA. */
 #define LBM_NOALLOC_MAX_ELEMENTS (1LL << 31)
 int lbm_field_sum_noalloc(const float* field, long long n, double* sum_out, void* stream);
 

@@ -29,7 +29,7 @@
  * order of Eq. 5.  M^-1 is obtained by a generic Gauss-Jordan elimination.  N and
  * N^-1 are the printed matrices of Eqs. 38 and 41.
  *
- * Readings where the paper is silent (each also listed in the design notes):
+ * Readings where the paper is silent (the same readings bind the CUDA path):
  *  - c = dt = dx = 1, cs^2 = 1/3, G = -1.
  *  - Tc = 0.0778 a / (0.45724 b R) (the paper's rounded PR constants, Eq. 49 text).
  *  - Eq. 48 is used at every node; Eq. 45 with the local varsigma_T.

@@ -218,6 +218,8 @@ int check_batch_flag(lbm_batch* b) {
     GB300_CK(cudaStreamSynchronize(b->stream));
     if (h) {
         GB300_CK(cudaMemsetAsync(b->base + b->off_flag, 0, sizeof(int), b->stream));
+        if (h & 4) return fail(LBM_EBOUNDS, "a kernel index fell outside its buffer (bounds-checked build, step %lld)",
+                               b->steps);
         if (h & 2) return fail(LBM_ETIMEOUT, "a bounded device wait gave up (step %lld)", b->steps);
         return fail(LBM_ENONFINITE, "non-finite rho/T/psi or psi^2 <= 0 in the batch after step %lld", b->steps);
     }
@@ -311,6 +313,7 @@ int lbm_batch_create(const lbm_params* common, int n_instances, const int* dims,
         delete b;
         return fail(LBM_ENOMEM, "cudaMalloc(%zu): %s", off, cudaGetErrorString(e));
     }
+    for (auto& d : b->dps) d.check_flag = (int*)(b->base + b->off_flag);
     e = cudaMemsetAsync(b->base + b->off_sums, 0, b->off_inst - b->off_sums, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     int rc = e == cudaSuccess ? set_plan(b, 0) : fail(LBM_ECUDA, "initial memset: %s", cudaGetErrorString(e));
@@ -371,6 +374,7 @@ int lbm_batch_init_fields(lbm_batch* b, const float* rho, const float* T, const 
 }
 
 int lbm_batch_step(lbm_batch* b, int n) {
+    NvtxRange range("lbm_batch_step");
     if (!b) return fail(LBM_EINVAL, "batch is NULL");
     if (!b->initialised) return fail(LBM_ESTATE, "lbm_batch_step before lbm_batch_init_fields");
     if (n < 0) return fail(LBM_EINVAL, "n < 0");

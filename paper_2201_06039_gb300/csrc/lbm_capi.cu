@@ -392,6 +392,8 @@ int check_flag(lbm_ctx* c) {
     CK(cudaStreamSynchronize(c->stream));
     if (h) {
         CK(cudaMemsetAsync(c->base + c->L.flag, 0, sizeof(int), c->stream));
+        if (h & 4) return fail(LBM_EBOUNDS, "a kernel index fell outside its buffer (bounds-checked build, step %lld)",
+                               c->steps);
         if (h & 2) return fail(LBM_ETIMEOUT, "a bounded pipeline wait in the fused kernel gave up (step %lld)", c->steps);
         return fail(LBM_ENONFINITE, "non-finite rho/T/psi or psi^2 <= 0 after step %lld", c->steps);
     }
@@ -554,6 +556,7 @@ int lbm_create(const lbm_params* p, lbm_ctx** out) {
     }
     c->plan_shape = -1;
     c->plan_zchunk = 0;
+    c->dp.check_flag = (int*)(c->base + c->L.flag);
     if (c->variant == LBM_KERNEL_FUSED && p->use_tma != 0) make_tma_maps(c);
     cudaError_t e = cudaMemsetAsync(c->base + c->L.sums, 0, c->L.flag + sizeof(int) - c->L.sums, c->stream);
     if (e == cudaSuccess && c->dp.wet) {   // scheme 0: the table is constant; scheme 1: refreshed every step
@@ -576,6 +579,7 @@ int lbm_create(const lbm_params* p, lbm_ctx** out) {
 }
 
 int lbm_init_fields(lbm_ctx* c, const float* rho, const float* T, const float* u) {
+    NvtxRange range("lbm_init_fields");
     if (!c) return fail(LBM_EINVAL, "ctx is NULL");
     if (!rho || !T) return fail(LBM_EINVAL, "rho and T are required");
     size_t N = (size_t)c->dp.N;
@@ -611,6 +615,7 @@ int lbm_init_fields(lbm_ctx* c, const float* rho, const float* T, const float* u
 }
 
 int lbm_step(lbm_ctx* c, int n) {
+    NvtxRange range("lbm_step");
     if (!c) return fail(LBM_EINVAL, "ctx is NULL");
     if (!c->initialised) return fail(LBM_ESTATE, "lbm_step before lbm_init_fields");
     if (n < 0) return fail(LBM_EINVAL, "n < 0");
@@ -647,6 +652,7 @@ int lbm_step_profiled(lbm_ctx* c, int n, double kernel_ms[3], int launches[3]) {
 }
 
 int lbm_get_moments(lbm_ctx* c, float* rho, float* ux, float* uy, float* uz, float* T) {
+    NvtxRange range("lbm_get_moments");
     if (!c) return fail(LBM_EINVAL, "ctx is NULL");
     if (!c->initialised) return fail(LBM_ESTATE, "lbm_get_moments before lbm_init_fields");
     size_t N = (size_t)c->dp.N;
@@ -821,6 +827,7 @@ int lbm_select_plan(lbm_ctx* c, int shape, int zchunk) {
 }
 
 int lbm_autotune(lbm_ctx* c, int steps, double* best_ms) {
+    NvtxRange range("lbm_autotune");
     if (!c) return fail(LBM_EINVAL, "ctx is NULL");
     if (!c->initialised) return fail(LBM_ESTATE, "lbm_autotune before lbm_init_fields");
     if (steps < 1) return fail(LBM_EINVAL, "steps must be >= 1");
@@ -929,6 +936,7 @@ const char* lbm_status_str(int s) {
     case LBM_ESTATE: return "call out of order";
     case LBM_ENONFINITE: return "non-finite value in the lattice";
     case LBM_ETIMEOUT: return "device wait timed out";
+    case LBM_EBOUNDS: return "kernel index out of bounds";
     }
     return "unknown status";
 }

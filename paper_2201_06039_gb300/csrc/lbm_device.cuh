@@ -84,7 +84,33 @@ struct DevParams {
     const float2* wall_tab;   // (psi, rho) of that layer per (x, y), nx * ny, x fastest (wet only)
     float shift_f[19];        // storage shift w_a rho_ref (16-bit storage only, else 0)
     float shift_g[7];         // storage shift w_a T_ref
+    int* check_flag;          // the context's flag word (bounds-checked builds record violations here)
 };
+
+// Debug builds (-DLBM_BOUNDS_CHECK): every population and field index of the update, and the
+// shared-memory offsets of the fused kernels, is checked before use.  An index outside its buffer
+// raises bit 4 of the context's flag word and the access goes to element 0 instead, so nothing
+// out of range is ever touched; lbm_step then reports LBM_EBOUNDS.  Release builds compile the
+// checks away.
+__device__ __forceinline__ long long bidx(const DevParams& P, long long i, long long n) {
+#ifdef LBM_BOUNDS_CHECK
+    if (i < 0 || i >= n) {
+        atomicOr(P.check_flag, 4);
+        return 0;
+    }
+#endif
+    return i;
+}
+// the same for a thread's base offset v that later accesses reach as v + [lo, hi]
+__device__ __forceinline__ int bbase(const DevParams& P, int v, int lo, int hi, int n) {
+#ifdef LBM_BOUNDS_CHECK
+    if (v + lo < 0 || v + hi >= n) {
+        atomicOr(P.check_flag, 4);
+        return -lo;
+    }
+#endif
+    return v;
+}
 
 // reference density of the buoyancy force F_b = (rho - rho_b) g: fixed, or the domain mean of the
 // previous step (Sec. IV.C) from its FP64 sum
@@ -191,9 +217,9 @@ __device__ __forceinline__ float pull_f_one(const DevParams& P, const S* __restr
                                             int x, int y, int z, const Nbr& n) {
     constexpr int ex = ex19(A), ey = ey19(A), ez = ez19(A);
     if (A != 0 && crosses<A>(n.fbb))   // Eq. 50: f_a(x_b, t+1) = f*_{abar}(x_b, t)
-        return Codec<S>::load(src + (size_t)fslot(opp(A)) * P.Ns + i, P.shift_f[opp(A)]);
+        return Codec<S>::load(src + (size_t)fslot(opp(A)) * P.Ns + bidx(P, i, P.Ns), P.shift_f[opp(A)]);
     int s = sidx(P, src_c(ex, x, n.xm, n.xp), src_c(ey, y, n.ym, n.yp), src_c(ez, z, n.zm, n.zp));
-    return Codec<S>::load(src + (size_t)fslot(A) * P.Ns + s, P.shift_f[A]);
+    return Codec<S>::load(src + (size_t)fslot(A) * P.Ns + bidx(P, s, P.Ns), P.shift_f[A]);
 }
 
 // Node at least one node away from every face: every pull source is i - (ex + nx ey + nx ny ez).
@@ -205,7 +231,8 @@ __device__ __forceinline__ bool deep_interior(const DevParams& P, int x, int y, 
 template <typename S, int A>
 __device__ __forceinline__ float pull_f_fast(const DevParams& P, const S* __restrict__ src, int i) {
     constexpr int ex = ex19(A), ey = ey19(A), ez = ez19(A);
-    return Codec<S>::load(src + (size_t)fslot(A) * P.Ns + (i - ex - ey * P.Ws - ez * P.splane), P.shift_f[A]);
+    return Codec<S>::load(src + (size_t)fslot(A) * P.Ns + bidx(P, i - ex - ey * P.Ws - ez * P.splane, P.Ns),
+                          P.shift_f[A]);
 }
 
 // Pull of all 19 f (pull != 0) or direct read of the node's own values (fresh state).
@@ -228,7 +255,7 @@ __device__ __forceinline__ void load_f(const DevParams& P, const S* __restrict__
 #undef GB300_PULL
     } else {
 #pragma unroll
-        for (int a = 0; a < 19; ++a) f[a] = Codec<S>::load(src + (size_t)fslot(a) * P.Ns + i, P.shift_f[a]);
+        for (int a = 0; a < 19; ++a) f[a] = Codec<S>::load(src + (size_t)fslot(a) * P.Ns + bidx(P, i, P.Ns), P.shift_f[a]);
     }
 }
 
@@ -239,24 +266,24 @@ __device__ __forceinline__ float pull_g_one(const DevParams& P, const S* __restr
     constexpr int face = ex > 0 ? 0 : ex < 0 ? 1 : ey > 0 ? 2 : ey < 0 ? 3 : ez > 0 ? 4 : 5;
     if (A != 0 && (n.gabb & (1u << face))) {
         // Eq. 51: g_a(x_b, t+1) = -g+_{abar}(x_b, t) + 2 w_abar T_w   (w_abar = w_a on D3Q7)
-        float gp = Codec<S>::load(src + (size_t)gslot(opp(A)) * P.Ns + i, P.shift_g[opp(A)]);
+        float gp = Codec<S>::load(src + (size_t)gslot(opp(A)) * P.Ns + bidx(P, i, P.Ns), P.shift_g[opp(A)]);
         return -gp + 2.f * P.w1 * wall_T(P, face, x, y);
     }
     int s = sidx(P, src_c(ex, x, n.xm, n.xp), src_c(ey, y, n.ym, n.yp), src_c(ez, z, n.zm, n.zp));
-    return Codec<S>::load(src + (size_t)gslot(A) * P.Ns + s, P.shift_g[A]);
+    return Codec<S>::load(src + (size_t)gslot(A) * P.Ns + bidx(P, s, P.Ns), P.shift_g[A]);
 }
 
 template <typename S>
 __device__ __forceinline__ void load_g(const DevParams& P, const S* __restrict__ src, int pull, int i,
                                        int x, int y, int z, const Nbr& n, float g[7]) {
     if (pull && deep_interior(P, x, y, z)) {
-        g[0] = Codec<S>::load(src + (size_t)gslot(0) * P.Ns + i, P.shift_g[0]);
-        g[1] = Codec<S>::load(src + (size_t)gslot(1) * P.Ns + (i - 1), P.shift_g[1]);
-        g[2] = Codec<S>::load(src + (size_t)gslot(2) * P.Ns + (i + 1), P.shift_g[2]);
-        g[3] = Codec<S>::load(src + (size_t)gslot(3) * P.Ns + (i - P.Ws), P.shift_g[3]);
-        g[4] = Codec<S>::load(src + (size_t)gslot(4) * P.Ns + (i + P.Ws), P.shift_g[4]);
-        g[5] = Codec<S>::load(src + (size_t)gslot(5) * P.Ns + (i - P.splane), P.shift_g[5]);
-        g[6] = Codec<S>::load(src + (size_t)gslot(6) * P.Ns + (i + P.splane), P.shift_g[6]);
+        g[0] = Codec<S>::load(src + (size_t)gslot(0) * P.Ns + bidx(P, i, P.Ns), P.shift_g[0]);
+        g[1] = Codec<S>::load(src + (size_t)gslot(1) * P.Ns + bidx(P, i - 1, P.Ns), P.shift_g[1]);
+        g[2] = Codec<S>::load(src + (size_t)gslot(2) * P.Ns + bidx(P, i + 1, P.Ns), P.shift_g[2]);
+        g[3] = Codec<S>::load(src + (size_t)gslot(3) * P.Ns + bidx(P, i - P.Ws, P.Ns), P.shift_g[3]);
+        g[4] = Codec<S>::load(src + (size_t)gslot(4) * P.Ns + bidx(P, i + P.Ws, P.Ns), P.shift_g[4]);
+        g[5] = Codec<S>::load(src + (size_t)gslot(5) * P.Ns + bidx(P, i - P.splane, P.Ns), P.shift_g[5]);
+        g[6] = Codec<S>::load(src + (size_t)gslot(6) * P.Ns + bidx(P, i + P.splane, P.Ns), P.shift_g[6]);
     } else if (pull) {
         g[0] = pull_g_one<S, 0>(P, src, i, x, y, z, n);
         g[1] = pull_g_one<S, 1>(P, src, i, x, y, z, n);
@@ -267,7 +294,7 @@ __device__ __forceinline__ void load_g(const DevParams& P, const S* __restrict__
         g[6] = pull_g_one<S, 6>(P, src, i, x, y, z, n);
     } else {
 #pragma unroll
-        for (int a = 0; a < 7; ++a) g[a] = Codec<S>::load(src + (size_t)gslot(a) * P.Ns + i, P.shift_g[a]);
+        for (int a = 0; a < 7; ++a) g[a] = Codec<S>::load(src + (size_t)gslot(a) * P.Ns + bidx(P, i, P.Ns), P.shift_g[a]);
     }
 }
 
@@ -275,7 +302,7 @@ __device__ __forceinline__ void load_g(const DevParams& P, const S* __restrict__
 template <typename S>
 __device__ __forceinline__ void store_slots(const DevParams& P, S* __restrict__ dst, int i, const float f[19],
                                             const float g[7]) {
-    S* q = dst + i;
+    S* q = dst + bidx(P, i, P.Ns);
 #define GB300_ST(V, SH) { Codec<S>::store(q, V, SH); q += P.Ns; }
     GB300_ST(f[0], P.shift_f[0]) GB300_ST(f[1], P.shift_f[1]) GB300_ST(f[2], P.shift_f[2])
     GB300_ST(f[3], P.shift_f[3]) GB300_ST(f[4], P.shift_f[4]) GB300_ST(f[7], P.shift_f[7])
@@ -353,7 +380,7 @@ __device__ __forceinline__ float2 wall_psirho(const DevParams& P, int x, int y, 
 }
 
 __device__ __forceinline__ float2 wall_entry(const DevParams& P, int x, int y) {
-    return __ldg(P.wall_tab + (size_t)y * P.nx + x);
+    return __ldg(P.wall_tab + bidx(P, (long long)y * P.nx + x, (long long)P.nx * P.ny));
 }
 
 // f = M^-1 m from the pair sums / differences of the raw moments: a* = f_+ + f_-, b* = f_+ - f_-

@@ -178,7 +178,7 @@ __device__ __forceinline__ void fused_column(const DevParams& P, const S* __rest
     const int mx = slot_used ? map_coord(gx, P.nx, P.bc[0], P.bc[1]) : 0;
     const int my = slot_used ? map_coord(gy, P.ny, P.bc[2], P.bc[3]) : 0;
     const bool owner = interior && gx < P.nx && gy < P.ny;
-    const int slot = ly * Sh::kRingW + lx;
+    const int slot = slot_used ? bbase(P, ly * Sh::kRingW + lx, 0, 0, Sh::kRingPlane) : 0;
 
     auto psi_pass = [&](int zp) {
         if (!slot_used) return;
@@ -211,7 +211,7 @@ __device__ __forceinline__ void fused_column(const DevParams& P, const S* __rest
     auto collide = [&](int z) {
         if (!owner) return;
         const int x = gx, y = gy;
-        const int i = sidx(P, x, y, z), d = node_of(P, x, y, z);
+        const int i = sidx(P, x, y, z), d = (int)bidx(P, node_of(P, x, y, z), P.N);
         const float* st = stage + ((z - z0) & 1) * Sh::kStageFloats + tid;
         float f[19], g[7];
 #pragma unroll
@@ -223,18 +223,21 @@ __device__ __forceinline__ void fused_column(const DevParams& P, const S* __rest
         const float2* r0 = ring + (z % 3) * Sh::kRingPlane;
         const float2* rp = ring + ((z + 1) % 3) * Sh::kRingPlane;
         const float2 me = r0[slot];
-        RingStencil rs = ring_stencil(rm, r0, rp, slot, Sh::kRingW);
+        RingStencil rs = ring_stencil(rm, r0, rp, bbase(P, slot, -(Sh::kRingW + 1), Sh::kRingW + 1, Sh::kRingPlane),
+                                      Sh::kRingW);
         const Forces F = total_force(P, me.x, rs.Fx, rs.Fy, rs.Fz, rho - rho_ave);
         NodeOut o = collide_f(P, f, rho, F.Fx, F.Fy, F.Fz, F.Fm2, me.x * me.x);
         float ph = collide_g(P, g, rho, T, o, rs.gx, rs.gy, rs.gz, phis[d], first);
         // frozen fields keep their stored values (no streaming, no collision)
         if (P.flow_off) {
 #pragma unroll
-            for (int a = 0; a < 19; ++a) f[a] = Codec<S>::load(src + (size_t)fslot(a) * P.Ns + i, P.shift_f[a]);
+            for (int a = 0; a < 19; ++a)
+                f[a] = Codec<S>::load(src + (size_t)fslot(a) * P.Ns + bidx(P, i, P.Ns), P.shift_f[a]);
         }
         if (P.thermal_off) {
 #pragma unroll
-            for (int a = 0; a < 7; ++a) g[a] = Codec<S>::load(src + (size_t)gslot(a) * P.Ns + i, P.shift_g[a]);
+            for (int a = 0; a < 7; ++a)
+                g[a] = Codec<S>::load(src + (size_t)gslot(a) * P.Ns + bidx(P, i, P.Ns), P.shift_g[a]);
         }
         store_node<S>(P, dst, i, x, y, z, f, g);
         phis[d] = ph;
@@ -548,7 +551,7 @@ __device__ __forceinline__ void stage_pulls(const DevParams& P, const typename S
     GB300_SG(0) GB300_SG(1) GB300_SG(2) GB300_SG(3) GB300_SG(4) GB300_SG(5) GB300_SG(6)
 #undef GB300_SG
     if (mz == 0 && P.bc[4] != BC_PERIODIC) {
-        const int i = sidx(P, mx, my, mz);
+        const int i = (int)bidx(P, sidx(P, mx, my, mz), P.Ns);
         if (P.bc[4] == BC_WALL) {
             f[5] = Codec<S>::load(src + (size_t)fslot(6) * P.Ns + i, P.shift_f[6]);
             f[11] = Codec<S>::load(src + (size_t)fslot(12) * P.Ns + i, P.shift_f[12]);
@@ -559,7 +562,7 @@ __device__ __forceinline__ void stage_pulls(const DevParams& P, const typename S
         g[5] = -Codec<S>::load(src + (size_t)gslot(6) * P.Ns + i, P.shift_g[6]) + 2.f * P.w1 * wall_T(P, 4, mx, my);
     }
     if (mz == P.nz - 1 && P.bc[5] != BC_PERIODIC) {
-        const int i = sidx(P, mx, my, mz);
+        const int i = (int)bidx(P, sidx(P, mx, my, mz), P.Ns);
         if (P.bc[5] == BC_WALL) {
             f[6] = Codec<S>::load(src + (size_t)fslot(5) * P.Ns + i, P.shift_f[5]);
             f[12] = Codec<S>::load(src + (size_t)fslot(11) * P.Ns + i, P.shift_f[11]);
@@ -740,10 +743,17 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
         const int ct = tid - 32 * Sh::kLeadWarps;
         const bool node_thread = ct < Sh::kInterior;
         const int lx = ct % TX_ + 1, ly = ct / TX_ + 1;
-        const int slot = ly * Sh::kRingW + lx;
-        const int woff = (ly + 1) * kWinW + lx - 1 + Sh::kXOff;
+        // (the shared-memory offsets a thread reaches from these bases stay inside the ring plane,
+        // each slot's window and the output tile; checked in bounds-checked builds)
+        const int slot = node_thread ? bbase(P, ly * Sh::kRingW + lx, -(Sh::kRingW + 1), Sh::kRingW + 1, kRP)
+                                     : ly * Sh::kRingW + lx;
+        const int woff = node_thread ? bbase(P, (ly + 1) * kWinW + lx - 1 + Sh::kXOff, -(kWinW + 1), kWinW + 1,
+                                             Sh::kWin)
+                                     : 0;
         const float rho_ave = buoyancy_ref(P, sums_cur[0], P.inv_N);
-        S* const outp = out + (ly - 1) * (kSlots * TX_) + (lx - 1);
+        S* const outp = out + (node_thread ? bbase(P, (ly - 1) * (kSlots * TX_) + (lx - 1), 0, (kSlots - 1) * TX_,
+                                                   kSlots * Sh::kInterior)
+                                           : 0);
         int bad = 0;
         unsigned k = 0;
         for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
@@ -768,7 +778,7 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
             const int rw = min(TX_, P.nx - x0);
             float r_sum = 0.f, r_c = 0.f, t_sum = 0.f, t_c = 0.f;
             // phi_s history of the thread's node, loaded one plane ahead of its use
-            float ph_next = owner ? phis[node_of(P, gx, gy, z0)] : 0.f;
+            float ph_next = owner ? phis[bidx(P, node_of(P, gx, gy, z0), P.N)] : 0.f;
 
             // pull plane p (stage use k) into (fo, go), put the node's (psi, rho) into ring plane k
             auto pull_plane = [&](int p, float* fo, float* go, float& ro, float& To, float& po) {
@@ -797,7 +807,7 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                 pull_plane(z + 1, fn, gn, rn, Tn, pn);
                 nb_sync(kBarRing, Sh::kCntRing);         // psi of planes z - 1, z, z + 1 in the ring
                 const float ph_prev = ph_next;
-                if (owner && z + 1 < z1) ph_next = phis[node_of(P, gx, gy, z + 1)];
+                if (owner && z + 1 < z1) ph_next = phis[bidx(P, node_of(P, gx, gy, z + 1), P.N)];
                 float ph = 0.f;
                 if (owner) {
                     const float2* rm = ring + ((k - 3) % kRing) * kRP;
@@ -848,7 +858,7 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                     fence_proxy_async_smem();
                     nb_arrive(kBarOutFull, Sh::kCntOut);
                 }
-                if (owner) phis[node_of(P, gx, gy, z)] = ph;
+                if (owner) phis[bidx(P, node_of(P, gx, gy, z), P.N)] = ph;
             };
 
             // the populations of the plane being collided (a) and of the plane pulled ahead (b)
@@ -900,13 +910,14 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                     if (gx < -1 || gx > P.nx || gy < -1 || gy > P.ny) continue;
                     const int mx = map_coord(gx, P.nx, P.bc[0], P.bc[1]);
                     const int my = map_coord(gy, P.ny, P.bc[2], P.bc[3]);
-                    const int roff = ly * Sh::kRingW + lx;
+                    const int roff = bbase(P, ly * Sh::kRingW + lx, 0, 0, kRP);
                     if (kWet && p < 0) {   // virtual (psi, rho) of the solid layer below a wetting -z wall
                         rp[roff] = wall_entry(P, mx, my);
                         continue;
                     }
                     float f[19], g[7];
-                    stage_pulls<Sh>(P, st + (ly + 1) * kWinW + lx - 1 + Sh::kXOff, src, mx, my, mz, f, g);
+                    stage_pulls<Sh>(P, st + bbase(P, (ly + 1) * kWinW + lx - 1 + Sh::kXOff, -(kWinW + 1), kWinW + 1, Sh::kWin),
+                                    src, mx, my, mz, f, g);
                     const float rho = sum19(f), T = sum7(g);
                     const float psi2 = psi_squared(P, rho, T);
                     rp[roff] = make_float2(psi_of(psi2), rho);

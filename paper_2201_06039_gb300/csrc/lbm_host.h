@@ -3,6 +3,7 @@
 #include <stddef.h>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/lbm.h"
 #include "lbm_device.cuh"
@@ -20,6 +21,15 @@ int validate(const lbm_params* p);
 // device-side constants of a parameter set (geometry, storage layout, model constants)
 DevParams make_dev(const lbm_params* p);
 bool is_device_ptr(const void* ptr);
+
+// NVTX range over the enclosing scope, named for the call (visible in Nsight Systems / Compute
+// timelines; a no-op unless a tool is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 }  // namespace gb300lbm
 

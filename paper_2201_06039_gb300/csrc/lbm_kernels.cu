@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(TPB) k_psi(DevParams P, const S* __restrict__ 
         float rho = sum19(f), T = sum7(g);
         float psi2 = psi_squared(P, rho, T);
         bad = !(psi2 > 0.f) || !isfinite(rho) || !isfinite(T);
-        psirho[node_of(P, x, y, z)] = make_float2(psi_of(psi2), rho);
+        psirho[bidx(P, node_of(P, x, y, z), P.N)] = make_float2(psi_of(psi2), rho);
         ra = rho;
         ta = T;
     }
@@ -113,7 +113,7 @@ __device__ __forceinline__ void stencil_term(const DevParams& P, const float2* _
                                              int z, const Nbr& n, Stencil& s) {
     constexpr int ex = ex19(A), ey = ey19(A), ez = ez19(A);
     constexpr float w = (ex * ex + ey * ey + ez * ez) == 1 ? (1.f / 6.f) : (1.f / 12.f);
-    int j = node_of(P, nb_c(ex, x, n.xm, n.xp), nb_c(ey, y, n.ym, n.yp), nb_c(ez, z, n.zm, n.zp));
+    int j = (int)bidx(P, node_of(P, nb_c(ex, x, n.xm, n.xp), nb_c(ey, y, n.ym, n.yp), nb_c(ez, z, n.zm, n.zp)), P.N);
     float2 q;
     if (ez < 0 && z == 0 && P.wet)   // solid layer below a wetting -z wall: virtual (psi, rho)
         q = wall_entry(P, nb_c(ex, x, n.xm, n.xp), nb_c(ey, y, n.ym, n.yp));
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(TPB) k_velocity(DevParams P, const S* __restri
                                                  const double* __restrict__ sums_cur, float4* __restrict__ vel) {
     int x = blockIdx.x * TPB_X + threadIdx.x, y = blockIdx.y * TPB_Y + threadIdx.y, z = blockIdx.z;
     if (x >= P.nx || y >= P.ny) return;
-    int i = sidx(P, x, y, z), d = node_of(P, x, y, z);
+    int i = sidx(P, x, y, z), d = (int)bidx(P, node_of(P, x, y, z), P.N);
     Nbr n = make_nbr(P, x, y, z);
     float f[19];
     load_f<S>(P, fs, pull_f, i, x, y, z, n, f);
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(TPB) k_collide(DevParams P, const S* __restric
                                                 float* __restrict__ phis, int first, const float4* __restrict__ vel) {
     int x = blockIdx.x * TPB_X + threadIdx.x, y = blockIdx.y * TPB_Y + threadIdx.y, z = blockIdx.z;
     if (x >= P.nx || y >= P.ny) return;
-    int i = sidx(P, x, y, z), d = node_of(P, x, y, z);
+    int i = sidx(P, x, y, z), d = (int)bidx(P, node_of(P, x, y, z), P.N);
     Nbr n = make_nbr(P, x, y, z);
     float f[19], g[7];
     load_f<S>(P, fs, pull_f, i, x, y, z, n, f);

@@ -13,8 +13,10 @@
 // last (atomic ticket) adds the partials in index order.  The result therefore depends only on
 // the input and the grid size, which is fixed by the input length.
 #include <mutex>
+#include <stdint.h>
 #include <stdio.h>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/lbm.h"
@@ -98,6 +100,79 @@ int scratch_for_current_device(void** out) {
     return LBM_OK;
 }
 
+// The input must be device (or managed) memory of the current device, and the n floats from
+// `field` must lie inside one allocation: a host pointer, another GPU's pointer or a range past
+// the end of the buffer would make the kernel read memory it does not own.  The allocation's
+// extent comes from the driver (cuMemGetAddressRange); where that query is unavailable only the
+// pointer's kind and device are checked.
+typedef CUresult (*AddressRangeFn)(CUdeviceptr*, size_t*, CUdeviceptr);
+
+int check_field(const float* field, long long n) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        gb300lbm_set_error("lbm_field_sum_noalloc: no usable current device");
+        return LBM_ECUDA;
+    }
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, field) != cudaSuccess) {
+        cudaGetLastError();
+        gb300lbm_set_error("lbm_field_sum_noalloc: field is not a pointer the CUDA runtime knows");
+        return LBM_EINVAL;
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) {
+        gb300lbm_set_error("lbm_field_sum_noalloc: field must be device or managed memory, not host memory");
+        return LBM_EINVAL;
+    }
+    if (at.type == cudaMemoryTypeDevice && at.device != dev) {
+        char m[160];
+        snprintf(m, sizeof(m), "lbm_field_sum_noalloc: field lives on device %d, the current device is %d", at.device,
+                 dev);
+        gb300lbm_set_error(m);
+        return LBM_EINVAL;
+    }
+    static AddressRangeFn range_fn = nullptr;
+    static bool looked_up = false;
+    {
+        std::lock_guard<std::mutex> lock(g_mu);
+        if (!looked_up) {
+            void* fn = nullptr;
+            cudaDriverEntryPointQueryResult q;
+            if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &fn, 12000, cudaEnableDefault, &q) ==
+                    cudaSuccess &&
+                q == cudaDriverEntryPointSuccess)
+                range_fn = (AddressRangeFn)fn;
+            cudaGetLastError();
+            looked_up = true;
+        }
+    }
+    if (range_fn) {
+        CUdeviceptr base = 0;
+        size_t size = 0;
+        if (range_fn(&base, &size, (CUdeviceptr)(uintptr_t)field) == CUDA_SUCCESS) {
+            const unsigned long long begin = (unsigned long long)(uintptr_t)field;
+            const unsigned long long end = begin + 4ull * (unsigned long long)n;
+            if (end > (unsigned long long)base + size) {
+                char m[200];
+                snprintf(m, sizeof(m),
+                         "lbm_field_sum_noalloc: %lld floats run %llu bytes past the end of the allocation holding "
+                         "field",
+                         n, end - ((unsigned long long)base + size));
+                gb300lbm_set_error(m);
+                return LBM_EINVAL;
+            }
+        }
+    }
+    return LBM_OK;
+}
+
+int cuda_fail(const char* what, cudaError_t e) {
+    char m[200];
+    snprintf(m, sizeof(m), "lbm_field_sum_noalloc: %s: %s", what, cudaGetErrorString(e));
+    gb300lbm_set_error(m);
+    return LBM_ECUDA;
+}
+
 }  // namespace
 
 extern "C" int lbm_field_sum_noalloc(const float* field, long long n, double* sum_out, void* cuda_stream) {
@@ -113,24 +188,36 @@ extern "C" int lbm_field_sum_noalloc(const float* field, long long n, double* su
         return LBM_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    void* p = nullptr;
-    int rc = scratch_for_current_device(&p);
-    if (rc != LBM_OK) return rc;
-    Scratch* sc = (Scratch*)p;
+    // the call synchronises its stream and copies the result to pageable host memory, so it can
+    // never be part of a captured graph; made during a capture it would invalidate the capture
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) return cuda_fail("cudaStreamIsCapturing", e);
+    if (cap != cudaStreamCaptureStatusNone) {
+        gb300lbm_set_error("lbm_field_sum_noalloc: the stream is being captured; call it outside stream capture");
+        return LBM_ESTATE;
+    }
     if (n == 0) {
         *sum_out = 0.0;
         return LBM_OK;
     }
-    // the ticket must start at zero (the kernel leaves it at zero; clear it in case an earlier
-    // launch on this device did not complete)
-    if (cudaMemsetAsync(&sc->ticket, 0, sizeof(unsigned), st) != cudaSuccess) return LBM_ECUDA;
+    int rc = check_field(field, n);
+    if (rc != LBM_OK) return rc;
+    void* p = nullptr;
+    rc = scratch_for_current_device(&p);
+    if (rc != LBM_OK) return rc;
+    Scratch* sc = (Scratch*)p;
+    // the ticket is zero here: it starts at zero and every completed launch resets it
     long long blocks = (n + kThreads - 1) / kThreads;
     if (blocks > kMaxBlocks) blocks = kMaxBlocks;
     k_field_sum_noalloc<<<(unsigned)blocks, kThreads, 0, st>>>(field, n, sc);
-    if (cudaGetLastError() != cudaSuccess) return LBM_ECUDA;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail("kernel launch", e);
     double2 r;
-    if (cudaMemcpyAsync(&r, &sc->result, sizeof(r), cudaMemcpyDeviceToHost, st) != cudaSuccess) return LBM_ECUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return LBM_ECUDA;
+    e = cudaMemcpyAsync(&r, &sc->result, sizeof(r), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail("result copy", e);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail("stream synchronisation", e);
     *sum_out = r.x;
     return LBM_OK;
 }

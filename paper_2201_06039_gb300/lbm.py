@@ -16,7 +16,7 @@ import numpy as np
 
 from . import build as _build
 
-LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ESTATE, LBM_ENONFINITE, LBM_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_ESTATE, LBM_ENONFINITE, LBM_ETIMEOUT, LBM_EBOUNDS = 0, -1, -2, -3, -4, -5, -6, -7
 LBM_NOALLOC_MAX_ELEMENTS = 1 << 31
 LBM_BC_PERIODIC, LBM_BC_WALL, LBM_BC_OUTFLOW, LBM_BC_THERMAL_ONLY = 0, 1, 2, 3
 LBM_FP32, LBM_BF16_SHIFTED, LBM_FP16_SHIFTED = 0, 1, 2
@@ -256,12 +256,33 @@ def lbm_autotune(ctx, steps: int) -> float:
 
 
 def lbm_field_sum_noalloc(field, n: int, stream=None) -> float:
-    """FP64 sum of n float32 values at device pointer `field` (int) or a CUDA tensor, using no
-    device allocation (see include/lbm.h)."""
-    ptr = field if isinstance(field, int) else _ptr(field)
-    out = C.c_double()
-    st = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
-    _check(lib().lbm_field_sum_noalloc(ptr, int(n), C.byref(out), st), "lbm_field_sum_noalloc")
+    """FP64 sum of n float32 values at device pointer `field` (int) or a CUDA float32 tensor,
+    using no device allocation (see include/lbm.h).
+
+    With a tensor, n must not exceed its element count, and the call runs with the tensor's device
+    current and, unless `stream` is given, on torch's current stream of that device (the stream
+    torch's own kernels that produced the field ran on).  With a raw pointer the current device
+    is used and `stream` None means the legacy default stream."""
+    if isinstance(field, int):
+        ptr = field
+        st = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+        out = C.c_double()
+        _check(lib().lbm_field_sum_noalloc(ptr, int(n), C.byref(out), st), "lbm_field_sum_noalloc")
+        return out.value
+    import torch
+    if not field.is_cuda:
+        raise ValueError("lbm_field_sum_noalloc: field must be a CUDA tensor")
+    if field.dtype != torch.float32 or not field.is_contiguous():
+        raise ValueError("lbm_field_sum_noalloc: field must be a contiguous float32 tensor")
+    if not 0 <= int(n) <= field.numel():
+        raise ValueError(f"lbm_field_sum_noalloc: n = {n} outside 0..{field.numel()} (the tensor's elements)")
+    with torch.cuda.device(field.device):
+        if stream is None:
+            st = torch.cuda.current_stream(field.device).cuda_stream
+        else:
+            st = stream if isinstance(stream, int) else stream.cuda_stream
+        out = C.c_double()
+        _check(lib().lbm_field_sum_noalloc(_ptr(field), int(n), C.byref(out), st), "lbm_field_sum_noalloc")
     return out.value
 
 

@@ -45,6 +45,11 @@ def _compare(case, steps, variant, fixed_bar=False, u=None):
         floor = fp32_floor(s, rho, T, u, steps, ref=orc)
         bar = bars(floor)
     print(case.get("name", ""), "variant", variant, "steps", steps, "gpu", err, "fp32 floor", floor)
+    if not fixed_bar:
+        # the required tolerance is 1e-5 on every field; where the FP32 floor of the case lies
+        # above it the asserted bar is the floor-based one, and the plain 1e-5 verdict is reported
+        print("  1e-5 bar:", {k: ("met" if v <= BAR else "NOT met") for k, v in err.items()},
+              "asserted bar:", {k: float(f"{b:.3g}") for k, b in bar.items()})
     for k, v in err.items():
         assert v <= bar[k], (k, v, bar[k], err, floor)
     return err

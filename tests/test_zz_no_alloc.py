@@ -39,7 +39,30 @@ def test_noalloc_sum_rejects_sizes_beyond_the_maximum():
     import torch
     from paper_2201_06039_gb300 import lbm
     x = torch.ones(16, dtype=torch.float32, device="cuda")
-    with pytest.raises(lbm.LbmError) as ei:
-        lbm.lbm_field_sum_noalloc(x, lbm.LBM_NOALLOC_MAX_ELEMENTS + 1)
+    with pytest.raises(lbm.LbmError) as ei:               # raw pointer: the library's own check
+        lbm.lbm_field_sum_noalloc(x.data_ptr(), lbm.LBM_NOALLOC_MAX_ELEMENTS + 1)
     assert ei.value.status == lbm.LBM_EINVAL
     assert "exceeds the maximum" in str(ei.value)
+
+
+def test_noalloc_sum_rejects_host_memory_and_ranges_past_the_buffer():
+    """Bad inputs are refused on the host before any launch: a host pointer, a tensor count above
+    the tensor's size (wrapper) and a raw-pointer range that runs past the allocation (library)."""
+    import torch
+    from paper_2201_06039_gb300 import lbm
+    host = np.ones(64, dtype=np.float32)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_field_sum_noalloc(host.ctypes.data, 64)
+    assert ei.value.status == lbm.LBM_EINVAL and "host memory" in str(ei.value)
+    x = torch.ones(1000, dtype=torch.float32, device="cuda")
+    with pytest.raises(ValueError):
+        lbm.lbm_field_sum_noalloc(x, 1001)
+    with pytest.raises(ValueError):
+        lbm.lbm_field_sum_noalloc(x.cpu(), 10)
+    # a raw pointer with a count far past its (caching-allocator) block is refused by the library
+    y = torch.ones(1 << 20, dtype=torch.float32, device="cuda")
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_field_sum_noalloc(y.data_ptr(), (1 << 31) - 1)
+    assert ei.value.status == lbm.LBM_EINVAL and "past the end" in str(ei.value)
+    # the context stays usable: a valid call right after the refusals
+    assert lbm.lbm_field_sum_noalloc(x, 1000) == 1000.0

@@ -101,7 +101,8 @@ def add_noise(field_: np.ndarray, seed: int, amp: float) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------------------
-# Lattice parameter sets of the workloads (values of Sec. IV; readings in the design notes)
+# Lattice parameter sets of the workloads (values of Sec. IV; where the paper is silent the value
+# is a reading stated beside it)
 # ----------------------------------------------------------------------------------------
 
 BC_PERIODIC, BC_WALL, BC_OUTFLOW, BC_THERMAL_ONLY = 0, 1, 2, 3
