@@ -48,6 +48,7 @@ class OrcParams(C.Structure):
         ("wall_rho", C.c_double), ("wall_rho_patch", C.c_double), ("wall_patch_half", C.c_double),
         ("wall_scheme", C.c_int), ("wall_phi", C.c_double), ("wall_drho", C.c_double),
         ("wall_phi_patch", C.c_double), ("wall_drho_patch", C.c_double),
+        ("thermal_q", C.c_int),
     ]
 
 
@@ -149,6 +150,7 @@ def params_from_setup(s) -> OrcParams:
     p.wall_scheme = int(getattr(s, "wall_scheme", 0))
     for k in ("wall_phi", "wall_drho", "wall_phi_patch", "wall_drho_patch"):
         setattr(p, k, float(getattr(s, k, 0.0)))
+    p.thermal_q = int(getattr(s, "thermal_q", 7))
     return p
 
 
@@ -244,11 +246,16 @@ class Oracle:
         rho, ux, uy, uz, T = [a.reshape(self.shape) for a in out]
         return dict(rho=rho, ux=ux, uy=uy, uz=uz, T=T)
 
+    @property
+    def thermal_q(self):
+        return 19 if int(getattr(self.setup, "thermal_q", 7)) == 19 else 7
+
     def pops(self):
+        q = self.thermal_q
         f = np.empty(self.N * 19)
-        g = np.empty(self.N * 7)
+        g = np.empty(self.N * q)
         self._L.orc_get_pops(self._h, _dp(f), _dp(g))
-        return f.reshape(self.N, 19), g.reshape(self.N, 7)
+        return f.reshape(self.N, 19), g.reshape(self.N, q)
 
     def set_pops(self, f, g):
         f = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)

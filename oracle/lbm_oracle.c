@@ -43,7 +43,10 @@
  *    solid node's fluid neighbours with (phi, drho) from a per-node wettability map
  *    (scheme 1; floored at rho_ave / 10, our addition).
  *  - Options outside the default path: BGK D3Q7 collision (thermal_bgk), isotropic
- *    finite-difference div u away from solid faces (divu_mode 1).
+ *    finite-difference div u away from solid faces (divu_mode 1), and the temperature LB on the
+ *    D3Q19 lattice (thermal_q 19): the BGK equation of Eq. 19 with the D3Q19 weights and
+ *    cs_T^2 = 1/3 (Sec. III.B), chi = (tau_g - 1/2) cs_T^2, grad T = -sum e g / (tau_g cs_T^2)
+ *    (the first moment, as Eq. 45 for D3Q7), the same source Q = w (3/2 phi_s - 1/2 phi_s(t-1)).
  *  - Outflow face: f unknowns copied from the layer inside (zero gradient), g by
  *    Eq. 51 with T fixed at the face temperature.
  *  - Bottom-face hot spot: T_w(x,y) = T_wall[-z] + dT exp(-((x-nx/2)^2+(y-ny/2)^2)/(2 s^2)).
@@ -70,6 +73,7 @@ typedef ORC_REAL real;
 
 #define Q19 19
 #define Q7 7
+#define QMAX 19   /* populations of the thermal lattice at most (D3Q19) */
 
 enum { ORC_PERIODIC = 0, ORC_WALL = 1, ORC_OUTFLOW = 2, ORC_THERMAL_ONLY = 3 };
 
@@ -100,6 +104,7 @@ typedef struct {
     int wall_scheme;         /* 1: virtual density phi rho_ave - drho (floored at rho_ave / 10) from
                                 the fluid neighbours of each solid node, every step */
     double wall_phi, wall_drho, wall_phi_patch, wall_drho_patch;
+    int thermal_q;           /* thermal lattice: 7 (default; 0 means 7) or 19 (Eq. 19 BGK on D3Q19) */
 } orc_params;
 
 typedef struct {
@@ -115,6 +120,7 @@ typedef struct {
     int first;
     double rho_ave;        /* value the next step uses (FP64 mean) */
     real M[Q19 * Q19], Minv[Q19 * Q19];
+    int qt;                /* populations of the thermal lattice (7 or 19) */
     int ok;
 } orc_state;
 
@@ -381,6 +387,24 @@ static real wall_T(const orc_params* p, int face, int x, int y) {
 static int opposite19(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
 static int opposite7(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
 
+/* weights and velocities of the thermal lattice: D3Q7 (w_0 = 1 - d, w_1..6 = d/6, Eq. 21) or
+   D3Q19 (the standard weights 1/3, 1/18, 1/36; Sec. III.B) */
+static void thermal_weights(const orc_state* s, real w[QMAX]) {
+    if (s->qt == 19) {
+        for (int a = 0; a < Q19; ++a) {
+            int e2 = EX[a] * EX[a] + EY[a] * EY[a] + EZ[a] * EZ[a];
+            w[a] = e2 == 0 ? 1.0 / 3.0 : (e2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+        }
+    } else {
+        w[0] = 1.0 - s->p.d;
+        for (int a = 1; a < Q7; ++a) w[a] = s->p.d / 6.0;
+    }
+}
+static void thermal_velocity(const orc_state* s, int a, int e[3]) {
+    if (s->qt == 19) { e[0] = EX[a]; e[1] = EY[a]; e[2] = EZ[a]; }
+    else { e[0] = TX[a]; e[1] = TY[a]; e[2] = TZ[a]; }
+}
+
 /* ---------------------------------------------------------------- API */
 
 /* M and its inverse in FP64, then stored in the state's precision */
@@ -402,9 +426,11 @@ orc_state* orc_create(const orc_params* p) {
     s->f = (real*)malloc(sizeof(real) * N * Q19);
     s->fn = (real*)malloc(sizeof(real) * N * Q19);
     s->fs = (real*)malloc(sizeof(real) * N * Q19);
-    s->g = (real*)malloc(sizeof(real) * N * Q7);
-    s->gn = (real*)malloc(sizeof(real) * N * Q7);
-    s->gp = (real*)malloc(sizeof(real) * N * Q7);
+    if (p->thermal_q != 0 && p->thermal_q != 7 && p->thermal_q != 19) { free(s); return NULL; }
+    s->qt = p->thermal_q == 19 ? 19 : 7;
+    s->g = (real*)malloc(sizeof(real) * N * s->qt);
+    s->gn = (real*)malloc(sizeof(real) * N * s->qt);
+    s->gp = (real*)malloc(sizeof(real) * N * s->qt);
     s->rho = (real*)malloc(sizeof(real) * N);
     s->T = (real*)malloc(sizeof(real) * N);
     s->psi = (real*)malloc(sizeof(real) * N);
@@ -461,10 +487,8 @@ void orc_destroy(orc_state* s) {
 
 /* f = M^-1 m_eq(rho, u0), g = w T (w_0 = 1-d, w_1..6 = d/6, Sec. III.B) */
 int orc_init(orc_state* s, const double* rho, const double* T, const double* u) {
-    const orc_params* p = &s->p;
-    real w7[Q7];
-    w7[0] = 1.0 - p->d;
-    for (int a = 1; a < Q7; ++a) w7[a] = p->d / 6.0;
+    real wT[QMAX];
+    thermal_weights(s, wT);
     double sum = 0.0;
     for (long i = 0; i < s->N; ++i) {
         real uu[3] = {0, 0, 0};
@@ -476,7 +500,7 @@ int orc_init(orc_state* s, const double* rho, const double* T, const double* u) 
             for (int k = 0; k < Q19; ++k) acc += s->Minv[a * Q19 + k] * meq[k];
             s->f[i * Q19 + a] = acc;
         }
-        for (int a = 0; a < Q7; ++a) s->g[i * Q7 + a] = w7[a] * (real)T[i];
+        for (int a = 0; a < s->qt; ++a) s->g[i * s->qt + a] = wT[a] * (real)T[i];
         sum += (double)(real)rho[i];
     }
     s->rho_ave = sum / (real)s->N;
@@ -493,7 +517,7 @@ static int macroscopic(orc_state* s) {
     for (long i = 0; i < N; ++i) {
         real r = 0.0, t = 0.0;
         for (int a = 0; a < Q19; ++a) r += s->f[i * Q19 + a];
-        for (int a = 0; a < Q7; ++a) t += s->g[i * Q7 + a];
+        for (int a = 0; a < s->qt; ++a) t += s->g[i * s->qt + a];
         s->rho[i] = r;
         s->T[i] = t;
         real arg = 2.0 * (p_eos(p, r, t) - r * CS2) / (G_INT * 1.0);   /* Eq. 8, c = 1 */
@@ -566,11 +590,11 @@ static void push_stream(orc_state* s) {
     const orc_params* p = &s->p;
     long N = s->N;
     int n[3] = {p->nx, p->ny, p->nz};
-    real w7[Q7];
-    w7[0] = 1.0 - p->d;
-    for (int a = 1; a < Q7; ++a) w7[a] = p->d / 6.0;
+    const int qt = s->qt;
+    real wT[QMAX];
+    thermal_weights(s, wT);
     for (long i = 0; i < N * Q19; ++i) s->fn[i] = NAN;
-    for (long i = 0; i < N * Q7; ++i) s->gn[i] = NAN;
+    for (long i = 0; i < N * qt; ++i) s->gn[i] = NAN;
 #pragma omp parallel for schedule(static)
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
@@ -594,8 +618,10 @@ static void push_stream(orc_state* s) {
                     }
                 }
                 if (!p->thermal_off) {
-                    for (int a = 0; a < Q7; ++a) {
-                        int c[3] = {x + TX[a], y + TY[a], z + TZ[a]};
+                    for (int a = 0; a < qt; ++a) {
+                        int e[3];
+                        thermal_velocity(s, a, e);
+                        int c[3] = {x + e[0], y + e[1], z + e[2]};
                         int face = -1;
                         for (int k = 0; k < 3; ++k) {
                             if (c[k] >= 0 && c[k] < n[k]) continue;
@@ -605,9 +631,9 @@ static void push_stream(orc_state* s) {
                         }
                         if (face >= 0) {   /* Eq. 51, anti-bounce-back with the face temperature */
                             real Tw = wall_T(p, face, c0[0], c0[1]);
-                            s->gn[i * Q7 + opposite7(a)] = -s->gp[i * Q7 + a] + 2.0 * w7[a] * Tw;
+                            s->gn[i * qt + opposite7(a)] = -s->gp[i * qt + a] + 2.0 * wT[a] * Tw;
                         } else {
-                            s->gn[node_index(p, c[0], c[1], c[2]) * Q7 + a] = s->gp[i * Q7 + a];
+                            s->gn[node_index(p, c[0], c[1], c[2]) * qt + a] = s->gp[i * qt + a];
                         }
                     }
                 }
@@ -632,7 +658,7 @@ static void push_stream(orc_state* s) {
                 }
     }
     if (p->flow_off) memcpy(s->fn, s->f, sizeof(real) * N * Q19);
-    if (p->thermal_off) memcpy(s->gn, s->g, sizeof(real) * N * Q7);
+    if (p->thermal_off) memcpy(s->gn, s->g, sizeof(real) * N * qt);
     real* t;
     t = s->f; s->f = s->fn; s->fn = t;
     t = s->g; s->g = s->gn; s->gn = t;
@@ -646,10 +672,10 @@ static int step_once(orc_state* s) {
     real rho_ave = p->rho_buoy > 0.0 ? (real)p->rho_buoy : (real)s->rho_ave;
     double sum = 0.0;
     for (long i = 0; i < N; ++i) sum += s->rho[i];
-    real w7[Q7];
-    w7[0] = 1.0 - p->d;
-    for (int a = 1; a < Q7; ++a) w7[a] = p->d / 6.0;
-    const real csT2 = p->d / 3.0;
+    const int qt = s->qt;
+    real wT[QMAX];
+    thermal_weights(s, wT);
+    const real csT2 = qt == 19 ? 1.0 / 3.0 : p->d / 3.0;   /* cs_T^2 = d/3 (D3Q7), 1/3 (D3Q19) */
     real Gam_q = 1.0 / p->varsigma_q, Gam_pi = 1.0 / p->varsigma_pi;
     if (p->divu_mode == 1) {
         /* u of every node first (Eq. 10 with the total force), for the finite differences */
@@ -685,17 +711,28 @@ static int step_once(orc_state* s) {
                 real Fu = F[0] * u[0] + F[1] * u[1] + F[2] * u[2];
                 real divu = (-m4neq / p->tau_e + (1.0 - 0.5 / p->tau_e) * S4 - 2.0 * Fu) / (2.0 * rho * CS2);
                 if (p->divu_mode == 1 && !next_to_solid(p, x, y, z)) divu = fd_divergence(p, s->uvec, x, y, z);
-                /* thermal moments, Eq. 38 */
-                real nm[Q7];
-                for (int k = 0; k < Q7; ++k) {
-                    real acc = 0.0;
-                    for (int a = 0; a < Q7; ++a) acc += NMAT[k][a] * s->g[i * Q7 + a];
-                    nm[k] = acc;
-                }
                 real chi = p->lambda_mode ? p->chi_or_lambda / (rho * p->cV) : p->chi_or_lambda;
-                real vsT = chi / csT2 + 0.5;     /* chi = (varsigma_T - 0.5) cs_T^2 dt */
+                real vsT = chi / csT2 + 0.5;     /* chi = (varsigma_T - 0.5) cs_T^2 dt (tau_g on D3Q19) */
                 real gT[3];
-                for (int k = 0; k < 3; ++k) gT[k] = -(nm[1 + k] - 0.0) / (vsT * csT2);   /* Eq. 45 */
+                real nm[Q7];
+                if (qt == 7) {
+                    /* thermal moments, Eq. 38 */
+                    for (int k = 0; k < Q7; ++k) {
+                        real acc = 0.0;
+                        for (int a = 0; a < Q7; ++a) acc += NMAT[k][a] * s->g[i * Q7 + a];
+                        nm[k] = acc;
+                    }
+                    for (int k = 0; k < 3; ++k) gT[k] = -(nm[1 + k] - 0.0) / (vsT * csT2);   /* Eq. 45 */
+                } else {
+                    /* D3Q19: the first moment is all non-equilibrium (sum e g_eq = 0, sum e Q = 0) */
+                    real j[3] = {0.0, 0.0, 0.0};
+                    for (int a = 0; a < Q19; ++a) {
+                        j[0] += EX[a] * s->g[i * Q19 + a];
+                        j[1] += EY[a] * s->g[i * Q19 + a];
+                        j[2] += EZ[a] * s->g[i * Q19 + a];
+                    }
+                    for (int k = 0; k < 3; ++k) gT[k] = -j[k] / (vsT * csT2);
+                }
                 /* Eq. 18 with cV constant: grad(rho cV)/(rho cV) = grad rho / rho.  A frozen flow is
                    a static fluid: u = 0 and div u = 0, and only the conduction term remains */
                 if (p->flow_off) {
@@ -706,17 +743,26 @@ static int step_once(orc_state* s) {
                 for (int k = 0; k < 3; ++k) phis += (chi * grho[k] / rho - u[k]) * gT[k];
                 phis -= T / (rho * p->cV) * dpdT(p, rho) * divu;
                 real phis_old = s->first ? phis : s->phis_prev[i];
-                /* Eq. 42 equilibrium moments and Eq. 43 rates */
-                real neq[Q7] = {T, 0.0, 0.0, 0.0, 3.0 * csT2 * T, 0.0, 0.0};
-                real Gm[Q7] = {1.0, 1.0 / vsT, 1.0 / vsT, 1.0 / vsT, Gam_q, Gam_pi, Gam_pi};
-                if (p->thermal_bgk) Gm[4] = Gm[5] = Gm[6] = 1.0 / vsT;   /* BGK: one rate */
-                real ns[Q7];
-                for (int k = 0; k < Q7; ++k) ns[k] = nm[k] - Gm[k] * (nm[k] - neq[k]);    /* Eq. 39 */
-                for (int a = 0; a < Q7; ++a) {
-                    real acc = 0.0;
-                    for (int k = 0; k < Q7; ++k) acc += NINV6[a][k] / 6.0 * ns[k];
-                    real Qa = 1.5 * w7[a] * phis - 0.5 * w7[a] * phis_old;             /* Eq. 23 */
-                    s->gp[i * Q7 + a] = acc + Qa;                                        /* Eq. 40 */
+                if (qt == 7) {
+                    /* Eq. 42 equilibrium moments and Eq. 43 rates */
+                    real neq[Q7] = {T, 0.0, 0.0, 0.0, 3.0 * csT2 * T, 0.0, 0.0};
+                    real Gm[Q7] = {1.0, 1.0 / vsT, 1.0 / vsT, 1.0 / vsT, Gam_q, Gam_pi, Gam_pi};
+                    if (p->thermal_bgk) Gm[4] = Gm[5] = Gm[6] = 1.0 / vsT;   /* BGK: one rate */
+                    real ns[Q7];
+                    for (int k = 0; k < Q7; ++k) ns[k] = nm[k] - Gm[k] * (nm[k] - neq[k]);    /* Eq. 39 */
+                    for (int a = 0; a < Q7; ++a) {
+                        real acc = 0.0;
+                        for (int k = 0; k < Q7; ++k) acc += NINV6[a][k] / 6.0 * ns[k];
+                        real Qa = 1.5 * wT[a] * phis - 0.5 * wT[a] * phis_old;             /* Eq. 23 */
+                        s->gp[i * Q7 + a] = acc + Qa;                                        /* Eq. 40 */
+                    }
+                } else {
+                    /* Eq. 19 with g_eq = w T and tau_g = vsT */
+                    for (int a = 0; a < Q19; ++a) {
+                        real ga = s->g[i * Q19 + a];
+                        real Qa = 1.5 * wT[a] * phis - 0.5 * wT[a] * phis_old;             /* Eq. 23 */
+                        s->gp[i * Q19 + a] = ga - (ga - wT[a] * T) / vsT + Qa;
+                    }
                 }
                 s->phis[i] = phis;
                 s->divu[i] = divu;
@@ -777,13 +823,14 @@ int orc_moments(orc_state* s, double* rho_o, double* ux, double* uy, double* uz,
 static void to_double(double* dst, const real* src, long n) { for (long k = 0; k < n; ++k) dst[k] = (double)src[k]; }
 static void to_real(real* dst, const double* src, long n) { for (long k = 0; k < n; ++k) dst[k] = (real)src[k]; }
 
+/* f: 19 per node; g: 7 or 19 per node (the thermal lattice) */
 void orc_get_pops(const orc_state* s, double* f, double* g) {
     if (f) to_double(f, s->f, s->N * Q19);
-    if (g) to_double(g, s->g, s->N * Q7);
+    if (g) to_double(g, s->g, s->N * s->qt);
 }
 void orc_set_pops(orc_state* s, const double* f, const double* g) {
     if (f) to_real(s->f, f, s->N * Q19);
-    if (g) to_real(s->g, g, s->N * Q7);
+    if (g) to_real(s->g, g, s->N * s->qt);
 }
 /* diagnostics of the last completed step (pre-streaming values at each node) */
 void orc_get_diag(const orc_state* s, double* divu, double* gradT, double* gradrho,

@@ -147,6 +147,7 @@ class LatticeSetup:
     wall_drho: float = 0.0
     wall_phi_patch: float = 0.0
     wall_drho_patch: float = 0.0
+    thermal_q: int = 7            # thermal lattice: 7 (D3Q7 MRT, Eqs. 37-43) or 19 (Eq. 19 BGK on D3Q19)
 
     @property
     def shape(self):
