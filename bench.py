@@ -489,7 +489,8 @@ def run_mine(args):
     rho, T = init_fields(case)
     stream = torch.cuda.current_stream()
     p = lbm.params_from_setup(s, kernel=KERNEL_CODE[args.kernel], precision=PREC_CODE[args.precision],
-                              use_graph=1, check_nonfinite=0, use_tma=0 if args.kernel == "fused_generic" else 1)
+                              use_graph=1, check_nonfinite=0, use_tma=0 if args.kernel == "fused_generic" else 1,
+                              thermal_q=args.thermal_q)
     if args.precision != "fp32":
         p.rho_ref = float(rho.mean())
         p.T_ref = 0.86 * lbm.lbm_eos_critical(p)[0]
@@ -527,7 +528,7 @@ def run_mine(args):
     k_idx = 1 if kernel_name == "collide" else 0
     k_avg_ms = kms[k_idx] / max(1, kn[k_idx])
     peak, peak_kind = measured_peaks()
-    bpn = BYTES_PER_NODE[args.precision]
+    bpn = BYTES_PER_NODE[args.precision] if args.thermal_q == 7 else (19 + 19) * 4 * 2 + 8   # D3Q19 g: 312 B
     achieved = bpn * N / (k_avg_ms * 1e-3) / 1e9
     traffic = committed_traffic(kernel_name, args.precision, N)
 
@@ -557,6 +558,7 @@ def run_mine(args):
         "dtype": "f32" if args.precision == "fp32" else f"f32 compute, {args.precision} storage",
         "data": "synthetic",
         "config": {"workload": case["name"], "nodes": N, "kernel": kernel_name, "precision": args.precision,
+                   "thermal_lattice": f"D3Q{args.thermal_q}",
                    "plan": None if tuned is None else {"tile": list(lbm.lbm_plan_shapes()[tuned["shape"]]),
                                                        "zchunk": tuned["zchunk"]},
                    "l2": "no flush: working set %.2f GB > 129 MB L2" % (lbm.lbm_workspace_bytes(p) / 1e9),
@@ -572,7 +574,8 @@ def run_mine(args):
         "finite": finite,
     }
     lat.close()
-    if args.precision == "fp32" and args.compare_16bit and args.workload == "pool_boiling" and not args.nx:
+    if args.precision == "fp32" and args.compare_16bit and args.workload == "pool_boiling" and not args.nx \
+            and args.thermal_q == 7:
         line["storage_16bit"] = compare_16bit(lbm, case, rho, T, stream, min(args.steps, 500))
     if args.cpu_baseline and rank == 0 and world == 1:
         line["cpu_baseline"] = {k: v for k, v in cpu_baseline_run(case).items() if k != "seconds"}
@@ -592,6 +595,8 @@ def main():
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--kernel", default="auto", choices=list(KERNEL_CODE))
     ap.add_argument("--precision", default="fp32", choices=list(PREC_CODE))
+    ap.add_argument("--thermal-q", dest="thermal_q", type=int, default=7, choices=[7, 19],
+                    help="temperature lattice: D3Q7 (MRT, default) or D3Q19 (Eq. 19 BGK; generic kernels)")
     ap.add_argument("--workload", default="pool_boiling")
     ap.add_argument("--nx", type=int, default=None, help="override the lattice size (profiling runs)")
     ap.add_argument("--ny", type=int, default=None)

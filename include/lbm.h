@@ -128,6 +128,10 @@ typedef struct {
                                      Needs a -z LBM_BC_WALL and wall_rho = wall_rho_patch = 0 */
     double wall_phi, wall_drho;               /* scheme 1: phi > 0 and drho >= 0 outside the patch */
     double wall_phi_patch, wall_drho_patch;   /* scheme 1: the same inside the patch */
+    int    thermal_q;             /* temperature lattice: 7 (0 also means 7; D3Q7 MRT, Eqs. 37-43) or 19
+                                     (the BGK equation of Eq. 19 on the D3Q19 lattice, its standard
+                                     weights, cs_T^2 = 1/3, Sec. III.B; 38 population slots per node,
+                                     generic and two-pass kernels, no batch) */
 } lbm_params;
 
 /* Fill *p with the workload-independent defaults of Sec. IV: tau_e = 1.25, tau_v = 0.8,

@@ -231,6 +231,8 @@ int check_batch_flag(lbm_batch* b) {
 extern "C" {
 
 int lbm_batch_create(const lbm_params* common, int n_instances, const int* dims, lbm_batch** out) {
+    if (common && common->thermal_q == 19)
+        return fail(LBM_EINVAL, "the batched ensemble runs the D3Q7 temperature lattice only");
     if (!out) return fail(LBM_EINVAL, "out is NULL");
     *out = nullptr;
     if (!common || !dims) return fail(LBM_EINVAL, "common and dims are required");

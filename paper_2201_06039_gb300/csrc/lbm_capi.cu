@@ -53,8 +53,8 @@ Layout layout_of(const lbm_params* p, const DevParams& dp) {
     Layout L;
     size_t N = (size_t)dp.N, pb = pop_bytes(p->precision), off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
-    L.pops[0] = take((size_t)kSlots * dp.Ns * pb);
-    L.pops[1] = take((size_t)kSlots * dp.Ns * pb);
+    L.pops[0] = take((size_t)slots_of(dp.qt) * dp.Ns * pb);
+    L.pops[1] = take((size_t)slots_of(dp.qt) * dp.Ns * pb);
     L.psirho = take(8 * N);
     L.phis = take(4 * N);
     L.sums = take(8 * sizeof(double));          // slots: [0..1] [2..3] rho_ave ping-pong, [4..5] totals
@@ -124,9 +124,12 @@ double critical_T(const lbm_params* p) { return 0.0778 * p->a / (0.45724 * p->b 
 int validate(const lbm_params* p) {
     if (!p) return fail(LBM_EINVAL, "params is NULL");
     if (p->nx < 1 || p->ny < 1 || p->nz < 1) return fail(LBM_EINVAL, "lattice size must be >= 1");
+    if (p->thermal_q != 0 && p->thermal_q != 7 && p->thermal_q != 19)
+        return fail(LBM_EINVAL, "thermal_q must be 7 (D3Q7) or 19 (D3Q19), not %d", p->thermal_q);
+    const int slots = slots_of(p->thermal_q == 19 ? 19 : 7);
     long long Ws = ((long long)p->nx + kGX + 2 + 7) / 8 * 8, Hs = (long long)p->ny + kGY + 2;
-    if ((long long)kSlots * Ws * Hs * p->nz >= (1LL << 31))
-        return fail(LBM_EINVAL, "lattice too large (26 x padded nodes must be < 2^31)");
+    if ((long long)slots * Ws * Hs * p->nz >= (1LL << 31))
+        return fail(LBM_EINVAL, "lattice too large (%d x padded nodes must be < 2^31)", slots);
     int n[3] = {p->nx, p->ny, p->nz};
     for (int f = 0; f < 6; ++f) {
         if (p->bc[f] < 0 || p->bc[f] > 3) return fail(LBM_EINVAL, "bc[%d] = %d is not an lbm_bc", f, p->bc[f]);
@@ -167,6 +170,12 @@ int validate(const lbm_params* p) {
     if (p->divu_mode == 1 && p->kernel == LBM_KERNEL_FUSED)
         return fail(LBM_EINVAL, "finite-difference div u runs on the two-pass kernels (kernel AUTO or TWO_PASS)");
     if (p->hot_dT != 0.0 && !(p->hot_sigma > 0)) return fail(LBM_EINVAL, "hot_sigma must be positive");
+    if (p->thermal_q == 19) {
+        if (p->precision != LBM_FP32) return fail(LBM_EINVAL, "the D3Q19 temperature lattice needs FP32 storage");
+        if (p->thermal_bgk) return fail(LBM_EINVAL, "thermal_bgk selects the D3Q7 BGK collision; D3Q19 is BGK already");
+        if (p->wall_scheme == 1 || p->wall_rho > 0.0)
+            return fail(LBM_EINVAL, "the wetting wall runs with the D3Q7 temperature lattice only");
+    }
     return LBM_OK;
 }
 
@@ -204,6 +213,7 @@ DevParams make_dev(const lbm_params* p) {
     d.gx = (float)p->g[0]; d.gy = (float)p->g[1]; d.gz = (float)p->g[2];
     d.rho_buoy = p->rho_buoy > 0.0 ? (float)p->rho_buoy : 0.f;
     d.flow_off = p->flow_off; d.thermal_off = p->thermal_off;
+    d.qt = p->thermal_q == 19 ? 19 : 7;
     d.test_stall = p->test_stall ? 1 : 0;
     d.thermal_bgk = p->thermal_bgk ? 1 : 0;
     d.divu_mode = p->divu_mode;
@@ -699,7 +709,7 @@ struct CkptHeader {
     long long steps, pop_bytes, phis_bytes;
 };
 const char kCkptMagic[8] = {'G', 'B', '3', 'L', 'B', 'M', 'C', 'K'};
-size_t ckpt_pop_bytes(const lbm_ctx* c) { return (size_t)kSlots * c->dp.Ns * pop_bytes(c->p.precision); }
+size_t ckpt_pop_bytes(const lbm_ctx* c) { return (size_t)slots_of(c->dp.qt) * c->dp.Ns * pop_bytes(c->p.precision); }
 }  // namespace
 
 size_t lbm_state_bytes(const lbm_ctx* c) {

@@ -45,6 +45,10 @@ __host__ __device__ constexpr int fslot(int a) {
 }
 __host__ __device__ constexpr int gslot(int a) { return a <= 4 ? 9 + a : a == 5 ? 19 : 25; }
 constexpr int kSlots = 26;
+// Temperature LB on the D3Q19 lattice (thermal_q 19): g_0..g_6 share the D3Q7 velocities and slots,
+// g_7..g_18 take 12 more slots after them.
+__host__ __device__ constexpr int gslot19(int a) { return a <= 6 ? gslot(a) : kSlots + (a - 7); }
+__host__ __device__ constexpr int slots_of(int qt) { return qt == 19 ? kSlots + 12 : kSlots; }
 constexpr int kGX = 8, kGY = 2;   // storage offsets: 8 columns (2 ghosts; rows stay 32-byte aligned), 2 rows
 
 // Lattice constants and model parameters, converted once on the host.
@@ -85,6 +89,7 @@ struct DevParams {
     float shift_f[19];        // storage shift w_a rho_ref (16-bit storage only, else 0)
     float shift_g[7];         // storage shift w_a T_ref
     int* check_flag;          // the context's flag word (bounds-checked builds record violations here)
+    int qt;                   // temperature lattice: 7 (D3Q7 MRT) or 19 (Eq. 19 BGK on D3Q19)
 };
 
 // Debug builds (-DLBM_BOUNDS_CHECK): every population and field index of the update, and the
@@ -600,5 +605,157 @@ __device__ __forceinline__ float collide_g(const DevParams& P, float g[7], float
     g[4] = h4 + q1; g[5] = h5 + q1; g[6] = h6 + q1;
     return phis;
 }
+
+// ---------------------------------------------------------------- D3Q19 temperature LB
+// The BGK equation of Eq. 19 on the D3Q19 lattice: g_eq = w_a T with the standard weights,
+// cs_T^2 = 1/3, chi = (tau_g - 1/2) cs_T^2; grad T = -sum e_a g_a / (tau_g cs_T^2) from the
+// pre-collision first moment (the D3Q19 form of Eq. 45: sum e g_eq = 0 and sum e Q = 0).
+__host__ __device__ constexpr float w19(int a) { return a == 0 ? 1.f / 3.f : a <= 6 ? 1.f / 18.f : 1.f / 36.f; }
+
+// Pull of g_a on the D3Q19 velocities: g_a(x, t+1) = g+_a(x - e_a, t), or, where x - e_a lies
+// behind a face that is not periodic for g, Eq. 51 at the node itself:
+// g_a(x, t+1) = -g+_abar(x, t) + 2 w_a T_w (the face of the highest axis crossed gives T_w).
+template <typename S, int A>
+__device__ __forceinline__ float pull_g19_one(const DevParams& P, const S* __restrict__ src, int i, int x, int y,
+                                              int z, const Nbr& n) {
+    constexpr int ex = ex19(A), ey = ey19(A), ez = ez19(A);
+    // faces crossed by the source x - e_a: ex > 0 -> -x (bit 0), ex < 0 -> +x (bit 1), etc.
+    const bool cx = ex > 0 ? (n.gabb & 1u) : ex < 0 ? (n.gabb & 2u) : 0u;
+    const bool cy = ey > 0 ? (n.gabb & 4u) : ey < 0 ? (n.gabb & 8u) : 0u;
+    const bool cz = ez > 0 ? (n.gabb & 16u) : ez < 0 ? (n.gabb & 32u) : 0u;
+    if (A != 0 && (cx || cy || cz)) {
+        const int face = cz ? (ez > 0 ? 4 : 5) : cy ? (ey > 0 ? 2 : 3) : (ex > 0 ? 0 : 1);
+        const float gp = Codec<S>::load(src + (size_t)gslot19(opp(A)) * P.Ns + bidx(P, i, P.Ns), 0.f);
+        return -gp + 2.f * w19(A) * wall_T(P, face, x, y);
+    }
+    const int s = sidx(P, src_c(ex, x, n.xm, n.xp), src_c(ey, y, n.ym, n.yp), src_c(ez, z, n.zm, n.zp));
+    return Codec<S>::load(src + (size_t)gslot19(A) * P.Ns + bidx(P, s, P.Ns), 0.f);
+}
+
+template <typename S>
+__device__ __forceinline__ void load_g19(const DevParams& P, const S* __restrict__ src, int pull, int i, int x,
+                                         int y, int z, const Nbr& n, float g[19]) {
+    if (pull) {
+#define GB300_PULL(A) g[A] = pull_g19_one<S, A>(P, src, i, x, y, z, n);
+        GB300_PULL(0) GB300_PULL(1) GB300_PULL(2) GB300_PULL(3) GB300_PULL(4) GB300_PULL(5)
+        GB300_PULL(6) GB300_PULL(7) GB300_PULL(8) GB300_PULL(9) GB300_PULL(10) GB300_PULL(11)
+        GB300_PULL(12) GB300_PULL(13) GB300_PULL(14) GB300_PULL(15) GB300_PULL(16) GB300_PULL(17)
+        GB300_PULL(18)
+#undef GB300_PULL
+    } else {
+#pragma unroll
+        for (int a = 0; a < 19; ++a) g[a] = Codec<S>::load(src + (size_t)gslot19(a) * P.Ns + bidx(P, i, P.Ns), 0.f);
+    }
+}
+
+// the 19 f and 19 g of a node at storage index i (FP32 storage only)
+template <typename S>
+__device__ __forceinline__ void store_slots19(const DevParams& P, S* __restrict__ dst, int i, const float f[19],
+                                              const float g[19]) {
+    S* q = dst + bidx(P, i, P.Ns);
+#pragma unroll
+    for (int a = 0; a < 19; ++a) Codec<S>::store(q + (size_t)fslot(a) * P.Ns, f[a], 0.f);
+#pragma unroll
+    for (int a = 0; a < 19; ++a) Codec<S>::store(q + (size_t)gslot19(a) * P.Ns, g[a], 0.f);
+}
+
+// In: post-streaming g (19), rho, T = sum g, the flow quantities o, grad rho, phi_s(t-1).
+// Out: g+ = g - (g - w T) / tau_g + Q (Eq. 19, Eq. 23) in place; returns phi_s (Eq. 18).
+__device__ __forceinline__ float collide_g19(const DevParams& P, float g[19], float rho, float T,
+                                             const NodeOut& o, float grx, float gry, float grz,
+                                             float phis_prev, int first) {
+    const float jx = ((g[1] - g[2]) + (g[7] - g[8])) + ((g[9] - g[10]) + (g[11] - g[12])) + (g[13] - g[14]);
+    const float jy = ((g[3] - g[4]) + (g[7] - g[8])) + ((g[10] - g[9]) + (g[15] - g[16])) + (g[17] - g[18]);
+    const float jz = ((g[5] - g[6]) + (g[11] - g[12])) + ((g[14] - g[13]) + (g[15] - g[16])) + (g[18] - g[17]);
+    const float inv_rho = o.inv_rho;
+    const float chi = P.lambda_mode ? P.chi_or_lambda * inv_rho * P.inv_cV : P.chi_or_lambda;
+    const float tau = __fmaf_rn(3.f, chi, 0.5f);             // chi = (tau_g - 1/2) / 3
+    const float inv_tau = __fdividef(1.f, tau);
+    const float k = -3.f * inv_tau;                          // -1 / (tau_g cs_T^2)
+    const float gTx = k * jx, gTy = k * jy, gTz = k * jz;
+    float phis;
+    if (!P.flow_off) {
+        phis = __fmaf_rn(chi * grz * inv_rho - o.uz, gTz,
+                         __fmaf_rn(chi * gry * inv_rho - o.uy, gTy, __fmul_rn(chi * grx * inv_rho - o.ux, gTx)));
+        phis -= __fdividef(T * P.R_over_cV, 1.f - P.b * rho) * o.divu;
+    } else {
+        phis = __fmaf_rn(chi * grz * inv_rho, gTz, __fmaf_rn(chi * gry * inv_rho, gTy, __fmul_rn(chi * grx * inv_rho, gTx)));
+    }
+    const float C = first ? phis : phis_prev;
+    const float qs = __fmaf_rn(-0.5f, C, __fmul_rn(1.5f, phis));
+    // g+_a = g_a - (g_a - w_a T) / tau + w_a qs for a >= 1; g+_0 = T + qs - sum of the others, so
+    // that sum g+ = T + qs holds free of rounding drift
+    float s = 0.f;
+#pragma unroll
+    for (int a = 1; a < 19; ++a) {
+        const float wa = w19(a);
+        g[a] = __fmaf_rn(wa, qs, __fmaf_rn(-inv_tau, __fsub_rn(g[a], __fmul_rn(wa, T)), g[a]));
+        s += g[a];
+    }
+    g[0] = (T + qs) - s;
+    return phis;
+}
+
+// ---------------------------------------------------------------- thermal lattice traits
+// The generic and two-pass kernels take the temperature lattice as a template parameter: QT = 7
+// (D3Q7 MRT, Eqs. 38-43) or 19 (Eq. 19 BGK on D3Q19, FP32 storage).
+template <int QT> struct Therm;
+template <> struct Therm<7> {
+    static constexpr int Q = 7;
+    template <typename S>
+    static __device__ __forceinline__ void load(const DevParams& P, const S* src, int pull, int i, int x, int y, int z,
+                                                const Nbr& n, float g[7]) {
+        load_g<S>(P, src, pull, i, x, y, z, n, g);
+    }
+    static __device__ __forceinline__ float sum(const float g[7]) { return sum7(g); }
+    static __device__ __forceinline__ float collide(const DevParams& P, float g[7], float rho, float T,
+                                                    const NodeOut& o, float grx, float gry, float grz,
+                                                    float phis_prev, int first) {
+        return collide_g(P, g, rho, T, o, grx, gry, grz, phis_prev, first);
+    }
+    template <typename S>
+    static __device__ __forceinline__ void store(const DevParams& P, S* dst, int i, const float f[19],
+                                                 const float g[7]) {
+        store_slots<S>(P, dst, i, f, g);
+    }
+    static __device__ __forceinline__ void equilibrium(const DevParams& P, float T, float g[7]) {
+        g[0] = P.w0 * T;
+#pragma unroll
+        for (int a = 1; a < 7; ++a) g[a] = P.w1 * T;
+    }
+    template <typename S>
+    static __device__ __forceinline__ void stored(const DevParams& P, const S* src, int i, float g[7]) {
+#pragma unroll
+        for (int a = 0; a < 7; ++a) g[a] = Codec<S>::load(src + (size_t)gslot(a) * P.Ns + bidx(P, i, P.Ns), P.shift_g[a]);
+    }
+};
+template <> struct Therm<19> {
+    static constexpr int Q = 19;
+    template <typename S>
+    static __device__ __forceinline__ void load(const DevParams& P, const S* src, int pull, int i, int x, int y, int z,
+                                                const Nbr& n, float g[19]) {
+        load_g19<S>(P, src, pull, i, x, y, z, n, g);
+    }
+    static __device__ __forceinline__ float sum(const float g[19]) { return sum19(g); }
+    static __device__ __forceinline__ float collide(const DevParams& P, float g[19], float rho, float T,
+                                                    const NodeOut& o, float grx, float gry, float grz,
+                                                    float phis_prev, int first) {
+        return collide_g19(P, g, rho, T, o, grx, gry, grz, phis_prev, first);
+    }
+    template <typename S>
+    static __device__ __forceinline__ void store(const DevParams& P, S* dst, int i, const float f[19],
+                                                 const float g[19]) {
+        store_slots19<S>(P, dst, i, f, g);
+    }
+    static __device__ __forceinline__ void equilibrium(const DevParams&, float T, float g[19]) {
+#pragma unroll
+        for (int a = 0; a < 19; ++a) g[a] = w19(a) * T;
+    }
+    template <typename S>
+    static __device__ __forceinline__ void stored(const DevParams& P, const S* src, int i, float g[19]) {
+#pragma unroll
+        for (int a = 0; a < 19; ++a) g[a] = Codec<S>::load(src + (size_t)gslot19(a) * P.Ns + bidx(P, i, P.Ns), 0.f);
+    }
+};
 
 }  // namespace gb300lbm

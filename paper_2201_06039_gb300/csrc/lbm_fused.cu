@@ -30,14 +30,15 @@ namespace {
 constexpr int TX = 32;
 constexpr int kTY = 8;
 
-template <int TY> struct FusedShape {
+template <int TY, int QT = 7> struct FusedShape {
     static constexpr int kInterior = TX * TY;
+    static constexpr int kPops = 19 + QT;   // populations of a node (f and the thermal lattice's g)
     static constexpr int kHaloNodes = 2 * (TX + 2) + 2 * TY;
     static constexpr int kHaloThreads = ((kHaloNodes + 31) / 32) * 32;
     static constexpr int kThreads = kInterior + kHaloThreads;
     static constexpr int kRingW = TX + 2, kRingH = TY + 2;
     static constexpr int kRingPlane = kRingW * kRingH;
-    static constexpr size_t kStageFloats = 26 * kInterior;
+    static constexpr size_t kStageFloats = (size_t)kPops * kInterior;
     static constexpr size_t kSmemBytes = 2 * kStageFloats * sizeof(float) + 3 * kRingPlane * sizeof(float2);
 };
 
@@ -163,12 +164,12 @@ __device__ void finish_sums(const double2* partial, int n, unsigned* counter, do
 // One tile column: the (x, y) tile at (x0, y0), planes [z0, z1), by all threads of the block.
 // Adds the tile's rho and T to the Kahan pairs (r_sum, r_c), (t_sum, t_c) of the owner threads
 // and ORs a non-finite / psi-domain failure into bad.
-template <typename S, int TY, bool kWet>
+template <typename S, int TY, bool kWet, int QT = 7>
 __device__ __forceinline__ void fused_column(const DevParams& P, const S* __restrict__ src, S* __restrict__ dst,
                                              int pull_f, int pull_g, float rho_ave, float* __restrict__ phis,
                                              int first, int x0, int y0, int z0, int z1, float* stage, float2* ring,
                                              float& r_sum, float& r_c, float& t_sum, float& t_c, int& bad) {
-    using Sh = FusedShape<TY>;
+    using Sh = FusedShape<TY, QT>;
     const int tid = threadIdx.x;
     int lx, ly;
     slot_of<TY>(tid, lx, ly);
@@ -190,10 +191,10 @@ __device__ __forceinline__ void fused_column(const DevParams& P, const S* __rest
         const int mz = map_coord(zp, P.nz, P.bc[4], P.bc[5]);
         const int i = sidx(P, mx, my, mz);
         Nbr n = make_nbr(P, mx, my, mz);
-        float f[19], g[7];
+        float f[19], g[QT];
         load_f<S>(P, src, pull_f, i, mx, my, mz, n, f);
-        load_g<S>(P, src, pull_g, i, mx, my, mz, n, g);
-        float rho = sum19(f), T = sum7(g);
+        Therm<QT>::template load<S>(P, src, pull_g, i, mx, my, mz, n, g);
+        float rho = sum19(f), T = Therm<QT>::sum(g);
         float psi2 = psi_squared(P, rho, T);
         ring[((zp + 3) % 3) * Sh::kRingPlane + slot] = make_float2(psi_of(psi2), rho);
         if (owner && in_chunk) {
@@ -201,7 +202,7 @@ __device__ __forceinline__ void fused_column(const DevParams& P, const S* __rest
 #pragma unroll
             for (int a = 0; a < 19; ++a) st[a * Sh::kInterior] = f[a];
 #pragma unroll
-            for (int a = 0; a < 7; ++a) st[(19 + a) * Sh::kInterior] = g[a];
+            for (int a = 0; a < QT; ++a) st[(19 + a) * Sh::kInterior] = g[a];
             kahan_add(r_sum, r_c, rho);
             kahan_add(t_sum, t_c, T);
             bad |= !(psi2 > 0.f) || !isfinite(rho) || !isfinite(T);
@@ -213,12 +214,12 @@ __device__ __forceinline__ void fused_column(const DevParams& P, const S* __rest
         const int x = gx, y = gy;
         const int i = sidx(P, x, y, z), d = (int)bidx(P, node_of(P, x, y, z), P.N);
         const float* st = stage + ((z - z0) & 1) * Sh::kStageFloats + tid;
-        float f[19], g[7];
+        float f[19], g[QT];
 #pragma unroll
         for (int a = 0; a < 19; ++a) f[a] = st[a * Sh::kInterior];
 #pragma unroll
-        for (int a = 0; a < 7; ++a) g[a] = st[(19 + a) * Sh::kInterior];
-        float rho = sum19(f), T = sum7(g);
+        for (int a = 0; a < QT; ++a) g[a] = st[(19 + a) * Sh::kInterior];
+        float rho = sum19(f), T = Therm<QT>::sum(g);
         const float2* rm = ring + ((z + 2) % 3) * Sh::kRingPlane;
         const float2* r0 = ring + (z % 3) * Sh::kRingPlane;
         const float2* rp = ring + ((z + 1) % 3) * Sh::kRingPlane;
@@ -227,19 +228,15 @@ __device__ __forceinline__ void fused_column(const DevParams& P, const S* __rest
                                       Sh::kRingW);
         const Forces F = total_force(P, me.x, rs.Fx, rs.Fy, rs.Fz, rho - rho_ave);
         NodeOut o = collide_f(P, f, rho, F.Fx, F.Fy, F.Fz, F.Fm2, me.x * me.x);
-        float ph = collide_g(P, g, rho, T, o, rs.gx, rs.gy, rs.gz, phis[d], first);
+        float ph = Therm<QT>::collide(P, g, rho, T, o, rs.gx, rs.gy, rs.gz, phis[d], first);
         // frozen fields keep their stored values (no streaming, no collision)
         if (P.flow_off) {
 #pragma unroll
             for (int a = 0; a < 19; ++a)
                 f[a] = Codec<S>::load(src + (size_t)fslot(a) * P.Ns + bidx(P, i, P.Ns), P.shift_f[a]);
         }
-        if (P.thermal_off) {
-#pragma unroll
-            for (int a = 0; a < 7; ++a)
-                g[a] = Codec<S>::load(src + (size_t)gslot(a) * P.Ns + bidx(P, i, P.Ns), P.shift_g[a]);
-        }
-        store_node<S>(P, dst, i, x, y, z, f, g);
+        if (P.thermal_off) Therm<QT>::template stored<S>(P, src, i, g);
+        Therm<QT>::template store<S>(P, dst, i, f, g);
         phis[d] = ph;
     };
 
@@ -254,12 +251,12 @@ __device__ __forceinline__ void fused_column(const DevParams& P, const S* __rest
     }
 }
 
-template <typename S, int TY>
-__global__ void __launch_bounds__(FusedShape<TY>::kThreads, 2)
+template <typename S, int TY, int QT>
+__global__ void __launch_bounds__(FusedShape<TY, QT>::kThreads, 2)
 k_fused(DevParams P, const S* __restrict__ src, S* __restrict__ dst, int pull_f, int pull_g,
         const double* __restrict__ sums_cur, double2* partial, unsigned* counter, double* sums_next,
         float* __restrict__ phis, int* flag, int first, int zchunk) {
-    using Sh = FusedShape<TY>;
+    using Sh = FusedShape<TY, QT>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     float* stage = reinterpret_cast<float*>(smem_raw);                       // [2][26][TY][32]
     float2* ring = reinterpret_cast<float2*>(stage + 2 * Sh::kStageFloats);  // [3][TY+2][34]
@@ -271,7 +268,7 @@ k_fused(DevParams P, const S* __restrict__ src, S* __restrict__ dst, int pull_f,
     float r_sum = 0.f, r_c = 0.f, t_sum = 0.f, t_c = 0.f;
     int bad = 0;
     const float rho_ave = buoyancy_ref(P, sums_cur[0], P.inv_N);
-    fused_column<S, TY, true>(P, src, dst, pull_f, pull_g, rho_ave, phis, first, blockIdx.x * TX, blockIdx.y * TY, z0,
+    fused_column<S, TY, true, QT>(P, src, dst, pull_f, pull_g, rho_ave, phis, first, blockIdx.x * TX, blockIdx.y * TY, z0,
                         min(P.nz, z0 + zchunk), stage, ring, r_sum, r_c, t_sum, t_c, bad);
 
     if (__syncthreads_or(bad) && tid == 0) atomicOr(flag, 1);
@@ -1056,7 +1053,7 @@ cudaError_t launch_ghosts(const DevParams& P, int precision, void* pops, cudaStr
 }
 
 bool tma_eligible(const DevParams& P, int precision) {
-    return precision >= 0 && precision <= 2 && P.nx >= 4 && P.ny >= 4 && f_wraps(P.bc[0]) && f_wraps(P.bc[1]) &&
+    return precision >= 0 && precision <= 2 && P.qt == 7 && P.nx >= 4 && P.ny >= 4 && f_wraps(P.bc[0]) && f_wraps(P.bc[1]) &&
            f_wraps(P.bc[2]) && f_wraps(P.bc[3]) && !P.flow_off && !P.thermal_off && (!P.wet || precision == 0);
 }
 
@@ -1133,19 +1130,26 @@ cudaError_t launch_fused(const DevParams& P, int precision, const StateBufs& B, 
     const int zc = zchunk_generic(P, tiles_x * tiles_y);
     dim3 grid(tiles_x, tiles_y, (P.nz + zc - 1) / zc);
     dim3 block(Sh::kThreads);
-#define GB300_FUSED(S)                                                                                          \
+#define GB300_FUSED(S, QT)                                                                                      \
     {                                                                                                          \
-        e = cudaFuncSetAttribute(k_fused<S, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::kSmemBytes); \
+        using ShQ = FusedShape<kTY, QT>;                                                                       \
+        e = cudaFuncSetAttribute(k_fused<S, kTY, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
+                                 (int)ShQ::kSmemBytes);                                                        \
         if (e != cudaSuccess) return e;                                                                        \
-        k_fused<S, kTY><<<grid, block, Sh::kSmemBytes, s>>>(P, (const S*)B.src, (S*)B.dst, B.pull_f, B.pull_g,  \
-                                                            sums_cur, B.partial, B.counter, sums_next, B.phis,  \
-                                                            B.flag, first, zc);                                \
+        k_fused<S, kTY, QT><<<grid, block, ShQ::kSmemBytes, s>>>(P, (const S*)B.src, (S*)B.dst, B.pull_f,        \
+                                                                B.pull_g, sums_cur, B.partial, B.counter,      \
+                                                                sums_next, B.phis, B.flag, first, zc);         \
     }
-    switch (precision) {
-    case 0: GB300_FUSED(float) break;
-    case 1: GB300_FUSED(__nv_bfloat16) break;
-    case 2: GB300_FUSED(__half) break;
-    default: return cudaErrorInvalidValue;
+    if (P.qt == 19) {   // the D3Q19 temperature lattice: FP32 storage only
+        if (precision != 0) return cudaErrorInvalidValue;
+        GB300_FUSED(float, 19)
+    } else {
+        switch (precision) {
+        case 0: GB300_FUSED(float, 7) break;
+        case 1: GB300_FUSED(__nv_bfloat16, 7) break;
+        case 2: GB300_FUSED(__half, 7) break;
+        default: return cudaErrorInvalidValue;
+        }
     }
 #undef GB300_FUSED
     if (e != cudaSuccess) return e;

@@ -59,7 +59,7 @@ __device__ void grid_sum2(double a, double b, double2* partial, unsigned* counte
 }
 
 // ---------------------------------------------------------------- init
-template <typename S>
+template <typename S, int QT>
 __global__ void __launch_bounds__(TPB) k_init(DevParams P, S* __restrict__ pops, const float* __restrict__ rho,
                                              const float* __restrict__ T, const float* __restrict__ u) {
     int x = blockIdx.x * TPB_X + threadIdx.x, y = blockIdx.y * TPB_Y + threadIdx.y, z = blockIdx.z;
@@ -68,16 +68,14 @@ __global__ void __launch_bounds__(TPB) k_init(DevParams P, S* __restrict__ pops,
     float r = rho[d], t = T[d];
     float ux = 0.f, uy = 0.f, uz = 0.f;
     if (u) { ux = u[d]; uy = u[P.N + d]; uz = u[2 * P.N + d]; }
-    float fe[19], ge[7];
+    float fe[19], ge[QT];
     feq(r, ux, uy, uz, fe);
-    ge[0] = P.w0 * t;
-#pragma unroll
-    for (int a = 1; a < 7; ++a) ge[a] = P.w1 * t;
-    store_node<S>(P, pops, sidx(P, x, y, z), x, y, z, fe, ge);
+    Therm<QT>::equilibrium(P, t, ge);
+    Therm<QT>::template store<S>(P, pops, sidx(P, x, y, z), fe, ge);
 }
 
 // ---------------------------------------------------------------- psi / EOS pass (S1-S2)
-template <typename S>
+template <typename S, int QT>
 __global__ void __launch_bounds__(TPB) k_psi(DevParams P, const S* __restrict__ fs, int pull_f, int pull_g, float2* __restrict__ psirho,
                                             double2* partial, unsigned* counter, double* sums, int* flag) {
     int x = blockIdx.x * TPB_X + threadIdx.x, y = blockIdx.y * TPB_Y + threadIdx.y, z = blockIdx.z;
@@ -86,10 +84,10 @@ __global__ void __launch_bounds__(TPB) k_psi(DevParams P, const S* __restrict__ 
     if (x < P.nx && y < P.ny) {
         int i = sidx(P, x, y, z);
         Nbr n = make_nbr(P, x, y, z);
-        float f[19], g[7];
+        float f[19], g[QT];
         load_f<S>(P, fs, pull_f, i, x, y, z, n, f);
-        load_g<S>(P, fs, pull_g, i, x, y, z, n, g);
-        float rho = sum19(f), T = sum7(g);
+        Therm<QT>::template load<S>(P, fs, pull_g, i, x, y, z, n, g);
+        float rho = sum19(f), T = Therm<QT>::sum(g);
         float psi2 = psi_squared(P, rho, T);
         bad = !(psi2 > 0.f) || !isfinite(rho) || !isfinite(T);
         psirho[bidx(P, node_of(P, x, y, z), P.N)] = make_float2(psi_of(psi2), rho);
@@ -198,7 +196,7 @@ __device__ __forceinline__ float fd_divergence(const DevParams& P, const float4*
 }
 
 // ---------------------------------------------------------------- stream-collide pass (S3-S12)
-template <typename S>
+template <typename S, int QT>
 __global__ void __launch_bounds__(TPB) k_collide(DevParams P, const S* __restrict__ fs, S* __restrict__ fd,
                                                 int pull_f, int pull_g,
                                                 const float2* __restrict__ psirho, const double* __restrict__ sums_cur,
@@ -207,32 +205,29 @@ __global__ void __launch_bounds__(TPB) k_collide(DevParams P, const S* __restric
     if (x >= P.nx || y >= P.ny) return;
     int i = sidx(P, x, y, z), d = (int)bidx(P, node_of(P, x, y, z), P.N);
     Nbr n = make_nbr(P, x, y, z);
-    float f[19], g[7];
+    float f[19], g[QT];
     load_f<S>(P, fs, pull_f, i, x, y, z, n, f);
-    load_g<S>(P, fs, pull_g, i, x, y, z, n, g);
-    float rho = sum19(f), T = sum7(g);
+    Therm<QT>::template load<S>(P, fs, pull_g, i, x, y, z, n, g);
+    float rho = sum19(f), T = Therm<QT>::sum(g);
     float2 me = __ldg(psirho + d);
     Stencil st = stencil(P, psirho, x, y, z, n);
     float rho_ave = buoyancy_ref(P, sums_cur[0], P.inv_N);
     const Forces F = total_force(P, me.x, st.x.x, st.y.x, st.z.x, rho - rho_ave);
     NodeOut o = collide_f(P, f, rho, F.Fx, F.Fy, F.Fz, F.Fm2, me.x * me.x);
     if (vel && !next_to_solid(P, x, y, z)) o.divu = fd_divergence(P, vel, x, y, z, n);   // divu_mode 1
-    float ph = collide_g(P, g, rho, T, o, st.x.y, st.y.y, st.z.y, phis[d], first);
+    float ph = Therm<QT>::collide(P, g, rho, T, o, st.x.y, st.y.y, st.z.y, phis[d], first);
     // frozen fields keep their stored values (no streaming, no collision)
     if (P.flow_off) {
 #pragma unroll
         for (int a = 0; a < 19; ++a) f[a] = Codec<S>::load(fs + (size_t)fslot(a) * P.Ns + i, P.shift_f[a]);
     }
-    if (P.thermal_off) {
-#pragma unroll
-        for (int a = 0; a < 7; ++a) g[a] = Codec<S>::load(fs + (size_t)gslot(a) * P.Ns + i, P.shift_g[a]);
-    }
-    store_node<S>(P, fd, i, x, y, z, f, g);
+    if (P.thermal_off) Therm<QT>::template stored<S>(P, fs, i, g);
+    Therm<QT>::template store<S>(P, fd, i, f, g);
     phis[d] = ph;
 }
 
 // ---------------------------------------------------------------- moments (lbm_get_moments)
-template <typename S>
+template <typename S, int QT>
 __global__ void __launch_bounds__(TPB) k_moments(DevParams P, const S* __restrict__ fs, int pull_f, int pull_g, const float2* __restrict__ psirho,
                                                 const double* __restrict__ sums_cur, float* __restrict__ orho,
                                                 float* __restrict__ oux, float* __restrict__ ouy,
@@ -241,10 +236,10 @@ __global__ void __launch_bounds__(TPB) k_moments(DevParams P, const S* __restric
     if (x >= P.nx || y >= P.ny) return;
     int i = sidx(P, x, y, z);
     Nbr n = make_nbr(P, x, y, z);
-    float f[19], g[7];
+    float f[19], g[QT];
     load_f<S>(P, fs, pull_f, i, x, y, z, n, f);
-    load_g<S>(P, fs, pull_g, i, x, y, z, n, g);
-    float rho = sum19(f), T = sum7(g);
+    Therm<QT>::template load<S>(P, fs, pull_g, i, x, y, z, n, g);
+    float rho = sum19(f), T = Therm<QT>::sum(g);
     i = node_of(P, x, y, z);
     float jx = (f[1] - f[2]) + (f[7] - f[8]) + (f[9] - f[10]) + (f[11] - f[12]) + (f[13] - f[14]);
     float jy = (f[3] - f[4]) + (f[7] - f[8]) - (f[9] - f[10]) + (f[15] - f[16]) + (f[17] - f[18]);
@@ -293,17 +288,28 @@ int max_partials(const DevParams& P) {
     case 2: { using S = __half; CALL; break; }                               \
     default: return cudaErrorInvalidValue;                                   \
     }
+// storage type and temperature lattice (QT = 19 with FP32 storage only)
+#define GB300_DISPATCH_QT(P, prec, CALL)                                     \
+    if ((P).qt == 19) {                                                      \
+        if (prec != 0) return cudaErrorInvalidValue;                         \
+        using S = float;                                                     \
+        constexpr int QT = 19;                                               \
+        CALL;                                                                \
+    } else {                                                                 \
+        constexpr int QT = 7;                                                \
+        GB300_DISPATCH(prec, CALL)                                           \
+    }
 
 cudaError_t launch_init(const DevParams& P, int precision, void* pops, const float* rho, const float* T,
                         const float* u, cudaStream_t s) {
     dim3 blk(TPB_X, TPB_Y);
-    GB300_DISPATCH(precision, (k_init<S><<<grid_of(P), blk, 0, s>>>(P, (S*)pops, rho, T, u)));
+    GB300_DISPATCH_QT(P, precision, (k_init<S, QT><<<grid_of(P), blk, 0, s>>>(P, (S*)pops, rho, T, u)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_psi(const DevParams& P, int precision, const StateBufs& B, double* sums, cudaStream_t s) {
     dim3 blk(TPB_X, TPB_Y);
-    GB300_DISPATCH(precision, (k_psi<S><<<grid_of(P), blk, 0, s>>>(P, (const S*)B.src, B.pull_f, B.pull_g, B.psirho,
+    GB300_DISPATCH_QT(P, precision, (k_psi<S, QT><<<grid_of(P), blk, 0, s>>>(P, (const S*)B.src, B.pull_f, B.pull_g, B.psirho,
                                                                     B.partial, B.counter, sums, B.flag)));
     return cudaGetLastError();
 }
@@ -311,7 +317,7 @@ cudaError_t launch_psi(const DevParams& P, int precision, const StateBufs& B, do
 cudaError_t launch_collide(const DevParams& P, int precision, const StateBufs& B, const double* sums_cur,
                            int first, cudaStream_t s) {
     dim3 blk(TPB_X, TPB_Y);
-    GB300_DISPATCH(precision, (k_collide<S><<<grid_of(P), blk, 0, s>>>(P, (const S*)B.src, (S*)B.dst, B.pull_f,
+    GB300_DISPATCH_QT(P, precision, (k_collide<S, QT><<<grid_of(P), blk, 0, s>>>(P, (const S*)B.src, (S*)B.dst, B.pull_f,
                                                                         B.pull_g, B.psirho, sums_cur, B.phis, first,
                                                                         B.vel)));
     return cudaGetLastError();
@@ -395,7 +401,7 @@ cudaError_t launch_velocity(const DevParams& P, int precision, const StateBufs& 
 cudaError_t launch_moments(const DevParams& P, int precision, const StateBufs& B, const double* sums_cur,
                            float* rho, float* ux, float* uy, float* uz, float* T, cudaStream_t s) {
     dim3 blk(TPB_X, TPB_Y);
-    GB300_DISPATCH(precision, (k_moments<S><<<grid_of(P), blk, 0, s>>>(P, (const S*)B.src, B.pull_f, B.pull_g,
+    GB300_DISPATCH_QT(P, precision, (k_moments<S, QT><<<grid_of(P), blk, 0, s>>>(P, (const S*)B.src, B.pull_f, B.pull_g,
                                                                         B.psirho, sums_cur, rho, ux, uy, uz, T)));
     return cudaGetLastError();
 }

@@ -44,6 +44,7 @@ class LbmParams(C.Structure):
         ("wall_rho", C.c_double), ("wall_rho_patch", C.c_double), ("wall_patch_half", C.c_double),
         ("wall_scheme", C.c_int), ("wall_phi", C.c_double), ("wall_drho", C.c_double),
         ("wall_phi_patch", C.c_double), ("wall_drho_patch", C.c_double),
+        ("thermal_q", C.c_int),
     ]
 
 
@@ -376,6 +377,7 @@ def params_from_setup(setup, **overrides) -> LbmParams:
     p.wall_scheme = getattr(setup, "wall_scheme", 0)
     for k in ("wall_phi", "wall_drho", "wall_phi_patch", "wall_drho_patch"):
         setattr(p, k, getattr(setup, k, 0.0))
+    p.thermal_q = int(getattr(setup, "thermal_q", 7))
     for k, v in overrides.items():
         setattr(p, k, v)
     return p
