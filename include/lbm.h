@@ -221,8 +221,8 @@ int lbm_kernel_in_use(const lbm_ctx* ctx);
  *                    for that shape); drops the captured step graphs.  LBM_EINVAL if the plan
  *                    does not fit (the previous plan is kept), LBM_ESTATE if the context does not
  *                    run the TMA kernel
- *   lbm_autotune     time `steps` steps of every shape (with its modelled z-chunk and with whole
- *                    columns) on the current state, keep the fastest and restore the state
+ *   lbm_autotune     time `steps` steps of every shape (with its three best modelled z-chunks
+ *                    and with whole columns) on the current state, keep the fastest, restore the state
  *                    exactly; best_ms (nullable) receives its time per step.  Takes the pending
  *                    first step after lbm_init_fields first.  Needs free device memory for one
  *                    copy of the state (LBM_ENOMEM otherwise).  Synchronises.

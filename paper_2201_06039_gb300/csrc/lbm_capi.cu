@@ -877,13 +877,14 @@ int lbm_autotune(lbm_ctx* c, int steps, double* best_ms) {
     int best_shape = -1, best_zc = 0;
     e = save_or_restore(false);
     if (e != cudaSuccess) rc = fail(LBM_ECUDA, "autotune save: %s", cudaGetErrorString(e));
-    // candidates: every tile shape with its modelled best z-chunk, and the whole column
+    // candidates: every tile shape with its three best modelled z-chunks and the whole column
     for (int sh = 0; sh < tma_num_shapes() && rc == LBM_OK; ++sh) {
-        int shape = -1, zc_model = 0, items = 0;
-        tma_plan_for(c->dp, sms, sh, 0, &shape, &zc_model, &items);
-        const int zcs[2] = {zc_model, c->dp.nz};
-        for (int q = 0; q < 2 && rc == LBM_OK; ++q) {
-            if (q == 1 && zcs[1] == zcs[0]) continue;
+        int zcs[4];
+        int nz = tma_zchunk_candidates(c->dp, sms, sh, zcs, 3);
+        bool whole = false;
+        for (int q = 0; q < nz; ++q) whole |= zcs[q] == c->dp.nz;
+        if (!whole) zcs[nz++] = c->dp.nz;
+        for (int q = 0; q < nz && rc == LBM_OK; ++q) {
             c->plan_shape = sh;
             c->plan_zchunk = zcs[q];
             drop_graphs(c);

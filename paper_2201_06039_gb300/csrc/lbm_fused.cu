@@ -385,42 +385,42 @@ template <int TX_, int TY_, typename S_ = float> struct TmaShape {
     static constexpr size_t kGrp1 = align128((size_t)14 * kWin * kE);
     static constexpr size_t kGrp2 = kGrp1 + align128((size_t)6 * kWin * kE);
     static constexpr size_t kStageOne = kGrp2 + align128((size_t)6 * kWin * kE);
-    // ring of (psi, rho) planes: planes z-1, z, z+1 of the collision and the plane pulled ahead
-    // (the halo warp writes the next item's first planes only once every warp has passed the
-    // stage barrier of that item, so four planes also cover the item boundaries)
-    static constexpr int kRing = 4;
-    // as many stages as fit in one CTA's 227 KB beside the other buffers (at most 3 for FP32, 4 for
-    // 16-bit storage; at least 2)
-    static constexpr size_t kFixed = align128((size_t)kSlots * kInterior * kE) +
-                                     align128((size_t)TY_ * kSlots * (16 / kE) * kE) +
-                                     align128((size_t)2 * kSlots * TX_ * kE) +
-                                     align128((size_t)2 * kSlots * (16 / kE) * kE) +
-                                     (size_t)kRing * (TX_ + 2) * (TY_ + 2) * sizeof(float2) + 2048;
-    static constexpr int kStagesFit = (int)((227 * 1024 - kFixed) / kStageOne);
-    static constexpr int kStages = kStagesFit > (kE == 4 ? 3 : 4) ? (kE == 4 ? 3 : 4) : kStagesFit;
-    static_assert(kStages >= 2, "two stages of the tile's window fit in shared memory");
-    static constexpr size_t kStageBytes = (size_t)kStages * kStageOne;
-    // collided plane, row-major [TY][26][TX]: source of one TMA tensor store per plane (a box of
-    // fewer rows reads a prefix of it)
-    static constexpr size_t kOutBytes = align128((size_t)kSlots * kInterior * kE);
-    // periodic images of an edge tile, tensor-stored into the ghost cells: kGW edge columns
-    // [TY][26][kGW], 2 edge rows [2][26][w] (w = the tile's real columns), and the kGW x 2 corner
-    // block [2][26][kGW]; each is laid out exactly as the box that stores it (kGW columns = 16 B)
+    // the collided plane and the periodic images of an edge tile are written into the stage whose
+    // pulls were just made (the pulls of the plane above), and leave it by TMA tensor stores; the
+    // stage is refilled once those stores have read it.  Inside a stage, from its start:
+    //   out   [TY][26][TX]   the collided plane (a box of fewer rows reads a prefix of it)
+    //   gcol  [TY][26][kGW]  kGW edge columns of an edge tile (kGW columns = 16 B)
+    //   grow  [2][26][w]     its 2 edge rows (w = the tile's real columns)
+    //   gcor  [2][26][kGW]   the kGW x 2 corner block
+    // each laid out exactly as the box that stores it
     static constexpr int kGW = 16 / kE;
-    static constexpr size_t kGColBytes = align128((size_t)TY_ * kSlots * kGW * kE);
-    static constexpr size_t kGRowBytes = align128((size_t)2 * kSlots * TX_ * kE);
-    static constexpr size_t kGCorBytes = align128((size_t)2 * kSlots * kGW * kE);
-    static constexpr size_t kGhostBytes = kGColBytes + kGRowBytes + kGCorBytes;
-    static constexpr size_t kRingOff = kStageBytes + kOutBytes + kGhostBytes;
+    static constexpr size_t kOutBytes = align128((size_t)kSlots * kInterior * kE);
+    static constexpr size_t kGColOff = kOutBytes;
+    static constexpr size_t kGRowOff = kGColOff + align128((size_t)TY_ * kSlots * kGW * kE);
+    static constexpr size_t kGCorOff = kGRowOff + align128((size_t)2 * kSlots * TX_ * kE);
+    static constexpr size_t kOutAllBytes = kGCorOff + align128((size_t)2 * kSlots * kGW * kE);
+    static_assert(kOutAllBytes <= kStageOne, "the collided plane and its ghost images fit in a stage");
+    // ring of (psi, rho) planes: planes z-1, z, z+1 of the collision and the plane pulled ahead
+    static constexpr int kRing = 4;
+    // as many stages as fit in one CTA's 227 KB beside the ring (at most 3 for FP32, 4 for 16-bit
+    // storage; at least 3: a stage holds a plane's pulls and then the collided plane below it)
+    static constexpr size_t kFixed = (size_t)kRing * (TX_ + 2) * (TY_ + 2) * sizeof(float2) + 2048;
+    static constexpr int kStagesFit = (int)((227 * 1024 - kFixed) / kStageOne);
+    static constexpr int kStagesCap = kE == 4 ? 3 : 4;
+    static constexpr int kStages = kStagesFit > kStagesCap ? kStagesCap : kStagesFit;
+    static_assert(kStages >= 3, "three stages of the tile's window fit in shared memory");
+    static constexpr size_t kStageBytes = (size_t)kStages * kStageOne;
+    static constexpr size_t kRingOff = kStageBytes;
     static constexpr size_t kSmem = kRingOff + (size_t)kRing * kRingPlane * sizeof(float2);
     // element offset of storage slot s inside a stage
     static constexpr __host__ __device__ int slot_off(int s) {
         return s < 14 ? s * kWin : s < 20 ? (int)(kGrp1 / kE) + (s - 14) * kWin : (int)(kGrp2 / kE) + (s - 20) * kWin;
     }
     // thread counts of the named barriers (see k_fused_tma)
-    static constexpr int kCntRing = kCompThreads + kHaloThreads;
-    static constexpr int kCntEmpty = kCompThreads + kHaloThreads + 32;
+    static constexpr int kCntRing = kCompThreads + kHaloThreads + 32;
     static constexpr int kCntOut = kCompThreads + 32;
+    static constexpr int kCntEmpty = 64;
+    static_assert(kStages <= 4, "three named barriers a stage, ids 2..13");
     static_assert(TX_ % 8 == 0 || kE == 4, "tile origins on 16-byte boundaries for 2-byte storage");
     static_assert(TX_ % 4 == 0, "tile origins on 16-byte boundaries");
     static_assert(kSmem <= 227 * 1024, "shared memory of one CTA");
@@ -580,8 +580,11 @@ __device__ __forceinline__ void stage_pulls(const DevParams& P, const typename S
 }
 
 // named barriers of the TMA kernel (bar.sync / bar.arrive; 0 is __syncthreads): the waiting
-// warps block in hardware and issue nothing while they wait
-constexpr int kBarRing = 1, kBarComp = 2, kBarOutFull = 3, kBarOutEmpty = 4, kBarEmpty0 = 5;
+// warps block in hardware and issue nothing while they wait.  Three per stage s (s < kStages <= 4).
+constexpr int kBarComp = 1;
+__device__ __forceinline__ int bar_ring(int s) { return 2 + s; }
+__device__ __forceinline__ int bar_out_full(int s) { return 6 + s; }
+__device__ __forceinline__ int bar_empty(int s) { return 10 + s; }
 __device__ __forceinline__ void nb_sync(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
@@ -589,21 +592,29 @@ __device__ __forceinline__ void nb_arrive(int id, int nthreads) {
     asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-// Warp roles: warp 0 = producer (TMA loads), warp 1 = storer (TMA stores; FP32 only), then the
-// compute warps (thread t owns tile node t: it pulls the node's 26 populations once, writes the
-// node's (psi, rho) into the ring, keeps the populations in registers and collides the node one
-// plane later), then one halo warp (psi of the ring around the tile, kHaloPerLane slots a lane).
-// Hand-offs:
-//   full[s]    mbarrier: the TMA bytes of stage s landed (producer -> compute, halo; bounded waits)
-//   EMPTY s    named, bar.sync by producer, compute and halo: the stage's pulls are done and it
-//              may be refilled (the producer waits for use k before loading use k + kStages)
-//   RING       named, bar.sync by compute and halo once per collided plane z: psi of z + 1 is in
-//   OUT_FULL   named, compute bar.arrive -> storer bar.sync: the out tile holds plane z (FP32)
-//   OUT_EMPTY  named, storer bar.arrive -> compute bar.sync: the tensor store has read it (FP32)
+// Warp roles: warp 0 = producer (TMA loads), warp 1 = storer (TMA stores), then the compute warps
+// (thread t owns tile node t: it pulls the node's 26 populations once, writes the node's
+// (psi, rho) into the ring, keeps the populations in registers and collides the node one plane
+// later), then one halo warp (psi of the ring around the tile, kHaloPerLane slots a lane).
+// Stage use k (plane p) goes through stage s = k % kStages:
+//   full[s]        mbarrier: the TMA bytes of use k landed (producer -> compute, halo; bounded waits)
+//   RING(s)        named: producer bar.arrive once use k's loads are issued; compute and halo
+//                  bar.sync once they have pulled plane p and put its psi into the ring.  After it
+//                  nobody reads the stage's window again, and the ring holds plane p.
+//   OUT_FULL(s)    named: compute bar.arrive -> storer bar.sync.  For the uses that carry an output
+//                  (p = z0 + 1 .. z1 of an item) the compute warps first write the collided plane
+//                  p - 1 (and an edge tile's periodic images) into the stage itself.
+//   EMPTY(s)       named, bar.sync by storer and producer: the tensor stores have read the stage
+//                  and it may be refilled (the producer waits for use k before loading k + kStages).
+// The collided plane thus leaves from the stage just pulled, so the compute warps never wait for
+// a store to drain: the storer and the next loads have kStages - 1 planes of time for it.
 // Stage uses and ring planes follow one plane counter k across the CTA's items.  Every role runs
 // the same sequence of named-barrier operations whatever happens: an abort (a TMA wait that ran
-// out) skips only the mbarrier waits, the copies and the work, so no barrier is left incomplete,
-// and since both sides of EMPTY wait, no role runs ahead of the others into a later barrier use.
+// out) skips only the mbarrier waits, the copies and the work, so no barrier is left incomplete.
+// No role laps another on a barrier: RING and EMPTY are synced by the roles that could run ahead
+// (compute, halo; storer, producer), the producer's next arrival on RING(s) follows its EMPTY(s)
+// sync of the previous use of s, and the compute warps' next arrival on OUT_FULL(s) follows their
+// RING(s) sync of the next use of s, which needs that arrival of the producer.
 template <int TX_, int TY_, typename S, bool kWet>
 __global__ void __maxnreg__((TmaShape<TX_, TY_, S>::kMaxRegs))
 k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ CUtensorMap map6,
@@ -619,11 +630,8 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
     constexpr int kComp = Sh::kCompThreads, kGW = Sh::kGW;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // stage s: smem_raw + s * kStageOne (three slot groups of [slots][TY+4][TX+2 kXOff])
-    S* out = reinterpret_cast<S*>(smem_raw + Sh::kStageBytes);                   // [TY][26][TX]
-    S* gcol = reinterpret_cast<S*>(smem_raw + Sh::kStageBytes + Sh::kOutBytes);  // [TY][26][kGW]
-    S* grow = reinterpret_cast<S*>(smem_raw + Sh::kStageBytes + Sh::kOutBytes + Sh::kGColBytes);  // [2][26][w]
-    S* gcor = reinterpret_cast<S*>(smem_raw + Sh::kStageBytes + Sh::kOutBytes + Sh::kGColBytes +
-                                   Sh::kGRowBytes);                              // [2][26][kGW]
+    // stage s: smem_raw + s * kStageOne; after its pulls it holds the collided plane below (out,
+    // gcol, grow, gcor at kGColOff, kGRowOff, kGCorOff)
     float2* ring = reinterpret_cast<float2*>(smem_raw + Sh::kRingOff);           // [kRing][TY+2][TX+2]
     __shared__ __align__(8) unsigned long long full_bar[kStages], stall_bar;
     __shared__ double red_a[kComp / 32], red_b[kComp / 32];
@@ -662,7 +670,7 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
             const int cx = x0 - Sh::kXOff + kGX, cy = y0;
             for (int p = z0 - 1; p <= z1; ++p, ++k) {
                 const int s = k % kStages;
-                if (k >= (unsigned)kStages) nb_sync(kBarEmpty0 + s, Sh::kCntEmpty);   // use k - kStages done
+                if (k >= (unsigned)kStages) nb_sync(bar_empty(s), Sh::kCntEmpty);   // use k - kStages stored
                 if (lane == 0) {
                     if (P.test_stall && k == 0) {
                         // timeout-path test: the first stage's data never comes; the producer waits
@@ -687,23 +695,23 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                     }
                 }
                 __syncwarp();
+                nb_arrive(bar_ring(s), Sh::kCntRing);   // use k is under way
             }
         }
-        // the releases of the last stage uses (every use of EMPTY is matched on both sides)
+        // the last stage uses (every use of EMPTY is matched on both sides)
         const unsigned q0 = k > (unsigned)kStages ? k - kStages : 0u;
-        for (unsigned q = q0; q < k; ++q) nb_sync(kBarEmpty0 + q % kStages, Sh::kCntEmpty);
+        for (unsigned q = q0; q < k; ++q) nb_sync(bar_empty(q % kStages), Sh::kCntEmpty);
         // copies still in flight land before the CTA exits (every use completes one phase; bounded)
         if (lane == 0)
             for (unsigned q = q0; q < k; ++q) mbar_wait(&full_bar[q % kStages], (q / kStages) & 1);
         __syncwarp();
     } else if (warp == 1) {
         // ------------------------------------------------------------ storer (lane 0 issues)
-        nb_arrive(kBarOutEmpty, Sh::kCntOut);   // the out tile starts free
+        unsigned k = 0;
         for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
             const int chunk = item / ntiles, tile = item % ntiles;
             const int x0 = (tile % tiles_x) * TX_, y0 = (tile / tiles_x) * TY_;
             const int z0 = chunk * zchunk, z1 = min(P.nz, z0 + zchunk);
-            const bool last_item = item + (int)gridDim.x >= n_items;
             // box (x, slot, y, z) at the tile origin (x a multiple of 4 floats); the last tile
             // row uses the map whose box holds exactly its rows, so a box never reaches past
             // ny; columns beyond nx fall outside the tensor and are not written
@@ -717,20 +725,22 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
             const int gy_row = top ? kGY - 2 : P.ny + kGY;        // destination of the row box
             const CUtensorMap* mc = y0 + TY_ > P.ny ? &map_gcol_top : &map_gcol;
             const CUtensorMap* mr = x0 + TX_ > P.nx ? &map_grow_right : &map_grow;
-            for (int z = z0; z < z1; ++z) {
-                nb_sync(kBarOutFull, Sh::kCntOut);
-                if (lane == 0 && !abort_flag) {
-                    tma_store_4d(m, out, x0 + kGX, 0, y0 + kGY, z);
-                    if (left || right) tma_store_4d(mc, gcol, gx_col, 0, y0 + kGY, z);
-                    if (top || bottom) tma_store_4d(mr, grow, x0 + kGX, 0, gy_row, z);
-                    if ((left || right) && (top || bottom)) tma_store_4d(&map_gcor, gcor, gx_col, 0, gy_row, z);
+            for (int p = z0 - 1; p <= z1; ++p, ++k) {
+                const int s = k % kStages;
+                nb_sync(bar_out_full(s), Sh::kCntOut);
+                if (p > z0 && lane == 0 && !abort_flag) {   // the stage holds collided plane p - 1
+                    const int z = p - 1;
+                    unsigned char* st = smem_raw + (size_t)s * Sh::kStageOne;
+                    tma_store_4d(m, st, x0 + kGX, 0, y0 + kGY, z);
+                    if (left || right) tma_store_4d(mc, st + Sh::kGColOff, gx_col, 0, y0 + kGY, z);
+                    if (top || bottom) tma_store_4d(mr, st + Sh::kGRowOff, x0 + kGX, 0, gy_row, z);
+                    if ((left || right) && (top || bottom))
+                        tma_store_4d(&map_gcor, st + Sh::kGCorOff, gx_col, 0, gy_row, z);
                     bulk_commit();
                     bulk_wait_read_all();
                 }
                 __syncwarp();
-                // the compute warps wait for this release before they write the next plane (none
-                // after the CTA's last plane)
-                if (!(last_item && z == z1 - 1)) nb_arrive(kBarOutEmpty, Sh::kCntOut);
+                nb_sync(bar_empty(s), Sh::kCntEmpty);   // the stage may be refilled
             }
         }
         if (lane == 0) bulk_wait_all();   // the stores have completed before the CTA exits
@@ -748,9 +758,9 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                                              Sh::kWin)
                                      : 0;
         const float rho_ave = buoyancy_ref(P, sums_cur[0], P.inv_N);
-        S* const outp = out + (node_thread ? bbase(P, (ly - 1) * (kSlots * TX_) + (lx - 1), 0, (kSlots - 1) * TX_,
-                                                   kSlots * Sh::kInterior)
-                                           : 0);
+        const int ooff = node_thread ? bbase(P, (ly - 1) * (kSlots * TX_) + (lx - 1), 0, (kSlots - 1) * TX_,
+                                             kSlots * Sh::kInterior)
+                                     : 0;   // the node's element in the out tile
         int bad = 0;
         unsigned k = 0;
         for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
@@ -794,15 +804,15 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                     *rp = make_float2(po, ro);
                     bad |= !(psi2 > 0.f) || !isfinite(ro) || !isfinite(To);
                 }
-                nb_sync(kBarEmpty0 + s, Sh::kCntEmpty);   // the stage may be refilled
+                nb_sync(bar_ring(s), Sh::kCntRing);   // the window is read; the ring holds plane p
                 ++k;
             };
             // one collided plane z: pull plane z + 1 (into the n-set), wait for the ring, collide
             // plane z (the c-set), store it
             auto iterate = [&](int z, float* fc, float* gc, float rc, float Tc, float pc, float* fn, float* gn,
                                float& rn, float& Tn, float& pn) {
-                pull_plane(z + 1, fn, gn, rn, Tn, pn);
-                nb_sync(kBarRing, Sh::kCntRing);         // psi of planes z - 1, z, z + 1 in the ring
+                pull_plane(z + 1, fn, gn, rn, Tn, pn);   // ring: psi of planes z - 1, z, z + 1
+                const int so = (k - 1) % kStages;       // the stage just pulled receives plane z
                 const float ph_prev = ph_next;
                 if (owner && z + 1 < z1) ph_next = phis[bidx(P, node_of(P, gx, gy, z + 1), P.N)];
                 float ph = 0.f;
@@ -817,8 +827,9 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                     NodeOut o = collide_f(P, fc, rc, F.Fx, F.Fy, F.Fz, F.Fm2, pc * pc);
                     ph = collide_g(P, gc, rc, Tc, o, rs.gx, rs.gy, rs.gz, ph_prev, first);
                 }
-                nb_sync(kBarOutEmpty, Sh::kCntOut);   // the tensor store has read the previous plane
                 {
+                    S* const sb = reinterpret_cast<S*>(smem_raw + (size_t)so * Sh::kStageOne);
+                    S* const outp = sb + ooff;
                     if (owner) {
                         S fe[19], ge[7];
 #pragma unroll
@@ -830,21 +841,21 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
 #pragma unroll
                         for (int a = 0; a < 7; ++a) outp[gslot(a) * TX_] = ge[a];
                         if (cx4 >= 0) {   // edge column: [TY][26][kGW]
-                            S* q = gcol + (ly - 1) * (kSlots * kGW) + cx4;
+                            S* q = sb + Sh::kGColOff / sizeof(S) + (ly - 1) * (kSlots * kGW) + cx4;
 #pragma unroll
                             for (int a = 0; a < 19; ++a) q[fslot(a) * kGW] = fe[a];
 #pragma unroll
                             for (int a = 0; a < 7; ++a) q[gslot(a) * kGW] = ge[a];
                         }
                         if (ry2 >= 0) {   // edge row: [2][26][rw]
-                            S* q = grow + ry2 * (kSlots * rw) + (lx - 1);
+                            S* q = sb + Sh::kGRowOff / sizeof(S) + ry2 * (kSlots * rw) + (lx - 1);
 #pragma unroll
                             for (int a = 0; a < 19; ++a) q[fslot(a) * rw] = fe[a];
 #pragma unroll
                             for (int a = 0; a < 7; ++a) q[gslot(a) * rw] = ge[a];
                         }
                         if (cx4 >= 0 && ry2 >= 0) {   // corner block: [2][26][kGW]
-                            S* q = gcor + ry2 * (kSlots * kGW) + cx4;
+                            S* q = sb + Sh::kGCorOff / sizeof(S) + ry2 * (kSlots * kGW) + cx4;
 #pragma unroll
                             for (int a = 0; a < 19; ++a) q[fslot(a) * kGW] = fe[a];
 #pragma unroll
@@ -853,7 +864,7 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                     }
                     // this thread's out writes become visible to the tensor store (async proxy)
                     fence_proxy_async_smem();
-                    nb_arrive(kBarOutFull, Sh::kCntOut);
+                    nb_arrive(bar_out_full(so), Sh::kCntOut);
                 }
                 if (owner) phis[bidx(P, node_of(P, gx, gy, z), P.N)] = ph;
             };
@@ -862,7 +873,9 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
             float fa[19], ga[7], ra = 0.f, Ta = 0.f, pa = 0.f;
             float fb[19], gb[7], rb = 0.f, Tb = 0.f, pb = 0.f;
             pull_plane(z0 - 1, fb, gb, rb, Tb, pb);   // psi only
+            nb_arrive(bar_out_full((k - 1) % kStages), Sh::kCntOut);   // no output in this use
             pull_plane(z0, fa, ga, ra, Ta, pa);
+            nb_arrive(bar_out_full((k - 1) % kStages), Sh::kCntOut);
             // one copy of the loop body (the instruction cache holds it; unrolled twice to swap the
             // two register sets it measured slower), so the pulled-ahead set is moved over
 #pragma unroll 1
@@ -920,8 +933,7 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                     rp[roff] = make_float2(psi_of(psi2), rho);
                     bad |= !(psi2 > 0.f) || !isfinite(rho) || !isfinite(T);
                 }
-                nb_sync(kBarEmpty0 + s, Sh::kCntEmpty);   // the stage may be refilled
-                if (p > z0) nb_sync(kBarRing, Sh::kCntRing);   // one ring barrier per collided plane
+                nb_sync(bar_ring(s), Sh::kCntRing);   // the window is read; the ring holds plane p
             }
         }
         if (bad) atomicOr(flag, 1);
@@ -983,16 +995,15 @@ __global__ void __launch_bounds__(256) k_ghosts(DevParams P, S* __restrict__ pop
     }
 }
 
-// Tile shapes of the TMA kernel (index = plan shape): 8 and 9 compute warps (about two per SM
-// sub-partition, up to 160 registers a thread), and two 384-node shapes with 12 (three per
-// sub-partition, 128 registers a thread).  kTmaRate is each shape's node rate per CTA relative
-// to 32 x 8, measured on the 200 x 200 x 300 pool (one GB300); 48 x 8 and 16 x 16 measured
-// slower still and are not offered.
-#define GB300_TMA_SHAPES(M) M(0, 32, 8) M(1, 40, 7) M(2, 32, 12) M(3, 24, 16)
-constexpr int kNumTmaShapes = 4;
-constexpr int kTmaTX[kNumTmaShapes] = {32, 40, 32, 24};
-constexpr int kTmaTY[kNumTmaShapes] = {8, 7, 12, 16};
-constexpr double kTmaRate[kNumTmaShapes] = {1.0, 1.0, 1.25, 1.12};
+// Tile shapes of the TMA kernel (index = plan shape): 8 to 13 compute warps of one tile node a
+// thread.  kTmaRate is each shape's node rate per CTA relative to 32 x 8 (a prior for the model
+// below, which lbm_autotune replaces by measurement).  The 40-wide shapes tile lattices whose nx
+// is a multiple of 40 (such as 200) without a partial tile column.
+#define GB300_TMA_SHAPES(M) M(0, 32, 8) M(1, 40, 7) M(2, 32, 12) M(3, 24, 16) M(4, 40, 8) M(5, 40, 10)
+constexpr int kNumTmaShapes = 6;
+constexpr int kTmaTX[kNumTmaShapes] = {32, 40, 32, 24, 40, 40};
+constexpr int kTmaTY[kNumTmaShapes] = {8, 7, 12, 16, 8, 10};
+constexpr double kTmaRate[kNumTmaShapes] = {1.0, 1.0, 1.25, 1.12, 1.1, 1.25};
 
 // Plan of the TMA kernel for a lattice: the tile shape and z-chunking with the least modelled
 // time of the busiest CTA.  Items (tile, z-chunk) go round robin to the persistent CTAs; a plane
@@ -1026,8 +1037,20 @@ void tma_plan(const DevParams& P, int ctas, int forced_shape, int forced_zchunk,
     }
 }
 
+// SM count of the current device (queried once per device)
+int device_sms() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+    if (dev < 64 && cached[dev] > 0) return cached[dev];
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    if (dev < 64) cached[dev] = n;
+    return n;
+}
+
 int zchunk_generic(const DevParams& P, int tiles) {
-    const int target = 152 * 2 * 4;   // about four waves of two CTAs per SM
+    const int target = device_sms() * 2 * 4;   // about four waves of two CTAs per SM
     int chunks = (target + tiles - 1) / tiles;
     int zc = (P.nz + chunks - 1) / chunks;
     if (zc < 8) zc = 8;
@@ -1071,6 +1094,34 @@ void tma_plan_for(const DevParams& P, int ctas, int forced_shape, int forced_zch
 }
 
 int tma_num_shapes() { return kNumTmaShapes; }
+
+int tma_zchunk_candidates(const DevParams& P, int ctas, int shape, int* zcs, int max) {
+    // the z-chunks of the shape in increasing modelled cost (distinct, at least 16 planes unless
+    // the column is shorter), the whole column included
+    const int tx = kTmaTX[shape], ty = kTmaTY[shape];
+    const long long tiles = (long long)((P.nx + tx - 1) / tx) * ((P.ny + ty - 1) / ty);
+    int n = 0;
+    double cost[64];
+    int zc_of[64];
+    for (int nch = 1; nch <= P.nz && n < 64; ++nch) {
+        const int zc = (P.nz + nch - 1) / nch;
+        if (zc < 16 && nch > 1) break;
+        if (n > 0 && zc_of[n - 1] == zc) continue;
+        const long long items = tiles * ((P.nz + zc - 1) / zc);
+        cost[n] = (double)((items + ctas - 1) / ctas) * (zc + 2.0);
+        zc_of[n++] = zc;
+    }
+    int out = 0;
+    bool taken[64] = {false};
+    while (out < max && out < n) {
+        int b = -1;
+        for (int i = 0; i < n; ++i)
+            if (!taken[i] && (b < 0 || cost[i] < cost[b])) b = i;
+        taken[b] = true;
+        zcs[out++] = zc_of[b];
+    }
+    return out;
+}
 
 int tma_box_w(int shape, int precision) { return kTmaTX[shape] + 2 * (precision == 0 ? 4 : 8); }
 int tma_box_h(int shape) { return kTmaTY[shape] + 4; }

@@ -74,6 +74,8 @@ cudaError_t launch_ghosts(const DevParams& P, int precision, void* pops, cudaStr
 void tma_plan_for(const DevParams& P, int ctas, int forced_shape, int forced_zchunk, int* shape, int* zchunk,
                   int* items);
 int tma_num_shapes();
+// up to max z-chunks of a shape, best modelled first (returns how many)
+int tma_zchunk_candidates(const DevParams& P, int ctas, int shape, int* zcs, int max);
 size_t tma_smem_bytes(int shape, int precision);
 int tma_box_w(int shape, int precision);
 int tma_box_h(int shape);
