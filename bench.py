@@ -499,7 +499,14 @@ def run_mine(args):
 
     # ---- device-resident timing
     lat.init(torch.from_numpy(rho).cuda(), torch.from_numpy(T).cuda())
-    tuned = lat.autotune(steps=20) if lat.kernel == lbm.LBM_KERNEL_FUSED_TMA else None   # plan by timing
+    tuned = None
+    if lat.kernel == lbm.LBM_KERNEL_FUSED_TMA:
+        if args.plan:   # pinned tile shape and z-chunk (profiling runs of one plan)
+            shape, zchunk = (int(v) for v in args.plan.split(","))
+            lat.select_plan(shape, zchunk)
+            tuned = {"shape": lat.plan[0], "zchunk": lat.plan[1]}
+        else:
+            tuned = lat.autotune(steps=20)   # plan by timing
     lat.step(args.warmup)
     lat.step(args.steps)            # captures the K-step graph outside the timed region
     torch.cuda.synchronize()
@@ -601,6 +608,7 @@ def main():
     ap.add_argument("--nx", type=int, default=None, help="override the lattice size (profiling runs)")
     ap.add_argument("--ny", type=int, default=None)
     ap.add_argument("--nz", type=int, default=None)
+    ap.add_argument("--plan", default=None, help="SHAPE,ZCHUNK: pin the TMA kernel's plan instead of autotuning")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-16bit", dest="compare_16bit", action="store_false",
                     help="skip the BF16 / FP16 storage comparison of the default run")
