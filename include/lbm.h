@@ -235,8 +235,10 @@ int lbm_autotune(lbm_ctx* ctx, int steps, double* best_ms);
 /* Enqueue n steps outside any graph and accumulate, per kernel kind, the device time
  * measured with CUDA events on the context's stream and the number of launches
  * (kernel_ms[0]: psi/EOS or fused kernel, [1]: stream-collide kernel, [2]: ghost-cell
- * refresh and the per-step table of a scheme-1 wetting wall).  Synchronises.  Used for the roofline figures; the event gaps make it slightly
- * slower than lbm_step. */
+ * refresh and the per-step table of a scheme-1 wetting wall).  Each launch is bracketed by a
+ * CUDA event pair on the context's stream; the n steps are enqueued back to back and the events
+ * read once at the end, so a launch starts as it would without the events.  Synchronises.  Used
+ * for the roofline figures. */
 int lbm_step_profiled(lbm_ctx* ctx, int n, double kernel_ms[3], int launches[3]);
 
 /* Allocation-free FP64 sum of a device float field (the paper has no counterpart: this is a

@@ -270,7 +270,7 @@ int lbm_batch_create(const lbm_params* common, int n_instances, const int* dims,
         I.pop_off = b->pop_elems;
         I.field_off = b->nodes;
         I.inv_N = d.inv_N;
-        b->pop_elems += (long long)kSlots * d.Ns;
+        b->pop_elems += (long long)pop_elems(d);
         b->nodes += d.N;
         b->max_N = std::max(b->max_N, d.N);
     }

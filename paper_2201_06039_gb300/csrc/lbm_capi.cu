@@ -8,6 +8,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "../../include/lbm.h"
 #include "lbm_host.h"
 #include "lbm_launch.h"
@@ -47,14 +49,14 @@ struct Layout {
     size_t pops[2], psirho, phis, sums, partial, counter, flag, vel, wall, wpar, wbad, total;
 };
 
-// Device memory of a context: two population buffers (26 slots of Ns elements: the padded,
+// Device memory of a context: two population buffers (rows of 26 or 38 slots: the padded,
 // ghost-carrying storage of lbm_device.cuh), dense (psi, rho) and phi_s fields, FP64 sums.
 Layout layout_of(const lbm_params* p, const DevParams& dp) {
     Layout L;
     size_t N = (size_t)dp.N, pb = pop_bytes(p->precision), off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
-    L.pops[0] = take((size_t)slots_of(dp.qt) * dp.Ns * pb);
-    L.pops[1] = take((size_t)slots_of(dp.qt) * dp.Ns * pb);
+    L.pops[0] = take(pop_elems(dp) * pb);
+    L.pops[1] = take(pop_elems(dp) * pb);
     L.psirho = take(8 * N);
     L.phis = take(4 * N);
     L.sums = take(8 * sizeof(double));          // slots: [0..1] [2..3] rho_ave ping-pong, [4..5] totals
@@ -187,8 +189,11 @@ DevParams make_dev(const lbm_params* p) {
     d.plane = p->nx * p->ny;
     d.Ws = (p->nx + kGX + 2 + 7) / 8 * 8;   // ghost columns -2..-1 and nx..nx+1; 32-byte aligned rows
     d.Hs = p->ny + kGY + 2;
-    d.splane = d.Ws * d.Hs;
-    d.Ns = d.splane * p->nz;
+    const int slots = slots_of(p->thermal_q == 19 ? 19 : 7);
+    d.Rs = slots * d.Ws;                    // the slots of a row follow each other
+    d.splane = d.Rs * d.Hs;
+    d.Ns = d.Ws;
+    d.Nidx = d.splane * p->nz - (slots - 1) * d.Ws;
     for (int k = 0; k < 6; ++k) { d.bc[k] = p->bc[k]; d.T_wall[k] = (float)p->T_wall[k]; }
     d.hot_dT = (float)p->hot_dT;
     d.hot_inv2s2 = p->hot_dT != 0.0 ? (float)(1.0 / (2.0 * p->hot_sigma * p->hot_sigma)) : 0.f;
@@ -267,76 +272,84 @@ void drop_graphs(lbm_ctx* c) {
     c->n_graphs = 0;
 }
 
-// Enqueue one time step of the selected variant on the context's stream.
-int enqueue_step(lbm_ctx* c, double* kernel_ms = nullptr, int* launches = nullptr, cudaEvent_t* ev = nullptr) {
+// Device durations of the kernels of a run of steps: an event pair around each launch, recorded
+// as the launches are enqueued (no synchronisation in between, so a launch follows the previous
+// one as it would without the events), read after the run.
+struct KernelTimer {
+    std::vector<cudaEvent_t> ev;   // two per launch
+    std::vector<int> kind;         // 0: psi/EOS or fused kernel, 1: stream-collide, 2: ghosts / wall table
+    void begin(cudaStream_t s) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        ev.push_back(a);
+        ev.push_back(b);
+        cudaEventRecord(a, s);
+    }
+    void end(int k, cudaStream_t s) {
+        cudaEventRecord(ev.back(), s);
+        kind.push_back(k);
+    }
+    // waits for the run, adds each launch's duration to kernel_ms[kind] and counts it
+    cudaError_t collect(double* kernel_ms, int* launches) {
+        cudaError_t r = ev.empty() ? cudaSuccess : cudaEventSynchronize(ev.back());
+        for (size_t i = 0; i < kind.size() && r == cudaSuccess; ++i) {
+            float ms = 0.f;
+            r = cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+            kernel_ms[kind[i]] += ms;
+            launches[kind[i]] += 1;
+        }
+        return r;
+    }
+    ~KernelTimer() {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
+// Enqueue one time step of the selected variant on the context's stream (each launch timed when
+// a timer is given).
+int enqueue_step(lbm_ctx* c, KernelTimer* timer = nullptr) {
     StateBufs B = c->bufs();
     cudaError_t e;
     bool ghosts_done = false;
     if (c->dp.wet && c->dp.wet_scheme == 1) {   // virtual densities of this step from the fluid layer z = 0
-        if (ev) cudaEventRecord(ev[0], c->launch);
+        if (timer) timer->begin(c->launch);
         e = launch_wall_table(c->dp, c->p.precision, B.src, B.pull_f, (float2*)(c->base + c->L.wall), c->launch);
         if (e != cudaSuccess) return fail(LBM_ECUDA, "wall table launch: %s", cudaGetErrorString(e));
-        if (ev) {
-            cudaEventRecord(ev[1], c->launch);
-            cudaEventSynchronize(ev[1]);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, ev[0], ev[1]);
-            kernel_ms[2] += ms;
-            launches[2] += 1;
-        }
+        if (timer) timer->end(2, c->launch);
     }
     if (c->variant == LBM_KERNEL_FUSED) {
-        if (ev) cudaEventRecord(ev[0], c->launch);
+        if (timer) timer->begin(c->launch);
         e = launch_fused(c->dp, c->p.precision, B, c->sums(c->slot), c->sums(c->slot ^ 1), c->first ? 1 : 0,
                          c->launch, c->maps.ok ? &c->maps : nullptr, &ghosts_done);
         if (e != cudaSuccess) return fail(LBM_ECUDA, "fused kernel launch: %s", cudaGetErrorString(e));
         if (c->maps.ok && B.pull_f && B.pull_g) c->dp.test_stall = 0;   // one stalled TMA step only
-        if (ev) {
-            cudaEventRecord(ev[1], c->launch);
-            cudaEventSynchronize(ev[1]);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, ev[0], ev[1]);
-            kernel_ms[0] += ms;
-            launches[0] += 1;
-        }
+        if (timer) timer->end(0, c->launch);
     } else {
-        if (ev) cudaEventRecord(ev[0], c->launch);
+        if (timer) timer->begin(c->launch);
         e = launch_psi(c->dp, c->p.precision, B, c->sums(c->slot ^ 1), c->launch);
         if (e != cudaSuccess) return fail(LBM_ECUDA, "psi kernel launch: %s", cudaGetErrorString(e));
-        if (ev) cudaEventRecord(ev[1], c->launch);
+        if (timer) {
+            timer->end(0, c->launch);
+            timer->begin(c->launch);
+        }
         if (B.vel) {   // u of every node for the finite-difference div u of the collide pass
             e = launch_velocity(c->dp, c->p.precision, B, c->sums(c->slot), c->launch);
             if (e != cudaSuccess) return fail(LBM_ECUDA, "velocity kernel launch: %s", cudaGetErrorString(e));
         }
         e = launch_collide(c->dp, c->p.precision, B, c->sums(c->slot), c->first ? 1 : 0, c->launch);
         if (e != cudaSuccess) return fail(LBM_ECUDA, "collide kernel launch: %s", cudaGetErrorString(e));
-        if (ev) {
-            cudaEventRecord(ev[2], c->launch);
-            cudaEventSynchronize(ev[2]);
-            float a = 0.f, b = 0.f;
-            cudaEventElapsedTime(&a, ev[0], ev[1]);
-            cudaEventElapsedTime(&b, ev[1], ev[2]);
-            kernel_ms[0] += a;
-            kernel_ms[1] += b;
-            launches[0] += 1;
-            launches[1] += 1;
-        }
+        if (timer) timer->end(1, c->launch);
     }
     // both fields are written every step (frozen ones copied through unchanged, so they stay
     // in their un-streamed "fresh" form)
     c->cur ^= 1;
     if (c->maps.ok && !ghosts_done) {   // the TMA path reads ghost cells: refresh them in the state just written
-        if (ev) cudaEventRecord(ev[0], c->launch);
+        if (timer) timer->begin(c->launch);
         e = launch_ghosts(c->dp, c->p.precision, B.dst, c->launch);
         if (e != cudaSuccess) return fail(LBM_ECUDA, "ghost refresh launch: %s", cudaGetErrorString(e));
-        if (ev) {
-            cudaEventRecord(ev[1], c->launch);
-            cudaEventSynchronize(ev[1]);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, ev[0], ev[1]);
-            kernel_ms[2] += ms;
-            launches[2] += 1;
-        }
+        if (timer) timer->end(2, c->launch);
     }
     if (!c->p.flow_off) c->fresh_f = false;
     if (!c->p.thermal_off) c->fresh_g = false;
@@ -435,7 +448,7 @@ bool make_tma_maps(lbm_ctx* c) {
     const CUtensorMapDataType dt = c->p.precision == LBM_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                  : c->p.precision == LBM_BF16_SHIFTED ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                                       : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-    cuuint64_t strides[3] = {(cuuint64_t)d.Ws * E, (cuuint64_t)d.splane * E, (cuuint64_t)d.Ns * E};
+    cuuint64_t strides[3] = {(cuuint64_t)d.Rs * E, (cuuint64_t)d.splane * E, (cuuint64_t)d.Ns * E};
     const cuuint32_t bw = (cuuint32_t)tma_box_w(shape, c->p.precision), bh = (cuuint32_t)tma_box_h(shape);
     cuuint32_t box14[4] = {bw, bh, 1, 14}, box6[4] = {bw, bh, 1, 6}, es[4] = {1, 1, 1, 1};
     // output tiles, dimensions ordered (x, slot, y, z) to match the [row][slot][x] out buffer; the
@@ -443,7 +456,7 @@ bool make_tma_maps(lbm_ctx* c) {
     // the last tile row gets a box of exactly its rows, so no box ever extends past ny
     const int th = tma_tile_h(shape), ry = d.ny - th * ((d.ny - 1) / th);
     cuuint64_t dims_out[4] = {(cuuint64_t)(d.nx + kGX), (cuuint64_t)kSlots, (cuuint64_t)(d.ny + kGY), (cuuint64_t)d.nz};
-    cuuint64_t strides_out[3] = {(cuuint64_t)d.Ns * E, (cuuint64_t)d.Ws * E, (cuuint64_t)d.splane * E};
+    cuuint64_t strides_out[3] = {(cuuint64_t)d.Ns * E, (cuuint64_t)d.Rs * E, (cuuint64_t)d.splane * E};
     cuuint32_t box_out[4] = {(cuuint32_t)tma_tile_w(shape), (cuuint32_t)kSlots, (cuuint32_t)th, 1};
     cuuint32_t box_top[4] = {(cuuint32_t)tma_tile_w(shape), (cuuint32_t)kSlots, (cuuint32_t)ry, 1};
     // ghost boxes over the whole padded plane (they always lie inside it)
@@ -593,7 +606,7 @@ int lbm_init_fields(lbm_ctx* c, const float* rho, const float* T, const float* u
     if (!c) return fail(LBM_EINVAL, "ctx is NULL");
     if (!rho || !T) return fail(LBM_EINVAL, "rho and T are required");
     size_t N = (size_t)c->dp.N;
-    // stage host inputs in the second population buffer (26 Ns * >= 2 bytes >= 5 N floats)
+    // stage host inputs in the second population buffer (>= 26 N elements of >= 2 bytes >= 5 N floats)
     float* stage = (float*)c->pbuf(1);
     const float *drho = rho, *dT = T, *du = u;
     if (!is_device_ptr(rho)) {
@@ -651,11 +664,13 @@ int lbm_step_profiled(lbm_ctx* c, int n, double kernel_ms[3], int launches[3]) {
     if (!c || !kernel_ms || !launches) return fail(LBM_EINVAL, "NULL argument");
     if (!c->initialised) return fail(LBM_ESTATE, "lbm_step before lbm_init_fields");
     for (int k = 0; k < 3; ++k) { kernel_ms[k] = 0.0; launches[k] = 0; }
-    cudaEvent_t ev[3];
-    for (int k = 0; k < 3; ++k) CK(cudaEventCreate(&ev[k]));
     int rc = LBM_OK;
-    for (int k = 0; k < n && rc == LBM_OK; ++k) rc = enqueue_step(c, kernel_ms, launches, ev);
-    for (int k = 0; k < 3; ++k) cudaEventDestroy(ev[k]);
+    {
+        KernelTimer timer;
+        for (int k = 0; k < n && rc == LBM_OK; ++k) rc = enqueue_step(c, &timer);
+        cudaError_t e = timer.collect(kernel_ms, launches);
+        if (rc == LBM_OK && e != cudaSuccess) rc = fail(LBM_ECUDA, "kernel timing: %s", cudaGetErrorString(e));
+    }
     if (rc) return rc;
     if (c->p.check_nonfinite) return check_flag(c);
     return LBM_OK;
@@ -700,8 +715,8 @@ int lbm_get_totals(lbm_ctx* c, double* mass, double* T_sum, double* rho_ave) {
 
 long long lbm_steps_done(const lbm_ctx* c) { return c ? c->steps : 0; }
 
-// Checkpoint layout: a fixed header, the current population buffer (26 slots of Ns elements,
-// ghost cells included), the phi_s history (N floats), the two sums of the next step's rho_ave.
+// Checkpoint layout: a fixed header, the current population buffer (its device layout: rows of
+// slots, ghost cells included), the phi_s history (N floats), the two sums of the next step's rho_ave.
 namespace {
 struct CkptHeader {
     char magic[8];
@@ -709,7 +724,7 @@ struct CkptHeader {
     long long steps, pop_bytes, phis_bytes;
 };
 const char kCkptMagic[8] = {'G', 'B', '3', 'L', 'B', 'M', 'C', 'K'};
-size_t ckpt_pop_bytes(const lbm_ctx* c) { return (size_t)slots_of(c->dp.qt) * c->dp.Ns * pop_bytes(c->p.precision); }
+size_t ckpt_pop_bytes(const lbm_ctx* c) { return pop_elems(c->dp) * pop_bytes(c->p.precision); }
 }  // namespace
 
 size_t lbm_state_bytes(const lbm_ctx* c) {
@@ -724,7 +739,7 @@ int lbm_save_state(lbm_ctx* c, void* buf, size_t bytes) {
     CkptHeader h;
     memset(&h, 0, sizeof(h));
     memcpy(h.magic, kCkptMagic, 8);
-    h.version = 1;
+    h.version = 2;   // 2: rows of slots
     h.nx = c->p.nx; h.ny = c->p.ny; h.nz = c->p.nz; h.precision = c->p.precision;
     h.fresh_f = c->fresh_f; h.fresh_g = c->fresh_g; h.first = c->first;
     h.steps = c->steps;
@@ -774,7 +789,7 @@ int lbm_load_state(lbm_ctx* c, const void* buf, size_t bytes) {
     if (bytes < sizeof(CkptHeader)) return fail(LBM_EINVAL, "not a checkpoint (%zu bytes)", bytes);
     CkptHeader h;
     memcpy(&h, buf, sizeof(h));
-    if (memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1) return fail(LBM_EINVAL, "not a checkpoint");
+    if (memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 2) return fail(LBM_EINVAL, "not a checkpoint of this layout");
     if (h.nx != c->p.nx || h.ny != c->p.ny || h.nz != c->p.nz || h.precision != c->p.precision)
         return fail(LBM_EINVAL, "checkpoint of a %d x %d x %d lattice (precision %d), context is %d x %d x %d (%d)",
                     h.nx, h.ny, h.nz, h.precision, c->p.nx, c->p.ny, c->p.nz, c->p.precision);
@@ -847,7 +862,7 @@ int lbm_autotune(lbm_ctx* c, int steps, double* best_ms) {
     int rc = LBM_OK;
     while (rc == LBM_OK && (c->first || c->fresh_f || c->fresh_g)) rc = enqueue_step(c);
     if (rc) return rc;
-    const size_t popb = (size_t)kSlots * c->dp.Ns * pop_bytes(c->p.precision), phib = 4 * (size_t)c->dp.N;
+    const size_t popb = pop_elems(c->dp) * pop_bytes(c->p.precision), phib = 4 * (size_t)c->dp.N;
     const size_t sumb = 8 * sizeof(double);
     char* save = nullptr;
     cudaError_t e = cudaMalloc((void**)&save, popb + phib + sumb);

@@ -56,10 +56,12 @@ struct DevParams {
     int nx, ny, nz;
     int N;                    // nx*ny*nz (< 2^31): dense fields (phi_s history, psi, user fields)
     int plane;                // nx*ny
-    // population storage: node (x, y, z) at (x + kGX) + Ws ((y + kGY) + Hs z), slot s at s * Ns.
+    // population storage, rows of slots: node (x, y, z) at i = (x + kGX) + Rs (y + kGY) + splane z,
+    // slot s at i + s Ns with Ns = Ws, so the slots of one row follow each other (Rs = slots x Ws,
+    // splane = Rs Hs).  Ws: padded row width, Hs: padded rows; Nidx bounds the node index i.
     // Columns x = -2, -1, nx, nx+1 and rows y = -2, -1, ny, ny+1 are ghost copies of the periodic
     // images (kept current by every kernel that writes populations, only on f-periodic axes).
-    int Ws, Hs, splane, Ns;
+    int Ws, Hs, Rs, splane, Ns, Nidx;
     int bc[6];
     float T_wall[6];
     float hot_dT, hot_inv2s2, hot_cx, hot_cy;
@@ -192,7 +194,7 @@ __device__ __forceinline__ int node_of(const DevParams& P, int x, int y, int z) 
     return x + P.nx * (y + P.ny * z);
 }
 __device__ __forceinline__ int sidx(const DevParams& P, int x, int y, int z) {
-    return (x + kGX) + P.Ws * ((y + kGY) + P.Hs * z);
+    return (x + kGX) + P.Rs * (y + kGY) + P.splane * z;
 }
 
 // Source coordinate of the pull along one axis for velocity component e (x - e).
@@ -222,9 +224,9 @@ __device__ __forceinline__ float pull_f_one(const DevParams& P, const S* __restr
                                             int x, int y, int z, const Nbr& n) {
     constexpr int ex = ex19(A), ey = ey19(A), ez = ez19(A);
     if (A != 0 && crosses<A>(n.fbb))   // Eq. 50: f_a(x_b, t+1) = f*_{abar}(x_b, t)
-        return Codec<S>::load(src + (size_t)fslot(opp(A)) * P.Ns + bidx(P, i, P.Ns), P.shift_f[opp(A)]);
+        return Codec<S>::load(src + (size_t)fslot(opp(A)) * P.Ns + bidx(P, i, P.Nidx), P.shift_f[opp(A)]);
     int s = sidx(P, src_c(ex, x, n.xm, n.xp), src_c(ey, y, n.ym, n.yp), src_c(ez, z, n.zm, n.zp));
-    return Codec<S>::load(src + (size_t)fslot(A) * P.Ns + bidx(P, s, P.Ns), P.shift_f[A]);
+    return Codec<S>::load(src + (size_t)fslot(A) * P.Ns + bidx(P, s, P.Nidx), P.shift_f[A]);
 }
 
 // Node at least one node away from every face: every pull source is i - (ex + nx ey + nx ny ez).
@@ -236,7 +238,7 @@ __device__ __forceinline__ bool deep_interior(const DevParams& P, int x, int y, 
 template <typename S, int A>
 __device__ __forceinline__ float pull_f_fast(const DevParams& P, const S* __restrict__ src, int i) {
     constexpr int ex = ex19(A), ey = ey19(A), ez = ez19(A);
-    return Codec<S>::load(src + (size_t)fslot(A) * P.Ns + bidx(P, i - ex - ey * P.Ws - ez * P.splane, P.Ns),
+    return Codec<S>::load(src + (size_t)fslot(A) * P.Ns + bidx(P, i - ex - ey * P.Rs - ez * P.splane, P.Nidx),
                           P.shift_f[A]);
 }
 
@@ -260,7 +262,7 @@ __device__ __forceinline__ void load_f(const DevParams& P, const S* __restrict__
 #undef GB300_PULL
     } else {
 #pragma unroll
-        for (int a = 0; a < 19; ++a) f[a] = Codec<S>::load(src + (size_t)fslot(a) * P.Ns + bidx(P, i, P.Ns), P.shift_f[a]);
+        for (int a = 0; a < 19; ++a) f[a] = Codec<S>::load(src + (size_t)fslot(a) * P.Ns + bidx(P, i, P.Nidx), P.shift_f[a]);
     }
 }
 
@@ -271,24 +273,24 @@ __device__ __forceinline__ float pull_g_one(const DevParams& P, const S* __restr
     constexpr int face = ex > 0 ? 0 : ex < 0 ? 1 : ey > 0 ? 2 : ey < 0 ? 3 : ez > 0 ? 4 : 5;
     if (A != 0 && (n.gabb & (1u << face))) {
         // Eq. 51: g_a(x_b, t+1) = -g+_{abar}(x_b, t) + 2 w_abar T_w   (w_abar = w_a on D3Q7)
-        float gp = Codec<S>::load(src + (size_t)gslot(opp(A)) * P.Ns + bidx(P, i, P.Ns), P.shift_g[opp(A)]);
+        float gp = Codec<S>::load(src + (size_t)gslot(opp(A)) * P.Ns + bidx(P, i, P.Nidx), P.shift_g[opp(A)]);
         return -gp + 2.f * P.w1 * wall_T(P, face, x, y);
     }
     int s = sidx(P, src_c(ex, x, n.xm, n.xp), src_c(ey, y, n.ym, n.yp), src_c(ez, z, n.zm, n.zp));
-    return Codec<S>::load(src + (size_t)gslot(A) * P.Ns + bidx(P, s, P.Ns), P.shift_g[A]);
+    return Codec<S>::load(src + (size_t)gslot(A) * P.Ns + bidx(P, s, P.Nidx), P.shift_g[A]);
 }
 
 template <typename S>
 __device__ __forceinline__ void load_g(const DevParams& P, const S* __restrict__ src, int pull, int i,
                                        int x, int y, int z, const Nbr& n, float g[7]) {
     if (pull && deep_interior(P, x, y, z)) {
-        g[0] = Codec<S>::load(src + (size_t)gslot(0) * P.Ns + bidx(P, i, P.Ns), P.shift_g[0]);
-        g[1] = Codec<S>::load(src + (size_t)gslot(1) * P.Ns + bidx(P, i - 1, P.Ns), P.shift_g[1]);
-        g[2] = Codec<S>::load(src + (size_t)gslot(2) * P.Ns + bidx(P, i + 1, P.Ns), P.shift_g[2]);
-        g[3] = Codec<S>::load(src + (size_t)gslot(3) * P.Ns + bidx(P, i - P.Ws, P.Ns), P.shift_g[3]);
-        g[4] = Codec<S>::load(src + (size_t)gslot(4) * P.Ns + bidx(P, i + P.Ws, P.Ns), P.shift_g[4]);
-        g[5] = Codec<S>::load(src + (size_t)gslot(5) * P.Ns + bidx(P, i - P.splane, P.Ns), P.shift_g[5]);
-        g[6] = Codec<S>::load(src + (size_t)gslot(6) * P.Ns + bidx(P, i + P.splane, P.Ns), P.shift_g[6]);
+        g[0] = Codec<S>::load(src + (size_t)gslot(0) * P.Ns + bidx(P, i, P.Nidx), P.shift_g[0]);
+        g[1] = Codec<S>::load(src + (size_t)gslot(1) * P.Ns + bidx(P, i - 1, P.Nidx), P.shift_g[1]);
+        g[2] = Codec<S>::load(src + (size_t)gslot(2) * P.Ns + bidx(P, i + 1, P.Nidx), P.shift_g[2]);
+        g[3] = Codec<S>::load(src + (size_t)gslot(3) * P.Ns + bidx(P, i - P.Rs, P.Nidx), P.shift_g[3]);
+        g[4] = Codec<S>::load(src + (size_t)gslot(4) * P.Ns + bidx(P, i + P.Rs, P.Nidx), P.shift_g[4]);
+        g[5] = Codec<S>::load(src + (size_t)gslot(5) * P.Ns + bidx(P, i - P.splane, P.Nidx), P.shift_g[5]);
+        g[6] = Codec<S>::load(src + (size_t)gslot(6) * P.Ns + bidx(P, i + P.splane, P.Nidx), P.shift_g[6]);
     } else if (pull) {
         g[0] = pull_g_one<S, 0>(P, src, i, x, y, z, n);
         g[1] = pull_g_one<S, 1>(P, src, i, x, y, z, n);
@@ -299,7 +301,7 @@ __device__ __forceinline__ void load_g(const DevParams& P, const S* __restrict__
         g[6] = pull_g_one<S, 6>(P, src, i, x, y, z, n);
     } else {
 #pragma unroll
-        for (int a = 0; a < 7; ++a) g[a] = Codec<S>::load(src + (size_t)gslot(a) * P.Ns + bidx(P, i, P.Ns), P.shift_g[a]);
+        for (int a = 0; a < 7; ++a) g[a] = Codec<S>::load(src + (size_t)gslot(a) * P.Ns + bidx(P, i, P.Nidx), P.shift_g[a]);
     }
 }
 
@@ -307,7 +309,7 @@ __device__ __forceinline__ void load_g(const DevParams& P, const S* __restrict__
 template <typename S>
 __device__ __forceinline__ void store_slots(const DevParams& P, S* __restrict__ dst, int i, const float f[19],
                                             const float g[7]) {
-    S* q = dst + bidx(P, i, P.Ns);
+    S* q = dst + bidx(P, i, P.Nidx);
 #define GB300_ST(V, SH) { Codec<S>::store(q, V, SH); q += P.Ns; }
     GB300_ST(f[0], P.shift_f[0]) GB300_ST(f[1], P.shift_f[1]) GB300_ST(f[2], P.shift_f[2])
     GB300_ST(f[3], P.shift_f[3]) GB300_ST(f[4], P.shift_f[4]) GB300_ST(f[7], P.shift_f[7])
@@ -625,11 +627,11 @@ __device__ __forceinline__ float pull_g19_one(const DevParams& P, const S* __res
     const bool cz = ez > 0 ? (n.gabb & 16u) : ez < 0 ? (n.gabb & 32u) : 0u;
     if (A != 0 && (cx || cy || cz)) {
         const int face = cz ? (ez > 0 ? 4 : 5) : cy ? (ey > 0 ? 2 : 3) : (ex > 0 ? 0 : 1);
-        const float gp = Codec<S>::load(src + (size_t)gslot19(opp(A)) * P.Ns + bidx(P, i, P.Ns), 0.f);
+        const float gp = Codec<S>::load(src + (size_t)gslot19(opp(A)) * P.Ns + bidx(P, i, P.Nidx), 0.f);
         return -gp + 2.f * w19(A) * wall_T(P, face, x, y);
     }
     const int s = sidx(P, src_c(ex, x, n.xm, n.xp), src_c(ey, y, n.ym, n.yp), src_c(ez, z, n.zm, n.zp));
-    return Codec<S>::load(src + (size_t)gslot19(A) * P.Ns + bidx(P, s, P.Ns), 0.f);
+    return Codec<S>::load(src + (size_t)gslot19(A) * P.Ns + bidx(P, s, P.Nidx), 0.f);
 }
 
 template <typename S>
@@ -644,7 +646,7 @@ __device__ __forceinline__ void load_g19(const DevParams& P, const S* __restrict
 #undef GB300_PULL
     } else {
 #pragma unroll
-        for (int a = 0; a < 19; ++a) g[a] = Codec<S>::load(src + (size_t)gslot19(a) * P.Ns + bidx(P, i, P.Ns), 0.f);
+        for (int a = 0; a < 19; ++a) g[a] = Codec<S>::load(src + (size_t)gslot19(a) * P.Ns + bidx(P, i, P.Nidx), 0.f);
     }
 }
 
@@ -652,7 +654,7 @@ __device__ __forceinline__ void load_g19(const DevParams& P, const S* __restrict
 template <typename S>
 __device__ __forceinline__ void store_slots19(const DevParams& P, S* __restrict__ dst, int i, const float f[19],
                                               const float g[19]) {
-    S* q = dst + bidx(P, i, P.Ns);
+    S* q = dst + bidx(P, i, P.Nidx);
 #pragma unroll
     for (int a = 0; a < 19; ++a) Codec<S>::store(q + (size_t)fslot(a) * P.Ns, f[a], 0.f);
 #pragma unroll
@@ -726,7 +728,7 @@ template <> struct Therm<7> {
     template <typename S>
     static __device__ __forceinline__ void stored(const DevParams& P, const S* src, int i, float g[7]) {
 #pragma unroll
-        for (int a = 0; a < 7; ++a) g[a] = Codec<S>::load(src + (size_t)gslot(a) * P.Ns + bidx(P, i, P.Ns), P.shift_g[a]);
+        for (int a = 0; a < 7; ++a) g[a] = Codec<S>::load(src + (size_t)gslot(a) * P.Ns + bidx(P, i, P.Nidx), P.shift_g[a]);
     }
 };
 template <> struct Therm<19> {
@@ -754,7 +756,7 @@ template <> struct Therm<19> {
     template <typename S>
     static __device__ __forceinline__ void stored(const DevParams& P, const S* src, int i, float g[19]) {
 #pragma unroll
-        for (int a = 0; a < 19; ++a) g[a] = Codec<S>::load(src + (size_t)gslot19(a) * P.Ns + bidx(P, i, P.Ns), 0.f);
+        for (int a = 0; a < 19; ++a) g[a] = Codec<S>::load(src + (size_t)gslot19(a) * P.Ns + bidx(P, i, P.Nidx), 0.f);
     }
 };
 

@@ -233,7 +233,7 @@ __device__ __forceinline__ void fused_column(const DevParams& P, const S* __rest
         if (P.flow_off) {
 #pragma unroll
             for (int a = 0; a < 19; ++a)
-                f[a] = Codec<S>::load(src + (size_t)fslot(a) * P.Ns + bidx(P, i, P.Ns), P.shift_f[a]);
+                f[a] = Codec<S>::load(src + (size_t)fslot(a) * P.Ns + bidx(P, i, P.Nidx), P.shift_f[a]);
         }
         if (P.thermal_off) Therm<QT>::template stored<S>(P, src, i, g);
         Therm<QT>::template store<S>(P, dst, i, f, g);
@@ -312,8 +312,10 @@ k_fused_batch(DevParams P, const BatchInst* __restrict__ insts, const BatchItem*
         Q.plane = I.nx * I.ny;
         Q.N = Q.plane * I.nz;
         Q.Ws = I.Ws; Q.Hs = I.Hs;
-        Q.splane = I.Ws * I.Hs;
-        Q.Ns = Q.splane * I.nz;
+        Q.Rs = kSlots * I.Ws;
+        Q.splane = Q.Rs * I.Hs;
+        Q.Ns = I.Ws;
+        Q.Nidx = Q.splane * I.nz - (kSlots - 1) * I.Ws;
         Q.inv_N = I.inv_N;
         Q.hot_cx = 0.5f * (float)I.nx;
         Q.hot_cy = 0.5f * (float)I.ny;
@@ -548,7 +550,7 @@ __device__ __forceinline__ void stage_pulls(const DevParams& P, const typename S
     GB300_SG(0) GB300_SG(1) GB300_SG(2) GB300_SG(3) GB300_SG(4) GB300_SG(5) GB300_SG(6)
 #undef GB300_SG
     if (mz == 0 && P.bc[4] != BC_PERIODIC) {
-        const int i = (int)bidx(P, sidx(P, mx, my, mz), P.Ns);
+        const int i = (int)bidx(P, sidx(P, mx, my, mz), P.Nidx);
         if (P.bc[4] == BC_WALL) {
             f[5] = Codec<S>::load(src + (size_t)fslot(6) * P.Ns + i, P.shift_f[6]);
             f[11] = Codec<S>::load(src + (size_t)fslot(12) * P.Ns + i, P.shift_f[12]);
@@ -559,7 +561,7 @@ __device__ __forceinline__ void stage_pulls(const DevParams& P, const typename S
         g[5] = -Codec<S>::load(src + (size_t)gslot(6) * P.Ns + i, P.shift_g[6]) + 2.f * P.w1 * wall_T(P, 4, mx, my);
     }
     if (mz == P.nz - 1 && P.bc[5] != BC_PERIODIC) {
-        const int i = (int)bidx(P, sidx(P, mx, my, mz), P.Ns);
+        const int i = (int)bidx(P, sidx(P, mx, my, mz), P.Nidx);
         if (P.bc[5] == BC_WALL) {
             f[6] = Codec<S>::load(src + (size_t)fslot(5) * P.Ns + i, P.shift_f[5]);
             f[12] = Codec<S>::load(src + (size_t)fslot(11) * P.Ns + i, P.shift_f[11]);

@@ -21,6 +21,8 @@ int validate(const lbm_params* p);
 // device-side constants of a parameter set (geometry, storage layout, model constants)
 DevParams make_dev(const lbm_params* p);
 bool is_device_ptr(const void* ptr);
+// elements of one population buffer (all slots, ghost cells and padding included)
+inline size_t pop_elems(const DevParams& d) { return (size_t)d.splane * d.nz; }
 
 // NVTX range over the enclosing scope, named for the call (visible in Nsight Systems / Compute
 // timelines; a no-op unless a tool is attached)

@@ -96,8 +96,8 @@ cudaError_t launch_sum_field(const float* a, int n, double2* partial, unsigned* 
 int max_partials(const DevParams& P);
 
 // ---------------------------------------------------------------- batched ensemble
-// Geometry of one instance (device table).  Instance k owns elements [pop_off, pop_off + 26 Ns)
-// of each population buffer (same padded layout as a single lattice) and nodes
+// Geometry of one instance (device table).  Instance k owns the elements [pop_off, pop_off + its
+// population-buffer size) of each population buffer (same padded layout as a single lattice) and nodes
 // [field_off, field_off + N) of the dense fields; its items are item0 .. item0 + n_items - 1.
 struct BatchInst {
     int nx, ny, nz, Ws, Hs;
