@@ -2,9 +2,9 @@
 // of uneven sizes advanced by one persistent kernel launch per time step.
 //
 // Device memory of a batch (one allocation):
-//   pops[2]   population buffers; instance k owns 26 * Ns_k elements at pop_off_k (the padded
-//             slot-grouped layout of a single lattice, so the per-instance set-up and read-out
-//             kernels run unchanged on the instance's block)
+//   pops[2]   population buffers; instance k owns its block at pop_off_k (the padded rows-of-
+//             slots layout of a single lattice, so the per-instance set-up and read-out kernels
+//             run unchanged on the instance's block)
 //   phis      phi_s history, instances concatenated (node offset field_off_k)
 //   psirho    (psi, rho) scratch of the largest instance (read-out only)
 //   sums      (sum rho, sum T) per instance: two ping-pong sets (rho_ave of the next step) and

@@ -93,3 +93,60 @@ def test_16bit_tma_kernel_bit_identical_to_generic(storage, dims):
     for k in tma:
         assert np.array_equal(tma[k], gen[k]), (storage, dims, k)
         assert np.array_equal(tma[k], two[k]), (storage, dims, k)
+
+
+STEPS_LONG = 2000
+# budgets after STEPS_LONG steps: the 16-bit errors grow with the step count (each step re-rounds
+# every population); u is also bounded in lattice units, where BF16 / FP16 resolve it to about
+# the population quantum (2^-9 / 2^-11 of the largest shifted population, a few 1e-3 / 1e-4)
+BUDGET_LONG = {
+    "fp32": dict(rho=1e-3, T=1e-4, u=0.1, u_abs=1e-5, interface=0.05),
+    "fp16": dict(rho=5e-2, T=5e-2, u=3.0, u_abs=2e-3, interface=0.5),
+    "bf16": dict(rho=1e-1, T=2e-1, u=10.0, u_abs=1e-2, interface=2.0),
+}
+
+
+def bubble_nodes(rho, rho_mid, z_interface):
+    """Vapour nodes (rho < rho_mid) below the interface height, away from the heater's first
+    two layers: a nucleated bubble."""
+    zi = int(np.floor(z_interface)) if np.isfinite(z_interface) else rho.shape[0]
+    return int((rho[2:max(2, zi - 2)] < rho_mid).sum())
+
+
+@pytest.fixture(scope="module")
+def downscaled_long():
+    case = W.pool_boiling_downscaled()
+    s = case["setup"]
+    rho, T, u = inputs(case)
+    ref = run_oracle(s, rho, T, u, STEPS_LONG)
+    Tc = oracle.Tc_of(s)
+    rl, rv, _ = oracle.maxwell(s, 0.86 * Tc)
+    return dict(case=case, rho=rho, T=T, u=u, ref=ref, Tc=Tc, mid=0.5 * (rl + rv))
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
+def test_shifted_storage_long_horizon_vs_fp64_oracle(downscaled_long, storage):
+    """Config-4 error study at a long horizon: per-field error of each storage format against the
+    FP64 oracle after 2000 steps of the 64 x 64 x 96 downscaled pool (rho, T, u relative, u in
+    lattice units, interface height), and the bubble-departure step, which this copy does not
+    have: no bubble nucleates in the oracle within the horizon, and none may appear in the GPU
+    run (16-bit noise must not nucleate one)."""
+    d = downscaled_long
+    s = d["case"]["setup"]
+    over = {}
+    if storage != "fp32":
+        over = dict(precision=PREC[storage], rho_ref=float(np.mean(d["rho"])), T_ref=0.86 * d["Tc"])
+    gpu, tot = run_gpu(s, d["rho"], d["T"], d["u"], STEPS_LONG, **over)
+    err = rel_errors(gpu, d["ref"])
+    err["u_abs"] = max(float(np.max(np.abs(gpu[k].astype(np.float64) - d["ref"][k]))) for k in ("ux", "uy", "uz"))
+    u_scale = max(float(np.max(np.abs(d["ref"][k]))) for k in ("ux", "uy", "uz"))
+    zi_ref = interface_height(d["ref"]["rho"], d["mid"])
+    zi = interface_height(gpu["rho"], d["mid"])
+    err["interface"] = abs(zi - zi_ref)
+    b_ref = bubble_nodes(d["ref"]["rho"], d["mid"], zi_ref)
+    b_gpu = bubble_nodes(gpu["rho"], d["mid"], zi)
+    print(f"storage {storage} steps {STEPS_LONG} errors {err} u_scale {u_scale:.3e} interface_ref {zi_ref:.4f} "
+          f"bubble nodes oracle {b_ref} gpu {b_gpu} mass {tot[0]:.9e}")
+    assert b_ref == 0 and b_gpu == 0, (b_ref, b_gpu)
+    for k, v in err.items():
+        assert np.isfinite(v) and v <= BUDGET_LONG[storage][k], (storage, k, v, err)
