@@ -289,20 +289,28 @@ int lbm_batch_create(const lbm_params* common, int n_instances, const int* dims,
 long long lbm_batch_nodes(const lbm_batch* b, int instance);
 int lbm_batch_init_fields(lbm_batch* b, const float* rho, const float* T, const float* u);
 int lbm_batch_step(lbm_batch* b, int n);
-/* Time every candidate work plan (tile rows 4 or 8, columns split into 1, 2 or 4 z-chunks)
- * over `steps` steps of the current state, keep the fastest, and restore the state exactly
+/* Time every candidate work plan (tile rows 4 or 8, columns split into 1, 2 or 4 z-chunks, and
+ * the TMA mode) over `steps` steps of the current state, keep the fastest, and restore the state exactly
  * (the candidates' steps are undone).  Needs free device memory for one copy of the state.
  * best_ms (nullable) receives the chosen plan's time per step. */
 int lbm_batch_autotune(lbm_batch* b, int steps, double* best_ms);
-/* the plan in use: tile rows, z-chunks per column, work items, persistent CTAs (each nullable) */
+/* the plan in use: tile rows, z-chunks per column, work items, persistent CTAs (each nullable).
+ * Tile rows 0 and z-chunks 0: the TMA mode (one TMA-kernel launch per instance, each with its
+ * own tile shape and whole-column items, the launches fanned out over 32 streams that fork from
+ * and join the batch's stream); items and CTAs are then the totals over the instances. */
 int lbm_batch_plan(const lbm_batch* b, int* tile_rows, int* z_split, int* items, int* ctas);
-/* Select a plan by its tile rows (4 or 8) and z-chunks per column (1, 2 or 4); LBM_EINVAL if
- * there is no such plan. */
+/* Select a plan by its tile rows (4 or 8) and z-chunks per column (1, 2 or 4), or the TMA mode
+ * (0, 0); LBM_EINVAL if there is no such plan, LBM_ESTATE if an instance cannot run the TMA
+ * kernel.  lbm_batch_autotune times the TMA mode beside the batched-kernel plans. */
 int lbm_batch_select_plan(lbm_batch* b, int tile_rows, int z_split);
 int lbm_batch_get_moments(lbm_batch* b, float* rho, float* ux, float* uy, float* uz, float* T);
 /* sums[2k] = sum of rho, sums[2k+1] = sum of T over instance k (FP64, host pointer) */
 int lbm_batch_get_totals(lbm_batch* b, double* sums);
 long long lbm_batch_steps_done(const lbm_batch* b);
+/* Kernel launches that one step of the current plan enqueues once the state is streamed: 1 for
+ * a persistent batched-kernel plan; in the TMA mode one per instance plus one ghost refresh for
+ * each instance whose tiles do not write their own ghost cells.  LBM_EINVAL if b is NULL. */
+int lbm_batch_launches_per_step(const lbm_batch* b);
 void lbm_batch_destroy(lbm_batch* b);
 
 /* Release everything the context owns.  NULL is ignored. */

@@ -18,6 +18,12 @@
 // one instance are contiguous; instances are ordered by size, largest first, so that the atomic
 // work counter hands out the longest items first.  lbm_batch_autotune times every candidate plan
 // on the current state (which it restores afterwards) and keeps the fastest.
+//
+// TMA mode (the last plan, tile rows 0): every instance runs the single-lattice TMA kernel on its
+// own block (its own tensor maps, tile shape and whole-column items, partial-sum range and
+// reduction counter), one launch per instance, fanned out over kSide streams that fork from and
+// join the batch's stream, so that the launches of many instances share the GPU.  Instances whose
+// tiles cannot write their periodic ghost cells get the ghost refresh kernel after their launch.
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -40,7 +46,10 @@ struct Plan {
     int ty, zsplit;
 };
 const Plan kPlans[] = {{8, 1}, {8, 2}, {4, 1}, {4, 2}, {8, 4}, {4, 4}};
-const int kNumPlans = (int)(sizeof(kPlans) / sizeof(kPlans[0]));
+const int kNumPlans = (int)(sizeof(kPlans) / sizeof(kPlans[0]));   // persistent batched-kernel plans
+const int kTmaPlan = kNumPlans;                                     // TMA mode
+const int kSide = 32;                                               // side streams of the TMA mode
+const int kTmaChain = 8;                                            // steps of one TMA-mode graph (even)
 
 struct BatchGraph {
     int n, cur, slot, plan;
@@ -68,10 +77,19 @@ struct lbm_batch {
     long long steps;
     BatchGraph graphs[kBatchGraphs];
     int n_graphs;
+    // TMA mode
+    std::vector<TmaMaps> tmaps;        // per instance (built when the mode is selected)
+    std::vector<int> t_part, t_cap;    // first partial slot / item capacity of each instance
+    int t_items;                       // items of all instances
+    int t_launches;                    // kernel launches of one step (TMA launches + ghost refreshes)
+    cudaStream_t side[kSide];
+    cudaEvent_t fork, join[kSide];
+    bool side_ok;
+    bool ghosts_valid;                 // ghost cells of the current buffer hold their periodic images
 
     char* pbuf(int k) { return base + off_pops[k]; }
     double* sums(int k) { return (double*)(base + off_sums) + (size_t)k * 2 * n; }   // k = 0, 1: ping-pong; 2: totals
-    unsigned* counters() { return (unsigned*)(base + off_counters); }
+    unsigned* counters() { return (unsigned*)(base + off_counters); }   // [0..3] shared, [4 + k] instance k
     float* phis() { return (float*)(base + off_phis); }
     BatchInst* d_inst() { return (BatchInst*)(base + off_inst); }
     BatchItem* d_items() { return (BatchItem*)(base + off_items); }
@@ -135,8 +153,49 @@ void drop_batch_graphs(lbm_batch* b) {
     b->n_graphs = 0;
 }
 
+// TMA mode: tensor maps and plan of every instance (the tile shape with the least padded volume
+// per node rate, whole-column items); LBM_ESTATE if an instance does not qualify.
+int set_tma_plan(lbm_batch* b) {
+    if (!b->side_ok) {
+        for (int q = 0; q < kSide; ++q) GB300_CK(cudaStreamCreateWithFlags(&b->side[q], cudaStreamNonBlocking));
+        GB300_CK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+        for (int q = 0; q < kSide; ++q) GB300_CK(cudaEventCreateWithFlags(&b->join[q], cudaEventDisableTiming));
+        b->side_ok = true;
+    }
+    long long cap = 0;
+    for (int k = 0; k < b->n; ++k) cap += b->t_cap[k];
+    if (cap > b->max_partial) return fail(LBM_ESTATE, "the TMA mode needs %lld partial sums, the batch holds %d", cap,
+                                          b->max_partial);
+    const size_t pb = pop_bytes(b->p.precision);
+    b->tmaps.assign(b->n, TmaMaps());
+    b->t_part.assign(b->n, 0);
+    int off = 0, ctas = 0, launches = 0;
+    for (int k = 0; k < b->n; ++k) {
+        const DevParams& d = b->dps[k];
+        const size_t po = (size_t)b->inst[k].pop_off * pb;
+        const bool tma = build_tma_maps(d, b->p.precision, b->pbuf(0) + po, b->pbuf(1) + po, 1, -1, d.nz,
+                                        b->t_cap[k], &b->tmaps[k]);
+        if (!tma && !fused_supported(d))
+            return fail(LBM_ESTATE, "instance %d (%d x %d x %d) runs neither the TMA nor the generic fused kernel", k,
+                        d.nx, d.ny, d.nz);
+        b->t_part[k] = off;
+        off += b->t_cap[k];
+        launches += tma && !b->tmaps[k].ghosts ? 2 : 1;
+        ctas += tma ? std::min(b->tmaps[k].items, b->tmaps[k].sms) : (int)fused_blocks(d);
+    }
+    b->t_items = off;
+    b->t_launches = launches;
+    b->n_items = 0;
+    for (int k = 0; k < b->n; ++k) b->n_items += b->tmaps[k].ok ? b->tmaps[k].items : (int)fused_blocks(b->dps[k]);
+    b->ctas = ctas;
+    b->plan = kTmaPlan;
+    drop_batch_graphs(b);
+    return LBM_OK;
+}
+
 // Upload the instance and item tables of plan `plan` and size the persistent grid.
 int set_plan(lbm_batch* b, int plan) {
+    if (plan == kTmaPlan) return set_tma_plan(b);
     const Plan& pl = kPlans[plan];
     std::vector<BatchItem> items;
     items.reserve(b->max_items);
@@ -154,12 +213,66 @@ int set_plan(lbm_batch* b, int plan) {
     return LBM_OK;
 }
 
+// m steps in TMA mode: the instances are independent, so each one's chain of m steps (the TMA
+// kernel once its state is streamed, the generic fused kernel on the first step, the ghost
+// refresh where its tiles do not write their ghost cells) runs on one side stream, round robin
+// over the side streams by size; the side streams fork from and join the batch's stream once.
+int enqueue_tma_steps(lbm_batch* b, int m) {
+    cudaError_t e = cudaEventRecord(b->fork, b->launch);
+    for (int q = 0; q < kSide && e == cudaSuccess; ++q) e = cudaStreamWaitEvent(b->side[q], b->fork, 0);
+    const bool fresh0 = b->first || (b->fresh_f && !b->p.flow_off) || (b->fresh_g && !b->p.thermal_off);
+    for (int idx = 0; idx < b->n && e == cudaSuccess; ++idx) {
+        const int k = b->order[idx];
+        cudaStream_t s = b->side[idx % kSide];
+        const TmaMaps* maps = &b->tmaps[k];
+        StateBufs B0 = b->bufs(k);
+        // a state the batched kernel wrote: refresh its ghost cells before the first TMA launch
+        if (!fresh0 && !b->ghosts_valid && maps->ok) e = launch_ghosts(b->dps[k], b->p.precision, (void*)B0.src, s);
+        for (int j = 0; j < m && e == cudaSuccess; ++j) {
+            const int cur = b->cur ^ (j & 1), slot = b->slot ^ (j & 1);
+            // a frozen field (flow_off / thermal_off) keeps its un-streamed form on every step
+            const bool ff = b->fresh_f && (j == 0 || b->p.flow_off), fg = b->fresh_g && (j == 0 || b->p.thermal_off);
+            StateBufs B = B0;
+            const size_t po = (size_t)b->inst[k].pop_off * pop_bytes(b->p.precision);
+            B.src = b->pbuf(cur) + po;
+            B.dst = b->pbuf(cur ^ 1) + po;
+            B.src_index = cur;
+            B.pull_f = ff ? 0 : 1;
+            B.pull_g = fg ? 0 : 1;
+            B.partial += b->t_part[k];
+            B.counter = b->counters() + 4 + k;
+            bool ghosts_done = false;
+            e = launch_fused(b->dps[k], b->p.precision, B, b->sums(slot) + 2 * k, b->sums(slot ^ 1) + 2 * k,
+                             j == 0 && b->first ? 1 : 0, s, maps, &ghosts_done);
+            // the next TMA launch reads ghost cells (the generic kernel wraps its pulls itself)
+            if (e == cudaSuccess && !ghosts_done && maps->ok) e = launch_ghosts(b->dps[k], b->p.precision, B.dst, s);
+        }
+    }
+    for (int q = 0; q < kSide && e == cudaSuccess; ++q) {
+        e = cudaEventRecord(b->join[q], b->side[q]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->launch, b->join[q], 0);
+    }
+    if (e != cudaSuccess) return fail(LBM_ECUDA, "TMA-mode steps: %s", cudaGetErrorString(e));
+    if (m > 0) {
+        b->ghosts_valid = true;
+        b->cur ^= m & 1;
+        b->slot ^= m & 1;
+        if (!b->p.flow_off) b->fresh_f = false;
+        if (!b->p.thermal_off) b->fresh_g = false;
+        b->first = false;
+        b->steps += m;
+    }
+    return LBM_OK;
+}
+
 int enqueue_batch_step(lbm_batch* b) {
+    if (b->plan == kTmaPlan) return enqueue_tma_steps(b, 1);
     StateBufs B = b->bufs(-1);
     cudaError_t e = launch_fused_batch(b->dps[0], b->p.precision, kPlans[b->plan].ty, b->d_inst(), b->d_items(),
                                        b->n_items, b->n, B, b->sums(b->slot), b->sums(b->slot ^ 1),
                                        b->first ? 1 : 0, b->ctas, b->launch);
     if (e != cudaSuccess) return fail(LBM_ECUDA, "batched kernel launch: %s", cudaGetErrorString(e));
+    b->ghosts_valid = false;   // the batched kernel does not write ghost cells
     b->cur ^= 1;
     b->slot ^= 1;
     if (!b->p.flow_off) b->fresh_f = false;
@@ -169,25 +282,29 @@ int enqueue_batch_step(lbm_batch* b) {
     return LBM_OK;
 }
 
-int run_batch_graph(lbm_batch* b, int n) {
+// Graph of m steps from the current (cur, slot), captured on first use.
+int batch_graph(lbm_batch* b, int m, cudaGraphExec_t* out) {
     BatchGraph* hit = nullptr;
     for (int k = 0; k < b->n_graphs; ++k) {
         BatchGraph& g = b->graphs[k];
-        if (g.n == n && g.cur == b->cur && g.slot == b->slot && g.plan == b->plan) hit = &g;
+        if (g.n == m && g.cur == b->cur && g.slot == b->slot && g.plan == b->plan) hit = &g;
     }
     if (!hit) {
         const int c0 = b->cur, s0 = b->slot;
-        const bool ff = b->fresh_f, fg = b->fresh_g, fi = b->first;
+        const bool ff = b->fresh_f, fg = b->fresh_g, fi = b->first, gv = b->ghosts_valid;
         const long long st = b->steps;
         if (!b->capture) GB300_CK(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking));
         cudaGraph_t graph;
         GB300_CK(cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal));
         b->launch = b->capture;
         int rc = LBM_OK;
-        for (int k = 0; k < n && rc == LBM_OK; ++k) rc = enqueue_batch_step(b);
+        if (b->plan == kTmaPlan) rc = enqueue_tma_steps(b, m);
+        else
+            for (int k = 0; k < m && rc == LBM_OK; ++k) rc = enqueue_batch_step(b);
         cudaError_t e = cudaStreamEndCapture(b->capture, &graph);
         b->launch = b->stream;
         b->cur = c0; b->slot = s0; b->fresh_f = ff; b->fresh_g = fg; b->first = fi; b->steps = st;
+        b->ghosts_valid = gv;
         if (rc != LBM_OK) { if (e == cudaSuccess) cudaGraphDestroy(graph); return rc; }
         if (e != cudaSuccess) return fail(LBM_ECUDA, "graph capture: %s", cudaGetErrorString(e));
         cudaGraphExec_t exec;
@@ -200,16 +317,32 @@ int run_batch_graph(lbm_batch* b, int n) {
             --b->n_graphs;
         }
         BatchGraph& g = b->graphs[b->n_graphs++];
-        g.n = n; g.cur = b->cur; g.slot = b->slot; g.plan = b->plan; g.exec = exec;
+        g.n = m; g.cur = b->cur; g.slot = b->slot; g.plan = b->plan; g.exec = exec;
         hit = &g;
     }
-    GB300_CK(cudaGraphLaunch(hit->exec, b->stream));
-    for (int k = 0; k < n; ++k) {
-        b->cur ^= 1;
-        b->slot ^= 1;
-    }
-    b->steps += n;
+    *out = hit->exec;
     return LBM_OK;
+}
+
+// n steps by graph replay: one graph of all n steps for a persistent plan (one node a step); in
+// the TMA mode (hundreds of launches a step) a graph of kTmaChain steps replayed n / kTmaChain
+// times, the remaining steps enqueued directly.
+int run_batch_graph(lbm_batch* b, int n) {
+    const int m = b->plan == kTmaPlan ? std::min(n, kTmaChain) : n;
+    cudaGraphExec_t exec = nullptr;
+    int rc = batch_graph(b, m, &exec);
+    if (rc) return rc;
+    for (int r = 0; r < n / m; ++r) {
+        GB300_CK(cudaGraphLaunch(exec, b->stream));
+        for (int k = 0; k < m; ++k) {   // m is even or n == m: (cur, slot) match the graph again
+            b->cur ^= 1;
+            b->slot ^= 1;
+        }
+        b->steps += m;
+        b->ghosts_valid = b->plan == kTmaPlan;   // the batched kernel does not write ghost cells
+    }
+    if (n % m) rc = b->plan == kTmaPlan ? enqueue_tma_steps(b, n % m) : enqueue_batch_step(b);
+    return rc;
 }
 
 int check_batch_flag(lbm_batch* b) {
@@ -286,6 +419,21 @@ int lbm_batch_create(const lbm_params* common, int n_instances, const int* dims,
     for (int q = 0; q < kNumPlans; ++q) b->max_items = std::max(b->max_items, items_of_plan(b, kPlans[q], nullptr, nullptr));
     b->max_partial = b->max_items;
     for (int k = 0; k < n_instances; ++k) b->max_partial = std::max(b->max_partial, max_partials(b->dps[k]));
+    // TMA mode: whole-column items, at most the tiles of the smallest tile shape per instance
+    // (or the blocks of the generic fused kernel, which runs an instance's first step and every
+    // step of an instance the TMA kernel cannot take)
+    b->t_cap.assign(n_instances, 0);
+    long long t_total = 0;
+    for (int k = 0; k < n_instances; ++k) {
+        const DevParams& d = b->dps[k];
+        b->t_cap[k] = (int)std::min<long long>(fused_blocks(d), 1 << 30);
+        for (int sh = 0; sh < tma_num_shapes(); ++sh) {
+            const int tiles = ((d.nx + tma_tile_w(sh) - 1) / tma_tile_w(sh)) * ((d.ny + tma_tile_h(sh) - 1) / tma_tile_h(sh));
+            b->t_cap[k] = std::max(b->t_cap[k], tiles);
+        }
+        t_total += b->t_cap[k];
+    }
+    if (t_total < (1LL << 30)) b->max_partial = std::max(b->max_partial, (int)t_total);
 
     const size_t pb = pop_bytes(common->precision);
     size_t off = 0;
@@ -296,13 +444,17 @@ int lbm_batch_create(const lbm_params* common, int n_instances, const int* dims,
     b->off_psirho = take(8 * (size_t)b->max_N);
     b->off_sums = take(sizeof(double) * 6 * (size_t)n_instances);
     b->off_partial = take(sizeof(double2) * (size_t)b->max_partial);
-    b->off_counters = take(4 * sizeof(unsigned));
+    b->off_counters = take((4 + (size_t)n_instances) * sizeof(unsigned));
     b->off_flag = take(sizeof(int));
     b->off_inst = take(sizeof(BatchInst) * (size_t)n_instances);
     b->off_items = take(sizeof(BatchItem) * (size_t)b->max_items);
     b->stream = (cudaStream_t)common->cuda_stream;
     b->launch = b->stream;
     b->capture = nullptr;
+    b->side_ok = false;
+    b->ghosts_valid = false;
+    b->t_items = 0;
+    b->t_launches = 0;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
@@ -370,6 +522,7 @@ int lbm_batch_init_fields(lbm_batch* b, const float* rho, const float* T, const 
     GB300_CK(cudaStreamSynchronize(b->stream));
     b->fresh_f = b->fresh_g = true;
     b->first = true;
+    b->ghosts_valid = false;
     b->initialised = true;
     b->steps = 0;
     return LBM_OK;
@@ -411,7 +564,7 @@ int lbm_batch_autotune(lbm_batch* b, int steps, double* best_ms) {
         return fail(LBM_ENOMEM, "autotune state copy: %s", cudaGetErrorString(e));
     }
     const int c0 = b->cur, s0 = b->slot;
-    const bool ff = b->fresh_f, fg = b->fresh_g, fi = b->first;
+    const bool ff = b->fresh_f, fg = b->fresh_g, fi = b->first, gv = b->ghosts_valid;
     const long long st = b->steps;
     auto save_or_restore = [&](bool restore) -> cudaError_t {
         char* a[3] = {b->pbuf(c0), (char*)b->phis(), (char*)b->sums(0)};
@@ -431,12 +584,18 @@ int lbm_batch_autotune(lbm_batch* b, int steps, double* best_ms) {
     float best_t = -1.f;
     e = save_or_restore(false);
     if (e != cudaSuccess) rc = fail(LBM_ECUDA, "autotune save: %s", cudaGetErrorString(e));
-    for (int q = 0; q < kNumPlans && rc == LBM_OK; ++q) {
+    for (int q = 0; q <= kTmaPlan && rc == LBM_OK; ++q) {
         rc = set_plan(b, q);
+        if (rc && q == kTmaPlan) {   // an instance the TMA kernel cannot run: not a candidate
+            rc = LBM_OK;
+            break;
+        }
         if (rc) break;
         rc = enqueue_batch_step(b);   // warm-up
         cudaEventRecord(ev[0], b->stream);
-        for (int k = 0; k < steps && rc == LBM_OK; ++k) rc = enqueue_batch_step(b);
+        if (q == kTmaPlan && rc == LBM_OK) rc = enqueue_tma_steps(b, steps);
+        else
+            for (int k = 0; k < steps && rc == LBM_OK; ++k) rc = enqueue_batch_step(b);
         cudaEventRecord(ev[1], b->stream);
         if (cudaEventSynchronize(ev[1]) != cudaSuccess) rc = fail(LBM_ECUDA, "autotune timing failed");
         float ms = 0.f;
@@ -448,6 +607,7 @@ int lbm_batch_autotune(lbm_batch* b, int steps, double* best_ms) {
         e = save_or_restore(true);
         if (e != cudaSuccess && rc == LBM_OK) rc = fail(LBM_ECUDA, "autotune restore: %s", cudaGetErrorString(e));
         b->cur = c0; b->slot = s0; b->fresh_f = ff; b->fresh_g = fg; b->first = fi; b->steps = st;
+        b->ghosts_valid = gv;
     }
     cudaStreamSynchronize(b->stream);
     cudaEventDestroy(ev[0]);
@@ -464,8 +624,8 @@ int lbm_batch_autotune(lbm_batch* b, int steps, double* best_ms) {
 
 int lbm_batch_plan(const lbm_batch* b, int* tile_rows, int* z_split, int* items, int* ctas) {
     if (!b) return fail(LBM_EINVAL, "batch is NULL");
-    if (tile_rows) *tile_rows = kPlans[b->plan].ty;
-    if (z_split) *z_split = kPlans[b->plan].zsplit;
+    if (tile_rows) *tile_rows = b->plan == kTmaPlan ? 0 : kPlans[b->plan].ty;
+    if (z_split) *z_split = b->plan == kTmaPlan ? 0 : kPlans[b->plan].zsplit;
     if (items) *items = b->n_items;
     if (ctas) *ctas = b->ctas;
     return LBM_OK;
@@ -473,6 +633,7 @@ int lbm_batch_plan(const lbm_batch* b, int* tile_rows, int* z_split, int* items,
 
 int lbm_batch_select_plan(lbm_batch* b, int tile_rows, int z_split) {
     if (!b) return fail(LBM_EINVAL, "batch is NULL");
+    if (tile_rows == 0 && z_split == 0) return set_plan(b, kTmaPlan);
     for (int q = 0; q < kNumPlans; ++q)
         if (kPlans[q].ty == tile_rows && kPlans[q].zsplit == z_split) return set_plan(b, q);
     return fail(LBM_EINVAL, "no plan with tile rows %d and %d z-chunks", tile_rows, z_split);
@@ -516,10 +677,22 @@ int lbm_batch_get_totals(lbm_batch* b, double* sums) {
 
 long long lbm_batch_steps_done(const lbm_batch* b) { return b ? b->steps : 0; }
 
+int lbm_batch_launches_per_step(const lbm_batch* b) {
+    if (!b) return fail(LBM_EINVAL, "batch is NULL");
+    return b->plan == kTmaPlan ? b->t_launches : 1;
+}
+
 void lbm_batch_destroy(lbm_batch* b) {
     if (!b) return;
     drop_batch_graphs(b);
     if (b->capture) cudaStreamDestroy(b->capture);
+    if (b->side_ok) {
+        for (int q = 0; q < kSide; ++q) {
+            cudaStreamDestroy(b->side[q]);
+            cudaEventDestroy(b->join[q]);
+        }
+        cudaEventDestroy(b->fork);
+    }
     if (b->base) cudaFree(b->base);
     delete b;
 }

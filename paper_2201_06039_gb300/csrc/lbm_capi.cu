@@ -423,17 +423,20 @@ int check_flag(lbm_ctx* c) {
     return LBM_OK;
 }
 
-bool make_tma_maps(lbm_ctx* c) {
-    c->maps.ok = false;
-    if (!tma_eligible(c->dp, c->p.precision)) return false;
+}  // namespace
+
+bool gb300lbm::build_tma_maps(const DevParams& d, int precision, void* buf0, void* buf1, int model_ctas,
+                              int forced_shape, int forced_zchunk, int max_items, TmaMaps* maps) {
+    maps->ok = false;
+    if (!tma_eligible(d, precision)) return false;
     int dev = 0, sms = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return false;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
     int shape = -1, zchunk = 0, items = 0;
-    tma_plan_for(c->dp, sms, c->plan_shape, c->plan_zchunk, &shape, &zchunk, &items);
-    if (shape < 0 || (size_t)optin < tma_smem_bytes(shape, c->p.precision)) return false;
-    if (items > max_partials(c->dp)) return false;
+    tma_plan_for(d, model_ctas > 0 ? model_ctas : sms, forced_shape, forced_zchunk, &shape, &zchunk, &items);
+    if (shape < 0 || (size_t)optin < tma_smem_bytes(shape, precision)) return false;
+    if (items > max_items) return false;
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
@@ -442,14 +445,13 @@ bool make_tma_maps(lbm_ctx* c) {
         return false;
     }
     EncodeTiledFn encode = (EncodeTiledFn)fn;
-    const DevParams& d = c->dp;
     cuuint64_t dims[4] = {(cuuint64_t)d.Ws, (cuuint64_t)d.Hs, (cuuint64_t)d.nz, (cuuint64_t)kSlots};
-    const cuuint64_t E = (cuuint64_t)pop_bytes(c->p.precision);
-    const CUtensorMapDataType dt = c->p.precision == LBM_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                 : c->p.precision == LBM_BF16_SHIFTED ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+    const cuuint64_t E = (cuuint64_t)pop_bytes(precision);
+    const CUtensorMapDataType dt = precision == LBM_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : precision == LBM_BF16_SHIFTED ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                                       : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     cuuint64_t strides[3] = {(cuuint64_t)d.Rs * E, (cuuint64_t)d.splane * E, (cuuint64_t)d.Ns * E};
-    const cuuint32_t bw = (cuuint32_t)tma_box_w(shape, c->p.precision), bh = (cuuint32_t)tma_box_h(shape);
+    const cuuint32_t bw = (cuuint32_t)tma_box_w(shape, precision), bh = (cuuint32_t)tma_box_h(shape);
     cuuint32_t box14[4] = {bw, bh, 1, 14}, box6[4] = {bw, bh, 1, 6}, es[4] = {1, 1, 1, 1};
     // output tiles, dimensions ordered (x, slot, y, z) to match the [row][slot][x] out buffer; the
     // tensor spans the real nodes only (x < nx, y < ny in storage coordinates + the offsets), and
@@ -462,48 +464,55 @@ bool make_tma_maps(lbm_ctx* c) {
     // ghost boxes over the whole padded plane (they always lie inside it)
     const int tw = tma_tile_w(shape), rx = d.nx - tw * ((d.nx - 1) / tw);
     cuuint64_t dims_pad[4] = {(cuuint64_t)d.Ws, (cuuint64_t)kSlots, (cuuint64_t)d.Hs, (cuuint64_t)d.nz};
-    const cuuint32_t gw = (cuuint32_t)tma_ghost_cols(c->p.precision);
+    const cuuint32_t gw = (cuuint32_t)tma_ghost_cols(precision);
     cuuint32_t box_gcol[4] = {gw, (cuuint32_t)kSlots, (cuuint32_t)th, 1};
     cuuint32_t box_gcol_top[4] = {gw, (cuuint32_t)kSlots, (cuuint32_t)ry, 1};
     cuuint32_t box_grow[4] = {(cuuint32_t)tw, (cuuint32_t)kSlots, 2, 1};
     cuuint32_t box_grow_right[4] = {(cuuint32_t)rx, (cuuint32_t)kSlots, 2, 1};
     cuuint32_t box_gcor[4] = {gw, (cuuint32_t)kSlots, 2, 1};
-    c->maps.ghosts = tma_ghosts_in_kernel(d, shape, c->p.precision);
+    maps->ghosts = tma_ghosts_in_kernel(d, shape, precision);
     for (int k = 0; k < 2; ++k) {
-        void* g = c->pbuf(k);
-        if (encode(&c->maps.m14[k], dt, 4, g, dims, strides, box14, es,
+        void* g = k == 0 ? buf0 : buf1;
+        if (encode(&maps->m14[k], dt, 4, g, dims, strides, box14, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;
-        if (encode(&c->maps.m6[k], dt, 4, g, dims, strides, box6, es,
+        if (encode(&maps->m6[k], dt, 4, g, dims, strides, box6, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;
-        if (encode(&c->maps.mout[k], dt, 4, g, dims_out, strides_out, box_out, es,
+        if (encode(&maps->mout[k], dt, 4, g, dims_out, strides_out, box_out, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;
-        if (encode(&c->maps.mout_top[k], dt, 4, g, dims_out, strides_out, box_top, es,
+        if (encode(&maps->mout_top[k], dt, 4, g, dims_out, strides_out, box_top, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;
-        if (c->maps.ghosts) {
-            CUtensorMap* gm[5] = {&c->maps.mgcol[k], &c->maps.mgcol_top[k], &c->maps.mgrow[k], &c->maps.mgrow_right[k],
-                                  &c->maps.mgcor[k]};
+        if (maps->ghosts) {
+            CUtensorMap* gm[5] = {&maps->mgcol[k], &maps->mgcol_top[k], &maps->mgrow[k], &maps->mgrow_right[k],
+                                  &maps->mgcor[k]};
             cuuint32_t* gb[5] = {box_gcol, box_gcol_top, box_grow, box_grow_right, box_gcor};
             for (int q = 0; q < 5; ++q)
                 if (encode(gm[q], dt, 4, g, dims_pad, strides_out, gb[q], es,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-                    c->maps.ghosts = false;
+                    maps->ghosts = false;
         }
     }
-    c->maps.sms = sms;
-    c->maps.shape = shape;
-    c->maps.zchunk = zchunk;
-    c->maps.items = items;
-    c->maps.ok = true;
+    maps->sms = sms;
+    maps->shape = shape;
+    maps->zchunk = zchunk;
+    maps->items = items;
+    maps->ok = true;
     return true;
+}
+
+namespace {
+
+bool make_tma_maps(lbm_ctx* c) {
+    return build_tma_maps(c->dp, c->p.precision, c->pbuf(0), c->pbuf(1), 0, c->plan_shape, c->plan_zchunk,
+                          max_partials(c->dp), &c->maps);
 }
 
 }  // namespace

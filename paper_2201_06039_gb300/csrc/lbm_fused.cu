@@ -1062,12 +1062,13 @@ int zchunk_generic(const DevParams& P, int tiles) {
 
 }  // namespace
 
-bool fused_supported(const DevParams& P) {
+long long fused_blocks(const DevParams& P) {
     int tiles = ((P.nx + TX - 1) / TX) * ((P.ny + kTY - 1) / kTY);
     int zc = zchunk_generic(P, tiles);
-    long long blocks = (long long)tiles * ((P.nz + zc - 1) / zc);
-    return blocks <= (long long)max_partials(P);
+    return (long long)tiles * ((P.nz + zc - 1) / zc);
 }
+
+bool fused_supported(const DevParams& P) { return fused_blocks(P) <= (long long)max_partials(P); }
 
 cudaError_t launch_ghosts(const DevParams& P, int precision, void* pops, cudaStream_t s) {
     const int per_plane = (P.ny + 4) * kSlots + 4 * kSlots * ((P.nx + 3) / 4);

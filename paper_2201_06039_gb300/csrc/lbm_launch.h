@@ -58,6 +58,15 @@ struct TmaMaps {
     int shape, zchunk, items;   // plan of tma_plan_for
 };
 
+// Tensor maps and plan of the TMA kernel for one lattice whose two population buffers start at
+// buf0 / buf1: the tile shape and z-chunk of tma_plan_for (forced_shape / forced_zchunk >= 0 / > 0
+// pin them; the model spreads the items over model_ctas persistent CTAs, the device's SM count if
+// <= 0).  false (maps->ok false) if the lattice does not qualify, the shape does not fit the
+// device, or the plan has more than max_items items (the capacity of the caller's partial-sum
+// buffer).
+bool build_tma_maps(const DevParams& d, int precision, void* buf0, void* buf1, int model_ctas, int forced_shape,
+                    int forced_zchunk, int max_items, TmaMaps* maps);
+
 // fused z-marching variant (psi of the tile halo recomputed from the populations); uses the
 // TMA kernel when maps are given and the lattice / state qualify (see tma_eligible).
 // *ghosts_written (nullable) tells whether the launch also refreshed the ghost cells of dst.
@@ -65,6 +74,8 @@ cudaError_t launch_fused(const DevParams& P, int precision, const StateBufs& B, 
                          double* sums_next, int first, cudaStream_t s, const TmaMaps* maps,
                          bool* ghosts_written = nullptr);
 bool fused_supported(const DevParams& P);
+// CTAs (partial sums) of one generic fused launch on P
+long long fused_blocks(const DevParams& P);
 bool tma_eligible(const DevParams& P, int precision);
 // refresh the ghost columns / rows of a population buffer from their periodic images
 cudaError_t launch_ghosts(const DevParams& P, int precision, void* pops, cudaStream_t s);

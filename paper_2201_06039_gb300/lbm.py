@@ -57,7 +57,7 @@ EXPORTS = ["lbm_params_default", "lbm_eos_critical", "lbm_workspace_bytes", "lbm
            "lbm_state_bytes", "lbm_save_state", "lbm_load_state", "lbm_set_wall_map",
            "lbm_batch_create", "lbm_batch_nodes", "lbm_batch_init_fields", "lbm_batch_step", "lbm_batch_autotune",
            "lbm_batch_plan", "lbm_batch_select_plan", "lbm_batch_get_moments", "lbm_batch_get_totals",
-           "lbm_batch_steps_done", "lbm_batch_destroy"]
+           "lbm_batch_steps_done", "lbm_batch_launches_per_step", "lbm_batch_destroy"]
 
 _lib = None
 
@@ -127,6 +127,7 @@ def lib(build_if_missing: bool = True):
     L.lbm_batch_get_totals.argtypes = [vp, dp]
     L.lbm_batch_steps_done.argtypes = [vp]
     L.lbm_batch_steps_done.restype = C.c_longlong
+    L.lbm_batch_launches_per_step.argtypes = [vp]
     L.lbm_batch_destroy.argtypes = [vp]
     L.lbm_batch_destroy.restype = None
     _lib = L
@@ -325,7 +326,8 @@ def lbm_batch_plan(b):
 
 
 def lbm_batch_select_plan(b, tile_rows: int, z_split: int):
-    """Select a work plan: tile rows 4 or 8, columns split into 1, 2 or 4 z-chunks."""
+    """Select a work plan: tile rows 4 or 8, columns split into 1, 2 or 4 z-chunks; (0, 0) selects
+    the TMA mode (one TMA-kernel launch per instance over 32 streams)."""
     _check(lib().lbm_batch_select_plan(b, tile_rows, z_split), "lbm_batch_select_plan")
 
 
@@ -341,6 +343,13 @@ def lbm_batch_get_totals(b, n_instances: int) -> np.ndarray:
 
 def lbm_batch_steps_done(b) -> int:
     return lib().lbm_batch_steps_done(b)
+
+
+def lbm_batch_launches_per_step(b) -> int:
+    """Kernel launches one step of the current plan enqueues (1 for a persistent batched plan)."""
+    n = lib().lbm_batch_launches_per_step(b)
+    _check(n if n < 0 else 0, "lbm_batch_launches_per_step")
+    return n
 
 
 def lbm_batch_destroy(b):

@@ -85,10 +85,12 @@ def test_batch_matches_single_lattices():
             assert v <= 1e-6, (c["name"], k, v)
 
 
-@pytest.mark.parametrize("plan", [(8, 1), (4, 2), (8, 4)])
+@pytest.mark.parametrize("plan", [(8, 1), (4, 2), (8, 4), (0, 0)])
 def test_batch_plans_bit_identical_to_single_lattices(plan):
     """Every work plan gives each instance exactly the state of its own single-lattice context
-    (the TMA kernel where the instance qualifies, the generic fused kernel otherwise)."""
+    (the TMA kernel where the instance qualifies, the generic fused kernel otherwise).  Plan
+    (0, 0) is the TMA mode: a TMA launch per instance (with the ghost refresh where its tiles do
+    not write their ghost cells), the generic fused kernel for the 5 x 3 x 2 box, on 32 streams."""
     from paper_2201_06039_gb300 import lbm
     cases = _cases()
     rho, T = _fields(cases)
@@ -119,7 +121,7 @@ def test_autotune_restores_state_and_keeps_results():
     before = b.moments()
     ms = b.autotune(2)
     plan = b.plan
-    assert ms > 0 and plan["tile_rows"] in (4, 8) and plan["z_split"] in (1, 2, 4)
+    assert ms > 0 and (plan["tile_rows"], plan["z_split"]) in [(4, 1), (4, 2), (4, 4), (8, 1), (8, 2), (8, 4), (0, 0)]
     assert plan["items"] >= len(cases) and plan["ctas"] >= 1
     after = b.moments()
     for x, y in zip(before, after):
@@ -173,3 +175,33 @@ def test_batch_of_256_ensemble_instances_steps_finite():
     tot = b.totals()
     b.close()
     assert np.all(np.isfinite(tot))
+
+
+def test_batch_tma_mode_graph_replay_and_switching():
+    """The TMA mode under CUDA-graph replay, entered from a state the persistent batched kernel
+    wrote (its ghost cells refreshed first) and left again, matches one plan run throughout."""
+    from paper_2201_06039_gb300 import lbm
+    cases = _cases()
+    rho, T = _fields(cases)
+    b = _batch(cases)
+    b.select_plan(8, 1)
+    b.init(rho, T)
+    b.step(7)
+    b.select_plan(0, 0)
+    assert lbm.lbm_batch_launches_per_step(b.b) >= len(cases)
+    b.step(12)                 # graph of 12 TMA-mode steps
+    b.step(12)                 # replayed
+    b.select_plan(4, 2)
+    b.step(5)
+    got = b.moments()
+    b.close()
+    ref = _batch(cases)
+    ref.select_plan(8, 1)
+    assert lbm.lbm_batch_launches_per_step(ref.b) == 1
+    ref.init(rho, T)
+    ref.step(36)
+    want = ref.moments()
+    ref.close()
+    for x, y in zip(got, want):
+        for k in x:
+            assert np.array_equal(x[k], y[k]), k
