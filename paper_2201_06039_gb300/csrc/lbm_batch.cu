@@ -153,8 +153,11 @@ void drop_batch_graphs(lbm_batch* b) {
     b->n_graphs = 0;
 }
 
-// TMA mode: tensor maps and plan of every instance (the tile shape with the least padded volume
-// per node rate, whole-column items); LBM_ESTATE if an instance does not qualify.
+// TMA mode: tensor maps and plan of every instance: whole-column items, and the tile shape the
+// plan model picks for a lattice alone on the GPU (for these sizes, the smallest tile per node
+// rate: most CTAs, so that the largest instances finish soonest; on the 256-instance ensemble
+// 13.1k MLUPS against 12.5k with the least padded volume per node rate).  LBM_ESTATE if an
+// instance runs neither the TMA nor the generic fused kernel.
 int set_tma_plan(lbm_batch* b) {
     if (!b->side_ok) {
         for (int q = 0; q < kSide; ++q) GB300_CK(cudaStreamCreateWithFlags(&b->side[q], cudaStreamNonBlocking));
@@ -173,7 +176,7 @@ int set_tma_plan(lbm_batch* b) {
     for (int k = 0; k < b->n; ++k) {
         const DevParams& d = b->dps[k];
         const size_t po = (size_t)b->inst[k].pop_off * pb;
-        const bool tma = build_tma_maps(d, b->p.precision, b->pbuf(0) + po, b->pbuf(1) + po, 1, -1, d.nz,
+        const bool tma = build_tma_maps(d, b->p.precision, b->pbuf(0) + po, b->pbuf(1) + po, 0, -1, d.nz,
                                         b->t_cap[k], &b->tmaps[k]);
         if (!tma && !fused_supported(d))
             return fail(LBM_ESTATE, "instance %d (%d x %d x %d) runs neither the TMA nor the generic fused kernel", k,
