@@ -470,7 +470,7 @@ bool gb300lbm::build_tma_maps(const DevParams& d, int precision, void* buf0, voi
     cuuint32_t box_grow[4] = {(cuuint32_t)tw, (cuuint32_t)kSlots, 2, 1};
     cuuint32_t box_grow_right[4] = {(cuuint32_t)rx, (cuuint32_t)kSlots, 2, 1};
     cuuint32_t box_gcor[4] = {gw, (cuuint32_t)kSlots, 2, 1};
-    maps->ghosts = tma_ghosts_in_kernel(d, shape, precision);
+    maps->ghosts = tma_ghost_mode(d, shape, precision);
     for (int k = 0; k < 2; ++k) {
         void* g = k == 0 ? buf0 : buf1;
         if (encode(&maps->m14[k], dt, 4, g, dims, strides, box14, es,
@@ -489,7 +489,7 @@ bool gb300lbm::build_tma_maps(const DevParams& d, int precision, void* buf0, voi
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return false;
-        if (maps->ghosts) {
+        if (maps->ghosts == 1) {
             CUtensorMap* gm[5] = {&maps->mgcol[k], &maps->mgcol_top[k], &maps->mgrow[k], &maps->mgrow_right[k],
                                   &maps->mgcor[k]};
             cuuint32_t* gb[5] = {box_gcol, box_gcol_top, box_grow, box_grow_right, box_gcor};
@@ -497,7 +497,7 @@ bool gb300lbm::build_tma_maps(const DevParams& d, int precision, void* buf0, voi
                 if (encode(gm[q], dt, 4, g, dims_pad, strides_out, gb[q], es,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-                    maps->ghosts = false;
+                    maps->ghosts = precision == 0 ? 2 : 0;
         }
     }
     maps->sms = sms;

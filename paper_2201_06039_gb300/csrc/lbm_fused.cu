@@ -721,16 +721,20 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
             // ghost cells written from this tile (storage coordinates; every box lies inside
             // the padded plane exactly): its 4 edge columns to the opposite ghost columns, its
             // 2 edge rows to the opposite ghost rows, and the corner block
-            const bool left = ghosts && x0 == 0, right = ghosts && x0 + TX_ >= P.nx;
-            const bool bottom = ghosts && y0 == 0, top = ghosts && y0 + TY_ >= P.ny;
+            const bool left = ghosts == 1 && x0 == 0, right = ghosts == 1 && x0 + TX_ >= P.nx;
+            const bool bottom = ghosts == 1 && y0 == 0, top = ghosts == 1 && y0 + TY_ >= P.ny;
             const int gx_col = right ? kGX - kGW : P.nx + kGX;    // destination of the column box
             const int gy_row = top ? kGY - 2 : P.ny + kGY;        // destination of the row box
             const CUtensorMap* mc = y0 + TY_ > P.ny ? &map_gcol_top : &map_gcol;
             const CUtensorMap* mr = x0 + TX_ > P.nx ? &map_grow_right : &map_grow;
+            // ghost mode 2, nx no multiple of the 16-byte band: the last tile column stores its
+            // nodes itself (a tensor store clipped at nx inside a 16-byte unit also writes the
+            // ghost columns past nx, which the first tile column's nodes write)
+            const bool direct_tile = ghosts == 2 && x0 + TX_ > P.nx && P.nx % kGW != 0;
             for (int p = z0 - 1; p <= z1; ++p, ++k) {
                 const int s = k % kStages;
                 nb_sync(bar_out_full(s), Sh::kCntOut);
-                if (p > z0 && lane == 0 && !abort_flag) {   // the stage holds collided plane p - 1
+                if (p > z0 && lane == 0 && !abort_flag && !direct_tile) {   // the stage holds collided plane p - 1
                     const int z = p - 1;
                     unsigned char* st = smem_raw + (size_t)s * Sh::kStageOne;
                     tma_store_4d(m, st, x0 + kGX, 0, y0 + kGY, z);
@@ -777,8 +781,14 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
             const int mx = used ? map_coord(gx, P.nx, P.bc[0], P.bc[1]) : 0;
             const int my = used ? map_coord(gy, P.ny, P.bc[2], P.bc[3]) : 0;
             // this node's place in the ghost staging tiles of an edge tile (-1: none)
-            const bool eright = ghosts && x0 + TX_ >= P.nx, eleft = ghosts && x0 == 0;
-            const bool etop = ghosts && y0 + TY_ >= P.ny, ebottom = ghosts && y0 == 0;
+            const bool eright = ghosts == 1 && x0 + TX_ >= P.nx, eleft = ghosts == 1 && x0 == 0;
+            const bool etop = ghosts == 1 && y0 + TY_ >= P.ny, ebottom = ghosts == 1 && y0 == 0;
+            // ghost mode 2: this node's periodic images in the ghost columns (hx) and rows (hy)
+            const bool hx = ghosts == 2 && owner && (gx < 2 || gx >= P.nx - 2);
+            const bool hy = ghosts == 2 && owner && (gy < 2 || gy >= P.ny - 2);
+            const int ix = gx < 2 ? gx + P.nx : gx - P.nx, iy = gy < 2 ? gy + P.ny : gy - P.ny;
+            // ... and the last tile column of such a lattice stores its nodes directly (see storer)
+            const bool direct_tile = ghosts == 2 && x0 + TX_ > P.nx && P.nx % kGW != 0;
             const int cx4 = !owner ? -1 : eright ? (gx >= P.nx - kGW ? gx - (P.nx - kGW) : -1)
                                         : eleft ? (gx < kGW ? gx : -1) : -1;
             const int ry2 = !owner ? -1 : etop ? (gy >= P.ny - 2 ? gy - (P.ny - 2) : -1)
@@ -838,10 +848,18 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                         for (int a = 0; a < 19; ++a) fe[a] = st_enc<S>(fc[a], P.shift_f[a]);
 #pragma unroll
                         for (int a = 0; a < 7; ++a) ge[a] = st_enc<S>(gc[a], P.shift_g[a]);
+                        if (direct_tile) {
+                            S* q = dst + bidx(P, sidx(P, gx, gy, z), P.Nidx);
 #pragma unroll
-                        for (int a = 0; a < 19; ++a) outp[fslot(a) * TX_] = fe[a];
+                            for (int a = 0; a < 19; ++a) q[(size_t)fslot(a) * P.Ns] = fe[a];
 #pragma unroll
-                        for (int a = 0; a < 7; ++a) outp[gslot(a) * TX_] = ge[a];
+                            for (int a = 0; a < 7; ++a) q[(size_t)gslot(a) * P.Ns] = ge[a];
+                        } else {
+#pragma unroll
+                            for (int a = 0; a < 19; ++a) outp[fslot(a) * TX_] = fe[a];
+#pragma unroll
+                            for (int a = 0; a < 7; ++a) outp[gslot(a) * TX_] = ge[a];
+                        }
                         if (cx4 >= 0) {   // edge column: [TY][26][kGW]
                             S* q = sb + Sh::kGColOff / sizeof(S) + (ly - 1) * (kSlots * kGW) + cx4;
 #pragma unroll
@@ -862,6 +880,18 @@ k_fused_tma(const __grid_constant__ CUtensorMap map14, const __grid_constant__ C
                             for (int a = 0; a < 19; ++a) q[fslot(a) * kGW] = fe[a];
 #pragma unroll
                             for (int a = 0; a < 7; ++a) q[gslot(a) * kGW] = ge[a];
+                        }
+                        if (hx || hy) {   // ghost mode 2: straight to the images in dst
+                            auto put = [&](int qx, int qy) {
+                                S* q = dst + bidx(P, sidx(P, qx, qy, z), P.Nidx);
+#pragma unroll
+                                for (int a = 0; a < 19; ++a) q[(size_t)fslot(a) * P.Ns] = fe[a];
+#pragma unroll
+                                for (int a = 0; a < 7; ++a) q[(size_t)gslot(a) * P.Ns] = ge[a];
+                            };
+                            if (hx) put(ix, gy);
+                            if (hy) put(gx, iy);
+                            if (hx && hy) put(ix, iy);
                         }
                     }
                     // this thread's out writes become visible to the tensor store (async proxy)
@@ -1130,12 +1160,13 @@ int tma_box_w(int shape, int precision) { return kTmaTX[shape] + 2 * (precision 
 int tma_box_h(int shape) { return kTmaTY[shape] + 4; }
 int tma_tile_w(int shape) { return kTmaTX[shape]; }
 int tma_ghost_cols(int precision) { return precision == 0 ? 4 : 8; }   // 16 bytes of columns
-bool tma_ghosts_in_kernel(const DevParams& P, int shape, int precision) {
+int tma_ghost_mode(const DevParams& P, int shape, int precision) {
     const int tx = tma_tile_w(shape), ty = kTmaTY[shape], gw = tma_ghost_cols(precision);
-    // ghost-column boxes (gw columns = 16 bytes) on 16-byte boundaries, at least two tiles per
-    // axis (an edge tile is never both left and right, top and bottom), edge tiles at least gw
-    // columns and 2 rows wide, and room for the gw ghost columns past nx in the padded rows
-    return P.nx % gw == 0 && P.nx > tx && P.ny > ty && P.ny % ty != 1 && P.Ws >= P.nx + kGX + gw;
+    // TMA ghost boxes: ghost-column boxes (gw columns = 16 bytes) on 16-byte boundaries, at least
+    // two tiles per axis (an edge tile is never both left and right, top and bottom), edge tiles at
+    // least gw columns and 2 rows wide, and room for the gw ghost columns past nx in the padded rows
+    if (P.nx % gw == 0 && P.nx > tx && P.ny > ty && P.ny % ty != 1 && P.Ws >= P.nx + kGX + gw) return 1;
+    return precision == 0 ? 2 : 0;   // direct stores of the images (FP32), else the refresh kernel
 }
 int tma_tile_h(int shape) { return kTmaTY[shape]; }
 
@@ -1149,7 +1180,7 @@ cudaError_t launch_fused(const DevParams& P, int precision, const StateBufs& B, 
         const int tx = kTmaTX[maps->shape], ty = kTmaTY[maps->shape];
         const int txs = (P.nx + tx - 1) / tx, tys = (P.ny + ty - 1) / ty;
         const int ctas = maps->sms < maps->items ? maps->sms : maps->items;
-        if (ghosts_written) *ghosts_written = maps->ghosts;
+        if (ghosts_written) *ghosts_written = maps->ghosts != 0;
 #define GB300_TMA(TXV, TYV, ST, WET)                                                                           \
         {                                                                                                      \
             using SH = TmaShape<TXV, TYV, ST>;                                                                 \
@@ -1160,7 +1191,7 @@ cudaError_t launch_fused(const DevParams& P, int precision, const StateBufs& B, 
                 maps->m14[B.src_index], maps->m6[B.src_index], maps->mout[B.src_index ^ 1],                    \
                 maps->mout_top[B.src_index ^ 1], maps->mgcol[B.src_index ^ 1], maps->mgcol_top[B.src_index ^ 1], \
                 maps->mgrow[B.src_index ^ 1], maps->mgrow_right[B.src_index ^ 1], maps->mgcor[B.src_index ^ 1], \
-                maps->ghosts ? 1 : 0, P, (const ST*)B.src, (ST*)B.dst, sums_cur, B.partial, B.counter,          \
+                maps->ghosts, P, (const ST*)B.src, (ST*)B.dst, sums_cur, B.partial, B.counter,                  \
                 sums_next, B.phis,                                                                             \
                 B.flag, first, maps->zchunk, txs, tys, maps->items);                                           \
         }

@@ -52,7 +52,10 @@ struct TmaMaps {
     // x rows of the last tile row), edge-row box TX x 26 x 2 (and x columns of the last tile
     // column), corner box gw x 26 x 2, gw = 16 bytes of columns
     CUtensorMap mgcol[2], mgcol_top[2], mgrow[2], mgrow_right[2], mgcor[2];
-    bool ghosts;   // the TMA kernel writes the ghost cells itself (no refresh kernel)
+    // ghost cells after a TMA step: 1 the edge tiles store them by TMA, 2 the edge nodes store their
+    // periodic images directly (FP32 lattices whose nx is no multiple of the 16-byte band, or with
+    // one tile across an axis), 0 the refresh kernel writes them
+    int ghosts;
     bool ok;
     int sms;
     int shape, zchunk, items;   // plan of tma_plan_for
@@ -91,7 +94,7 @@ size_t tma_smem_bytes(int shape, int precision);
 int tma_box_w(int shape, int precision);
 int tma_box_h(int shape);
 int tma_tile_w(int shape);
-bool tma_ghosts_in_kernel(const DevParams& P, int shape, int precision);
+int tma_ghost_mode(const DevParams& P, int shape, int precision);
 int tma_ghost_cols(int precision);
 int tma_tile_h(int shape);
 
