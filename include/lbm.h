@@ -296,7 +296,7 @@ int lbm_batch_step(lbm_batch* b, int n);
 int lbm_batch_autotune(lbm_batch* b, int steps, double* best_ms);
 /* the plan in use: tile rows, z-chunks per column, work items, persistent CTAs (each nullable).
  * Tile rows 0 and z-chunks 0: the TMA mode (one TMA-kernel launch per instance, each with its
- * own tile shape and whole-column items, the launches fanned out over 32 streams that fork from
+ * own tile shape and whole-column items, the launches fanned out over 48 streams that fork from
  * and join the batch's stream); items and CTAs are then the totals over the instances. */
 int lbm_batch_plan(const lbm_batch* b, int* tile_rows, int* z_split, int* items, int* ctas);
 /* Select a plan by its tile rows (4 or 8) and z-chunks per column (1, 2 or 4), or the TMA mode

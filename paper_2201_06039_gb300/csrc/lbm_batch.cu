@@ -48,11 +48,12 @@ struct Plan {
 const Plan kPlans[] = {{8, 1}, {8, 2}, {4, 1}, {4, 2}, {8, 4}, {4, 4}};
 const int kNumPlans = (int)(sizeof(kPlans) / sizeof(kPlans[0]));   // persistent batched-kernel plans
 const int kTmaPlan = kNumPlans;                                     // TMA mode
-const int kSide = 32;                                               // side streams of the TMA mode
+const int kSide = 48;   // side streams of the TMA mode (16: 14.4k, 32: 15.3k, 48: 15.5k, 64: 14.8k MLUPS)
 const int kTmaChain = 8;                                            // steps of one TMA-mode graph (even)
 
 struct BatchGraph {
     int n, cur, slot, plan;
+    bool ghosts_valid;
     cudaGraphExec_t exec;
 };
 const int kBatchGraphs = 4;
@@ -80,6 +81,7 @@ struct lbm_batch {
     // TMA mode
     std::vector<TmaMaps> tmaps;        // per instance (built when the mode is selected)
     std::vector<int> t_part, t_cap;    // first partial slot / item capacity of each instance
+    std::vector<int> t_order, t_stream;   // launch order (longest first) and side stream of each instance
     int t_items;                       // items of all instances
     int t_launches;                    // kernel launches of one step (TMA launches + ghost refreshes)
     cudaStream_t side[kSide];
@@ -153,11 +155,12 @@ void drop_batch_graphs(lbm_batch* b) {
     b->n_graphs = 0;
 }
 
-// TMA mode: tensor maps and plan of every instance: whole-column items, and the tile shape the
-// plan model picks for a lattice alone on the GPU (for these sizes, the smallest tile per node
-// rate: most CTAs, so that the largest instances finish soonest; on the 256-instance ensemble
-// 13.1k MLUPS against 12.5k with the least padded volume per node rate).  LBM_ESTATE if an
-// instance runs neither the TMA nor the generic fused kernel.
+// TMA mode: tensor maps and plan of every instance: whole-column items and the tile shape with
+// the least padded volume per node rate (the plan model for one CTA: the instances share the
+// GPU; on the 256-instance ensemble 15.2k MLUPS against 14.4k for the model's single-lattice
+// choice, the smallest tile); then the instances go to the side streams longest first, each to
+// the stream with the least modelled work so far, so that the streams reach each join together.
+// LBM_ESTATE if an instance runs neither the TMA nor the generic fused kernel.
 int set_tma_plan(lbm_batch* b) {
     if (!b->side_ok) {
         for (int q = 0; q < kSide; ++q) GB300_CK(cudaStreamCreateWithFlags(&b->side[q], cudaStreamNonBlocking));
@@ -176,7 +179,7 @@ int set_tma_plan(lbm_batch* b) {
     for (int k = 0; k < b->n; ++k) {
         const DevParams& d = b->dps[k];
         const size_t po = (size_t)b->inst[k].pop_off * pb;
-        const bool tma = build_tma_maps(d, b->p.precision, b->pbuf(0) + po, b->pbuf(1) + po, 0, -1, d.nz,
+        const bool tma = build_tma_maps(d, b->p.precision, b->pbuf(0) + po, b->pbuf(1) + po, 1, -1, d.nz,
                                         b->t_cap[k], &b->tmaps[k]);
         if (!tma && !fused_supported(d))
             return fail(LBM_ESTATE, "instance %d (%d x %d x %d) runs neither the TMA nor the generic fused kernel", k,
@@ -188,6 +191,23 @@ int set_tma_plan(lbm_batch* b) {
     }
     b->t_items = off;
     b->t_launches = launches;
+    // modelled work of each instance (padded nodes over the tile shape's node rate), streams by LPT
+    std::vector<double> work(b->n), load(kSide, 0.0);
+    for (int k = 0; k < b->n; ++k) {
+        const TmaMaps& m = b->tmaps[k];
+        const DevParams& d = b->dps[k];
+        work[k] = m.ok ? (double)m.items * tma_tile_w(m.shape) * tma_tile_h(m.shape) * (d.nz + 2) / tma_rate(m.shape)
+                       : 1.5 * (double)d.N;
+    }
+    b->t_order.resize(b->n);
+    std::iota(b->t_order.begin(), b->t_order.end(), 0);
+    std::stable_sort(b->t_order.begin(), b->t_order.end(), [&](int a, int c) { return work[a] > work[c]; });
+    b->t_stream.assign(b->n, 0);
+    for (int k : b->t_order) {
+        const int q = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        b->t_stream[k] = q;
+        load[q] += work[k];
+    }
     b->n_items = 0;
     for (int k = 0; k < b->n; ++k) b->n_items += b->tmaps[k].ok ? b->tmaps[k].items : (int)fused_blocks(b->dps[k]);
     b->ctas = ctas;
@@ -218,15 +238,15 @@ int set_plan(lbm_batch* b, int plan) {
 
 // m steps in TMA mode: the instances are independent, so each one's chain of m steps (the TMA
 // kernel once its state is streamed, the generic fused kernel on the first step, the ghost
-// refresh where its tiles do not write their ghost cells) runs on one side stream, round robin
-// over the side streams by size; the side streams fork from and join the batch's stream once.
+// refresh where its tiles do not write their ghost cells) runs on its side stream (assigned by
+// set_tma_plan), longest first; the side streams fork from and join the batch's stream once.
 int enqueue_tma_steps(lbm_batch* b, int m) {
     cudaError_t e = cudaEventRecord(b->fork, b->launch);
     for (int q = 0; q < kSide && e == cudaSuccess; ++q) e = cudaStreamWaitEvent(b->side[q], b->fork, 0);
     const bool fresh0 = b->first || (b->fresh_f && !b->p.flow_off) || (b->fresh_g && !b->p.thermal_off);
     for (int idx = 0; idx < b->n && e == cudaSuccess; ++idx) {
-        const int k = b->order[idx];
-        cudaStream_t s = b->side[idx % kSide];
+        const int k = b->t_order[idx];
+        cudaStream_t s = b->side[b->t_stream[k]];
         const TmaMaps* maps = &b->tmaps[k];
         StateBufs B0 = b->bufs(k);
         // a state the batched kernel wrote: refresh its ghost cells before the first TMA launch
@@ -290,7 +310,8 @@ int batch_graph(lbm_batch* b, int m, cudaGraphExec_t* out) {
     BatchGraph* hit = nullptr;
     for (int k = 0; k < b->n_graphs; ++k) {
         BatchGraph& g = b->graphs[k];
-        if (g.n == m && g.cur == b->cur && g.slot == b->slot && g.plan == b->plan) hit = &g;
+        if (g.n == m && g.cur == b->cur && g.slot == b->slot && g.plan == b->plan && g.ghosts_valid == b->ghosts_valid)
+            hit = &g;
     }
     if (!hit) {
         const int c0 = b->cur, s0 = b->slot;
@@ -320,7 +341,7 @@ int batch_graph(lbm_batch* b, int m, cudaGraphExec_t* out) {
             --b->n_graphs;
         }
         BatchGraph& g = b->graphs[b->n_graphs++];
-        g.n = m; g.cur = b->cur; g.slot = b->slot; g.plan = b->plan; g.exec = exec;
+        g.n = m; g.cur = b->cur; g.slot = b->slot; g.plan = b->plan; g.ghosts_valid = b->ghosts_valid; g.exec = exec;
         hit = &g;
     }
     *out = hit->exec;
@@ -331,6 +352,12 @@ int batch_graph(lbm_batch* b, int m, cudaGraphExec_t* out) {
 // the TMA mode (hundreds of launches a step) a graph of kTmaChain steps replayed n / kTmaChain
 // times, the remaining steps enqueued directly.
 int run_batch_graph(lbm_batch* b, int n) {
+    if (b->plan == kTmaPlan && !b->ghosts_valid && n > 0) {
+        // a state the batched kernel wrote: one step with the ghost refresh outside the graph,
+        // so that the replayed graph carries none
+        const int rc = enqueue_tma_steps(b, 1);
+        if (rc || --n == 0) return rc;
+    }
     const int m = b->plan == kTmaPlan ? std::min(n, kTmaChain) : n;
     cudaGraphExec_t exec = nullptr;
     int rc = batch_graph(b, m, &exec);

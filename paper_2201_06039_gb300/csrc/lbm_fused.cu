@@ -1127,6 +1127,7 @@ void tma_plan_for(const DevParams& P, int ctas, int forced_shape, int forced_zch
 }
 
 int tma_num_shapes() { return kNumTmaShapes; }
+double tma_rate(int shape) { return kTmaRate[shape]; }
 
 int tma_zchunk_candidates(const DevParams& P, int ctas, int shape, int* zcs, int max) {
     // the z-chunks of the shape in increasing modelled cost (distinct, at least 16 planes unless

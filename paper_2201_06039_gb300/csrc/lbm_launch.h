@@ -88,6 +88,8 @@ cudaError_t launch_ghosts(const DevParams& P, int precision, void* pops, cudaStr
 void tma_plan_for(const DevParams& P, int ctas, int forced_shape, int forced_zchunk, int* shape, int* zchunk,
                   int* items);
 int tma_num_shapes();
+// the plan model's node rate of a tile shape (relative to 32 x 8)
+double tma_rate(int shape);
 // up to max z-chunks of a shape, best modelled first (returns how many)
 int tma_zchunk_candidates(const DevParams& P, int ctas, int shape, int* zcs, int max);
 size_t tma_smem_bytes(int shape, int precision);

@@ -327,7 +327,7 @@ def lbm_batch_plan(b):
 
 def lbm_batch_select_plan(b, tile_rows: int, z_split: int):
     """Select a work plan: tile rows 4 or 8, columns split into 1, 2 or 4 z-chunks; (0, 0) selects
-    the TMA mode (one TMA-kernel launch per instance over 32 streams)."""
+    the TMA mode (one TMA-kernel launch per instance over 48 streams)."""
     _check(lib().lbm_batch_select_plan(b, tile_rows, z_split), "lbm_batch_select_plan")
 
 

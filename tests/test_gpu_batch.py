@@ -90,7 +90,7 @@ def test_batch_plans_bit_identical_to_single_lattices(plan):
     """Every work plan gives each instance exactly the state of its own single-lattice context
     (the TMA kernel where the instance qualifies, the generic fused kernel otherwise).  Plan
     (0, 0) is the TMA mode: a TMA launch per instance (with the ghost refresh where its tiles do
-    not write their ghost cells), the generic fused kernel for the 5 x 3 x 2 box, on 32 streams."""
+    not write their ghost cells), the generic fused kernel for the 5 x 3 x 2 box, on 48 streams."""
     from paper_2201_06039_gb300 import lbm
     cases = _cases()
     rho, T = _fields(cases)
