@@ -176,9 +176,10 @@ def init_fields(case):
     return rho.astype(np.float32), T.astype(np.float32)
 
 
-def cpu_baseline_run(case, budget_s=20.0, steps=None, warm=1):
+def cpu_baseline_run(case, budget_s=20.0, steps=None, warm=1, one_thread=True):
     """Time the FP64 oracle on a bounded sample: a z-slab of the same workload sized so that one
-    step takes about budget_s / steps seconds (all host cores through OpenMP)."""
+    step takes about budget_s / steps seconds (all host cores through OpenMP), then (one_thread)
+    the same slab on one thread."""
     import oracle
     s = case["setup"]
     probe_nodes = 200 * 200 * 10
@@ -204,11 +205,42 @@ def cpu_baseline_run(case, budget_s=20.0, steps=None, warm=1):
     o.step(n)
     dt = time.perf_counter() - t0
     mlups = sub_setup.n_nodes * n / dt / 1e6
+    cores = oracle.num_threads()
+    if not one_thread:
+        o.close()
+        return dict(value=mlups, unit="MLUPS", cores=cores, kind="oracle", sample="sizing probe", seconds=dt)
+    # the same slab on one thread (a few steps, bounded to about budget_s / 2 seconds)
+    oracle.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        o.step(1)
+        one = time.perf_counter() - t0
+        n1 = max(1, min(10, int(0.5 * budget_s / max(one, 1e-3))))
+        t0 = time.perf_counter()
+        o.step(n1)
+        mlups_1 = sub_setup.n_nodes * n1 / (time.perf_counter() - t0) / 1e6
+    finally:
+        oracle.set_num_threads(cores)
     o.close()
-    return dict(value=mlups, unit="MLUPS", cores=oracle.num_threads(), kind="oracle",
+    return dict(value=mlups, unit="MLUPS", cores=cores, kind="oracle",
                 sample=f"{n} steps of a {s.nx}x{s.ny}x{nz_probe} z-slab of the same workload (same "
                        f"boundaries and parameters), FP64, after {warm + 1} warm-up steps",
-                seconds=dt)
+                value_1_thread=mlups_1, steps_1_thread=n1, cpu_model=cpu_model(), seconds=dt)
+
+
+def cpu_model():
+    """The host CPU as lscpu names it (model name, or vendor and part on Arm), and its core count."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        f = {}
+        for line in out.splitlines():
+            if ":" in line:
+                k, v = line.split(":", 1)
+                f.setdefault(k.strip(), v.strip())
+        name = f.get("Model name") or f.get("Vendor ID") or "unknown"
+        return f"{name}, {os.cpu_count()} logical CPUs"
+    except Exception:
+        return f"unknown, {os.cpu_count()} logical CPUs"
 
 
 def run_reference(args):
@@ -221,7 +253,7 @@ def run_reference(args):
     total_budget = 150.0
     per_step_budget = total_budget / max(1, args.steps + args.warmup)
     # size a z-slab of the workload so that one oracle step fits the per-step budget
-    probe = cpu_baseline_run(case, steps=1, warm=0)
+    probe = cpu_baseline_run(case, steps=1, warm=0, one_thread=False)
     nodes = max(s.nx * s.ny * 2, int(probe["value"] * 1e6 * per_step_budget))
     nz = max(2, min(s.nz, nodes // (s.nx * s.ny)))
     sub = dict(case)

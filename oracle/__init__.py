@@ -112,6 +112,8 @@ def _bind(L):
     L.orc_fd_divergence.argtypes = [C.POINTER(OrcParams), dp, dp]
     L.orc_fd_divergence.restype = None
     L.orc_num_threads.restype = C.c_int
+    L.orc_set_num_threads.argtypes = [C.c_int]
+    L.orc_set_num_threads.restype = None
     return L
 
 
@@ -345,3 +347,8 @@ def fd_divergence(setup, u: np.ndarray) -> np.ndarray:
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's following calls (OpenMP)."""
+    lib().orc_set_num_threads(int(n))

@@ -909,3 +909,12 @@ int orc_num_threads(void) {
     return 1;
 #endif
 }
+
+/* threads of the following calls (n >= 1; no effect without OpenMP) */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
